@@ -1,0 +1,19 @@
+"""Seeded synthetic inputs (ReLU MLP implicit surfaces and seed rays).
+
+This package only *builds* networks and rays from seeds.  It holds none of
+the meshing arithmetic, so that both the CPU oracle and the CUDA path can
+consume the same inputs without sharing any code of the method itself.
+"""
+from .nets import (  # noqa: F401
+    MLP,
+    octahedron,
+    polytope_max_of_planes,
+    fibonacci_normals,
+    geometric_init,
+    sphere_net,
+    decoder_net,
+    batch_nets,
+    proposal_target_net,
+    tiny_net,
+    seed_rays,
+)
