@@ -1,0 +1,180 @@
+/*
+ * analytic_marching.h -- C ABI of the GB300 analytic-marching library.
+ *
+ * Analytic marching (Lei, Jia & Ma, arXiv 2106.10031) extracts the exact polygon mesh of
+ * the zero level set of a ReLU MLP F = f o T (Sec. 2, Sec. 3).  Every linear region
+ * (cell) of the MLP is labelled by its activation pattern s (Def. 2); inside a cell F is
+ * affine (Lemma 1, Cor. 1), the cell is the polyhedron of Eq. 10 and its face is the
+ * polygon of Eq. 12.  Algorithm 1 walks from cell to cell across the edges of the faces,
+ * flipping the state of the neuron that carries each edge.
+ *
+ * The calls follow Algorithm 1's statement of the problem: INPUT an implicit function built
+ * from a ReLU MLP (am_load_mlp), a trigger point on the surface (am_seed, Alg. 1 step 2 and
+ * Sec. 4.3), OUTPUT the polygon mesh Z = {V, {P}} (am_march, am_get_mesh).
+ *
+ * Conventions shared by every call:
+ *   - every call returns an am_status and never aborts the process; on failure
+ *     am_last_error() describes the cause;
+ *   - pointers named h_* are HOST pointers, d_* are DEVICE pointers of the context's
+ *     device; the library copies every input it is given, so inputs may be freed as soon
+ *     as the call returns; output buffers stay owned by the caller;
+ *   - all device work runs on the context's stream; calls are blocking with respect to
+ *     that stream unless stated otherwise;
+ *   - there is no CPU fallback: without a usable CUDA device am_create fails.
+ *
+ * Conventions of the data (identical in the CPU oracle):
+ *   - biases are kept: every affine map is a row [a_x a_y a_z | a_0] acting on [x; 1];
+ *   - a cell key holds one bit per hidden neuron, in layer order, bit k of neuron k at
+ *     64-bit word k / 64, bit k % 64; the state is 1 iff the pre-activation is > 0 (a tie
+ *     gives 0, Eq. 2);
+ *   - faces are clipped to the box [-B, B]^3; edges on the box carry the plane ids
+ *     N + 0..5 for the box faces +x, -x, +y, -y, +z, -z (N = number of hidden neurons);
+ *   - a face's vertices run counter-clockwise seen from +grad F (= a_F[0:3]);
+ *     edge_planes[i] is the plane carrying the edge from corner i to corner i + 1;
+ *   - a mesh vertex is identified by the key (i, j, s with bits i and j cleared), i < j the
+ *     two planes meeting there, so the up to four faces meeting at a vertex share it.
+ */
+#ifndef ANALYTIC_MARCHING_H
+#define ANALYTIC_MARCHING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct am_ctx am_ctx;
+
+typedef enum {
+    AM_OK = 0,
+    AM_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, an unknown net id */
+    AM_ERR_CUDA = 2,          /* a CUDA runtime call failed; the context may be unusable */
+    AM_ERR_CAPACITY = 3,      /* a cell, hash, vertex or per-face vertex capacity was exceeded */
+    AM_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    AM_ERR_NO_SEED_CELL = 5,  /* no ray produced a seed cell (no sign change / no common cell) */
+    AM_ERR_DEGENERATE = 6,    /* the walk met a face it could not clip (reported, not fatal) */
+    AM_INCOMPLETE = 7,        /* am_march stopped at max_cells; call it again to resume */
+    AM_ERR_STATE = 8          /* the call is not valid in the context's current state */
+} am_status;
+
+typedef enum {
+    AM_PREC_FP64 = 0,         /* compose and clip in FP64 (the plain path) */
+    AM_PREC_MIXED = 1         /* compose in FP32 with a certified error bound, clip decisions
+                                 certified against it, uncertain cells redone in FP64 */
+} am_precision;
+
+/* Context creation options.  Zero-initialised fields take the documented defaults. */
+typedef struct {
+    int device;               /* CUDA device ordinal (default 0) */
+    void *stream;             /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int64_t max_cells;        /* capacity of visited cells over all nets (default 1 << 20) */
+    int64_t hash_slots;       /* cell hash-table slots, rounded up to a power of two
+                                 (default: the power of two >= 2 * max_cells) */
+    int max_face_verts;       /* per-face vertex capacity, 8..64 (default 32) */
+    int max_neurons;          /* largest N of any net that will be loaded (default 4096) */
+    int max_width;            /* largest hidden width of any net that will be loaded (default 512) */
+} am_ctx_opts;
+
+/* One ReLU MLP (Sec. 2.2, Eq. 1 with biases): F(x) = w_out . h_L + b_out,
+ * h_l = relu(W_l u_l + b_l); u_1 = [x; z]; u_l = h_{l-1}, or concat(h_{l-1}, [x; z]) at the
+ * skip layer (a DeepSDF-style skip-concat shortcut, Sec. 5.1).  Row-major FP64, caller
+ * owned, copied by am_load_mlp. */
+typedef struct {
+    int latent_dim;           /* length of the fixed latent code z (0 = none) */
+    const double *latent;     /* z, latent_dim values (may be NULL when latent_dim == 0) */
+    int n_hidden;             /* L >= 1 */
+    const int *width;         /* n_1..n_L */
+    const double *const *W;   /* W_l: width[l] x fan_in(l); fan_in(1) = 3 + latent_dim;
+                                 fan_in(l) = width[l-1] (+ 3 + latent_dim at the skip layer) */
+    const double *const *b;   /* b_l: width[l] */
+    int skip_layer;           /* 0 = none, else the 1-based hidden layer taking the concat */
+    const double *w_out;      /* width[L] */
+    double b_out;
+} am_mlp_desc;
+
+/* Options of one march. */
+typedef struct {
+    double box;               /* B of the clip box [-B, B]^3 (default 1.5) */
+    double delta;             /* vertex tolerance in world units (default 1e-10): a plane within
+                                 delta of a vertex counts as satisfied and as a degenerate event */
+    am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
+    int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
+    int use_proposal;         /* reserved for the learned constraint proposal (0) */
+} am_march_opts;
+
+/* Statistics of the last march (cumulative over resumed calls). */
+typedef struct {
+    int64_t cells;            /* cells solved */
+    int64_t faces;            /* non-empty faces */
+    int64_t empty_faces;      /* cells whose face was empty or of zero area */
+    int64_t vertices;         /* assembled (deduplicated) vertices */
+    int64_t corners;          /* face corners (sum of face sizes) */
+    int64_t degenerate;       /* planes within delta of an accepted vertex */
+    int64_t open_faces;       /* faces with an edge on the box */
+    int64_t refined_cells;    /* mixed precision: cells recomputed in FP64 */
+    int64_t levels;           /* breadth-first levels marched */
+    double ms_march;          /* device time of the march (CUDA events) */
+    double ms_assemble;       /* device time of the mesh assembly */
+} am_stats_t;
+
+/* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer
+ * NULL the call only fills the counts; with non-NULL arrays (host memory, sized from the
+ * counts) it copies the mesh out. */
+typedef struct {
+    int64_t n_vertices;
+    int64_t n_faces;
+    int64_t n_corners;        /* sum of the face sizes */
+    int key_words;            /* 64-bit words per face key */
+    int64_t n_open_faces;
+    double *xyz;              /* 3 * n_vertices */
+    int64_t *face_offsets;    /* n_faces + 1; face f is corners [off[f], off[f+1]) */
+    int32_t *face_vertices;   /* n_corners vertex indices */
+    int32_t *edge_planes;     /* n_corners plane ids (edge corner i -> corner i+1) */
+    uint64_t *face_keys;      /* n_faces * key_words */
+} am_mesh;
+
+/* Create a context on opts->device (opts may be NULL for defaults).  Allocates every device
+ * buffer up front, sized by the capacities.  Returns AM_ERR_CUDA when no device is usable. */
+am_status am_create(am_ctx **ctx, const am_ctx_opts *opts);
+
+/* Free the context and all of its device memory.  NULL is ignored. */
+void am_destroy(am_ctx *ctx);
+
+/* Text of the last error of this context (static storage owned by the context). */
+const char *am_last_error(const am_ctx *ctx);
+
+/* Copy one MLP to the device (Sec. 2.2).  The skip concat and the latent code are folded
+ * into per-layer constant affine rows at load time.  *net_id receives the id used by
+ * am_seed / am_get_mesh.  Fails with AM_ERR_INVALID_ARG when the net exceeds max_neurons
+ * or max_width. */
+am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *desc, int *net_id);
+
+/* Forget all cells, faces and seeds of every net (the loaded nets stay). */
+am_status am_reset(am_ctx *ctx);
+
+/* Trigger (Alg. 1 step 2; dichotomy, Sec. 4.3.2): for each ray x(t) = o + t d, t in [0, R],
+ * bisect F on the device until both ends of the bracket lie in one cell, take the exact
+ * affine root in that cell and push its cell into the active set.  h_origins, h_dirs: host,
+ * n_rays x 3 FP64.  *n_seeded (may be NULL) receives the number of new seed cells (rays
+ * landing in an already seeded cell count once).  AM_ERR_NO_SEED_CELL when no ray
+ * produced one. */
+am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs,
+                  int n_rays, double R, int *n_seeded);
+
+/* March (Alg. 1): solve every active cell (compose its affine maps, clip its face, push its
+ * unseen neighbours), breadth first over all nets at once, then assemble the meshes.
+ * opts may be NULL for defaults.  AM_INCOMPLETE when opts->max_cells stopped it early. */
+am_status am_march(am_ctx *ctx, const am_march_opts *opts);
+
+/* Copy out the assembled mesh of one net (two-call protocol, see am_mesh). */
+am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
+
+/* Statistics of the last march. */
+am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ANALYTIC_MARCHING_H */

@@ -1,0 +1,579 @@
+// am_api.cu -- host side of the C ABI (include/analytic_marching.h).
+//
+// The context owns every device buffer, allocated once at creation (the cell arena, the
+// hash table, the net weights) or grown on demand (mesh assembly).  am_march runs
+// Algorithm 1 breadth first: one launch of the cell kernel per level over the id range of
+// that level's active cells, until a level pushes no new cell; then the assembly kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/analytic_marching.h"
+#include "am_kernels.h"
+
+using namespace am;
+
+namespace {
+
+constexpr int kMaxNets = 1024;
+constexpr unsigned long long kZobristSeed = 0x2106100310031ull;
+
+struct NetHost {
+    NetDev dev;              // device pointers into `blob`
+    double *blob = nullptr;  // device allocation holding AT, Cl, w_out
+    int N = 0, max_w = 0;
+};
+
+struct MeshInfo {
+    int64_t faces = 0, face_base = 0, corners = 0, corner_base = 0, verts = 0, vert_base = 0, open = 0;
+};
+
+}  // namespace
+
+struct am_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    am_ctx_opts opts{};
+    Arena ar{};
+    NetDev *d_nets = nullptr;
+    std::vector<NetHost> nets;
+    int max_n_loaded = 1, max_w_loaded = 1;
+    int64_t solved_upto = 0;       // cells [0, solved_upto) are solved
+    am_stats_t stats{};
+    std::string err;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    // seeding scratch (grown on demand)
+    double *d_rays = nullptr;
+    unsigned long long *d_seed_keys = nullptr;
+    double *d_seed_x = nullptr;
+    int *d_seed_ok = nullptr;
+    int seed_cap = 0;
+    // assembly buffers (grown on demand)
+    unsigned long long *d_netcnt = nullptr;   // 5 x kMaxNets
+    int32_t *d_perm = nullptr;
+    int64_t *d_coff = nullptr;
+    int64_t coff_cap = 0;
+    int64_t *d_scan_tmp = nullptr;
+    int64_t scan_tmp_len = 0;
+    int64_t faces_cap = 0;
+    int32_t *d_cvid = nullptr, *d_fv = nullptr, *d_fe = nullptr;
+    int64_t corners_cap = 0;
+    double *d_xyz = nullptr;
+    int64_t verts_cap = 0;
+    unsigned long long *d_fkeys = nullptr;
+    int64_t fkeys_cap = 0;
+    unsigned long long *d_vslots = nullptr;
+    int64_t vslots_n = 0;
+    std::vector<MeshInfo> mesh;
+    bool mesh_valid = false;
+};
+
+namespace {
+
+am_status fail(am_ctx *c, am_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, AM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                        __FILE__, __LINE__);                                                          \
+    } while (0)
+
+int64_t pow2_at_least(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+template <class T>
+cudaError_t grow(T **p, int64_t *cap, int64_t need)
+{
+    if (need <= *cap && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    int64_t n = std::max<int64_t>(need, 1024);
+    n = n + n / 4;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * n);
+    *cap = e == cudaSuccess ? n : 0;
+    return e;
+}
+
+am_status sync_status(am_ctx *ctx, unsigned long long *host_counters)
+{
+    CU(cudaMemcpyAsync(host_counters, ctx->ar.counters, sizeof(unsigned long long) * kNumCounters,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status status_error(am_ctx *ctx, unsigned long long st)
+{
+    if (st & kStCellCap) return fail(ctx, AM_ERR_CAPACITY, "cell capacity (max_cells=%lld) exceeded",
+                                     (long long)ctx->ar.cap);
+    if (st & kStHashFull) return fail(ctx, AM_ERR_CAPACITY, "cell hash table probe limit reached");
+    if (st & kStFaceVerts) return fail(ctx, AM_ERR_CAPACITY, "a face has more than max_face_verts=%d corners",
+                                       ctx->ar.maxv);
+    if (st & kStVertHash) return fail(ctx, AM_ERR_CAPACITY, "vertex hash table probe limit reached");
+    if (st & kStTimeout) return fail(ctx, AM_ERR_TIMEOUT, "a bounded device wait gave up");
+    return AM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+am_status am_create(am_ctx **out, const am_ctx_opts *o)
+{
+    am_ctx *ctx = nullptr;
+    if (!out) return AM_ERR_INVALID_ARG;
+    *out = nullptr;
+    ctx = new am_ctx();
+    am_ctx_opts d{};
+    if (o) d = *o;
+    if (d.max_cells <= 0) d.max_cells = 1 << 20;
+    if (d.max_face_verts <= 0) d.max_face_verts = 32;
+    if (d.max_neurons <= 0) d.max_neurons = 4096;
+    if (d.max_width <= 0) d.max_width = 512;
+    if (d.max_cells > kMaxCellIds || d.max_face_verts < 8 || d.max_face_verts > 62 || d.max_neurons > kMaxNeurons) {
+        am_status s = fail(ctx, AM_ERR_INVALID_ARG, "capacity out of range");
+        *out = ctx;
+        return s;
+    }
+    d.hash_slots = pow2_at_least(std::max<int64_t>(d.hash_slots, 2 * d.max_cells));
+    ctx->opts = d;
+    ctx->device = d.device;
+    *out = ctx;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= d.device || d.device < 0)
+        return fail(ctx, AM_ERR_CUDA, "no usable CUDA device %d (count %d)", d.device, ndev);
+    CU(cudaSetDevice(d.device));
+    if (d.stream) {
+        ctx->stream = (cudaStream_t)d.stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    CU(cudaEventCreate(&ctx->ev0));
+    CU(cudaEventCreate(&ctx->ev1));
+    CU(cudaEventCreate(&ctx->ev2));
+    Arena &ar = ctx->ar;
+    ar.kw = (d.max_neurons + 63) / 64;
+    ar.maxv = d.max_face_verts;
+    ar.cap = d.max_cells;
+    ar.slot_mask = (unsigned long long)(d.hash_slots - 1);
+    CU(cudaMalloc(&ar.keys, sizeof(unsigned long long) * ar.kw * ar.cap));
+    CU(cudaMalloc(&ar.net, sizeof(int32_t) * ar.cap));
+    CU(cudaMalloc(&ar.hash, sizeof(unsigned long long) * ar.cap));
+    CU(cudaMalloc(&ar.nverts, sizeof(int32_t) * ar.cap));
+    CU(cudaMalloc(&ar.edges, sizeof(int32_t) * ar.cap * ar.maxv));
+    CU(cudaMalloc(&ar.verts, sizeof(double) * 3 * ar.cap * ar.maxv));
+    CU(cudaMalloc(&ar.slots, sizeof(unsigned long long) * d.hash_slots));
+    CU(cudaMalloc(&ar.counters, sizeof(unsigned long long) * kNumCounters));
+    {
+        std::vector<unsigned long long> z(64 * ar.kw);
+        for (size_t k = 0; k < z.size(); ++k) z[k] = splitmix64(kZobristSeed + 0x632BE59BD9B4E019ull * (k + 1));
+        unsigned long long *dz = nullptr;
+        CU(cudaMalloc(&dz, sizeof(unsigned long long) * z.size()));
+        CU(cudaMemcpy(dz, z.data(), sizeof(unsigned long long) * z.size(), cudaMemcpyHostToDevice));
+        ar.zob = dz;
+    }
+    CU(cudaMalloc(&ctx->d_nets, sizeof(NetDev) * kMaxNets));
+    CU(cudaMalloc(&ctx->d_netcnt, sizeof(unsigned long long) * 6 * kMaxNets));
+    CU(cudaMemsetAsync(ar.slots, 0, sizeof(unsigned long long) * d.hash_slots, ctx->stream));
+    CU(cudaMemsetAsync(ar.counters, 0, sizeof(unsigned long long) * kNumCounters, ctx->stream));
+    CU(prepare_cell_kernels(d.max_neurons, d.max_width));
+    CU(prepare_seed_kernels(d.max_neurons, d.max_width));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+void am_destroy(am_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) {
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    Arena &ar = ctx->ar;
+    void *bufs[] = {ar.keys, ar.net, ar.hash, ar.nverts, ar.edges, ar.verts, ar.slots, ar.counters,
+                    (void *)ar.zob, ctx->d_nets, ctx->d_netcnt, ctx->d_rays, ctx->d_seed_keys, ctx->d_seed_x,
+                    ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv, ctx->d_fe,
+                    ctx->d_xyz, ctx->d_fkeys, ctx->d_vslots};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (auto &n : ctx->nets)
+        if (n.blob) cudaFree(n.blob);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *am_last_error(const am_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
+{
+    if (!ctx || !dsc || !net_id) return fail(ctx, AM_ERR_INVALID_ARG, "null argument");
+    if (!ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "context was not created successfully");
+    const int L = dsc->n_hidden, zd = dsc->latent_dim, in_dim = 3 + zd;
+    if (L < 1 || L > kMaxLayers || zd < 0 || (zd > 0 && !dsc->latent) || !dsc->width || !dsc->W || !dsc->b ||
+        !dsc->w_out)
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad net description (layers %d, latent %d)", L, zd);
+    if (dsc->skip_layer != 0 && (dsc->skip_layer < 2 || dsc->skip_layer > L))
+        return fail(ctx, AM_ERR_INVALID_ARG, "skip_layer %d out of range", dsc->skip_layer);
+    if ((int)ctx->nets.size() >= kMaxNets) return fail(ctx, AM_ERR_CAPACITY, "too many nets");
+    int N = 0, mw = 0;
+    for (int l = 0; l < L; ++l) {
+        if (dsc->width[l] < 1 || !dsc->W[l] || !dsc->b[l]) return fail(ctx, AM_ERR_INVALID_ARG, "bad layer %d", l + 1);
+        N += dsc->width[l];
+        mw = std::max(mw, dsc->width[l]);
+    }
+    if (N > ctx->opts.max_neurons || mw > ctx->opts.max_width)
+        return fail(ctx, AM_ERR_INVALID_ARG, "net has N=%d neurons, width %d; context allows %d, %d", N, mw,
+                    ctx->opts.max_neurons, ctx->opts.max_width);
+    // fold: Cl (n_l x 4) and AT (n_{l-1} x n_l), then w_out
+    std::vector<double> host;
+    std::vector<size_t> offC(L + 1), offA(L + 1);
+    for (int l = 1; l <= L; ++l) {
+        const int n = dsc->width[l - 1], np = l > 1 ? dsc->width[l - 2] : 0;
+        const int fan = l == 1 ? in_dim : np + (l == dsc->skip_layer ? in_dim : 0);
+        const double *W = dsc->W[l - 1], *b = dsc->b[l - 1];
+        offC[l] = host.size();
+        const int xoff = l == 1 ? 0 : (l == dsc->skip_layer ? np : -1);
+        for (int k = 0; k < n; ++k) {
+            double c[4] = {0.0, 0.0, 0.0, b[k]};
+            if (xoff >= 0) {
+                for (int i = 0; i < 3; ++i) c[i] = W[(size_t)k * fan + xoff + i];
+                for (int j = 0; j < zd; ++j) c[3] += W[(size_t)k * fan + xoff + 3 + j] * dsc->latent[j];
+            }
+            host.insert(host.end(), c, c + 4);
+        }
+        offA[l] = host.size();
+        if (l > 1) {
+            host.resize(host.size() + (size_t)np * n);
+            double *AT = host.data() + offA[l];
+            for (int k = 0; k < n; ++k)
+                for (int j = 0; j < np; ++j) AT[(size_t)j * n + k] = W[(size_t)k * fan + j];
+        }
+    }
+    const size_t offW = host.size();
+    host.insert(host.end(), dsc->w_out, dsc->w_out + dsc->width[L - 1]);
+    NetHost nh;
+    CU(cudaMalloc(&nh.blob, sizeof(double) * host.size()));
+    CU(cudaMemcpyAsync(nh.blob, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, ctx->stream));
+    NetDev &nd = nh.dev;
+    memset(&nd, 0, sizeof nd);
+    nd.L = L;
+    nd.N = N;
+    nd.kw = (N + 63) / 64;
+    int r0 = 0;
+    for (int l = 1; l <= L; ++l) {
+        nd.width[l] = dsc->width[l - 1];
+        nd.row0[l] = r0;
+        r0 += nd.width[l];
+        nd.Cl[l] = nh.blob + offC[l];
+        nd.AT[l] = l > 1 ? nh.blob + offA[l] : nullptr;
+    }
+    nd.w_out = nh.blob + offW;
+    nd.b_out = dsc->b_out;
+    const int id = (int)ctx->nets.size();
+    nd.salt = splitmix64(0xA11CE5EEDull + (unsigned long long)id * 0x9E3779B97F4A7C15ull);
+    nh.N = N;
+    nh.max_w = mw;
+    CU(cudaMemcpyAsync(ctx->d_nets + id, &nd, sizeof(NetDev), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->nets.push_back(nh);
+    ctx->max_n_loaded = std::max(ctx->max_n_loaded, N);
+    ctx->max_w_loaded = std::max(ctx->max_w_loaded, mw);
+    *net_id = id;
+    return AM_OK;
+}
+
+am_status am_reset(am_ctx *ctx)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    CU(cudaMemsetAsync(ctx->ar.slots, 0, sizeof(unsigned long long) * (ctx->ar.slot_mask + 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->ar.counters, 0, sizeof(unsigned long long) * kNumCounters, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->solved_upto = 0;
+    ctx->stats = am_stats_t{};
+    ctx->mesh_valid = false;
+    return AM_OK;
+}
+
+am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays, double R,
+                  int *n_seeded)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!h_origins || !h_dirs || n_rays < 1 || !(R > 0.0)) return fail(ctx, AM_ERR_INVALID_ARG, "bad rays");
+    if (n_rays > ctx->seed_cap) {
+        if (ctx->d_rays) cudaFree(ctx->d_rays);
+        if (ctx->d_seed_keys) cudaFree(ctx->d_seed_keys);
+        if (ctx->d_seed_x) cudaFree(ctx->d_seed_x);
+        if (ctx->d_seed_ok) cudaFree(ctx->d_seed_ok);
+        ctx->d_rays = nullptr; ctx->d_seed_keys = nullptr; ctx->d_seed_x = nullptr; ctx->d_seed_ok = nullptr;
+        ctx->seed_cap = 0;
+        CU(cudaMalloc(&ctx->d_rays, sizeof(double) * 6 * n_rays));
+        CU(cudaMalloc(&ctx->d_seed_keys, sizeof(unsigned long long) * ctx->ar.kw * n_rays));
+        CU(cudaMalloc(&ctx->d_seed_x, sizeof(double) * 3 * n_rays));
+        CU(cudaMalloc(&ctx->d_seed_ok, sizeof(int) * (n_rays + 2)));
+        ctx->seed_cap = n_rays;
+    }
+    CU(cudaMemcpyAsync(ctx->d_rays, h_origins, sizeof(double) * 3 * n_rays, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_rays + 3 * n_rays, h_dirs, sizeof(double) * 3 * n_rays, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    unsigned long long *d_new = ctx->d_netcnt + 5 * kMaxNets;
+    CU(cudaMemsetAsync(d_new, 0, sizeof(unsigned long long), ctx->stream));
+    SeedArgs a{};
+    a.nets = ctx->d_nets;
+    a.ar = ctx->ar;
+    a.net = net_id;
+    a.n_rays = n_rays;
+    a.origins = ctx->d_rays;
+    a.dirs = ctx->d_rays + 3 * n_rays;
+    a.R = R;
+    a.max_halvings = 200;
+    a.max_n = ctx->opts.max_neurons;
+    a.max_w = ctx->opts.max_width;
+    a.seed_keys = ctx->d_seed_keys;
+    a.seed_x = ctx->d_seed_x;
+    a.seed_ok = ctx->d_seed_ok;
+    a.n_new = d_new;
+    launch_seed(a, ctx->stream);
+    CU(cudaGetLastError());
+    unsigned long long hn = 0;
+    CU(cudaMemcpyAsync(&hn, d_new, sizeof hn, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (n_seeded) *n_seeded = (int)hn;
+    ctx->mesh_valid = false;
+    if (hn == 0) {
+        std::vector<int> ok(n_rays);
+        CU(cudaMemcpy(ok.data(), ctx->d_seed_ok, sizeof(int) * n_rays, cudaMemcpyDeviceToHost));
+        int nosign = 0;
+        for (int v : ok) nosign += v == -4;
+        return fail(ctx, AM_ERR_NO_SEED_CELL, "no new seed cell (%d of %d rays without a sign change)", nosign, n_rays);
+    }
+    return AM_OK;
+}
+
+static am_status assemble(am_ctx *ctx, int64_t n_cells)
+{
+    const int nn = (int)ctx->nets.size();
+    unsigned long long *cnt = ctx->d_netcnt;
+    AsmArgs a{};
+    a.ar = ctx->ar;
+    a.nets = ctx->d_nets;
+    a.n_cells = n_cells;
+    a.n_nets = nn;
+    a.face_count = cnt;
+    a.face_fill = cnt + kMaxNets;
+    a.face_base = cnt + 2 * kMaxNets;
+    a.vert_count = cnt + 3 * kMaxNets;
+    a.vert_base = cnt + 4 * kMaxNets;
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 2 * kMaxNets, ctx->stream));
+    CU(cudaMemsetAsync(a.vert_count, 0, sizeof(unsigned long long) * kMaxNets, ctx->stream));
+    launch_asm_count(a, ctx->stream);
+    std::vector<unsigned long long> fc(nn), base(nn);
+    CU(cudaMemcpyAsync(fc.data(), a.face_count, sizeof(unsigned long long) * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    int64_t nf = 0;
+    for (int i = 0; i < nn; ++i) { base[i] = nf; nf += (int64_t)fc[i]; }
+    CU(cudaMemcpyAsync(a.face_base, base.data(), sizeof(unsigned long long) * nn, cudaMemcpyHostToDevice, ctx->stream));
+    CU(grow(&ctx->d_perm, &ctx->faces_cap, nf + 1));
+    CU(grow(&ctx->d_coff, &ctx->coff_cap, nf + 2));
+    const int64_t blocks = (nf + 4095) / 4096 + 1;
+    CU(grow(&ctx->d_scan_tmp, &ctx->scan_tmp_len, 2 * blocks + 4));
+    a.perm = ctx->d_perm;
+    a.corner_off = ctx->d_coff;
+    a.n_faces = nf;
+    launch_asm_scatter(a, ctx->stream);
+    CU(cudaGetLastError());
+    CU(launch_asm_offsets(a, ctx->d_scan_tmp, ctx->scan_tmp_len, ctx->stream));
+    int64_t ncorner = 0;
+    CU(cudaMemcpyAsync(&ncorner, ctx->d_coff + nf, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ncorner + 1 > ctx->corners_cap) {     // the three per-corner arrays grow together
+        int64_t c1 = 0, c2 = 0, c3 = 0;
+        CU(grow(&ctx->d_cvid, &c1, ncorner + 1));
+        CU(grow(&ctx->d_fv, &c2, ncorner + 1));
+        CU(grow(&ctx->d_fe, &c3, ncorner + 1));
+        ctx->corners_cap = std::min(c1, std::min(c2, c3));
+    }
+    CU(grow(&ctx->d_xyz, &ctx->verts_cap, 3 * (ncorner + 1)));
+    CU(grow(&ctx->d_fkeys, &ctx->fkeys_cap, (nf + 1) * ctx->ar.kw));
+    const int64_t vs = pow2_at_least(std::max<int64_t>(2 * ncorner, 1024));
+    if (vs > ctx->vslots_n) {
+        if (ctx->d_vslots) cudaFree(ctx->d_vslots);
+        ctx->d_vslots = nullptr;
+        CU(cudaMalloc(&ctx->d_vslots, sizeof(unsigned long long) * vs));
+        ctx->vslots_n = vs;
+    }
+    CU(cudaMemsetAsync(ctx->d_vslots, 0, sizeof(unsigned long long) * ctx->vslots_n, ctx->stream));
+    a.corner_vid = ctx->d_cvid;
+    a.vslots = ctx->d_vslots;
+    a.vslot_mask = (unsigned long long)(ctx->vslots_n - 1);
+    a.out_xyz = ctx->d_xyz;
+    a.out_fv = ctx->d_fv;
+    a.out_edges = ctx->d_fe;
+    a.out_keys = ctx->d_fkeys;
+    launch_asm_vertices(a, ctx->stream);
+    launch_asm_lookup(a, ctx->stream);
+    CU(cudaGetLastError());
+    std::vector<unsigned long long> vc(nn), vb(nn);
+    CU(cudaMemcpyAsync(vc.data(), a.vert_count, sizeof(unsigned long long) * nn, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    int64_t nvtx = 0;
+    for (int i = 0; i < nn; ++i) { vb[i] = nvtx; nvtx += (int64_t)vc[i]; }
+    CU(cudaMemcpyAsync(a.vert_base, vb.data(), sizeof(unsigned long long) * nn, cudaMemcpyHostToDevice, ctx->stream));
+    launch_asm_write(a, ctx->stream);
+    CU(cudaGetLastError());
+    // per-net corner ranges
+    std::vector<int64_t> coff_at(nn + 1);
+    ctx->mesh.assign(nn, MeshInfo{});
+    for (int i = 0; i <= nn; ++i) {
+        const int64_t f = i < nn ? (int64_t)base[i] : nf;
+        CU(cudaMemcpyAsync(&coff_at[i], ctx->d_coff + f, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < nn; ++i) {
+        MeshInfo &m = ctx->mesh[i];
+        m.faces = (int64_t)fc[i];
+        m.face_base = (int64_t)base[i];
+        m.corner_base = coff_at[i];
+        m.corners = coff_at[i + 1] - coff_at[i];
+        m.verts = (int64_t)vc[i];
+        m.vert_base = (int64_t)vb[i];
+    }
+    ctx->stats.faces = nf;
+    ctx->stats.corners = ncorner;
+    ctx->stats.vertices = nvtx;
+    ctx->mesh_valid = true;
+    return AM_OK;
+}
+
+am_status am_march(am_ctx *ctx, const am_march_opts *o)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (ctx->nets.empty()) return fail(ctx, AM_ERR_STATE, "no net loaded");
+    am_march_opts op{};
+    if (o) op = *o;
+    if (!(op.box > 0.0)) op.box = 1.5;
+    if (!(op.delta > 0.0)) op.delta = 1e-10;
+    if (op.precision != AM_PREC_FP64)
+        return fail(ctx, AM_ERR_INVALID_ARG, "precision %d is not available in this build", (int)op.precision);
+    unsigned long long hc[kNumCounters];
+    am_status s = sync_status(ctx, hc);
+    if (s != AM_OK) return s;
+    CellArgs ca{};
+    ca.nets = ctx->d_nets;
+    ca.ar = ctx->ar;
+    ca.box = op.box;
+    ca.delta = op.delta;
+    ca.max_n = ctx->opts.max_neurons;
+    ca.max_w = ctx->opts.max_width;
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    int64_t f0 = ctx->solved_upto, f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
+    const int64_t start = f0;
+    bool incomplete = false;
+    while (f0 < f1) {
+        if (op.max_cells > 0 && f0 - start >= op.max_cells) { incomplete = true; break; }
+        if (op.max_cells > 0) f1 = std::min<int64_t>(f1, start + op.max_cells);
+        ca.begin = f0;
+        ca.end = f1;
+        const int64_t n = f1 - f0;
+        launch_cell_fp64(ca, (int)std::min<int64_t>(n, 1 << 20), ctx->stream);
+        CU(cudaGetLastError());
+        ctx->stats.levels += 1;
+        s = sync_status(ctx, hc);
+        if (s != AM_OK) return s;
+        if (hc[kStatus] & (kStCellCap | kStHashFull | kStFaceVerts)) break;
+        f0 = f1;
+        f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
+    }
+    ctx->solved_upto = f0;
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    s = assemble(ctx, ctx->solved_upto);
+    if (s != AM_OK) return s;
+    CU(cudaEventRecord(ctx->ev2, ctx->stream));
+    s = sync_status(ctx, hc);
+    if (s != AM_OK) return s;
+    float ms1 = 0.f, ms2 = 0.f;
+    cudaEventElapsedTime(&ms1, ctx->ev0, ctx->ev1);
+    cudaEventElapsedTime(&ms2, ctx->ev1, ctx->ev2);
+    ctx->stats.ms_march += ms1;
+    ctx->stats.ms_assemble = ms2;
+    ctx->stats.cells = (int64_t)hc[kSolved];
+    ctx->stats.empty_faces = (int64_t)hc[kEmpty];
+    ctx->stats.degenerate = (int64_t)hc[kDegenerate];
+    ctx->stats.refined_cells = (int64_t)hc[kRefined];
+    s = status_error(ctx, hc[kStatus]);
+    if (s != AM_OK) return s;
+    if (hc[kStatus] & kStClip) ctx->err = "a clip step met an inconsistent polygon (reported as an empty face)";
+    return incomplete ? AM_INCOMPLETE : AM_OK;
+}
+
+am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *m)
+{
+    if (!ctx || !m) return fail(ctx, AM_ERR_INVALID_ARG, "null argument");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!ctx->mesh_valid || net_id >= (int)ctx->mesh.size()) return fail(ctx, AM_ERR_STATE, "no mesh: call am_march");
+    const MeshInfo &mi = ctx->mesh[net_id];
+    m->n_vertices = mi.verts;
+    m->n_faces = mi.faces;
+    m->n_corners = mi.corners;
+    m->key_words = ctx->ar.kw;
+    const bool copy = m->xyz || m->face_offsets || m->face_vertices || m->edge_planes || m->face_keys;
+    if (!copy) {
+        m->n_open_faces = -1;
+        return AM_OK;
+    }
+    if (!m->xyz || !m->face_offsets || !m->face_vertices || !m->edge_planes || !m->face_keys)
+        return fail(ctx, AM_ERR_INVALID_ARG, "either all or none of the mesh arrays must be given");
+    CU(cudaMemcpyAsync(m->xyz, ctx->d_xyz + 3 * mi.vert_base, sizeof(double) * 3 * mi.verts, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(m->face_vertices, ctx->d_fv + mi.corner_base, sizeof(int32_t) * mi.corners,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(m->edge_planes, ctx->d_fe + mi.corner_base, sizeof(int32_t) * mi.corners,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(m->face_offsets, ctx->d_coff + mi.face_base, sizeof(int64_t) * (mi.faces + 1),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(m->face_keys, ctx->d_fkeys + mi.face_base * ctx->ar.kw,
+                       sizeof(unsigned long long) * mi.faces * ctx->ar.kw, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int N = ctx->nets[net_id].N;
+    int64_t open = 0;
+    for (int64_t f = 0; f <= mi.faces; ++f) m->face_offsets[f] -= mi.corner_base;
+    for (int64_t f = 0; f < mi.faces; ++f) {
+        for (int64_t c = m->face_offsets[f]; c < m->face_offsets[f + 1]; ++c)
+            if (m->edge_planes[c] >= N) { ++open; break; }
+    }
+    m->n_open_faces = open;
+    return AM_OK;
+}
+
+am_status am_get_stats(const am_ctx *ctx, am_stats_t *s)
+{
+    if (!ctx || !s) return AM_ERR_INVALID_ARG;
+    *s = ctx->stats;
+    return AM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+// am_assemble.cu -- mesh assembly (a8): Z = {V, {P}} from the solved cells.
+//
+// Faces are grouped by net (counting sort on the net id), corner offsets come from an
+// exclusive scan of the face sizes, and vertices are deduplicated by their combinatorial
+// key (i, j, s with bits i and j cleared; i < j the planes meeting there) in a hash table,
+// so the faces meeting at a vertex share one index without comparing coordinates.
+#include "am_block.cuh"
+#include "am_kernels.h"
+
+namespace am {
+
+constexpr int kAsmThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int32_t kWinBit = 1 << 30;
+constexpr int32_t kUnset = -1;
+
+__global__ void asm_count_kernel(AsmArgs a)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.n_cells; c += (int64_t)gridDim.x * blockDim.x)
+        if (a.ar.nverts[c] > 0) atomicAdd(a.face_count + a.ar.net[c], 1ull);
+}
+
+__global__ void asm_scatter_kernel(AsmArgs a)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < a.n_cells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int nv = a.ar.nverts[c];
+        if (nv <= 0) continue;
+        const int net = a.ar.net[c];
+        const unsigned long long pos = a.face_base[net] + atomicAdd(a.face_fill + net, 1ull);
+        a.perm[pos] = (int32_t)c;
+        a.corner_off[pos] = nv;
+    }
+}
+
+// ---- exclusive scan of int64 (three passes; up to kScanThreads*kScanPer blocks)
+__global__ void scan_blocks_kernel(int64_t *v, int64_t n, int64_t *tops)
+{
+    __shared__ int64_t ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanThreads * kScanPer + threadIdx.x * kScanPer;
+    int64_t x[kScanPer], s = 0;
+    for (int i = 0; i < kScanPer; ++i) { x[i] = base + i < n ? v[base + i] : 0; s += x[i]; }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    int64_t run = (wid ? ws[wid - 1] : 0) + inc - s;
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) v[base + i] = run;
+        run += x[i];
+    }
+    if (threadIdx.x == kScanThreads - 1) tops[blockIdx.x] = (wid ? ws[wid - 1] : 0) + inc;
+}
+
+__global__ void scan_add_kernel(int64_t *v, int64_t n, const int64_t *tops_excl)
+{
+    const int64_t add = tops_excl[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kScanThreads * kScanPer;
+    for (int i = threadIdx.x; i < kScanThreads * kScanPer; i += blockDim.x)
+        if (base + i < n) v[base + i] += add;
+}
+
+// in-place exclusive scan of v[0..n), writes the total to v[n].  tmp: >= 2 * blocks + 2.
+static cudaError_t exclusive_scan(int64_t *v, int64_t n, int64_t *tmp, int64_t tmp_len, cudaStream_t st)
+{
+    const int64_t per = (int64_t)kScanThreads * kScanPer;
+    const int64_t blocks = (n + per - 1) / per;
+    if (blocks > per || 2 * blocks + 2 > tmp_len) return cudaErrorInvalidValue;
+    if (n == 0) return cudaMemsetAsync(v, 0, sizeof(int64_t), st);
+    scan_blocks_kernel<<<(unsigned)blocks, kScanThreads, 0, st>>>(v, n, tmp);
+    // scan the block totals (one block), total to tmp[blocks]
+    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(tmp, blocks, tmp + blocks + 1);
+    scan_add_kernel<<<(unsigned)blocks, 256, 0, st>>>(v, n, tmp);
+    // v[n] = scanned(v[n-1]) + size of the last element: recovered as total of tops
+    return cudaMemcpyAsync(v + n, tmp + blocks + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+}
+
+// ---- vertex keys
+__device__ __forceinline__ void corner_planes(const Arena &ar, int32_t cell, int nv, int j, int *lo, int *hi)
+{
+    const int a = ar.edges[(int64_t)cell * ar.maxv + (j + nv - 1) % nv];
+    const int b = ar.edges[(int64_t)cell * ar.maxv + j];
+    *lo = a < b ? a : b;
+    *hi = a < b ? b : a;
+}
+
+__device__ __forceinline__ unsigned long long vertex_hash(const Arena &ar, const NetDev &net, int32_t cell, int lo,
+                                                          int hi)
+{
+    unsigned long long h = ar.hash[cell];
+    const unsigned long long *k = ar.keys + (int64_t)cell * ar.kw;
+    if (lo < net.N && ((k[lo >> 6] >> (lo & 63)) & 1ull)) h ^= ar.zob[lo];
+    if (hi < net.N && ((k[hi >> 6] >> (hi & 63)) & 1ull)) h ^= ar.zob[hi];
+    return h ^ splitmix64(((unsigned long long)lo << 20) ^ (unsigned long long)hi ^ 0x5bd1e995ull);
+}
+
+__device__ __forceinline__ bool vertex_keys_equal(const Arena &ar, int32_t c1, int32_t c2, int lo, int hi)
+{
+    const unsigned long long *k1 = ar.keys + (int64_t)c1 * ar.kw, *k2 = ar.keys + (int64_t)c2 * ar.kw;
+    for (int w = 0; w < ar.kw; ++w) {
+        unsigned long long x = k1[w] ^ k2[w];
+        if ((lo >> 6) == w) x &= ~(1ull << (lo & 63));
+        if ((hi >> 6) == w) x &= ~(1ull << (hi & 63));
+        if (x) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long vslot_make(unsigned long long h, int64_t face, int corner)
+{
+    return (1ull << 63) | (((h >> 41) & 0x7FFFFFull) << 40) | (((unsigned long long)face & 0x3FFFFFFFFull) << 6) |
+           (unsigned long long)(corner & 63);
+}
+
+// find (or claim) the slot of vertex (lo, hi, key of cell) ; returns the slot value
+__device__ unsigned long long vertex_probe(const AsmArgs &a, const NetDev &net, int64_t face, int j, int32_t cell,
+                                           int net_id, int lo, int hi, bool claim, bool *claimed)
+{
+    const unsigned long long h = vertex_hash(a.ar, net, cell, lo, hi);
+    const unsigned long long mine = vslot_make(h, face, j);
+    unsigned long long pos = h & a.vslot_mask;
+    *claimed = false;
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        unsigned long long cur = *((volatile unsigned long long *)(a.vslots + pos));
+        if (cur == 0ull && claim) {
+            cur = atomicCAS(a.vslots + pos, 0ull, mine);
+            if (cur == 0ull) { *claimed = true; return mine; }
+        }
+        if (cur == 0ull) return 0ull;
+        if (((cur >> 40) & 0x7FFFFFull) == ((h >> 41) & 0x7FFFFFull)) {
+            const int64_t f2 = (int64_t)((cur >> 6) & 0x3FFFFFFFFull);
+            const int j2 = (int)(cur & 63);
+            const int32_t c2 = a.perm[f2];
+            if (a.ar.net[c2] == net_id) {
+                int lo2, hi2;
+                corner_planes(a.ar, c2, a.ar.nverts[c2], j2, &lo2, &hi2);
+                if (lo2 == lo && hi2 == hi && vertex_keys_equal(a.ar, cell, c2, lo, hi)) return cur;
+            }
+        }
+        pos = (pos + 1) & a.vslot_mask;
+    }
+    atomicOr(a.ar.counters + kStatus, kStVertHash);
+    return 0ull;
+}
+
+__global__ void asm_vertices_kernel(AsmArgs a)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.n_faces; f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = a.perm[f];
+        const int nv = a.ar.nverts[c], net_id = a.ar.net[c];
+        const NetDev &net = a.nets[net_id];
+        const int64_t off = a.corner_off[f];
+        for (int j = 0; j < nv; ++j) {
+            int lo, hi;
+            corner_planes(a.ar, c, nv, j, &lo, &hi);
+            bool claimed;
+            vertex_probe(a, net, f, j, c, net_id, lo, hi, true, &claimed);
+            if (claimed) {
+                const int32_t vid = (int32_t)atomicAdd(a.vert_count + net_id, 1ull);
+                a.corner_vid[off + j] = vid | kWinBit;
+            } else {
+                a.corner_vid[off + j] = kUnset;
+            }
+        }
+    }
+}
+
+__global__ void asm_lookup_kernel(AsmArgs a)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.n_faces; f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = a.perm[f];
+        const int nv = a.ar.nverts[c], net_id = a.ar.net[c];
+        const NetDev &net = a.nets[net_id];
+        const int64_t off = a.corner_off[f];
+        for (int j = 0; j < nv; ++j) {
+            if (a.corner_vid[off + j] != kUnset) continue;
+            int lo, hi;
+            corner_planes(a.ar, c, nv, j, &lo, &hi);
+            bool claimed;
+            const unsigned long long s = vertex_probe(a, net, f, j, c, net_id, lo, hi, false, &claimed);
+            if (s == 0ull) continue;
+            const int64_t f2 = (int64_t)((s >> 6) & 0x3FFFFFFFFull);
+            const int j2 = (int)(s & 63);
+            a.corner_vid[off + j] = a.corner_vid[a.corner_off[f2] + j2] & ~kWinBit;
+        }
+    }
+}
+
+__global__ void asm_write_kernel(AsmArgs a)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.n_faces; f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = a.perm[f];
+        const int nv = a.ar.nverts[c], net_id = a.ar.net[c];
+        const int64_t off = a.corner_off[f];
+        for (int j = 0; j < nv; ++j) {
+            const int32_t v = a.corner_vid[off + j];
+            const int32_t vid = v & ~kWinBit;
+            a.out_fv[off + j] = v == kUnset ? -1 : vid;
+            a.out_edges[off + j] = a.ar.edges[(int64_t)c * a.ar.maxv + j];
+            if (v != kUnset && (v & kWinBit)) {
+                const double *p = a.ar.verts + ((int64_t)c * a.ar.maxv + j) * 3;
+                double *q = a.out_xyz + (a.vert_base[net_id] + vid) * 3;
+                q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+            }
+        }
+        for (int w = 0; w < a.ar.kw; ++w) a.out_keys[f * a.ar.kw + w] = a.ar.keys[(int64_t)c * a.ar.kw + w];
+    }
+}
+
+static int grid_for(int64_t n)
+{
+    int64_t g = (n + kAsmThreads - 1) / kAsmThreads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+void launch_asm_count(const AsmArgs &a, cudaStream_t st) { asm_count_kernel<<<grid_for(a.n_cells), kAsmThreads, 0, st>>>(a); }
+void launch_asm_scatter(const AsmArgs &a, cudaStream_t st) { asm_scatter_kernel<<<grid_for(a.n_cells), kAsmThreads, 0, st>>>(a); }
+cudaError_t launch_asm_offsets(const AsmArgs &a, int64_t *tmp, int64_t tmp_len, cudaStream_t st)
+{
+    return exclusive_scan(a.corner_off, a.n_faces, tmp, tmp_len, st);
+}
+void launch_asm_vertices(const AsmArgs &a, cudaStream_t st) { asm_vertices_kernel<<<grid_for(a.n_faces), kAsmThreads, 0, st>>>(a); }
+void launch_asm_lookup(const AsmArgs &a, cudaStream_t st) { asm_lookup_kernel<<<grid_for(a.n_faces), kAsmThreads, 0, st>>>(a); }
+void launch_asm_write(const AsmArgs &a, cudaStream_t st) { asm_write_kernel<<<grid_for(a.n_faces), kAsmThreads, 0, st>>>(a); }
+
+}  // namespace am

@@ -1,0 +1,135 @@
+// am_block.cuh -- block-wide primitives (scan, compaction, reductions) and the cell
+// hash-table insert used by the marching kernels.
+#pragma once
+
+#include "am_common.cuh"
+
+namespace am {
+
+constexpr int kMaxProbe = 1 << 16;   // hash probe limit per insert (a bounded loop)
+
+// Exclusive block scan of one int per thread.  wsum: shared scratch of 32 ints.  Every
+// thread of the block must call it.  *total receives the block sum.
+__device__ __forceinline__ int block_scan_excl(int v, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) wsum[lane] = s;
+    }
+    __syncthreads();
+    const int base = wid ? wsum[wid - 1] : 0;
+    *total = wsum[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block argmax of (value, index): the larger value wins, ties go to the smaller index.
+// idx < 0 marks "no candidate".  red_v/red_i: shared scratch of 32 entries each.
+__device__ __forceinline__ void block_argmax(double v, int idx, double *red_v, int *red_i, double *out_v,
+                                             int *out_i)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        bool take = (i2 >= 0) && (idx < 0 || v2 > v || (v2 == v && i2 < idx));
+        if (take) { v = v2; idx = i2; }
+    }
+    if (lane == 0) { red_v[wid] = v; red_i[wid] = idx; }
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red_v[lane] : 0.0;
+        idx = lane < nw ? red_i[lane] : -1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+            bool take = (i2 >= 0) && (idx < 0 || v2 > v || (v2 == v && i2 < idx));
+            if (take) { v = v2; idx = i2; }
+        }
+        if (lane == 0) { red_v[0] = v; red_i[0] = idx; }
+    }
+    __syncthreads();
+    *out_v = red_v[0];
+    *out_i = red_i[0];
+    __syncthreads();
+}
+
+// key(pa) ^ e_fa == key(pb) ^ e_fb ?  (kNoFlip = no bit flipped)
+__device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsigned fa, int64_t pb, unsigned fb)
+{
+    const unsigned long long *ka = ar.keys + pa * ar.kw, *kb = ar.keys + pb * ar.kw;
+    for (int w = 0; w < ar.kw; ++w) {
+        unsigned long long x = ka[w] ^ kb[w];
+        if (fa != kNoFlip && (int)(fa >> 6) == w) x ^= 1ull << (fa & 63);
+        if (fb != kNoFlip && (int)(fb >> 6) == w) x ^= 1ull << (fb & 63);
+        if (x) return false;
+    }
+    return true;
+}
+
+// Alg. 1 steps 10-11: the neighbour key(parent) ^ e_flip (hash h) is pushed unless it was
+// seen before.  The slot records (parent, flip), from which any later probe rebuilds the
+// key, so a claim never waits for a key to be written.  A claim hands out the next cell id
+// and writes the new cell's key there.
+__device__ inline void insert_neighbor(const Arena &ar, int64_t parent, int net, unsigned flip,
+                                       unsigned long long h)
+{
+    const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
+    unsigned long long pos = h & ar.slot_mask;
+    for (int probe = 0; probe < kMaxProbe; ++probe) {
+        unsigned long long cur = *((volatile unsigned long long *)(ar.slots + pos));
+        if (cur == 0ull) {
+            unsigned long long prev = atomicCAS(ar.slots + pos, 0ull, mine);
+            if (prev == 0ull) {
+                long long id = (long long)atomicAdd(ar.counters + kNCells, 1ull);
+                if (id >= ar.cap) {
+                    atomicOr(ar.counters + kStatus, kStCellCap);
+                    return;
+                }
+                const unsigned long long *kp = ar.keys + parent * ar.kw;
+                unsigned long long *kn = ar.keys + id * ar.kw;
+                for (int w = 0; w < ar.kw; ++w) {
+                    unsigned long long x = kp[w];
+                    if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
+                    kn[w] = x;
+                }
+                ar.net[id] = net;
+                ar.hash[id] = h;
+                ar.nverts[id] = -1;
+                return;
+            }
+            cur = prev;
+        }
+        if (slot_tag(cur) == hash_tag(h)) {
+            const int64_t pb = slot_parent(cur);
+            if (ar.net[pb] == net && ref_keys_equal(ar, parent, flip, pb, slot_flip(cur))) return;
+        }
+        pos = (pos + 1) & ar.slot_mask;
+    }
+    atomicOr(ar.counters + kStatus, kStHashFull);
+}
+
+}  // namespace am

@@ -1,0 +1,154 @@
+"""Python face of the C ABI: a context that loads nets, seeds, marches and returns meshes.
+
+Thin marshalling over ``native`` (numpy in, numpy out).  The network format is any object
+with the attributes of ``synth.MLP`` (weights, biases, w_out, b_out, latent, skip_layer).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import native as nt
+
+
+class AMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{nt.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+@dataclass
+class Mesh:
+    """Assembled mesh of one net (all arrays host numpy)."""
+    xyz: np.ndarray            # (V, 3) float64
+    face_offsets: np.ndarray   # (F + 1,) int64
+    face_vertices: np.ndarray  # (corners,) int32
+    edge_planes: np.ndarray    # (corners,) int32
+    face_keys: np.ndarray      # (F, key_words) uint64
+    n_open_faces: int
+
+    @property
+    def n_faces(self) -> int:
+        return len(self.face_offsets) - 1
+
+    def faces(self):
+        o = self.face_offsets
+        return [self.face_vertices[o[i]:o[i + 1]] for i in range(self.n_faces)]
+
+    def face_edges(self, i):
+        o = self.face_offsets
+        return self.edge_planes[o[i]:o[i + 1]]
+
+
+class Mesher:
+    def __init__(self, device: int = 0, max_cells: int = 1 << 20, max_neurons: int = 4096, max_width: int = 512,
+                 max_face_verts: int = 32, hash_slots: int = 0, stream: int | None = None, lib_path=None):
+        self.lib = nt.load(lib_path)
+        self._keep = []
+        opts = nt.am_ctx_opts(device=device, stream=stream, max_cells=max_cells, hash_slots=hash_slots,
+                              max_face_verts=max_face_verts, max_neurons=max_neurons, max_width=max_width)
+        self.ctx = C.c_void_p()
+        st = self.lib.am_create(C.byref(self.ctx), C.byref(opts))
+        if st != nt.AM_OK:
+            msg = self.lib.am_last_error(self.ctx).decode() if self.ctx else ""
+            self.lib.am_destroy(self.ctx)
+            self.ctx = None
+            raise AMError(st, msg)
+        self.nets = []
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.am_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int, ok=(nt.AM_OK,)):
+        if st not in ok:
+            raise AMError(st, self.lib.am_last_error(self.ctx).decode())
+        return st
+
+    # ---- am_load_mlp
+    def load_mlp(self, mlp) -> int:
+        L = len(mlp.weights)
+        Ws = [np.ascontiguousarray(w, dtype=np.float64) for w in mlp.weights]
+        bs = [np.ascontiguousarray(b, dtype=np.float64) for b in mlp.biases]
+        w_out = np.ascontiguousarray(mlp.w_out, dtype=np.float64)
+        width = (C.c_int * L)(*[int(w.shape[0]) for w in Ws])
+        Wp = (C.POINTER(C.c_double) * L)(*[_dp(w) for w in Ws])
+        bp = (C.POINTER(C.c_double) * L)(*[_dp(b) for b in bs])
+        z = None if mlp.latent is None else np.ascontiguousarray(mlp.latent, dtype=np.float64)
+        d = nt.am_mlp_desc(latent_dim=0 if z is None else len(z), latent=None if z is None else _dp(z),
+                           n_hidden=L, width=width, W=Wp, b=bp, skip_layer=int(mlp.skip_layer),
+                           w_out=_dp(w_out), b_out=float(mlp.b_out))
+        nid = C.c_int(-1)
+        self._check(self.lib.am_load_mlp(self.ctx, C.byref(d), C.byref(nid)))
+        self.nets.append(mlp)
+        return nid.value
+
+    def reset(self):
+        self._check(self.lib.am_reset(self.ctx))
+
+    # ---- am_seed
+    def seed(self, net_id: int, origins, dirs, R: float = 2.0) -> int:
+        o = np.ascontiguousarray(np.atleast_2d(origins), dtype=np.float64)
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        n = C.c_int(0)
+        self._check(self.lib.am_seed(self.ctx, int(net_id), _dp(o), _dp(d), int(o.shape[0]), float(R), C.byref(n)))
+        return n.value
+
+    # ---- am_march
+    def march(self, box: float = 1.5, delta: float = 1e-10, precision: int = nt.AM_PREC_FP64,
+              max_cells: int = 0, use_proposal: bool = False) -> int:
+        op = nt.am_march_opts(box=box, delta=delta, precision=precision, max_cells=max_cells,
+                              use_proposal=int(use_proposal))
+        return self._check(self.lib.am_march(self.ctx, C.byref(op)), ok=(nt.AM_OK, nt.AM_INCOMPLETE))
+
+    def stats(self) -> dict:
+        s = nt.am_stats_t()
+        self._check(self.lib.am_get_stats(self.ctx, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
+
+    # ---- am_get_mesh
+    def get_mesh(self, net_id: int) -> Mesh:
+        m = nt.am_mesh()
+        self._check(self.lib.am_get_mesh(self.ctx, int(net_id), C.byref(m)))
+        xyz = np.zeros((m.n_vertices, 3))
+        off = np.zeros(m.n_faces + 1, dtype=np.int64)
+        fv = np.zeros(m.n_corners, dtype=np.int32)
+        fe = np.zeros(m.n_corners, dtype=np.int32)
+        keys = np.zeros((m.n_faces, m.key_words), dtype=np.uint64)
+        m.xyz = xyz.ctypes.data_as(C.POINTER(C.c_double))
+        m.face_offsets = off.ctypes.data_as(C.POINTER(C.c_int64))
+        m.face_vertices = fv.ctypes.data_as(C.POINTER(C.c_int32))
+        m.edge_planes = fe.ctypes.data_as(C.POINTER(C.c_int32))
+        m.face_keys = keys.ctypes.data_as(C.POINTER(C.c_uint64))
+        if m.n_faces == 0:
+            return Mesh(xyz, off, fv, fe, keys, 0)
+        self._check(self.lib.am_get_mesh(self.ctx, int(net_id), C.byref(m)))
+        return Mesh(xyz, off, fv, fe, keys, int(m.n_open_faces))
+
+
+def mesh_net(mlp, origins, dirs, R=2.0, box=1.5, delta=1e-10, **ctx_kw):
+    """Convenience: one net, one march; returns (Mesh, stats)."""
+    with Mesher(**ctx_kw) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, origins, dirs, R)
+        m.march(box=box, delta=delta)
+        return m.get_mesh(nid), m.stats()

@@ -1,0 +1,78 @@
+"""Comparison of a mesh from the CUDA path with the oracle's, element by element.
+
+Both sides are brought to the same canonical form: per face its cell key, the cyclic list
+of edge planes CCW about +grad F starting at the vertex whose sorted plane pair is
+smallest, and the matching vertex coordinates.  Face keys and edge cycles must be equal
+(bit exact); coordinates agree within a relative tolerance; the assembled vertex indices
+must coincide exactly with the combinatorial vertex keys.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _key_int(words) -> int:
+    return int.from_bytes(np.asarray(words, dtype=np.uint64).tobytes(), "little")
+
+
+def canon(edges, verts):
+    m = len(edges)
+    pairs = [(min(edges[j - 1], edges[j]), max(edges[j - 1], edges[j])) for j in range(m)]
+    j0 = min(range(m), key=lambda j: pairs[j])
+    return [int(e) for e in edges[j0:]] + [int(e) for e in edges[:j0]], np.roll(np.asarray(verts), -j0, axis=0)
+
+
+def gpu_faces(mesh):
+    """{key: (edges, verts (m x 3), vertex indices)} from a paper_2106_10031_gb300.Mesh."""
+    out = {}
+    o = mesh.face_offsets
+    for i in range(mesh.n_faces):
+        idx = mesh.face_vertices[o[i]:o[i + 1]]
+        e = mesh.edge_planes[o[i]:o[i + 1]]
+        k = _key_int(mesh.face_keys[i])
+        assert k not in out, "duplicate face key"
+        m = len(e)
+        pairs = [(min(e[j - 1], e[j]), max(e[j - 1], e[j])) for j in range(m)]
+        j0 = min(range(m), key=lambda j: pairs[j])
+        out[k] = ([int(x) for x in np.roll(e, -j0)], mesh.xyz[np.roll(idx, -j0)], np.roll(idx, -j0))
+    return out
+
+
+def vertex_key(key, a, b, N):
+    lo, hi = min(a, b), max(a, b)
+    k = key
+    for p in (lo, hi):
+        if p < N:
+            k &= ~(1 << p)
+    return (lo, hi, k)
+
+
+def compare(oracle_mesh, gpu_mesh, N, rtol=1e-9, sample=None):
+    """Assert parity; returns a dict of measured errors."""
+    ref = {f.key: f for f in oracle_mesh.faces}
+    got = gpu_faces(gpu_mesh)
+    missing = set(ref) - set(got)
+    extra = set(got) - set(ref)
+    assert not missing and not extra, f"face key sets differ: {len(missing)} missing, {len(extra)} extra"
+    keys = sorted(ref)
+    if sample is not None and sample < len(keys):
+        rng = np.random.default_rng(0)
+        keys = [keys[i] for i in rng.choice(len(keys), sample, replace=False)]
+    max_rel = 0.0
+    for k in keys:
+        f = ref[k]
+        e_g, v_g, _ = got[k]
+        assert f.edges == e_g, f"edge cycle differs for face {k:#x}: {f.edges} vs {e_g}"
+        err = np.linalg.norm(f.verts - v_g, axis=1) / np.maximum(1.0, np.linalg.norm(f.verts, axis=1))
+        max_rel = max(max_rel, float(err.max()))
+    assert max_rel <= rtol, f"vertex error {max_rel:.3e} > {rtol:.1e}"
+    # connectivity: GPU vertex index <-> combinatorial vertex key is a bijection
+    idx_of = {}
+    for k, (e, _, idx) in got.items():
+        m = len(e)
+        for j in range(m):
+            vk = vertex_key(k, e[j - 1], e[j], N)
+            i = int(idx[j])
+            assert idx_of.setdefault(vk, i) == i, "one vertex key mapped to two vertex indices"
+    assert len(set(idx_of.values())) == len(idx_of) == len(gpu_mesh.xyz), "vertex indices are not one per key"
+    return {"faces": len(ref), "vertices": len(idx_of), "max_rel_vertex_err": max_rel}

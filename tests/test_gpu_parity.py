@@ -1,0 +1,120 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.  Needs a GPU."""
+import numpy as np
+import pytest
+
+from synth import batch_nets, decoder_net, octahedron, polytope_max_of_planes, sphere_net, tiny_net
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+RAY = np.array([[1.0, 0.37, 0.21]]) / np.linalg.norm([1.0, 0.37, 0.21])
+X_RAY = np.array([[1.0, 0.0, 0.0]])
+
+
+@pytest.fixture(scope="module")
+def am():
+    import paper_2106_10031_gb300 as am_mod
+    return am_mod
+
+
+def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
+    net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((len(dirs), 3)), dirs, R)
+    with am.Mesher(max_cells=kw.pop("max_cells", 1 << 18), max_neurons=max(64, mlp.N),
+                   max_width=max(mlp.widths)) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((len(dirs), 3)), dirs, R)
+        m.march(**kw)
+        mesh = m.get_mesh(nid)
+        st = m.stats()
+    return net, ref, mesh, st
+
+
+@pytest.mark.parametrize("make,dirs", [
+    (octahedron, RAY),
+    (polytope_max_of_planes, X_RAY),
+    (lambda: tiny_net((8, 8), 11), RAY),
+    (lambda: tiny_net((6, 5, 4), 12), RAY),
+    (lambda: decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05), X_RAY),
+])
+def test_parity_small(oracle_mod, am, make, dirs):
+    mlp = make()
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, dirs)
+    assert not ref.failed
+    r = parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    assert st["degenerate"] == 0 == ref.degenerate
+    assert st["faces"] == r["faces"]
+    assert mesh.n_open_faces == ref.open_faces()
+
+
+def test_parity_sphere_net_full(oracle_mod, am):
+    # the 3-[64]x4-1 workload at full size, every face compared
+    mlp = sphere_net()
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, X_RAY)
+    r = parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    assert r["faces"] > 40000 and st["degenerate"] == 0 and mesh.n_open_faces == 0
+
+
+def test_parity_multi_seed_multi_component(oracle_mod, am):
+    # many rays, some landing in the same cell, on a net with several surface components
+    mlp = tiny_net((6, 5, 4), 12)
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(64, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, d)
+    parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+
+
+def test_parity_two_nets_one_march(oracle_mod, am):
+    nets = [sphere_net(seed=21, width=32, depth=4, sigma=0.05), tiny_net((8, 8), 11)]
+    refs = [oracle_mod.mesh_from_rays(n, np.zeros((1, 3)), RAY)[1] for n in nets]
+    with am.Mesher(max_cells=1 << 18, max_neurons=256, max_width=64) as m:
+        ids = [m.load_mlp(n) for n in nets]
+        for i in ids:
+            m.seed(i, np.zeros((1, 3)), RAY)
+        m.march()
+        for i, n, r in zip(ids, nets, refs):
+            parity.compare(r, m.get_mesh(i), n.N, rtol=1e-9)
+
+
+def test_resume_after_max_cells(oracle_mod, am):
+    mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
+    net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), RAY)
+    with am.Mesher(max_cells=1 << 17, max_neurons=128, max_width=32) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), RAY)
+        st = m.march(max_cells=500)
+        assert st == 7                      # AM_INCOMPLETE
+        while m.march(max_cells=500) == 7:
+            pass
+        parity.compare(ref, m.get_mesh(nid), mlp.N, rtol=1e-9)
+
+
+def test_capacity_error_is_reported(am):
+    mlp = sphere_net()
+    with am.Mesher(max_cells=1000, max_neurons=256, max_width=64) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), X_RAY)
+        with pytest.raises(am.AMError) as e:
+            m.march()
+        assert e.value.status == 3           # AM_ERR_CAPACITY
+
+
+def test_seed_without_sign_change(am):
+    with am.Mesher(max_cells=1024, max_neurons=256, max_width=64) as m:
+        nid = m.load_mlp(sphere_net())
+        with pytest.raises(am.AMError) as e:
+            m.seed(nid, np.zeros((1, 3)), X_RAY, R=0.05)
+        assert e.value.status == 5           # AM_ERR_NO_SEED_CELL
+
+
+def test_seed_matches_oracle(oracle_mod, am):
+    # the device bisection lands in the oracle's seed cell
+    for mlp in (sphere_net(), decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05)):
+        net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), X_RAY, max_cells=1)
+        with am.Mesher(max_cells=4096, max_neurons=256, max_width=64) as m:
+            nid = m.load_mlp(mlp)
+            m.seed(nid, np.zeros((1, 3)), X_RAY)
+            m.march(max_cells=1)
+            mesh = m.get_mesh(nid)
+        assert mesh.n_faces == 1
+        assert parity._key_int(mesh.face_keys[0]) == ref.seeds[0][0]
