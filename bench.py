@@ -1,0 +1,390 @@
+"""Benchmark: analytic faces per second of analytic marching on one GB300.
+
+One step = the whole hot path on one mesh: forget the previous cells, trigger the seed
+cell by bisection on the device, march every analytic cell (compose, clip, emit, hash
+march) and assemble the mesh.  The workload is the 3-[64]x4-1 geometric-init SDF net
+(seed 2, every parameter perturbed by N(0, 0.05^2)) with one seed ray along +x, clipped
+to the box [-1.5, 1.5]^3 (43,780 faces).  Inputs (the net) are resident in HBM when the
+timed region starts; the e2e leg repeats the step through the C ABI from pinned host
+buffers (net upload, seed ray, mesh download) inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64] [--impl reference]
+
+Multi-GPU: each rank meshes its own copy of the workload (replicas, no collective on the
+data path); the job's value is the faces of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh)"
+UNIT = "faces/s"
+WORKLOAD = "3-[64]x4-1 geometric-init SDF MLP (seed 2, sigma 0.05), 1 seed ray +x, box 1.5"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from synth import sphere_net
+    return sphere_net(seed=2, width=64, depth=4, sigma=0.05), np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+
+
+class Dist:
+    def __init__(self, n_gpus):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def allreduce(self, x: float, op: str) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = f"cuda:{self.local}" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work of the cell kernel
+
+
+def algorithmic_flops(mlp, mesh) -> tuple:
+    """FP64 flops the method must do per solved cell, summed over the mesh's faces.
+
+    compose (Cor. 1, masked): for l >= 2, 4 columns x n_l rows x |active(l-1)| FMAs, plus a_F
+    over |active(L)|; clip certification (Alg. 1 step 8 for the output): every row checked at
+    every final vertex, one 4-term dot product (8 flops) per (row, vertex)."""
+    widths = mlp.widths
+    N = mlp.N
+    keys = mesh.face_keys
+    bits = np.unpackbits(keys.view(np.uint8), axis=1, bitorder="little")[:, :N].astype(np.int64)
+    r = np.cumsum([0] + widths)
+    compose = np.zeros(len(keys), dtype=np.int64)
+    for l in range(1, len(widths)):
+        act_prev = bits[:, r[l - 1]:r[l]].sum(1)
+        compose += 8 * widths[l] * act_prev
+    compose += 8 * bits[:, r[-2]:r[-1]].sum(1)
+    nverts = np.diff(mesh.face_offsets)
+    clip = 8 * (N + 6) * nverts
+    return int(compose.sum()), int(clip.sum())
+
+
+# ------------------------------------------------------------------------------------------
+
+
+def cpu_baseline(mlp, o, d, budget_s=12.0):
+    """The oracle as it stands, single-threaded on this host, on a bounded prefix of the
+    same march (breadth-first order, at most budget_s of CPU time)."""
+    from oracle import oracle as O
+    O.build()
+    net = O.OracleNet(mlp)
+    seeds = O.seed_cells(net, o, d)
+    probe = 500
+    t0 = time.perf_counter()
+    O.march(net, seeds, max_cells=probe)
+    per = (time.perf_counter() - t0) / probe
+    n = max(probe, min(60000, int(budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    mesh = O.march(net, seeds, max_cells=n)
+    dt = time.perf_counter() - t0
+    faces = len(mesh.faces)
+    return {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} cells of the breadth-first march ({faces} faces) in {dt:.1f} s, "
+                      f"single thread (plain C per cell + Python loop)"}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return 0
+    mlp, o, d = workload()
+    from oracle import oracle as O
+    O.build()
+    net = O.OracleNet(mlp)
+    seeds = O.seed_cells(net, o, d)
+    cells = 3000
+    for _ in range(max(0, args.warmup)):
+        O.march(net, seeds, max_cells=200)
+    t0 = time.perf_counter()
+    faces = 0
+    for _ in range(args.steps):
+        faces += len(O.march(net, seeds, max_cells=cells).faces)
+    dt = time.perf_counter() - t0
+    v = faces / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"first {cells} cells of the march per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: first {cells} cells of the breadth-first march, single thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
+    """Same step through the C ABI with host buffers: upload the net from pinned memory,
+    seed from a pinned host ray, march, copy the mesh back into pinned host buffers."""
+    import torch
+
+    from paper_2106_10031_gb300 import native as nt
+    lib = nt.load()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).pin_memory()  # noqa: E731
+    Wp = [pin(w) for w in mlp.weights]
+    bp = [pin(b) for b in mlp.biases]
+    wo = pin(mlp.w_out)
+    ray_o, ray_d = pin(o), pin(d)
+    L = mlp.L
+    dp = lambda t: C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_double))  # noqa: E731
+    desc = nt.am_mlp_desc(latent_dim=0, latent=None, n_hidden=L, width=(C.c_int * L)(*mlp.widths),
+                          W=(C.POINTER(C.c_double) * L)(*[dp(w) for w in Wp]),
+                          b=(C.POINTER(C.c_double) * L)(*[dp(b) for b in bp]), skip_layer=0,
+                          w_out=dp(wo), b_out=float(mlp.b_out))
+    ctx = C.c_void_p()
+    opts = nt.am_ctx_opts(device=device, stream=stream_ptr, max_cells=1 << 17, hash_slots=0, max_face_verts=32,
+                          max_neurons=256, max_width=64)
+    assert lib.am_create(C.byref(ctx), C.byref(opts)) == 0, lib.am_last_error(ctx)
+    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, use_proposal=0)
+    bufs = None
+    h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + 48
+    d2h = 0
+
+    def step():
+        nonlocal bufs, d2h
+        assert lib.am_release_nets(ctx) == 0
+        nid = C.c_int()
+        assert lib.am_load_mlp(ctx, C.byref(desc), C.byref(nid)) == 0
+        ns = C.c_int()
+        assert lib.am_seed(ctx, nid, dp(ray_o), dp(ray_d), 1, 2.0, C.byref(ns)) == 0
+        assert lib.am_march(ctx, C.byref(mo)) == 0, lib.am_last_error(ctx)
+        m = nt.am_mesh()
+        assert lib.am_get_mesh(ctx, nid, C.byref(m)) == 0
+        if bufs is None:
+            bufs = {"xyz": torch.empty(3 * m.n_vertices + 3, dtype=torch.float64).pin_memory(),
+                    "off": torch.empty(m.n_faces + 1, dtype=torch.int64).pin_memory(),
+                    "fv": torch.empty(m.n_corners + 1, dtype=torch.int32).pin_memory(),
+                    "fe": torch.empty(m.n_corners + 1, dtype=torch.int32).pin_memory(),
+                    "keys": torch.empty(m.n_faces * m.key_words + 1, dtype=torch.int64).pin_memory()}
+            d2h = (3 * m.n_vertices * 8 + (m.n_faces + 1) * 8 + 2 * m.n_corners * 4 + m.n_faces * m.key_words * 8)
+        m.xyz = C.cast(C.c_void_p(bufs["xyz"].data_ptr()), C.POINTER(C.c_double))
+        m.face_offsets = C.cast(C.c_void_p(bufs["off"].data_ptr()), C.POINTER(C.c_int64))
+        m.face_vertices = C.cast(C.c_void_p(bufs["fv"].data_ptr()), C.POINTER(C.c_int32))
+        m.edge_planes = C.cast(C.c_void_p(bufs["fe"].data_ptr()), C.POINTER(C.c_int32))
+        m.face_keys = C.cast(C.c_void_p(bufs["keys"].data_ptr()), C.POINTER(C.c_uint64))
+        assert lib.am_get_mesh(ctx, nid, C.byref(m)) == 0
+        return m.n_faces
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    faces = 0
+    for _ in range(steps):
+        faces += step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    lib.am_destroy(ctx)
+    return {"value": faces / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": dt / steps * 1e3}
+
+
+def run_ours(args, dist):
+    import torch
+
+    import paper_2106_10031_gb300 as am
+    from paper_2106_10031_gb300 import native as nt
+    mlp, o, d = workload()
+    base = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(mlp, o, d)          # before any GPU work
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    precision = nt.AM_PREC_FP64 if args.precision == "fp64" else nt.AM_PREC_MIXED
+    m = am.Mesher(device=dev, max_cells=1 << 17, max_neurons=256, max_width=64, stream=stream.cuda_stream)
+    nid = m.load_mlp(mlp)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 129 MB L2
+
+    def step():
+        m.reset()
+        m.seed(nid, o, d)
+        m.march(precision=precision)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    mesh = m.get_mesh(nid)
+    faces_per_step = mesh.n_faces
+    f_compose, f_clip = algorithmic_flops(mlp, mesh)
+    torch.cuda.synchronize()
+    dist.barrier()
+    total_ms, cell_ms, launches, cell_launches = 0.0, 0.0, 0, 0
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            st = m.stats()
+            cell_ms += st["ms_cell_kernels"]
+            cell_launches += st["cell_launches"]
+            launches += st["kernel_launches"]
+    torch.cuda.synchronize()
+    dist.barrier()
+    max_ms = dist.allreduce(total_ms, "max")
+    all_faces = dist.allreduce(float(faces_per_step * args.steps), "sum")
+    value = all_faces / (max_ms / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg(mlp, o, d, args.steps, dev, stream.cuda_stream, precision)
+        e2e_ms = dist.allreduce(e2e.pop("ms_per_step") * args.steps, "max")
+        e2e["value"] = dist.allreduce(float(faces_per_step * args.steps), "sum") / (e2e_ms / 1e3)
+    m.close()
+    if dist.rank != 0:
+        return 0
+    flops_per_step = f_compose + f_clip
+    per_launch_flops = flops_per_step / max(1, cell_launches / args.steps)
+    per_launch_ms = cell_ms / max(1, cell_launches)
+    achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": args.precision,
+                   "parallelism": f"replicas x{dist.world}", "l2": "flushed before every step (256 MiB write)"},
+        "roofline": {"kernel": "cell_fp64_kernel", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None, "flops_per_launch": per_launch_flops,
+                     "launch_ms": per_launch_ms, "cell_kernel_share_of_step": cell_ms / max(total_ms, 1e-9),
+                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.19 TFLOP/s at 1995 MHz)"},
+        "cpu_baseline": base,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    dist = Dist(args.gpus)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, dist)
+        return run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -116,6 +116,9 @@ typedef struct {
     int64_t levels;           /* breadth-first levels marched */
     double ms_march;          /* device time of the march (CUDA events) */
     double ms_assemble;       /* device time of the mesh assembly */
+    double ms_cell_kernels;   /* summed device time of the cell-solving kernel launches */
+    int64_t cell_launches;    /* launches of the cell-solving kernel */
+    int64_t kernel_launches;  /* all kernel launches of the library since the last am_reset */
 } am_stats_t;
 
 /* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer
@@ -152,6 +155,9 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *desc, int *net_id);
 
 /* Forget all cells, faces and seeds of every net (the loaded nets stay). */
 am_status am_reset(am_ctx *ctx);
+
+/* Forget all cells and faces (as am_reset) and free every loaded net; net ids restart at 0. */
+am_status am_release_nets(am_ctx *ctx);
 
 /* Trigger (Alg. 1 step 2; dichotomy, Sec. 4.3.2): for each ray x(t) = o + t d, t in [0, R],
  * bisect F on the device until both ends of the bracket lie in one cell, take the exact

@@ -46,7 +46,7 @@ struct am_ctx {
     int64_t solved_upto = 0;       // cells [0, solved_upto) are solved
     am_stats_t stats{};
     std::string err;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
     // seeding scratch (grown on demand)
     double *d_rays = nullptr;
     unsigned long long *d_seed_keys = nullptr;
@@ -172,6 +172,8 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaEventCreate(&ctx->ev0));
     CU(cudaEventCreate(&ctx->ev1));
     CU(cudaEventCreate(&ctx->ev2));
+    CU(cudaEventCreate(&ctx->evk0));
+    CU(cudaEventCreate(&ctx->evk1));
     Arena &ar = ctx->ar;
     ar.kw = (d.max_neurons + 63) / 64;
     ar.maxv = d.max_face_verts;
@@ -222,6 +224,8 @@ void am_destroy(am_ctx *ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    if (ctx->evk0) cudaEventDestroy(ctx->evk0);
+    if (ctx->evk1) cudaEventDestroy(ctx->evk1);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -318,6 +322,18 @@ am_status am_reset(am_ctx *ctx)
     return AM_OK;
 }
 
+am_status am_release_nets(am_ctx *ctx)
+{
+    am_status s = am_reset(ctx);
+    if (s != AM_OK) return s;
+    for (auto &n : ctx->nets)
+        if (n.blob) CU(cudaFree(n.blob));
+    ctx->nets.clear();
+    ctx->mesh.clear();
+    ctx->max_n_loaded = ctx->max_w_loaded = 1;
+    return AM_OK;
+}
+
 am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays, double R,
                   int *n_seeded)
 {
@@ -359,6 +375,7 @@ am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double
     a.n_new = d_new;
     launch_seed(a, ctx->stream);
     CU(cudaGetLastError());
+    ctx->stats.kernel_launches += 2;
     unsigned long long hn = 0;
     CU(cudaMemcpyAsync(&hn, d_new, sizeof hn, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -462,6 +479,7 @@ static am_status assemble(am_ctx *ctx, int64_t n_cells)
         m.verts = (int64_t)vc[i];
         m.vert_base = (int64_t)vb[i];
     }
+    ctx->stats.kernel_launches += nf > 0 ? 8 : 6;
     ctx->stats.faces = nf;
     ctx->stats.corners = ncorner;
     ctx->stats.vertices = nvtx;
@@ -499,11 +517,20 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         ca.begin = f0;
         ca.end = f1;
         const int64_t n = f1 - f0;
+        CU(cudaEventRecord(ctx->evk0, ctx->stream));
         launch_cell_fp64(ca, (int)std::min<int64_t>(n, 1 << 20), ctx->stream);
         CU(cudaGetLastError());
+        CU(cudaEventRecord(ctx->evk1, ctx->stream));
         ctx->stats.levels += 1;
+        ctx->stats.cell_launches += 1;
+        ctx->stats.kernel_launches += 1;
         s = sync_status(ctx, hc);
         if (s != AM_OK) return s;
+        {
+            float kms = 0.f;
+            CU(cudaEventElapsedTime(&kms, ctx->evk0, ctx->evk1));
+            ctx->stats.ms_cell_kernels += kms;
+        }
         if (hc[kStatus] & (kStCellCap | kStHashFull | kStFaceVerts)) break;
         f0 = f1;
         f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);

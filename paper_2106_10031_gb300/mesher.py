@@ -105,6 +105,10 @@ class Mesher:
     def reset(self):
         self._check(self.lib.am_reset(self.ctx))
 
+    def release_nets(self):
+        self._check(self.lib.am_release_nets(self.ctx))
+        self.nets = []
+
     # ---- am_seed
     def seed(self, net_id: int, origins, dirs, R: float = 2.0) -> int:
         o = np.ascontiguousarray(np.atleast_2d(origins), dtype=np.float64)

@@ -52,7 +52,8 @@ class am_stats_t(C.Structure):
     _fields_ = [("cells", C.c_int64), ("faces", C.c_int64), ("empty_faces", C.c_int64),
                 ("vertices", C.c_int64), ("corners", C.c_int64), ("degenerate", C.c_int64),
                 ("open_faces", C.c_int64), ("refined_cells", C.c_int64), ("levels", C.c_int64),
-                ("ms_march", C.c_double), ("ms_assemble", C.c_double)]
+                ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
+                ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 class am_mesh(C.Structure):
@@ -70,6 +71,7 @@ ENTRY_POINTS = [
     ("am_last_error", C.c_char_p, [C.c_void_p]),
     ("am_load_mlp", C.c_int, [C.c_void_p, C.POINTER(am_mlp_desc), C.POINTER(C.c_int)]),
     ("am_reset", C.c_int, [C.c_void_p]),
+    ("am_release_nets", C.c_int, [C.c_void_p]),
     ("am_seed", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
                           C.c_double, C.POINTER(C.c_int)]),
     ("am_march", C.c_int, [C.c_void_p, C.POINTER(am_march_opts)]),
