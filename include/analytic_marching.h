@@ -179,6 +179,41 @@ am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
 
+/* ---- allocation-free vertex assignment ---------------------------------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot allocate device
+ * memory.  Code captured into a CUDA graph cannot call cudaMalloc, and some host frameworks
+ * hand out every device byte from their own pool.  Such callers can still build the mesh's
+ * vertex indices from faces they hold.
+ *
+ * For every corner of n_faces analytic faces it writes the index of the corner's mesh vertex,
+ * the same grouping as am_march's assembly: corners share an index exactly when their
+ * combinatorial vertex keys (i, j, s with bits i and j cleared) are equal.  The faces use the
+ * layout am_get_mesh returns:
+ *   d_face_keys      n_faces x key_words cell keys (device)
+ *   d_face_offsets   n_faces + 1 corner offsets, d_face_offsets[0] == 0 (device)
+ *   d_edge_planes    n_corners plane ids, edge corner c -> corner c + 1 (device)
+ *   n_neurons        N of the net; plane ids >= N (the box) carry no key bit
+ *   d_corner_vertex  out: n_corners vertex indices in [0, *d_n_vertices) (device)
+ *   d_n_vertices     out: one int64, the number of distinct vertices (device)
+ *   stream           cudaStream_t of the caller (NULL = the legacy default stream); the call is
+ *                    asynchronous on it
+ * Vertex indices are numbered in no particular order.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch
+ * memory is one file-scope device table of 2^22 hash slots (32 MiB) that every GPU loading the
+ * library keeps until the process exits.  The first call on a device looks up the table's
+ * device address with that device current; make that first call before any stream capture.
+ * Every call shares the table and clears the part it uses, so calls whose work overlaps on the
+ * GPU (two streams, or two host threads) race and give wrong results: serialise them.
+ * Returns AM_ERR_CAPACITY when n_corners > 2^21 (AM_NOALLOC_MAX_CORNERS), AM_ERR_INVALID_ARG
+ * for a NULL pointer or a negative size, AM_ERR_CUDA when no device is current or a launch
+ * fails. */
+#define AM_NOALLOC_MAX_CORNERS ((int64_t)1 << 21)
+am_status am_assign_vertices_noalloc(const uint64_t *d_face_keys, int key_words,
+                                     const int64_t *d_face_offsets, const int32_t *d_edge_planes,
+                                     int64_t n_faces, int64_t n_corners, int n_neurons,
+                                     int32_t *d_corner_vertex, int64_t *d_n_vertices, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
