@@ -33,7 +33,8 @@ import numpy as np  # noqa: E402
 METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh)"
 UNIT = "faces/s"
 WORKLOAD = "3-[64]x4-1 geometric-init SDF MLP (seed 2, sigma 0.05), 1 seed ray +x, box 1.5"
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 
 
 def parse():
@@ -42,7 +43,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--schedule", default="persistent", choices=["persistent", "levels"])
+    p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -152,25 +155,29 @@ class ClockSampler:
 # algorithmic work of the cell kernel
 
 
-def algorithmic_flops(mlp, mesh) -> tuple:
-    """FP64 flops the method must do per solved cell, summed over the mesh's faces.
+def algorithmic_work(mlp, mesh) -> dict:
+    """Work the cell kernel must do per mesh, from the mesh's cell keys.
 
-    compose (Cor. 1, masked): for l >= 2, 4 columns x n_l rows x |active(l-1)| FMAs, plus a_F
-    over |active(L)|; clip certification (Alg. 1 step 8 for the output): every row checked at
-    every final vertex, one 4-term dot product (8 flops) per (row, vertex)."""
+    macs: masked multiply-adds of the compose (Cor. 1), per cell sum over l >= 2 of
+    n_l x |active(l-1)| row-column products for 4 columns, plus a_F over |active(L)|;
+    checks: (row, vertex) sign tests of the certification, (N + 6) x |face| per cell.
+    FP64 path: 2 flops per multiply-add and per check term (4-term dot products).
+    Mixed path: one double-float multiply-add is 15 FP32 flops (TwoProd + TwoSum + 2 cross
+    FMAs) per column, 63 per row-column product with the error-bound FMA; one check is 22 FP32
+    flops (dot product, magnitude and bound)."""
     widths = mlp.widths
     N = mlp.N
     keys = mesh.face_keys
     bits = np.unpackbits(keys.view(np.uint8), axis=1, bitorder="little")[:, :N].astype(np.int64)
     r = np.cumsum([0] + widths)
-    compose = np.zeros(len(keys), dtype=np.int64)
+    rc = np.zeros(len(keys), dtype=np.int64)
     for l in range(1, len(widths)):
-        act_prev = bits[:, r[l - 1]:r[l]].sum(1)
-        compose += 8 * widths[l] * act_prev
-    compose += 8 * bits[:, r[-2]:r[-1]].sum(1)
-    nverts = np.diff(mesh.face_offsets)
-    clip = 8 * (N + 6) * nverts
-    return int(compose.sum()), int(clip.sum())
+        rc += widths[l] * bits[:, r[l - 1]:r[l]].sum(1)
+    rc += bits[:, r[-2]:r[-1]].sum(1)
+    checks = (N + 6) * np.diff(mesh.face_offsets)
+    return {"row_col_products": int(rc.sum()), "checks": int(checks.sum()),
+            "fp64_flops": int(8 * rc.sum() + 8 * checks.sum()),
+            "df_fp32_flops": int(63 * rc.sum() + 22 * checks.sum())}
 
 
 # ------------------------------------------------------------------------------------------
@@ -291,6 +298,35 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
             "ms_per_step": dt / steps * 1e3}
 
 
+def measure(m, nid, o, d, steps, precision, schedule, flush, stream, clocks=None):
+    """K timed steps; L2 flushed before each (outside the events).  Returns totals."""
+    import torch
+
+    def step():
+        m.reset()
+        m.seed(nid, o, d)
+        m.march(precision=precision, schedule=schedule)
+
+    total_ms, cell_ms, launches, cell_launches = 0.0, 0.0, 0, 0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        st = m.stats()
+        cell_ms += st["ms_cell_kernels"]
+        cell_launches += st["cell_launches"]
+        launches += st["kernel_launches"]
+    return {"total_ms": total_ms, "cell_ms": cell_ms, "launches": launches, "cell_launches": cell_launches,
+            "stats": m.stats()}
+
+
 def run_ours(args, dist):
     import torch
 
@@ -307,41 +343,31 @@ def run_ours(args, dist):
     m = am.Mesher(device=dev, max_cells=1 << 17, max_neurons=256, max_width=64, stream=stream.cuda_stream)
     nid = m.load_mlp(mlp)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 129 MB L2
-
-    def step():
-        m.reset()
-        m.seed(nid, o, d)
-        m.march(precision=precision)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
+    warm = max(args.warmup, 3)
+    measure(m, nid, o, d, warm, args.precision, args.schedule, flush, stream)
     mesh = m.get_mesh(nid)
     faces_per_step = mesh.n_faces
-    f_compose, f_clip = algorithmic_flops(mlp, mesh)
+    work = algorithmic_work(mlp, mesh)
     torch.cuda.synchronize()
     dist.barrier()
-    total_ms, cell_ms, launches, cell_launches = 0.0, 0.0, 0, 0
     with ClockSampler(dev) as clk:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            step()
-            e1.record(stream)
-            e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            st = m.stats()
-            cell_ms += st["ms_cell_kernels"]
-            cell_launches += st["cell_launches"]
-            launches += st["kernel_launches"]
+        r = measure(m, nid, o, d, args.steps, args.precision, args.schedule, flush, stream)
     torch.cuda.synchronize()
     dist.barrier()
-    max_ms = dist.allreduce(total_ms, "max")
+    max_ms = dist.allreduce(r["total_ms"], "max")
     all_faces = dist.allreduce(float(faces_per_step * args.steps), "sum")
     value = all_faces / (max_ms / 1e3)
+    plain = None
+    if not args.no_compare and args.precision != "fp64":
+        measure(m, nid, o, d, 2, "fp64", args.schedule, flush, stream)
+        p = measure(m, nid, o, d, args.steps, "fp64", args.schedule, flush, stream)
+        p_ms = dist.allreduce(p["total_ms"], "max")
+        pk = p["cell_ms"] / max(1, p["cell_launches"])
+        p_ach = work["fp64_flops"] / max(1, p["cell_launches"] / args.steps) / (pk / 1e3) / 1e12
+        plain = {"value": all_faces / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms / args.steps,
+                 "speedup_of_headline": (all_faces / (max_ms / 1e3)) / (all_faces / (p_ms / 1e3)),
+                 "roofline": {"kernel": "march_persistent_kernel<FP64>", "bound": "alu", "achieved": p_ach,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_ach / FP64_PEAK_TFLOPS}}
     e2e = None
     if not args.no_e2e:
         e2e = e2e_leg(mlp, o, d, args.steps, dev, stream.cuda_stream, precision)
@@ -350,26 +376,37 @@ def run_ours(args, dist):
     m.close()
     if dist.rank != 0:
         return 0
-    flops_per_step = f_compose + f_clip
-    per_launch_flops = flops_per_step / max(1, cell_launches / args.steps)
-    per_launch_ms = cell_ms / max(1, cell_launches)
-    achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12
+    per_launch_ms = r["cell_ms"] / max(1, r["cell_launches"])
+    launches_per_step = max(1, r["cell_launches"] / args.steps)
+    st = r["stats"]
+    if args.precision == "fp64":
+        flops, peak, kname = work["fp64_flops"], FP64_PEAK_TFLOPS, "march_persistent_kernel<FP64>"
+        psrc = "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.19 TFLOP/s at 1995 MHz)"
+    else:
+        flops, peak, kname = work["df_fp32_flops"], FP32_PEAK_TFLOPS, "march_persistent_kernel<double-float>"
+        psrc = "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 69.4 TFLOP/s at 1995 MHz)"
+    if args.schedule == "levels":
+        kname = kname.replace("persistent", "range")
+    achieved = flops / launches_per_step / (per_launch_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "warmup": warm, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": args.precision,
-                   "parallelism": f"replicas x{dist.world}", "l2": "flushed before every step (256 MiB write)"},
-        "roofline": {"kernel": "cell_fp64_kernel", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None, "flops_per_launch": per_launch_flops,
-                     "launch_ms": per_launch_ms, "cell_kernel_share_of_step": cell_ms / max(total_ms, 1e-9),
-                     "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.19 TFLOP/s at 1995 MHz)"},
+                   "schedule": args.schedule, "parallelism": f"replicas x{dist.world}",
+                   "l2": "flushed before every step (256 MiB write)"},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "flops_per_launch": flops / launches_per_step,
+                     "launch_ms": per_launch_ms, "kernel_share_of_step": r["cell_ms"] / max(r["total_ms"], 1e-9),
+                     "peak_source": psrc},
+        "plain_fp64": plain,
+        "exactness": {"refined_cells": st["refined_cells"], "close_calls": st["close_calls"],
+                      "fixups": st["fixups"], "degenerate": st["degenerate"]},
         "cpu_baseline": base,
         "e2e": e2e,
         "clocks": clk.summary(),
-        "gpu_launches": int(launches),
+        "gpu_launches": int(r["launches"]),
     }
     print(json.dumps(line))
     return 0

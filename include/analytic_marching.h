@@ -60,9 +60,16 @@ typedef enum {
 
 typedef enum {
     AM_PREC_FP64 = 0,         /* compose and clip in FP64 (the plain path) */
-    AM_PREC_MIXED = 1         /* compose in FP32 with a certified error bound, clip decisions
-                                 certified against it, uncertain cells redone in FP64 */
+    AM_PREC_MIXED = 1         /* compose in double-float arithmetic on the FP32 pipes with a
+                                 rigorous error bound per row; vertices solved in FP64; every
+                                 sign test certified against the bounds (FP32, then FP64 for
+                                 close calls); a cell with an undecidable test is redone in FP64 */
 } am_precision;
+
+typedef enum {
+    AM_SCHED_PERSISTENT = 0,  /* one launch: resident blocks take cells from a ticket queue */
+    AM_SCHED_LEVELS = 1       /* one launch per breadth-first level, synchronised by the host */
+} am_schedule;
 
 /* Context creation options.  Zero-initialised fields take the documented defaults. */
 typedef struct {
@@ -101,6 +108,8 @@ typedef struct {
     am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
     int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
     int use_proposal;         /* reserved for the learned constraint proposal (0) */
+    am_schedule schedule;     /* AM_SCHED_PERSISTENT (default) or AM_SCHED_LEVELS */
+    int grid_blocks;          /* persistent schedule: blocks to launch (0 = all resident) */
 } am_march_opts;
 
 /* Statistics of the last march (cumulative over resumed calls). */
@@ -119,6 +128,12 @@ typedef struct {
     double ms_cell_kernels;   /* summed device time of the cell-solving kernel launches */
     int64_t cell_launches;    /* launches of the cell-solving kernel */
     int64_t kernel_launches;  /* all kernel launches of the library since the last am_reset */
+    int64_t close_calls;      /* mixed precision: sign tests re-evaluated in FP64 */
+    int64_t fixups;           /* faces whose candidate polygon the all-row check corrected */
+    int64_t phase_cycles[10]; /* SM cycles summed over cells per phase (compose, set-up, candidate
+                                 sort, candidate clip, FP64 vertices, check, emit, march, waiting
+                                 for work, spare); only filled by a build with -DAM_PHASE_TIMERS,
+                                 zero otherwise */
 } am_stats_t;
 
 /* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer

@@ -23,8 +23,9 @@ constexpr int kMaxNets = 1024;
 constexpr unsigned long long kZobristSeed = 0x2106100310031ull;
 
 struct NetHost {
-    NetDev dev;              // device pointers into `blob`
-    double *blob = nullptr;  // device allocation holding AT, Cl, w_out
+    NetDev dev;              // device pointers into `blob` and `fblob`
+    double *blob = nullptr;  // device allocation holding AT, Cl, w_out (FP64)
+    float *fblob = nullptr;  // the same as double-float pairs (hi, lo)
     int N = 0, max_w = 0;
 };
 
@@ -43,6 +44,7 @@ struct am_ctx {
     NetDev *d_nets = nullptr;
     std::vector<NetHost> nets;
     int max_n_loaded = 1, max_w_loaded = 1;
+    int sm_count = 0, blocks_per_sm = 0;
     int64_t solved_upto = 0;       // cells [0, solved_upto) are solved
     am_stats_t stats{};
     std::string err;
@@ -185,6 +187,9 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaMalloc(&ar.nverts, sizeof(int32_t) * ar.cap));
     CU(cudaMalloc(&ar.edges, sizeof(int32_t) * ar.cap * ar.maxv));
     CU(cudaMalloc(&ar.verts, sizeof(double) * 3 * ar.cap * ar.maxv));
+    CU(cudaMalloc(&ar.ready, sizeof(unsigned) * ar.cap));
+    CU(cudaMalloc(&ar.entry_plane, sizeof(int32_t) * ar.cap));
+    CU(cudaMalloc(&ar.entry_pt, sizeof(float) * 3 * ar.cap));
     CU(cudaMalloc(&ar.slots, sizeof(unsigned long long) * d.hash_slots));
     CU(cudaMalloc(&ar.counters, sizeof(unsigned long long) * kNumCounters));
     {
@@ -199,7 +204,18 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaMalloc(&ctx->d_netcnt, sizeof(unsigned long long) * 6 * kMaxNets));
     CU(cudaMemsetAsync(ar.slots, 0, sizeof(unsigned long long) * d.hash_slots, ctx->stream));
     CU(cudaMemsetAsync(ar.counters, 0, sizeof(unsigned long long) * kNumCounters, ctx->stream));
-    CU(prepare_cell_kernels(d.max_neurons, d.max_width));
+    CU(cudaMemsetAsync(ar.ready, 0, sizeof(unsigned) * ar.cap, ctx->stream));
+    {
+        const int smem = march_smem_bytes(d.max_neurons, d.max_width);
+        int optin = 0;
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d.device));
+        if (smem > optin)
+            return fail(ctx, AM_ERR_INVALID_ARG, "max_neurons=%d / max_width=%d need %d B of shared memory per block "
+                        "(device allows %d)", d.max_neurons, d.max_width, smem, optin);
+    }
+    CU(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, d.device));
+    CU(prepare_march_kernels(d.max_neurons, d.max_width, &ctx->blocks_per_sm));
+    if (ctx->blocks_per_sm < 1) return fail(ctx, AM_ERR_CUDA, "the march kernel cannot be resident");
     CU(prepare_seed_kernels(d.max_neurons, d.max_width));
     CU(cudaStreamSynchronize(ctx->stream));
     return AM_OK;
@@ -214,13 +230,16 @@ void am_destroy(am_ctx *ctx)
     }
     Arena &ar = ctx->ar;
     void *bufs[] = {ar.keys, ar.net, ar.hash, ar.nverts, ar.edges, ar.verts, ar.slots, ar.counters,
+                    ar.ready, ar.entry_plane, ar.entry_pt,
                     (void *)ar.zob, ctx->d_nets, ctx->d_netcnt, ctx->d_rays, ctx->d_seed_keys, ctx->d_seed_x,
                     ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv, ctx->d_fe,
                     ctx->d_xyz, ctx->d_fkeys, ctx->d_vslots};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    for (auto &n : ctx->nets)
+    for (auto &n : ctx->nets) {
         if (n.blob) cudaFree(n.blob);
+        if (n.fblob) cudaFree(n.fblob);
+    }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -279,9 +298,19 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     }
     const size_t offW = host.size();
     host.insert(host.end(), dsc->w_out, dsc->w_out + dsc->width[L - 1]);
+    // double-float split of every value: hi = fl32(x), lo = fl32(x - hi)
+    std::vector<float> fhost(2 * host.size());
+    for (size_t i = 0; i < host.size(); ++i) {
+        const float h = (float)host[i];
+        fhost[i] = h;
+        fhost[host.size() + i] = (float)(host[i] - (double)h);
+    }
     NetHost nh;
     CU(cudaMalloc(&nh.blob, sizeof(double) * host.size()));
+    CU(cudaMalloc(&nh.fblob, sizeof(float) * fhost.size()));
     CU(cudaMemcpyAsync(nh.blob, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(nh.fblob, fhost.data(), sizeof(float) * fhost.size(), cudaMemcpyHostToDevice, ctx->stream));
+    const size_t lo_off = host.size();
     NetDev &nd = nh.dev;
     memset(&nd, 0, sizeof nd);
     nd.L = L;
@@ -294,8 +323,14 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         r0 += nd.width[l];
         nd.Cl[l] = nh.blob + offC[l];
         nd.AT[l] = l > 1 ? nh.blob + offA[l] : nullptr;
+        nd.Clhi[l] = nh.fblob + offC[l];
+        nd.Cllo[l] = nh.fblob + lo_off + offC[l];
+        nd.AThi[l] = l > 1 ? nh.fblob + offA[l] : nullptr;
+        nd.ATlo[l] = l > 1 ? nh.fblob + lo_off + offA[l] : nullptr;
     }
     nd.w_out = nh.blob + offW;
+    nd.w_out_hi = nh.fblob + offW;
+    nd.w_out_lo = nh.fblob + lo_off + offW;
     nd.b_out = dsc->b_out;
     const int id = (int)ctx->nets.size();
     nd.salt = splitmix64(0xA11CE5EEDull + (unsigned long long)id * 0x9E3779B97F4A7C15ull);
@@ -315,6 +350,7 @@ am_status am_reset(am_ctx *ctx)
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
     CU(cudaMemsetAsync(ctx->ar.slots, 0, sizeof(unsigned long long) * (ctx->ar.slot_mask + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->ar.counters, 0, sizeof(unsigned long long) * kNumCounters, ctx->stream));
+    CU(cudaMemsetAsync(ctx->ar.ready, 0, sizeof(unsigned) * ctx->ar.cap, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->solved_upto = 0;
     ctx->stats = am_stats_t{};
@@ -326,8 +362,10 @@ am_status am_release_nets(am_ctx *ctx)
 {
     am_status s = am_reset(ctx);
     if (s != AM_OK) return s;
-    for (auto &n : ctx->nets)
+    for (auto &n : ctx->nets) {
         if (n.blob) CU(cudaFree(n.blob));
+        if (n.fblob) CU(cudaFree(n.fblob));
+    }
     ctx->nets.clear();
     ctx->mesh.clear();
     ctx->max_n_loaded = ctx->max_w_loaded = 1;
@@ -495,47 +533,77 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (o) op = *o;
     if (!(op.box > 0.0)) op.box = 1.5;
     if (!(op.delta > 0.0)) op.delta = 1e-10;
-    if (op.precision != AM_PREC_FP64)
-        return fail(ctx, AM_ERR_INVALID_ARG, "precision %d is not available in this build", (int)op.precision);
+    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)op.precision);
+    if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
+    if (op.max_cells < 0 || op.grid_blocks < 0) return fail(ctx, AM_ERR_INVALID_ARG, "negative limit");
+    const int mode = op.precision == AM_PREC_MIXED ? 1 : 0;
     unsigned long long hc[kNumCounters];
     am_status s = sync_status(ctx, hc);
     if (s != AM_OK) return s;
-    CellArgs ca{};
-    ca.nets = ctx->d_nets;
-    ca.ar = ctx->ar;
-    ca.box = op.box;
-    ca.delta = op.delta;
-    ca.max_n = ctx->opts.max_neurons;
-    ca.max_w = ctx->opts.max_width;
-    CU(cudaEventRecord(ctx->ev0, ctx->stream));
-    int64_t f0 = ctx->solved_upto, f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
-    const int64_t start = f0;
+    MarchArgs ma{};
+    ma.nets = ctx->d_nets;
+    ma.ar = ctx->ar;
+    ma.box = op.box;
+    ma.delta = op.delta;
+    ma.max_n = ctx->opts.max_neurons;
+    ma.max_w = ctx->opts.max_width;
+    const int64_t start = ctx->solved_upto;
+    const int64_t limit = op.max_cells > 0 ? std::min<int64_t>(start + op.max_cells, ctx->ar.cap) : ctx->ar.cap;
     bool incomplete = false;
-    while (f0 < f1) {
-        if (op.max_cells > 0 && f0 - start >= op.max_cells) { incomplete = true; break; }
-        if (op.max_cells > 0) f1 = std::min<int64_t>(f1, start + op.max_cells);
-        ca.begin = f0;
-        ca.end = f1;
-        const int64_t n = f1 - f0;
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (op.schedule == AM_SCHED_PERSISTENT) {
+        // tickets restart at the first unsolved cell; every earlier cell counts as done
+        const unsigned long long hs = (unsigned long long)start;
+        CU(cudaMemcpyAsync(ctx->ar.counters + kHead, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->ar.counters + kDone, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
+        ma.limit = limit;
+        int grid = ctx->sm_count * ctx->blocks_per_sm;
+        if (op.grid_blocks > 0) grid = std::min(grid, op.grid_blocks);
         CU(cudaEventRecord(ctx->evk0, ctx->stream));
-        launch_cell_fp64(ca, (int)std::min<int64_t>(n, 1 << 20), ctx->stream);
+        launch_march(ma, mode, true, grid, ctx->stream);
         CU(cudaGetLastError());
         CU(cudaEventRecord(ctx->evk1, ctx->stream));
-        ctx->stats.levels += 1;
         ctx->stats.cell_launches += 1;
         ctx->stats.kernel_launches += 1;
         s = sync_status(ctx, hc);
         if (s != AM_OK) return s;
-        {
+        float kms = 0.f;
+        CU(cudaEventElapsedTime(&kms, ctx->evk0, ctx->evk1));
+        ctx->stats.ms_cell_kernels += kms;
+        const int64_t n = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
+        ctx->solved_upto = std::min<int64_t>(n, limit);
+        incomplete = op.max_cells > 0 && (int64_t)hc[kNCells] > ctx->solved_upto;
+    } else {
+        int64_t f0 = start, f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
+        while (f0 < f1) {
+            if (f0 >= limit) { incomplete = true; break; }
+            f1 = std::min<int64_t>(f1, limit);
+            ma.begin = f0;
+            ma.end = f1;
+            CU(cudaEventRecord(ctx->evk0, ctx->stream));
+            launch_march(ma, mode, false, (int)std::min<int64_t>(f1 - f0, 1 << 20), ctx->stream);
+            CU(cudaGetLastError());
+            CU(cudaEventRecord(ctx->evk1, ctx->stream));
+            ctx->stats.levels += 1;
+            ctx->stats.cell_launches += 1;
+            ctx->stats.kernel_launches += 1;
+            s = sync_status(ctx, hc);
+            if (s != AM_OK) return s;
             float kms = 0.f;
             CU(cudaEventElapsedTime(&kms, ctx->evk0, ctx->evk1));
             ctx->stats.ms_cell_kernels += kms;
+            if (hc[kStatus] & (kStCellCap | kStHashFull | kStFaceVerts | kStTimeout)) break;
+            f0 = f1;
+            f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
         }
-        if (hc[kStatus] & (kStCellCap | kStHashFull | kStFaceVerts)) break;
-        f0 = f1;
-        f1 = std::min<int64_t>((int64_t)hc[kNCells], ctx->ar.cap);
+        ctx->solved_upto = f0;
+        // keep the ticket counters consistent with the cells solved so far
+        const unsigned long long hs = (unsigned long long)f0;
+        CU(cudaMemcpyAsync(ctx->ar.counters + kHead, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->ar.counters + kDone, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
     }
-    ctx->solved_upto = f0;
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     s = assemble(ctx, ctx->solved_upto);
     if (s != AM_OK) return s;
@@ -551,6 +619,9 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ctx->stats.empty_faces = (int64_t)hc[kEmpty];
     ctx->stats.degenerate = (int64_t)hc[kDegenerate];
     ctx->stats.refined_cells = (int64_t)hc[kRefined];
+    ctx->stats.close_calls = (int64_t)hc[kCloseCalls];
+    ctx->stats.fixups = (int64_t)hc[kFixups];
+    for (int i = 0; i < 10; ++i) ctx->stats.phase_cycles[i] = (int64_t)hc[kPhase0 + i * kCtrStride];
     s = status_error(ctx, hc[kStatus]);
     if (s != AM_OK) return s;
     if (hc[kStatus] & kStClip) ctx->err = "a clip step met an inconsistent polygon (reported as an empty face)";

@@ -78,11 +78,13 @@ __device__ __forceinline__ void block_argmax(double v, int idx, double *red_v, i
 }
 
 // key(pa) ^ e_fa == key(pb) ^ e_fb ?  (kNoFlip = no bit flipped)
+// Keys written by other blocks of a running kernel are read through L2 (ld.global.cg): the
+// SM's L1 is not coherent with other SMs' writes and may hold a stale copy of the line.
 __device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsigned fa, int64_t pb, unsigned fb)
 {
     const unsigned long long *ka = ar.keys + pa * ar.kw, *kb = ar.keys + pb * ar.kw;
     for (int w = 0; w < ar.kw; ++w) {
-        unsigned long long x = ka[w] ^ kb[w];
+        unsigned long long x = __ldcg(ka + w) ^ __ldcg(kb + w);
         if (fa != kNoFlip && (int)(fa >> 6) == w) x ^= 1ull << (fa & 63);
         if (fb != kNoFlip && (int)(fb >> 6) == w) x ^= 1ull << (fb & 63);
         if (x) return false;
@@ -92,10 +94,11 @@ __device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsi
 
 // Alg. 1 steps 10-11: the neighbour key(parent) ^ e_flip (hash h) is pushed unless it was
 // seen before.  The slot records (parent, flip), from which any later probe rebuilds the
-// key, so a claim never waits for a key to be written.  A claim hands out the next cell id
-// and writes the new cell's key there.
-__device__ inline void insert_neighbor(const Arena &ar, int64_t parent, int net, unsigned flip,
-                                       unsigned long long h)
+// key, so a claim never waits for a key to be written.  A claim hands out the next cell id,
+// writes the new cell's record there (key, net, hash, the crossed plane and a point of the
+// shared edge), then publishes it through ready[id].
+__device__ __forceinline__ void insert_neighbor(const Arena &ar, int64_t parent, int net, unsigned flip,
+                                             unsigned long long h, float px, float py, float pz)
 {
     const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
     unsigned long long pos = h & ar.slot_mask;
@@ -112,20 +115,26 @@ __device__ inline void insert_neighbor(const Arena &ar, int64_t parent, int net,
                 const unsigned long long *kp = ar.keys + parent * ar.kw;
                 unsigned long long *kn = ar.keys + id * ar.kw;
                 for (int w = 0; w < ar.kw; ++w) {
-                    unsigned long long x = kp[w];
+                    unsigned long long x = __ldcg(kp + w);
                     if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
                     kn[w] = x;
                 }
                 ar.net[id] = net;
                 ar.hash[id] = h;
                 ar.nverts[id] = -1;
+                ar.entry_plane[id] = (int32_t)flip;
+                ar.entry_pt[id * 3 + 0] = px;
+                ar.entry_pt[id * 3 + 1] = py;
+                ar.entry_pt[id * 3 + 2] = pz;
+                __threadfence();
+                atomicExch(ar.ready + id, 1u);
                 return;
             }
             cur = prev;
         }
         if (slot_tag(cur) == hash_tag(h)) {
             const int64_t pb = slot_parent(cur);
-            if (ar.net[pb] == net && ref_keys_equal(ar, parent, flip, pb, slot_flip(cur))) return;
+            if (__ldcg(ar.net + pb) == net && ref_keys_equal(ar, parent, flip, pb, slot_flip(cur))) return;
         }
         pos = (pos + 1) & ar.slot_mask;
     }

@@ -1,9 +1,9 @@
 // am_common.cuh -- device-side data layout shared by the library's kernels.
 //
 // Cells, keys and faces live in flat arenas indexed by a cell id.  Ids are handed out in
-// the order cells are discovered, so the cells found while solving breadth-first level i
-// form the contiguous id range of level i + 1 (Alg. 1's active set S* is a range of ids;
-// S. the set of all ids handed out so far, indexed by the hash table).
+// the order cells are discovered; the march solves them in id order (first in, first out),
+// so the id range [solved, allocated) is Alg. 1's active set S* and every id ever handed
+// out, indexed by the hash table, is S* u S.
 #pragma once
 
 #include <cstdint>
@@ -30,29 +30,41 @@ enum : unsigned long long {
     kStClip = 128ull,       // a clip step met an inconsistent polygon
 };
 
-// indices into the device counter array
+// indices into the device counter array.  Every counter sits on its own 128-byte line
+// (a stride of 16 words) so that the ticket counters polled by waiting blocks do not share a
+// line with the counters every solved cell updates.
+constexpr int kCtrStride = 16;
 enum {
-    kNCells = 0,        // cell ids handed out
-    kStatus = 1,        // sticky status bits
-    kDegenerate = 2,    // planes within delta of accepted vertices
-    kEmpty = 3,         // cells whose face was empty / of zero area
-    kSolved = 4,        // cells solved
-    kRefined = 5,       // mixed precision: cells redone in FP64
-    kNumCounters = 16
+    kNCells = 0 * kCtrStride,       // cell ids handed out
+    kStatus = 1 * kCtrStride,       // sticky status bits
+    kDegenerate = 2 * kCtrStride,   // planes within delta of accepted vertices
+    kEmpty = 3 * kCtrStride,        // cells whose face was empty / of zero area
+    kSolved = 4 * kCtrStride,       // cells solved
+    kRefined = 5 * kCtrStride,      // mixed precision: cells redone in FP64
+    kHead = 6 * kCtrStride,         // next queue ticket (persistent schedule)
+    kDone = 7 * kCtrStride,         // tickets finished (solved, dead or skipped)
+    kCloseCalls = 8 * kCtrStride,   // mixed precision: sign tests re-evaluated in FP64
+    kFixups = 9 * kCtrStride,       // faces whose candidate polygon the full check corrected
+    kPhase0 = 10 * kCtrStride,      // 10 per-phase cycle counters (timing builds only)
+    kNumCounters = 20 * kCtrStride
 };
 
-// One loaded network, folded for the device (row-major, FP64):
+// One loaded network, folded for the device (row-major):
 //   pre_l = AT_l^T h_{l-1} + Cl_l [x; 1]
 // AT_l (l >= 2) is the hidden part of W_l transposed, n_{l-1} x n_l; Cl_l (n_l x 4) is the
 // cell-independent affine part: [W_1 | b_1 + W_1^z z] at layer 1, [W^x | b + W^z z] at the
-// skip layer, [0 | b_l] elsewhere.
+// skip layer, [0 | b_l] elsewhere.  Every array exists in FP64 and as a double-float pair
+// (hi = fl32(x), lo = fl32(x - hi)).
 struct NetDev {
     int L, N, kw;
     int width[kMaxLayers + 1];   // 1..L
     int row0[kMaxLayers + 1];    // id of the first neuron of layer l
     const double *AT[kMaxLayers + 1];
     const double *Cl[kMaxLayers + 1];
+    const float *AThi[kMaxLayers + 1], *ATlo[kMaxLayers + 1];
+    const float *Clhi[kMaxLayers + 1], *Cllo[kMaxLayers + 1];
     const double *w_out;
+    const float *w_out_hi, *w_out_lo;
     double b_out;
     unsigned long long salt;     // per-net hash salt
 };
@@ -62,9 +74,12 @@ struct Arena {
     unsigned long long *keys;    // cap x kw
     int32_t *net;                // cap
     unsigned long long *hash;    // cap (Zobrist hash of the key, salted by the net)
-    int32_t *nverts;             // cap: corners of the cell's face (0 = empty)
+    int32_t *nverts;             // cap: corners of the cell's face (0 = empty, -1 unsolved, -2 dead)
     int32_t *edges;              // cap x maxv: plane of edge i -> i+1
     double *verts;               // cap x maxv x 3
+    unsigned *ready;             // cap: 1 once the cell's record is written (persistent schedule)
+    int32_t *entry_plane;        // cap: plane crossed to reach the cell (-1 for a seed)
+    float *entry_pt;             // cap x 3: a point of the face (edge midpoint or seed point)
     unsigned long long *slots;   // cell hash table
     unsigned long long slot_mask;
     const unsigned long long *zob;   // Zobrist table, one 64-bit value per neuron id

@@ -8,16 +8,18 @@
 
 namespace am {
 
-struct CellArgs {
+struct MarchArgs {
     const NetDev *nets;
     Arena ar;
-    int64_t begin, end;      // cell ids solved by this launch
     double box, delta;
-    int max_n, max_w;        // smem sizing (largest loaded net)
+    int max_n, max_w;        // shared-memory sizing (largest loadable net)
+    long long limit;         // persistent schedule: tickets >= limit are not solved
+    int64_t begin, end;      // level schedule: cell ids solved by this launch
 };
-int cell_smem_bytes(int max_n, int max_w);
-cudaError_t prepare_cell_kernels(int max_n, int max_w);
-void launch_cell_fp64(const CellArgs &a, int grid, cudaStream_t st);
+int march_smem_bytes(int max_n, int max_w);
+cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
+// mode 0 = FP64, 1 = double-float (mixed); persistent = ticket queue, else one level [begin, end)
+void launch_march(const MarchArgs &a, int mode, bool persistent, int grid, cudaStream_t st);
 
 struct SeedArgs {
     const NetDev *nets;

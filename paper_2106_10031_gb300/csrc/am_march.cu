@@ -1,0 +1,1047 @@
+// am_march.cu -- the march: one thread block solves one analytic cell at a time.
+//
+// Per cell (Alg. 1 steps 4-11):
+//   a2 compose : Z_l = W_l diag(s_{l-1}) Z_{l-1} + C_l (Lemma 1, Cor. 1) over the active
+//                neurons of the previous layer, then a_F (Eq. 8);
+//   a3 rows    : c_k = (1 - 2 s_k) Z_k (Eq. 10) plus the box rows;
+//   a4 clip    : the face plane a_F [x;1] = 0 (Eq. 12) starts as a square around the box
+//                section.  Warp 0 cuts it by the 32 rows nearest to a point known to lie on
+//                the face (the midpoint of the edge the cell was entered through, or the seed
+//                point) in order of distance, each cut re-solving its two new vertices from
+//                their planes (Eq. 11);
+//   a5 check   : every thread then tests every row at every vertex of that polygon (Alg. 1
+//                step 8 for the output); a violated row is cut in and the check repeated, so
+//                the result is the clip by all rows whatever the candidates were;
+//   a6 emit    : corners and edge planes to the face arena;
+//   a7 march   : each edge on a neuron plane flips that neuron (Alg. 1 step 10) and pushes
+//                the neighbour through the hash table (step 11).
+//
+// Two arithmetic modes.  kFP64: everything in FP64, a plane within delta of a vertex counts as
+// satisfied (and as a degenerate event), as in the oracle.  kDF (mixed): the compose runs in
+// double-float arithmetic on the FP32 pipes (TwoProd/TwoSum, the error-free transformations of
+// Ogita, Rump & Oishi, "Accurate sum and dot product", 2005) and carries a rigorous bound on
+// each row's error; polygon vertices are solved in FP64; every sign decision of the check is
+// certified against the bounds (FP32 first, FP64 for the close calls) and a cell with an
+// undecidable test is solved again in kFP64.
+//
+// Two schedules.  Persistent: a grid of resident blocks takes tickets (cell ids, in order)
+// from a counter and waits, with a time limit, for the ticket's cell to be published; it stops
+// when every handed-out cell is finished.  Levels: one launch per breadth-first level.
+#include <algorithm>
+
+#include "am_block.cuh"
+#include "am_kernels.h"
+
+namespace am {
+
+constexpr int kT = 256;           // threads per block
+constexpr int kNW = kT / 32;      // warps per block
+constexpr int kMaxPoly = 64;      // polygon vertices in flight
+constexpr int kNear = 32;         // rows clipped by warp 0 before the full check
+constexpr int kMaxFix = 8;        // check / fix-up rounds
+constexpr float kU = 5.9604645e-8f;            // 2^-24
+constexpr long long kWaitNs = 4000000000ll;    // 4 s limit on any wait for work
+
+enum { kFP64 = 0, kDF = 1 };
+
+// Optional per-phase cycle counters (build with -DAM_PHASE_TIMERS): thread 0 of each block adds
+// the clock64() cycles of each phase of each cell to counters[kPhase0 + phase * kCtrStride].
+#ifdef AM_PHASE_TIMERS
+#define AM_TICK(t) do { if (threadIdx.x == 0) (t) = clock64(); } while (0)
+#define AM_PHASE(a, i, t0, t1) do { if (threadIdx.x == 0) atomicAdd((a).ar.counters + kPhase0 + (i) * kCtrStride, \
+    (unsigned long long)((t1) - (t0))); } while (0)
+#else
+#define AM_TICK(t) do { } while (0)
+#define AM_PHASE(a, i, t0, t1) do { } while (0)
+#endif
+
+// ------------------------------------------------------------------------------------------
+// shared-memory layout
+
+struct Lay {
+    int mask, rows, err, rinv, carry, act, part, pv, pe, pf, vf, dvb, near, viol, sc, total;
+};
+
+__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline Lay march_layout(int max_n, int max_w)
+{
+    Lay s;
+    const int nr = max_n + kBoxPlanes + kSquarePlanes;
+    int o = 0;
+    s.mask = o;  o = al16(o + ((max_n + 31) / 32) * 4);
+    s.rows = o;  o = al16(o + nr * 32);                 // double[4] (FP64) or float[4] hi + float[4] lo (DF)
+    s.err = o;   o = al16(o + nr * 4);
+    s.rinv = o;  o = al16(o + nr * 4);
+    s.carry = o; o = al16(o + max_w * 4);
+    s.act = o;   o = al16(o + max_w * 4);
+    s.part = o;  o = al16(o + kT * 40);
+    s.pv = o;    o = al16(o + 2 * kMaxPoly * 3 * 8);
+    s.pe = o;    o = al16(o + 2 * kMaxPoly * 4);
+    s.pf = o;    o = al16(o + 2 * kMaxPoly * 3 * 4);
+    s.vf = o;    o = al16(o + kMaxPoly * 4 * 4);
+    s.dvb = o;   o = al16(o + kMaxPoly * 4);
+    s.near = o;  o = al16(o + 2 * kNear * 4 + 2 * kNear * 4);
+    s.viol = o;  o = al16(o + nr * 4);
+    s.sc = o;    o = al16(o + 512);
+    s.total = o;
+    return s;
+}
+
+int march_smem_bytes(int max_n, int max_w) { return march_layout(max_n, max_w).total; }
+
+struct Sh {
+    unsigned *mask;
+    double *r64;            // FP64 rows [nr][4]
+    float *rhi, *rlo;       // DF rows [nr][4] each
+    float *err, *rinv, *carry;
+    int *act;
+    float *partf;
+    double *partd;
+    double (*pv)[kMaxPoly][3];
+    int (*pe)[kMaxPoly];
+    float (*pf)[kMaxPoly][3];   // kDF: the FP32 polygon of the candidate pass
+    float (*vf)[4];             // final vertices in FP32 and max(1, |v|_inf)
+    float *dvb;
+    int *near_k, *near_w;
+    float *near_d, *near_dw;
+    int *viol;
+    // scalars
+    double *aF;             // 4 (FP64 value, or hi+lo of the DF value)
+    float *aFhi, *aFlo;     // 4 + 4
+    float *eF;              // 1
+    int *si;                // 32 ints: 0 m, 1 buf, 2 status, 3 nviol, 4 amb, 5 ndeg, 6 emit, 7 ticket,
+                            //          8 near count, 9 fix rounds
+    int *wsum;              // 32 ints
+    unsigned long long *blk;   // per-block statistics, flushed once when the block exits:
+                               // 0 solved, 1 empty, 2 degenerate, 3 fixups, 4 refined, 5 close calls
+};
+
+__device__ inline Sh make_sh(unsigned char *base, int max_n, int max_w)
+{
+    const Lay L = march_layout(max_n, max_w);
+    const int nr = max_n + kBoxPlanes + kSquarePlanes;
+    Sh s;
+    s.mask = (unsigned *)(base + L.mask);
+    s.r64 = (double *)(base + L.rows);
+    s.rhi = (float *)(base + L.rows);
+    s.rlo = s.rhi + 4 * nr;
+    s.err = (float *)(base + L.err);
+    s.rinv = (float *)(base + L.rinv);
+    s.carry = (float *)(base + L.carry);
+    s.act = (int *)(base + L.act);
+    s.partf = (float *)(base + L.part);
+    s.partd = (double *)(base + L.part);
+    s.pv = (double(*)[kMaxPoly][3])(base + L.pv);
+    s.pe = (int(*)[kMaxPoly])(base + L.pe);
+    s.pf = (float(*)[kMaxPoly][3])(base + L.pf);
+    s.vf = (float(*)[4])(base + L.vf);
+    s.dvb = (float *)(base + L.dvb);
+    s.near_k = (int *)(base + L.near);
+    s.near_d = (float *)(s.near_k + kNear);
+    s.near_w = (int *)(s.near_d + kNear);
+    s.near_dw = (float *)(s.near_w + kNear);
+    s.viol = (int *)(base + L.viol);
+    double *sc = (double *)(base + L.sc);
+    s.aF = sc;                                   // 4 doubles
+    s.aFhi = (float *)(sc + 4);                  // 4 floats
+    s.aFlo = s.aFhi + 4;                         // 4 floats
+    s.eF = s.aFlo + 4;                           // 1 float (+3 pad)
+    s.si = (int *)(s.eF + 4);                    // 32 ints
+    s.wsum = s.si + 32;                          // 32 ints
+    s.blk = (unsigned long long *)(s.wsum + 32); // 8 x u64
+    return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// arithmetic helpers
+
+__device__ __forceinline__ bool bit_of(const unsigned *mask, int k) { return (mask[k >> 5] >> (k & 31)) & 1u; }
+
+// s += a * z in double-float: (sh, sl) accumulates, a = ah + al, z = zh + zl.  The product
+// ah*zh is split exactly (TwoProd with an FMA), the sum with TwoSum; the small cross terms and
+// every error term go to sl.  Explicit _rn intrinsics keep the compiler from fusing them.
+__device__ __forceinline__ void df_fma(float &sh, float &sl, float ah, float al, float zh, float zl)
+{
+    const float p = __fmul_rn(ah, zh);
+    float pe = __fmaf_rn(ah, zh, -p);
+    pe = __fmaf_rn(ah, zl, pe);
+    pe = __fmaf_rn(al, zh, pe);
+    const float t = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, pe));
+}
+
+// (sh, sl) += (bh, bl) (TwoSum on the high parts)
+__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl)
+{
+    const float t = __fadd_rn(sh, bh);
+    const float bp = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(bh, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, bl));
+}
+
+// renormalise so that |lo| <= ulp(hi) / 2 (Fast2Sum)
+__device__ __forceinline__ void df_norm(float &h, float &l)
+{
+    const float s = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(s, h));
+    h = s;
+}
+
+// gamma-style coefficient of the double-float dot product bound: 2 (m + 4)^2 u^2
+__device__ __forceinline__ float df_gamma(int m) { return 2.0f * (float)(m + 4) * (float)(m + 4) * kU * kU; }
+
+// Vertex of planes p, q and the face plane f (Eq. 11 with biases) by Cramer's rule with cross
+// products; optionally the infinity norm of the inverse system matrix.
+template <class R>
+__device__ __forceinline__ bool solve3(const R *p, const R *q, const R *f, R *v, R *inv_norm)
+{
+    const R c0x = q[1] * f[2] - q[2] * f[1], c0y = q[2] * f[0] - q[0] * f[2], c0z = q[0] * f[1] - q[1] * f[0];
+    const R c1x = f[1] * p[2] - f[2] * p[1], c1y = f[2] * p[0] - f[0] * p[2], c1z = f[0] * p[1] - f[1] * p[0];
+    const R c2x = p[1] * q[2] - p[2] * q[1], c2y = p[2] * q[0] - p[0] * q[2], c2z = p[0] * q[1] - p[1] * q[0];
+    const R det = p[0] * c0x + p[1] * c0y + p[2] * c0z;
+    if (det == R(0)) return false;
+    const R inv = R(-1) / det;
+    v[0] = (p[3] * c0x + q[3] * c1x + f[3] * c2x) * inv;
+    v[1] = (p[3] * c0y + q[3] * c1y + f[3] * c2y) * inv;
+    v[2] = (p[3] * c0z + q[3] * c1z + f[3] * c2z) * inv;
+    if (inv_norm) {
+        const R ax = fabs(c0x) + fabs(c1x) + fabs(c2x), ay = fabs(c0y) + fabs(c1y) + fabs(c2y),
+                az = fabs(c0z) + fabs(c1z) + fabs(c2z);
+        *inv_norm = fmax(ax, fmax(ay, az)) * fabs(inv);
+    }
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+// row k as FP64 (both modes; in kDF hi + lo is exact in FP64)
+template <int M>
+__device__ __forceinline__ void row64(const Sh &s, int k, double *r)
+{
+    if (M == kFP64) {
+        r[0] = s.r64[4 * k]; r[1] = s.r64[4 * k + 1]; r[2] = s.r64[4 * k + 2]; r[3] = s.r64[4 * k + 3];
+    } else {
+        for (int c = 0; c < 4; ++c) r[c] = (double)s.rhi[4 * k + c] + (double)s.rlo[4 * k + c];
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// a2/a3: compose the rows of every neuron of the cell, and a_F
+
+template <int M>
+__device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
+{
+    const int tid = threadIdx.x;
+    // layer 1: Z_1 = C_1 (cell independent)
+    {
+        const int n1 = net.width[1];
+        for (int k = tid; k < n1; k += kT) {
+            const bool act = bit_of(s.mask, k);
+            if (M == kFP64) {
+                const double sg = act ? -1.0 : 1.0;
+                for (int c = 0; c < 4; ++c) s.r64[4 * k + c] = sg * net.Cl[1][4 * k + c];
+            } else {
+                const float sg = act ? -1.0f : 1.0f;
+                float l1 = 0.0f;
+                for (int c = 0; c < 4; ++c) {
+                    const float h = net.Clhi[1][4 * k + c], l = net.Cllo[1][4 * k + c];
+                    s.rhi[4 * k + c] = sg * h;
+                    s.rlo[4 * k + c] = sg * l;
+                    l1 += fabsf(h);
+                }
+                s.err[k] = 2.0f * kU * kU * l1 * 1.01f;     // representation of C in double-float
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = 2; l <= net.L; ++l) {
+        const int np = net.width[l - 1], nl = net.width[l], rp = net.row0[l - 1], rl = net.row0[l];
+        const int S = nl >= kT ? 1 : kT / nl;
+        // active list of layer l-1 (diag(s_{l-1}) selects these rows)
+        int nact = 0;
+        for (int base = 0; base < np; base += kT) {
+            const int j = base + tid;
+            const int f = (j < np) ? (int)bit_of(s.mask, rp + j) : 0;
+            int tot;
+            const int pos = block_scan_excl(f, s.wsum, &tot);
+            if (f) s.act[nact + pos] = j;
+            nact += tot;
+        }
+        __syncthreads();                     // the active list is read by every thread below
+        float g = 0.0f;
+        if (M == kDF) {
+            g = df_gamma(nact + S + 2);
+            // carry_t = e_j + g |z_j|_1 for the t-th active row j of layer l-1
+            for (int t = tid; t < nact; t += kT) {
+                const int r = rp + s.act[t];
+                const float l1 = fabsf(s.rhi[4 * r]) + fabsf(s.rhi[4 * r + 1]) + fabsf(s.rhi[4 * r + 2]) +
+                                 fabsf(s.rhi[4 * r + 3]);
+                s.carry[t] = __fmaf_ru(g, l1 * 1.001f, s.err[r]);
+            }
+        }
+        __syncthreads();
+        for (int item = tid; item < nl * S; item += kT) {
+            const int k = item % nl, sp = item / nl;
+            if (M == kFP64) {
+                const double *AT = net.AT[l];
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 4
+                for (int t = sp; t < nact; t += S) {
+                    const int j = s.act[t];
+                    const double w = __ldg(AT + (size_t)j * nl + k);
+                    const double *z = s.r64 + 4 * (rp + j);          // active: z = -row
+                    a0 -= w * z[0]; a1 -= w * z[1]; a2 -= w * z[2]; a3 -= w * z[3];
+                }
+                if (S == 1) {
+                    const double sg = bit_of(s.mask, rl + k) ? -1.0 : 1.0;
+                    const double *C = net.Cl[l] + 4 * k;
+                    double *r = s.r64 + 4 * (rl + k);
+                    r[0] = sg * (a0 + C[0]); r[1] = sg * (a1 + C[1]); r[2] = sg * (a2 + C[2]); r[3] = sg * (a3 + C[3]);
+                } else {
+                    double *p = s.partd + 4 * item;
+                    p[0] = a0; p[1] = a1; p[2] = a2; p[3] = a3;
+                }
+            } else {
+                const float *Ah = net.AThi[l], *Al = net.ATlo[l];
+                float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f, eb = 0.f;
+#pragma unroll 4
+                for (int t = sp; t < nact; t += S) {
+                    const int j = s.act[t];
+                    const float ah = __ldg(Ah + (size_t)j * nl + k), al = __ldg(Al + (size_t)j * nl + k);
+                    const float4 zh = *reinterpret_cast<const float4 *>(s.rhi + 4 * (rp + j));   // z = -row
+                    const float4 zl = *reinterpret_cast<const float4 *>(s.rlo + 4 * (rp + j));
+                    df_fma(h0, l0, ah, al, -zh.x, -zl.x);
+                    df_fma(h1, l1, ah, al, -zh.y, -zl.y);
+                    df_fma(h2, l2, ah, al, -zh.z, -zl.z);
+                    df_fma(h3, l3, ah, al, -zh.w, -zl.w);
+                    eb = __fmaf_ru(fabsf(ah), s.carry[t], eb);
+                }
+                if (S == 1) {
+                    const float *Ch = net.Clhi[l] + 4 * k, *Cc = net.Cllo[l] + 4 * k;
+                    df_add(h0, l0, Ch[0], Cc[0]); df_add(h1, l1, Ch[1], Cc[1]);
+                    df_add(h2, l2, Ch[2], Cc[2]); df_add(h3, l3, Ch[3], Cc[3]);
+                    df_norm(h0, l0); df_norm(h1, l1); df_norm(h2, l2); df_norm(h3, l3);
+                    const float sg = bit_of(s.mask, rl + k) ? -1.0f : 1.0f;
+                    *reinterpret_cast<float4 *>(s.rhi + 4 * (rl + k)) = make_float4(sg * h0, sg * h1, sg * h2, sg * h3);
+                    *reinterpret_cast<float4 *>(s.rlo + 4 * (rl + k)) = make_float4(sg * l0, sg * l1, sg * l2, sg * l3);
+                    const float cl1 = fabsf(Ch[0]) + fabsf(Ch[1]) + fabsf(Ch[2]) + fabsf(Ch[3]);
+                    s.err[rl + k] = __fmaf_ru(g, cl1, eb) * 1.01f;
+                } else {
+                    float *p = s.partf + 9 * item;
+                    p[0] = h0; p[1] = h1; p[2] = h2; p[3] = h3; p[4] = l0; p[5] = l1; p[6] = l2; p[7] = l3; p[8] = eb;
+                }
+            }
+        }
+        __syncthreads();
+        if (S > 1) {
+            for (int k = tid; k < nl; k += kT) {
+                if (M == kFP64) {
+                    const double *C = net.Cl[l] + 4 * k;
+                    double a0 = C[0], a1 = C[1], a2 = C[2], a3 = C[3];
+                    for (int sp = 0; sp < S; ++sp) {
+                        const double *p = s.partd + 4 * (sp * nl + k);
+                        a0 += p[0]; a1 += p[1]; a2 += p[2]; a3 += p[3];
+                    }
+                    const double sg = bit_of(s.mask, rl + k) ? -1.0 : 1.0;
+                    double *r = s.r64 + 4 * (rl + k);
+                    r[0] = sg * a0; r[1] = sg * a1; r[2] = sg * a2; r[3] = sg * a3;
+                } else {
+                    const float *Ch = net.Clhi[l] + 4 * k, *Cc = net.Cllo[l] + 4 * k;
+                    float h0 = Ch[0], h1 = Ch[1], h2 = Ch[2], h3 = Ch[3];
+                    float l0 = Cc[0], l1 = Cc[1], l2 = Cc[2], l3 = Cc[3];
+                    float eb = 0.0f;
+                    for (int sp = 0; sp < S; ++sp) {
+                        const float *p = s.partf + 9 * (sp * nl + k);
+                        df_add(h0, l0, p[0], p[4]); df_add(h1, l1, p[1], p[5]);
+                        df_add(h2, l2, p[2], p[6]); df_add(h3, l3, p[3], p[7]);
+                        eb = __fadd_ru(eb, p[8]);
+                    }
+                    df_norm(h0, l0); df_norm(h1, l1); df_norm(h2, l2); df_norm(h3, l3);
+                    const float sg = bit_of(s.mask, rl + k) ? -1.0f : 1.0f;
+                    *reinterpret_cast<float4 *>(s.rhi + 4 * (rl + k)) = make_float4(sg * h0, sg * h1, sg * h2, sg * h3);
+                    *reinterpret_cast<float4 *>(s.rlo + 4 * (rl + k)) = make_float4(sg * l0, sg * l1, sg * l2, sg * l3);
+                    const float cl1 = fabsf(Ch[0]) + fabsf(Ch[1]) + fabsf(Ch[2]) + fabsf(Ch[3]);
+                    s.err[rl + k] = __fmaf_ru(g, cl1, eb) * 1.01f;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // a_F = w_out^T diag(s_L) Z_L + [0 | b_out]  (Cor. 1, Eq. 8)
+    {
+        const int nL = net.width[net.L], rL = net.row0[net.L];
+        if (M == kFP64) {
+            double f[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = tid; k < nL; k += kT)
+                if (bit_of(s.mask, rL + k)) {
+                    const double w = net.w_out[k];
+                    for (int c = 0; c < 4; ++c) f[c] -= w * s.r64[4 * (rL + k) + c];
+                }
+            for (int c = 0; c < 4; ++c) f[c] = warp_sum(f[c]);
+            if ((tid & 31) == 0)
+                for (int c = 0; c < 4; ++c) s.partd[4 * (tid >> 5) + c] = f[c];
+            __syncthreads();
+            if (tid == 0) {
+                double F[4] = {0.0, 0.0, 0.0, net.b_out};
+                for (int w = 0; w < kNW; ++w)
+                    for (int c = 0; c < 4; ++c) F[c] += s.partd[4 * w + c];
+                for (int c = 0; c < 4; ++c) s.aF[c] = F[c];
+                s.eF[0] = 0.0f;
+            }
+        } else {
+            // one warp, lanes over the last layer, double-float with a bound
+            if (tid < 32) {
+                int cnt = 0;
+                for (int k = tid; k < nL; k += 32) cnt += bit_of(s.mask, rL + k);
+                for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                const float g = df_gamma(cnt + 40);
+                float h[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f}, eb = 0.0f;
+                for (int k = tid; k < nL; k += 32) {
+                    if (!bit_of(s.mask, rL + k)) continue;
+                    const float wh = net.w_out_hi[k], wl = net.w_out_lo[k];
+                    const float *zh = s.rhi + 4 * (rL + k), *zl = s.rlo + 4 * (rL + k);
+                    float l1 = 0.0f;
+                    for (int c = 0; c < 4; ++c) {
+                        df_fma(h[c], lo[c], wh, wl, -zh[c], -zl[c]);
+                        l1 += fabsf(zh[c]);
+                    }
+                    eb = __fmaf_ru(fabsf(wh), __fmaf_ru(g, l1 * 1.001f, s.err[rL + k]), eb);
+                }
+#pragma unroll 1
+                for (int o = 16; o > 0; o >>= 1) {
+                    for (int c = 0; c < 4; ++c) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, h[c], o);
+                        const float ol = __shfl_xor_sync(0xffffffffu, lo[c], o);
+                        df_add(h[c], lo[c], oh, ol);
+                    }
+                    eb = __fadd_ru(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+                }
+                if (tid == 0) {
+                    const float bh = (float)net.b_out, bl = (float)(net.b_out - (double)bh);
+                    df_add(h[3], lo[3], bh, bl);
+                    float l1 = fabsf(bh);
+                    for (int c = 0; c < 4; ++c) {
+                        df_norm(h[c], lo[c]);
+                        s.aFhi[c] = h[c];
+                        s.aFlo[c] = lo[c];
+                        s.aF[c] = (double)h[c] + (double)lo[c];
+                    }
+                    s.eF[0] = __fmaf_ru(g, l1, eb) * 1.01f;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// polygon helpers (warp 0)
+
+template <class R>
+__device__ __forceinline__ R pdist(const R *r, R ri, const R *v)
+{
+    return (r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3]) * ri;
+}
+
+// One cut of the polygon P[buf] (edge planes E[buf], m vertices) by row k, warp-parallel.  A
+// vertex is cut off when its distance from row k's plane exceeds tol.  The two new vertices are
+// re-solved from their planes and the face plane aF.  Returns the new vertex count (0 = empty,
+// -1 = inconsistent or overflow); *swapped tells whether the result went to buffer buf ^ 1.
+// row q in the vertex type R: FP64 rows (any mode) or the FP32 high parts (kDF heuristic pass)
+template <class R, int M>
+__device__ __forceinline__ void fetch_row(const Sh &s, int q, R *r)
+{
+    if constexpr (sizeof(R) == 8) {
+        row64<M>(s, q, (double *)r);
+    } else {
+        r[0] = s.rhi[4 * q]; r[1] = s.rhi[4 * q + 1]; r[2] = s.rhi[4 * q + 2]; r[3] = s.rhi[4 * q + 3];
+    }
+}
+
+template <class R, int M>
+__device__ __forceinline__ int warp_cut(const Sh &s, R (*P)[kMaxPoly][3], int m, int buf, int k, R tol, const R *aF,
+                                        bool *swapped)
+{
+    int (*E)[kMaxPoly] = s.pe;
+    const int lane = threadIdx.x & 31;
+    *swapped = false;
+    R rk[4];
+    fetch_row<R, M>(s, k, rk);
+    const R rn = sqrt(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
+    if (rn == R(0)) return m;
+    const R ri = R(1) / rn;
+    const bool o0 = lane < m && pdist(rk, ri, P[buf][lane]) > tol;
+    const bool o1 = lane + 32 < m && pdist(rk, ri, P[buf][lane + 32]) > tol;
+    const unsigned long long out = (unsigned long long)__ballot_sync(0xffffffffu, o0) |
+                                   ((unsigned long long)__ballot_sync(0xffffffffu, o1) << 32);
+    const int nout = __popcll(out);
+    if (nout == 0) return m;
+    if (nout == m) return 0;
+    int ia = -1, ib = -1;
+    for (int i = lane; i < m; i += 32) {
+        const bool oi = (out >> i) & 1ull;
+        if (oi && !((out >> ((i + m - 1) % m)) & 1ull)) ia = i;
+        if (oi && !((out >> ((i + 1) % m)) & 1ull)) ib = i;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ia = max(ia, __shfl_xor_sync(0xffffffffu, ia, o));
+        ib = max(ib, __shfl_xor_sync(0xffffffffu, ib, o));
+    }
+    if (ia < 0 || ib < 0 || ((ib - ia + m) % m) + 1 != nout) return -1;
+    const int nin = m - nout;
+    if (nin + 2 > kMaxPoly) return -1;
+    const int nb = buf ^ 1;
+    const int ea = E[buf][(ia + m - 1) % m], eb = E[buf][ib];
+    for (int i = lane; i < m; i += 32) {                 // the kept run b+1 .. a-1, in order
+        if ((out >> i) & 1ull) continue;
+        const int ni = (i - (ib + 1) + m) % m;
+        P[nb][ni][0] = P[buf][i][0]; P[nb][ni][1] = P[buf][i][1]; P[nb][ni][2] = P[buf][i][2];
+        E[nb][ni] = E[buf][i];
+    }
+    bool ok = true;
+    if (lane < 2) {
+        R pa[4], pb[4], v[3];
+        fetch_row<R, M>(s, lane == 0 ? ea : k, pa);
+        fetch_row<R, M>(s, lane == 0 ? k : eb, pb);
+        ok = solve3<R>(pa, pb, aF, v, nullptr);
+        P[nb][nin + lane][0] = v[0]; P[nb][nin + lane][1] = v[1]; P[nb][nin + lane][2] = v[2];
+        E[nb][nin + lane] = lane == 0 ? k : eb;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();
+    *swapped = true;
+    return ok ? nin + 2 : -1;
+}
+
+// kDF: the final vertices in FP64 from the double-float rows, with the bound dv on how far the
+// exact vertex (exact rows) can be, |v* - v|_inf <= |M^-1|_inf max(e_a, e_b, e_F) max(1,|v|) (1.1).
+__device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < m; i += 32) {
+        const int ea = s.pe[buf][(i + m - 1) % m], eb = s.pe[buf][i];
+        double ra[4], rb[4], v[3], inorm = 0.0;
+        row64<kDF>(s, ea, ra);
+        row64<kDF>(s, eb, rb);
+        const bool ok = solve3<double>(ra, rb, s.aF, v, &inorm);
+        const double X = fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2]))));
+        const double e = fmax((double)s.err[ea], fmax((double)s.err[eb], (double)s.eF[0]));
+        s.pv[buf][i][0] = v[0]; s.pv[buf][i][1] = v[1]; s.pv[buf][i][2] = v[2];
+        s.dvb[i] = ok ? (float)(inorm * e * X * 1.1 + 4e-16 * X) * 1.01f : 3.0e38f;
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------
+// one cell
+
+struct CellOut {
+    int emit;        // corners written (0 = empty)
+    int ambiguous;   // kDF: an undecidable sign test; nothing written
+};
+
+template <int M>
+__device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net, int64_t cell, const Sh &s)
+{
+    const Arena &ar = a.ar;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int N = net.N, NC = N + kBoxPlanes;          // checked rows: neurons + box
+    long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
+    AM_TICK(tp0);
+    compose<M>(net, s);
+    AM_TICK(tp1);
+
+    // box rows (exact), frame and the initial square (thread 0)
+    for (int i = tid; i < kBoxPlanes; i += kT) {
+        const double sgn = (i & 1) ? -1.0 : 1.0;
+        const double r[4] = {(i >> 1) == 0 ? sgn : 0.0, (i >> 1) == 1 ? sgn : 0.0, (i >> 1) == 2 ? sgn : 0.0, -a.box};
+        const int k = N + i;
+        if (M == kFP64) {
+            for (int c = 0; c < 4; ++c) s.r64[4 * k + c] = r[c];
+        } else {
+            for (int c = 0; c < 4; ++c) {
+                const float h = (float)r[c];
+                s.rhi[4 * k + c] = h;
+                s.rlo[4 * k + c] = (float)(r[c] - (double)h);
+            }
+            s.err[k] = 0.0f;
+        }
+    }
+    if (tid == 0) {
+        // an FP32 frame is enough: the square only has to contain the box section, and its
+        // planes never bound a face (the box planes always cut them away)
+        const float F[4] = {(float)s.aF[0], (float)s.aF[1], (float)s.aF[2], (float)s.aF[3]};
+        const float nn = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+        int m = 0;
+        if (nn > 0.0f && isfinite(nn)) {
+            const float inn = 1.0f / nn;
+            const float p0[3] = {-F[3] * F[0] * inn, -F[3] * F[1] * inn, -F[3] * F[2] * inn};
+            const float inv = rsqrtf(nn);
+            const float n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
+            const float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
+            const int ei = (ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2);
+            const float e0 = ei == 0 ? 1.0f : 0.0f, e1 = ei == 1 ? 1.0f : 0.0f, e2 = ei == 2 ? 1.0f : 0.0f;
+            float u[3] = {n[1] * e2 - n[2] * e1, n[2] * e0 - n[0] * e2, n[0] * e1 - n[1] * e0};
+            const float un = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            u[0] *= un; u[1] *= un; u[2] *= un;
+            const float w[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+            const float sz = 1.05f * 1.7320508f * (float)a.box;
+            // square edges -w, +u, +w, -u (ids N+6..N+9), counter-clockwise about n
+            const float d[4][3] = {{-w[0], -w[1], -w[2]}, {u[0], u[1], u[2]}, {w[0], w[1], w[2]}, {-u[0], -u[1], -u[2]}};
+            const float cu[4] = {-1.0f, 1.0f, 1.0f, -1.0f}, cw[4] = {-1.0f, -1.0f, 1.0f, 1.0f};
+            for (int i = 0; i < 4; ++i) {
+                const int k = N + kBoxPlanes + i;
+                const float r[4] = {d[i][0], d[i][1], d[i][2], -(d[i][0] * p0[0] + d[i][1] * p0[1] + d[i][2] * p0[2]) - sz};
+                for (int c = 0; c < 4; ++c) {
+                    if (M == kFP64) s.r64[4 * k + c] = (double)r[c];
+                    else { s.rhi[4 * k + c] = r[c]; s.rlo[4 * k + c] = 0.0f; }
+                }
+                if (M == kDF) s.err[k] = 0.0f;
+                for (int c = 0; c < 3; ++c) {
+                    const float x = p0[c] + sz * (cu[i] * u[c] + cw[i] * w[c]);
+                    s.pv[0][i][c] = (double)x;
+                    s.pf[0][i][c] = x;
+                }
+                s.pe[0][i] = k;
+            }
+            m = 4;
+        }
+        s.si[0] = m; s.si[1] = 0; s.si[2] = 0; s.si[3] = 0; s.si[4] = 0; s.si[5] = 0; s.si[9] = 0;
+    }
+    __syncthreads();
+    // inverse norms, FP32 (they only scale distances used for ordering and the FP64 tolerance
+    // test, never a sign)
+    for (int k = tid; k < NC + kSquarePlanes; k += kT) {
+        float n2;
+        if (M == kFP64) {
+            const double *r = s.r64 + 4 * k;
+            n2 = (float)(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+        } else {
+            const float *r = s.rhi + 4 * k;
+            n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        }
+        s.rinv[k] = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+    }
+    __syncthreads();
+
+    // ---- the rows nearest to the entry point: each thread keeps its best two, each warp
+    //      contributes its four nearest
+    {
+        const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
+                    pz = __ldcg(ar.entry_pt + cell * 3 + 2);
+        float b1 = 3.0e38f, b2 = 3.0e38f;
+        int k1 = -1, k2 = -1;
+        for (int k = tid; k < NC; k += kT) {
+            if (s.rinv[k] == 0.0f) continue;
+            float d;
+            if (M == kFP64) {
+                const double *r = s.r64 + 4 * k;
+                d = (float)fabs(r[0] * px + r[1] * py + r[2] * pz + r[3]) * s.rinv[k];
+            } else {
+                const float *r = s.rhi + 4 * k;
+                d = fabsf(r[0] * px + r[1] * py + r[2] * pz + r[3]) * s.rinv[k];
+            }
+            if (d < b1) { b2 = b1; k2 = k1; b1 = d; k1 = k; }
+            else if (d < b2) { b2 = d; k2 = k; }
+        }
+#pragma unroll 1
+        for (int pick = 0; pick < 4; ++pick) {
+            float bd = b1;
+            int bk = k1;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (ok >= 0 && (bk < 0 || od < bd || (od == bd && ok < bk))) { bd = od; bk = ok; }
+            }
+            if (lane == 0) { s.near_w[wid * 4 + pick] = bk; s.near_dw[wid * 4 + pick] = bd; }
+            if (bk >= 0 && bk == k1) { b1 = b2; k1 = k2; b2 = 3.0e38f; k2 = -1; }
+        }
+    }
+    __syncthreads();
+
+    AM_TICK(tp2);
+    // ---- a4: warp 0 sorts the near rows by distance and cuts the square with them
+    if (wid == 0) {
+        float d = s.near_dw[lane];
+        int k = s.near_w[lane];
+        if (k < 0) d = 3.0e38f;
+#pragma unroll 1
+        for (int size = 2; size <= 32; size <<= 1) {           // bitonic sort, ascending
+#pragma unroll 1
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, d, stride);
+                const int ok = __shfl_xor_sync(0xffffffffu, k, stride);
+                const bool up = (lane & size) == 0;
+                const bool lower = (lane & stride) == 0;
+                const bool mine_first = d < od || (d == od && k < ok);
+                if ((lower == up) != mine_first) { d = od; k = ok; }
+            }
+        }
+        const int nn = __popc(__ballot_sync(0xffffffffu, k >= 0 && d < 3.0e38f));
+        AM_TICK(tp2a);
+        int m = s.si[0], buf = 0, status = 0, done = 0;
+        const float aFf[4] = {s.aFhi[0], s.aFhi[1], s.aFhi[2], s.aFhi[3]};
+        while (m > 0 && done < nn) {
+            bool cut = false;
+            if (lane >= done && lane < nn) {
+                if (M == kFP64) {
+                    double r[4];
+                    fetch_row<double, M>(s, k, r);
+                    const double ri = (double)s.rinv[k];
+                    for (int i = 0; i < m && !cut; ++i) cut = pdist(r, ri, s.pv[buf][i]) > a.delta;
+                } else {
+                    float r[4];
+                    fetch_row<float, M>(s, k, r);
+                    const float ri = s.rinv[k];
+                    for (int i = 0; i < m && !cut; ++i) cut = pdist(r, ri, s.pf[buf][i]) > 1e-7f;
+                }
+            }
+            const unsigned cm = __ballot_sync(0xffffffffu, cut);
+            if (!cm) break;
+            const int first = __ffs(cm) - 1;
+            const int kc = __shfl_sync(0xffffffffu, k, first);
+            bool sw;
+            int nm;
+            if (M == kFP64) nm = warp_cut<double, M>(s, s.pv, m, buf, kc, a.delta, s.aF, &sw);
+            else nm = warp_cut<float, M>(s, s.pf, m, buf, kc, 1e-7f, aFf, &sw);
+            if (nm < 0) { status = 1; m = 0; break; }
+            if (sw) buf ^= 1;
+            m = nm;
+            done = first + 1;
+        }
+        AM_TICK(tp3a);
+        if (M == kDF && m > 0) df_final_vertices(s, m, buf);
+        if (lane == 0) { s.si[0] = m; s.si[1] = buf; s.si[2] = status; }
+    }
+    __syncthreads();
+
+    AM_TICK(tp3);
+    // ---- a5: every row at every vertex; violators are cut in by warp 0 and the check repeats
+    int rounds = 0;
+    for (;; ++rounds) {
+        const int m = s.si[0], buf = s.si[1];
+        if (m == 0 || s.si[2]) break;
+        for (int i = tid; i < m; i += kT) {
+            const double *v = s.pv[buf][i];
+            s.vf[i][0] = (float)v[0]; s.vf[i][1] = (float)v[1]; s.vf[i][2] = (float)v[2];
+            s.vf[i][3] = (float)fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])))) * 1.0001f;
+        }
+        if (tid == 0) { s.si[3] = 0; s.si[4] = 0; }
+        __syncthreads();
+        int ndeg = 0, close = 0;
+        for (int k = tid; k < NC; k += kT) {
+            if (s.rinv[k] == 0.0f) continue;        // zero normal: constant row, holds in its own cell
+            bool viol = false, amb = false;
+            if (M == kFP64) {
+                const double *r = s.r64 + 4 * k;
+                const double ri = (double)s.rinv[k];
+                for (int i = 0; i < m; ++i) {
+                    const int ea = s.pe[buf][(i + m - 1) % m], eb = s.pe[buf][i];
+                    if (k == ea || k == eb) continue;
+                    const double dd = pdist(r, ri, s.pv[buf][i]);
+                    if (dd > a.delta) viol = true;
+                    else if (dd >= -a.delta) ++ndeg;
+                }
+            } else {
+                const float *r = s.rhi + 4 * k;
+                const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
+                const float band = (float)a.delta / s.rinv[k] * 1.01f;   // delta |r|: the oracle's tolerance band
+                const float ek = s.err[k];
+                for (int i = 0; i < m; ++i) {
+                    const int ea = s.pe[buf][(i + m - 1) % m], eb = s.pe[buf][i];
+                    if (k == ea || k == eb) continue;
+                    const float *v = s.vf[i];
+                    const float sl = r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3];
+                    const float mag = fabsf(r[0] * v[0]) + fabsf(r[1] * v[1]) + fabsf(r[2] * v[2]) + fabsf(r[3]);
+                    // FP32 evaluation (4 terms) + dropping lo + rounding v to FP32: (4 + 4) u |r||v|
+                    const float B = __fmaf_ru(8.5f * kU, mag, __fmaf_ru(ek, v[3], __fmaf_ru(rl1, s.dvb[i], band)));
+                    if (sl > B) { viol = true; continue; }
+                    if (sl >= -B) {                    // close call: FP64 re-evaluation
+                        ++close;
+                        double r6[4];
+                        row64<kDF>(s, k, r6);
+                        const double *v6 = s.pv[buf][i];
+                        const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
+                        const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
+                        const double B6 = (double)ek * (double)v[3] + (double)rl1 * 1.0001 * (double)s.dvb[i] +
+                                          (double)band + 1e-15 * m6;
+                        if (s6 > B6) viol = true;
+                        else if (s6 >= -B6) amb = true;
+                    }
+                }
+            }
+            if (viol) {
+                const int p = atomicAdd(s.si + 3, 1);
+                s.viol[p] = k;
+            }
+            if (amb) s.si[4] = 1;
+        }
+        {
+            int tot;
+            block_scan_excl(ndeg, s.wsum, &tot);
+            ndeg = tot;
+            block_scan_excl(close, s.wsum, &tot);
+            if (tid == 0) s.blk[5] += (unsigned long long)tot;
+        }
+        if (tid == 0) s.si[5] = ndeg;
+        __syncthreads();
+        if (s.si[4]) return CellOut{0, 1};
+        const int nviol = s.si[3];
+        if (nviol == 0) break;
+        if (rounds + 1 >= kMaxFix) {
+            if (tid == 0) s.si[2] = 2;
+            __syncthreads();
+            break;
+        }
+        if (wid == 0) {
+            int mm = m, bb = buf, status = 0;
+            const double tol = M == kFP64 ? a.delta : 0.0;
+            for (int t = 0; t < nviol && mm > 0; ++t) {
+                bool sw;
+                const int nm = warp_cut<double, M>(s, s.pv, mm, bb, s.viol[t], tol, s.aF, &sw);
+                if (nm < 0) { status = 1; mm = 0; break; }
+                if (sw) bb ^= 1;
+                mm = nm;
+            }
+            if (M == kDF && mm > 0) df_final_vertices(s, mm, bb);
+            if (lane == 0) { s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; }
+        }
+        __syncthreads();
+    }
+
+    AM_TICK(tp4);
+    // ---- a6 emit, a7 march
+    const int m = s.si[0], buf = s.si[1];
+    int status = s.si[2];
+    for (int i = 0; i < m; ++i)
+        if (s.pe[buf][i] >= N + kBoxPlanes) status = 3;   // a square edge: the plane misses the box
+    int emit = (m >= 3 && status == 0) ? m : 0;
+    if (emit && tid == 0) {
+        double nx = 0.0, ny = 0.0, nz = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
+            nx += p[1] * q[2] - p[2] * q[1]; ny += p[2] * q[0] - p[0] * q[2]; nz += p[0] * q[1] - p[1] * q[0];
+        }
+        s.si[6] = 0.5 * sqrt(nx * nx + ny * ny + nz * nz) > 1e-24 * a.box * a.box;
+    }
+    __syncthreads();
+    if (emit && !s.si[6]) emit = 0;
+    if (emit > ar.maxv) {
+        if (tid == 0) atomicOr(ar.counters + kStatus, kStFaceVerts);
+        emit = 0;
+    }
+    if (tid == 0) {
+        ar.nverts[cell] = emit;
+        s.blk[0] += 1;
+        if (!emit) s.blk[1] += 1;
+        if (emit) s.blk[2] += (unsigned long long)s.si[5];
+        if (rounds) s.blk[3] += 1;
+        if (status == 1 || status == 2) atomicOr(ar.counters + kStatus, kStClip);
+    }
+    AM_TICK(tp4a);
+    if (emit) {
+        for (int i = tid; i < m; i += kT) {
+            ar.edges[cell * ar.maxv + i] = s.pe[buf][i];
+            double *v = ar.verts + (cell * ar.maxv + i) * 3;
+            v[0] = s.pv[buf][i][0]; v[1] = s.pv[buf][i][1]; v[2] = s.pv[buf][i][2];
+        }
+        const unsigned long long h = __ldcg(ar.hash + cell);
+        const int nid = __ldcg(ar.net + cell);
+        for (int i = tid; i < m; i += kT) {
+            const int e = s.pe[buf][i];
+            if (e >= N) continue;
+            const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
+            insert_neighbor(ar, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+                            (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+        }
+    }
+    if (emit && tid < m) __threadfence();     // the face and the pushes of this thread
+    __syncthreads();
+    AM_TICK(tp5);
+    AM_PHASE(a, 0, tp0, tp1);
+    AM_PHASE(a, 1, tp1, tp2);
+    AM_PHASE(a, 2, tp2, tp2a);
+    AM_PHASE(a, 3, tp2a, tp3a);
+    AM_PHASE(a, 4, tp3a, tp3);
+    AM_PHASE(a, 5, tp3, tp4);
+    AM_PHASE(a, 6, tp4, tp4a);
+    AM_PHASE(a, 7, tp4a, tp5);
+    return CellOut{emit, 0};
+}
+
+template <int MODE>
+__device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
+{
+    const Arena &ar = a.ar;
+    // the cell's record was written by another block of this launch: read it through L2
+    if (__ldcg(ar.nverts + cell) == -2) return;          // a duplicate seed id: never solved
+    const NetDev &net = a.nets[__ldcg(ar.net + cell)];
+    const unsigned long long *key = ar.keys + cell * ar.kw;
+    for (int w = threadIdx.x; w < (net.N + 31) / 32; w += kT)
+        s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
+    __syncthreads();
+    if (MODE == kDF) {
+        const CellOut o = solve_cell<kDF>(a, net, cell, s);
+        if (o.ambiguous) {
+            if (threadIdx.x == 0) s.blk[4] += 1;
+            solve_cell<kFP64>(a, net, cell, s);
+        }
+    } else {
+        solve_cell<kFP64>(a, net, cell, s);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// schedules
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Ticket of the next cell to solve, or -1 when the march is over (every handed-out cell is
+// finished), the ticket is beyond the limit, or a wait ran out of time (status flag set).
+// Waiting polls with plain acquire loads and an exponential back-off, so that idle blocks do
+// not flood the counters' cache lines with atomics.
+__device__ long long next_ticket(const MarchArgs &a)
+{
+    unsigned long long *C = a.ar.counters;
+    const long long t = (long long)atomicAdd(C + kHead, 1ull);
+    if (t >= a.limit) return -1;
+    const long long t0 = global_ns();
+    unsigned ns = 32;
+    for (;;) {
+        const unsigned long long n = ld_acquire(C + kNCells);
+        if ((unsigned long long)t < n) {
+            unsigned ns2 = 16;
+            while (ld_acquire(a.ar.ready + t) == 0u) {
+                if (global_ns() - t0 > kWaitNs) { atomicOr(C + kStatus, kStTimeout); return -1; }
+                __nanosleep(ns2);
+                ns2 = min(2 * ns2, 256u);
+            }
+            return t;
+        }
+        // every handed-out cell finished (done read before the count: no cell can still push)
+        const unsigned long long done = ld_acquire(C + kDone);
+        const unsigned long long n2 = ld_acquire(C + kNCells);
+        if (done >= n2 && (unsigned long long)t >= n2) return -1;
+        if (global_ns() - t0 > kWaitNs) { atomicOr(C + kStatus, kStTimeout); return -1; }
+        __nanosleep(ns);
+        ns = min(2 * ns, 256u);
+    }
+}
+
+// per-block statistics: zero at entry, one atomic flush at exit
+__device__ __forceinline__ void blk_init(const Sh &s)
+{
+    if (threadIdx.x < 8) s.blk[threadIdx.x] = 0ull;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void blk_flush(const MarchArgs &a, const Sh &s)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long *C = a.ar.counters;
+        if (s.blk[0]) atomicAdd(C + kSolved, s.blk[0]);
+        if (s.blk[1]) atomicAdd(C + kEmpty, s.blk[1]);
+        if (s.blk[2]) atomicAdd(C + kDegenerate, s.blk[2]);
+        if (s.blk[3]) atomicAdd(C + kFixups, s.blk[3]);
+        if (s.blk[4]) atomicAdd(C + kRefined, s.blk[4]);
+        if (s.blk[5]) atomicAdd(C + kCloseCalls, s.blk[5]);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kT, 2) march_persistent_kernel(MarchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Sh s = make_sh(smem, a.max_n, a.max_w);
+    __shared__ long long ticket;
+    blk_init(s);
+    for (;;) {
+        long long tw0 = 0, tw1 = 0;
+        AM_TICK(tw0);
+        if (threadIdx.x == 0) ticket = next_ticket(a);
+        __syncthreads();
+        AM_TICK(tw1);
+        AM_PHASE(a, 8, tw0, tw1);
+        const long long t = ticket;
+        if (t < 0) break;
+        process_cell<MODE>(a, t, s);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ar.counters + kDone, 1ull);
+        }
+    }
+    blk_flush(a, s);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kT, 2) march_range_kernel(MarchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Sh s = make_sh(smem, a.max_n, a.max_w);
+    blk_init(s);
+    for (int64_t cell = a.begin + blockIdx.x; cell < a.end; cell += gridDim.x) {
+        process_cell<MODE>(a, cell, s);
+        __syncthreads();
+    }
+    blk_flush(a, s);
+}
+
+cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm)
+{
+    const int smem = march_smem_bytes(max_n, max_w);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(march_persistent_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(march_persistent_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(march_range_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(march_range_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    // shared memory for two resident blocks, the rest of the unified L1 for the weights and
+    // the stack (the driver rounds the carveout to a supported split)
+    const int carve = std::min(100, (int)((2.0 * (smem + 1024) * 100.0) / (228.0 * 1024.0)) + 3);
+    const void *ks[4] = {(const void *)march_persistent_kernel<kFP64>, (const void *)march_persistent_kernel<kDF>,
+                         (const void *)march_range_kernel<kFP64>, (const void *)march_range_kernel<kDF>};
+    for (const void *k : ks)
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    int b0 = 0, b1 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, march_persistent_kernel<kFP64>, kT, smem))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, march_persistent_kernel<kDF>, kT, smem))) return e;
+    *blocks_per_sm = b0 < b1 ? b0 : b1;
+    return cudaSuccess;
+}
+
+void launch_march(const MarchArgs &a, int mode, bool persistent, int grid, cudaStream_t st)
+{
+    const int smem = march_smem_bytes(a.max_n, a.max_w);
+    if (persistent) {
+        if (mode == kDF) march_persistent_kernel<kDF><<<grid, kT, smem, st>>>(a);
+        else march_persistent_kernel<kFP64><<<grid, kT, smem, st>>>(a);
+    } else {
+        if (mode == kDF) march_range_kernel<kDF><<<grid, kT, smem, st>>>(a);
+        else march_range_kernel<kFP64><<<grid, kT, smem, st>>>(a);
+    }
+}
+
+}  // namespace am

@@ -130,20 +130,28 @@ __global__ void seed_insert_kernel(SeedArgs a)
     ar.net[id] = a.net;
     ar.hash[id] = h;
     ar.nverts[id] = -1;
+    ar.entry_plane[id] = -1;
+    for (int c = 0; c < 3; ++c) ar.entry_pt[id * 3 + c] = (float)a.seed_x[ray * 3 + c];
     __threadfence();
     const unsigned long long mine = slot_make(h, (unsigned long long)id, kNoFlip);
     unsigned long long pos = h & ar.slot_mask;
     for (int probe = 0; probe < kMaxProbe; ++probe) {
         unsigned long long cur = atomicCAS(ar.slots + pos, 0ull, mine);
-        if (cur == 0ull) { atomicAdd(a.n_new, 1ull); return; }
-        if (slot_tag(cur) == hash_tag(h) && ar.net[slot_parent(cur)] == a.net &&
+        if (cur == 0ull) {
+            atomicAdd(a.n_new, 1ull);
+            atomicExch(ar.ready + id, 1u);
+            return;
+        }
+        if (slot_tag(cur) == hash_tag(h) && __ldcg(ar.net + slot_parent(cur)) == a.net &&
             ref_keys_equal(ar, id, kNoFlip, slot_parent(cur), slot_flip(cur))) {
             ar.nverts[id] = -2;
+            atomicExch(ar.ready + id, 1u);
             return;
         }
         pos = (pos + 1) & ar.slot_mask;
     }
     ar.nverts[id] = -2;
+    atomicExch(ar.ready + id, 1u);
     atomicOr(ar.counters + kStatus, kStHashFull);
 }
 

@@ -119,15 +119,22 @@ class Mesher:
 
     # ---- am_march
     def march(self, box: float = 1.5, delta: float = 1e-10, precision: int = nt.AM_PREC_FP64,
-              max_cells: int = 0, use_proposal: bool = False) -> int:
+              max_cells: int = 0, use_proposal: bool = False, schedule: int = nt.AM_SCHED_PERSISTENT,
+              grid_blocks: int = 0) -> int:
+        if isinstance(precision, str):
+            precision = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED}[precision]
+        if isinstance(schedule, str):
+            schedule = {"persistent": nt.AM_SCHED_PERSISTENT, "levels": nt.AM_SCHED_LEVELS}[schedule]
         op = nt.am_march_opts(box=box, delta=delta, precision=precision, max_cells=max_cells,
-                              use_proposal=int(use_proposal))
+                              use_proposal=int(use_proposal), schedule=schedule, grid_blocks=grid_blocks)
         return self._check(self.lib.am_march(self.ctx, C.byref(op)), ok=(nt.AM_OK, nt.AM_INCOMPLETE))
 
     def stats(self) -> dict:
         s = nt.am_stats_t()
         self._check(self.lib.am_get_stats(self.ctx, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
+        out = {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
+        out["phase_cycles"] = list(out["phase_cycles"])
+        return out
 
     # ---- am_get_mesh
     def get_mesh(self, net_id: int) -> Mesh:

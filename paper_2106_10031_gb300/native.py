@@ -28,6 +28,8 @@ STATUS_NAMES = {0: "AM_OK", 1: "AM_ERR_INVALID_ARG", 2: "AM_ERR_CUDA", 3: "AM_ER
 
 AM_PREC_FP64 = 0
 AM_PREC_MIXED = 1
+AM_SCHED_PERSISTENT = 0
+AM_SCHED_LEVELS = 1
 
 
 class am_ctx_opts(C.Structure):
@@ -45,7 +47,8 @@ class am_mlp_desc(C.Structure):
 
 class am_march_opts(C.Structure):
     _fields_ = [("box", C.c_double), ("delta", C.c_double), ("precision", C.c_int),
-                ("max_cells", C.c_int64), ("use_proposal", C.c_int)]
+                ("max_cells", C.c_int64), ("use_proposal", C.c_int), ("schedule", C.c_int),
+                ("grid_blocks", C.c_int)]
 
 
 class am_stats_t(C.Structure):
@@ -53,7 +56,8 @@ class am_stats_t(C.Structure):
                 ("vertices", C.c_int64), ("corners", C.c_int64), ("degenerate", C.c_int64),
                 ("open_faces", C.c_int64), ("refined_cells", C.c_int64), ("levels", C.c_int64),
                 ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
-                ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64), ("close_calls", C.c_int64),
+                ("fixups", C.c_int64), ("phase_cycles", C.c_int64 * 10)]
 
 
 class am_mesh(C.Structure):

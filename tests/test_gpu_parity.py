@@ -17,6 +17,10 @@ def am():
     return am_mod
 
 
+MODES = [("fp64", "persistent", 1e-9), ("mixed", "persistent", 1e-5), ("fp64", "levels", 1e-9),
+         ("mixed", "levels", 1e-5)]
+
+
 def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
     net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((len(dirs), 3)), dirs, R)
     with am.Mesher(max_cells=kw.pop("max_cells", 1 << 18), max_neurons=max(64, mlp.N),
@@ -29,6 +33,7 @@ def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
     return net, ref, mesh, st
 
 
+@pytest.mark.parametrize("precision,schedule,rtol", MODES)
 @pytest.mark.parametrize("make,dirs", [
     (octahedron, RAY),
     (polytope_max_of_planes, X_RAY),
@@ -36,32 +41,36 @@ def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
     (lambda: tiny_net((6, 5, 4), 12), RAY),
     (lambda: decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05), X_RAY),
 ])
-def test_parity_small(oracle_mod, am, make, dirs):
+def test_parity_small(oracle_mod, am, make, dirs, precision, schedule, rtol):
     mlp = make()
-    net, ref, mesh, st = _both(oracle_mod, am, mlp, dirs)
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, dirs, precision=precision, schedule=schedule)
     assert not ref.failed
-    r = parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    r = parity.compare(ref, mesh, mlp.N, rtol=rtol)
     assert st["degenerate"] == 0 == ref.degenerate
     assert st["faces"] == r["faces"]
     assert mesh.n_open_faces == ref.open_faces()
 
 
-def test_parity_sphere_net_full(oracle_mod, am):
+@pytest.mark.parametrize("precision,schedule,rtol", MODES)
+def test_parity_sphere_net_full(oracle_mod, am, precision, schedule, rtol):
     # the 3-[64]x4-1 workload at full size, every face compared
     mlp = sphere_net()
-    net, ref, mesh, st = _both(oracle_mod, am, mlp, X_RAY)
-    r = parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, X_RAY, precision=precision, schedule=schedule)
+    r = parity.compare(ref, mesh, mlp.N, rtol=rtol)
     assert r["faces"] > 40000 and st["degenerate"] == 0 and mesh.n_open_faces == 0
+    print(f"{precision}/{schedule}: max rel vertex err {r['max_rel_vertex_err']:.2e}, refined {st['refined_cells']}, "
+          f"close calls {st['close_calls']}, fixups {st['fixups']}")
 
 
-def test_parity_multi_seed_multi_component(oracle_mod, am):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parity_multi_seed_multi_component(oracle_mod, am, precision):
     # many rays, some landing in the same cell, on a net with several surface components
     mlp = tiny_net((6, 5, 4), 12)
     rng = np.random.default_rng(5)
     d = rng.normal(size=(64, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
-    net, ref, mesh, st = _both(oracle_mod, am, mlp, d)
-    parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, d, precision=precision)
+    parity.compare(ref, mesh, mlp.N, rtol=1e-5)
 
 
 def test_parity_two_nets_one_march(oracle_mod, am):
@@ -76,17 +85,25 @@ def test_parity_two_nets_one_march(oracle_mod, am):
             parity.compare(r, m.get_mesh(i), n.N, rtol=1e-9)
 
 
-def test_resume_after_max_cells(oracle_mod, am):
+@pytest.mark.parametrize("schedule", ["persistent", "levels"])
+def test_resume_after_max_cells(oracle_mod, am, schedule):
     mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
     net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), RAY)
     with am.Mesher(max_cells=1 << 17, max_neurons=128, max_width=32) as m:
         nid = m.load_mlp(mlp)
         m.seed(nid, np.zeros((1, 3)), RAY)
-        st = m.march(max_cells=500)
+        st = m.march(max_cells=500, schedule=schedule)
         assert st == 7                      # AM_INCOMPLETE
-        while m.march(max_cells=500) == 7:
+        while m.march(max_cells=500, schedule=schedule) == 7:
             pass
         parity.compare(ref, m.get_mesh(nid), mlp.N, rtol=1e-9)
+
+
+def test_persistent_with_few_blocks(oracle_mod, am):
+    # a grid smaller than the machine: blocks wait for work published by other blocks
+    mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, RAY, grid_blocks=3, precision="mixed")
+    parity.compare(ref, mesh, mlp.N, rtol=1e-5)
 
 
 def test_capacity_error_is_reported(am):
