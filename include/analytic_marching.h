@@ -121,7 +121,9 @@ typedef struct {
     int64_t corners;          /* face corners (sum of face sizes) */
     int64_t degenerate;       /* planes within delta of an accepted vertex */
     int64_t open_faces;       /* faces with an edge on the box */
-    int64_t refined_cells;    /* mixed precision: cells recomputed in FP64 */
+    int64_t refined_cells;    /* mixed precision: cells solved in FP64, because a sign test could not
+                                 be certified or because the net is too deep and wide for the
+                                 double-float bound (decided per net at load time) */
     int64_t levels;           /* breadth-first levels marched */
     double ms_march;          /* device time of the march (CUDA events) */
     double ms_assemble;       /* device time of the mesh assembly */

@@ -334,6 +334,29 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     nd.b_out = dsc->b_out;
     const int id = (int)ctx->nets.size();
     nd.salt = splitmix64(0xA11CE5EEDull + (unsigned long long)id * 0x9E3779B97F4A7C15ull);
+    {
+        // The mixed path's rigorous row-error bound grows layer by layer by at most the largest
+        // row sum of |W_l| (hidden part); its per-product coefficient is 2 (n + 4)^2 u^2 with
+        // u = 2^-24.  When the predicted relative bound at the last layer exceeds 1e-7, the
+        // sign tests of this net cannot be certified in double-float and its cells go to FP64.
+        double growth = 1.0, rel = 0.0;
+        const double u = 5.9604644775390625e-8;
+        for (int l = 1; l <= L; ++l) {
+            const int n = dsc->width[l - 1], np = l > 1 ? dsc->width[l - 2] : 0;
+            const int fan = l == 1 ? in_dim : np + (l == dsc->skip_layer ? in_dim : 0);
+            if (l > 1) {
+                double mx = 0.0;
+                for (int k = 0; k < n; ++k) {
+                    double rs = 0.0;
+                    for (int j = 0; j < np; ++j) rs += fabs(dsc->W[l - 1][(size_t)k * fan + j]);
+                    mx = std::max(mx, rs);
+                }
+                growth *= std::max(mx, 1.0);
+            }
+            rel += 2.0 * (np + 8.0) * (np + 8.0) * u * u * growth;
+        }
+        nd.df_ok = rel < 1e-7 ? 1 : 0;
+    }
     nh.N = N;
     nh.max_w = mw;
     CU(cudaMemcpyAsync(ctx->d_nets + id, &nd, sizeof(NetDev), cudaMemcpyHostToDevice, ctx->stream));

@@ -67,6 +67,7 @@ struct NetDev {
     const float *w_out_hi, *w_out_lo;
     double b_out;
     unsigned long long salt;     // per-net hash salt
+    int df_ok;                   // 1: the double-float bound stays useful through this net's depth
 };
 
 // Device arenas (all sized at context creation).

@@ -40,6 +40,7 @@ constexpr int kMaxPoly = 64;      // polygon vertices in flight
 constexpr int kNear = 32;         // rows clipped by warp 0 before the full check
 constexpr int kMaxFix = 8;        // check / fix-up rounds
 constexpr float kU = 5.9604645e-8f;            // 2^-24
+constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
 constexpr long long kWaitNs = 4000000000ll;    // 4 s limit on any wait for work
 
 enum { kFP64 = 0, kDF = 1 };
@@ -625,7 +626,18 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         }
         s.rinv[k] = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
     }
-    __syncthreads();
+    if (M == kDF) {
+        // When a row's certified error, as a distance, exceeds kDfLoose the sign tests of this
+        // cell cannot be certified in any useful number: the rigorous bound grows by the row
+        // sums of |W_l| per layer (deep, wide nets).  Go to FP64 at once instead of clipping
+        // twice.
+        int loose = 0;
+        for (int k = tid; k < N; k += kT) loose |= s.err[k] * s.rinv[k] > kDfLoose;
+        if (tid == 0) loose |= s.eF[0] * rsqrtf((float)(s.aF[0] * s.aF[0] + s.aF[1] * s.aF[1] + s.aF[2] * s.aF[2])) > kDfLoose;
+        if (__syncthreads_or(loose)) return CellOut{0, 1};
+    } else {
+        __syncthreads();
+    }
 
     // ---- the rows nearest to the entry point: each thread keeps its best two, each warp
     //      contributes its four nearest
@@ -883,7 +895,10 @@ __device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
     for (int w = threadIdx.x; w < (net.N + 31) / 32; w += kT)
         s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
     __syncthreads();
-    if (MODE == kDF) {
+    if (MODE == kDF && !net.df_ok) {
+        if (threadIdx.x == 0) s.blk[4] += 1;             // solved in FP64 (the net's bound is too loose)
+        solve_cell<kFP64>(a, net, cell, s);
+    } else if (MODE == kDF) {
         const CellOut o = solve_cell<kDF>(a, net, cell, s);
         if (o.ambiguous) {
             if (threadIdx.x == 0) s.blk[4] += 1;

@@ -138,9 +138,19 @@ def polytope_max_of_planes(seed: int = 1, offset: float = 0.5, C: float = 10.0) 
 # geometric-init networks
 
 
+def _value_at_origin(m: MLP) -> float:
+    """F(0) of the network (plain numpy evaluation of Eq. 1)."""
+    u0 = np.zeros(3) if m.latent is None else np.concatenate([np.zeros(3), m.latent])
+    h = None
+    for l, (W, b) in enumerate(zip(m.weights, m.biases), start=1):
+        inp = u0 if l == 1 else (np.concatenate([h, u0]) if l == m.skip_layer else h)
+        h = np.maximum(W @ inp + b, 0.0)
+    return float(m.w_out @ h + m.b_out)
+
+
 def geometric_init(widths, seed: int, sigma: float, radius: float = 0.6,
                    latent_dim: int = 0, latent_std: float = 0.0, skip_layer: int = 0,
-                   name: str = "") -> MLP:
+                   name: str = "", recenter: bool = False) -> MLP:
     """Geometric sphere initialisation, then every parameter perturbed by N(0, sigma^2).
 
     Hidden W ~ N(0, 2 / n_out), b = 0; output w ~ N(sqrt(pi)/sqrt(n_L), 1e-6^2),
@@ -148,6 +158,11 @@ def geometric_init(widths, seed: int, sigma: float, radius: float = 0.6,
     (geometric initialisation of Atzmon & Lipman, SAL, 2020).  The skip layer's
     weights are scaled by 1/sqrt(2) so that the concatenated input keeps the
     norm of a plain layer's input.
+
+    recenter: shift b_out after the perturbation so that F(0) = -radius again.  In deep,
+    wide nets the rectified bias perturbations add up to a positive offset (F ~ 3 over the
+    whole box for 3-[256]x8-1 at sigma = 0.05) that leaves no zero level set; the shift
+    restores the surface around the origin.
     """
     rng = np.random.default_rng(seed)
     widths = [int(w) for w in widths]
@@ -170,7 +185,9 @@ def geometric_init(widths, seed: int, sigma: float, radius: float = 0.6,
         w_out = w_out + rng.normal(0.0, sigma, w_out.shape)
         b_out = b_out + float(rng.normal(0.0, sigma))
     m = MLP(Ws, bs, w_out, float(b_out), latent=latent, skip_layer=skip_layer, name=name,
-            meta={"seed": seed, "sigma": sigma, "radius": radius})
+            meta={"seed": seed, "sigma": sigma, "radius": radius, "recentered": recenter})
+    if recenter:
+        m.b_out = float(m.b_out - (_value_at_origin(m) + radius))
     m.validate()
     return m
 
@@ -184,7 +201,7 @@ def decoder_net(seed: int = 3, width: int = 512, depth: int = 8, latent_dim: int
                 skip_layer: int = 4, sigma: float = 0.02) -> MLP:
     """(3 + latent) -> [width] x depth -> 1 with skip-concat of [x; z] at hidden layer 4."""
     return geometric_init([width] * depth, seed, sigma, latent_dim=latent_dim, latent_std=0.01,
-                          skip_layer=skip_layer, name=f"decoder_w{width}_d{depth}_s{seed}")
+                          skip_layer=skip_layer, name=f"decoder_w{width}_d{depth}_s{seed}", recenter=True)
 
 
 def batch_nets(master_seed: int = 4, count: int = 64) -> list:
@@ -196,12 +213,12 @@ def batch_nets(master_seed: int = 4, count: int = 64) -> list:
         d = int(rng.choice([4, 6, 8]))
         s = float(rng.uniform(0.02, 0.1))
         sub = int(rng.integers(0, 2 ** 31 - 1))
-        out.append(geometric_init([w] * d, sub, s, name=f"batch{i}_w{w}_d{d}"))
+        out.append(geometric_init([w] * d, sub, s, name=f"batch{i}_w{w}_d{d}", recenter=True))
     return out
 
 
 def proposal_target_net(seed: int = 5, width: int = 256, depth: int = 8, sigma: float = 0.05) -> MLP:
-    return geometric_init([width] * depth, seed, sigma, name=f"proposal_w{width}_d{depth}_s{seed}")
+    return geometric_init([width] * depth, seed, sigma, name=f"proposal_w{width}_d{depth}_s{seed}", recenter=True)
 
 
 def tiny_net(widths, seed: int, sigma: float = 0.1, radius: float = 0.6) -> MLP:

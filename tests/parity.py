@@ -76,3 +76,45 @@ def compare(oracle_mesh, gpu_mesh, N, rtol=1e-9, sample=None):
             assert idx_of.setdefault(vk, i) == i, "one vertex key mapped to two vertex indices"
     assert len(set(idx_of.values())) == len(idx_of) == len(gpu_mesh.xyz), "vertex indices are not one per key"
     return {"faces": len(ref), "vertices": len(idx_of), "max_rel_vertex_err": max_rel}
+
+
+def closure(gpu_mesh, N):
+    """Completeness without the oracle: every edge on a neuron plane has its reciprocal
+    face (cell ^ e_k, same plane) in the set (Thm. 1 / Alg. 1 steps 10-11), and every
+    vertex is shared by at least 3 corners unless it lies on the box."""
+    got = gpu_faces(gpu_mesh)
+    for k, (e, _, _) in got.items():
+        for p in e:
+            if p < N:
+                g = got.get(k ^ (1 << p))
+                assert g is not None and p in g[0], f"edge {p} of face {k:#x} has no reciprocal"
+    uses = np.bincount(gpu_mesh.face_vertices, minlength=len(gpu_mesh.xyz))
+    on_box = np.zeros(len(gpu_mesh.xyz), dtype=bool)
+    o = gpu_mesh.face_offsets
+    for i in range(gpu_mesh.n_faces):
+        e = gpu_mesh.edge_planes[o[i]:o[i + 1]]
+        idx = gpu_mesh.face_vertices[o[i]:o[i + 1]]
+        for j in range(len(e)):
+            if e[j - 1] >= N or e[j] >= N:
+                on_box[idx[j]] = True
+    assert np.all(uses[~on_box] >= 3)
+    return len(got)
+
+
+def compare_sampled(oracle_mod, net, gpu_mesh, N, sample, rtol, box, seed=0):
+    """Each sampled GPU face is re-solved by the oracle (Alg. 2 from the nearest line to the
+    GPU face's centroid) and must match exactly (edges) and within rtol (vertices)."""
+    got = gpu_faces(gpu_mesh)
+    keys = sorted(got)
+    rng = np.random.default_rng(seed)
+    pick = [keys[i] for i in rng.choice(len(keys), min(sample, len(keys)), replace=False)]
+    worst = 0.0
+    for k in pick:
+        e_g, v_g, _ = got[k]
+        f, rc = oracle_mod.solve_cell(net, k, None, v_g.mean(0), box)
+        assert rc == 0 and f is not None, f"oracle could not clip face {k:#x}"
+        assert f.edges == e_g, f"edge cycle differs for face {k:#x}: {f.edges} vs {e_g}"
+        err = np.linalg.norm(f.verts - v_g, axis=1) / np.maximum(1.0, np.linalg.norm(f.verts, axis=1))
+        worst = max(worst, float(err.max()))
+    assert worst <= rtol, worst
+    return worst
