@@ -255,7 +255,7 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
     opts = nt.am_ctx_opts(device=device, stream=stream_ptr, max_cells=1 << 17, hash_slots=0, max_face_verts=32,
                           max_neurons=256, max_width=64)
     assert lib.am_create(C.byref(ctx), C.byref(opts)) == 0, lib.am_last_error(ctx)
-    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, use_proposal=0)
+    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=nt.AM_CAND_NEAREST)
     bufs = None
     h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + 48
     d2h = 0

@@ -71,6 +71,16 @@ typedef enum {
     AM_SCHED_LEVELS = 1       /* one launch per breadth-first level, synchronised by the host */
 } am_schedule;
 
+/* Rows a cell's face is clipped with before the all-row check (which keeps the result exact
+ * whatever the candidates are: any violated row is cut in and the check repeated). */
+typedef enum {
+    AM_CAND_NEAREST = 0,      /* the 32 rows nearest to the point the cell was entered through */
+    AM_CAND_LEARNED = 1,      /* the 32 rows the learned proposal scores highest (am_proposal_*);
+                                 nets whose N or depth do not match the proposal fall back to
+                                 AM_CAND_NEAREST */
+    AM_CAND_NONE = 2          /* no candidates: the all-row check clips alone (the plain clip) */
+} am_candidates;
+
 /* Context creation options.  Zero-initialised fields take the documented defaults. */
 typedef struct {
     int device;               /* CUDA device ordinal (default 0) */
@@ -107,7 +117,7 @@ typedef struct {
                                  delta of a vertex counts as satisfied and as a degenerate event */
     am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
     int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
-    int use_proposal;         /* reserved for the learned constraint proposal (0) */
+    am_candidates candidates; /* AM_CAND_NEAREST (default), AM_CAND_LEARNED or AM_CAND_NONE */
     am_schedule schedule;     /* AM_SCHED_PERSISTENT (default) or AM_SCHED_LEVELS */
     int grid_blocks;          /* persistent schedule: blocks to launch (0 = all resident) */
 } am_march_opts;
@@ -132,6 +142,7 @@ typedef struct {
     int64_t kernel_launches;  /* all kernel launches of the library since the last am_reset */
     int64_t close_calls;      /* mixed precision: sign tests re-evaluated in FP64 */
     int64_t fixups;           /* faces whose candidate polygon the all-row check corrected */
+    int64_t cuts;             /* half-plane cuts applied to face polygons (candidates + corrections) */
     int64_t phase_cycles[10]; /* SM cycles summed over cells per phase (compose, set-up, candidate
                                  sort, candidate clip, FP64 vertices, check, emit, march, waiting
                                  for work, spare); only filled by a build with -DAM_PHASE_TIMERS,
@@ -195,6 +206,46 @@ am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
 
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
+
+/* ---- learned constraint proposal --------------------------------------------------------
+ * No counterpart in the paper.  A small MLP, x (7 + L) -> H -> H -> n_out, ReLU hidden layers,
+ * sigmoid scores, that predicts which of the n_out = N neurons of a net carry the edges of a
+ * cell's face.  Features of a cell: the point it was entered through (3), the unit normal of its
+ * face plane a_F[0:3] / |a_F[0:3]| (3), the plane offset a_F[3] / |a_F[0:3]| (1), and the active
+ * fraction of each hidden layer (L).  Parameters are one flat FP32 array, in this order:
+ * W1 (H x n_in), b1 (H), W2 (H x H), b2 (H), W3 (n_out x H), b3 (n_out), matrices row-major.
+ * Training uses BF16 operands with FP32 accumulation and Adam on FP32 master weights. */
+
+/* Training samples from the mesh of net_id assembled by the last am_march (labels are what the
+ * march found, so they are exact whatever candidates it used): one sample per corner of every
+ * face, in the assembled face order; the entry point of a sample is the midpoint of the edge that
+ * leaves its corner, the plane is the face's (Newell normal of its vertices).  Writes
+ * n = min(corners, max_samples) rows of d_X (n x (7 + L) FP32, device) and d_Y (n x N FP32 0/1,
+ * device) and returns n in *n_samples; with d_X or d_Y NULL only *n_samples is set. */
+am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, int64_t max_samples,
+                              int64_t *n_samples);
+
+/* Create (or replace) the context's proposal with Kaiming-normal weights drawn from seed.
+ * max_batch bounds the samples of one forward / gradient call.  hidden <= 1024. */
+am_status am_proposal_init(am_ctx *ctx, int n_in, int hidden, int n_out, int max_batch, uint64_t seed);
+
+/* Copy the flat FP32 parameters out of / into the context (host arrays of n_params values). */
+am_status am_proposal_get_params(am_ctx *ctx, float *h_params, int64_t n_params);
+am_status am_proposal_set_params(am_ctx *ctx, const float *h_params, int64_t n_params);
+
+/* Logits of n samples: d_X (n x n_in FP32, device) -> d_Z (n x n_out FP32, device). */
+am_status am_proposal_forward(am_ctx *ctx, const float *d_X, int n, float *d_Z);
+
+/* Mean binary cross-entropy of n <= max_batch samples (labels d_Y, n x n_out, 0/1 FP32,
+ * device) and its gradient w.r.t. every parameter (host array of n_params values). */
+am_status am_proposal_grad(am_ctx *ctx, const float *d_X, const float *d_Y, int n, float *h_grads,
+                           int64_t n_params, float *h_loss);
+
+/* steps Adam steps (learning rate lr) on minibatches of `batch` consecutive samples, cycling
+ * through the n samples of d_X / d_Y (device).  h_losses (host, may be NULL) receives the loss
+ * of each step. */
+am_status am_proposal_train(am_ctx *ctx, const float *d_X, const float *d_Y, int64_t n, int batch, int steps,
+                            float lr, float *h_losses);
 
 /* ---- allocation-free vertex assignment ---------------------------------------------------
  * The paper has no counterpart to this call; it serves callers that cannot allocate device

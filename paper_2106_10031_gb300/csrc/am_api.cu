@@ -73,6 +73,7 @@ struct am_ctx {
     int64_t vslots_n = 0;
     std::vector<MeshInfo> mesh;
     bool mesh_valid = false;
+    ProposalDev prop;
 };
 
 namespace {
@@ -245,6 +246,7 @@ void am_destroy(am_ctx *ctx)
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
     if (ctx->evk0) cudaEventDestroy(ctx->evk0);
     if (ctx->evk1) cudaEventDestroy(ctx->evk1);
+    proposal_free(ctx->prop);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -572,6 +574,23 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ma.delta = op.delta;
     ma.max_n = ctx->opts.max_neurons;
     ma.max_w = ctx->opts.max_width;
+    if (op.candidates != AM_CAND_NEAREST && op.candidates != AM_CAND_LEARNED && op.candidates != AM_CAND_NONE)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unknown candidates mode %d", (int)op.candidates);
+    if (op.candidates == AM_CAND_LEARNED && !ctx->prop.w)
+        return fail(ctx, AM_ERR_STATE, "AM_CAND_LEARNED needs a proposal (am_proposal_init / am_proposal_train)");
+    ma.candidates = (int)op.candidates;
+    if (ctx->prop.w) {
+        ProposalDev &p = ctx->prop;
+        ma.prop.w1 = p.wb + p.off[0];
+        ma.prop.b1 = p.w + p.off[1];
+        ma.prop.w2t = p.w2t;
+        ma.prop.b2 = p.w + p.off[3];
+        ma.prop.w3t = p.w3t;
+        ma.prop.b3 = p.w + p.off[5];
+        ma.prop.n_in = p.n_in;
+        ma.prop.hidden = p.hidden;
+        ma.prop.n_out = p.n_out;
+    }
     const int64_t start = ctx->solved_upto;
     const int64_t limit = op.max_cells > 0 ? std::min<int64_t>(start + op.max_cells, ctx->ar.cap) : ctx->ar.cap;
     bool incomplete = false;
@@ -644,11 +663,131 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ctx->stats.refined_cells = (int64_t)hc[kRefined];
     ctx->stats.close_calls = (int64_t)hc[kCloseCalls];
     ctx->stats.fixups = (int64_t)hc[kFixups];
+    ctx->stats.cuts = (int64_t)hc[kCuts];
     for (int i = 0; i < 10; ++i) ctx->stats.phase_cycles[i] = (int64_t)hc[kPhase0 + i * kCtrStride];
     s = status_error(ctx, hc[kStatus]);
     if (s != AM_OK) return s;
     if (hc[kStatus] & kStClip) ctx->err = "a clip step met an inconsistent polygon (reported as an empty face)";
     return incomplete ? AM_INCOMPLETE : AM_OK;
+}
+
+am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, int64_t max_samples,
+                              int64_t *n_samples)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (!ctx->mesh_valid || net_id < 0 || net_id >= (int)ctx->mesh.size())
+        return fail(ctx, AM_ERR_STATE, "no mesh for net %d: call am_march", net_id);
+    if (!n_samples || max_samples < 0) return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    const MeshInfo &mi = ctx->mesh[net_id];
+    const int64_t n = std::min(mi.corners, max_samples);
+    *n_samples = n;
+    if (!d_X || !d_Y || n == 0) return AM_OK;
+    const NetHost &nh = ctx->nets[net_id];
+    SampleArgs a{};
+    a.ar = ctx->ar;
+    a.perm = ctx->d_perm;
+    a.coff = ctx->d_coff;
+    a.f0 = mi.face_base;
+    a.nf = mi.faces;
+    a.c0 = mi.corner_base;
+    a.max_samples = n;
+    a.N = nh.dev.N;
+    a.L = nh.dev.L;
+    a.n_in = 7 + nh.dev.L;
+    for (int l = 0; l <= nh.dev.L; ++l) { a.row0[l] = nh.dev.row0[l]; a.width[l] = nh.dev.width[l]; }
+    a.X = d_X;
+    a.Y = d_Y;
+    launch_proposal_samples(a, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    return AM_OK;
+}
+
+am_status am_proposal_init(am_ctx *ctx, int n_in, int hidden, int n_out, int max_batch, uint64_t seed)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (n_in < 1 || n_in > 64 || hidden < 1 || hidden > 1024 || n_out < 1 || n_out > kMaxNeurons || max_batch < 1)
+        return fail(ctx, AM_ERR_INVALID_ARG, "proposal shape out of range");
+    proposal_free(ctx->prop);
+    CU(proposal_alloc(ctx->prop, n_in, hidden, n_out, max_batch));
+    ProposalDev &p = ctx->prop;
+    // Kaiming-normal weights (Box-Muller on splitmix64 draws), zero biases, output bias logit(1/32)
+    std::vector<float> w((size_t)p.n_params, 0.0f);
+    unsigned long long st = seed * 0x9E3779B97F4A7C15ull + 0x5EEDull;
+    auto normal = [&]() {
+        const double u1 = ((splitmix64(st++) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((splitmix64(st++) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    };
+    const int fans[3] = {n_in, hidden, hidden};
+    const double gains[3] = {2.0, 2.0, 1.0};
+    for (int l = 0; l < 3; ++l) {
+        const double sd = sqrt(gains[l] / fans[l]);
+        for (int64_t i = p.off[2 * l]; i < p.off[2 * l + 1]; ++i) w[i] = (float)(sd * normal());
+    }
+    for (int64_t i = p.off[5]; i < p.off[6]; ++i) w[i] = (float)log(1.0 / 31.0);
+    CU(cudaMemcpyAsync(p.w, w.data(), sizeof(float) * p.n_params, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(p.m, 0, sizeof(float) * p.n_params, ctx->stream));
+    CU(cudaMemsetAsync(p.v, 0, sizeof(float) * p.n_params, ctx->stream));
+    proposal_sync_copies(p, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status am_proposal_get_params(am_ctx *ctx, float *h, int64_t n)
+{
+    if (!ctx || !ctx->prop.w) return fail(ctx, AM_ERR_STATE, "no proposal");
+    if (!h || n != ctx->prop.n_params) return fail(ctx, AM_ERR_INVALID_ARG, "expected %lld parameters",
+                                                   (long long)ctx->prop.n_params);
+    CU(cudaMemcpyAsync(h, ctx->prop.w, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status am_proposal_set_params(am_ctx *ctx, const float *h, int64_t n)
+{
+    if (!ctx || !ctx->prop.w) return fail(ctx, AM_ERR_STATE, "no proposal");
+    if (!h || n != ctx->prop.n_params) return fail(ctx, AM_ERR_INVALID_ARG, "expected %lld parameters",
+                                                   (long long)ctx->prop.n_params);
+    CU(cudaMemcpyAsync(ctx->prop.w, h, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+    proposal_sync_copies(ctx->prop, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status am_proposal_forward(am_ctx *ctx, const float *d_X, int n, float *d_Z)
+{
+    if (!ctx || !ctx->prop.w) return fail(ctx, AM_ERR_STATE, "no proposal");
+    if (!d_X || !d_Z || n < 1) return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    CU(proposal_forward(ctx->prop, d_X, n, d_Z, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status am_proposal_grad(am_ctx *ctx, const float *d_X, const float *d_Y, int n, float *h_grads, int64_t n_params,
+                           float *h_loss)
+{
+    if (!ctx || !ctx->prop.w) return fail(ctx, AM_ERR_STATE, "no proposal");
+    if (!d_X || !d_Y || !h_grads || !h_loss || n < 1 || n > ctx->prop.max_batch || n_params != ctx->prop.n_params)
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    CU(proposal_grad(ctx->prop, d_X, d_Y, n, h_loss, ctx->stream));
+    CU(cudaMemcpyAsync(h_grads, ctx->prop.g, sizeof(float) * n_params, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
+}
+
+am_status am_proposal_train(am_ctx *ctx, const float *d_X, const float *d_Y, int64_t n, int batch, int steps,
+                            float lr, float *h_losses)
+{
+    if (!ctx || !ctx->prop.w) return fail(ctx, AM_ERR_STATE, "no proposal");
+    if (!d_X || !d_Y || batch < 1 || batch > ctx->prop.max_batch || n < batch || steps < 0 || !(lr > 0.0f))
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad training arguments");
+    CU(proposal_train(ctx->prop, d_X, d_Y, n, batch, steps, lr, h_losses, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return AM_OK;
 }
 
 am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *m)

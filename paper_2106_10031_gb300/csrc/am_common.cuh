@@ -46,7 +46,8 @@ enum {
     kCloseCalls = 8 * kCtrStride,   // mixed precision: sign tests re-evaluated in FP64
     kFixups = 9 * kCtrStride,       // faces whose candidate polygon the full check corrected
     kPhase0 = 10 * kCtrStride,      // 10 per-phase cycle counters (timing builds only)
-    kNumCounters = 20 * kCtrStride
+    kCuts = 20 * kCtrStride,        // half-plane cuts applied to candidate polygons (clip work)
+    kNumCounters = 21 * kCtrStride
 };
 
 // One loaded network, folded for the device (row-major):

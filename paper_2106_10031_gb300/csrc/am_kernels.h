@@ -2,11 +2,26 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "am_common.cuh"
 
 namespace am {
+
+// candidate rows clipped before the all-row check
+enum { kCandNearest = 0, kCandLearned = 1, kCandNone = 2 };
+
+// the learned proposal as the march reads it (BF16 weights, W2 and W3 transposed)
+struct ProposalView {
+    const __nv_bfloat16 *w1;      // hidden x n_in
+    const float *b1;              // hidden
+    const __nv_bfloat16 *w2t;     // hidden x hidden, [in][out]
+    const float *b2;
+    const __nv_bfloat16 *w3t;     // hidden x n_out, [in][out]
+    const float *b3;
+    int n_in, hidden, n_out;
+};
 
 struct MarchArgs {
     const NetDev *nets;
@@ -15,6 +30,8 @@ struct MarchArgs {
     int max_n, max_w;        // shared-memory sizing (largest loadable net)
     long long limit;         // persistent schedule: tickets >= limit are not solved
     int64_t begin, end;      // level schedule: cell ids solved by this launch
+    int candidates;          // kCandNearest / kCandLearned / kCandNone
+    ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
 };
 int march_smem_bytes(int max_n, int max_w);
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
@@ -38,6 +55,26 @@ struct SeedArgs {
 cudaError_t prepare_seed_kernels(int max_n, int max_w);
 void launch_seed(const SeedArgs &a, cudaStream_t st);
 
+// ---- learned proposal (training and batch inference)
+struct ProposalDev {
+    int n_in = 0, hidden = 0, n_out = 0, max_batch = 0;
+    int64_t off[7] = {};
+    int64_t n_params = 0;
+    int64_t step = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master weights, grads, Adam state
+    __nv_bfloat16 *wb = nullptr, *w2t = nullptr, *w3t = nullptr;     // BF16 copies
+    float *buf[8] = {};
+    __nv_bfloat16 *bbuf[4] = {};
+    float *loss_parts = nullptr;
+};
+cudaError_t proposal_alloc(ProposalDev &p, int n_in, int hidden, int n_out, int max_batch);
+void proposal_free(ProposalDev &p);
+void proposal_sync_copies(ProposalDev &p, cudaStream_t st);
+cudaError_t proposal_forward(ProposalDev &p, const float *X, int n, float *Z, cudaStream_t st);
+cudaError_t proposal_grad(ProposalDev &p, const float *X, const float *Y, int n, float *loss, cudaStream_t st);
+cudaError_t proposal_train(ProposalDev &p, const float *X, const float *Y, int64_t n, int batch, int steps, float lr,
+                           float *losses, cudaStream_t st);
+
 // ---- mesh assembly
 struct AsmArgs {
     Arena ar;
@@ -60,6 +97,21 @@ struct AsmArgs {
     unsigned long long *out_keys;     // faces x kw
     int64_t n_faces;
 };
+// Training samples of the learned proposal from an assembled mesh: one per corner of every face
+// of one net (faces f0 .. f0 + nf - 1 of the assembled order, corners from c0), truncated at
+// max_samples.  X: samples x n_in FP32, Y: samples x N FP32 (0/1 edge-neuron labels).
+struct SampleArgs {
+    Arena ar;
+    const int32_t *perm;
+    const int64_t *coff;
+    int64_t f0, nf, c0, max_samples;
+    int N, L, n_in;
+    int row0[kMaxLayers + 2];
+    int width[kMaxLayers + 1];
+    float *X, *Y;
+};
+void launch_proposal_samples(const SampleArgs &a, cudaStream_t st);
+
 void launch_asm_count(const AsmArgs &a, cudaStream_t st);
 void launch_asm_scatter(const AsmArgs &a, cudaStream_t st);
 cudaError_t launch_asm_offsets(const AsmArgs &a, int64_t *scan_tmp, int64_t scan_tmp_len, cudaStream_t st);

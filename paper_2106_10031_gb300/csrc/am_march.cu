@@ -28,6 +28,7 @@
 // from a counter and waits, with a time limit, for the ticket's cell to be published; it stops
 // when every handed-out cell is finished.  Levels: one launch per breadth-first level.
 #include <algorithm>
+#include <cuda_bf16.h>
 
 #include "am_block.cuh"
 #include "am_kernels.h"
@@ -115,7 +116,8 @@ struct Sh {
                             //          8 near count, 9 fix rounds
     int *wsum;              // 32 ints
     unsigned long long *blk;   // per-block statistics, flushed once when the block exits:
-                               // 0 solved, 1 empty, 2 degenerate, 3 fixups, 4 refined, 5 close calls
+                               // 0 solved, 1 empty, 2 degenerate, 3 fixups, 4 refined, 5 close calls,
+                               // 6 cuts
 };
 
 __device__ inline Sh make_sh(unsigned char *base, int max_n, int max_w)
@@ -537,6 +539,74 @@ __device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf)
 }
 
 // ------------------------------------------------------------------------------------------
+// learned proposal: scores of every neuron row for this cell (block-wide forward pass)
+
+// Features: entry point (3), unit face-plane normal (3), plane offset (1), active fraction of
+// each hidden layer (L).  Scores go to z[0..N) (logits; larger = more likely an edge plane).
+__device__ void proposal_scores(const MarchArgs &a, const NetDev &net, int64_t cell, const Sh &s, float *z)
+{
+    const ProposalView &P = a.prop;
+    const int tid = threadIdx.x, H = P.hidden, O = P.n_out, I = P.n_in;
+    float *x = s.partf;            // the compose partial sums are free here
+    float *h1 = x + 64, *h2 = h1 + H;
+    if (tid == 0) {
+        x[0] = __ldcg(a.ar.entry_pt + cell * 3);
+        x[1] = __ldcg(a.ar.entry_pt + cell * 3 + 1);
+        x[2] = __ldcg(a.ar.entry_pt + cell * 3 + 2);
+        const double *F = s.aF;
+        const double inv = 1.0 / sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+        x[3] = (float)(F[0] * inv); x[4] = (float)(F[1] * inv); x[5] = (float)(F[2] * inv); x[6] = (float)(F[3] * inv);
+        for (int l = 1; l <= net.L; ++l) {
+            const int r0 = net.row0[l], n = net.width[l];
+            int cnt = 0;
+            for (int w = r0 >> 5; w <= (r0 + n - 1) >> 5; ++w) {
+                unsigned bits = s.mask[w];
+                const int lo = max(r0 - 32 * w, 0), hi = min(r0 + n - 32 * w, 32);
+                bits &= (hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                cnt += __popc(bits);
+            }
+            x[6 + l] = (float)cnt / (float)n;
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < H; t += kT) {
+        float acc = P.b1[t];
+        for (int i = 0; i < I; ++i) acc = fmaf(__bfloat162float(P.w1[(size_t)t * I + i]), x[i], acc);
+        h1[t] = fmaxf(acc, 0.0f);
+    }
+    __syncthreads();
+    for (int t = tid; t < H; t += kT) {
+        float acc = P.b2[t];
+        for (int j = 0; j < H; ++j) acc = fmaf(__bfloat162float(P.w2t[(size_t)j * H + t]), h1[j], acc);
+        h2[t] = fmaxf(acc, 0.0f);
+    }
+    __syncthreads();
+    for (int base = 0; base < O; base += 8 * kT) {
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int o = base + tid + i * kT;
+            acc[i] = o < O ? P.b3[o] : 0.0f;
+        }
+        for (int j = 0; j < H; ++j) {
+            const float hj = h2[j];
+            const __nv_bfloat16 *wr = P.w3t + (size_t)j * O;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int o = base + tid + i * kT;
+                if (o < O) acc[i] = fmaf(__bfloat162float(wr[o]), hj, acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int o = base + tid + i * kT;
+            if (o < O) z[o] = acc[i];
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
 // one cell
 
 struct CellOut {
@@ -639,17 +709,25 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         __syncthreads();
     }
 
-    // ---- the rows nearest to the entry point: each thread keeps its best two, each warp
-    //      contributes its four nearest
+    // ---- candidate rows, each thread keeps its best two, each warp contributes its four best:
+    //      the rows nearest to the entry point, or the rows the learned proposal scores highest
+    //      (the entry plane first), or none at all (the all-row check then clips alone)
+    const bool learned = a.candidates == kCandLearned && a.prop.n_out == N && a.prop.n_in == 7 + net.L;
+    float *score = (float *)s.viol;
+    if (learned) proposal_scores(a, net, cell, s, score);
     {
         const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
                     pz = __ldcg(ar.entry_pt + cell * 3 + 2);
+        const int entry = __ldcg(ar.entry_plane + cell);
         float b1 = 3.0e38f, b2 = 3.0e38f;
         int k1 = -1, k2 = -1;
-        for (int k = tid; k < NC; k += kT) {
+        for (int k = (a.candidates == kCandNone ? NC : tid); k < NC; k += kT) {
             if (s.rinv[k] == 0.0f) continue;
             float d;
-            if (M == kFP64) {
+            if (learned) {
+                if (k >= N) continue;
+                d = k == entry ? -3.0e37f : -score[k];
+            } else if (M == kFP64) {
                 const double *r = s.r64 + 4 * k;
                 d = (float)fabs(r[0] * px + r[1] * py + r[2] * pz + r[3]) * s.rinv[k];
             } else {
@@ -694,7 +772,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         }
         const int nn = __popc(__ballot_sync(0xffffffffu, k >= 0 && d < 3.0e38f));
         AM_TICK(tp2a);
-        int m = s.si[0], buf = 0, status = 0, done = 0;
+        int m = s.si[0], buf = 0, status = 0, done = 0, ncut = 0;
         const float aFf[4] = {s.aFhi[0], s.aFhi[1], s.aFhi[2], s.aFhi[3]};
         while (m > 0 && done < nn) {
             bool cut = false;
@@ -723,10 +801,11 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             if (sw) buf ^= 1;
             m = nm;
             done = first + 1;
+            ++ncut;
         }
         AM_TICK(tp3a);
         if (M == kDF && m > 0) df_final_vertices(s, m, buf);
-        if (lane == 0) { s.si[0] = m; s.si[1] = buf; s.si[2] = status; }
+        if (lane == 0) { s.si[0] = m; s.si[1] = buf; s.si[2] = status; s.blk[6] += (unsigned long long)ncut; }
     }
     __syncthreads();
 
@@ -809,9 +888,9 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             break;
         }
         if (wid == 0) {
-            int mm = m, bb = buf, status = 0;
+            int mm = m, bb = buf, status = 0, t = 0;
             const double tol = M == kFP64 ? a.delta : 0.0;
-            for (int t = 0; t < nviol && mm > 0; ++t) {
+            for (; t < nviol && mm > 0; ++t) {
                 bool sw;
                 const int nm = warp_cut<double, M>(s, s.pv, mm, bb, s.viol[t], tol, s.aF, &sw);
                 if (nm < 0) { status = 1; mm = 0; break; }
@@ -819,7 +898,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                 mm = nm;
             }
             if (M == kDF && mm > 0) df_final_vertices(s, mm, bb);
-            if (lane == 0) { s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; }
+            if (lane == 0) { s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; s.blk[6] += (unsigned long long)t; }
         }
         __syncthreads();
     }
@@ -983,6 +1062,7 @@ __device__ __forceinline__ void blk_flush(const MarchArgs &a, const Sh &s)
         if (s.blk[3]) atomicAdd(C + kFixups, s.blk[3]);
         if (s.blk[4]) atomicAdd(C + kRefined, s.blk[4]);
         if (s.blk[5]) atomicAdd(C + kCloseCalls, s.blk[5]);
+        if (s.blk[6]) atomicAdd(C + kCuts, s.blk[6]);
     }
 }
 

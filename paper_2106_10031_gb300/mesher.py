@@ -60,6 +60,7 @@ class Mesher:
             self.lib.am_destroy(self.ctx)
             self.ctx = None
             raise AMError(st, msg)
+        self.device = device
         self.nets = []
 
     def close(self):
@@ -119,14 +120,17 @@ class Mesher:
 
     # ---- am_march
     def march(self, box: float = 1.5, delta: float = 1e-10, precision: int = nt.AM_PREC_FP64,
-              max_cells: int = 0, use_proposal: bool = False, schedule: int = nt.AM_SCHED_PERSISTENT,
+              max_cells: int = 0, candidates: int = nt.AM_CAND_NEAREST, schedule: int = nt.AM_SCHED_PERSISTENT,
               grid_blocks: int = 0) -> int:
         if isinstance(precision, str):
             precision = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED}[precision]
         if isinstance(schedule, str):
             schedule = {"persistent": nt.AM_SCHED_PERSISTENT, "levels": nt.AM_SCHED_LEVELS}[schedule]
+        if isinstance(candidates, str):
+            candidates = {"nearest": nt.AM_CAND_NEAREST, "learned": nt.AM_CAND_LEARNED,
+                          "none": nt.AM_CAND_NONE}[candidates]
         op = nt.am_march_opts(box=box, delta=delta, precision=precision, max_cells=max_cells,
-                              use_proposal=int(use_proposal), schedule=schedule, grid_blocks=grid_blocks)
+                              candidates=candidates, schedule=schedule, grid_blocks=grid_blocks)
         return self._check(self.lib.am_march(self.ctx, C.byref(op)), ok=(nt.AM_OK, nt.AM_INCOMPLETE))
 
     def stats(self) -> dict:
@@ -135,6 +139,60 @@ class Mesher:
         out = {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
         out["phase_cycles"] = list(out["phase_cycles"])
         return out
+
+    # ---- learned proposal (device arrays are torch CUDA tensors)
+    def proposal_init(self, n_in: int, hidden: int, n_out: int, max_batch: int = 4096, seed: int = 0):
+        self._check(self.lib.am_proposal_init(self.ctx, n_in, hidden, n_out, max_batch, seed))
+        self.prop_shape = (n_in, hidden, n_out)
+
+    def proposal_samples(self, net_id: int = 0, max_samples: int = 1 << 40):
+        """(X, Y) training samples (torch CUDA tensors) from the last march's mesh of net_id."""
+        import torch
+        n = C.c_int64()
+        self._check(self.lib.am_proposal_samples(self.ctx, net_id, None, None, max_samples, C.byref(n)))
+        L, N = self.nets[net_id].L, self.nets[net_id].N
+        dev = torch.device("cuda", self.device)
+        X = torch.empty((max(n.value, 1), 7 + L), dtype=torch.float32, device=dev)
+        Y = torch.empty((max(n.value, 1), N), dtype=torch.float32, device=dev)
+        self._check(self.lib.am_proposal_samples(self.ctx, net_id, C.c_void_p(X.data_ptr()),
+                                                 C.c_void_p(Y.data_ptr()), max_samples, C.byref(n)))
+        return X[:n.value], Y[:n.value]
+
+    def proposal_n_params(self) -> int:
+        I, H, O = self.prop_shape
+        return H * I + H + H * H + H + O * H + O
+
+    def proposal_params(self) -> np.ndarray:
+        n = self.proposal_n_params()
+        p = np.zeros(n, dtype=np.float32)
+        self._check(self.lib.am_proposal_get_params(self.ctx, p.ctypes.data_as(C.c_void_p), n))
+        return p
+
+    def proposal_set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.am_proposal_set_params(self.ctx, p.ctypes.data_as(C.c_void_p), len(p)))
+
+    def proposal_forward(self, X):
+        import torch
+        Z = torch.empty((X.shape[0], self.prop_shape[2]), dtype=torch.float32, device=X.device)
+        self._check(self.lib.am_proposal_forward(self.ctx, C.c_void_p(X.data_ptr()), X.shape[0],
+                                                 C.c_void_p(Z.data_ptr())))
+        return Z
+
+    def proposal_grad(self, X, Y):
+        n = self.proposal_n_params()
+        g = np.zeros(n, dtype=np.float32)
+        loss = C.c_float()
+        self._check(self.lib.am_proposal_grad(self.ctx, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+                                              X.shape[0], g.ctypes.data_as(C.c_void_p), n, C.byref(loss)))
+        return float(loss.value), g
+
+    def proposal_train(self, X, Y, batch: int, steps: int, lr: float) -> np.ndarray:
+        losses = np.zeros(steps, dtype=np.float32)
+        self._check(self.lib.am_proposal_train(self.ctx, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
+                                               X.shape[0], batch, steps, float(lr),
+                                               losses.ctypes.data_as(C.c_void_p)))
+        return losses
 
     # ---- am_get_mesh
     def get_mesh(self, net_id: int) -> Mesh:

@@ -30,6 +30,9 @@ AM_PREC_FP64 = 0
 AM_PREC_MIXED = 1
 AM_SCHED_PERSISTENT = 0
 AM_SCHED_LEVELS = 1
+AM_CAND_NEAREST = 0
+AM_CAND_LEARNED = 1
+AM_CAND_NONE = 2
 
 
 class am_ctx_opts(C.Structure):
@@ -47,7 +50,7 @@ class am_mlp_desc(C.Structure):
 
 class am_march_opts(C.Structure):
     _fields_ = [("box", C.c_double), ("delta", C.c_double), ("precision", C.c_int),
-                ("max_cells", C.c_int64), ("use_proposal", C.c_int), ("schedule", C.c_int),
+                ("max_cells", C.c_int64), ("candidates", C.c_int), ("schedule", C.c_int),
                 ("grid_blocks", C.c_int)]
 
 
@@ -57,7 +60,7 @@ class am_stats_t(C.Structure):
                 ("open_faces", C.c_int64), ("refined_cells", C.c_int64), ("levels", C.c_int64),
                 ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
                 ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64), ("close_calls", C.c_int64),
-                ("fixups", C.c_int64), ("phase_cycles", C.c_int64 * 10)]
+                ("fixups", C.c_int64), ("cuts", C.c_int64), ("phase_cycles", C.c_int64 * 10)]
 
 
 class am_mesh(C.Structure):
@@ -81,6 +84,15 @@ ENTRY_POINTS = [
     ("am_march", C.c_int, [C.c_void_p, C.POINTER(am_march_opts)]),
     ("am_get_mesh", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_get_stats", C.c_int, [C.c_void_p, C.POINTER(am_stats_t)]),
+    ("am_proposal_samples", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("am_proposal_init", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
+    ("am_proposal_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    ("am_proposal_set_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    ("am_proposal_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    ("am_proposal_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int64,
+                                   C.c_void_p]),
+    ("am_proposal_train", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_float,
+                                    C.c_void_p]),
     ("am_assign_vertices_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                              C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]

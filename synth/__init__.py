@@ -10,6 +10,7 @@ from .nets import (  # noqa: F401
     polytope_max_of_planes,
     fibonacci_normals,
     geometric_init,
+    sibling,
     sphere_net,
     decoder_net,
     batch_nets,

@@ -221,6 +221,18 @@ def proposal_target_net(seed: int = 5, width: int = 256, depth: int = 8, sigma: 
     return geometric_init([width] * depth, seed, sigma, name=f"proposal_w{width}_d{depth}_s{seed}", recenter=True)
 
 
+def sibling(mlp: MLP, seed: int, sigma: float = 0.005) -> MLP:
+    """The same network with every hidden weight and bias moved by N(0, sigma^2): a nearby
+    checkpoint of it (the training nets of the learned proposal)."""
+    rng = np.random.default_rng(seed)
+    m = MLP([w + rng.normal(0.0, sigma, w.shape) for w in mlp.weights],
+            [b + rng.normal(0.0, sigma, b.shape) for b in mlp.biases],
+            mlp.w_out.copy(), float(mlp.b_out), None if mlp.latent is None else mlp.latent.copy(),
+            mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta))
+    m.validate()
+    return m
+
+
 def tiny_net(widths, seed: int, sigma: float = 0.1, radius: float = 0.6) -> MLP:
     """Small geometric-init nets (<= 16 ReLUs) for exhaustive enumeration."""
     return geometric_init(list(widths), seed, sigma, radius=radius,

@@ -1,0 +1,218 @@
+"""The learned constraint proposal on the GPU (through the C ABI): forward and gradients against
+the FP64 oracle, training samples against the oracle's, and a march with learned candidates that
+must give the oracle's mesh while clipping far less than the plain full clip.  Needs a GPU."""
+import numpy as np
+import pytest
+
+from oracle import proposal as P
+from synth import sibling, sphere_net, tiny_net
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+RAY = np.array([[1.0, 0.37, 0.21]]) / np.linalg.norm([1.0, 0.37, 0.21])
+X_RAY = np.array([[1.0, 0.0, 0.0]])
+
+
+@pytest.fixture(scope="module")
+def am():
+    import paper_2106_10031_gb300 as am_mod
+    return am_mod
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def unflatten(p, I, H, O):
+    p = np.asarray(p, dtype=np.float64)
+    shapes = [("W1", (H, I)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (O, H)), ("b3", (O,))]
+    out, o = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp))
+        out[name] = p[o:o + n].reshape(shp)
+        o += n
+    assert o == len(p)
+    return out
+
+
+def bf16(torch, x):
+    return torch.as_tensor(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _rand_xy(B, I, O, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(B, I)).astype(np.float32)
+    Y = (rng.uniform(size=(B, O)) < 0.1).astype(np.float32)
+    return X, Y
+
+
+# I, H, O span several 64-wide tiles with ragged tails
+SHAPES = [(11, 64, 40), (12, 200, 300), (9, 256, 256)]
+
+
+@pytest.mark.parametrize("I,H,O", SHAPES)
+def test_forward_matches_oracle(am, torch, I, H, O):
+    X, _ = _rand_xy(333, I, O, 1)
+    with am.Mesher(max_cells=1024, max_neurons=64, max_width=32) as m:
+        m.proposal_init(I, H, O, max_batch=128, seed=3)     # 333 samples: three batches
+        prm = unflatten(m.proposal_params(), I, H, O)
+        Z = m.proposal_forward(torch.as_tensor(X, device="cuda")).cpu().numpy().astype(np.float64)
+    z_ref, _ = P.forward(prm, X.astype(np.float64))
+    rel = np.linalg.norm(Z - z_ref) / np.linalg.norm(z_ref)
+    assert rel < 2e-2, rel                                   # BF16 operands, FP32 accumulation
+    # the same arithmetic staged exactly: BF16 operands, exact products, FP64 sums
+    q = {k: (bf16(torch, v) if k[0] == "W" else v) for k, v in prm.items()}
+    h1 = bf16(torch, np.maximum(bf16(torch, X) @ q["W1"].T + q["b1"], 0))
+    h2 = bf16(torch, np.maximum(h1 @ q["W2"].T + q["b2"], 0))
+    z_em = h2 @ q["W3"].T + q["b3"]
+    rel_em = np.linalg.norm(Z - z_em) / np.linalg.norm(z_em)
+    assert rel_em < 2e-3, rel_em
+
+
+@pytest.mark.parametrize("I,H,O", SHAPES)
+def test_gradients_match_oracle(am, torch, I, H, O):
+    X, Y = _rand_xy(250, I, O, 2)
+    with am.Mesher(max_cells=1024, max_neurons=64, max_width=32) as m:
+        m.proposal_init(I, H, O, max_batch=256, seed=5)
+        # non-zero biases so that every bias gradient path is exercised
+        p = m.proposal_params()
+        rng = np.random.default_rng(7)
+        p = p + 0.05 * rng.normal(size=p.shape).astype(np.float32)
+        m.proposal_set_params(p)
+        prm = unflatten(m.proposal_params(), I, H, O)
+        loss, g = m.proposal_grad(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda"))
+    z, cache = P.forward(prm, X.astype(np.float64))
+    want = P.loss(z, Y.astype(np.float64))
+    g_ref = P.backward(prm, z, Y.astype(np.float64), cache)
+    assert abs(loss - want) <= 5e-3 * abs(want), (loss, want)
+    got = unflatten(g, I, H, O)
+    # against the FP64 oracle: BF16 rounding of activations and of their gradients, amplified by
+    # the cancellation in the sums over samples, leaves a few per cent
+    for k in g_ref:
+        a, b = got[k].ravel(), g_ref[k].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert rel < 8e-2 and cos > 0.998, (k, rel, cos)
+    # against the same arithmetic staged exactly (BF16 operands of every product, exact
+    # products, FP32 gradients for the biases)
+    Xd = X.astype(np.float64)
+    q = {k: (bf16(torch, v) if k[0] == "W" else v) for k, v in prm.items()}
+    xb = bf16(torch, Xd)
+    a1 = xb @ q["W1"].T + q["b1"]
+    h1 = bf16(torch, np.maximum(a1, 0))
+    a2 = h1 @ q["W2"].T + q["b2"]
+    h2 = bf16(torch, np.maximum(a2, 0))
+    z = h2 @ q["W3"].T + q["b3"]
+    dz = (1 / (1 + np.exp(-z)) - Y) / Y.size
+    em = {"W3": bf16(torch, dz).T @ h2, "b3": dz.sum(0)}
+    da2 = (bf16(torch, dz) @ q["W3"]) * (a2 > 0)
+    em["W2"], em["b2"] = bf16(torch, da2).T @ h1, da2.sum(0)
+    da1 = (bf16(torch, da2) @ q["W2"]) * (a1 > 0)
+    em["W1"], em["b1"] = bf16(torch, da1).T @ xb, da1.sum(0)
+    for k in em:
+        rel = np.linalg.norm(got[k] - em[k]) / max(np.linalg.norm(em[k]), 1e-30)
+        assert rel < 5e-3, (k, rel)
+
+
+@pytest.mark.parametrize("make,dirs", [(lambda: tiny_net((8, 8), 11), RAY),
+                                       (lambda: sphere_net(seed=21, width=32, depth=4, sigma=0.05), RAY)])
+def test_samples_match_oracle(oracle_mod, am, torch, make, dirs):
+    mlp = make()
+    net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), dirs)
+    Xo, Yo, tags = P.face_samples(ref, mlp.widths)
+    with am.Mesher(max_cells=1 << 17, max_neurons=128, max_width=32) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), dirs)
+        m.march()
+        mesh = m.get_mesh(nid)
+        X, Y = m.proposal_samples(nid)
+        X, Y = X.cpu().numpy(), Y.cpu().numpy()
+        Xh, _ = m.proposal_samples(nid, max_samples=7)
+        assert Xh.shape[0] == 7 and np.array_equal(Xh.cpu().numpy(), X[:7])
+    assert len(X) == len(Xo) == len(mesh.face_vertices)
+    row = {t: i for i, t in enumerate(tags)}
+    o = mesh.face_offsets
+    for f in range(mesh.n_faces):
+        key = parity._key_int(mesh.face_keys[f])
+        for c in range(o[f], o[f + 1]):
+            i = row[(key, int(mesh.edge_planes[c]))]
+            assert np.array_equal(Y[c], Yo[i].astype(np.float32))
+            # entry point and layer fractions to FP32 rounding; the plane from the vertices
+            # (Newell) agrees with a_F up to vertex rounding, which slivers amplify
+            np.testing.assert_allclose(X[c][[0, 1, 2] + list(range(7, X.shape[1]))],
+                                       Xo[i][[0, 1, 2] + list(range(7, X.shape[1]))], rtol=0, atol=2e-6)
+            np.testing.assert_allclose(X[c][3:7], Xo[i][3:7], rtol=0, atol=1e-4)
+
+
+def test_training_reduces_loss(am, torch):
+    mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
+    with am.Mesher(max_cells=1 << 17, max_neurons=128, max_width=32) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), RAY)
+        m.march()
+        X, Y = m.proposal_samples(nid)
+        m.proposal_init(7 + mlp.L, 128, mlp.N, max_batch=512, seed=0)
+        losses = m.proposal_train(X, Y, batch=512, steps=600, lr=2e-3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.7 * losses[:5].mean(), (losses[:5], losses[-50:].mean())
+
+
+def _recall_at(scores, Y, k):
+    top = np.argsort(-scores, axis=1)[:, :k]
+    hit = np.take_along_axis(Y, top, axis=1).sum(1)
+    return float(hit.sum() / Y.sum())
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-9), ("mixed", 1e-5)])
+def test_learned_march_is_exact_and_clips_less(oracle_mod, am, torch, precision, rtol):
+    """The 3-[64]x4-1 workload, meshed with a proposal trained on the plain method's mesh of a
+    nearby checkpoint of it (every weight moved by N(0, 0.005^2)).  The plain method clips each
+    face with every row that cuts it.  The learned march must give the oracle's mesh, with a
+    small fraction of the plain clip's cuts and less time."""
+    mlp = sphere_net()
+    net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), X_RAY)
+    kw = dict(max_cells=1 << 18, max_neurons=256, max_width=64)
+    with am.Mesher(**kw) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), X_RAY)
+        m.march(precision=precision, candidates="none")            # the plain method
+        plain = m.stats()
+        parity.compare(ref, m.get_mesh(nid), mlp.N, rtol=rtol)
+        m.reset()
+        m.seed(nid, np.zeros((1, 3)), X_RAY)
+        m.march(precision=precision, candidates="nearest")
+        near = m.stats()
+        # training data: the plain method on the checkpoint
+        m.reset()
+        m.release_nets()
+        sid = m.load_mlp(sibling(mlp, seed=99))
+        m.seed(sid, np.zeros((1, 3)), X_RAY)
+        m.march(precision="fp64", candidates="none")
+        X, Y = m.proposal_samples(sid)
+        m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
+        losses = m.proposal_train(X, Y, batch=1024, steps=3000, lr=2e-3)
+        m.reset()
+        m.release_nets()
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), X_RAY)
+        m.march(precision=precision, candidates="learned")
+        lrn = m.stats()
+        mesh = m.get_mesh(nid)
+        Xa, Ya = m.proposal_samples(nid)
+        recall = _recall_at(m.proposal_forward(Xa).cpu().numpy(), Ya.cpu().numpy(), 32)
+    r = parity.compare(ref, mesh, mlp.N, rtol=rtol)
+    assert r["faces"] > 40000 and mesh.n_open_faces == 0
+
+    def line(name, st):
+        return (f"{name}: {st['cuts'] / st['cells']:.2f} cuts/cell, {st['fixups'] / st['cells']:.3f} corrected, "
+                f"{st['ms_march']:.2f} ms")
+    print(f"\n{precision}: {len(X)} samples, loss {losses[:5].mean():.4f} -> {losses[-50:].mean():.4f}, "
+          f"recall@32 {recall:.4f}; {line('plain', plain)}; {line('learned', lrn)}; {line('nearest', near)}")
+    assert recall > 0.6
+    assert lrn["cuts"] / lrn["cells"] < 0.25 * plain["cuts"] / plain["cells"]
+    assert lrn["fixups"] < plain["fixups"]
+    assert lrn["ms_march"] < plain["ms_march"]
