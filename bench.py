@@ -4,11 +4,15 @@ One step = the whole hot path on one mesh: forget the previous cells, trigger th
 cell by bisection on the device, march every analytic cell (compose, clip, emit, hash
 march) and assemble the mesh.  The workload is the 3-[64]x4-1 geometric-init SDF net
 (seed 2, every parameter perturbed by N(0, 0.05^2)) with one seed ray along +x, clipped
-to the box [-1.5, 1.5]^3 (43,780 faces).  Inputs (the net) are resident in HBM when the
-timed region starts; the e2e leg repeats the step through the C ABI from pinned host
-buffers (net upload, seed ray, mesh download) inside the timed region.
+to the box [-1.5, 1.5]^3 (43,780 faces).  The headline is mixed precision with the learned
+constraint proposal (trained before timing on the plain method's mesh of a nearby checkpoint
+of the net); the comparison legs time the plain FP64 method (every cutting row clipped), the
+nearest-row candidates and the other precision.  Inputs (the net, the proposal) are resident
+in HBM when the timed region starts; the e2e leg repeats the step through the C ABI from
+pinned host buffers (net upload, seed ray, mesh download) inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                  [--candidates learned|nearest|none] [--impl reference]
 
 Multi-GPU: each rank meshes its own copy of the workload (replicas, no collective on the
 data path); the job's value is the faces of all ranks over the slowest rank's time.
@@ -30,11 +34,28 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh)"
+METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh); mixed+learned vs plain FP64"
 UNIT = "faces/s"
 WORKLOAD = "3-[64]x4-1 geometric-init SDF MLP (seed 2, sigma 0.05), 1 seed ray +x, box 1.5"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
+
+
+# DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
+# workload) from the committed ncu capture, valid while the kernel source is the one captured
+TRAFFIC_CAPTURE = {"sha256_prefix": "8795d1a8059cc349", "precision": "mixed", "candidates": "learned",
+                   "bytes": 3.351808e6 + 0.537344e6}
+
+
+def captured_traffic(precision, candidates):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2106_10031_gb300", "csrc", "am_march.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    c = TRAFFIC_CAPTURE
+    if h == c["sha256_prefix"] and (precision, candidates) == (c["precision"], c["candidates"]):
+        return c["bytes"]
+    return None
 
 
 def parse():
@@ -45,7 +66,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     p.add_argument("--schedule", default="persistent", choices=["persistent", "levels"])
-    p.add_argument("--no-compare", action="store_true", help="skip the plain FP64 comparison leg")
+    p.add_argument("--candidates", default="learned", choices=["nearest", "learned", "none"])
+    p.add_argument("--no-compare", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -162,6 +184,7 @@ def algorithmic_work(mlp, mesh) -> dict:
     n_l x |active(l-1)| row-column products for 4 columns, plus a_F over |active(L)|;
     checks: (row, vertex) sign tests of the certification, (N + 6) x |face| per cell.
     FP64 path: 2 flops per multiply-add and per check term (4-term dot products).
+    Learned candidates add the proposal's forward pass, 2 (I H + H H + H N) FP32 flops per cell.
     Mixed path: one double-float multiply-add is 15 FP32 flops (TwoProd + TwoSum + 2 cross
     FMAs) per column, 63 per row-column product with the error-bound FMA; one check is 22 FP32
     flops (dot product, magnitude and bound)."""
@@ -175,7 +198,9 @@ def algorithmic_work(mlp, mesh) -> dict:
         rc += widths[l] * bits[:, r[l - 1]:r[l]].sum(1)
     rc += bits[:, r[-2]:r[-1]].sum(1)
     checks = (N + 6) * np.diff(mesh.face_offsets)
-    return {"row_col_products": int(rc.sum()), "checks": int(checks.sum()),
+    I, H = 7 + len(widths), 256
+    prop = 2 * (I * H + H * H + H * N) * len(keys)          # the learned proposal's forward per cell
+    return {"row_col_products": int(rc.sum()), "checks": int(checks.sum()), "proposal_fp32_flops": int(prop),
             "fp64_flops": int(8 * rc.sum() + 8 * checks.sum()),
             "df_fp32_flops": int(63 * rc.sum() + 22 * checks.sum())}
 
@@ -233,9 +258,10 @@ def run_reference(args, dist):
     return 0
 
 
-def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
+def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, candidates, prop=None):
     """Same step through the C ABI with host buffers: upload the net from pinned memory,
-    seed from a pinned host ray, march, copy the mesh back into pinned host buffers."""
+    seed from a pinned host ray, march, copy the mesh back into pinned host buffers.  A
+    learned proposal (prop = (params, (n_in, hidden, n_out))) is loaded once, untimed."""
     import torch
 
     from paper_2106_10031_gb300 import native as nt
@@ -255,7 +281,12 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
     opts = nt.am_ctx_opts(device=device, stream=stream_ptr, max_cells=1 << 17, hash_slots=0, max_face_verts=32,
                           max_neurons=256, max_width=64)
     assert lib.am_create(C.byref(ctx), C.byref(opts)) == 0, lib.am_last_error(ctx)
-    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=nt.AM_CAND_NEAREST)
+    cand = {"nearest": nt.AM_CAND_NEAREST, "learned": nt.AM_CAND_LEARNED, "none": nt.AM_CAND_NONE}[candidates]
+    if cand == nt.AM_CAND_LEARNED:
+        params, (n_in, hidden, n_out) = prop
+        assert lib.am_proposal_init(ctx, n_in, hidden, n_out, 1024, 0) == 0
+        assert lib.am_proposal_set_params(ctx, params.ctypes.data_as(C.c_void_p), len(params)) == 0
+    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=cand)
     bufs = None
     h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + 48
     d2h = 0
@@ -298,14 +329,14 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision):
             "ms_per_step": dt / steps * 1e3}
 
 
-def measure(m, nid, o, d, steps, precision, schedule, flush, stream, clocks=None):
+def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates="nearest"):
     """K timed steps; L2 flushed before each (outside the events).  Returns totals."""
     import torch
 
     def step():
         m.reset()
         m.seed(nid, o, d)
-        m.march(precision=precision, schedule=schedule)
+        m.march(precision=precision, schedule=schedule, candidates=candidates)
 
     total_ms, cell_ms, launches, cell_launches = 0.0, 0.0, 0, 0
     for _ in range(steps):
@@ -327,6 +358,39 @@ def measure(m, nid, o, d, steps, precision, schedule, flush, stream, clocks=None
             "stats": m.stats()}
 
 
+def train_proposal(m, mlp, o, d):
+    """The learned proposal for the workload: trained on the plain method's mesh (full clip,
+    FP64) of a nearby checkpoint of the net (every weight moved by N(0, 0.005^2)), outside
+    every timed region.  Leaves the context holding the workload net only."""
+    from synth import sibling
+    m.reset()
+    m.release_nets()
+    sid = m.load_mlp(sibling(mlp, seed=99))
+    m.seed(sid, o, d)
+    m.march(precision="fp64", candidates="none")
+    X, Y = m.proposal_samples(sid)
+    m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
+    t0 = time.perf_counter()
+    losses = m.proposal_train(X, Y, batch=1024, steps=3000, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    m.reset()
+    m.release_nets()
+    nid = m.load_mlp(mlp)
+    return nid, {"samples": int(X.shape[0]), "steps": 3000, "batch": 1024, "train_s": train_s,
+                 "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean())}
+
+
+def leg(m, nid, o, d, steps, precision, schedule, flush, stream, candidates, dist, all_faces):
+    measure(m, nid, o, d, 2, precision, schedule, flush, stream, candidates)
+    p = measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates)
+    p_ms = dist.allreduce(p["total_ms"], "max")
+    st = p["stats"]
+    return {"value": all_faces / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms / steps,
+            "precision": precision, "candidates": candidates,
+            "cuts_per_cell": st["cuts"] / max(1, st["cells"]), "corrected_frac": st["fixups"] / max(1, st["cells"]),
+            "_cell_ms": p["cell_ms"], "_cell_launches": p["cell_launches"]}
+
+
 def run_ours(args, dist):
     import torch
 
@@ -344,33 +408,47 @@ def run_ours(args, dist):
     nid = m.load_mlp(mlp)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 129 MB L2
     warm = max(args.warmup, 3)
-    measure(m, nid, o, d, warm, args.precision, args.schedule, flush, stream)
+    train = None
+    if args.candidates == "learned" or not args.no_compare:
+        nid, train = train_proposal(m, mlp, o, d)
+    measure(m, nid, o, d, warm, args.precision, args.schedule, flush, stream, args.candidates)
     mesh = m.get_mesh(nid)
     faces_per_step = mesh.n_faces
     work = algorithmic_work(mlp, mesh)
     torch.cuda.synchronize()
     dist.barrier()
     with ClockSampler(dev) as clk:
-        r = measure(m, nid, o, d, args.steps, args.precision, args.schedule, flush, stream)
+        torch.cuda.nvtx.range_push("timed")        # lets a profiler select the timed steps
+        r = measure(m, nid, o, d, args.steps, args.precision, args.schedule, flush, stream, args.candidates)
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     dist.barrier()
     max_ms = dist.allreduce(r["total_ms"], "max")
     all_faces = dist.allreduce(float(faces_per_step * args.steps), "sum")
     value = all_faces / (max_ms / 1e3)
-    plain = None
-    if not args.no_compare and args.precision != "fp64":
-        measure(m, nid, o, d, 2, "fp64", args.schedule, flush, stream)
-        p = measure(m, nid, o, d, args.steps, "fp64", args.schedule, flush, stream)
-        p_ms = dist.allreduce(p["total_ms"], "max")
-        pk = p["cell_ms"] / max(1, p["cell_launches"])
-        p_ach = work["fp64_flops"] / max(1, p["cell_launches"] / args.steps) / (pk / 1e3) / 1e12
-        plain = {"value": all_faces / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms / args.steps,
-                 "speedup_of_headline": (all_faces / (max_ms / 1e3)) / (all_faces / (p_ms / 1e3)),
-                 "roofline": {"kernel": "march_persistent_kernel<FP64>", "bound": "alu", "achieved": p_ach,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_ach / FP64_PEAK_TFLOPS}}
+    legs = None
+    if not args.no_compare:
+        legs = {}
+        for name, prec, cand in (("plain_fp64", "fp64", "none"), ("fp64_nearest", "fp64", "nearest"),
+                                 ("mixed_nearest", "mixed", "nearest"), ("fp64_learned", "fp64", "learned"),
+                                 ("mixed_learned", "mixed", "learned")):
+            if (prec, cand) == (args.precision, args.candidates):
+                continue
+            g = leg(m, nid, o, d, args.steps, prec, args.schedule, flush, stream, cand, dist, all_faces)
+            if prec == "fp64":
+                pk = g["_cell_ms"] / max(1, g["_cell_launches"])
+                p_ach = work["fp64_flops"] / max(1, g["_cell_launches"] / args.steps) / (pk / 1e3) / 1e12
+                g["roofline"] = {"kernel": "march_persistent_kernel<FP64>", "bound": "alu", "achieved": p_ach,
+                                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_ach / FP64_PEAK_TFLOPS,
+                                 "counts": "compose + checks FP64 flops only"}
+            g.pop("_cell_ms"), g.pop("_cell_launches")
+            g["headline_speedup"] = value / g["value"]
+            legs[name] = g
+        legs["proposal_training"] = train
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_leg(mlp, o, d, args.steps, dev, stream.cuda_stream, precision)
+        prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
+        e2e = e2e_leg(mlp, o, d, args.steps, dev, stream.cuda_stream, precision, args.candidates, prop)
         e2e_ms = dist.allreduce(e2e.pop("ms_per_step") * args.steps, "max")
         e2e["value"] = dist.allreduce(float(faces_per_step * args.steps), "sum") / (e2e_ms / 1e3)
     m.close()
@@ -384,6 +462,8 @@ def run_ours(args, dist):
         psrc = "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.19 TFLOP/s at 1995 MHz)"
     else:
         flops, peak, kname = work["df_fp32_flops"], FP32_PEAK_TFLOPS, "march_persistent_kernel<double-float>"
+        if args.candidates == "learned":
+            flops += work["proposal_fp32_flops"]
         psrc = "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 69.4 TFLOP/s at 1995 MHz)"
     if args.schedule == "levels":
         kname = kname.replace("persistent", "range")
@@ -394,15 +474,17 @@ def run_ours(args, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": args.precision,
-                   "schedule": args.schedule, "parallelism": f"replicas x{dist.world}",
+                   "candidates": args.candidates, "schedule": args.schedule,
+                   "parallelism": f"replicas x{dist.world}",
                    "l2": "flushed before every step (256 MiB write)"},
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "flops_per_launch": flops / launches_per_step,
+                     "frac": achieved / peak, "traffic": captured_traffic(args.precision, args.candidates), "flops_per_launch": flops / launches_per_step,
                      "launch_ms": per_launch_ms, "kernel_share_of_step": r["cell_ms"] / max(r["total_ms"], 1e-9),
                      "peak_source": psrc},
-        "plain_fp64": plain,
+        "legs": legs,
         "exactness": {"refined_cells": st["refined_cells"], "close_calls": st["close_calls"],
-                      "fixups": st["fixups"], "degenerate": st["degenerate"]},
+                      "fixups": st["fixups"], "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
+                      "degenerate": st["degenerate"]},
         "cpu_baseline": base,
         "e2e": e2e,
         "clocks": clk.summary(),

@@ -226,7 +226,8 @@ am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, i
                               int64_t *n_samples);
 
 /* Create (or replace) the context's proposal with Kaiming-normal weights drawn from seed.
- * max_batch bounds the samples of one forward / gradient call.  hidden <= 1024. */
+ * max_batch bounds the samples of one forward / gradient call.  n_in <= 64; hidden is even and
+ * <= 768 (the march evaluates the proposal in shared memory with BF16-pair loads). */
 am_status am_proposal_init(am_ctx *ctx, int n_in, int hidden, int n_out, int max_batch, uint64_t seed);
 
 /* Copy the flat FP32 parameters out of / into the context (host arrays of n_params values). */

@@ -707,8 +707,9 @@ am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, i
 am_status am_proposal_init(am_ctx *ctx, int n_in, int hidden, int n_out, int max_batch, uint64_t seed)
 {
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
-    if (n_in < 1 || n_in > 64 || hidden < 1 || hidden > 1024 || n_out < 1 || n_out > kMaxNeurons || max_batch < 1)
-        return fail(ctx, AM_ERR_INVALID_ARG, "proposal shape out of range");
+    if (n_in < 1 || n_in > 64 || hidden < 2 || hidden > 768 || (hidden & 1) || n_out < 1 || n_out > kMaxNeurons ||
+        max_batch < 1)
+        return fail(ctx, AM_ERR_INVALID_ARG, "proposal shape out of range (n_in <= 64, even hidden <= 768)");
     proposal_free(ctx->prop);
     CU(proposal_alloc(ctx->prop, n_in, hidden, n_out, max_batch));
     ProposalDev &p = ctx->prop;

@@ -18,7 +18,7 @@ struct ProposalView {
     const float *b1;              // hidden
     const __nv_bfloat16 *w2t;     // hidden x hidden, [in][out]
     const float *b2;
-    const __nv_bfloat16 *w3t;     // hidden x n_out, [in][out]
+    const __nv_bfloat16 *w3t;     // hidden x (n_out rounded up to even), [in][out]
     const float *b3;
     int n_in, hidden, n_out;
 };

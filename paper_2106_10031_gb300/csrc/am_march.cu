@@ -543,12 +543,57 @@ __device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf)
 
 // Features: entry point (3), unit face-plane normal (3), plane offset (1), active fraction of
 // each hidden layer (L).  Scores go to z[0..N) (logits; larger = more likely an edge plane).
+// y = W x for one cell, W^T stored as n_in rows of n_pairs BF16 pairs (row stride 2 n_pairs).
+// Threads take output pairs; when there are fewer pairs than threads the j range is split G
+// ways and the partial sums go to part (G x 2 n_pairs floats).  G == 1: y = act(W x + b).
+__device__ __forceinline__ void gemv_bf16x2(const __nv_bfloat16 *wt, int n_pairs, int n_in, int n_out,
+                                            const float *x, const float *b, bool relu, float *y, float *part, int G)
+{
+    const __nv_bfloat162 *w = reinterpret_cast<const __nv_bfloat162 *>(wt);
+    for (int q = threadIdx.x; q < n_pairs * G; q += kT) {
+        const int pr = q % n_pairs, g = q / n_pairs;
+        const int j0 = g * n_in / G, j1 = (g + 1) * n_in / G;
+        float a0 = 0.0f, a1 = 0.0f;
+        const __nv_bfloat162 *wp = w + pr;
+#pragma unroll 8
+        for (int j = j0; j < j1; ++j) {
+            const float2 wf = __bfloat1622float2(wp[(size_t)j * n_pairs]);
+            const float xj = x[j];
+            a0 = fmaf(wf.x, xj, a0);
+            a1 = fmaf(wf.y, xj, a1);
+        }
+        const int o = 2 * pr;
+        if (G == 1) {
+            a0 += b[o];
+            y[o] = relu ? fmaxf(a0, 0.0f) : a0;
+            if (o + 1 < n_out) {
+                a1 += b[o + 1];
+                y[o + 1] = relu ? fmaxf(a1, 0.0f) : a1;
+            }
+        } else {
+            part[g * 2 * n_pairs + o] = a0;
+            part[g * 2 * n_pairs + o + 1] = a1;
+        }
+    }
+    if (G > 1) {
+        __syncthreads();
+        for (int o = threadIdx.x; o < n_out; o += kT) {
+            float a = b[o];
+            for (int g = 0; g < G; ++g) a += part[g * 2 * n_pairs + o];
+            y[o] = relu ? fmaxf(a, 0.0f) : a;
+        }
+    }
+}
+
+// Learned proposal (no counterpart in the paper): sigmoid-free scores z[0:N] of every neuron for
+// this cell, from its entry point, the unit normal and offset of a_F and the per-layer active
+// fractions of its pattern.  Hidden widths are even (BF16 pairs); W3^T rows are padded to even.
 __device__ void proposal_scores(const MarchArgs &a, const NetDev &net, int64_t cell, const Sh &s, float *z)
 {
     const ProposalView &P = a.prop;
     const int tid = threadIdx.x, H = P.hidden, O = P.n_out, I = P.n_in;
     float *x = s.partf;            // the compose partial sums are free here
-    float *h1 = x + 64, *h2 = h1 + H;
+    float *h1 = x + 64, *h2 = h1 + H, *part = h2 + H;
     if (tid == 0) {
         x[0] = __ldcg(a.ar.entry_pt + cell * 3);
         x[1] = __ldcg(a.ar.entry_pt + cell * 3 + 1);
@@ -575,34 +620,10 @@ __device__ void proposal_scores(const MarchArgs &a, const NetDev &net, int64_t c
         h1[t] = fmaxf(acc, 0.0f);
     }
     __syncthreads();
-    for (int t = tid; t < H; t += kT) {
-        float acc = P.b2[t];
-        for (int j = 0; j < H; ++j) acc = fmaf(__bfloat162float(P.w2t[(size_t)j * H + t]), h1[j], acc);
-        h2[t] = fmaxf(acc, 0.0f);
-    }
+    const int H2 = H >> 1, O2 = (O + 1) >> 1;
+    gemv_bf16x2(P.w2t, H2, H, H, h1, P.b2, true, h2, part, H2 >= kT ? 1 : kT / H2);
     __syncthreads();
-    for (int base = 0; base < O; base += 8 * kT) {
-        float acc[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int o = base + tid + i * kT;
-            acc[i] = o < O ? P.b3[o] : 0.0f;
-        }
-        for (int j = 0; j < H; ++j) {
-            const float hj = h2[j];
-            const __nv_bfloat16 *wr = P.w3t + (size_t)j * O;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int o = base + tid + i * kT;
-                if (o < O) acc[i] = fmaf(__bfloat162float(wr[o]), hj, acc[i]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int o = base + tid + i * kT;
-            if (o < O) z[o] = acc[i];
-        }
-    }
+    gemv_bf16x2(P.w3t, O2, H, O, h2, P.b3, false, z, part, O2 >= kT ? 1 : kT / O2);
     __syncthreads();
 }
 

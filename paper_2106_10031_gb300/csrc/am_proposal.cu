@@ -152,13 +152,14 @@ __global__ void adam_kernel(float *w, const float *g, float *m, float *v, __nv_b
     }
 }
 
-// transposed BF16 copy of a rows x cols FP32 matrix (for coalesced reads in the march)
-__global__ void transpose_bf16_kernel(const float *W, int rows, int cols, __nv_bfloat16 *WT)
+// transposed BF16 copy of a rows x cols FP32 matrix with row stride ld >= rows (the padding is
+// zero), for coalesced BF16-pair reads in the march
+__global__ void transpose_bf16_kernel(const float *W, int rows, int cols, int ld, __nv_bfloat16 *WT)
 {
-    const int64_t n = (int64_t)rows * cols;
+    const int64_t n = (int64_t)ld * cols;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / cols), c = (int)(i % cols);
-        WT[(size_t)c * rows + r] = __float2bfloat16_rn(W[i]);
+        const int c = (int)(i / ld), r = (int)(i % ld);
+        WT[i] = __float2bfloat16_rn(r < rows ? W[(size_t)r * cols + c] : 0.0f);
     }
 }
 
@@ -244,7 +245,7 @@ cudaError_t proposal_alloc(ProposalDev &p, int n_in, int hidden, int n_out, int 
     if ((e = cudaMalloc(&p.v, sizeof(float) * tot))) return e;
     if ((e = cudaMalloc(&p.wb, sizeof(__nv_bfloat16) * tot))) return e;
     if ((e = cudaMalloc(&p.w2t, sizeof(__nv_bfloat16) * hidden * hidden))) return e;
-    if ((e = cudaMalloc(&p.w3t, sizeof(__nv_bfloat16) * hidden * n_out))) return e;
+    if ((e = cudaMalloc(&p.w3t, sizeof(__nv_bfloat16) * hidden * (n_out + 1)))) return e;
     const int64_t act = (int64_t)max_batch * std::max(std::max(hidden, n_out), n_in);
     for (int i = 0; i < 8; ++i)
         if ((e = cudaMalloc(&p.buf[i], sizeof(float) * act))) return e;
@@ -269,8 +270,11 @@ void proposal_free(ProposalDev &p)
 void proposal_sync_copies(ProposalDev &p, cudaStream_t st)
 {
     to_bf16_kernel<<<blocks_for(p.n_params), 256, 0, st>>>(p.w, p.wb, p.n_params);
-    transpose_bf16_kernel<<<blocks_for((int64_t)p.hidden * p.hidden), 256, 0, st>>>(p.w + p.off[2], p.hidden, p.hidden, p.w2t);
-    transpose_bf16_kernel<<<blocks_for((int64_t)p.n_out * p.hidden), 256, 0, st>>>(p.w + p.off[4], p.n_out, p.hidden, p.w3t);
+    const int ld3 = (p.n_out + 1) & ~1;
+    transpose_bf16_kernel<<<blocks_for((int64_t)p.hidden * p.hidden), 256, 0, st>>>(p.w + p.off[2], p.hidden, p.hidden,
+                                                                                   p.hidden, p.w2t);
+    transpose_bf16_kernel<<<blocks_for((int64_t)ld3 * p.hidden), 256, 0, st>>>(p.w + p.off[4], p.n_out, p.hidden, ld3,
+                                                                              p.w3t);
 }
 
 // Forward pass over B samples (B <= max_batch).  Activations: buf0 a1, buf1 a2, buf2 z (FP32);
