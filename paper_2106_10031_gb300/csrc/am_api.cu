@@ -578,6 +578,9 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown candidates mode %d", (int)op.candidates);
     if (op.candidates == AM_CAND_LEARNED && !ctx->prop.w)
         return fail(ctx, AM_ERR_STATE, "AM_CAND_LEARNED needs a proposal (am_proposal_init / am_proposal_train)");
+    if (op.candidates == AM_CAND_LEARNED && ctx->prop.hidden > proposal_max_hidden())
+        return fail(ctx, AM_ERR_INVALID_ARG, "proposal hidden width %d above the march's %d", ctx->prop.hidden,
+                    proposal_max_hidden());
     ma.candidates = (int)op.candidates;
     if (ctx->prop.w) {
         ProposalDev &p = ctx->prop;

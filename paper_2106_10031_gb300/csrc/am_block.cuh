@@ -97,40 +97,36 @@ __device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsi
 // key, so a claim never waits for a key to be written.  A claim hands out the next cell id,
 // writes the new cell's record there (key, net, hash, the crossed plane and a point of the
 // shared edge), then publishes it through ready[id].
-__device__ __forceinline__ void insert_neighbor(const Arena &ar, int64_t parent, int net, unsigned flip,
-                                             unsigned long long h, float px, float py, float pz)
+__device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned *mask, int64_t parent, int net,
+                                                unsigned flip, unsigned long long h, float px, float py, float pz)
 {
     const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
     unsigned long long pos = h & ar.slot_mask;
     for (int probe = 0; probe < kMaxProbe; ++probe) {
-        unsigned long long cur = *((volatile unsigned long long *)(ar.slots + pos));
+        const unsigned long long cur = atomicCAS(ar.slots + pos, 0ull, mine);
         if (cur == 0ull) {
-            unsigned long long prev = atomicCAS(ar.slots + pos, 0ull, mine);
-            if (prev == 0ull) {
-                long long id = (long long)atomicAdd(ar.counters + kNCells, 1ull);
-                if (id >= ar.cap) {
-                    atomicOr(ar.counters + kStatus, kStCellCap);
-                    return;
-                }
-                const unsigned long long *kp = ar.keys + parent * ar.kw;
-                unsigned long long *kn = ar.keys + id * ar.kw;
-                for (int w = 0; w < ar.kw; ++w) {
-                    unsigned long long x = __ldcg(kp + w);
-                    if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
-                    kn[w] = x;
-                }
-                ar.net[id] = net;
-                ar.hash[id] = h;
-                ar.nverts[id] = -1;
-                ar.entry_plane[id] = (int32_t)flip;
-                ar.entry_pt[id * 3 + 0] = px;
-                ar.entry_pt[id * 3 + 1] = py;
-                ar.entry_pt[id * 3 + 2] = pz;
-                __threadfence();
-                atomicExch(ar.ready + id, 1u);
+            long long id = (long long)atomicAdd(ar.counters + kNCells, 1ull);
+            if (id >= ar.cap) {
+                atomicOr(ar.counters + kStatus, kStCellCap);
                 return;
             }
-            cur = prev;
+            // the parent's key is its state, held by the block in shared memory
+            unsigned long long *kn = ar.keys + id * ar.kw;
+            for (int w = 0; w < ar.kw; ++w) {
+                unsigned long long x = (unsigned long long)mask[2 * w] | ((unsigned long long)mask[2 * w + 1] << 32);
+                if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
+                kn[w] = x;
+            }
+            ar.net[id] = net;
+            ar.hash[id] = h;
+            ar.nverts[id] = -1;
+            ar.entry_plane[id] = (int32_t)flip;
+            ar.entry_pt[id * 3 + 0] = px;
+            ar.entry_pt[id * 3 + 1] = py;
+            ar.entry_pt[id * 3 + 2] = pz;
+            // publish: every write above is visible to whoever acquires the flag
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ar.ready + id), "r"(1u) : "memory");
+            return;
         }
         if (slot_tag(cur) == hash_tag(h)) {
             const int64_t pb = slot_parent(cur);

@@ -34,6 +34,7 @@ struct MarchArgs {
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
 };
 int march_smem_bytes(int max_n, int max_w);
+int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
 // mode 0 = FP64, 1 = double-float (mixed); persistent = ticket queue, else one level [begin, end)
 void launch_march(const MarchArgs &a, int mode, bool persistent, int grid, cudaStream_t st);

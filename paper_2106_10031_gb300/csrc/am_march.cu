@@ -35,10 +35,20 @@
 
 namespace am {
 
-constexpr int kT = 256;           // threads per block
+// Threads per block and the minimum resident blocks per SM the compiler must allow for
+// (register budget); both can be set at build time for launch-shape sweeps.
+#ifndef AM_THREADS
+#define AM_THREADS 256
+#endif
+#ifndef AM_MIN_BLOCKS
+#define AM_MIN_BLOCKS 2
+#endif
+constexpr int kT = AM_THREADS;    // threads per block
 constexpr int kNW = kT / 32;      // warps per block
 constexpr int kMaxPoly = 64;      // polygon vertices in flight
 constexpr int kNear = 32;         // rows clipped by warp 0 before the full check
+constexpr int kPicks = kNear / kNW;   // candidates each warp contributes
+static_assert(kT % 32 == 0 && kNW <= 32 && kNear % kNW == 0, "block shape");
 constexpr int kMaxFix = 8;        // check / fix-up rounds
 constexpr float kU = 5.9604645e-8f;            // 2^-24
 constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
@@ -71,7 +81,7 @@ __host__ __device__ inline Lay march_layout(int max_n, int max_w)
     Lay s;
     const int nr = max_n + kBoxPlanes + kSquarePlanes;
     int o = 0;
-    s.mask = o;  o = al16(o + ((max_n + 31) / 32) * 4);
+    s.mask = o;  o = al16(o + ((max_n + 63) / 64) * 8);   // the whole key (kw 64-bit words)
     s.rows = o;  o = al16(o + nr * 32);                 // double[4] (FP64) or float[4] hi + float[4] lo (DF)
     s.err = o;   o = al16(o + nr * 4);
     s.rinv = o;  o = al16(o + nr * 4);
@@ -91,6 +101,9 @@ __host__ __device__ inline Lay march_layout(int max_n, int max_w)
 }
 
 int march_smem_bytes(int max_n, int max_w) { return march_layout(max_n, max_w).total; }
+
+// The proposal's scores use the compose scratch: 64 features + 2 hidden layers + 2 kT partials.
+int proposal_max_hidden() { return (kT * 10 - 64 - 2 * kT) / 2; }
 
 struct Sh {
     unsigned *mask;
@@ -759,7 +772,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             else if (d < b2) { b2 = d; k2 = k; }
         }
 #pragma unroll 1
-        for (int pick = 0; pick < 4; ++pick) {
+        for (int pick = 0; pick < kPicks; ++pick) {
             float bd = b1;
             int bk = k1;
             for (int o = 16; o > 0; o >>= 1) {
@@ -767,37 +780,28 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                 const int ok = __shfl_xor_sync(0xffffffffu, bk, o);
                 if (ok >= 0 && (bk < 0 || od < bd || (od == bd && ok < bk))) { bd = od; bk = ok; }
             }
-            if (lane == 0) { s.near_w[wid * 4 + pick] = bk; s.near_dw[wid * 4 + pick] = bd; }
+            if (lane == 0) { s.near_w[wid * kPicks + pick] = bk; s.near_dw[wid * kPicks + pick] = bd; }
             if (bk >= 0 && bk == k1) { b1 = b2; k1 = k2; b2 = 3.0e38f; k2 = -1; }
         }
     }
     __syncthreads();
 
     AM_TICK(tp2);
-    // ---- a4: warp 0 sorts the near rows by distance and cuts the square with them
+    // ---- a4: warp 0 cuts the square with the candidates, nearest cutting row first.  A row
+    // that holds on the polygon holds on every later (smaller) one, so it retires at once.
     if (wid == 0) {
-        float d = s.near_dw[lane];
-        int k = s.near_w[lane];
-        if (k < 0) d = 3.0e38f;
-#pragma unroll 1
-        for (int size = 2; size <= 32; size <<= 1) {           // bitonic sort, ascending
-#pragma unroll 1
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                const float od = __shfl_xor_sync(0xffffffffu, d, stride);
-                const int ok = __shfl_xor_sync(0xffffffffu, k, stride);
-                const bool up = (lane & size) == 0;
-                const bool lower = (lane & stride) == 0;
-                const bool mine_first = d < od || (d == od && k < ok);
-                if ((lower == up) != mine_first) { d = od; k = ok; }
-            }
-        }
-        const int nn = __popc(__ballot_sync(0xffffffffu, k >= 0 && d < 3.0e38f));
+        const float d = s.near_dw[lane];
+        const int k = s.near_w[lane];
+        bool live = k >= 0 && d < 3.0e38f;
+        // order-preserving unsigned image of the distance (scores may be negative)
+        const unsigned du = __float_as_uint(d);
+        const unsigned key = (du & 0x80000000u) ? ~du : (du | 0x80000000u);
         AM_TICK(tp2a);
-        int m = s.si[0], buf = 0, status = 0, done = 0, ncut = 0;
+        int m = s.si[0], buf = 0, status = 0, ncut = 0;
         const float aFf[4] = {s.aFhi[0], s.aFhi[1], s.aFhi[2], s.aFhi[3]};
-        while (m > 0 && done < nn) {
+        while (m > 0) {
             bool cut = false;
-            if (lane >= done && lane < nn) {
+            if (live) {
                 if (M == kFP64) {
                     double r[4];
                     fetch_row<double, M>(s, k, r);
@@ -810,10 +814,11 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                     for (int i = 0; i < m && !cut; ++i) cut = pdist(r, ri, s.pf[buf][i]) > 1e-7f;
                 }
             }
-            const unsigned cm = __ballot_sync(0xffffffffu, cut);
-            if (!cm) break;
-            const int first = __ffs(cm) - 1;
-            const int kc = __shfl_sync(0xffffffffu, k, first);
+            live = cut;
+            if (!__any_sync(0xffffffffu, cut)) break;
+            const unsigned kmin = __reduce_min_sync(0xffffffffu, cut ? key : 0xffffffffu);
+            const int kc = (int)__reduce_min_sync(0xffffffffu, (cut && key == kmin) ? (unsigned)k : 0xffffffffu);
+            if (k == kc) live = false;
             bool sw;
             int nm;
             if (M == kFP64) nm = warp_cut<double, M>(s, s.pv, m, buf, kc, a.delta, s.aF, &sw);
@@ -821,7 +826,6 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             if (nm < 0) { status = 1; m = 0; break; }
             if (sw) buf ^= 1;
             m = nm;
-            done = first + 1;
             ++ncut;
         }
         AM_TICK(tp3a);
@@ -931,13 +935,19 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     for (int i = 0; i < m; ++i)
         if (s.pe[buf][i] >= N + kBoxPlanes) status = 3;   // a square edge: the plane misses the box
     int emit = (m >= 3 && status == 0) ? m : 0;
-    if (emit && tid == 0) {
+    if (emit && wid == 0) {
+        // area of the polygon, as a fan about vertex 0 summed over the warp's lanes
+        const double *p0 = s.pv[buf][0];
         double nx = 0.0, ny = 0.0, nz = 0.0;
-        for (int i = 0; i < m; ++i) {
-            const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
-            nx += p[1] * q[2] - p[2] * q[1]; ny += p[2] * q[0] - p[0] * q[2]; nz += p[0] * q[1] - p[1] * q[0];
+        for (int i = lane + 1; i < m - 1; i += 32) {
+            const double *p = s.pv[buf][i], *q = s.pv[buf][i + 1];
+            const double ax = p[0] - p0[0], ay = p[1] - p0[1], az = p[2] - p0[2];
+            const double bx = q[0] - p0[0], by = q[1] - p0[1], bz = q[2] - p0[2];
+            nx += ay * bz - az * by; ny += az * bx - ax * bz; nz += ax * by - ay * bx;
         }
-        s.si[6] = 0.5 * sqrt(nx * nx + ny * ny + nz * nz) > 1e-24 * a.box * a.box;
+        nx = warp_sum(nx); ny = warp_sum(ny); nz = warp_sum(nz);
+        const double amin = 2e-24 * a.box * a.box;          // twice the smallest kept area
+        if (lane == 0) s.si[6] = nx * nx + ny * ny + nz * nz > amin * amin;
     }
     __syncthreads();
     if (emit && !s.si[6]) emit = 0;
@@ -966,7 +976,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             const int e = s.pe[buf][i];
             if (e >= N) continue;
             const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
-            insert_neighbor(ar, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+            insert_neighbor(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
                             (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
         }
     }
@@ -992,7 +1002,7 @@ __device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
     if (__ldcg(ar.nverts + cell) == -2) return;          // a duplicate seed id: never solved
     const NetDev &net = a.nets[__ldcg(ar.net + cell)];
     const unsigned long long *key = ar.keys + cell * ar.kw;
-    for (int w = threadIdx.x; w < (net.N + 31) / 32; w += kT)
+    for (int w = threadIdx.x; w < 2 * ar.kw; w += kT)       // all key words: pushes copy them
         s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
     __syncthreads();
     if (MODE == kDF && !net.df_ok) {
@@ -1088,7 +1098,7 @@ __device__ __forceinline__ void blk_flush(const MarchArgs &a, const Sh &s)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kT, 2) march_persistent_kernel(MarchArgs a)
+__global__ void __launch_bounds__(kT, AM_MIN_BLOCKS) march_persistent_kernel(MarchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Sh s = make_sh(smem, a.max_n, a.max_w);
@@ -1114,7 +1124,7 @@ __global__ void __launch_bounds__(kT, 2) march_persistent_kernel(MarchArgs a)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kT, 2) march_range_kernel(MarchArgs a)
+__global__ void __launch_bounds__(kT, AM_MIN_BLOCKS) march_range_kernel(MarchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Sh s = make_sh(smem, a.max_n, a.max_w);
