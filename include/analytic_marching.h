@@ -60,10 +60,18 @@ typedef enum {
 
 typedef enum {
     AM_PREC_FP64 = 0,         /* compose and clip in FP64 (the plain path) */
-    AM_PREC_MIXED = 1         /* compose in double-float arithmetic on the FP32 pipes with a
+    AM_PREC_MIXED = 1,        /* compose in double-float arithmetic on the FP32 pipes with a
                                  rigorous error bound per row; vertices solved in FP64; every
                                  sign test certified against the bounds (FP32, then FP64 for
                                  close calls); a cell with an undecidable test is redone in FP64 */
+    AM_PREC_TENSOR = 2        /* compose of the hidden layers on the tensor cores: W and Z split
+                                 into three BF16 parts, four mma.sync products per tile
+                                 accumulated in FP32; each row carries an error ESTIMATE (random-
+                                 sign model of the accumulation with a safety factor 8, root-mean-
+                                 square propagation of the previous layers' errors), not a bound; the
+                                 tests, vertices and refinement are those of AM_PREC_MIXED.
+                                 Vertices are accurate to about 1e-6 relative.  Needs
+                                 32 ceil(n_{l-1} / 16) <= max_neurons + 10 for l >= 2. */
 } am_precision;
 
 typedef enum {
@@ -115,7 +123,7 @@ typedef struct {
     double box;               /* B of the clip box [-B, B]^3 (default 1.5) */
     double delta;             /* vertex tolerance in world units (default 1e-10): a plane within
                                  delta of a vertex counts as satisfied and as a degenerate event */
-    am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
+    am_precision precision;   /* AM_PREC_FP64 (default), AM_PREC_MIXED or AM_PREC_TENSOR */
     int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
     am_candidates candidates; /* AM_CAND_NEAREST (default), AM_CAND_LEARNED or AM_CAND_NONE */
     am_schedule schedule;     /* AM_SCHED_PERSISTENT (default) or AM_SCHED_LEVELS */
@@ -206,6 +214,15 @@ am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
 
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
+
+/* Compose only (Lemma 1, Cor. 1; Eq. 10): the affine rows of the cells whose activation
+ * patterns are d_keys (device, n x ceil(N/64) words, bit k = state of neuron k), for net_id, in
+ * the given precision.  d_rows (device, n x (N + 1) x 4 doubles) receives for each key the N
+ * sign-adjusted rows (1 - 2 s_k) [a_k | a_k0] of Eq. 10 followed by [a_F | a_F0] (Eq. 8);
+ * d_err (device, n x (N + 1) floats, may be NULL) the per-row error bound (AM_PREC_MIXED),
+ * estimate (AM_PREC_TENSOR) or 0 (AM_PREC_FP64), as an l1 bound on the 4 coefficients. */
+am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, am_precision precision,
+                     double *d_rows, float *d_err);
 
 /* ---- learned constraint proposal --------------------------------------------------------
  * No counterpart in the paper.  A small MLP, x (7 + L) -> H -> H -> n_out, ReLU hidden layers,

@@ -23,11 +23,29 @@ constexpr int kMaxNets = 1024;
 constexpr unsigned long long kZobristSeed = 0x2106100310031ull;
 
 struct NetHost {
-    NetDev dev;              // device pointers into `blob` and `fblob`
+    NetDev dev;              // device pointers into `blob`, `fblob` and `tblob`
     double *blob = nullptr;  // device allocation holding AT, Cl, w_out (FP64)
     float *fblob = nullptr;  // the same as double-float pairs (hi, lo)
+    void *tblob = nullptr;   // BF16 hi/lo fragments of W_l and row norms (tensor-core compose)
     int N = 0, max_w = 0;
 };
+
+// FP32 -> BF16, round to nearest even (finite inputs)
+uint16_t bf16_rn(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_float(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
 
 struct MeshInfo {
     int64_t faces = 0, face_base = 0, corners = 0, corner_base = 0, verts = 0, vert_base = 0, open = 0;
@@ -240,6 +258,7 @@ void am_destroy(am_ctx *ctx)
     for (auto &n : ctx->nets) {
         if (n.blob) cudaFree(n.blob);
         if (n.fblob) cudaFree(n.fblob);
+        if (n.tblob) cudaFree(n.tblob);
     }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -330,6 +349,67 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         nd.AThi[l] = l > 1 ? nh.fblob + offA[l] : nullptr;
         nd.ATlo[l] = l > 1 ? nh.fblob + lo_off + offA[l] : nullptr;
     }
+    {
+        // tensor-core operands: BF16 hi/lo of W_l (hidden part) in A-fragment order, row norms
+        std::vector<size_t> offF(L + 1, 0), offN(L + 1, 0);
+        size_t words = 0;                          // in uint4 units
+        for (int l = 2; l <= L; ++l) {
+            const int n = dsc->width[l - 1], np = dsc->width[l - 2];
+            offF[l] = words;
+            words += (size_t)((n + 15) / 16) * ((np + 15) / 16) * 96;
+        }
+        for (int l = 2; l <= L; ++l) {
+            offN[l] = words;
+            words += (size_t)(2 * dsc->width[l - 1] + 3) / 4;
+        }
+        std::vector<uint32_t> tb(4 * std::max<size_t>(words, 1), 0u);
+        for (int l = 2; l <= L; ++l) {
+            const int n = dsc->width[l - 1], np = dsc->width[l - 2];
+            const int fan = np + (l == dsc->skip_layer ? in_dim : 0);
+            const double *W = dsc->W[l - 1];
+            const int Mt = (n + 15) / 16, Kt = (np + 15) / 16;
+            auto wat = [&](int m, int k) { return (m < n && k < np) ? W[(size_t)m * fan + k] : 0.0; };
+            for (int mt = 0; mt < Mt; ++mt)
+                for (int kt = 0; kt < Kt; ++kt)
+                    for (int lane = 0; lane < 32; ++lane) {
+                        const int g = lane >> 2, t = lane & 3;
+                        // a0..a7: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1), then the same at k + 8
+                        const int rows[8] = {g, g, g + 8, g + 8, g, g, g + 8, g + 8};
+                        const int cols[8] = {2 * t, 2 * t + 1, 2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9, 2 * t + 8, 2 * t + 9};
+                        uint16_t part[3][8];              // w = hi + mid + lo (+ |w| 2^-27)
+                        for (int i = 0; i < 8; ++i) {
+                            double w = wat(mt * 16 + rows[i], kt * 16 + cols[i]);
+                            for (int q = 0; q < 3; ++q) {
+                                part[q][i] = bf16_rn((float)w);
+                                w -= (double)bf16_to_float(part[q][i]);
+                            }
+                        }
+                        for (int q = 0; q < 3; ++q) {
+                            uint32_t *t = tb.data() + 4 * (offF[l] + ((size_t)mt * Kt + kt) * 96 + 32 * q + lane);
+                            for (int r = 0; r < 4; ++r)
+                                t[r] = (uint32_t)part[q][2 * r] | ((uint32_t)part[q][2 * r + 1] << 16);
+                        }
+                    }
+            float *wn = reinterpret_cast<float *>(tb.data() + 4 * offN[l]);     // (|W_m|_2, max_j |W_mj|)
+            for (int m = 0; m < n; ++m) {
+                double s2 = 0.0, mx = 0.0;
+                for (int k = 0; k < np; ++k) {
+                    const double w = W[(size_t)m * fan + k];
+                    s2 += w * w;
+                    mx = std::max(mx, fabs(w));
+                }
+                wn[2 * m] = (float)(sqrt(s2) * (1.0 + 1e-6));
+                wn[2 * m + 1] = (float)(mx * (1.0 + 1e-6));
+            }
+        }
+        CU(cudaMalloc(&nh.tblob, sizeof(uint32_t) * tb.size()));
+        CU(cudaMemcpyAsync(nh.tblob, tb.data(), sizeof(uint32_t) * tb.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));      // tb is released at the end of this scope
+        for (int l = 2; l <= L; ++l) {
+            nd.Wf[l] = reinterpret_cast<const uint4 *>(nh.tblob) + offF[l];
+            nd.wn[l] = reinterpret_cast<const float *>(reinterpret_cast<const uint4 *>(nh.tblob) + offN[l]);
+        }
+    }
     nd.w_out = nh.blob + offW;
     nd.w_out_hi = nh.fblob + offW;
     nd.w_out_lo = nh.fblob + lo_off + offW;
@@ -390,6 +470,7 @@ am_status am_release_nets(am_ctx *ctx)
     for (auto &n : ctx->nets) {
         if (n.blob) CU(cudaFree(n.blob));
         if (n.fblob) CU(cudaFree(n.fblob));
+        if (n.tblob) CU(cudaFree(n.tblob));
     }
     ctx->nets.clear();
     ctx->mesh.clear();
@@ -558,12 +639,17 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (o) op = *o;
     if (!(op.box > 0.0)) op.box = 1.5;
     if (!(op.delta > 0.0)) op.delta = 1e-10;
-    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED)
+    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED && op.precision != AM_PREC_TENSOR)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)op.precision);
+    if (op.precision == AM_PREC_TENSOR)
+        for (const NetHost &n : ctx->nets)
+            if (!tc_fits(n.dev.width, n.dev.L, ctx->opts.max_neurons))
+                return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= "
+                            "max_neurons + 10 for every layer");
     if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
     if (op.max_cells < 0 || op.grid_blocks < 0) return fail(ctx, AM_ERR_INVALID_ARG, "negative limit");
-    const int mode = op.precision == AM_PREC_MIXED ? 1 : 0;
+    const int mode = op.precision == AM_PREC_FP64 ? 0 : 1;
     unsigned long long hc[kNumCounters];
     am_status s = sync_status(ctx, hc);
     if (s != AM_OK) return s;
@@ -574,6 +660,7 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ma.delta = op.delta;
     ma.max_n = ctx->opts.max_neurons;
     ma.max_w = ctx->opts.max_width;
+    ma.tc = op.precision == AM_PREC_TENSOR ? 1 : 0;
     if (op.candidates != AM_CAND_NEAREST && op.candidates != AM_CAND_LEARNED && op.candidates != AM_CAND_NONE)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown candidates mode %d", (int)op.candidates);
     if (op.candidates == AM_CAND_LEARNED && !ctx->prop.w)
@@ -672,6 +759,32 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (s != AM_OK) return s;
     if (hc[kStatus] & kStClip) ctx->err = "a clip step met an inconsistent polygon (reported as an empty face)";
     return incomplete ? AM_INCOMPLETE : AM_OK;
+}
+
+am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, am_precision precision,
+                     double *d_rows, float *d_err)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (n < 0 || (n > 0 && (!d_keys || !d_rows))) return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    if (precision != AM_PREC_FP64 && precision != AM_PREC_MIXED && precision != AM_PREC_TENSOR)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+    const NetHost &nh = ctx->nets[net_id];
+    if (precision == AM_PREC_TENSOR && !tc_fits(nh.dev.width, nh.dev.L, ctx->opts.max_neurons))
+        return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= max_neurons + 10");
+    if (n == 0) return AM_OK;
+    MarchArgs ma{};
+    ma.nets = ctx->d_nets;
+    ma.ar = ctx->ar;
+    ma.max_n = ctx->opts.max_neurons;
+    ma.max_w = ctx->opts.max_width;
+    ma.tc = precision == AM_PREC_TENSOR ? 1 : 0;
+    launch_compose(ma, precision == AM_PREC_FP64 ? 0 : 1, ctx->d_nets + net_id,
+                   reinterpret_cast<const unsigned long long *>(d_keys), nh.dev.kw, n, d_rows, d_err, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    return AM_OK;
 }
 
 am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, int64_t max_samples,

@@ -67,6 +67,11 @@ struct NetDev {
     const double *w_out;
     const float *w_out_hi, *w_out_lo;
     double b_out;
+    // tensor-core compose: W_l (hidden part) as three BF16 parts (hi, mid, lo) in mma.m16n8k16
+    // A-fragment order, tile (mt, kt) at (mt * Kt + kt) * 96 uint4 (32 lanes per part), and the
+    // per row m of W_l the pair (|W_m|_2, max_j |W_mj|)
+    const uint4 *Wf[kMaxLayers + 1];
+    const float *wn[kMaxLayers + 1];
     unsigned long long salt;     // per-net hash salt
     int df_ok;                   // 1: the double-float bound stays useful through this net's depth
 };

@@ -31,6 +31,7 @@ struct MarchArgs {
     long long limit;         // persistent schedule: tickets >= limit are not solved
     int64_t begin, end;      // level schedule: cell ids solved by this launch
     int candidates;          // kCandNearest / kCandLearned / kCandNone
+    int tc;                  // mode 1 only: hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
 };
 int march_smem_bytes(int max_n, int max_w);
@@ -38,6 +39,12 @@ int proposal_max_hidden();      // widest proposal hidden layer the march can ev
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
 // mode 0 = FP64, 1 = double-float (mixed); persistent = ticket queue, else one level [begin, end)
 void launch_march(const MarchArgs &a, int mode, bool persistent, int grid, cudaStream_t st);
+// compose only: rows (n x (N + 1) x 4 doubles, a_F last) and errors of the cells with the given
+// keys (n x key_words words) of one net; mode as launch_march (a.tc selects the tensor cores)
+void launch_compose(const MarchArgs &a, int mode, const NetDev *net, const unsigned long long *keys, int key_words,
+                    int64_t n, double *rows, float *err, cudaStream_t st);
+// whether the tensor-core compose's scratch fits a net (width[1..L]) in a context of max_n rows
+bool tc_fits(const int *width, int L, int max_n);
 
 struct SeedArgs {
     const NetDev *nets;

@@ -52,6 +52,8 @@ static_assert(kT % 32 == 0 && kNW <= 32 && kNear % kNW == 0, "block shape");
 constexpr int kMaxFix = 8;        // check / fix-up rounds
 constexpr float kU = 5.9604645e-8f;            // 2^-24
 constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
+constexpr float kTcLoose = 3.0e38f;            // the tensor-core path lets each test decide
+constexpr double kVertexTol = 1e-5;            // largest vertex error bound (relative) kept from kDF
 constexpr long long kWaitNs = 4000000000ll;    // 4 s limit on any wait for work
 
 enum { kFP64 = 0, kDF = 1 };
@@ -105,6 +107,15 @@ int march_smem_bytes(int max_n, int max_w) { return march_layout(max_n, max_w).t
 // The proposal's scores use the compose scratch: 64 features + 2 hidden layers + 2 kT partials.
 int proposal_max_hidden() { return (kT * 10 - 64 - 2 * kT) / 2; }
 
+// The tensor-core compose keeps one layer's B fragments (16 bytes per lane per 16 input rows)
+// in the low-part row array (16 bytes per row): 32 ceil(n_{l-1} / 16) <= max_n + 10 rows.
+bool tc_fits(const int *width, int L, int max_n)
+{
+    for (int l = 2; l <= L; ++l)
+        if (32 * ((width[l - 1] + 15) / 16) > max_n + kBoxPlanes + kSquarePlanes) return false;
+    return true;
+}
+
 struct Sh {
     unsigned *mask;
     double *r64;            // FP64 rows [nr][4]
@@ -126,7 +137,7 @@ struct Sh {
     float *aFhi, *aFlo;     // 4 + 4
     float *eF;              // 1
     int *si;                // 32 ints: 0 m, 1 buf, 2 status, 3 nviol, 4 amb, 5 ndeg, 6 emit, 7 ticket,
-                            //          8 near count, 9 fix rounds
+                            //          8 near count, 9 fix rounds, 10 a vertex too uncertain
     int *wsum;              // 32 ints
     unsigned long long *blk;   // per-block statistics, flushed once when the block exits:
                                // 0 solved, 1 empty, 2 degenerate, 3 fixups, 4 refined, 5 close calls,
@@ -245,10 +256,148 @@ __device__ __forceinline__ void row64(const Sh &s, int k, double *r)
 }
 
 // ------------------------------------------------------------------------------------------
+// a2 on the tensor cores: hidden layers 2..L of the compose as split-BF16 products
+
+// D (16 x 8, FP32) += A (16 x 16, BF16, row) * B (16 x 8, BF16, col); fragments as in the PTX
+// ISA's mma.m16n8k16 layouts (a: 4 x b32, b: 2 x b32, lower element in the lower half)
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint4 &a, const uint2 &b)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+}
+
+__device__ __forceinline__ unsigned bf16_bits(float x)
+{
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+constexpr int kTcTiles = 4;         // 16-row output tiles a warp accumulates at once
+
+// Z_l = W_l diag(s_{l-1}) Z_{l-1} + C_l for l = 2..L on the tensor cores.  Z_{l-1} (FP32 rows,
+// sign-adjusted, in s.rhi; inactive rows zero) is split into three BF16 parts and laid out as
+// B1 = [Z_hi | Z_mid] and B2 = [Z_lo | 0] (16 x 8 fragments); W_l comes as three BF16 parts.
+// Four MMAs per tile: (W_hi + W_mid + W_lo) B1 + W_hi B2, whose two column halves sum to
+// W (Z_hi + Z_mid) + W_hi Z_lo: the dropped products and split residuals are below 2^-26 |W||Z|,
+// so the FP32 accumulation dominates.  The B fragments live in s.rlo, unused by this path
+// (it is zeroed before return: tensor-core rows have no low part).
+// Error estimate per row m (l1 over its 4 coefficients), not a bound:
+//   8 (2.8 2^-24 sqrt(T) + 2^-25) max_j |W_mj| sum_c |z_c|_2  +  |W_m|_2 rms(e_{l-1}),  T = 4 Kt
+// (random-sign model of the accumulation over T MMAs, each product's share bounded through
+// max|W_mj| and the column norm; the previous rows' estimates propagate by root mean square,
+// without a new factor, so the safety does not compound with depth).
+__device__ __noinline__ void compose_tc_layers(const NetDev &net, const Sh &s, int nr)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, g = lane >> 2, t4 = lane & 3;
+    uint4 *Bf = reinterpret_cast<uint4 *>(s.rlo);   // per (kt, lane): B1 (x, y), B2 (z, w)
+    float *red = reinterpret_cast<float *>(s.wsum);   // 0..3: sum z_c^2, 4: sum e^2 (no scans here)
+    for (int l = 2; l <= net.L; ++l) {
+        const int np = net.width[l - 1], nl = net.width[l], rp = net.row0[l - 1], rl = net.row0[l];
+        const int Kt = (np + 15) >> 4, Mt = (nl + 15) >> 4;
+        if (tid < 8) red[tid] = 0.0f;
+        __syncthreads();
+        // B fragments: item (kt, lane') holds rows kt*16 + 2t' + {0, 1, 8, 9} of column g'
+        for (int it = tid; it < Kt * 32; it += kT) {
+            const int kt = it >> 5, gg = (it & 31) >> 2, tt = it & 3;
+            const int c = gg & 3;
+            const bool second = gg >= 4;              // columns 4..7: Z_mid in B1, zero in B2
+            unsigned v1[4], v2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = kt * 16 + 2 * tt + (q & 1) + (q >> 1) * 8;
+                float z = 0.0f;
+                if (k < np && bit_of(s.mask, rp + k)) z = -s.rhi[4 * (rp + k) + c];   // active: z = -row
+                const float zh = __bfloat162float(__float2bfloat16_rn(z));
+                const float zm = __bfloat162float(__float2bfloat16_rn(z - zh));
+                v1[q] = bf16_bits(second ? zm : zh);
+                v2[q] = second ? 0u : bf16_bits((z - zh) - zm);
+            }
+            Bf[it] = make_uint4(v1[0] | (v1[1] << 16), v1[2] | (v1[3] << 16), v2[0] | (v2[1] << 16),
+                                v2[2] | (v2[3] << 16));
+        }
+        {
+            float z2[4] = {0.0f, 0.0f, 0.0f, 0.0f}, e2 = 0.0f;
+            for (int k = tid; k < np; k += kT)
+                if (bit_of(s.mask, rp + k)) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) z2[c] = fmaf(s.rhi[4 * (rp + k) + c], s.rhi[4 * (rp + k) + c], z2[c]);
+                    e2 = fmaf(s.err[rp + k], s.err[rp + k], e2);
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) z2[c] += __shfl_xor_sync(0xffffffffu, z2[c], o);
+                e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) atomicAdd(red + c, z2[c]);
+                atomicAdd(red + 4, e2);
+            }
+        }
+        __syncthreads();
+        const float zn = sqrtf(red[0]) + sqrtf(red[1]) + sqrtf(red[2]) + sqrtf(red[3]);
+        const float erms = sqrtf(red[4] / (float)np);
+        const float kloc = 8.0f * (2.8f * 5.9604644775390625e-8f * sqrtf((float)(4 * Kt)) + 2.98023223876953125e-8f);
+        const uint4 *Wf = net.Wf[l];
+        const float *wn = net.wn[l];
+        for (int mt0 = wid; mt0 < Mt; mt0 += kNW * kTcTiles) {
+            float acc[kTcTiles][4];
+#pragma unroll
+            for (int i = 0; i < kTcTiles; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+            for (int kt = 0; kt < Kt; ++kt) {
+                const uint4 bb = Bf[kt * 32 + lane];
+                const uint2 b1 = make_uint2(bb.x, bb.y), b2 = make_uint2(bb.z, bb.w);
+#pragma unroll
+                for (int i = 0; i < kTcTiles; ++i) {
+                    const int mt = mt0 + i * kNW;
+                    if (mt < Mt) {
+                        const uint4 *tp = Wf + ((size_t)mt * Kt + kt) * 96;
+                        const uint4 ah = __ldg(tp + lane), am = __ldg(tp + 32 + lane), al = __ldg(tp + 64 + lane);
+                        mma_bf16_16816(acc[i], ah, b1);
+                        mma_bf16_16816(acc[i], am, b1);
+                        mma_bf16_16816(acc[i], al, b1);
+                        mma_bf16_16816(acc[i], ah, b2);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kTcTiles; ++i) {
+                const int mt = mt0 + i * kNW;
+                if (mt >= Mt) continue;                  // warp-uniform
+                float o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = acc[i][q] + __shfl_xor_sync(0xffffffffu, acc[i][q], 2);
+                if (t4 < 2) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {        // rows g and g + 8
+                        const int m = mt * 16 + g + 8 * h;
+                        if (m >= nl) continue;
+                        const int r = rl + m;
+                        const float sg = bit_of(s.mask, r) ? -1.0f : 1.0f;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int c = 2 * t4 + j;
+                            const float v = o[2 * h + j] + (net.Clhi[l][4 * m + c] + net.Cllo[l][4 * m + c]);
+                            s.rhi[4 * r + c] = sg * v;
+                        }
+                        if (t4 == 0) s.err[r] = fmaf(kloc * wn[2 * m + 1], zn, wn[2 * m] * erms);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < 4 * nr; i += kT) s.rlo[i] = 0.0f;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
 // a2/a3: compose the rows of every neuron of the cell, and a_F
 
 template <int M>
-__device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
+__device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc, int nrows)
 {
     const int tid = threadIdx.x;
     // layer 1: Z_1 = C_1 (cell independent)
@@ -268,12 +417,14 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
                     s.rlo[4 * k + c] = sg * l;
                     l1 += fabsf(h);
                 }
-                s.err[k] = 2.0f * kU * kU * l1 * 1.01f;     // representation of C in double-float
+                // representation of C: double-float, or FP32 alone on the tensor-core path
+                s.err[k] = tc ? kU * l1 * 1.01f : 2.0f * kU * kU * l1 * 1.01f;
             }
         }
     }
     __syncthreads();
-    for (int l = 2; l <= net.L; ++l) {
+    if (M == kDF && tc) compose_tc_layers(net, s, nrows);
+    for (int l = (M == kDF && tc) ? net.L + 1 : 2; l <= net.L; ++l) {
         const int np = net.width[l - 1], nl = net.width[l], rp = net.row0[l - 1], rl = net.row0[l];
         const int S = nl >= kT ? 1 : kT / nl;
         // active list of layer l-1 (diag(s_{l-1}) selects these rows)
@@ -414,7 +565,7 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
                 for (int k = tid; k < nL; k += 32) cnt += bit_of(s.mask, rL + k);
                 for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
                 const float g = df_gamma(cnt + 40);
-                float h[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f}, eb = 0.0f;
+                float h[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f}, eb = 0.0f, e2 = 0.0f;
                 for (int k = tid; k < nL; k += 32) {
                     if (!bit_of(s.mask, rL + k)) continue;
                     const float wh = net.w_out_hi[k], wl = net.w_out_lo[k];
@@ -424,7 +575,12 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
                         df_fma(h[c], lo[c], wh, wl, -zh[c], -zl[c]);
                         l1 += fabsf(zh[c]);
                     }
-                    eb = __fmaf_ru(fabsf(wh), __fmaf_ru(g, l1 * 1.001f, s.err[rL + k]), eb);
+                    if (tc) {           // this product's rounding (bound) + propagated estimates (rms)
+                        eb = __fmaf_ru(fabsf(wh), g * l1 * 1.001f, eb);
+                        e2 = fmaf(wh * s.err[rL + k], wh * s.err[rL + k], e2);
+                    } else {
+                        eb = __fmaf_ru(fabsf(wh), __fmaf_ru(g, l1 * 1.001f, s.err[rL + k]), eb);
+                    }
                 }
 #pragma unroll 1
                 for (int o = 16; o > 0; o >>= 1) {
@@ -434,7 +590,9 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s)
                         df_add(h[c], lo[c], oh, ol);
                     }
                     eb = __fadd_ru(eb, __shfl_xor_sync(0xffffffffu, eb, o));
+                    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
                 }
+                if (tc) eb += 2.0f * sqrtf(e2);
                 if (tid == 0) {
                     const float bh = (float)net.b_out, bl = (float)(net.b_out - (double)bh);
                     df_add(h[3], lo[3], bh, bl);
@@ -534,7 +692,7 @@ __device__ __forceinline__ int warp_cut(const Sh &s, R (*P)[kMaxPoly][3], int m,
 
 // kDF: the final vertices in FP64 from the double-float rows, with the bound dv on how far the
 // exact vertex (exact rows) can be, |v* - v|_inf <= |M^-1|_inf max(e_a, e_b, e_F) max(1,|v|) (1.1).
-__device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf)
+__device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf, double vtol)
 {
     const int lane = threadIdx.x & 31;
     for (int i = lane; i < m; i += 32) {
@@ -547,6 +705,7 @@ __device__ __forceinline__ void df_final_vertices(const Sh &s, int m, int buf)
         const double e = fmax((double)s.err[ea], fmax((double)s.err[eb], (double)s.eF[0]));
         s.pv[buf][i][0] = v[0]; s.pv[buf][i][1] = v[1]; s.pv[buf][i][2] = v[2];
         s.dvb[i] = ok ? (float)(inorm * e * X * 1.1 + 4e-16 * X) * 1.01f : 3.0e38f;
+        if (s.dvb[i] > vtol * X) s.si[10] = 1;           // this vertex is not known well enough
     }
     __syncwarp();
 }
@@ -656,7 +815,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     const int N = net.N, NC = N + kBoxPlanes;          // checked rows: neurons + box
     long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
     AM_TICK(tp0);
-    compose<M>(net, s);
+    compose<M>(net, s, a.tc != 0, a.max_n + kBoxPlanes + kSquarePlanes);
     AM_TICK(tp1);
 
     // box rows (exact), frame and the initial square (thread 0)
@@ -714,7 +873,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             }
             m = 4;
         }
-        s.si[0] = m; s.si[1] = 0; s.si[2] = 0; s.si[3] = 0; s.si[4] = 0; s.si[5] = 0; s.si[9] = 0;
+        s.si[0] = m; s.si[1] = 0; s.si[2] = 0; s.si[3] = 0; s.si[4] = 0; s.si[5] = 0; s.si[9] = 0; s.si[10] = 0;
     }
     __syncthreads();
     // inverse norms, FP32 (they only scale distances used for ordering and the FP64 tolerance
@@ -736,8 +895,9 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         // sums of |W_l| per layer (deep, wide nets).  Go to FP64 at once instead of clipping
         // twice.
         int loose = 0;
-        for (int k = tid; k < N; k += kT) loose |= s.err[k] * s.rinv[k] > kDfLoose;
-        if (tid == 0) loose |= s.eF[0] * rsqrtf((float)(s.aF[0] * s.aF[0] + s.aF[1] * s.aF[1] + s.aF[2] * s.aF[2])) > kDfLoose;
+        const float thr = a.tc ? kTcLoose : kDfLoose;
+        for (int k = tid; k < N; k += kT) loose |= s.err[k] * s.rinv[k] > thr;
+        if (tid == 0) loose |= s.eF[0] * rsqrtf((float)(s.aF[0] * s.aF[0] + s.aF[1] * s.aF[1] + s.aF[2] * s.aF[2])) > thr;
         if (__syncthreads_or(loose)) return CellOut{0, 1};
     } else {
         __syncthreads();
@@ -829,7 +989,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             ++ncut;
         }
         AM_TICK(tp3a);
-        if (M == kDF && m > 0) df_final_vertices(s, m, buf);
+        if (M == kDF && m > 0) df_final_vertices(s, m, buf, kVertexTol);
         if (lane == 0) { s.si[0] = m; s.si[1] = buf; s.si[2] = status; s.blk[6] += (unsigned long long)ncut; }
     }
     __syncthreads();
@@ -839,6 +999,10 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     int rounds = 0;
     for (;; ++rounds) {
         const int m = s.si[0], buf = s.si[1];
+        if (M == kDF && s.si[10]) return CellOut{0, 1};     // a vertex too uncertain: FP64
+        // kDF: a polygon emptied (or a clip that failed) in the uncertified FP32 candidate pass
+        // proves nothing: FP64 decides
+        if (M == kDF && (m == 0 || s.si[2])) return CellOut{0, 1};
         if (m == 0 || s.si[2]) break;
         for (int i = tid; i < m; i += kT) {
             const double *v = s.pv[buf][i];
@@ -922,7 +1086,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                 if (sw) bb ^= 1;
                 mm = nm;
             }
-            if (M == kDF && mm > 0) df_final_vertices(s, mm, bb);
+            if (M == kDF && mm > 0) df_final_vertices(s, mm, bb, kVertexTol);
             if (lane == 0) { s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; s.blk[6] += (unsigned long long)t; }
         }
         __syncthreads();
@@ -1005,7 +1169,7 @@ __device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
     for (int w = threadIdx.x; w < 2 * ar.kw; w += kT)       // all key words: pushes copy them
         s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
     __syncthreads();
-    if (MODE == kDF && !net.df_ok) {
+    if (MODE == kDF && !net.df_ok && !a.tc) {
         if (threadIdx.x == 0) s.blk[4] += 1;             // solved in FP64 (the net's bound is too loose)
         solve_cell<kFP64>(a, net, cell, s);
     } else if (MODE == kDF) {
@@ -1136,6 +1300,44 @@ __global__ void __launch_bounds__(kT, AM_MIN_BLOCKS) march_range_kernel(MarchArg
     blk_flush(a, s);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(kT, AM_MIN_BLOCKS)
+    compose_kernel(MarchArgs a, const NetDev *netp, const unsigned long long *keys, int kw_in, int64_t n,
+                   double *rows, float *err)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Sh s = make_sh(smem, a.max_n, a.max_w);
+    const NetDev &net = *netp;
+    const int N = net.N, mw = 2 * ((a.max_n + 63) / 64);
+    for (int64_t c = blockIdx.x; c < n; c += gridDim.x) {
+        for (int w = threadIdx.x; w < mw; w += kT)
+            s.mask[w] = (w >> 1) < kw_in ? (unsigned)(keys[c * kw_in + (w >> 1)] >> ((w & 1) * 32)) : 0u;
+        __syncthreads();
+        compose<MODE>(net, s, a.tc != 0, a.max_n + kBoxPlanes + kSquarePlanes);
+        double *out = rows + c * (int64_t)(N + 1) * 4;
+        for (int k = threadIdx.x; k < N; k += kT) {
+            double r[4];
+            row64<MODE>(s, k, r);
+            out[4 * k] = r[0]; out[4 * k + 1] = r[1]; out[4 * k + 2] = r[2]; out[4 * k + 3] = r[3];
+            if (err) err[c * (N + 1) + k] = MODE == kFP64 ? 0.0f : s.err[k];
+        }
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 4; ++q) out[4 * N + q] = s.aF[q];
+            if (err) err[c * (N + 1) + N] = MODE == kFP64 ? 0.0f : s.eF[0];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_compose(const MarchArgs &a, int mode, const NetDev *net, const unsigned long long *keys, int key_words,
+                    int64_t n, double *rows, float *err, cudaStream_t st)
+{
+    const int smem = march_smem_bytes(a.max_n, a.max_w);
+    const int grid = (int)std::min<int64_t>(n, 152 * 8);
+    if (mode == kDF) compose_kernel<kDF><<<grid, kT, smem, st>>>(a, net, keys, key_words, n, rows, err);
+    else compose_kernel<kFP64><<<grid, kT, smem, st>>>(a, net, keys, key_words, n, rows, err);
+}
+
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm)
 {
     const int smem = march_smem_bytes(max_n, max_w);
@@ -1144,6 +1346,8 @@ cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm)
     if ((e = cudaFuncSetAttribute(march_persistent_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     if ((e = cudaFuncSetAttribute(march_range_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     if ((e = cudaFuncSetAttribute(march_range_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(compose_kernel<kFP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(compose_kernel<kDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     // shared memory for two resident blocks, the rest of the unified L1 for the weights and
     // the stack (the driver rounds the carveout to a supported split)
     const int carve = std::min(100, (int)((2.0 * (smem + 1024) * 100.0) / (228.0 * 1024.0)) + 3);

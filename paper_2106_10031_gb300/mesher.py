@@ -19,6 +19,9 @@ class AMError(RuntimeError):
         self.status = status
 
 
+PRECISIONS = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED, "tensor": nt.AM_PREC_TENSOR}
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -123,7 +126,7 @@ class Mesher:
               max_cells: int = 0, candidates: int = nt.AM_CAND_NEAREST, schedule: int = nt.AM_SCHED_PERSISTENT,
               grid_blocks: int = 0) -> int:
         if isinstance(precision, str):
-            precision = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED}[precision]
+            precision = PRECISIONS[precision]
         if isinstance(schedule, str):
             schedule = {"persistent": nt.AM_SCHED_PERSISTENT, "levels": nt.AM_SCHED_LEVELS}[schedule]
         if isinstance(candidates, str):
@@ -139,6 +142,23 @@ class Mesher:
         out = {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
         out["phase_cycles"] = list(out["phase_cycles"])
         return out
+
+    # ---- compose only
+    def compose(self, net_id: int, keys, precision="fp64"):
+        """Rows of the cells with activation patterns `keys` ((n, ceil(N/64)) uint64): returns
+        (rows (n, N + 1, 4) float64, sign-adjusted neuron rows then a_F; err (n, N + 1))."""
+        import torch
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        N = self.nets[net_id].N
+        dev = torch.device("cuda", self.device)
+        k = torch.as_tensor(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64), device=dev)
+        n = k.shape[0]
+        rows = torch.empty((n, N + 1, 4), dtype=torch.float64, device=dev)
+        err = torch.empty((n, N + 1), dtype=torch.float32, device=dev)
+        self._check(self.lib.am_compose(self.ctx, net_id, C.c_void_p(k.data_ptr()), n, precision,
+                                        C.c_void_p(rows.data_ptr()), C.c_void_p(err.data_ptr())))
+        return rows.cpu().numpy(), err.cpu().numpy()
 
     # ---- learned proposal (device arrays are torch CUDA tensors)
     def proposal_init(self, n_in: int, hidden: int, n_out: int, max_batch: int = 4096, seed: int = 0):

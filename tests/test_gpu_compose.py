@@ -1,0 +1,79 @@
+"""The compose step alone (Lemma 1, Cor. 1, Eq. 10) through am_compose, against the oracle's
+compose, in the three precisions.  FP64 agrees to rounding; the double-float rows lie within
+their rigorous bounds; the tensor-core rows lie within their estimates.  Needs a GPU."""
+import numpy as np
+import pytest
+
+from synth import decoder_net, proposal_target_net, sphere_net, tiny_net
+
+pytestmark = pytest.mark.gpu
+X_RAY = np.array([[1.0, 0.0, 0.0]])
+
+
+def _keys_from_states(S, N):
+    kw = (N + 63) // 64
+    K = np.zeros((len(S), kw), dtype=np.uint64)
+    for i, s in enumerate(S):
+        for k in np.flatnonzero(s):
+            K[i, k >> 6] |= np.uint64(1) << np.uint64(k & 63)
+    return K
+
+
+def _march_states(am, mlp, n, max_neurons, max_width):
+    """Patterns of real cells: the first n cells of a march."""
+    with am.Mesher(max_cells=1 << 16, max_neurons=max_neurons, max_width=max_width) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), X_RAY)
+        m.march(max_cells=n)
+        keys = m.get_mesh(nid).face_keys
+    bits = np.unpackbits(keys.view(np.uint8), axis=1, bitorder="little")[:, :mlp.N]
+    return bits.astype(np.uint8)
+
+
+NETS = [
+    ("tiny", lambda: tiny_net((8, 8), 11), 64, 32),
+    ("sphere64x4", lambda: sphere_net(), 256, 64),
+    ("decoder24x6", lambda: decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05), 256, 32),
+    ("proposal256x8", lambda: proposal_target_net(), 2048, 256),
+    ("decoder512x8", lambda: decoder_net(), 4096, 512),
+]
+
+
+@pytest.mark.parametrize("name,make,max_n,max_w", NETS)
+def test_compose_matches_oracle(oracle_mod, name, make, max_n, max_w):
+    import paper_2106_10031_gb300 as am
+    mlp = make()
+    net = oracle_mod.OracleNet(mlp)
+    rng = np.random.default_rng(3)
+    # random patterns (Lemma 1 holds for every pattern) and patterns of real cells
+    S = np.concatenate([rng.integers(0, 2, (6, mlp.N)).astype(np.uint8),
+                        _march_states(am, mlp, 10, max_n, max_w)[:10]])
+    keys = _keys_from_states(S, mlp.N)
+    ref = []
+    for s in S:
+        A, aF = net.compose(s)
+        sg = (1.0 - 2.0 * s)[:, None]
+        ref.append(np.vstack([sg * A, aF[None, :]]))
+    ref = np.asarray(ref)
+    scale = 1.0 + np.abs(ref).max(axis=2)
+    with am.Mesher(max_cells=1 << 10, max_neurons=max_n, max_width=max_w) as m:
+        nid = m.load_mlp(mlp)
+        r64, _ = m.compose(nid, keys, "fp64")
+        rdf, edf = m.compose(nid, keys, "mixed")
+        rtc, etc = m.compose(nid, keys, "tensor")
+    err64 = np.abs(r64 - ref).max(axis=2) / scale
+    assert err64.max() < 1e-11, err64.max()
+    # double-float: the l1 error of each row's 4 coefficients is within its rigorous bound
+    # (plus the oracle's own FP64 rounding)
+    l1 = np.abs(rdf - ref).sum(axis=2)
+    assert np.all(l1 <= edf + 1e-12 * scale), (l1 - edf).max()
+    # tensor cores: within the estimate on every row
+    l1t = np.abs(rtc - ref).sum(axis=2)
+    ratio = l1t / np.maximum(etc, 1e-30)
+    rel = l1t / np.abs(ref).sum(axis=2).clip(1e-30)
+    deep = ratio[:, mlp.widths[0]:]                  # rows of the tensor-core layers and a_F
+    print(f"\n{name}: fp64 {err64.max():.1e}; mixed max err/bound {(l1 / np.maximum(edf, 1e-30)).max():.2e}; "
+          f"tensor max rel {rel.max():.1e}, layers >= 2: max err/estimate {deep.max():.3f}, "
+          f"p99 {np.quantile(deep, 0.99):.3f}, median {np.median(deep):.4f}; "
+          f"median estimate (rel) {np.median(etc[:, mlp.widths[0]:] / np.abs(ref).sum(axis=2)[:, mlp.widths[0]:].clip(1e-30)):.1e}")
+    assert np.all(l1t <= etc + 1e-12 * scale), ratio.max()
