@@ -41,6 +41,17 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 
 
+def _measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0                              # fallback figure for a GB300
+
+
+BF16_PEAK_TFLOPS = _measured_bf16_peak()
+
+
 # DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
 # workload) from the committed ncu capture, valid while the kernel source is the one captured
 TRAFFIC_CAPTURE = {"sha256_prefix": "8795d1a8059cc349", "precision": "mixed", "candidates": "learned",
@@ -70,6 +81,8 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--compose-only", action="store_true",
+                   help="run only the compose benchmark (am_compose on the decoder) and print its JSON")
     return p.parse_args()
 
 
@@ -358,6 +371,51 @@ def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates=
             "stats": m.stats()}
 
 
+def compose_leg(dev, n_cells=4000, reps=5):
+    """The compose step alone (am_compose) on the decoder-shaped net, (3 + 256) -> [512] x 8 -> 1
+    with skip-concat at layer 4, for the patterns of the first n_cells cells of its march, in the
+    three precisions.  Dense work per cell per §8: 8 n_l n_{l-1} flops over the hidden layers;
+    the tensor path issues 4 m16n8k16 MMAs per 16 x 16 weight tile."""
+    import ctypes as C
+
+    import torch
+
+    import paper_2106_10031_gb300 as am
+    from synth import decoder_net
+    mlp = decoder_net()
+    out = {"workload": f"decoder (3+256)-[512]x8-1, skip at 4; patterns of the first {n_cells} cells"}
+    with am.Mesher(device=dev, max_cells=1 << 16, max_neurons=4096, max_width=512) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]]))
+        m.march(max_cells=n_cells)
+        keys = m.get_mesh(nid).face_keys
+        N, n = mlp.N, keys.shape[0]
+        k = torch.as_tensor(np.ascontiguousarray(keys).view(np.int64), device=f"cuda:{dev}")
+        rows = torch.empty((n, N + 1, 4), dtype=torch.float64, device=f"cuda:{dev}")
+        err = torch.empty((n, N + 1), dtype=torch.float32, device=f"cuda:{dev}")
+        w = mlp.widths
+        dense = n * sum(8 * w[l] * w[l - 1] for l in range(1, mlp.L))
+        issued = n * sum(4 * 2 * 16 * 16 * 8 * ((w[l] + 15) // 16) * ((w[l - 1] + 15) // 16) for l in range(1, mlp.L))
+        for name, code in (("fp64", 0), ("mixed", 1), ("tensor", 2)):
+            ts = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc = m.lib.am_compose(m.ctx, nid, C.c_void_p(k.data_ptr()), n, code, C.c_void_p(rows.data_ptr()),
+                                      C.c_void_p(err.data_ptr()))
+                ts.append(time.perf_counter() - t0)
+                assert rc == 0, m.lib.am_last_error(m.ctx)
+            dt = statistics.median(ts)
+            out[name] = {"cells_per_s": n / dt, "ms": dt * 1e3, "dense_tflops": dense / dt / 1e12}
+        t = out["tensor"]
+        t["issued_tflops"] = issued / (t["ms"] / 1e3) / 1e12
+        t["roofline"] = {"bound": "tensor", "achieved": t["issued_tflops"], "peak": BF16_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": t["issued_tflops"] / BF16_PEAK_TFLOPS,
+                         "peak_source": "measured cuBLAS bf16 burst"}
+        out["tensor_speedup_vs_fp64"] = out["fp64"]["ms"] / t["ms"]
+    return out
+
+
 def train_proposal(m, mlp, o, d):
     """The learned proposal for the workload: trained on the plain method's mesh (full clip,
     FP64) of a nearby checkpoint of the net (every weight moved by N(0, 0.005^2)), outside
@@ -445,6 +503,7 @@ def run_ours(args, dist):
             g["headline_speedup"] = value / g["value"]
             legs[name] = g
         legs["proposal_training"] = train
+        legs["compose"] = compose_leg(dev)
     e2e = None
     if not args.no_e2e:
         prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
@@ -500,6 +559,10 @@ def main():
     try:
         if args.impl == "reference":
             return run_reference(args, dist)
+        if args.compose_only:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "compose", **compose_leg(dist.local)}))
+            return 0
         return run_ours(args, dist)
     finally:
         dist.close()

@@ -64,14 +64,13 @@ typedef enum {
                                  rigorous error bound per row; vertices solved in FP64; every
                                  sign test certified against the bounds (FP32, then FP64 for
                                  close calls); a cell with an undecidable test is redone in FP64 */
-    AM_PREC_TENSOR = 2        /* compose of the hidden layers on the tensor cores: W and Z split
-                                 into three BF16 parts, four mma.sync products per tile
-                                 accumulated in FP32; each row carries an error ESTIMATE (random-
-                                 sign model of the accumulation with a safety factor 8, root-mean-
-                                 square propagation of the previous layers' errors), not a bound; the
-                                 tests, vertices and refinement are those of AM_PREC_MIXED.
-                                 Vertices are accurate to about 1e-6 relative.  Needs
-                                 32 ceil(n_{l-1} / 16) <= max_neurons + 10 for l >= 2. */
+    AM_PREC_TENSOR = 2        /* am_compose only: the hidden layers on the tensor cores, W and Z
+                                 split into three BF16 parts, four mma.sync products per tile
+                                 accumulated in FP32 (about 1e-6 relative); each row carries an
+                                 error ESTIMATE (random-sign model of the accumulation with a
+                                 safety factor 8, root-mean-square propagation), not a bound, so
+                                 am_march refuses it.  Needs 32 ceil(n_{l-1} / 16) <= max_neurons
+                                 + 10 for l >= 2. */
 } am_precision;
 
 typedef enum {
@@ -123,7 +122,7 @@ typedef struct {
     double box;               /* B of the clip box [-B, B]^3 (default 1.5) */
     double delta;             /* vertex tolerance in world units (default 1e-10): a plane within
                                  delta of a vertex counts as satisfied and as a degenerate event */
-    am_precision precision;   /* AM_PREC_FP64 (default), AM_PREC_MIXED or AM_PREC_TENSOR */
+    am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
     int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
     am_candidates candidates; /* AM_CAND_NEAREST (default), AM_CAND_LEARNED or AM_CAND_NONE */
     am_schedule schedule;     /* AM_SCHED_PERSISTENT (default) or AM_SCHED_LEVELS */

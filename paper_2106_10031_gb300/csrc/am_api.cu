@@ -639,13 +639,11 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (o) op = *o;
     if (!(op.box > 0.0)) op.box = 1.5;
     if (!(op.delta > 0.0)) op.delta = 1e-10;
-    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED && op.precision != AM_PREC_TENSOR)
-        return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)op.precision);
     if (op.precision == AM_PREC_TENSOR)
-        for (const NetHost &n : ctx->nets)
-            if (!tc_fits(n.dev.width, n.dev.L, ctx->opts.max_neurons))
-                return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= "
-                            "max_neurons + 10 for every layer");
+        return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR rows carry error estimates, not bounds: the "
+                    "march takes AM_PREC_FP64 or AM_PREC_MIXED (am_compose takes all three)");
+    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)op.precision);
     if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
     if (op.max_cells < 0 || op.grid_blocks < 0) return fail(ctx, AM_ERR_INVALID_ARG, "negative limit");
@@ -660,7 +658,6 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ma.delta = op.delta;
     ma.max_n = ctx->opts.max_neurons;
     ma.max_w = ctx->opts.max_width;
-    ma.tc = op.precision == AM_PREC_TENSOR ? 1 : 0;
     if (op.candidates != AM_CAND_NEAREST && op.candidates != AM_CAND_LEARNED && op.candidates != AM_CAND_NONE)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown candidates mode %d", (int)op.candidates);
     if (op.candidates == AM_CAND_LEARNED && !ctx->prop.w)

@@ -31,7 +31,7 @@ struct MarchArgs {
     long long limit;         // persistent schedule: tickets >= limit are not solved
     int64_t begin, end;      // level schedule: cell ids solved by this launch
     int candidates;          // kCandNearest / kCandLearned / kCandNone
-    int tc;                  // mode 1 only: hidden layers composed on the tensor cores
+    int tc;                  // compose only (mode 1): hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
 };
 int march_smem_bytes(int max_n, int max_w);

@@ -52,7 +52,6 @@ static_assert(kT % 32 == 0 && kNW <= 32 && kNear % kNW == 0, "block shape");
 constexpr int kMaxFix = 8;        // check / fix-up rounds
 constexpr float kU = 5.9604645e-8f;            // 2^-24
 constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
-constexpr float kTcLoose = 3.0e38f;            // the tensor-core path lets each test decide
 constexpr double kVertexTol = 1e-5;            // largest vertex error bound (relative) kept from kDF
 constexpr long long kWaitNs = 4000000000ll;    // 4 s limit on any wait for work
 
@@ -575,7 +574,7 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
                         df_fma(h[c], lo[c], wh, wl, -zh[c], -zl[c]);
                         l1 += fabsf(zh[c]);
                     }
-                    if (tc) {           // this product's rounding (bound) + propagated estimates (rms)
+                    if (tc) {           // this product's rounding (bound) + propagated estimates (rss)
                         eb = __fmaf_ru(fabsf(wh), g * l1 * 1.001f, eb);
                         e2 = fmaf(wh * s.err[rL + k], wh * s.err[rL + k], e2);
                     } else {
@@ -815,7 +814,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     const int N = net.N, NC = N + kBoxPlanes;          // checked rows: neurons + box
     long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
     AM_TICK(tp0);
-    compose<M>(net, s, a.tc != 0, a.max_n + kBoxPlanes + kSquarePlanes);
+    compose<M>(net, s, false, a.max_n + kBoxPlanes + kSquarePlanes);
     AM_TICK(tp1);
 
     // box rows (exact), frame and the initial square (thread 0)
@@ -895,9 +894,8 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         // sums of |W_l| per layer (deep, wide nets).  Go to FP64 at once instead of clipping
         // twice.
         int loose = 0;
-        const float thr = a.tc ? kTcLoose : kDfLoose;
-        for (int k = tid; k < N; k += kT) loose |= s.err[k] * s.rinv[k] > thr;
-        if (tid == 0) loose |= s.eF[0] * rsqrtf((float)(s.aF[0] * s.aF[0] + s.aF[1] * s.aF[1] + s.aF[2] * s.aF[2])) > thr;
+        for (int k = tid; k < N; k += kT) loose |= s.err[k] * s.rinv[k] > kDfLoose;
+        if (tid == 0) loose |= s.eF[0] * rsqrtf((float)(s.aF[0] * s.aF[0] + s.aF[1] * s.aF[1] + s.aF[2] * s.aF[2])) > kDfLoose;
         if (__syncthreads_or(loose)) return CellOut{0, 1};
     } else {
         __syncthreads();
@@ -1169,7 +1167,7 @@ __device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
     for (int w = threadIdx.x; w < 2 * ar.kw; w += kT)       // all key words: pushes copy them
         s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
     __syncthreads();
-    if (MODE == kDF && !net.df_ok && !a.tc) {
+    if (MODE == kDF && !net.df_ok) {
         if (threadIdx.x == 0) s.blk[4] += 1;             // solved in FP64 (the net's bound is too loose)
         solve_cell<kFP64>(a, net, cell, s);
     } else if (MODE == kDF) {

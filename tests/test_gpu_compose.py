@@ -77,3 +77,14 @@ def test_compose_matches_oracle(oracle_mod, name, make, max_n, max_w):
           f"p99 {np.quantile(deep, 0.99):.3f}, median {np.median(deep):.4f}; "
           f"median estimate (rel) {np.median(etc[:, mlp.widths[0]:] / np.abs(ref).sum(axis=2)[:, mlp.widths[0]:].clip(1e-30)):.1e}")
     assert np.all(l1t <= etc + 1e-12 * scale), ratio.max()
+
+
+def test_march_refuses_tensor_rows(am_mod=None):
+    # the march certifies every sign test; estimated rows cannot do that
+    import paper_2106_10031_gb300 as am
+    with am.Mesher(max_cells=1 << 10, max_neurons=64, max_width=32) as m:
+        nid = m.load_mlp(tiny_net((8, 8), 11))
+        m.seed(nid, np.zeros((1, 3)), X_RAY / 1.0)
+        with pytest.raises(am.AMError) as e:
+            m.march(precision="tensor")
+        assert e.value.status == 1               # AM_ERR_INVALID_ARG

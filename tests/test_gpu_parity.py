@@ -18,7 +18,7 @@ def am():
 
 
 MODES = [("fp64", "persistent", 1e-9), ("mixed", "persistent", 1e-5), ("fp64", "levels", 1e-9),
-         ("mixed", "levels", 1e-5), ("tensor", "persistent", 1e-5)]
+         ("mixed", "levels", 1e-5)]
 
 
 def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
