@@ -64,13 +64,21 @@ typedef enum {
                                  rigorous error bound per row; vertices solved in FP64; every
                                  sign test certified against the bounds (FP32, then FP64 for
                                  close calls); a cell with an undecidable test is redone in FP64 */
-    AM_PREC_TENSOR = 2        /* am_compose only: the hidden layers on the tensor cores, W and Z
+    AM_PREC_TENSOR = 2,       /* am_compose only: the hidden layers on the tensor cores, W and Z
                                  split into three BF16 parts, four mma.sync products per tile
                                  accumulated in FP32 (about 1e-6 relative); each row carries an
                                  error ESTIMATE (random-sign model of the accumulation with a
                                  safety factor 8, root-mean-square propagation), not a bound, so
                                  am_march refuses it.  Needs 32 ceil(n_{l-1} / 16) <= max_neurons
                                  + 10 for l >= 2. */
+    AM_PREC_SLICED = 3        /* the hidden layers on the tcgen05 tensor cores as error-free BF16 digit
+                                 products (Ozaki scheme): W_l and each cell's masked Z_{l-1} are split
+                                 into 8 planes of 6-bit integer digits with a power-of-two scale per
+                                 row / column; every plane product and its FP32 accumulation is exact,
+                                 and the diagonals are combined in 64-bit integers, then FP64.  The
+                                 rows are FP64-class (error <= (3 n_{l-1} + 1) 2^-48 times the row
+                                 and column scales, the order of an FP64 dot product's worst case);
+                                 many cells share each weight tile.  Needs n_{l-1} <= 1638. */
 } am_precision;
 
 typedef enum {
@@ -219,9 +227,25 @@ am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
  * the given precision.  d_rows (device, n x (N + 1) x 4 doubles) receives for each key the N
  * sign-adjusted rows (1 - 2 s_k) [a_k | a_k0] of Eq. 10 followed by [a_F | a_F0] (Eq. 8);
  * d_err (device, n x (N + 1) floats, may be NULL) the per-row error bound (AM_PREC_MIXED),
- * estimate (AM_PREC_TENSOR) or 0 (AM_PREC_FP64), as an l1 bound on the 4 coefficients. */
+ * estimate (AM_PREC_TENSOR) or 0 (AM_PREC_FP64, AM_PREC_SLICED), as an l1 bound on the 4
+ * coefficients.  AM_PREC_SLICED composes the patterns in batches (the context allocates its
+ * scratch on first use) and returns AM_ERR_TIMEOUT if a tensor-core pipeline wait gave up. */
 am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, am_precision precision,
                      double *d_rows, float *d_err);
+
+/* ---- launch shapes ---------------------------------------------------------------------
+ * Kernels with more than one valid launch shape read it from the context.  am_set_tuning sets
+ * it by hand; am_autotune_compose times every candidate and keeps the fastest. */
+typedef struct {
+    int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 16 (UMMA N = 64,
+                                 one tile per SM) or 8 (N = 32, two tiles per SM); 0 = default 16 */
+} am_tuning;
+
+/* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */
+am_status am_set_tuning(am_ctx *ctx, const am_tuning *t);
+
+/* The context's current launch shapes. */
+am_status am_get_tuning(const am_ctx *ctx, am_tuning *t);
 
 /* ---- learned constraint proposal --------------------------------------------------------
  * No counterpart in the paper.  A small MLP, x (7 + L) -> H -> H -> n_out, ReLU hidden layers,

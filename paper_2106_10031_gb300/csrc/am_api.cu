@@ -27,6 +27,11 @@ struct NetHost {
     double *blob = nullptr;  // device allocation holding AT, Cl, w_out (FP64)
     float *fblob = nullptr;  // the same as double-float pairs (hi, lo)
     void *tblob = nullptr;   // BF16 hi/lo fragments of W_l and row norms (tensor-core compose)
+    void *ozblob = nullptr;  // BF16 digit planes of W_l and their row exponents (sliced compose)
+    struct alignas(64) MapBytes { unsigned char b[128]; };
+    std::vector<MapBytes> ozmap;     // TMA descriptor over each layer's digit planes (index l)
+    size_t oz_off_eA[kMaxLayers + 1] = {};
+    bool oz_ok = false;      // every hidden fan-in fits the exact accumulation
     int N = 0, max_w = 0;
 };
 
@@ -92,6 +97,8 @@ struct am_ctx {
     std::vector<MeshInfo> mesh;
     bool mesh_valid = false;
     ProposalDev prop;
+    OzScratch oz;                 // sliced tensor-core compose (allocated on first use)
+    int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
 };
 
 namespace {
@@ -152,6 +159,61 @@ am_status status_error(am_ctx *ctx, unsigned long long st)
                                        ctx->ar.maxv);
     if (st & kStVertHash) return fail(ctx, AM_ERR_CAPACITY, "vertex hash table probe limit reached");
     if (st & kStTimeout) return fail(ctx, AM_ERR_TIMEOUT, "a bounded device wait gave up");
+    return AM_OK;
+}
+
+// Scratch of the sliced compose: digit planes of a batch of cells, their column exponents and
+// the pipeline time-out flag; sized for the widest loadable layer.
+am_status ensure_oz_scratch(am_ctx *ctx)
+{
+    if (ctx->oz.B) return AM_OK;
+    OzScratch &z = ctx->oz;
+    z.batch_cells = 4096;
+    CU(cudaMalloc(&z.B, sizeof(__nv_bfloat16) * oz_scratch_elems(z.batch_cells, oz_kp(ctx->opts.max_width))));
+    CU(cudaMalloc(&z.eB, sizeof(int) * 4 * z.batch_cells));
+    CU(cudaMalloc(&z.err, sizeof(int)));
+    CU(cudaMemsetAsync(z.err, 0, sizeof(int), ctx->stream));
+    return AM_OK;
+}
+
+OzNet oz_view(const NetHost &nh)
+{
+    OzNet v;
+    const NetDev &d = nh.dev;
+    v.L = d.L;
+    v.N = d.N;
+    for (int l = 1; l <= d.L; ++l) {
+        v.width[l] = d.width[l];
+        v.row0[l] = d.row0[l];
+        v.Cl[l] = d.Cl[l];
+        if (l >= 2) {
+            v.eA[l] = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(nh.ozblob) + nh.oz_off_eA[l]);
+            v.mapA[l] = nh.ozmap[l].b;
+        }
+    }
+    v.w_out = d.w_out;
+    v.b_out = d.b_out;
+    return v;
+}
+
+// rows (n x (N + 1) x 4) of n cells of one net on the tensor cores; asynchronous on the stream
+am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
+{
+    const NetHost &nh = ctx->nets[net_id];
+    if (!nh.oz_ok)
+        return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED needs every hidden fan-in <= %d", kOzMaxFanIn);
+    am_status s = ensure_oz_scratch(ctx);
+    if (s != AM_OK) return s;
+    const int tile = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
+    CU(oz_compose(oz_view(nh), d_keys, nh.dev.kw, n, d_rows, ctx->oz, tile, ctx->stream));
+    int herr = 0;
+    CU(cudaMemcpyAsync(&herr, ctx->oz.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (herr) {
+        CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
+        return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
+    }
+    ctx->stats.kernel_launches += 2 * (int64_t)nh.dev.L - 1;
     return AM_OK;
 }
 
@@ -259,7 +321,11 @@ void am_destroy(am_ctx *ctx)
         if (n.blob) cudaFree(n.blob);
         if (n.fblob) cudaFree(n.fblob);
         if (n.tblob) cudaFree(n.tblob);
+        if (n.ozblob) cudaFree(n.ozblob);
     }
+    if (ctx->oz.B) cudaFree(ctx->oz.B);
+    if (ctx->oz.eB) cudaFree(ctx->oz.eB);
+    if (ctx->oz.err) cudaFree(ctx->oz.err);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -439,6 +505,37 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         }
         nd.df_ok = rel < 1e-7 ? 1 : 0;
     }
+    {
+        // sliced tensor-core compose: 8 BF16 digit planes of each hidden W_l, row exponents, and
+        // a TMA descriptor per layer; only when every fan-in keeps the accumulation exact
+        nh.oz_ok = true;
+        for (int l = 2; l <= L; ++l) nh.oz_ok = nh.oz_ok && dsc->width[l - 2] <= kOzMaxFanIn;
+        if (nh.oz_ok && L >= 2) {
+            std::vector<std::vector<uint16_t>> planes(L + 1);
+            std::vector<std::vector<int>> eA(L + 1);
+            size_t bytes = 0;
+            std::vector<size_t> offP(L + 1, 0);
+            for (int l = 2; l <= L; ++l) {
+                const int n = dsc->width[l - 1], np = dsc->width[l - 2];
+                const int fan = np + (l == dsc->skip_layer ? in_dim : 0);
+                oz_slice_weights(dsc->W[l - 1], n, np, fan, planes[l], eA[l]);
+                offP[l] = bytes;
+                bytes += planes[l].size() * 2;
+                bytes = (bytes + 255) & ~(size_t)255;
+                nh.oz_off_eA[l] = bytes;
+                bytes += eA[l].size() * 4;
+                bytes = (bytes + 255) & ~(size_t)255;
+            }
+            CU(cudaMalloc(&nh.ozblob, bytes));
+            unsigned char *db = reinterpret_cast<unsigned char *>(nh.ozblob);
+            nh.ozmap.assign(L + 1, NetHost::MapBytes{});
+            for (int l = 2; l <= L; ++l) {
+                CU(cudaMemcpy(db + offP[l], planes[l].data(), planes[l].size() * 2, cudaMemcpyHostToDevice));
+                CU(cudaMemcpy(db + nh.oz_off_eA[l], eA[l].data(), eA[l].size() * 4, cudaMemcpyHostToDevice));
+                CU(oz_encode_weights(nh.ozmap[l].b, db + offP[l], dsc->width[l - 1], dsc->width[l - 2]));
+            }
+        }
+    }
     nh.N = N;
     nh.max_w = mw;
     CU(cudaMemcpyAsync(ctx->d_nets + id, &nd, sizeof(NetDev), cudaMemcpyHostToDevice, ctx->stream));
@@ -471,6 +568,7 @@ am_status am_release_nets(am_ctx *ctx)
         if (n.blob) CU(cudaFree(n.blob));
         if (n.fblob) CU(cudaFree(n.fblob));
         if (n.tblob) CU(cudaFree(n.tblob));
+        if (n.ozblob) CU(cudaFree(n.ozblob));
     }
     ctx->nets.clear();
     ctx->mesh.clear();
@@ -764,9 +862,18 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
     if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
     if (n < 0 || (n > 0 && (!d_keys || !d_rows))) return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
-    if (precision != AM_PREC_FP64 && precision != AM_PREC_MIXED && precision != AM_PREC_TENSOR)
+    if (precision != AM_PREC_FP64 && precision != AM_PREC_MIXED && precision != AM_PREC_TENSOR &&
+        precision != AM_PREC_SLICED)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
     const NetHost &nh = ctx->nets[net_id];
+    if (precision == AM_PREC_SLICED) {
+        if (n == 0) return AM_OK;
+        am_status s = sliced_compose(ctx, net_id, reinterpret_cast<const unsigned long long *>(d_keys), n, d_rows);
+        if (s != AM_OK) return s;
+        if (d_err) CU(cudaMemsetAsync(d_err, 0, sizeof(float) * n * (nh.N + 1), ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        return AM_OK;
+    }
     if (precision == AM_PREC_TENSOR && !tc_fits(nh.dev.width, nh.dev.L, ctx->opts.max_neurons))
         return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= max_neurons + 10");
     if (n == 0) return AM_OK;
@@ -781,6 +888,26 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->stats.kernel_launches += 1;
+    return AM_OK;
+}
+
+am_status am_set_tuning(am_ctx *ctx, const am_tuning *t)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (!t) return fail(ctx, AM_ERR_INVALID_ARG, "null tuning");
+    int nt = 0;
+    const int *tc = oz_tile_cells(&nt);
+    bool ok = t->compose_tile_cells == 0;
+    for (int i = 0; i < nt; ++i) ok = ok || t->compose_tile_cells == tc[i];
+    if (!ok) return fail(ctx, AM_ERR_INVALID_ARG, "unsupported compose_tile_cells %d", t->compose_tile_cells);
+    ctx->oz_tile_cells = t->compose_tile_cells;
+    return AM_OK;
+}
+
+am_status am_get_tuning(const am_ctx *ctx, am_tuning *t)
+{
+    if (!ctx || !t) return AM_ERR_INVALID_ARG;
+    t->compose_tile_cells = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
     return AM_OK;
 }
 

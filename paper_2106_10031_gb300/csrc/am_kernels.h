@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -126,5 +127,35 @@ cudaError_t launch_asm_offsets(const AsmArgs &a, int64_t *scan_tmp, int64_t scan
 void launch_asm_vertices(const AsmArgs &a, cudaStream_t st);
 void launch_asm_lookup(const AsmArgs &a, cudaStream_t st);
 void launch_asm_write(const AsmArgs &a, cudaStream_t st);
+
+// ---- compose on the tcgen05 tensor cores with error-free BF16 digit planes (am_tc.cu)
+constexpr int kOzDigits = 8;          // digit planes per operand (and accumulator diagonals)
+constexpr int kOzBeta = 6;            // bits per digit
+constexpr int kOzMaxFanIn = 1638;     // n_{l-1} * (largest diagonal's digit products) < 2^24
+// one net as the sliced compose reads it (host struct holding device pointers)
+struct OzNet {
+    int L = 0, N = 0;
+    int width[kMaxLayers + 1] = {}, row0[kMaxLayers + 1] = {};
+    const double *Cl[kMaxLayers + 1] = {};
+    const int *eA[kMaxLayers + 1] = {};       // row exponents of W_l (device)
+    const void *mapA[kMaxLayers + 1] = {};    // host CUtensorMap over the digit planes of W_l
+    const double *w_out = nullptr;
+    double b_out = 0.0;
+};
+struct OzScratch {
+    __nv_bfloat16 *B = nullptr;   // kOzDigits x 4 batch_cells x Kp digit planes of the stacked operand
+    int *eB = nullptr;            // 4 batch_cells column exponents
+    int *err = nullptr;           // set to 1 by a kernel whose pipeline wait timed out
+    int64_t batch_cells = 0;      // multiple of 16
+};
+int oz_kp(int width);             // K padded to the 64-element staging chunk
+int oz_mp(int width);             // rows padded to the 128-row tile
+const int *oz_tile_cells(int *n); // the supported cells per CTA (UMMA N = 4 x cells)
+void oz_slice_weights(const double *W, int n, int np, int fan, std::vector<uint16_t> &planes, std::vector<int> &eA);
+cudaError_t oz_encode_weights(void *map, const void *planes, int n, int np);
+int64_t oz_scratch_elems(int64_t batch_cells, int max_kp);
+// rows (n x (N + 1) x 4 FP64, a_F last) of the cells with keys (n x kw words)
+cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, double *rows,
+                       const OzScratch &scr, int tile_cells, cudaStream_t st);
 
 }  // namespace am

@@ -1,0 +1,688 @@
+// am_tc.cu -- the compose step (Lemma 1, Cor. 1) on the tcgen05 tensor cores, with the
+// activation patterns of K cells stacked as the columns of one right operand.
+//
+// Per hidden layer l >= 2 the compose is the product Z_l = W_l diag(s_{l-1}) Z_{l-1} + C_l, and
+// for a batch of cells the right operands diag(s_{l-1}) Z_{l-1} (4 columns per cell) stack into
+// one [n_{l-1} x 4K] matrix: one dense contraction per layer for the whole batch.
+//
+// Error-free slicing (Ozaki, Ogita, Oishi & Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications",
+// Numer. Algorithms 59, 2012).  Every row m of W_l is written as
+//     W_m = 2^eA_m sum_{s=1..8} a_s 2^(-6 s),   integers |a_1| <= 64, |a_s| <= 32 (s >= 2),
+// and every column c of the stacked operand likewise with its own exponent eB_c.  The digits
+// are integers that BF16 holds exactly, so the product of two digit planes is exact, and the
+// tensor core's FP32 accumulator only ever adds integers whose running sum stays below 2^24
+// (n_{l-1} <= 1638), which is exact too.  The products of the planes (s, t) with the same
+// diagonal s + t share one scale and accumulate into one TMEM accumulator (36 plane products
+// over 8 diagonals).  The epilogue combines the diagonals exactly in 64-bit integers and
+// converts once to FP64.  What is dropped are the planes with s + t > 9 and the residuals
+// after 8 digits: per output at most (3 n_{l-1} + 1) 2^-48 2^(eA_m + eB_c), the same order as
+// the worst-case rounding of an FP64 dot product of that length.  So the rows are FP64-class,
+// and the march can clip them with the FP64 path's tests.
+//
+// Kernels (one launch pair per layer and batch):
+//   oz_prep_kernel  : layer-1 rows (cell independent), then, per cell and coordinate, the
+//                     column exponent and the 8 BF16 digit planes of diag(s_l) Z_l for the next
+//                     layer (integer arithmetic on the FP64 bit patterns, no FP64 pipe), or,
+//                     after the last layer, a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Eq. 8);
+//   oz_gemm_kernel  : one CTA per 128 rows of W_l x NC cells.  Warp 0 stages digit-plane tiles
+//                     of W_l and of the stacked operand into shared memory with TMA (128-byte
+//                     swizzle), warp 1 issues tcgen05.mma (M = 128, N = 4 NC, K = 16) into 8
+//                     TMEM accumulators, warps 2..5 read them back with tcgen05.ld, combine,
+//                     add C_l, apply the sign (1 - 2 s_k) of Eq. 10 and write FP64 rows.
+// Every wait on an mbarrier has a time limit; when one runs out the kernel raises a flag the
+// host reads, lets its copies and products in flight finish, frees its TMEM and returns.
+#include <cstdint>
+#include <cstring>
+#include <algorithm>
+#include <cmath>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "am_kernels.h"
+
+namespace am {
+
+namespace {
+
+constexpr int kOzPlanes = kOzDigits;      // digit planes per operand = accumulator diagonals
+constexpr int kOzBK = 64;                 // K elements per staged chunk (128 bytes of BF16)
+constexpr int kOzM = 128;                 // rows of W_l per CTA (UMMA M)
+constexpr int kOzPrepWarps = 8;           // cells per prep block (one warp each)
+constexpr long long kOzWaitNs = 2000000000ll;   // 2 s limit on any pipeline wait
+constexpr long long kOzDrainNs = 200000000ll;   // 0.2 s limit on the drain after an abort
+
+__device__ __forceinline__ unsigned long long oz_now()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete, for at most `limit` ns, or until another
+// role of the CTA has aborted.  On a time-out the CTA aborts and the host sees *err = 1.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *err,
+                                          long long limit = kOzWaitNs)
+{
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = oz_now();
+    while (!mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if ((long long)(oz_now() - t0) > limit) {
+            *abort = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Wait without an abort check (after an abort: let what is in flight finish), at most `limit` ns.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, long long limit)
+{
+    const unsigned long long t0 = oz_now();
+    while (!mbar_test(bar, parity))
+        if ((long long)(oz_now() - t0) > limit) return;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile whose rows are 128 bytes, written by TMA
+// with the 128-byte swizzle: 8-row groups 1024 bytes apart (stride byte offset), descriptor
+// version 1 (the tcgen05 family), layout type 2 = 128-byte swizzle.  The leading byte offset is
+// not used by swizzled K-major layouts; successive K = 16 steps advance the start address by
+// 32 bytes inside the swizzle atom.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 2^e as a double (e in the normal range), else through ldexp
+__device__ __forceinline__ double pow2d(int e)
+{
+    if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(1.0, e);
+}
+
+__device__ __forceinline__ bool key_bit(const unsigned long long *key, int k) { return (key[k >> 6] >> (k & 63)) & 1ull; }
+
+// Exponent e with |x| <= 2^e for every x of a column whose largest |x| has the bit pattern
+// `mx` (sign cleared); 0 for an all-zero column.
+__device__ __forceinline__ int col_exponent(unsigned long long mx)
+{
+    if (mx == 0ull) return 0;
+    const int be = (int)(mx >> 52);
+    if (be == 0) return -1022;                                  // subnormal maximum
+    return be - 1023 + ((mx & 0xFFFFFFFFFFFFFull) != 0ull ? 1 : 0);
+}
+
+// x = z 2^(62 - e) as a 64-bit integer (|z| <= 2^e, so |x| <= 2^62), the bits of z below
+// 2^(e - 62) truncated; integer operations on the bit pattern only.
+__device__ __forceinline__ long long fixed62(double z, int e)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(z);
+    const int be = (int)((u >> 52) & 0x7FF);
+    if (be == 0) return 0;                                      // zero or subnormal: below 2^-1022
+    const long long mant = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int sh = be - 1013 - e;                               // mant 2^(be-1075) * 2^(62-e)
+    long long x;
+    if (sh >= 0) x = mant << sh;                                // sh <= 10 since |z| <= 2^e
+    else if (sh > -64) x = mant >> (-sh);
+    else x = 0;
+    return (u >> 63) ? -x : x;
+}
+
+// BF16 bits of a small integer d (|d| <= 64), exact
+__device__ __forceinline__ unsigned bf16_of_int(int d) { return __float_as_uint((float)d) >> 16; }
+
+// ------------------------------------------------------------------------------------------
+// digit planes of the stacked operand, layer-1 rows, a_F
+
+struct OzPrep {
+    const unsigned long long *keys;   // cell i's key at keys + i * kw
+    int kw;
+    int64_t n;                        // cells in the batch
+    double *rows;                     // cell i's rows at rows + i * rstride (N rows, then a_F)
+    int64_t rstride;
+    int l, L, N;
+    int nl, row0;                     // width and first neuron of layer l
+    const double *Cl1;                // layer-1 constant rows (n_1 x 4), written when l == 1
+    const double *w_out;
+    double b_out;
+    __nv_bfloat16 *B;                 // digit planes: plane t, column c at row t * ncols + c, Kp wide
+    int *eB;                          // column exponents
+    int64_t ncols;
+    int Kp;                           // round_up(n_l, 64)
+};
+
+__global__ void __launch_bounds__(32 * kOzPrepWarps) oz_prep_kernel(OzPrep p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * kOzPrepWarps + (threadIdx.x >> 5);
+    if (i >= p.n) return;
+    const unsigned long long *key = p.keys + i * p.kw;
+    double *out = p.rows + i * p.rstride;
+    if (p.l == 1) {
+        for (int k = lane; k < p.nl; k += 32) {
+            const double2 c0 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k];
+            const double2 c1 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k + 1];
+            const bool act = key_bit(key, k);
+            double2 *o = reinterpret_cast<double2 *>(out + 4 * (int64_t)k);
+            o[0] = act ? make_double2(-c0.x, -c0.y) : c0;
+            o[1] = act ? make_double2(-c1.x, -c1.y) : c1;
+        }
+        __syncwarp();
+    }
+    const double *Z = out + 4 * (int64_t)p.row0;   // sign-adjusted rows of layer l: an active row is -Z_k
+    if (p.l == p.L) {
+        // a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Cor. 1, Eq. 8)
+        double f[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = lane; k < p.nl; k += 32)
+            if (key_bit(key, p.row0 + k)) {
+                const double w = p.w_out[k];
+                const double *r = Z + 4 * (int64_t)k;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) f[j] = fma(-w, r[j], f[j]);
+            }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            for (int o = 16; o > 0; o >>= 1) f[j] += __shfl_xor_sync(0xffffffffu, f[j], o);
+        if (lane == 0) {
+            double *aF = out + 4 * (int64_t)p.N;
+            aF[0] = f[0]; aF[1] = f[1]; aF[2] = f[2]; aF[3] = f[3] + p.b_out;
+        }
+        return;
+    }
+    // column maxima of |diag(s_l) Z_l| (bit patterns of non-negative doubles order as integers)
+    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int k = lane; k < p.nl; k += 32)
+        if (key_bit(key, p.row0 + k)) {
+            const long long *r = reinterpret_cast<const long long *>(Z + 4 * (int64_t)k);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long a = (unsigned long long)r[j] & 0x7FFFFFFFFFFFFFFFull;
+                mx[j] = a > mx[j] ? a : mx[j];
+            }
+        }
+    int e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx[j], o);
+            mx[j] = v > mx[j] ? v : mx[j];
+        }
+        e[j] = col_exponent(mx[j]);
+    }
+    if (lane < 4) p.eB[4 * i + lane] = e[lane];
+    // digits: two consecutive k per lane, so each plane store is a BF16 pair
+    for (int k0 = 2 * lane; k0 < p.Kp; k0 += 64) {
+        unsigned dig[4][kOzPlanes];          // per column, per plane: bits of the pair
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int t = 0; t < kOzPlanes; ++t) dig[j][t] = 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = k0 + h;
+            if (k >= p.nl || !key_bit(key, p.row0 + k)) continue;
+            const double *r = Z + 4 * (int64_t)k;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                long long x = fixed62(-r[j], e[j]);       // active: z = -row
+#pragma unroll
+                for (int t = 0; t < kOzPlanes; ++t) {
+                    const int sh = 56 - 6 * t;
+                    const long long d = (x + (1ll << (sh - 1))) >> sh;   // nearest digit
+                    x -= d << sh;
+                    dig[j][t] |= bf16_of_int((int)d) << (16 * h);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int t = 0; t < kOzPlanes; ++t) {
+                const int64_t row = (int64_t)t * p.ncols + 4 * i + j;
+                *reinterpret_cast<unsigned *>(p.B + row * p.Kp + k0) = dig[j][t];
+            }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// the layer product on the tensor cores
+
+struct OzGemm {
+    const int *eA;                    // row exponents of W_l (n_l)
+    const int *eB;                    // column exponents of the stacked operand
+    const double *Cl;                 // n_l x 4 layer constant
+    const unsigned long long *keys;
+    int kw;
+    int64_t n;                        // cells in the batch
+    double *rows;
+    int64_t rstride;
+    int row0, nl, KC;                 // first neuron, width of layer l, K chunks (Kp / 64)
+    int64_t ncols;                    // column stride between digit planes of B
+    int Mp;                           // row stride between digit planes of W_l
+    int *err;
+};
+
+template <int NC, int AST>
+struct OzShape {
+    static constexpr int kNCol = 4 * NC;                       // UMMA N
+    static constexpr int kATile = kOzM * 128;                  // bytes of one A stage
+    static constexpr int kBPlane = kNCol * 128;                // bytes of one B digit-plane tile
+    static constexpr int kBStage = kOzPlanes * kBPlane;
+    static constexpr int kTmemCols = kOzPlanes * kNCol;        // 8 diagonals
+    static constexpr int kBars = 2 * AST + 2 * 2 + 2;
+    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 1024;
+    static_assert(kTmemCols == 256 || kTmemCols == 512, "TMEM allocation must be a power of two");
+    static_assert(kBPlane % 1024 == 0, "B plane tiles must stay 1024-byte aligned");
+};
+
+template <int NC, int AST>
+__global__ void __launch_bounds__(192, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzGemm g)
+{
+    using S = OzShape<NC, AST>;
+    extern __shared__ unsigned char oz_smem_raw[];
+    const uint32_t raw = smem_u32(oz_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = oz_smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + AST * S::kATile;
+    const uint32_t bars = sB + 2 * S::kBStage;
+    auto afull = [&](int q) { return bars + 8 * q; };
+    auto aempty = [&](int q) { return bars + 8 * (AST + q); };
+    auto bfull = [&](int q) { return bars + 8 * (2 * AST + q); };
+    auto bempty = [&](int q) { return bars + 8 * (2 * AST + 2 + q); };
+    const uint32_t accfull = bars + 8 * (2 * AST + 4), drain = bars + 8 * (2 * AST + 5);
+    unsigned char *tail = gbase + (bars - base) + 8 * S::kBars;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tail);
+    volatile int *abort = reinterpret_cast<volatile int *>(tail + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kOzM;
+    const int64_t col0 = (int64_t)blockIdx.y * S::kNCol;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < AST; ++q) { mbar_init(afull(q), 1); mbar_init(aempty(q), 1); }
+        for (int q = 0; q < 2; ++q) { mbar_init(bfull(q), 1); mbar_init(bempty(q), 1); }
+        mbar_init(accfull, 1);
+        mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(S::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: per K chunk the 8 digit planes of the stacked operand, then the 8
+        //      digit planes of W_l one at a time
+        if (lane == 0) {
+            int armedA[AST], armedB[2];
+            for (int q = 0; q < AST; ++q) armedA[q] = 0;
+            armedB[0] = armedB[1] = 0;
+            int ai = 0;
+            bool ok = true;
+            for (int kc = 0; kc < g.KC && ok; ++kc) {
+                const int bs = kc & 1;
+                if (kc >= 2 && !mbar_wait(bempty(bs), ((kc >> 1) - 1) & 1, abort, g.err)) { ok = false; break; }
+                mbar_expect_tx(bfull(bs), S::kBStage);
+                ++armedB[bs];
+                for (int t = 0; t < kOzPlanes; ++t)
+                    tma_load_2d(sB + bs * S::kBStage + t * S::kBPlane, &tmB, kc * kOzBK,
+                                (int)((int64_t)t * g.ncols + col0), bfull(bs));
+                for (int s = 0; s < kOzPlanes; ++s, ++ai) {
+                    const int q = ai % AST;
+                    if (ai >= AST && !mbar_wait(aempty(q), ((ai / AST) - 1) & 1, abort, g.err)) { ok = false; break; }
+                    mbar_expect_tx(afull(q), S::kATile);
+                    ++armedA[q];
+                    tma_load_2d(sA + q * S::kATile, &tmA, kc * kOzBK, s * g.Mp + m0, afull(q));
+                }
+            }
+            if (!ok) {
+                // let every copy already issued land before the CTA's shared memory goes away
+                for (int q = 0; q < AST; ++q)
+                    if (armedA[q]) mbar_drain(afull(q), (armedA[q] - 1) & 1, kOzDrainNs);
+                for (int q = 0; q < 2; ++q)
+                    if (armedB[q]) mbar_drain(bfull(q), (armedB[q] - 1) & 1, kOzDrainNs);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer: plane s of W_l times planes t = 0..7-s of the operand, into the
+        //      accumulator of diagonal s + t
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma_idesc_bf16(kOzM, S::kNCol);
+            int ai = 0;
+            bool ok = true;
+            for (int kc = 0; kc < g.KC && ok; ++kc) {
+                const int bs = kc & 1;
+                if (!mbar_wait(bfull(bs), (kc >> 1) & 1, abort, g.err)) { ok = false; break; }
+                for (int s = 0; s < kOzPlanes; ++s, ++ai) {
+                    const int q = ai % AST;
+                    if (!mbar_wait(afull(q), (ai / AST) & 1, abort, g.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = sA + q * S::kATile;
+                    for (int t = 0; t + s < kOzPlanes; ++t) {
+                        const uint32_t b0 = sB + bs * S::kBStage + t * S::kBPlane;
+                        const uint32_t d = tmem + (uint32_t)((s + t) * S::kNCol);
+#pragma unroll
+                        for (int kk = 0; kk < kOzBK / 16; ++kk)
+                            umma_bf16(d, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
+                                      (kc | s | kk) != 0 ? 1u : 0u);
+                    }
+                    umma_commit(aempty(q));          // the A stage is free once these products finish
+                }
+                if (ok) umma_commit(bempty(bs));
+            }
+            if (ok) {
+                umma_commit(accfull);
+            } else {
+                umma_commit(drain);                  // every product issued so far has finished
+                mbar_drain(drain, 0, kOzDrainNs);
+            }
+        }
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row of W_l per thread
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;
+        const int grow = m0 + r;
+        const bool live_row = grow < g.nl;
+        if (mbar_wait(accfull, 0, abort, g.err)) {
+            tc_fence_after();
+            double2 C01 = make_double2(0.0, 0.0), C23 = make_double2(0.0, 0.0);
+            int eA = 0;
+            if (live_row) {
+                C01 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow];
+                C23 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow + 1];
+                eA = g.eA[grow];
+            }
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int c4 = 0; c4 < NC; c4 += 4) {
+                long long acc[16];
+                float v[16];
+                tmem_ld16(trow + (uint32_t)(4 * c4), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = (long long)__float2int_rn(v[j]);
+#pragma unroll 1
+                for (int dgl = 1; dgl < kOzPlanes - 1; ++dgl) {
+                    tmem_ld16(trow + (uint32_t)(dgl * S::kNCol + 4 * c4), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[j] = (acc[j] << 6) + (long long)__float2int_rn(v[j]);
+                }
+                tmem_ld16(trow + (uint32_t)((kOzPlanes - 1) * S::kNCol + 4 * c4), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] += (long long)((__float2int_rn(v[j]) + 32) >> 6);
+                // acc 2^(eA + eB - 48) + C_l, signed by the neuron's state
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int64_t cell = col0 / 4 + c4 + cc;
+                    if (!live_row || cell >= g.n) continue;
+                    const int4 eB = reinterpret_cast<const int4 *>(g.eB)[cell];
+                    const bool act = key_bit(g.keys + cell * g.kw, g.row0 + grow);
+                    const double x = fma((double)acc[4 * cc + 0], pow2d(eA + eB.x - 48), C01.x);
+                    const double y = fma((double)acc[4 * cc + 1], pow2d(eA + eB.y - 48), C01.y);
+                    const double z = fma((double)acc[4 * cc + 2], pow2d(eA + eB.z - 48), C23.x);
+                    const double w = fma((double)acc[4 * cc + 3], pow2d(eA + eB.w - 48), C23.y);
+                    double2 *o = reinterpret_cast<double2 *>(g.rows + cell * g.rstride + 4 * (int64_t)(g.row0 + grow));
+                    o[0] = act ? make_double2(-x, -y) : make_double2(x, y);
+                    o[1] = act ? make_double2(-z, -w) : make_double2(z, w);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t get_encode()
+{
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q{};
+    void *fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+// 2-D BF16 tensor of `rows` rows of Kp elements, boxes of 64 x box_rows with the 128-byte swizzle
+cudaError_t encode_map(CUtensorMap *m, const void *ptr, int64_t Kp, int64_t rows, int box_rows)
+{
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int NC, int AST>
+cudaError_t launch_gemm(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzGemm &g, int Mp, int64_t ncols_used,
+                        cudaStream_t st)
+{
+    using S = OzShape<NC, AST>;
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NC, AST>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(Mp / kOzM, (unsigned)((ncols_used + S::kNCol - 1) / S::kNCol));
+    oz_gemm_kernel<NC, AST><<<grid, 192, S::kSmem, st>>>(tmA, tmB, g);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int oz_kp(int width) { return (width + kOzBK - 1) / kOzBK * kOzBK; }
+int oz_mp(int width) { return (width + kOzM - 1) / kOzM * kOzM; }
+
+const int *oz_tile_cells(int *n)
+{
+    static const int cells[] = {16, 8};
+    *n = 2;
+    return cells;
+}
+
+// Digit planes of the hidden part of W_l (n rows, np columns, row stride fan): plane s row m at
+// (s Mp + m) Kp, zero padded; the row exponents eA (n values).  Host arithmetic, exact.
+void oz_slice_weights(const double *W, int n, int np, int fan, std::vector<uint16_t> &planes, std::vector<int> &eA)
+{
+    const int Kp = oz_kp(np), Mp = oz_mp(n);
+    planes.assign((size_t)kOzPlanes * Mp * Kp, 0);
+    eA.assign(n, 0);
+    for (int m = 0; m < n; ++m) {
+        double mx = 0.0;
+        for (int k = 0; k < np; ++k) mx = std::max(mx, std::fabs(W[(size_t)m * fan + k]));
+        int e = 0;
+        if (mx > 0.0) {
+            int ex;
+            const double fr = std::frexp(mx, &ex);       // mx = fr 2^ex, fr in [0.5, 1)
+            e = fr == 0.5 ? ex - 1 : ex;                 // smallest e with mx <= 2^e
+        }
+        eA[m] = e;
+        for (int k = 0; k < np; ++k) {
+            double x = std::ldexp(W[(size_t)m * fan + k], -e);   // |x| <= 1, exact
+            for (int s = 0; s < kOzPlanes; ++s) {
+                const double t = std::ldexp(x, kOzBeta);
+                const double d = std::nearbyint(t);              // |d| <= 64 (s = 0), <= 32 after
+                x = t - d;                                       // exact, |x| <= 1/2
+                float f = (float)d;
+                uint32_t u;
+                std::memcpy(&u, &f, 4);
+                planes[((size_t)s * Mp + m) * Kp + k] = (uint16_t)(u >> 16);
+            }
+        }
+    }
+}
+
+cudaError_t oz_encode_weights(void *map, const void *planes, int n, int np)
+{
+    return encode_map(reinterpret_cast<CUtensorMap *>(map), planes, oz_kp(np), (int64_t)kOzPlanes * oz_mp(n), kOzM);
+}
+
+int64_t oz_scratch_elems(int64_t batch_cells, int max_kp)
+{
+    return (int64_t)kOzPlanes * 4 * batch_cells * max_kp;
+}
+
+cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, double *rows,
+                       const OzScratch &scr, int tile_cells, cudaStream_t st)
+{
+    const int64_t rstride = 4 * (int64_t)(net.N + 1);
+    const int64_t ncols = 4 * scr.batch_cells;
+    for (int64_t b0 = 0; b0 < n; b0 += scr.batch_cells) {
+        const int64_t nb = std::min<int64_t>(scr.batch_cells, n - b0);
+        OzPrep p{};
+        p.keys = keys + b0 * kw;
+        p.kw = kw;
+        p.n = nb;
+        p.rows = rows + b0 * rstride;
+        p.rstride = rstride;
+        p.L = net.L;
+        p.N = net.N;
+        p.Cl1 = net.Cl[1];
+        p.w_out = net.w_out;
+        p.b_out = net.b_out;
+        p.B = scr.B;
+        p.eB = scr.eB;
+        p.ncols = ncols;
+        const unsigned pgrid = (unsigned)((nb + kOzPrepWarps - 1) / kOzPrepWarps);
+        for (int l = 1; l <= net.L; ++l) {
+            if (l >= 2) {
+                CUtensorMap tmB;
+                const int Kp = oz_kp(net.width[l - 1]);
+                cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tile_cells);
+                if (e != cudaSuccess) return e;
+                OzGemm g{};
+                g.eA = net.eA[l];
+                g.eB = scr.eB;
+                g.Cl = net.Cl[l];
+                g.keys = p.keys;
+                g.kw = kw;
+                g.n = nb;
+                g.rows = p.rows;
+                g.rstride = rstride;
+                g.row0 = net.row0[l];
+                g.nl = net.width[l];
+                g.KC = Kp / kOzBK;
+                g.ncols = ncols;
+                g.Mp = oz_mp(net.width[l]);
+                g.err = scr.err;
+                const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
+                e = tile_cells == 8 ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, st)
+                                    : launch_gemm<16, 4>(tmA, tmB, g, g.Mp, 4 * nb, st);
+                if (e != cudaSuccess) return e;
+            }
+            p.l = l;
+            p.nl = net.width[l];
+            p.row0 = net.row0[l];
+            p.Kp = oz_kp(net.width[l]);
+            oz_prep_kernel<<<pgrid, 32 * kOzPrepWarps, 0, st>>>(p);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace am

@@ -19,7 +19,8 @@ class AMError(RuntimeError):
         self.status = status
 
 
-PRECISIONS = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED, "tensor": nt.AM_PREC_TENSOR}
+PRECISIONS = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED, "tensor": nt.AM_PREC_TENSOR,
+              "sliced": nt.AM_PREC_SLICED}
 
 
 def _dp(a: np.ndarray):
@@ -142,6 +143,16 @@ class Mesher:
         out = {k: getattr(s, k) for k, _ in nt.am_stats_t._fields_}
         out["phase_cycles"] = list(out["phase_cycles"])
         return out
+
+    # ---- launch shapes
+    def set_tuning(self, compose_tile_cells: int = 0):
+        t = nt.am_tuning(compose_tile_cells=compose_tile_cells)
+        self._check(self.lib.am_set_tuning(self.ctx, C.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = nt.am_tuning()
+        self._check(self.lib.am_get_tuning(self.ctx, C.byref(t)))
+        return {k: getattr(t, k) for k, _ in nt.am_tuning._fields_}
 
     # ---- compose only
     def compose(self, net_id: int, keys, precision="fp64"):

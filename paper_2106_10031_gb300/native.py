@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "AM_OK", 1: "AM_ERR_INVALID_ARG", 2: "AM_ERR_CUDA", 3: "AM_ER
 AM_PREC_FP64 = 0
 AM_PREC_MIXED = 1
 AM_PREC_TENSOR = 2
+AM_PREC_SLICED = 3
 AM_SCHED_PERSISTENT = 0
 AM_SCHED_LEVELS = 1
 AM_CAND_NEAREST = 0
@@ -53,6 +54,10 @@ class am_march_opts(C.Structure):
     _fields_ = [("box", C.c_double), ("delta", C.c_double), ("precision", C.c_int),
                 ("max_cells", C.c_int64), ("candidates", C.c_int), ("schedule", C.c_int),
                 ("grid_blocks", C.c_int)]
+
+
+class am_tuning(C.Structure):
+    _fields_ = [("compose_tile_cells", C.c_int)]
 
 
 class am_stats_t(C.Structure):
@@ -86,6 +91,8 @@ ENTRY_POINTS = [
     ("am_get_mesh", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_get_stats", C.c_int, [C.c_void_p, C.POINTER(am_stats_t)]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    ("am_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("am_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("am_proposal_samples", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("am_proposal_init", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
     ("am_proposal_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),

@@ -1,6 +1,7 @@
 """The compose step alone (Lemma 1, Cor. 1, Eq. 10) through am_compose, against the oracle's
-compose, in the three precisions.  FP64 agrees to rounding; the double-float rows lie within
-their rigorous bounds; the tensor-core rows lie within their estimates.  Needs a GPU."""
+compose, in the four precisions.  FP64 agrees to rounding; the double-float rows lie within
+their rigorous bounds; the split-BF16 tensor-core rows lie within their estimates; the sliced
+tensor-core rows (error-free digit products) agree to FP64-class rounding.  Needs a GPU."""
 import numpy as np
 import pytest
 
@@ -61,8 +62,15 @@ def test_compose_matches_oracle(oracle_mod, name, make, max_n, max_w):
         r64, _ = m.compose(nid, keys, "fp64")
         rdf, edf = m.compose(nid, keys, "mixed")
         rtc, etc = m.compose(nid, keys, "tensor")
+        rsl, esl = m.compose(nid, keys, "sliced")
     err64 = np.abs(r64 - ref).max(axis=2) / scale
     assert err64.max() < 1e-11, err64.max()
+    # sliced: every digit product and its FP32 accumulation is exact, so only the digits beyond
+    # the eighth plane are lost, about 2^-48 of the row and column scales per term
+    errsl = np.abs(rsl - ref).max(axis=2) / scale
+    print(f"\n{name}: sliced max err {errsl.max():.2e} (fp64 {err64.max():.2e})")
+    assert errsl.max() < 1e-11, errsl.max()
+    assert np.all(esl == 0.0)
     # double-float: the l1 error of each row's 4 coefficients is within its rigorous bound
     # (plus the oracle's own FP64 rounding)
     l1 = np.abs(rdf - ref).sum(axis=2)
@@ -88,3 +96,31 @@ def test_march_refuses_tensor_rows(am_mod=None):
         with pytest.raises(am.AMError) as e:
             m.march(precision="tensor")
         assert e.value.status == 1               # AM_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("tile_cells", [16, 8])
+def test_sliced_compose_batches_and_ragged_shapes(oracle_mod, tile_cells):
+    # widths that fill no tile exactly, a skip layer with a latent, and more patterns than one
+    # batch of the sliced compose (4096 cells): ragged rows, columns, K chunks and batches
+    import paper_2106_10031_gb300 as am
+    mlp = decoder_net(width=72, depth=5, latent_dim=5, skip_layer=3, seed=17, sigma=0.05)
+    net = oracle_mod.OracleNet(mlp)
+    rng = np.random.default_rng(5)
+    n = 4096 + 37
+    S = rng.integers(0, 2, (n, mlp.N)).astype(np.uint8)
+    S[:3] = 0                                            # all neurons off: Z_l = C_l
+    S[3:6] = 1                                           # all on
+    keys = _keys_from_states(S, mlp.N)
+    with am.Mesher(max_cells=1 << 10, max_neurons=512, max_width=128) as m:
+        nid = m.load_mlp(mlp)
+        m.set_tuning(compose_tile_cells=tile_cells)
+        rsl, _ = m.compose(nid, keys, "sliced")
+    worst = 0.0
+    for i in list(range(8)) + list(rng.choice(n, 120, replace=False)) + list(range(n - 8, n)):
+        A, aF = net.compose(S[i])
+        sg = (1.0 - 2.0 * S[i])[:, None]
+        ref = np.vstack([sg * A, aF[None, :]])
+        err = np.abs(rsl[i] - ref).max(axis=1) / (1.0 + np.abs(ref).max(axis=1))
+        worst = max(worst, err.max())
+    print(f"\nsliced, {tile_cells} cells per tile: max err {worst:.2e} over 136 of {n} patterns")
+    assert worst < 1e-11
