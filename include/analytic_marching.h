@@ -130,7 +130,9 @@ typedef struct {
     double box;               /* B of the clip box [-B, B]^3 (default 1.5) */
     double delta;             /* vertex tolerance in world units (default 1e-10): a plane within
                                  delta of a vertex counts as satisfied and as a degenerate event */
-    am_precision precision;   /* AM_PREC_FP64 (default) or AM_PREC_MIXED */
+    am_precision precision;   /* AM_PREC_FP64 (default), AM_PREC_MIXED or AM_PREC_SLICED (one net per
+                                 context; level schedule: per batch of a level's cells the rows are
+                                 composed on the tensor cores into device memory, then clipped in FP64) */
     int64_t max_cells;        /* stop after this many cells have been solved (0 = no limit) */
     am_candidates candidates; /* AM_CAND_NEAREST (default), AM_CAND_LEARNED or AM_CAND_NONE */
     am_schedule schedule;     /* AM_SCHED_PERSISTENT (default) or AM_SCHED_LEVELS */

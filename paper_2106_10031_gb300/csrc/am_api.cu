@@ -99,6 +99,8 @@ struct am_ctx {
     ProposalDev prop;
     OzScratch oz;                 // sliced tensor-core compose (allocated on first use)
     int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
+    double *oz_rows = nullptr;    // march with AM_PREC_SLICED: rows of one batch of cells
+    int64_t oz_rows_cap = 0;      // doubles
 };
 
 namespace {
@@ -196,8 +198,8 @@ OzNet oz_view(const NetHost &nh)
     return v;
 }
 
-// rows (n x (N + 1) x 4) of n cells of one net on the tensor cores; asynchronous on the stream
-am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
+// rows (n x (N + 1) x 4) of n cells of one net on the tensor cores, asynchronous on the stream
+am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
 {
     const NetHost &nh = ctx->nets[net_id];
     if (!nh.oz_ok)
@@ -206,6 +208,14 @@ am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_ke
     if (s != AM_OK) return s;
     const int tile = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
     CU(oz_compose(oz_view(nh), d_keys, nh.dev.kw, n, d_rows, ctx->oz, tile, ctx->stream));
+    const int64_t batches = (n + ctx->oz.batch_cells - 1) / ctx->oz.batch_cells;
+    ctx->stats.kernel_launches += (2 * (int64_t)nh.dev.L - 1) * batches;
+    return AM_OK;
+}
+
+// AM_ERR_TIMEOUT if a tensor-core pipeline wait gave up since the last check (synchronises)
+am_status sliced_check(am_ctx *ctx)
+{
     int herr = 0;
     CU(cudaMemcpyAsync(&herr, ctx->oz.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -213,8 +223,13 @@ am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_ke
         CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
         return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
     }
-    ctx->stats.kernel_launches += 2 * (int64_t)nh.dev.L - 1;
     return AM_OK;
+}
+
+am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
+{
+    am_status s = sliced_compose_async(ctx, net_id, d_keys, n, d_rows);
+    return s != AM_OK ? s : sliced_check(ctx);
 }
 
 }  // namespace
@@ -326,6 +341,7 @@ void am_destroy(am_ctx *ctx)
     if (ctx->oz.B) cudaFree(ctx->oz.B);
     if (ctx->oz.eB) cudaFree(ctx->oz.eB);
     if (ctx->oz.err) cudaFree(ctx->oz.err);
+    if (ctx->oz_rows) cudaFree(ctx->oz_rows);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -739,13 +755,33 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (!(op.delta > 0.0)) op.delta = 1e-10;
     if (op.precision == AM_PREC_TENSOR)
         return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR rows carry error estimates, not bounds: the "
-                    "march takes AM_PREC_FP64 or AM_PREC_MIXED (am_compose takes all three)");
-    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED)
+                    "march takes AM_PREC_FP64, AM_PREC_MIXED or AM_PREC_SLICED (am_compose takes all four)");
+    if (op.precision != AM_PREC_FP64 && op.precision != AM_PREC_MIXED && op.precision != AM_PREC_SLICED)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown precision %d", (int)op.precision);
+    const bool sliced = op.precision == AM_PREC_SLICED;
+    if (sliced) {
+        // the tensor-core compose runs per net over a batch of cells: one net per march
+        if (ctx->nets.size() != 1)
+            return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED marches one net (context holds %d)",
+                        (int)ctx->nets.size());
+        if (!ctx->nets[0].oz_ok)
+            return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED needs every hidden fan-in <= %d", kOzMaxFanIn);
+        op.schedule = AM_SCHED_LEVELS;
+        am_status se = ensure_oz_scratch(ctx);
+        if (se != AM_OK) return se;
+        const int64_t need = ctx->oz.batch_cells * 4 * (int64_t)(ctx->nets[0].N + 1);
+        if (ctx->oz_rows_cap < need) {
+            if (ctx->oz_rows) CU(cudaFree(ctx->oz_rows));
+            ctx->oz_rows = nullptr;
+            ctx->oz_rows_cap = 0;
+            CU(cudaMalloc(&ctx->oz_rows, sizeof(double) * need));
+            ctx->oz_rows_cap = need;
+        }
+    }
     if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
     if (op.max_cells < 0 || op.grid_blocks < 0) return fail(ctx, AM_ERR_INVALID_ARG, "negative limit");
-    const int mode = op.precision == AM_PREC_FP64 ? 0 : 1;
+    const int mode = op.precision == AM_PREC_MIXED ? 1 : 0;   // kDF only for the double-float path
     unsigned long long hc[kNumCounters];
     am_status s = sync_status(ctx, hc);
     if (s != AM_OK) return s;
@@ -807,17 +843,34 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         while (f0 < f1) {
             if (f0 >= limit) { incomplete = true; break; }
             f1 = std::min<int64_t>(f1, limit);
-            ma.begin = f0;
-            ma.end = f1;
             CU(cudaEventRecord(ctx->evk0, ctx->stream));
-            launch_march(ma, mode, false, (int)std::min<int64_t>(f1 - f0, 1 << 20), ctx->stream);
-            CU(cudaGetLastError());
+            if (sliced) {
+                // per batch of the level: the rows on the tensor cores, then the FP64 clip and march
+                for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells) {
+                    const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
+                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, c1 - c0, ctx->oz_rows);
+                    if (s != AM_OK) return s;
+                    ma.begin = c0;
+                    ma.end = c1;
+                    ma.rows_in = ctx->oz_rows;
+                    launch_march(ma, 0, false, (int)(c1 - c0), ctx->stream);
+                    CU(cudaGetLastError());
+                    ctx->stats.cell_launches += 1;
+                    ctx->stats.kernel_launches += 1;
+                }
+            } else {
+                ma.begin = f0;
+                ma.end = f1;
+                launch_march(ma, mode, false, (int)std::min<int64_t>(f1 - f0, 1 << 20), ctx->stream);
+                CU(cudaGetLastError());
+                ctx->stats.cell_launches += 1;
+                ctx->stats.kernel_launches += 1;
+            }
             CU(cudaEventRecord(ctx->evk1, ctx->stream));
             ctx->stats.levels += 1;
-            ctx->stats.cell_launches += 1;
-            ctx->stats.kernel_launches += 1;
             s = sync_status(ctx, hc);
             if (s != AM_OK) return s;
+            if (sliced && (s = sliced_check(ctx)) != AM_OK) return s;
             float kms = 0.f;
             CU(cudaEventElapsedTime(&kms, ctx->evk0, ctx->evk1));
             ctx->stats.ms_cell_kernels += kms;

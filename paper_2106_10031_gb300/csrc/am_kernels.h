@@ -34,6 +34,8 @@ struct MarchArgs {
     int candidates;          // kCandNearest / kCandLearned / kCandNone
     int tc;                  // compose only (mode 1): hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
+    const double *rows_in;   // level schedule, FP64 mode: rows (n x (N + 1) x 4, a_F last) of cells
+                             // [begin, end) composed beforehand (sliced tensor-core compose)
 };
 int march_smem_bytes(int max_n, int max_w);
 int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate

@@ -814,7 +814,17 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     const int N = net.N, NC = N + kBoxPlanes;          // checked rows: neurons + box
     long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
     AM_TICK(tp0);
-    compose<M>(net, s, false, a.max_n + kBoxPlanes + kSquarePlanes);
+    if (M == kFP64 && a.rows_in) {
+        // rows composed beforehand on the tensor cores (same layout and signs as compose<kFP64>)
+        const double2 *src = reinterpret_cast<const double2 *>(a.rows_in + (cell - a.begin) * (int64_t)(N + 1) * 4);
+        double2 *dst = reinterpret_cast<double2 *>(s.r64);
+        for (int i = tid; i < 2 * N; i += kT) dst[i] = __ldcs(src + i);
+        if (tid < 4) s.aF[tid] = __ldcs(reinterpret_cast<const double *>(src) + 4 * N + tid);
+        if (tid == 0) s.eF[0] = 0.0f;
+        __syncthreads();
+    } else {
+        compose<M>(net, s, false, a.max_n + kBoxPlanes + kSquarePlanes);
+    }
     AM_TICK(tp1);
 
     // box rows (exact), frame and the initial square (thread 0)

@@ -17,8 +17,10 @@ def am():
     return am_mod
 
 
+# sliced: the compose on the tensor cores as exact digit-plane products (FP64-class rows), the
+# clip in FP64; it always runs the level schedule
 MODES = [("fp64", "persistent", 1e-9), ("mixed", "persistent", 1e-5), ("fp64", "levels", 1e-9),
-         ("mixed", "levels", 1e-5)]
+         ("mixed", "levels", 1e-5), ("sliced", "levels", 1e-9)]
 
 
 def _both(oracle_mod, am, mlp, dirs, R=2.0, **kw):
@@ -135,3 +137,14 @@ def test_seed_matches_oracle(oracle_mod, am):
             mesh = m.get_mesh(nid)
         assert mesh.n_faces == 1
         assert parity._key_int(mesh.face_keys[0]) == ref.seeds[0][0]
+
+
+def test_sliced_march_needs_one_net(am):
+    # the tensor-core compose works on batches of one net's cells
+    with am.Mesher(max_cells=1 << 12, max_neurons=256, max_width=64) as m:
+        for n in (sphere_net(seed=21, width=32, depth=4, sigma=0.05), tiny_net((8, 8), 11)):
+            i = m.load_mlp(n)
+            m.seed(i, np.zeros((1, 3)), RAY)
+        with pytest.raises(am.AMError) as e:
+            m.march(precision="sliced")
+        assert e.value.status == 1           # AM_ERR_INVALID_ARG

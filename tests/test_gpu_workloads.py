@@ -43,7 +43,7 @@ def test_batch_of_nets_in_one_march(oracle_mod, precision):
             parity.compare_sampled(oracle_mod, net, mesh, nt.N, 8, 1e-9 if precision == "fp64" else 1e-5, box)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64", "sliced"])
 def test_full_decoder_sampled(oracle_mod, precision):
     # (3 + 256 latent) -> 512 x 8 -> 1, skip-concat of [x; z] at hidden layer 4 (N = 4096):
     # the first 60000 cells of the march, every sampled face re-solved by the oracle
@@ -60,4 +60,4 @@ def test_full_decoder_sampled(oracle_mod, precision):
           f"fixups {stats['fixups']}")
     assert st == 7 and mesh.n_faces >= 59000
     net = oracle_mod.OracleNet(nt)
-    parity.compare_sampled(oracle_mod, net, mesh, nt.N, 24, 1e-9 if precision == "fp64" else 1e-5, 1.5)
+    parity.compare_sampled(oracle_mod, net, mesh, nt.N, 24, 1e-5 if precision == "mixed" else 1e-9, 1.5)
