@@ -52,6 +52,17 @@ def _measured_bf16_peak():
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
 
 
+def _measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0                              # fallback figure for a GB300
+
+
+HBM_PEAK_GBS = _measured_hbm_peak()
+
+
 # DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
 # workload) from the committed ncu capture, valid while the kernel source is the one captured
 TRAFFIC_CAPTURE = {"sha256_prefix": "8795d1a8059cc349", "precision": "mixed", "candidates": "learned",
@@ -81,6 +92,8 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--decoder-only", action="store_true",
+                   help="run only the decoder march leg (FP64 vs sliced tensor-core compose) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
                    help="run only the compose benchmark (am_compose on the decoder) and print its JSON")
     return p.parse_args()
@@ -396,6 +409,7 @@ def compose_leg(dev, n_cells=4000, reps=5):
         w = mlp.widths
         dense = n * sum(8 * w[l] * w[l - 1] for l in range(1, mlp.L))
         issued = n * sum(4 * 2 * 16 * 16 * 8 * ((w[l] + 15) // 16) * ((w[l - 1] + 15) // 16) for l in range(1, mlp.L))
+        out["autotune"] = m.autotune_compose(nid, keys=keys, reps=3)      # picks the sliced tile shape
         for name, code in (("fp64", 0), ("mixed", 1), ("tensor", 2), ("sliced", 3)):
             ts = []
             for _ in range(reps):
@@ -414,15 +428,63 @@ def compose_leg(dev, n_cells=4000, reps=5):
                          "peak_source": "measured cuBLAS bf16 burst"}
         out["tensor_speedup_vs_fp64"] = out["fp64"]["ms"] / t["ms"]
         # sliced: 36 digit-plane products per 128-row tile of W_l (rows and K padded to 128 / 64),
-        # N = 4 x 16 cells per tile
+        # N = 4 x (cells per tile) columns
         sl = out["sliced"]
-        cols = -(-n // 16) * 64
+        tc = out["autotune"]["compose_tile_cells"]
+        cols = -(-n // tc) * 4 * tc
         sl["issued_tflops"] = 36 * 2 * cols * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
                                                   for l in range(1, mlp.L)) / (sl["ms"] / 1e3) / 1e12
         sl["roofline"] = {"bound": "tensor", "achieved": sl["issued_tflops"], "peak": BF16_PEAK_TFLOPS,
                           "unit": "TFLOP/s", "frac": sl["issued_tflops"] / BF16_PEAK_TFLOPS,
                           "peak_source": "measured cuBLAS bf16 burst", "scope": "whole am_compose call"}
         out["sliced_speedup_vs_fp64"] = out["fp64"]["ms"] / sl["ms"]
+    return out
+
+
+def decoder_leg(dev, n_cells=60000, reps=2):
+    """The decoder-shaped workload, (3 + 256) -> [512] x 8 -> 1 with skip-concat of [x; z] at
+    hidden layer 4 (N = 4096), one seed ray along +x: the first n_cells cells of its march
+    (the whole mesh exceeds 4e6 cells), timed by am_march's CUDA events, seeding outside.
+    Plain FP64 (compose and clip in one persistent kernel) against the sliced path (the compose
+    of each level's cells on the tensor cores into device memory, then the FP64 clip reading
+    those rows).  Rooflines of the two sliced kernels: the compose's issued tensor flops (36
+    digit-plane products per layer) and the clip's algorithmic bytes (its rows, (N + 1) x 32 B
+    per cell, plus the key and the face record) over their own device time."""
+    import paper_2106_10031_gb300 as am
+    from synth import decoder_net
+    mlp = decoder_net()
+    o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
+    out = {"workload": f"decoder (3+256)-[512]x8-1, skip at 4, seed 3; first {n_cells} cells of the march"}
+    with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=4096, max_width=512) as m:
+        nid = m.load_mlp(mlp)
+        out["autotune"] = m.autotune_compose(nid, n=4096, reps=3)
+        for prec in ("fp64", "sliced"):
+            runs = []
+            for _ in range(reps + 1):                   # the first run warms up
+                m.reset()
+                m.seed(nid, o, d)
+                m.march(precision=prec, max_cells=n_cells)
+                runs.append(m.stats())
+            st = min(runs[1:], key=lambda x: x["ms_march"])
+            out[prec] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
+                         "levels": st["levels"], "launches": st["kernel_launches"], "degenerate": st["degenerate"]}
+            if prec == "sliced":
+                w, tc = mlp.widths, out["autotune"]["compose_tile_cells"]
+                cells = st["cells"]
+                issued = 36 * 2 * 4 * tc * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
+                                               for l in range(1, mlp.L)) * (cells / tc)
+                ach = issued / (st["ms_compose"] / 1e3) / 1e12
+                out[prec]["ms_compose"], out[prec]["ms_clip"] = st["ms_compose"], st["ms_clip"]
+                out[prec]["compose_roofline"] = {"kernel": "oz_gemm_kernel + oz_prep_kernel", "bound": "tensor",
+                                                 "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                                 "frac": ach / BF16_PEAK_TFLOPS}
+                kw = (mlp.N + 63) // 64
+                clip_bytes = cells * ((mlp.N + 1) * 32 + 8 * kw + 32 * (24 + 4) + 64)
+                gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
+                out[prec]["clip_roofline"] = {"kernel": "march_range_kernel<FP64> (rows from HBM)", "bound": "hbm",
+                                              "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                              "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells}
+        out["sliced_speedup_vs_fp64"] = out["sliced"]["faces_per_s"] / out["fp64"]["faces_per_s"]
     return out
 
 
@@ -514,6 +576,7 @@ def run_ours(args, dist):
             legs[name] = g
         legs["proposal_training"] = train
         legs["compose"] = compose_leg(dev)
+        legs["decoder"] = decoder_leg(dev)
     e2e = None
     if not args.no_e2e:
         prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
@@ -572,6 +635,10 @@ def main():
         if args.compose_only:
             if dist.rank == 0:
                 print(json.dumps({"leg": "compose", **compose_leg(dist.local)}))
+            return 0
+        if args.decoder_only:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "decoder", **decoder_leg(dist.local)}))
             return 0
         return run_ours(args, dist)
     finally:

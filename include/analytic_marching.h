@@ -164,6 +164,8 @@ typedef struct {
                                  sort, candidate clip, FP64 vertices, check, emit, march, waiting
                                  for work, spare); only filled by a build with -DAM_PHASE_TIMERS,
                                  zero otherwise */
+    double ms_compose;        /* AM_PREC_SLICED march: device time of the tensor-core compose launches */
+    double ms_clip;           /* AM_PREC_SLICED march: device time of the clip launches reading those rows */
 } am_stats_t;
 
 /* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer
@@ -248,6 +250,22 @@ am_status am_set_tuning(am_ctx *ctx, const am_tuning *t);
 
 /* The context's current launch shapes. */
 am_status am_get_tuning(const am_ctx *ctx, am_tuning *t);
+
+/* One timed candidate of the autotuner. */
+typedef struct {
+    int compose_tile_cells;   /* the candidate's cells per tensor-core tile */
+    float ms;                 /* median device time of one am_compose(AM_PREC_SLICED) call */
+} am_tune_point;
+
+/* Autotuner of the sliced tensor-core compose (K-stacking tile shape).  For every supported
+ * compose_tile_cells it runs am_compose(AM_PREC_SLICED) of the n patterns d_keys (device,
+ * n x ceil(N/64) words) of net_id into d_rows (device, n x (N + 1) x 4 doubles) once untimed,
+ * then `reps` times between CUDA events on the context's stream; it keeps the candidate with
+ * the smallest median in the context (as am_set_tuning would) and writes every candidate, in
+ * the order tried, to h_points (host, at most max_points entries; *n_points receives how many
+ * were tried).  Every candidate computes the same rows bit for bit; only the time differs. */
+am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, double *d_rows, int reps,
+                              am_tune_point *h_points, int max_points, int *n_points);
 
 /* ---- learned constraint proposal --------------------------------------------------------
  * No counterpart in the paper.  A small MLP, x (7 + L) -> H -> H -> n_out, ReLU hidden layers,

@@ -72,6 +72,7 @@ struct am_ctx {
     am_stats_t stats{};
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
+    cudaEvent_t evc0 = nullptr, evc1 = nullptr, evc2 = nullptr;   // sliced march: compose / clip split
     // seeding scratch (grown on demand)
     double *d_rays = nullptr;
     unsigned long long *d_seed_keys = nullptr;
@@ -272,6 +273,9 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaEventCreate(&ctx->ev2));
     CU(cudaEventCreate(&ctx->evk0));
     CU(cudaEventCreate(&ctx->evk1));
+    CU(cudaEventCreate(&ctx->evc0));
+    CU(cudaEventCreate(&ctx->evc1));
+    CU(cudaEventCreate(&ctx->evc2));
     Arena &ar = ctx->ar;
     ar.kw = (d.max_neurons + 63) / 64;
     ar.maxv = d.max_face_verts;
@@ -347,6 +351,8 @@ void am_destroy(am_ctx *ctx)
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
     if (ctx->evk0) cudaEventDestroy(ctx->evk0);
     if (ctx->evk1) cudaEventDestroy(ctx->evk1);
+    for (cudaEvent_t e : {ctx->evc0, ctx->evc1, ctx->evc2})
+        if (e) cudaEventDestroy(e);
     proposal_free(ctx->prop);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -848,15 +854,24 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
                 // per batch of the level: the rows on the tensor cores, then the FP64 clip and march
                 for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells) {
                     const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
+                    CU(cudaEventRecord(ctx->evc0, ctx->stream));
                     s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, c1 - c0, ctx->oz_rows);
                     if (s != AM_OK) return s;
+                    CU(cudaEventRecord(ctx->evc1, ctx->stream));
                     ma.begin = c0;
                     ma.end = c1;
                     ma.rows_in = ctx->oz_rows;
                     launch_march(ma, 0, false, (int)(c1 - c0), ctx->stream);
                     CU(cudaGetLastError());
+                    CU(cudaEventRecord(ctx->evc2, ctx->stream));
                     ctx->stats.cell_launches += 1;
                     ctx->stats.kernel_launches += 1;
+                    CU(cudaEventSynchronize(ctx->evc2));
+                    float a = 0.f, b = 0.f;
+                    CU(cudaEventElapsedTime(&a, ctx->evc0, ctx->evc1));
+                    CU(cudaEventElapsedTime(&b, ctx->evc1, ctx->evc2));
+                    ctx->stats.ms_compose += a;
+                    ctx->stats.ms_clip += b;
                 }
             } else {
                 ma.begin = f0;
@@ -961,6 +976,47 @@ am_status am_get_tuning(const am_ctx *ctx, am_tuning *t)
 {
     if (!ctx || !t) return AM_ERR_INVALID_ARG;
     t->compose_tile_cells = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
+    return AM_OK;
+}
+
+am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, double *d_rows, int reps,
+                              am_tune_point *h_points, int max_points, int *n_points)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (n < 1 || !d_keys || !d_rows || reps < 1 || max_points < 0 || (max_points > 0 && !h_points))
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    const auto *keys = reinterpret_cast<const unsigned long long *>(d_keys);
+    int nt = 0;
+    const int *tiles = oz_tile_cells(&nt);
+    const int saved = ctx->oz_tile_cells;
+    int best = -1;
+    float best_ms = 0.0f;
+    for (int i = 0; i < nt; ++i) {
+        ctx->oz_tile_cells = tiles[i];
+        am_status s = sliced_compose(ctx, net_id, keys, n, d_rows);     // warm-up, untimed
+        if (s != AM_OK) { ctx->oz_tile_cells = saved; return s; }
+        std::vector<float> ms(reps);
+        for (int r = 0; r < reps; ++r) {
+            CU(cudaEventRecord(ctx->evk0, ctx->stream));
+            s = sliced_compose_async(ctx, net_id, keys, n, d_rows);
+            if (s != AM_OK) { ctx->oz_tile_cells = saved; return s; }
+            CU(cudaEventRecord(ctx->evk1, ctx->stream));
+            CU(cudaEventSynchronize(ctx->evk1));
+            CU(cudaEventElapsedTime(&ms[r], ctx->evk0, ctx->evk1));
+        }
+        s = sliced_check(ctx);
+        if (s != AM_OK) { ctx->oz_tile_cells = saved; return s; }
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[reps / 2];
+        if (i < max_points) {
+            h_points[i].compose_tile_cells = tiles[i];
+            h_points[i].ms = med;
+        }
+        if (best < 0 || med < best_ms) { best = tiles[i]; best_ms = med; }
+    }
+    ctx->oz_tile_cells = best;
+    if (n_points) *n_points = nt;
     return AM_OK;
 }
 

@@ -50,7 +50,7 @@ namespace {
 constexpr int kOzPlanes = kOzDigits;      // digit planes per operand = accumulator diagonals
 constexpr int kOzBK = 64;                 // K elements per staged chunk (128 bytes of BF16)
 constexpr int kOzM = 128;                 // rows of W_l per CTA (UMMA M)
-constexpr int kOzPrepWarps = 8;           // cells per prep block (one warp each)
+constexpr int kOzPrepThreads = 128;       // threads of the prep block of one cell
 constexpr long long kOzWaitNs = 2000000000ll;   // 2 s limit on any pipeline wait
 constexpr long long kOzDrainNs = 200000000ll;   // 0.2 s limit on the drain after an abort
 
@@ -162,25 +162,35 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes; the caller waits (tcgen05.wait::ld)
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8])
 {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
-// 2^e as a double (e in the normal range), else through ldexp
-__device__ __forceinline__ double pow2d(int e)
+// acc 2^e as a double, rounded to nearest even, with integer operations on the bit pattern
+// (the FP64 pipe of this part is narrow); results outside the normal range go through ldexp
+__device__ __forceinline__ double i64_ldexp(long long acc, int e)
 {
-    if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
-    return ldexp(1.0, e);
+    if (acc == 0) return 0.0;
+    const unsigned long long sgn = acc < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long m = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    const int sh = 11 - __clzll(m);               // bits beyond 53
+    if (sh > 0) {
+        const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        m >>= sh;
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        e += sh;
+        if (m >> 53) { m >>= 1; ++e; }
+    } else {
+        m <<= -sh;
+        e += sh;
+    }
+    const int be = e + 52 + 1023;                 // m in [2^52, 2^53)
+    if (be <= 0 || be >= 2047) return ldexp(sgn ? -(double)m : (double)m, e);
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
 __device__ __forceinline__ bool key_bit(const unsigned long long *key, int k) { return (key[k >> 6] >> (k & 63)) & 1ull; }
@@ -234,15 +244,18 @@ struct OzPrep {
     int Kp;                           // round_up(n_l, 64)
 };
 
-__global__ void __launch_bounds__(32 * kOzPrepWarps) oz_prep_kernel(OzPrep p)
+// One block of kOzPrepThreads per cell.
+__global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * kOzPrepWarps + (threadIdx.x >> 5);
-    if (i >= p.n) return;
+    constexpr int kW = kOzPrepThreads / 32;
+    __shared__ unsigned long long red[kW][4];
+    __shared__ double fred[kW][4];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t i = blockIdx.x;
     const unsigned long long *key = p.keys + i * p.kw;
     double *out = p.rows + i * p.rstride;
     if (p.l == 1) {
-        for (int k = lane; k < p.nl; k += 32) {
+        for (int k = tid; k < p.nl; k += kOzPrepThreads) {
             const double2 c0 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k];
             const double2 c1 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k + 1];
             const bool act = key_bit(key, k);
@@ -250,13 +263,13 @@ __global__ void __launch_bounds__(32 * kOzPrepWarps) oz_prep_kernel(OzPrep p)
             o[0] = act ? make_double2(-c0.x, -c0.y) : c0;
             o[1] = act ? make_double2(-c1.x, -c1.y) : c1;
         }
-        __syncwarp();
+        __syncthreads();
     }
     const double *Z = out + 4 * (int64_t)p.row0;   // sign-adjusted rows of layer l: an active row is -Z_k
     if (p.l == p.L) {
         // a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Cor. 1, Eq. 8)
         double f[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = lane; k < p.nl; k += 32)
+        for (int k = tid; k < p.nl; k += kOzPrepThreads)
             if (key_bit(key, p.row0 + k)) {
                 const double w = p.w_out[k];
                 const double *r = Z + 4 * (int64_t)k;
@@ -264,17 +277,21 @@ __global__ void __launch_bounds__(32 * kOzPrepWarps) oz_prep_kernel(OzPrep p)
                 for (int j = 0; j < 4; ++j) f[j] = fma(-w, r[j], f[j]);
             }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 4; ++j) {
             for (int o = 16; o > 0; o >>= 1) f[j] += __shfl_xor_sync(0xffffffffu, f[j], o);
-        if (lane == 0) {
-            double *aF = out + 4 * (int64_t)p.N;
-            aF[0] = f[0]; aF[1] = f[1]; aF[2] = f[2]; aF[3] = f[3] + p.b_out;
+            if (lane == 0) fred[wid][j] = f[j];
+        }
+        __syncthreads();
+        if (tid < 4) {
+            double F = tid == 3 ? p.b_out : 0.0;
+            for (int w = 0; w < kW; ++w) F += fred[w][tid];
+            out[4 * (int64_t)p.N + tid] = F;
         }
         return;
     }
     // column maxima of |diag(s_l) Z_l| (bit patterns of non-negative doubles order as integers)
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int k = lane; k < p.nl; k += 32)
+    for (int k = tid; k < p.nl; k += kOzPrepThreads)
         if (key_bit(key, p.row0 + k)) {
             const long long *r = reinterpret_cast<const long long *>(Z + 4 * (int64_t)k);
 #pragma unroll
@@ -283,18 +300,25 @@ __global__ void __launch_bounds__(32 * kOzPrepWarps) oz_prep_kernel(OzPrep p)
                 mx[j] = a > mx[j] ? a : mx[j];
             }
         }
-    int e[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx[j], o);
             mx[j] = v > mx[j] ? v : mx[j];
         }
-        e[j] = col_exponent(mx[j]);
+        if (lane == 0) red[wid][j] = mx[j];
     }
-    if (lane < 4) p.eB[4 * i + lane] = e[lane];
-    // digits: two consecutive k per lane, so each plane store is a BF16 pair
-    for (int k0 = 2 * lane; k0 < p.Kp; k0 += 64) {
+    __syncthreads();
+    int e[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        unsigned long long m = 0ull;
+        for (int w = 0; w < kW; ++w) m = red[w][j] > m ? red[w][j] : m;
+        e[j] = col_exponent(m);
+    }
+    if (tid < 4) p.eB[4 * i + tid] = e[tid];
+    // digits: two consecutive k per thread, so each plane store is a BF16 pair
+    for (int k0 = 2 * tid; k0 < p.Kp; k0 += 2 * kOzPrepThreads) {
         unsigned dig[4][kOzPlanes];          // per column, per plane: bits of the pair
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -353,7 +377,7 @@ struct OzShape {
     static constexpr int kBStage = kOzPlanes * kBPlane;
     static constexpr int kTmemCols = kOzPlanes * kNCol;        // 8 diagonals
     static constexpr int kBars = 2 * AST + 2 * 2 + 2;
-    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 1024;
+    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 16 * NC + 1024;
     static_assert(kTmemCols == 256 || kTmemCols == 512, "TMEM allocation must be a power of two");
     static_assert(kBPlane % 1024 == 0, "B plane tiles must stay 1024-byte aligned");
 };
@@ -377,6 +401,7 @@ __global__ void __launch_bounds__(192, 1)
     unsigned char *tail = gbase + (bars - base) + 8 * S::kBars;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tail);
     volatile int *abort = reinterpret_cast<volatile int *>(tail + 4);
+    int *eBs = reinterpret_cast<int *>(tail + 16);                 // 4 NC column exponents
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kOzM;
@@ -470,51 +495,61 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row of W_l per thread
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row of W_l per thread.
+        //      While the products run it fetches what it needs besides the accumulators: the
+        //      cells' column exponents (shared memory), this row's neuron state in each cell (a
+        //      bit mask), C_l and the row exponent.
         const int quarter = warp & 3;
         const int r = quarter * 32 + lane;
         const int grow = m0 + r;
         const bool live_row = grow < g.nl;
+        const int et = threadIdx.x - 64;                 // 0..127 over the epilogue warps
+        const int64_t cell0 = col0 / 4;
+        if (et < 4 * NC) eBs[et] = cell0 + et / 4 < g.n ? g.eB[col0 + et] : 0;
+        unsigned act = 0u;
+        double2 C01 = make_double2(0.0, 0.0), C23 = make_double2(0.0, 0.0);
+        int eA = 0;
+        if (live_row) {
+            for (int cc = 0; cc < NC; ++cc)
+                if (cell0 + cc < g.n && key_bit(g.keys + (cell0 + cc) * g.kw, g.row0 + grow)) act |= 1u << cc;
+            C01 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow];
+            C23 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow + 1];
+            eA = g.eA[grow];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the epilogue warps only
         if (mbar_wait(accfull, 0, abort, g.err)) {
             tc_fence_after();
-            double2 C01 = make_double2(0.0, 0.0), C23 = make_double2(0.0, 0.0);
-            int eA = 0;
-            if (live_row) {
-                C01 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow];
-                C23 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow + 1];
-                eA = g.eA[grow];
-            }
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-            for (int c4 = 0; c4 < NC; c4 += 4) {
-                long long acc[16];
-                float v[16];
-                tmem_ld16(trow + (uint32_t)(4 * c4), v);
+            for (int c2 = 0; c2 < NC; c2 += 2) {
+                // 8 columns (two cells) of all 8 diagonals, one wait for the lot
+                uint32_t v[kOzPlanes][8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] = (long long)__float2int_rn(v[j]);
-#pragma unroll 1
-                for (int dgl = 1; dgl < kOzPlanes - 1; ++dgl) {
-                    tmem_ld16(trow + (uint32_t)(dgl * S::kNCol + 4 * c4), v);
+                for (int dg = 0; dg < kOzPlanes; ++dg) tmem_ld8_nowait(trow + (uint32_t)(dg * S::kNCol + 4 * c2), v[dg]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                long long acc[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[j] = (acc[j] << 6) + (long long)__float2int_rn(v[j]);
+                for (int j = 0; j < 8; ++j) {
+                    long long a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
+#pragma unroll
+                    for (int dg = 1; dg < kOzPlanes - 1; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
+                    acc[j] = a + (long long)((__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j])) + 32) >> 6);
                 }
-                tmem_ld16(trow + (uint32_t)((kOzPlanes - 1) * S::kNCol + 4 * c4), v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] += (long long)((__float2int_rn(v[j]) + 32) >> 6);
                 // acc 2^(eA + eB - 48) + C_l, signed by the neuron's state
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int64_t cell = col0 / 4 + c4 + cc;
+                for (int h = 0; h < 2; ++h) {
+                    const int cc = c2 + h;
+                    const int64_t cell = cell0 + cc;
                     if (!live_row || cell >= g.n) continue;
-                    const int4 eB = reinterpret_cast<const int4 *>(g.eB)[cell];
-                    const bool act = key_bit(g.keys + cell * g.kw, g.row0 + grow);
-                    const double x = fma((double)acc[4 * cc + 0], pow2d(eA + eB.x - 48), C01.x);
-                    const double y = fma((double)acc[4 * cc + 1], pow2d(eA + eB.y - 48), C01.y);
-                    const double z = fma((double)acc[4 * cc + 2], pow2d(eA + eB.z - 48), C23.x);
-                    const double w = fma((double)acc[4 * cc + 3], pow2d(eA + eB.w - 48), C23.y);
+                    const int *eB = eBs + 4 * cc;
+                    const double x = i64_ldexp(acc[4 * h + 0], eA + eB[0] - 48) + C01.x;
+                    const double y = i64_ldexp(acc[4 * h + 1], eA + eB[1] - 48) + C01.y;
+                    const double z = i64_ldexp(acc[4 * h + 2], eA + eB[2] - 48) + C23.x;
+                    const double w = i64_ldexp(acc[4 * h + 3], eA + eB[3] - 48) + C23.y;
+                    const bool neg = (act >> cc) & 1u;
                     double2 *o = reinterpret_cast<double2 *>(g.rows + cell * g.rstride + 4 * (int64_t)(g.row0 + grow));
-                    o[0] = act ? make_double2(-x, -y) : make_double2(x, y);
-                    o[1] = act ? make_double2(-z, -w) : make_double2(z, w);
+                    o[0] = neg ? make_double2(-x, -y) : make_double2(x, y);
+                    o[1] = neg ? make_double2(-z, -w) : make_double2(z, w);
                 }
             }
         }
@@ -646,7 +681,7 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
         p.B = scr.B;
         p.eB = scr.eB;
         p.ncols = ncols;
-        const unsigned pgrid = (unsigned)((nb + kOzPrepWarps - 1) / kOzPrepWarps);
+        const unsigned pgrid = (unsigned)nb;
         for (int l = 1; l <= net.L; ++l) {
             if (l >= 2) {
                 CUtensorMap tmB;
@@ -670,14 +705,14 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
                 g.err = scr.err;
                 const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
                 e = tile_cells == 8 ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, st)
-                                    : launch_gemm<16, 4>(tmA, tmB, g, g.Mp, 4 * nb, st);
+                                    : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, st);
                 if (e != cudaSuccess) return e;
             }
             p.l = l;
             p.nl = net.width[l];
             p.row0 = net.row0[l];
             p.Kp = oz_kp(net.width[l]);
-            oz_prep_kernel<<<pgrid, 32 * kOzPrepWarps, 0, st>>>(p);
+            oz_prep_kernel<<<pgrid, kOzPrepThreads, 0, st>>>(p);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

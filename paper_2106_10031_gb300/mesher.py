@@ -154,6 +154,49 @@ class Mesher:
         self._check(self.lib.am_get_tuning(self.ctx, C.byref(t)))
         return {k: getattr(t, k) for k, _ in nt.am_tuning._fields_}
 
+    def autotune_compose(self, net_id: int, keys=None, n: int = 4096, reps: int = 5, cache: str | None = None,
+                         seed: int = 0) -> dict:
+        """Pick the sliced compose's tile shape for net_id by timing every candidate
+        (am_autotune_compose) on `keys` ((n, ceil(N/64)) uint64 activation patterns; random
+        patterns when None: the tensor work does not depend on them).  With `cache` (a JSON
+        file path) a result stored for the same device, layer widths and precision is reused
+        without timing, and a new one is stored."""
+        import json
+        import os
+
+        import torch
+        net = self.nets[net_id]
+        dev = torch.device("cuda", self.device)
+        cache_key = f"{torch.cuda.get_device_name(dev)}|sm_{''.join(map(str, torch.cuda.get_device_capability(dev)))}" \
+                    f"|{'x'.join(map(str, net.widths))}|sliced"
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if cache_key in table:
+                self.set_tuning(compose_tile_cells=int(table[cache_key]["compose_tile_cells"]))
+                return dict(table[cache_key], cached=True)
+        kw = (net.N + 63) // 64
+        if keys is None:
+            g = torch.Generator(device="cpu").manual_seed(seed)
+            k = torch.randint(-2**62, 2**62, (n, kw), generator=g, dtype=torch.int64).to(dev)
+        else:
+            k = torch.as_tensor(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64), device=dev)
+        n = k.shape[0]
+        rows = torch.empty((n, net.N + 1, 4), dtype=torch.float64, device=dev)
+        pts = (nt.am_tune_point * 8)()
+        cnt = C.c_int(0)
+        self._check(self.lib.am_autotune_compose(self.ctx, net_id, C.c_void_p(k.data_ptr()), n,
+                                                 C.c_void_p(rows.data_ptr()), reps, pts, 8, C.byref(cnt)))
+        res = {"compose_tile_cells": self.get_tuning()["compose_tile_cells"], "cells": int(n),
+               "candidates": [{"compose_tile_cells": pts[i].compose_tile_cells, "ms": pts[i].ms}
+                              for i in range(cnt.value)]}
+        if cache:
+            table[cache_key] = res
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return dict(res, cached=False)
+
     # ---- compose only
     def compose(self, net_id: int, keys, precision="fp64"):
         """Rows of the cells with activation patterns `keys` ((n, ceil(N/64)) uint64): returns

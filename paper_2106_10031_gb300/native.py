@@ -60,13 +60,18 @@ class am_tuning(C.Structure):
     _fields_ = [("compose_tile_cells", C.c_int)]
 
 
+class am_tune_point(C.Structure):
+    _fields_ = [("compose_tile_cells", C.c_int), ("ms", C.c_float)]
+
+
 class am_stats_t(C.Structure):
     _fields_ = [("cells", C.c_int64), ("faces", C.c_int64), ("empty_faces", C.c_int64),
                 ("vertices", C.c_int64), ("corners", C.c_int64), ("degenerate", C.c_int64),
                 ("open_faces", C.c_int64), ("refined_cells", C.c_int64), ("levels", C.c_int64),
                 ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
                 ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64), ("close_calls", C.c_int64),
-                ("fixups", C.c_int64), ("cuts", C.c_int64), ("phase_cycles", C.c_int64 * 10)]
+                ("fixups", C.c_int64), ("cuts", C.c_int64), ("phase_cycles", C.c_int64 * 10),
+                ("ms_compose", C.c_double), ("ms_clip", C.c_double)]
 
 
 class am_mesh(C.Structure):
@@ -92,6 +97,8 @@ ENTRY_POINTS = [
     ("am_get_stats", C.c_int, [C.c_void_p, C.POINTER(am_stats_t)]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     ("am_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("am_autotune_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
+                                      C.c_int, C.c_void_p]),
     ("am_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("am_proposal_samples", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("am_proposal_init", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),

@@ -124,3 +124,30 @@ def test_sliced_compose_batches_and_ragged_shapes(oracle_mod, tile_cells):
         worst = max(worst, err.max())
     print(f"\nsliced, {tile_cells} cells per tile: max err {worst:.2e} over 136 of {n} patterns")
     assert worst < 1e-11
+
+
+def test_autotune_compose_and_tile_shapes_agree_bitwise(oracle_mod, tmp_path):
+    # every tile shape sums the same exact digit products: the rows agree bit for bit; the
+    # autotuner times each shape, keeps the fastest and caches its choice per net shape
+    import paper_2106_10031_gb300 as am
+    mlp = proposal_target_net()
+    rng = np.random.default_rng(9)
+    keys = _keys_from_states(rng.integers(0, 2, (700, mlp.N)).astype(np.uint8), mlp.N)
+    cache = str(tmp_path / "tune.json")
+    with am.Mesher(max_cells=1 << 10, max_neurons=2048, max_width=256) as m:
+        nid = m.load_mlp(mlp)
+        rows = {}
+        for t in (16, 8):
+            m.set_tuning(compose_tile_cells=t)
+            rows[t], _ = m.compose(nid, keys, "sliced")
+        assert np.array_equal(rows[16], rows[8])
+        res = m.autotune_compose(nid, keys, reps=3, cache=cache)
+        assert not res["cached"] and res["compose_tile_cells"] in (8, 16)
+        assert sorted(c["compose_tile_cells"] for c in res["candidates"]) == [8, 16]
+        assert all(c["ms"] > 0 for c in res["candidates"])
+        assert m.get_tuning()["compose_tile_cells"] == res["compose_tile_cells"]
+        again = m.autotune_compose(nid, keys, cache=cache)
+        assert again["cached"] and again["compose_tile_cells"] == res["compose_tile_cells"]
+        with pytest.raises(am.AMError):
+            m.set_tuning(compose_tile_cells=12)
+        print(f"\nautotune: {res}")
