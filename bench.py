@@ -481,7 +481,7 @@ def decoder_leg(dev, n_cells=60000, reps=2):
                 kw = (mlp.N + 63) // 64
                 clip_bytes = cells * ((mlp.N + 1) * 32 + 8 * kw + 32 * (24 + 4) + 64)
                 gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
-                out[prec]["clip_roofline"] = {"kernel": "march_range_kernel<FP64> (rows from HBM)", "bound": "hbm",
+                out[prec]["clip_roofline"] = {"kernel": "march_range_kernel<double-float> (rows from HBM)", "bound": "hbm",
                                               "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                                               "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells}
         out["sliced_speedup_vs_fp64"] = out["sliced"]["faces_per_s"] / out["fp64"]["faces_per_s"]

@@ -173,7 +173,9 @@ am_status ensure_oz_scratch(am_ctx *ctx)
     OzScratch &z = ctx->oz;
     z.batch_cells = 4096;
     CU(cudaMalloc(&z.B, sizeof(__nv_bfloat16) * oz_scratch_elems(z.batch_cells, oz_kp(ctx->opts.max_width))));
-    CU(cudaMalloc(&z.eB, sizeof(int) * 4 * z.batch_cells));
+    CU(cudaMalloc(&z.eB[0], sizeof(int) * 4 * z.batch_cells));
+    CU(cudaMalloc(&z.eB[1], sizeof(int) * 4 * z.batch_cells));
+    CU(cudaMalloc(&z.P, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width)));
     CU(cudaMalloc(&z.err, sizeof(int)));
     CU(cudaMemsetAsync(z.err, 0, sizeof(int), ctx->stream));
     return AM_OK;
@@ -189,6 +191,8 @@ OzNet oz_view(const NetHost &nh)
         v.width[l] = d.width[l];
         v.row0[l] = d.row0[l];
         v.Cl[l] = d.Cl[l];
+        v.Clhi[l] = d.Clhi[l];
+        v.Cllo[l] = d.Cllo[l];
         if (l >= 2) {
             v.eA[l] = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(nh.ozblob) + nh.oz_off_eA[l]);
             v.mapA[l] = nh.ozmap[l].b;
@@ -200,7 +204,8 @@ OzNet oz_view(const NetHost &nh)
 }
 
 // rows (n x (N + 1) x 4) of n cells of one net on the tensor cores, asynchronous on the stream
-am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
+am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, void *d_rows,
+                               bool df = false)
 {
     const NetHost &nh = ctx->nets[net_id];
     if (!nh.oz_ok)
@@ -208,7 +213,7 @@ am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long
     am_status s = ensure_oz_scratch(ctx);
     if (s != AM_OK) return s;
     const int tile = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
-    CU(oz_compose(oz_view(nh), d_keys, nh.dev.kw, n, d_rows, ctx->oz, tile, ctx->stream));
+    CU(oz_compose(oz_view(nh), d_keys, nh.dev.kw, n, d_rows, df, ctx->oz, tile, ctx->sm_count, ctx->stream));
     const int64_t batches = (n + ctx->oz.batch_cells - 1) / ctx->oz.batch_cells;
     ctx->stats.kernel_launches += (2 * (int64_t)nh.dev.L - 1) * batches;
     return AM_OK;
@@ -343,7 +348,8 @@ void am_destroy(am_ctx *ctx)
         if (n.ozblob) cudaFree(n.ozblob);
     }
     if (ctx->oz.B) cudaFree(ctx->oz.B);
-    if (ctx->oz.eB) cudaFree(ctx->oz.eB);
+    for (void *b : {(void *)ctx->oz.eB[0], (void *)ctx->oz.eB[1], (void *)ctx->oz.P})
+        if (b) cudaFree(b);
     if (ctx->oz.err) cudaFree(ctx->oz.err);
     if (ctx->oz_rows) cudaFree(ctx->oz_rows);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -855,13 +861,13 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
                 for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells) {
                     const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
                     CU(cudaEventRecord(ctx->evc0, ctx->stream));
-                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, c1 - c0, ctx->oz_rows);
+                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, c1 - c0, ctx->oz_rows, true);
                     if (s != AM_OK) return s;
                     CU(cudaEventRecord(ctx->evc1, ctx->stream));
                     ma.begin = c0;
                     ma.end = c1;
                     ma.rows_in = ctx->oz_rows;
-                    launch_march(ma, 0, false, (int)(c1 - c0), ctx->stream);
+                    launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
                     CU(cudaGetLastError());
                     CU(cudaEventRecord(ctx->evc2, ctx->stream));
                     ctx->stats.cell_launches += 1;

@@ -34,8 +34,8 @@ struct MarchArgs {
     int candidates;          // kCandNearest / kCandLearned / kCandNone
     int tc;                  // compose only (mode 1): hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
-    const double *rows_in;   // level schedule, FP64 mode: rows (n x (N + 1) x 4, a_F last) of cells
-                             // [begin, end) composed beforehand (sliced tensor-core compose)
+    const void *rows_in;     // level schedule: rows of cells [begin, end) composed beforehand on the
+                             // tensor cores, n x (N + 1) FP32 pairs [hi x 4 | lo x 4], a_F last
 };
 int march_smem_bytes(int max_n, int max_w);
 int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate
@@ -139,6 +139,7 @@ struct OzNet {
     int L = 0, N = 0;
     int width[kMaxLayers + 1] = {}, row0[kMaxLayers + 1] = {};
     const double *Cl[kMaxLayers + 1] = {};
+    const float *Clhi[kMaxLayers + 1] = {}, *Cllo[kMaxLayers + 1] = {};   // C_l as double-float pairs
     const int *eA[kMaxLayers + 1] = {};       // row exponents of W_l (device)
     const void *mapA[kMaxLayers + 1] = {};    // host CUtensorMap over the digit planes of W_l
     const double *w_out = nullptr;
@@ -146,7 +147,8 @@ struct OzNet {
 };
 struct OzScratch {
     __nv_bfloat16 *B = nullptr;   // kOzDigits x 4 batch_cells x Kp digit planes of the stacked operand
-    int *eB = nullptr;            // 4 batch_cells column exponents
+    int *eB[2] = {nullptr, nullptr};   // 4 batch_cells column exponents, for alternate layers
+    long long *P = nullptr;       // 4 batch_cells x Mp exact products of one layer (64-bit integers)
     int *err = nullptr;           // set to 1 by a kernel whose pipeline wait timed out
     int64_t batch_cells = 0;      // multiple of 16
 };
@@ -156,8 +158,10 @@ const int *oz_tile_cells(int *n); // the supported cells per CTA (UMMA N = 4 x c
 void oz_slice_weights(const double *W, int n, int np, int fan, std::vector<uint16_t> &planes, std::vector<int> &eA);
 cudaError_t oz_encode_weights(void *map, const void *planes, int n, int np);
 int64_t oz_scratch_elems(int64_t batch_cells, int max_kp);
-// rows (n x (N + 1) x 4 FP64, a_F last) of the cells with keys (n x kw words)
-cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, double *rows,
-                       const OzScratch &scr, int tile_cells, cudaStream_t st);
+// rows of the cells with keys (n x kw words): n x (N + 1) rows of 32 bytes, a_F last, each row
+// FP64 [a | a0] or, with df, FP32 pairs [hi x 4 | lo x 4]; batches smaller than sms x the tiles
+// resident per SM split the product's K over several CTAs
+cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, void *rows, bool df,
+                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st);
 
 }  // namespace am

@@ -814,12 +814,29 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     const int N = net.N, NC = N + kBoxPlanes;          // checked rows: neurons + box
     long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
     AM_TICK(tp0);
-    if (M == kFP64 && a.rows_in) {
-        // rows composed beforehand on the tensor cores (same layout and signs as compose<kFP64>)
-        const double2 *src = reinterpret_cast<const double2 *>(a.rows_in + (cell - a.begin) * (int64_t)(N + 1) * 4);
-        double2 *dst = reinterpret_cast<double2 *>(s.r64);
-        for (int i = tid; i < 2 * N; i += kT) dst[i] = __ldcs(src + i);
-        if (tid < 4) s.aF[tid] = __ldcs(reinterpret_cast<const double *>(src) + 4 * N + tid);
+    if (a.rows_in) {
+        // rows composed beforehand on the tensor cores, as FP32 pairs [hi x 4 | lo x 4] per row
+        // (signs as compose<M>, a_F last).  The pairs are the rows: the double-float tests are
+        // certified against them with no further row error, as FP64 tests take FP64 rows.
+        const float4 *src = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * (int64_t)(N + 1) * 2;
+        for (int k = tid; k < N; k += kT) {
+            const float4 h = __ldcs(src + 2 * k), l = __ldcs(src + 2 * k + 1);
+            if (M == kFP64) {
+                double *r = s.r64 + 4 * k;
+                r[0] = (double)h.x + (double)l.x; r[1] = (double)h.y + (double)l.y;
+                r[2] = (double)h.z + (double)l.z; r[3] = (double)h.w + (double)l.w;
+            } else {
+                *reinterpret_cast<float4 *>(s.rhi + 4 * k) = h;
+                *reinterpret_cast<float4 *>(s.rlo + 4 * k) = l;
+                s.err[k] = 0.0f;
+            }
+        }
+        if (tid < 4) {
+            const float h = reinterpret_cast<const float *>(src + 2 * N)[tid];
+            const float l = reinterpret_cast<const float *>(src + 2 * N + 1)[tid];
+            s.aF[tid] = (double)h + (double)l;
+            if (M == kDF) { s.aFhi[tid] = h; s.aFlo[tid] = l; }
+        }
         if (tid == 0) s.eF[0] = 0.0f;
         __syncthreads();
     } else {
@@ -1177,7 +1194,7 @@ __device__ void process_cell(const MarchArgs &a, int64_t cell, const Sh &s)
     for (int w = threadIdx.x; w < 2 * ar.kw; w += kT)       // all key words: pushes copy them
         s.mask[w] = (unsigned)(__ldcg(key + (w >> 1)) >> ((w & 1) * 32));
     __syncthreads();
-    if (MODE == kDF && !net.df_ok) {
+    if (MODE == kDF && !net.df_ok && !a.rows_in) {
         if (threadIdx.x == 0) s.blk[4] += 1;             // solved in FP64 (the net's bound is too loose)
         solve_cell<kFP64>(a, net, cell, s);
     } else if (MODE == kDF) {

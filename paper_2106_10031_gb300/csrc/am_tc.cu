@@ -231,20 +231,90 @@ struct OzPrep {
     const unsigned long long *keys;   // cell i's key at keys + i * kw
     int kw;
     int64_t n;                        // cells in the batch
-    double *rows;                     // cell i's rows at rows + i * rstride (N rows, then a_F)
-    int64_t rstride;
+    void *rows;                       // cell i's rows at rows + i * rstride (N rows, then a_F), 32 B each:
+    int64_t rstride;                  //   FP64 [a | a0], or FP32 pairs [hi x4 | lo x4] when df
+    int df;
     int l, L, N;
     int nl, row0;                     // width and first neuron of layer l
-    const double *Cl1;                // layer-1 constant rows (n_1 x 4), written when l == 1
+    const long long *P;               // l >= 2: the exact products of layer l, column c at P + c Mp
+    int Mp;
+    const int *eA;                    // l >= 2: row exponents of W_l
+    const int *eBin;                  // l >= 2: column exponents of layer l's right operand
+    const double *Cl;                 // layer l constant rows (n_l x 4), FP64 ...
+    const float *Clhi, *Cllo;         // ... and as double-float pairs
     const double *w_out;
     double b_out;
-    __nv_bfloat16 *B;                 // digit planes: plane t, column c at row t * ncols + c, Kp wide
-    int *eB;                          // column exponents
+    __nv_bfloat16 *B;                 // digit planes for layer l + 1: plane t, column c at row t ncols + c
+    int *eBout;                       // column exponents for layer l + 1
     int64_t ncols;
     int Kp;                           // round_up(n_l, 64)
 };
 
-// One block of kOzPrepThreads per cell.
+// (sh, sl) += (bh, bl): double-float addition, TwoSum on the high parts (Knuth), then the
+// renormalisation |sl| <= ulp(sh) / 2 (Fast2Sum)
+__device__ __forceinline__ void df_add(float &sh, float &sl, float bh, float bl)
+{
+    const float t = __fadd_rn(sh, bh);
+    const float bp = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(bh, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, bl));
+}
+
+__device__ __forceinline__ void df_norm(float &h, float &l)
+{
+    const float s = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(s, h));
+    h = s;
+}
+
+// nearest FP32 of acc 2^e (integer operations; outside the normal range through ldexpf) and the
+// 64-bit integer that FP32 stands for at scale 2^e
+__device__ __forceinline__ float i64_to_f32(long long acc, int e, long long *as_int)
+{
+    if (acc == 0) { *as_int = 0; return 0.0f; }
+    const bool neg = acc < 0;
+    unsigned long long m = neg ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+    const int sh = 40 - __clzll(m);               // bits beyond 24
+    int ee = e;
+    if (sh > 0) {
+        const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        m >>= sh;
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+        ee += sh;
+        *as_int = (long long)(m << sh);
+        if (m >> 24) { m >>= 1; ++ee; }
+    } else {
+        *as_int = (long long)m;
+        m <<= -sh;
+        ee += sh;
+    }
+    if (neg) *as_int = -*as_int;
+    const int be = ee + 23 + 127;                 // m in [2^23, 2^24)
+    float f;
+    if (be <= 0 || be >= 255) f = ldexpf((float)m, ee);
+    else f = __uint_as_float(((unsigned)be << 23) | ((unsigned)m & 0x7FFFFFu));
+    return neg ? -f : f;
+}
+
+// x 2^(62 - e) as a 64-bit integer for an FP32 x with |x| < 2^e (truncated below 2^(e - 62))
+__device__ __forceinline__ long long fixed62f(float x, int e)
+{
+    const unsigned u = __float_as_uint(x);
+    const int be = (int)((u >> 23) & 0xFF);
+    if (be == 0) return 0;
+    const long long mant = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = be - 88 - e;                   // mant 2^(be-150) 2^(62-e)
+    long long v;
+    if (sh >= 0) v = mant << sh;
+    else if (sh > -64) v = mant >> (-sh);
+    else v = 0;
+    return (u >> 31) ? -v : v;
+}
+
+// One block of kOzPrepThreads per cell: the rows of layer l (from the exact products, or the
+// cell-independent C_1 at layer 1), then the digit planes of diag(s_l) Z_l for layer l + 1, or
+// a_F after the last layer.
 __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 {
     constexpr int kW = kOzPrepThreads / 32;
@@ -253,28 +323,71 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t i = blockIdx.x;
     const unsigned long long *key = p.keys + i * p.kw;
-    double *out = p.rows + i * p.rstride;
-    if (p.l == 1) {
-        for (int k = tid; k < p.nl; k += kOzPrepThreads) {
-            const double2 c0 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k];
-            const double2 c1 = reinterpret_cast<const double2 *>(p.Cl1)[2 * k + 1];
-            const bool act = key_bit(key, k);
-            double2 *o = reinterpret_cast<double2 *>(out + 4 * (int64_t)k);
-            o[0] = act ? make_double2(-c0.x, -c0.y) : c0;
-            o[1] = act ? make_double2(-c1.x, -c1.y) : c1;
+    double *out = reinterpret_cast<double *>(p.rows) + i * p.rstride;     // 4 doubles = 8 floats per row
+    float *outf = reinterpret_cast<float *>(out);
+    // ---- rows of layer l, signed (1 - 2 s_k) as in Eq. 10, and the column maxima of
+    //      |diag(s_l) Z_l| (bit patterns of non-negative values order as integers)
+    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int k = tid; k < p.nl; k += kOzPrepThreads) {
+        const int r = p.row0 + k;
+        const bool act = key_bit(key, r);
+        if (!p.df) {
+            double v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (p.l == 1) v[j] = p.Cl[4 * k + j];
+                else v[j] = i64_ldexp(p.P[(4 * i + j) * p.Mp + k], p.eA[k] + p.eBin[4 * i + j] - 48) + p.Cl[4 * k + j];
+                if (act) v[j] = -v[j];
+                if (act) {
+                    const unsigned long long a = (unsigned long long)__double_as_longlong(v[j]) & 0x7FFFFFFFFFFFFFFFull;
+                    mx[j] = a > mx[j] ? a : mx[j];
+                }
+            }
+            double2 *o = reinterpret_cast<double2 *>(out + 4 * (int64_t)r);
+            o[0] = make_double2(v[0], v[1]);
+            o[1] = make_double2(v[2], v[3]);
+        } else {
+            float h[4], lo[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                h[j] = p.Clhi[4 * k + j];
+                lo[j] = p.Cllo[4 * k + j];
+                if (p.l > 1) {
+                    const long long acc = p.P[(4 * i + j) * p.Mp + k];
+                    const int e = p.eA[k] + p.eBin[4 * i + j] - 48;
+                    long long hi_int;
+                    const float ah = i64_to_f32(acc, e, &hi_int);
+                    long long dummy;
+                    const float al = i64_to_f32(acc - hi_int, e, &dummy);
+                    df_add(h[j], lo[j], ah, al);
+                    df_norm(h[j], lo[j]);
+                }
+                if (act) {
+                    h[j] = -h[j];
+                    lo[j] = -lo[j];
+                    const unsigned long long a = __float_as_uint(h[j]) & 0x7FFFFFFFu;
+                    mx[j] = a > mx[j] ? a : mx[j];
+                }
+            }
+            float4 *o = reinterpret_cast<float4 *>(outf + 8 * (int64_t)r);
+            o[0] = make_float4(h[0], h[1], h[2], h[3]);
+            o[1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
-        __syncthreads();
     }
-    const double *Z = out + 4 * (int64_t)p.row0;   // sign-adjusted rows of layer l: an active row is -Z_k
+    __syncthreads();                               // the block reads back the rows it wrote
+    const double *Z = out + 4 * (int64_t)p.row0;
+    const float *Zf = outf + 8 * (int64_t)p.row0;
     if (p.l == p.L) {
-        // a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Cor. 1, Eq. 8)
+        // a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Cor. 1, Eq. 8); an active row is -Z_k
         double f[4] = {0.0, 0.0, 0.0, 0.0};
         for (int k = tid; k < p.nl; k += kOzPrepThreads)
             if (key_bit(key, p.row0 + k)) {
                 const double w = p.w_out[k];
-                const double *r = Z + 4 * (int64_t)k;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) f[j] = fma(-w, r[j], f[j]);
+                for (int j = 0; j < 4; ++j) {
+                    const double r = p.df ? (double)Zf[8 * k + j] + (double)Zf[8 * k + 4 + j] : Z[4 * k + j];
+                    f[j] = fma(-w, r, f[j]);
+                }
             }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -285,21 +398,16 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
         if (tid < 4) {
             double F = tid == 3 ? p.b_out : 0.0;
             for (int w = 0; w < kW; ++w) F += fred[w][tid];
-            out[4 * (int64_t)p.N + tid] = F;
+            if (!p.df) {
+                out[4 * (int64_t)p.N + tid] = F;
+            } else {
+                const float h = (float)F;
+                outf[8 * (int64_t)p.N + tid] = h;
+                outf[8 * (int64_t)p.N + 4 + tid] = (float)(F - (double)h);
+            }
         }
         return;
     }
-    // column maxima of |diag(s_l) Z_l| (bit patterns of non-negative doubles order as integers)
-    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int k = tid; k < p.nl; k += kOzPrepThreads)
-        if (key_bit(key, p.row0 + k)) {
-            const long long *r = reinterpret_cast<const long long *>(Z + 4 * (int64_t)k);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const unsigned long long a = (unsigned long long)r[j] & 0x7FFFFFFFFFFFFFFFull;
-                mx[j] = a > mx[j] ? a : mx[j];
-            }
-        }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -314,9 +422,15 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
     for (int j = 0; j < 4; ++j) {
         unsigned long long m = 0ull;
         for (int w = 0; w < kW; ++w) m = red[w][j] > m ? red[w][j] : m;
-        e[j] = col_exponent(m);
+        if (!p.df) {
+            e[j] = col_exponent(m);
+        } else {
+            // |hi + lo| <= |hi| (1 + 2^-24): one binade of headroom above the largest |hi|
+            const int be = (int)(m >> 23);
+            e[j] = m == 0ull ? 0 : (be == 0 ? -126 : be - 127 + 1);
+        }
     }
-    if (tid < 4) p.eB[4 * i + tid] = e[tid];
+    if (tid < 4) p.eBout[4 * i + tid] = e[tid];
     // digits: two consecutive k per thread, so each plane store is a BF16 pair
     for (int k0 = 2 * tid; k0 < p.Kp; k0 += 2 * kOzPrepThreads) {
         unsigned dig[4][kOzPlanes];          // per column, per plane: bits of the pair
@@ -328,10 +442,11 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
         for (int h = 0; h < 2; ++h) {
             const int k = k0 + h;
             if (k >= p.nl || !key_bit(key, p.row0 + k)) continue;
-            const double *r = Z + 4 * (int64_t)k;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                long long x = fixed62(-r[j], e[j]);       // active: z = -row
+                // active: z = -row
+                long long x = p.df ? -(fixed62f(Zf[8 * k + j], e[j]) + fixed62f(Zf[8 * k + 4 + j], e[j]))
+                                   : fixed62(-Z[4 * k + j], e[j]);
 #pragma unroll
                 for (int t = 0; t < kOzPlanes; ++t) {
                     const int sh = 56 - 6 * t;
@@ -355,17 +470,12 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 // the layer product on the tensor cores
 
 struct OzGemm {
-    const int *eA;                    // row exponents of W_l (n_l)
-    const int *eB;                    // column exponents of the stacked operand
-    const double *Cl;                 // n_l x 4 layer constant
-    const unsigned long long *keys;
-    int kw;
+    long long *P;                     // exact products, column c at P + c Mp (rows 0..Mp-1)
+    int Mp;                           // row stride between digit planes of W_l, and of P
     int64_t n;                        // cells in the batch
-    double *rows;
-    int64_t rstride;
-    int row0, nl, KC;                 // first neuron, width of layer l, K chunks (Kp / 64)
+    int KC;                           // K chunks (Kp / 64) of the whole product
+    int split;                        // K chunks split over gridDim.z CTAs: partial sums added atomically
     int64_t ncols;                    // column stride between digit planes of B
-    int Mp;                           // row stride between digit planes of W_l
     int *err;
 };
 
@@ -377,7 +487,7 @@ struct OzShape {
     static constexpr int kBStage = kOzPlanes * kBPlane;
     static constexpr int kTmemCols = kOzPlanes * kNCol;        // 8 diagonals
     static constexpr int kBars = 2 * AST + 2 * 2 + 2;
-    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 16 * NC + 1024;
+    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 1024;
     static_assert(kTmemCols == 256 || kTmemCols == 512, "TMEM allocation must be a power of two");
     static_assert(kBPlane % 1024 == 0, "B plane tiles must stay 1024-byte aligned");
 };
@@ -401,11 +511,13 @@ __global__ void __launch_bounds__(192, 1)
     unsigned char *tail = gbase + (bars - base) + 8 * S::kBars;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tail);
     volatile int *abort = reinterpret_cast<volatile int *>(tail + 4);
-    int *eBs = reinterpret_cast<int *>(tail + 16);                 // 4 NC column exponents
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kOzM;
     const int64_t col0 = (int64_t)blockIdx.y * S::kNCol;
+    // K chunks [kc0, kc0 + nkc) of this CTA (split-K over gridDim.z)
+    const int kc0 = (int)((int64_t)g.KC * blockIdx.z / gridDim.z);
+    const int nkc = (int)((int64_t)g.KC * (blockIdx.z + 1) / gridDim.z) - kc0;
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < AST; ++q) { mbar_init(afull(q), 1); mbar_init(aempty(q), 1); }
@@ -436,9 +548,9 @@ __global__ void __launch_bounds__(192, 1)
             armedB[0] = armedB[1] = 0;
             int ai = 0;
             bool ok = true;
-            for (int kc = 0; kc < g.KC && ok; ++kc) {
-                const int bs = kc & 1;
-                if (kc >= 2 && !mbar_wait(bempty(bs), ((kc >> 1) - 1) & 1, abort, g.err)) { ok = false; break; }
+            for (int it = 0; it < nkc && ok; ++it) {
+                const int kc = kc0 + it, bs = it & 1;
+                if (it >= 2 && !mbar_wait(bempty(bs), ((it >> 1) - 1) & 1, abort, g.err)) { ok = false; break; }
                 mbar_expect_tx(bfull(bs), S::kBStage);
                 ++armedB[bs];
                 for (int t = 0; t < kOzPlanes; ++t)
@@ -467,9 +579,9 @@ __global__ void __launch_bounds__(192, 1)
             constexpr uint32_t idesc = umma_idesc_bf16(kOzM, S::kNCol);
             int ai = 0;
             bool ok = true;
-            for (int kc = 0; kc < g.KC && ok; ++kc) {
-                const int bs = kc & 1;
-                if (!mbar_wait(bfull(bs), (kc >> 1) & 1, abort, g.err)) { ok = false; break; }
+            for (int it = 0; it < nkc && ok; ++it) {
+                const int bs = it & 1;
+                if (!mbar_wait(bfull(bs), (it >> 1) & 1, abort, g.err)) { ok = false; break; }
                 for (int s = 0; s < kOzPlanes; ++s, ++ai) {
                     const int q = ai % AST;
                     if (!mbar_wait(afull(q), (ai / AST) & 1, abort, g.err)) { ok = false; break; }
@@ -481,7 +593,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                         for (int kk = 0; kk < kOzBK / 16; ++kk)
                             umma_bf16(d, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
-                                      (kc | s | kk) != 0 ? 1u : 0u);
+                                      (it | s | kk) != 0 ? 1u : 0u);
                     }
                     umma_commit(aempty(q));          // the A stage is free once these products finish
                 }
@@ -495,28 +607,11 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row of W_l per thread.
-        //      While the products run it fetches what it needs besides the accumulators: the
-        //      cells' column exponents (shared memory), this row's neuron state in each cell (a
-        //      bit mask), C_l and the row exponent.
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row of W_l per thread,
+        //      and writes the exact product of each column as a 64-bit integer at scale 2^-48
+        //      (the prep kernel applies the exponents, C_l and the sign)
         const int quarter = warp & 3;
-        const int r = quarter * 32 + lane;
-        const int grow = m0 + r;
-        const bool live_row = grow < g.nl;
-        const int et = threadIdx.x - 64;                 // 0..127 over the epilogue warps
-        const int64_t cell0 = col0 / 4;
-        if (et < 4 * NC) eBs[et] = cell0 + et / 4 < g.n ? g.eB[col0 + et] : 0;
-        unsigned act = 0u;
-        double2 C01 = make_double2(0.0, 0.0), C23 = make_double2(0.0, 0.0);
-        int eA = 0;
-        if (live_row) {
-            for (int cc = 0; cc < NC; ++cc)
-                if (cell0 + cc < g.n && key_bit(g.keys + (cell0 + cc) * g.kw, g.row0 + grow)) act |= 1u << cc;
-            C01 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow];
-            C23 = reinterpret_cast<const double2 *>(g.Cl)[2 * grow + 1];
-            eA = g.eA[grow];
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // the epilogue warps only
+        const int grow = m0 + quarter * 32 + lane;
         if (mbar_wait(accfull, 0, abort, g.err)) {
             tc_fence_after();
             const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -527,29 +622,18 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                 for (int dg = 0; dg < kOzPlanes; ++dg) tmem_ld8_nowait(trow + (uint32_t)(dg * S::kNCol + 4 * c2), v[dg]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                long long acc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     long long a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
 #pragma unroll
                     for (int dg = 1; dg < kOzPlanes - 1; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
-                    acc[j] = a + (long long)((__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j])) + 32) >> 6);
-                }
-                // acc 2^(eA + eB - 48) + C_l, signed by the neuron's state
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int cc = c2 + h;
-                    const int64_t cell = cell0 + cc;
-                    if (!live_row || cell >= g.n) continue;
-                    const int *eB = eBs + 4 * cc;
-                    const double x = i64_ldexp(acc[4 * h + 0], eA + eB[0] - 48) + C01.x;
-                    const double y = i64_ldexp(acc[4 * h + 1], eA + eB[1] - 48) + C01.y;
-                    const double z = i64_ldexp(acc[4 * h + 2], eA + eB[2] - 48) + C23.x;
-                    const double w = i64_ldexp(acc[4 * h + 3], eA + eB[3] - 48) + C23.y;
-                    const bool neg = (act >> cc) & 1u;
-                    double2 *o = reinterpret_cast<double2 *>(g.rows + cell * g.rstride + 4 * (int64_t)(g.row0 + grow));
-                    o[0] = neg ? make_double2(-x, -y) : make_double2(x, y);
-                    o[1] = neg ? make_double2(-z, -w) : make_double2(z, w);
+                    a += (long long)((__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j])) + 32) >> 6);
+                    const int64_t col = col0 + 4 * c2 + j;
+                    if (col < 4 * g.n) {
+                        long long *dst = g.P + col * g.Mp + grow;
+                        if (g.split) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
+                        else *dst = a;
+                    }
                 }
             }
         }
@@ -596,12 +680,12 @@ cudaError_t encode_map(CUtensorMap *m, const void *ptr, int64_t Kp, int64_t rows
 
 template <int NC, int AST>
 cudaError_t launch_gemm(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzGemm &g, int Mp, int64_t ncols_used,
-                        cudaStream_t st)
+                        int split, cudaStream_t st)
 {
     using S = OzShape<NC, AST>;
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<NC, AST>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(Mp / kOzM, (unsigned)((ncols_used + S::kNCol - 1) / S::kNCol));
+    const dim3 grid(Mp / kOzM, (unsigned)((ncols_used + S::kNCol - 1) / S::kNCol), (unsigned)split);
     oz_gemm_kernel<NC, AST><<<grid, 192, S::kSmem, st>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
@@ -660,59 +744,66 @@ int64_t oz_scratch_elems(int64_t batch_cells, int max_kp)
     return (int64_t)kOzPlanes * 4 * batch_cells * max_kp;
 }
 
-cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, double *rows,
-                       const OzScratch &scr, int tile_cells, cudaStream_t st)
+cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, void *rows, bool df,
+                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st)
 {
     const int64_t rstride = 4 * (int64_t)(net.N + 1);
     const int64_t ncols = 4 * scr.batch_cells;
+    const int per_sm = tile_cells == 8 ? 2 : 1;        // resident tiles per SM (shared memory)
     for (int64_t b0 = 0; b0 < n; b0 += scr.batch_cells) {
         const int64_t nb = std::min<int64_t>(scr.batch_cells, n - b0);
         OzPrep p{};
         p.keys = keys + b0 * kw;
         p.kw = kw;
         p.n = nb;
-        p.rows = rows + b0 * rstride;
+        p.rows = reinterpret_cast<double *>(rows) + b0 * rstride;
         p.rstride = rstride;
+        p.df = df ? 1 : 0;
         p.L = net.L;
         p.N = net.N;
-        p.Cl1 = net.Cl[1];
         p.w_out = net.w_out;
         p.b_out = net.b_out;
         p.B = scr.B;
-        p.eB = scr.eB;
+        p.P = scr.P;
         p.ncols = ncols;
-        const unsigned pgrid = (unsigned)nb;
         for (int l = 1; l <= net.L; ++l) {
+            p.eBin = scr.eB[l & 1];                    // written by the prep of layer l - 1
+            p.eBout = scr.eB[(l + 1) & 1];
             if (l >= 2) {
                 CUtensorMap tmB;
                 const int Kp = oz_kp(net.width[l - 1]);
                 cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tile_cells);
                 if (e != cudaSuccess) return e;
                 OzGemm g{};
-                g.eA = net.eA[l];
-                g.eB = scr.eB;
-                g.Cl = net.Cl[l];
-                g.keys = p.keys;
-                g.kw = kw;
+                g.P = scr.P;
+                g.Mp = oz_mp(net.width[l]);
                 g.n = nb;
-                g.rows = p.rows;
-                g.rstride = rstride;
-                g.row0 = net.row0[l];
-                g.nl = net.width[l];
                 g.KC = Kp / kOzBK;
                 g.ncols = ncols;
-                g.Mp = oz_mp(net.width[l]);
                 g.err = scr.err;
+                // a batch too small to fill the SMs splits K over more CTAs (exact integer sums)
+                const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tile_cells - 1) / (4 * tile_cells));
+                int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
+                g.split = split > 1 ? 1 : 0;
+                if (g.split) {
+                    e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * 4 * nb * g.Mp, st);
+                    if (e != cudaSuccess) return e;
+                }
                 const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
-                e = tile_cells == 8 ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, st)
-                                    : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, st);
+                e = tile_cells == 8 ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                                    : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
                 if (e != cudaSuccess) return e;
+                p.Mp = g.Mp;
+                p.eA = net.eA[l];
             }
             p.l = l;
             p.nl = net.width[l];
             p.row0 = net.row0[l];
+            p.Cl = net.Cl[l];
+            p.Clhi = net.Clhi[l];
+            p.Cllo = net.Cllo[l];
             p.Kp = oz_kp(net.width[l]);
-            oz_prep_kernel<<<pgrid, kOzPrepThreads, 0, st>>>(p);
+            oz_prep_kernel<<<(unsigned)nb, kOzPrepThreads, 0, st>>>(p);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
