@@ -446,8 +446,8 @@ def decoder_leg(dev, n_cells=60000, reps=2):
     hidden layer 4 (N = 4096), one seed ray along +x: the first n_cells cells of its march
     (the whole mesh exceeds 4e6 cells), timed by am_march's CUDA events, seeding outside.
     Plain FP64 (compose and clip in one persistent kernel) against the sliced path (the compose
-    of each level's cells on the tensor cores into device memory, then the FP64 clip reading
-    those rows).  Rooflines of the two sliced kernels: the compose's issued tensor flops (36
+    of each level's cells on the tensor cores into device memory as FP32 pairs, then the clip
+    reading those rows with certified FP32 sign tests, FP64 for the close calls).  Rooflines of the two sliced kernels: the compose's issued tensor flops (36
     digit-plane products per layer) and the clip's algorithmic bytes (its rows, (N + 1) x 32 B
     per cell, plus the key and the face record) over their own device time."""
     import paper_2106_10031_gb300 as am
