@@ -50,6 +50,7 @@ constexpr int kNear = 32;         // rows clipped by warp 0 before the full chec
 constexpr int kPicks = kNear / kNW;   // candidates each warp contributes
 static_assert(kT % 32 == 0 && kNW <= 32 && kNear % kNW == 0, "block shape");
 constexpr int kMaxFix = 8;        // check / fix-up rounds
+constexpr int kThreadPushWords = 8;   // keys up to this many 64-bit words are pushed by one thread per edge
 constexpr float kU = 5.9604645e-8f;            // 2^-24
 constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
 constexpr double kVertexTol = 1e-5;            // largest vertex error bound (relative) kept from kDF
@@ -1161,12 +1162,24 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         }
         const unsigned long long h = __ldcg(ar.hash + cell);
         const int nid = __ldcg(ar.net + cell);
-        for (int i = tid; i < m; i += kT) {
-            const int e = s.pe[buf][i];
-            if (e >= N) continue;
-            const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
-            insert_neighbor(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
-                            (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+        if (ar.kw <= kThreadPushWords) {
+            // narrow keys: one thread per edge
+            for (int i = tid; i < m; i += kT) {
+                const int e = s.pe[buf][i];
+                if (e >= N) continue;
+                const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
+                insert_neighbor(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+                                (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+            }
+        } else {
+            // wide keys: one warp per edge, the key words split over the lanes
+            for (int i = wid; i < m; i += kNW) {
+                const int e = s.pe[buf][i];
+                if (e >= N) continue;
+                const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
+                insert_neighbor_warp(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+                                     (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+            }
         }
     }
     if (emit && tid < m) __threadfence();     // the face and the pushes of this thread
