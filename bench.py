@@ -65,8 +65,8 @@ HBM_PEAK_GBS = _measured_hbm_peak()
 
 # DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
 # workload) from the committed ncu capture, valid while the kernel source is the one captured
-TRAFFIC_CAPTURE = {"sha256_prefix": "c7193a7b44c495bf", "precision": "mixed", "candidates": "learned",
-                   "bytes": 2.959872e6 + 0.520704e6}
+TRAFFIC_CAPTURE = {"sha256_prefix": "3933f98dc34e45d5", "precision": "mixed", "candidates": "learned",
+                   "bytes": 2.954752e6 + 0.512768e6}
 
 
 def captured_traffic(precision, candidates):
