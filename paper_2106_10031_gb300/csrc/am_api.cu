@@ -204,8 +204,10 @@ OzNet oz_view(const NetHost &nh)
 }
 
 // rows (n x (N + 1) x 4) of n cells of one net on the tensor cores, asynchronous on the stream
-am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, void *d_rows,
-                               bool df = false)
+// d_keys: cell i's key at d_keys + i * key_stride words (the net's own width for am_compose's
+// caller-packed keys, the arena's width inside the march)
+am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int key_stride, int64_t n,
+                               void *d_rows, bool df = false)
 {
     const NetHost &nh = ctx->nets[net_id];
     if (!nh.oz_ok)
@@ -213,7 +215,7 @@ am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long
     am_status s = ensure_oz_scratch(ctx);
     if (s != AM_OK) return s;
     const int tile = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
-    CU(oz_compose(oz_view(nh), d_keys, nh.dev.kw, n, d_rows, df, ctx->oz, tile, ctx->sm_count, ctx->stream));
+    CU(oz_compose(oz_view(nh), d_keys, key_stride, n, d_rows, df, ctx->oz, tile, ctx->sm_count, ctx->stream));
     const int64_t batches = (n + ctx->oz.batch_cells - 1) / ctx->oz.batch_cells;
     ctx->stats.kernel_launches += (2 * (int64_t)nh.dev.L - 1) * batches;
     return AM_OK;
@@ -234,7 +236,7 @@ am_status sliced_check(am_ctx *ctx)
 
 am_status sliced_compose(am_ctx *ctx, int net_id, const unsigned long long *d_keys, int64_t n, double *d_rows)
 {
-    am_status s = sliced_compose_async(ctx, net_id, d_keys, n, d_rows);
+    am_status s = sliced_compose_async(ctx, net_id, d_keys, ctx->nets[net_id].dev.kw, n, d_rows);
     return s != AM_OK ? s : sliced_check(ctx);
 }
 
@@ -861,7 +863,8 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
                 for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells) {
                     const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
                     CU(cudaEventRecord(ctx->evc0, ctx->stream));
-                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, c1 - c0, ctx->oz_rows, true);
+                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, ctx->ar.kw, c1 - c0, ctx->oz_rows,
+                                             true);
                     if (s != AM_OK) return s;
                     CU(cudaEventRecord(ctx->evc1, ctx->stream));
                     ma.begin = c0;
@@ -1005,7 +1008,7 @@ am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, i
         std::vector<float> ms(reps);
         for (int r = 0; r < reps; ++r) {
             CU(cudaEventRecord(ctx->evk0, ctx->stream));
-            s = sliced_compose_async(ctx, net_id, keys, n, d_rows);
+            s = sliced_compose_async(ctx, net_id, keys, ctx->nets[net_id].dev.kw, n, d_rows);
             if (s != AM_OK) { ctx->oz_tile_cells = saved; return s; }
             CU(cudaEventRecord(ctx->evk1, ctx->stream));
             CU(cudaEventSynchronize(ctx->evk1));

@@ -139,6 +139,18 @@ def test_seed_matches_oracle(oracle_mod, am):
         assert parity._key_int(mesh.face_keys[0]) == ref.seeds[0][0]
 
 
+def test_sliced_march_with_a_wider_context(oracle_mod, am):
+    # the context's key width (max_neurons) larger than the net's: the march's cell keys are
+    # strided by the context, the compose's by the net
+    mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
+    net, ref = oracle_mod.mesh_from_rays(mlp, np.zeros((1, 3)), RAY)
+    with am.Mesher(max_cells=1 << 17, max_neurons=512, max_width=64) as m:
+        nid = m.load_mlp(mlp)
+        m.seed(nid, np.zeros((1, 3)), RAY)
+        m.march(precision="sliced")
+        parity.compare(ref, m.get_mesh(nid), mlp.N, rtol=1e-9)
+
+
 def test_sliced_march_needs_one_net(am):
     # the tensor-core compose works on batches of one net's cells
     with am.Mesher(max_cells=1 << 12, max_neurons=256, max_width=64) as m:
