@@ -92,6 +92,8 @@ def parse():
     p.add_argument("--no-compare", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--learned-only", action="store_true",
+                   help="run only the 3-[256]x8-1 learned-proposal leg and print its JSON")
     p.add_argument("--decoder-only", action="store_true",
                    help="run only the decoder march leg (FP64 vs sliced tensor-core compose) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
@@ -488,6 +490,55 @@ def decoder_leg(dev, n_cells=60000, reps=2):
     return out
 
 
+def learned_leg(dev, n_cells=60000, reps=2):
+    """The learned-proposal workload: 3 -> [256] x 8 -> 1 (geometric init, sigma 0.05, seed 5;
+    N = 2048) with a proposal 15 -> 256 -> 256 -> 2048 (BF16 operands, FP32 accumulation),
+    trained before timing on the plain method's mesh of a nearby checkpoint of the net (first
+    n_cells cells).  The first n_cells cells of the net's own march, one seed ray along +x,
+    timed by am_march's CUDA events: the plain FP64 method (every cutting row clipped) against
+    mixed precision (compose on the tensor cores, certified clip) with learned candidates, and
+    the other candidate rules for context.  Every configuration's mesh is exact: the all-row
+    check corrects any face the candidates got wrong."""
+    import paper_2106_10031_gb300 as am
+    from synth import proposal_target_net, sibling
+    mlp = proposal_target_net()
+    o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
+    out = {"workload": f"3-[256]x8-1 geometric init (seed 5, sigma 0.05), proposal 15-256-256-2048; "
+                       f"first {n_cells} cells of the march"}
+    with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=2048, max_width=256) as m:
+        sid = m.load_mlp(sibling(mlp, seed=99))
+        m.seed(sid, o, d)
+        m.march(precision="fp64", candidates="none", max_cells=n_cells)
+        X, Y = m.proposal_samples(sid, max_samples=120000)
+        m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
+        t0 = time.perf_counter()
+        losses = m.proposal_train(X, Y, batch=1024, steps=3000, lr=2e-3)
+        out["training"] = {"samples": int(X.shape[0]), "steps": 3000, "train_s": time.perf_counter() - t0,
+                           "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean())}
+        del X, Y
+        m.reset()
+        m.release_nets()
+        nid = m.load_mlp(mlp)
+        out["autotune"] = m.autotune_compose(nid, n=4096, reps=3)
+        for name, prec, cand in (("plain_fp64", "fp64", "none"), ("fp64_learned", "fp64", "learned"),
+                                 ("sliced_learned", "sliced", "learned"), ("fp64_nearest", "fp64", "nearest"),
+                                 ("sliced_nearest", "sliced", "nearest")):
+            runs = []
+            for _ in range(reps + 1):                   # the first run warms up
+                m.reset()
+                m.seed(nid, o, d)
+                m.march(precision=prec, candidates=cand, max_cells=n_cells)
+                runs.append(m.stats())
+            st = min(runs[1:], key=lambda x: x["ms_march"])
+            out[name] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
+                         "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
+                         "corrected_frac": st["fixups"] / max(1, st["cells"]), "degenerate": st["degenerate"]}
+        base = out["plain_fp64"]["faces_per_s"]
+        for k in ("fp64_learned", "sliced_learned", "fp64_nearest", "sliced_nearest"):
+            out[k]["speedup_vs_plain_fp64"] = out[k]["faces_per_s"] / base
+    return out
+
+
 def train_proposal(m, mlp, o, d):
     """The learned proposal for the workload: trained on the plain method's mesh (full clip,
     FP64) of a nearby checkpoint of the net (every weight moved by N(0, 0.005^2)), outside
@@ -577,6 +628,7 @@ def run_ours(args, dist):
         legs["proposal_training"] = train
         legs["compose"] = compose_leg(dev)
         legs["decoder"] = decoder_leg(dev)
+        legs["learned_256x8"] = learned_leg(dev)
     e2e = None
     if not args.no_e2e:
         prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
@@ -639,6 +691,10 @@ def main():
         if args.decoder_only:
             if dist.rank == 0:
                 print(json.dumps({"leg": "decoder", **decoder_leg(dist.local)}))
+            return 0
+        if args.learned_only:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "learned_256x8", **learned_leg(dist.local)}))
             return 0
         return run_ours(args, dist)
     finally:

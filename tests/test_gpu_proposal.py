@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import proposal as P
-from synth import sibling, sphere_net, tiny_net
+from synth import proposal_target_net, sibling, sphere_net, tiny_net
 from tests import parity
 
 pytestmark = pytest.mark.gpu
@@ -216,3 +216,42 @@ def test_learned_march_is_exact_and_clips_less(oracle_mod, am, torch, precision,
     assert lrn["cuts"] / lrn["cells"] < 0.25 * plain["cuts"] / plain["cells"]
     assert lrn["fixups"] < plain["fixups"]
     assert lrn["ms_march"] < plain["ms_march"]
+
+
+def test_learned_256x8_with_tensor_core_rows(oracle_mod, am, torch):
+    # The learned-proposal workload: 3 -> [256] x 8 -> 1 (N = 2048), a proposal with 2048
+    # outputs trained on the plain method's mesh of a nearby checkpoint, the compose on the
+    # tensor cores (sliced), the first 20000 cells.  The faces are the plain FP64 method's
+    # (the same edge cycles and vertices), sampled faces are the oracle's.
+    mlp = proposal_target_net()
+    o, d = np.zeros((1, 3)), X_RAY
+    n = 20000
+    with am.Mesher(max_cells=1 << 16, max_neurons=2048, max_width=256) as m:
+        sid = m.load_mlp(sibling(mlp, seed=99))
+        m.seed(sid, o, d)
+        m.march(precision="fp64", candidates="none", max_cells=n)
+        X, Y = m.proposal_samples(sid, max_samples=60000)
+        m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
+        losses = m.proposal_train(X, Y, batch=1024, steps=1500, lr=2e-3)
+        assert losses[-50:].mean() < losses[:5].mean()
+        m.reset()
+        m.release_nets()
+        nid = m.load_mlp(mlp)
+        meshes, stats = {}, {}
+        for prec, cand in (("fp64", "none"), ("sliced", "learned")):
+            m.reset()
+            m.seed(nid, o, d)
+            m.march(precision=prec, candidates=cand, max_cells=n)
+            meshes[prec], stats[prec] = m.get_mesh(nid), m.stats()
+    # a truncated march keeps the first n cells in discovery order, which differs between the
+    # schedules within the last level: compare the faces both meshes hold
+    plain, learned = parity.gpu_faces(meshes["fp64"]), parity.gpu_faces(meshes["sliced"])
+    common = set(plain) & set(learned)
+    assert len(common) > 0.9 * n
+    assert all(plain[k][0] == learned[k][0] for k in common)
+    assert max(np.abs(plain[k][1] - learned[k][1]).max() for k in common) < 1e-9
+    assert stats["sliced"]["degenerate"] == 0
+    print(f"\n256x8: plain FP64 {stats['fp64']['ms_march']:.1f} ms ({stats['fp64']['cuts'] / n:.0f} cuts/cell), "
+          f"sliced + learned {stats['sliced']['ms_march']:.1f} ms ({stats['sliced']['cuts'] / n:.1f} cuts/cell, "
+          f"corrected {stats['sliced']['fixups'] / n:.2f})")
+    parity.compare_sampled(oracle_mod, oracle_mod.OracleNet(mlp), meshes["sliced"], mlp.N, 16, 1e-9, 1.5)
