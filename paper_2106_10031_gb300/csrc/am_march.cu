@@ -976,9 +976,24 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     // ---- a4: warp 0 cuts the square with the candidates, nearest cutting row first.  A row
     // that holds on the polygon holds on every later (smaller) one, so it retires at once.
     if (wid == 0) {
-        const float d = s.near_dw[lane];
+        float d = s.near_dw[lane];
         const int k = s.near_w[lane];
         bool live = k >= 0 && d < 3.0e38f;
+        if (learned && live) {
+            // the proposal chose the rows; they are cut nearest first, as the geometric rule's
+            // (the entry plane passes through the entry point, so it still comes first)
+            const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
+                        pz = __ldcg(ar.entry_pt + cell * 3 + 2);
+            float r[4];
+            if (M == kFP64) {
+                double r64[4];
+                fetch_row<double, M>(s, k, r64);
+                r[0] = (float)r64[0]; r[1] = (float)r64[1]; r[2] = (float)r64[2]; r[3] = (float)r64[3];
+            } else {
+                fetch_row<float, M>(s, k, r);
+            }
+            d = fabsf(r[0] * px + r[1] * py + r[2] * pz + r[3]) * s.rinv[k];
+        }
         // order-preserving unsigned image of the distance (scores may be negative)
         const unsigned du = __float_as_uint(d);
         const unsigned key = (du & 0x80000000u) ? ~du : (du | 0x80000000u);
