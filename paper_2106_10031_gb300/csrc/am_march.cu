@@ -727,8 +727,8 @@ __device__ __forceinline__ void gemv_bf16x2(const __nv_bfloat16 *wt, int n_pairs
         const int j0 = g * n_in / G, j1 = (g + 1) * n_in / G;
         float a0 = 0.0f, a1 = 0.0f;
         const __nv_bfloat162 *wp = w + pr;
-#pragma unroll 8
-        for (int j = j0; j < j1; ++j) {
+#pragma unroll 32
+        for (int j = j0; j < j1; ++j) {         // 32 weight loads in flight: the weights stream from L2
             const float2 wf = __bfloat1622float2(wp[(size_t)j * n_pairs]);
             const float xj = x[j];
             a0 = fmaf(wf.x, xj, a0);
