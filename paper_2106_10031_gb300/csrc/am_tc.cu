@@ -154,6 +154,61 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
         : "memory");
 }
 
+// The same product with the A operand kept in the tensor core's collector buffer: kind 1 reads A
+// from shared memory and keeps it (fill), 2 reuses the kept A (use), 3 reuses it for the last
+// time (lastuse).  Consecutive products with one A tile read it from shared memory once.
+template <int KIND>
+__device__ __forceinline__ void umma_bf16_collect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                  uint32_t accumulate)
+{
+    if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (KIND == 2) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+// The products of one W_l plane s (its A tile at adesc) with the operand planes t = 0 .. NT - 1
+// (B tiles bplane bytes apart from bdesc) into the accumulators of diagonals s + t, for the 4
+// K = 16 steps of a staged chunk.  Per K step the A slice is read into the collector once and
+// reused by the NT products.  Descriptor start addresses advance in 16-byte units.
+template <int NT, int NCOL, int BPLANE>
+__device__ __forceinline__ void issue_plane(uint32_t tmem, int s, uint64_t adesc, uint64_t bdesc, uint32_t acc0)
+{
+    constexpr uint32_t idesc = umma_idesc_bf16(128, NCOL);
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t ad = adesc + (uint64_t)(2 * kk);
+        const uint32_t acc = (acc0 | kk) != 0 ? 1u : 0u;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const uint64_t bd = bdesc + (uint64_t)((t * BPLANE + 32 * kk) >> 4);
+            const uint32_t d = tmem + (uint32_t)((s + t) * NCOL);
+            if constexpr (NT == 1) umma_bf16(d, ad, bd, idesc, acc);
+            else if (t == 0) umma_bf16_collect<1>(d, ad, bd, idesc, acc);
+            else if (t + 1 < NT) umma_bf16_collect<2>(d, ad, bd, idesc, acc);
+            else umma_bf16_collect<3>(d, ad, bd, idesc, acc);
+        }
+    }
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -576,7 +631,6 @@ __global__ void __launch_bounds__(192, 1)
         // ---- MMA issuer: plane s of W_l times planes t = 0..7-s of the operand, into the
         //      accumulator of diagonal s + t
         if (lane == 0) {
-            constexpr uint32_t idesc = umma_idesc_bf16(kOzM, S::kNCol);
             int ai = 0;
             bool ok = true;
             for (int it = 0; it < nkc && ok; ++it) {
@@ -587,13 +641,17 @@ __global__ void __launch_bounds__(192, 1)
                     if (!mbar_wait(afull(q), (ai / AST) & 1, abort, g.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = sA + q * S::kATile;
-                    for (int t = 0; t + s < kOzPlanes; ++t) {
-                        const uint32_t b0 = sB + bs * S::kBStage + t * S::kBPlane;
-                        const uint32_t d = tmem + (uint32_t)((s + t) * S::kNCol);
-#pragma unroll
-                        for (int kk = 0; kk < kOzBK / 16; ++kk)
-                            umma_bf16(d, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
-                                      (it | s | kk) != 0 ? 1u : 0u);
+                    const uint64_t adesc = sw128_desc(a0), bdesc = sw128_desc(sB + bs * S::kBStage);
+                    const uint32_t acc0 = (it | s) != 0 ? 1u : 0u;
+                    switch (kOzPlanes - s) {                  // operand planes t = 0 .. 7 - s
+                    case 8: issue_plane<8, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 7: issue_plane<7, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 6: issue_plane<6, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 5: issue_plane<5, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 4: issue_plane<4, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 3: issue_plane<3, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    case 2: issue_plane<2, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
+                    default: issue_plane<1, S::kNCol, S::kBPlane>(tmem, s, adesc, bdesc, acc0); break;
                     }
                     umma_commit(aempty(q));          // the A stage is free once these products finish
                 }
