@@ -241,8 +241,10 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
  * Kernels with more than one valid launch shape read it from the context.  am_set_tuning sets
  * it by hand; am_autotune_compose times every candidate and keeps the fastest. */
 typedef struct {
-    int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 16 (UMMA N = 64,
-                                 one tile per SM) or 8 (N = 32, two tiles per SM); 0 = default 16 */
+    int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 32 (UMMA N = 128,
+                                 the 8 diagonals in two passes of 4), 16 (N = 64, all 8 diagonals
+                                 at once, one tile per SM) or 8 (N = 32, two tiles per SM);
+                                 0 = default 16 */
 } am_tuning;
 
 /* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */

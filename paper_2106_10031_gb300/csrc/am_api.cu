@@ -176,6 +176,7 @@ am_status ensure_oz_scratch(am_ctx *ctx)
     CU(cudaMalloc(&z.eB[0], sizeof(int) * 4 * z.batch_cells));
     CU(cudaMalloc(&z.eB[1], sizeof(int) * 4 * z.batch_cells));
     CU(cudaMalloc(&z.P, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width)));
+    CU(cudaMalloc(&z.Q, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width)));
     CU(cudaMalloc(&z.err, sizeof(int)));
     CU(cudaMemsetAsync(z.err, 0, sizeof(int), ctx->stream));
     return AM_OK;
@@ -350,7 +351,7 @@ void am_destroy(am_ctx *ctx)
         if (n.ozblob) cudaFree(n.ozblob);
     }
     if (ctx->oz.B) cudaFree(ctx->oz.B);
-    for (void *b : {(void *)ctx->oz.eB[0], (void *)ctx->oz.eB[1], (void *)ctx->oz.P})
+    for (void *b : {(void *)ctx->oz.eB[0], (void *)ctx->oz.eB[1], (void *)ctx->oz.P, (void *)ctx->oz.Q})
         if (b) cudaFree(b);
     if (ctx->oz.err) cudaFree(ctx->oz.err);
     if (ctx->oz_rows) cudaFree(ctx->oz_rows);

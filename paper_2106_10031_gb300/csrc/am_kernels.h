@@ -148,7 +148,8 @@ struct OzNet {
 struct OzScratch {
     __nv_bfloat16 *B = nullptr;   // kOzDigits x 4 batch_cells x Kp digit planes of the stacked operand
     int *eB[2] = {nullptr, nullptr};   // 4 batch_cells column exponents, for alternate layers
-    long long *P = nullptr;       // 4 batch_cells x Mp exact products of one layer (64-bit integers)
+    long long *P = nullptr;       // 4 batch_cells x Mp exact products of one layer (64-bit integers) ...
+    long long *Q = nullptr;       // ... and the raw sums of its last diagonal, rounded once by the prep
     int *err = nullptr;           // set to 1 by a kernel whose pipeline wait timed out
     int64_t batch_cells = 0;      // multiple of 16
 };

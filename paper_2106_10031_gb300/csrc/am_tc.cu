@@ -291,7 +291,8 @@ struct OzPrep {
     int df;
     int l, L, N;
     int nl, row0;                     // width and first neuron of layer l
-    const long long *P;               // l >= 2: the exact products of layer l, column c at P + c Mp
+    const long long *P, *Q;           // l >= 2: the exact products of layer l (diagonals 0..6, and the raw
+                                      // sum of diagonal 7), column c at P + c Mp
     int Mp;
     const int *eA;                    // l >= 2: row exponents of W_l
     const int *eBin;                  // l >= 2: column exponents of layer l's right operand
@@ -367,6 +368,15 @@ __device__ __forceinline__ long long fixed62f(float x, int e)
     return (u >> 31) ? -v : v;
 }
 
+// The exact product of column 4 i + j, row k at scale 2^-48: diagonals 0..6 plus diagonal 7
+// rounded to the scale, once, after every split of K has added in (so the rows do not depend on
+// the launch shape)
+__device__ __forceinline__ long long oz_product(const OzPrep &p, int64_t i, int j, int k)
+{
+    const int64_t o = (4 * i + j) * p.Mp + k;
+    return p.P[o] + ((p.Q[o] + 32) >> 6);
+}
+
 // One block of kOzPrepThreads per cell: the rows of layer l (from the exact products, or the
 // cell-independent C_1 at layer 1), then the digit planes of diag(s_l) Z_l for layer l + 1, or
 // a_F after the last layer.
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (p.l == 1) v[j] = p.Cl[4 * k + j];
-                else v[j] = i64_ldexp(p.P[(4 * i + j) * p.Mp + k], p.eA[k] + p.eBin[4 * i + j] - 48) + p.Cl[4 * k + j];
+                else v[j] = i64_ldexp(oz_product(p, i, j, k), p.eA[k] + p.eBin[4 * i + j] - 48) + p.Cl[4 * k + j];
                 if (act) v[j] = -v[j];
                 if (act) {
                     const unsigned long long a = (unsigned long long)__double_as_longlong(v[j]) & 0x7FFFFFFFFFFFFFFFull;
@@ -408,7 +418,7 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                 h[j] = p.Clhi[4 * k + j];
                 lo[j] = p.Cllo[4 * k + j];
                 if (p.l > 1) {
-                    const long long acc = p.P[(4 * i + j) * p.Mp + k];
+                    const long long acc = oz_product(p, i, j, k);
                     const int e = p.eA[k] + p.eBin[4 * i + j] - 48;
                     long long hi_int;
                     const float ah = i64_to_f32(acc, e, &hi_int);
@@ -525,7 +535,8 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 // the layer product on the tensor cores
 
 struct OzGemm {
-    long long *P;                     // exact products, column c at P + c Mp (rows 0..Mp-1)
+    long long *P;                     // exact products of diagonals 0..6, column c at P + c Mp (rows 0..Mp-1)
+    long long *Q;                     // the raw sum of diagonal 7, same layout (rounded once, by the prep)
     int Mp;                           // row stride between digit planes of W_l, and of P
     int64_t n;                        // cells in the batch
     int KC;                           // K chunks (Kp / 64) of the whole product
@@ -685,14 +696,275 @@ __global__ void __launch_bounds__(192, 1)
                     long long a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
 #pragma unroll
                     for (int dg = 1; dg < kOzPlanes - 1; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
-                    a += (long long)((__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j])) + 32) >> 6);
+                    const long long a7 = (long long)__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j]));
                     const int64_t col = col0 + 4 * c2 + j;
                     if (col < 4 * g.n) {
-                        long long *dst = g.P + col * g.Mp + grow;
-                        if (g.split) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
-                        else *dst = a;
+                        long long *dst = g.P + col * g.Mp + grow, *dq = g.Q + col * g.Mp + grow;
+                        if (g.split) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
+                            atomicAdd(reinterpret_cast<unsigned long long *>(dq), (unsigned long long)a7);
+                        } else {
+                            *dst = a;
+                            *dq = a7;
+                        }
                     }
                 }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// the wide tile: 32 cells (UMMA N = 128), the diagonals in two passes
+//
+// A stream of M = 128 products from one CTA costs at least about 71 clock cycles per
+// instruction for any N <= 128 (measured on this part), so N = 64 tiles reach at most 45 % of
+// the tensor peak and N = 128 tiles 90 %.  All 8 diagonal accumulators at N = 128 would need
+// 1024 TMEM columns, so this tile keeps 4 at a time: pass 1 accumulates diagonals 0..3, the
+// epilogue drains them (exact 64-bit integers), pass 2 accumulates diagonals 4..7 into the same
+// columns.  Pass 2 runs as two sweeps over K, operand planes 0..3 then 4..7, so that a B stage
+// holds 4 planes (64 KB) and two stages fit beside six A stages.
+
+template <int SW> struct OzSweep;     // diagonal base, operand planes [tlo, thi], W planes [slo, shi]
+template <> struct OzSweep<0> { static constexpr int base = 0, tlo = 0, thi = 3, slo = 0, shi = 3; };
+template <> struct OzSweep<1> { static constexpr int base = 4, tlo = 0, thi = 3, slo = 1, shi = 7; };
+template <> struct OzSweep<2> { static constexpr int base = 4, tlo = 4, thi = 7, slo = 0, shi = 3; };
+
+constexpr int oz_imax(int a, int b) { return a > b ? a : b; }
+constexpr int oz_imin(int a, int b) { return a < b ? a : b; }
+
+// The products of W plane SS with the sweep's operand planes whose diagonal lies in
+// [base, base + 3], for the 4 K steps of a chunk, A kept in the collector per K step.  init:
+// bit j set once accumulator j holds a value (its first product overwrites).
+template <int SW, int SS, int NCOL, int BPLANE>
+__device__ __forceinline__ void oz_issue_wide(uint32_t tmem, uint64_t adesc, uint64_t bdesc, unsigned &init)
+{
+    using W = OzSweep<SW>;
+    constexpr int t0 = oz_imax(W::tlo, W::base - SS), t1 = oz_imin(W::thi, W::base + 3 - SS);
+    if constexpr (t1 >= t0) {
+        constexpr int cnt = t1 - t0 + 1;
+        constexpr uint32_t idesc = umma_idesc_bf16(128, NCOL);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = adesc + (uint64_t)(2 * kk);
+#pragma unroll
+            for (int t = t0; t <= t1; ++t) {
+                const int slot = SS + t - W::base;
+                const uint64_t bd = bdesc + (uint64_t)(((t - W::tlo) * BPLANE + 32 * kk) >> 4);
+                const uint32_t d = tmem + (uint32_t)(slot * NCOL);
+                const uint32_t acc = (init >> slot) & 1u;
+                init |= 1u << slot;
+                if constexpr (cnt == 1) umma_bf16(d, ad, bd, idesc, acc);
+                else if (t == t0) umma_bf16_collect<1>(d, ad, bd, idesc, acc);
+                else if (t < t1) umma_bf16_collect<2>(d, ad, bd, idesc, acc);
+                else umma_bf16_collect<3>(d, ad, bd, idesc, acc);
+            }
+        }
+    }
+}
+
+template <int SW, int NCOL, int BPLANE>
+__device__ __forceinline__ void oz_issue_wide_s(int s, uint32_t tmem, uint64_t adesc, uint64_t bdesc, unsigned &init)
+{
+    switch (s) {
+    case 0: oz_issue_wide<SW, 0, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 1: oz_issue_wide<SW, 1, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 2: oz_issue_wide<SW, 2, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 3: oz_issue_wide<SW, 3, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 4: oz_issue_wide<SW, 4, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 5: oz_issue_wide<SW, 5, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    case 6: oz_issue_wide<SW, 6, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    default: oz_issue_wide<SW, 7, NCOL, BPLANE>(tmem, adesc, bdesc, init); break;
+    }
+}
+
+__host__ __device__ constexpr int oz_sweep_slo(int sw) { return sw == 1 ? 1 : 0; }
+__host__ __device__ constexpr int oz_sweep_shi(int sw) { return sw == 1 ? 7 : 3; }
+__host__ __device__ constexpr int oz_sweep_tlo(int sw) { return sw == 2 ? 4 : 0; }
+
+template <int AST>
+struct OzWideShape {
+    static constexpr int kNCol = 128;                          // 32 cells
+    static constexpr int kATile = kOzM * 128;
+    static constexpr int kBPlane = kNCol * 128;                // 16 KB
+    static constexpr int kBStage = 4 * kBPlane;                // 4 operand planes
+    static constexpr int kTmemCols = 4 * kNCol;                // 4 diagonals at a time
+    static constexpr int kBars = 2 * AST + 2 * 2 + 3;
+    static constexpr int kSmem = AST * kATile + 2 * kBStage + kBars * 8 + 16 + 1024;
+    static_assert(kSmem <= 232448, "shared memory");
+};
+
+template <int AST>
+__global__ void __launch_bounds__(192, 1)
+    oz_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzGemm g)
+{
+    using S = OzWideShape<AST>;
+    extern __shared__ unsigned char oz_smem_raw[];
+    const uint32_t raw = smem_u32(oz_smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = oz_smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + AST * S::kATile;
+    const uint32_t bars = sB + 2 * S::kBStage;
+    auto afull = [&](int q) { return bars + 8 * q; };
+    auto aempty = [&](int q) { return bars + 8 * (AST + q); };
+    auto bfull = [&](int q) { return bars + 8 * (2 * AST + q); };
+    auto bempty = [&](int q) { return bars + 8 * (2 * AST + 2 + q); };
+    const uint32_t accfull = bars + 8 * (2 * AST + 4), drain = bars + 8 * (2 * AST + 5),
+                   tmem_empty = bars + 8 * (2 * AST + 6);
+    unsigned char *tail = gbase + (bars - base) + 8 * S::kBars;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tail);
+    volatile int *abort = reinterpret_cast<volatile int *>(tail + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kOzM;
+    const int64_t col0 = (int64_t)blockIdx.y * S::kNCol;
+    const int kc0 = (int)((int64_t)g.KC * blockIdx.z / gridDim.z);
+    const int nkc = (int)((int64_t)g.KC * (blockIdx.z + 1) / gridDim.z) - kc0;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < AST; ++q) { mbar_init(afull(q), 1); mbar_init(aempty(q), 1); }
+        for (int q = 0; q < 2; ++q) { mbar_init(bfull(q), 1); mbar_init(bempty(q), 1); }
+        mbar_init(accfull, 1);
+        mbar_init(drain, 1);
+        mbar_init(tmem_empty, 4);                 // one arrival per epilogue warp
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(S::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---- producer: three sweeps over this CTA's K chunks; per chunk the sweep's 4 operand
+        //      planes, then its W planes one at a time
+        if (lane == 0) {
+            int armedA[AST], armedB[2];
+            for (int q = 0; q < AST; ++q) armedA[q] = 0;
+            armedB[0] = armedB[1] = 0;
+            int ai = 0, bi = 0;
+            bool ok = true;
+            for (int sw = 0; sw < 3 && ok; ++sw) {
+                for (int it = 0; it < nkc && ok; ++it, ++bi) {
+                    const int kc = kc0 + it, bs = bi & 1;
+                    if (bi >= 2 && !mbar_wait(bempty(bs), ((bi >> 1) - 1) & 1, abort, g.err)) { ok = false; break; }
+                    mbar_expect_tx(bfull(bs), S::kBStage);
+                    ++armedB[bs];
+                    for (int t = 0; t < 4; ++t)
+                        tma_load_2d(sB + bs * S::kBStage + t * S::kBPlane, &tmB, kc * kOzBK,
+                                    (int)((int64_t)(oz_sweep_tlo(sw) + t) * g.ncols + col0), bfull(bs));
+                    for (int sp = oz_sweep_slo(sw); sp <= oz_sweep_shi(sw); ++sp, ++ai) {
+                        const int q = ai % AST;
+                        if (ai >= AST && !mbar_wait(aempty(q), ((ai / AST) - 1) & 1, abort, g.err)) { ok = false; break; }
+                        mbar_expect_tx(afull(q), S::kATile);
+                        ++armedA[q];
+                        tma_load_2d(sA + q * S::kATile, &tmA, kc * kOzBK, sp * g.Mp + m0, afull(q));
+                    }
+                }
+            }
+            if (!ok) {
+                for (int q = 0; q < AST; ++q)
+                    if (armedA[q]) mbar_drain(afull(q), (armedA[q] - 1) & 1, kOzDrainNs);
+                for (int q = 0; q < 2; ++q)
+                    if (armedB[q]) mbar_drain(bfull(q), (armedB[q] - 1) & 1, kOzDrainNs);
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int ai = 0, bi = 0;
+            bool ok = true;
+            unsigned init = 0u;
+            for (int sw = 0; sw < 3 && ok; ++sw) {
+                if (sw == 1) {
+                    // pass 2 reuses the accumulators: wait until the epilogue has read pass 1
+                    if (!mbar_wait(tmem_empty, 0, abort, g.err)) { ok = false; break; }
+                    tc_fence_after();
+                    init = 0u;
+                }
+                for (int it = 0; it < nkc && ok; ++it, ++bi) {
+                    const int bs = bi & 1;
+                    if (!mbar_wait(bfull(bs), (bi >> 1) & 1, abort, g.err)) { ok = false; break; }
+                    for (int sp = oz_sweep_slo(sw); sp <= oz_sweep_shi(sw); ++sp, ++ai) {
+                        const int q = ai % AST;
+                        if (!mbar_wait(afull(q), (ai / AST) & 1, abort, g.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint64_t ad = sw128_desc(sA + q * S::kATile), bd = sw128_desc(sB + bs * S::kBStage);
+                        if (sw == 0) oz_issue_wide_s<0, S::kNCol, S::kBPlane>(sp, tmem, ad, bd, init);
+                        else if (sw == 1) oz_issue_wide_s<1, S::kNCol, S::kBPlane>(sp, tmem, ad, bd, init);
+                        else oz_issue_wide_s<2, S::kNCol, S::kBPlane>(sp, tmem, ad, bd, init);
+                        umma_commit(aempty(q));
+                    }
+                    if (ok) umma_commit(bempty(bs));
+                }
+                if (ok && sw != 1) umma_commit(accfull);     // after pass 1 (sweep 0) and pass 2 (sweep 2)
+            }
+            if (!ok) {
+                umma_commit(drain);
+                mbar_drain(drain, 0, kOzDrainNs);
+            }
+        }
+    } else {
+        // ---- epilogue: twice, once per pass; exact 64-bit products at scale 2^-48
+        const int quarter = warp & 3;
+        const int grow = m0 + quarter * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
+        for (int pass = 0; pass < 2; ++pass) {
+            if (!mbar_wait(accfull, pass, abort, g.err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c8 = 0; c8 < S::kNCol; c8 += 8) {
+                uint32_t v[4][8];
+#pragma unroll
+                for (int dg = 0; dg < 4; ++dg) tmem_ld8_nowait(trow + (uint32_t)(dg * S::kNCol + c8), v[dg]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    long long a;
+                    if (pass == 0) {         // D0 2^36 + D1 2^30 + D2 2^24 + D3 2^18
+                        a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
+#pragma unroll
+                        for (int dg = 1; dg < 4; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
+                        a <<= 18;
+                    } else {                 // D4 2^12 + D5 2^6 + D6, and D7 to Q
+                        a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
+                        a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[1][j]));
+                        a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[2][j]));
+                    }
+                    const int64_t col = col0 + c8 + j;
+                    if (col < 4 * g.n) {
+                        long long *dst = g.P + col * g.Mp + grow;
+                        const long long a7 = pass ? (long long)__float2int_rn(__uint_as_float(v[3][j])) : 0;
+                        if (g.split) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
+                            if (pass) atomicAdd(reinterpret_cast<unsigned long long *>(g.Q + col * g.Mp + grow),
+                                                (unsigned long long)a7);
+                        } else if (pass == 0) {
+                            *dst = a;
+                        } else {
+                            *dst += a;
+                            g.Q[col * g.Mp + grow] = a7;
+                        }
+                    }
+                }
+            }
+            if (pass == 0) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tmem_empty) : "memory");
             }
         }
     }
@@ -748,6 +1020,18 @@ cudaError_t launch_gemm(const CUtensorMap &tmA, const CUtensorMap &tmB, const Oz
     return cudaGetLastError();
 }
 
+template <int AST>
+cudaError_t launch_gemm_wide(const CUtensorMap &tmA, const CUtensorMap &tmB, const OzGemm &g, int Mp,
+                             int64_t ncols_used, int split, cudaStream_t st)
+{
+    using S = OzWideShape<AST>;
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_wide_kernel<AST>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(Mp / kOzM, (unsigned)((ncols_used + S::kNCol - 1) / S::kNCol), (unsigned)split);
+    oz_gemm_wide_kernel<AST><<<grid, 192, S::kSmem, st>>>(tmA, tmB, g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int oz_kp(int width) { return (width + kOzBK - 1) / kOzBK * kOzBK; }
@@ -755,8 +1039,8 @@ int oz_mp(int width) { return (width + kOzM - 1) / kOzM * kOzM; }
 
 const int *oz_tile_cells(int *n)
 {
-    static const int cells[] = {16, 8};
-    *n = 2;
+    static const int cells[] = {32, 16, 8};
+    *n = 3;
     return cells;
 }
 
@@ -808,6 +1092,7 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
     const int64_t rstride = 4 * (int64_t)(net.N + 1);
     const int64_t ncols = 4 * scr.batch_cells;
     const int per_sm = tile_cells == 8 ? 2 : 1;        // resident tiles per SM (shared memory)
+    // the wide tile splits K at most over the 8 chunks of each of its 3 sweeps
     for (int64_t b0 = 0; b0 < n; b0 += scr.batch_cells) {
         const int64_t nb = std::min<int64_t>(scr.batch_cells, n - b0);
         OzPrep p{};
@@ -823,6 +1108,7 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
         p.b_out = net.b_out;
         p.B = scr.B;
         p.P = scr.P;
+        p.Q = scr.Q;
         p.ncols = ncols;
         for (int l = 1; l <= net.L; ++l) {
             p.eBin = scr.eB[l & 1];                    // written by the prep of layer l - 1
@@ -834,6 +1120,7 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
                 if (e != cudaSuccess) return e;
                 OzGemm g{};
                 g.P = scr.P;
+                g.Q = scr.Q;
                 g.Mp = oz_mp(net.width[l]);
                 g.n = nb;
                 g.KC = Kp / kOzBK;
@@ -845,11 +1132,13 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
                 g.split = split > 1 ? 1 : 0;
                 if (g.split) {
                     e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * 4 * nb * g.Mp, st);
+                    if (e == cudaSuccess) e = cudaMemsetAsync(scr.Q, 0, sizeof(long long) * 4 * nb * g.Mp, st);
                     if (e != cudaSuccess) return e;
                 }
                 const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
-                e = tile_cells == 8 ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
-                                    : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
+                e = tile_cells == 8    ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                    : tile_cells == 32 ? launch_gemm_wide<6>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                                       : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
                 if (e != cudaSuccess) return e;
                 p.Mp = g.Mp;
                 p.eA = net.eA[l];

@@ -98,7 +98,7 @@ def test_march_refuses_tensor_rows(am_mod=None):
         assert e.value.status == 1               # AM_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("tile_cells", [16, 8])
+@pytest.mark.parametrize("tile_cells", [32, 16, 8])
 def test_sliced_compose_batches_and_ragged_shapes(oracle_mod, tile_cells):
     # widths that fill no tile exactly, a skip layer with a latent, and more patterns than one
     # batch of the sliced compose (4096 cells): ragged rows, columns, K chunks and batches
@@ -137,13 +137,13 @@ def test_autotune_compose_and_tile_shapes_agree_bitwise(oracle_mod, tmp_path):
     with am.Mesher(max_cells=1 << 10, max_neurons=2048, max_width=256) as m:
         nid = m.load_mlp(mlp)
         rows = {}
-        for t in (16, 8):
+        for t in (32, 16, 8):
             m.set_tuning(compose_tile_cells=t)
             rows[t], _ = m.compose(nid, keys, "sliced")
-        assert np.array_equal(rows[16], rows[8])
+        assert np.array_equal(rows[16], rows[8]) and np.array_equal(rows[32], rows[8])
         res = m.autotune_compose(nid, keys, reps=3, cache=cache)
-        assert not res["cached"] and res["compose_tile_cells"] in (8, 16)
-        assert sorted(c["compose_tile_cells"] for c in res["candidates"]) == [8, 16]
+        assert not res["cached"] and res["compose_tile_cells"] in (8, 16, 32)
+        assert sorted(c["compose_tile_cells"] for c in res["candidates"]) == [8, 16, 32]
         assert all(c["ms"] > 0 for c in res["candidates"])
         assert m.get_tuning()["compose_tile_cells"] == res["compose_tile_cells"]
         again = m.autotune_compose(nid, keys, cache=cache)
