@@ -368,9 +368,10 @@ __device__ __forceinline__ long long fixed62f(float x, int e)
     return (u >> 31) ? -v : v;
 }
 
-// The exact product of column 4 i + j, row k at scale 2^-48: diagonals 0..6 plus diagonal 7
-// rounded to the scale, once, after every split of K has added in (so the rows do not depend on
-// the launch shape)
+// The exact product of column 4 i + j, row k at scale 2^-48: P (diagonals 0..6, or 0..3 for the
+// wide tile) plus Q (diagonal 7, or diagonals 4..7 for the wide tile, at scale 2^-54) rounded to
+// the scale once, after every split of K has added in (so the rows do not depend on the launch
+// shape)
 __device__ __forceinline__ long long oz_product(const OzPrep &p, int64_t i, int j, int k)
 {
     const int64_t o = (4 * i + j) * p.Mp + k;
@@ -939,25 +940,18 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
                         for (int dg = 1; dg < 4; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
                         a <<= 18;
-                    } else {                 // D4 2^12 + D5 2^6 + D6, and D7 to Q
+                    } else {                 // D4 2^18 + D5 2^12 + D6 2^6 + D7, at scale 2^-54, to Q
                         a = (long long)__float2int_rn(__uint_as_float(v[0][j]));
-                        a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[1][j]));
-                        a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[2][j]));
+#pragma unroll
+                        for (int dg = 1; dg < 4; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
                     }
+                    // pass 1 to P, pass 2 to Q: the prep's P + round(Q / 64) adds them exactly,
+                    // so neither pass reads the other's result back
                     const int64_t col = col0 + c8 + j;
                     if (col < 4 * g.n) {
-                        long long *dst = g.P + col * g.Mp + grow;
-                        const long long a7 = pass ? (long long)__float2int_rn(__uint_as_float(v[3][j])) : 0;
-                        if (g.split) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
-                            if (pass) atomicAdd(reinterpret_cast<unsigned long long *>(g.Q + col * g.Mp + grow),
-                                                (unsigned long long)a7);
-                        } else if (pass == 0) {
-                            *dst = a;
-                        } else {
-                            *dst += a;
-                            g.Q[col * g.Mp + grow] = a7;
-                        }
+                        long long *dst = (pass ? g.Q : g.P) + col * g.Mp + grow;
+                        if (g.split) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
+                        else *dst = a;
                     }
                 }
             }
