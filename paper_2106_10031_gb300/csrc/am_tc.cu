@@ -802,7 +802,7 @@ struct OzWideShape {
 };
 
 template <int AST>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     oz_gemm_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzGemm g)
 {
     using S = OzWideShape<AST>;
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int q = 0; q < 2; ++q) { mbar_init(bfull(q), 1); mbar_init(bempty(q), 1); }
         mbar_init(accfull, 1);
         mbar_init(drain, 1);
-        mbar_init(tmem_empty, 4);                 // one arrival per epilogue warp
+        mbar_init(tmem_empty, 8);                 // one arrival per epilogue warp
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -919,15 +919,17 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // ---- epilogue: twice, once per pass; exact 64-bit products at scale 2^-48
+        // ---- epilogue (warps 2..9, two per TMEM lane quarter, each half of the columns): twice,
+        //      once per pass; exact 64-bit products
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int grow = m0 + quarter * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
         for (int pass = 0; pass < 2; ++pass) {
             if (!mbar_wait(accfull, pass, abort, g.err)) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int c8 = 0; c8 < S::kNCol; c8 += 8) {
+            for (int c8 = half * (S::kNCol / 2); c8 < (half + 1) * (S::kNCol / 2); c8 += 8) {
                 uint32_t v[4][8];
 #pragma unroll
                 for (int dg = 0; dg < 4; ++dg) tmem_ld8_nowait(trow + (uint32_t)(dg * S::kNCol + c8), v[dg]);
@@ -1022,7 +1024,7 @@ cudaError_t launch_gemm_wide(const CUtensorMap &tmA, const CUtensorMap &tmB, con
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_wide_kernel<AST>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
     if (e != cudaSuccess) return e;
     const dim3 grid(Mp / kOzM, (unsigned)((ncols_used + S::kNCol - 1) / S::kNCol), (unsigned)split);
-    oz_gemm_wide_kernel<AST><<<grid, 192, S::kSmem, st>>>(tmA, tmB, g);
+    oz_gemm_wide_kernel<AST><<<grid, 320, S::kSmem, st>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
 
