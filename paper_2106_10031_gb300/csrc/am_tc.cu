@@ -14,22 +14,27 @@
 // tensor core's FP32 accumulator only ever adds integers whose running sum stays below 2^24
 // (n_{l-1} <= 1638), which is exact too.  The products of the planes (s, t) with the same
 // diagonal s + t share one scale and accumulate into one TMEM accumulator (36 plane products
-// over 8 diagonals).  The epilogue combines the diagonals exactly in 64-bit integers and
-// converts once to FP64.  What is dropped are the planes with s + t > 9 and the residuals
-// after 8 digits: per output at most (3 n_{l-1} + 1) 2^-48 2^(eA_m + eB_c), the same order as
-// the worst-case rounding of an FP64 dot product of that length.  So the rows are FP64-class,
-// and the march can clip them with the FP64 path's tests.
+// over 8 diagonals).  The epilogue combines the diagonals exactly in 64-bit integers; the prep
+// kernel converts once to FP64 (or to FP32 pairs for the march).  What is dropped are the
+// planes with s + t > 9 and the residuals after 8 digits: per output at most
+// (3 n_{l-1} + 1) 2^-48 2^(eA_m + eB_c), the same order as the worst-case rounding of an FP64
+// dot product of that length.  So the rows are FP64-class, and the march can clip them with
+// the tests it uses for FP64 rows.
 //
-// Kernels (one launch pair per layer and batch):
-//   oz_prep_kernel  : layer-1 rows (cell independent), then, per cell and coordinate, the
-//                     column exponent and the 8 BF16 digit planes of diag(s_l) Z_l for the next
-//                     layer (integer arithmetic on the FP64 bit patterns, no FP64 pipe), or,
-//                     after the last layer, a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Eq. 8);
-//   oz_gemm_kernel  : one CTA per 128 rows of W_l x NC cells.  Warp 0 stages digit-plane tiles
-//                     of W_l and of the stacked operand into shared memory with TMA (128-byte
-//                     swizzle), warp 1 issues tcgen05.mma (M = 128, N = 4 NC, K = 16) into 8
-//                     TMEM accumulators, warps 2..5 read them back with tcgen05.ld, combine,
-//                     add C_l, apply the sign (1 - 2 s_k) of Eq. 10 and write FP64 rows.
+// Kernels (per layer and batch):
+//   oz_prep_kernel      : the rows of layer l from the exact products (exponents, C_l, the sign
+//                         (1 - 2 s_k) of Eq. 10; layer 1 is cell independent), then, per cell
+//                         and coordinate, the column exponent and the 8 BF16 digit planes of
+//                         diag(s_l) Z_l for the next layer (integer arithmetic on the bit
+//                         patterns), or, after the last layer, a_F = w_out^T diag(s_L) Z_L +
+//                         [0 | b_out] (Eq. 8);
+//   oz_gemm_kernel      : one CTA per 128 rows of W_l x NC cells (NC = 16 or 8).  Warp 0 stages
+//                         digit-plane tiles of W_l and of the stacked operand into shared memory
+//                         with TMA (128-byte swizzle), warp 1 issues tcgen05.mma (M = 128,
+//                         N = 4 NC, K = 16) into 8 TMEM accumulators, keeping each A slice in
+//                         the collector, warps 2..5 read them back with tcgen05.ld and write
+//                         the exact products as 64-bit integers;
+//   oz_gemm_wide_kernel : the same for 32 cells (N = 128), the diagonals in two passes of 4.
 // Every wait on an mbarrier has a time limit; when one runs out the kernel raises a flag the
 // host reads, lets its copies and products in flight finish, frees its TMEM and returns.
 #include <cstdint>
@@ -423,8 +428,8 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                     const int e = p.eA[k] + p.eBin[4 * i + j] - 48;
                     long long hi_int;
                     const float ah = i64_to_f32(acc, e, &hi_int);
-                    long long dummy;
-                    const float al = i64_to_f32(acc - hi_int, e, &dummy);
+                    long long lo_int;
+                    const float al = i64_to_f32(acc - hi_int, e, &lo_int);
                     df_add(h[j], lo[j], ah, al);
                     df_norm(h[j], lo[j]);
                 }
