@@ -65,8 +65,8 @@ HBM_PEAK_GBS = _measured_hbm_peak()
 
 # DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
 # workload) from the committed ncu capture, valid while the kernel source is the one captured
-TRAFFIC_CAPTURE = {"sha256_prefix": "3933f98dc34e45d5", "precision": "mixed", "candidates": "learned",
-                   "bytes": 2.954752e6 + 0.512768e6}
+TRAFFIC_CAPTURE = {"sha256_prefix": "46d62118611829ca", "precision": "mixed", "candidates": "learned",
+                   "bytes": 2.973440e6 + 0.518912e6}
 
 
 def captured_traffic(precision, candidates):
@@ -459,7 +459,7 @@ def decoder_leg(dev, n_cells=60000, reps=2):
     out = {"workload": f"decoder (3+256)-[512]x8-1, skip at 4, seed 3; first {n_cells} cells of the march"}
     with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=4096, max_width=512) as m:
         nid = m.load_mlp(mlp)
-        out["autotune"] = m.autotune_compose(nid, n=4096, reps=3)
+        out["autotune"] = m.autotune_compose(nid, n=512, reps=3)      # batches of a breadth-first level
         for prec in ("fp64", "sliced"):
             runs = []
             for _ in range(reps + 1):                   # the first run warms up
@@ -519,7 +519,7 @@ def learned_leg(dev, n_cells=60000, reps=2):
         m.reset()
         m.release_nets()
         nid = m.load_mlp(mlp)
-        out["autotune"] = m.autotune_compose(nid, n=4096, reps=3)
+        out["autotune"] = m.autotune_compose(nid, n=512, reps=3)      # batches of a breadth-first level
         for name, prec, cand in (("plain_fp64", "fp64", "none"), ("fp64_learned", "fp64", "learned"),
                                  ("sliced_learned", "sliced", "learned"), ("fp64_nearest", "fp64", "nearest"),
                                  ("sliced_nearest", "sliced", "nearest")):

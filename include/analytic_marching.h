@@ -265,7 +265,9 @@ typedef struct {
  * then `reps` times between CUDA events on the context's stream; it keeps the candidate with
  * the smallest median in the context (as am_set_tuning would) and writes every candidate, in
  * the order tried, to h_points (host, at most max_points entries; *n_points receives how many
- * were tried).  Every candidate computes the same rows bit for bit; only the time differs. */
+ * were tried).  Every candidate computes the same rows bit for bit; only the time differs.
+ * The best shape depends on the batch size: tune on batches of the size that will be composed
+ * (for AM_PREC_SLICED marches, one breadth-first level: typically a few hundred cells). */
 am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, double *d_rows, int reps,
                               am_tune_point *h_points, int max_points, int *n_points);
 
