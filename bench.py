@@ -487,6 +487,7 @@ def decoder_leg(dev, n_cells=60000, reps=2):
                                               "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                                               "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells}
         out["sliced_speedup_vs_fp64"] = out["sliced"]["faces_per_s"] / out["fp64"]["faces_per_s"]
+        out["march_autotune"] = m.autotune_march(nid, o, d, max_cells=n_cells, reps=1)
     return out
 
 
@@ -536,6 +537,7 @@ def learned_leg(dev, n_cells=60000, reps=2):
         base = out["plain_fp64"]["faces_per_s"]
         for k in ("fp64_learned", "sliced_learned", "fp64_nearest", "sliced_nearest"):
             out[k]["speedup_vs_plain_fp64"] = out[k]["faces_per_s"] / base
+        out["march_autotune"] = m.autotune_march(nid, o, d, max_cells=n_cells, reps=1, candidates="learned")
     return out
 
 

@@ -271,6 +271,27 @@ typedef struct {
 am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, double *d_rows, int reps,
                               am_tune_point *h_points, int max_points, int *n_points);
 
+/* One timed candidate of the march autotuner. */
+typedef struct {
+    am_precision precision;
+    am_schedule schedule;
+    float ms;                 /* median device time of am_march over the repetitions */
+} am_march_point;
+
+/* Autotuner of the march's execution path.  Every precision and schedule gives the same exact
+ * mesh, so the choice is a matter of time.  For each candidate (FP64 and mixed precision, each
+ * with the persistent and the level schedule, and AM_PREC_SLICED when the context holds this
+ * one net and its fan-ins allow it), it marches net_id from the given rays (as am_seed; host
+ * arrays, n_rays x 3) up to max_cells cells (0 = the whole mesh), `reps` times after one untimed
+ * run, timing each am_march with its CUDA events.  *best (in/out): its other fields (box,
+ * delta, candidates, grid_blocks) are used as given; precision and schedule are set to the
+ * fastest candidate's.  h_points (host, may be NULL) receives up to max_points candidates in
+ * the order tried; *n_points (may be NULL) how many were tried.  Ends with am_reset: the
+ * context holds no cells afterwards. */
+am_status am_autotune_march(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays,
+                            double R, int64_t max_cells, int reps, am_march_opts *best, am_march_point *h_points,
+                            int max_points, int *n_points);
+
 /* ---- learned constraint proposal --------------------------------------------------------
  * No counterpart in the paper.  A small MLP, x (7 + L) -> H -> H -> n_out, ReLU hidden layers,
  * sigmoid scores, that predicts which of the n_out = N neurons of a net carry the edges of a

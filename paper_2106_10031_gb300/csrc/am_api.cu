@@ -1030,6 +1030,46 @@ am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, i
     return AM_OK;
 }
 
+am_status am_autotune_march(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays,
+                            double R, int64_t max_cells, int reps, am_march_opts *best, am_march_point *h_points,
+                            int max_points, int *n_points)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!best || reps < 1 || max_cells < 0 || max_points < 0 || (max_points > 0 && !h_points))
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    struct Cand { am_precision p; am_schedule s; };
+    std::vector<Cand> cands = {{AM_PREC_FP64, AM_SCHED_PERSISTENT}, {AM_PREC_MIXED, AM_SCHED_PERSISTENT},
+                               {AM_PREC_FP64, AM_SCHED_LEVELS}, {AM_PREC_MIXED, AM_SCHED_LEVELS}};
+    if (ctx->nets.size() == 1 && ctx->nets[0].oz_ok) cands.push_back({AM_PREC_SLICED, AM_SCHED_LEVELS});
+    int bi = -1;
+    float bms = 0.0f;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        am_march_opts op = *best;
+        op.precision = cands[c].p;
+        op.schedule = cands[c].s;
+        op.max_cells = max_cells;
+        std::vector<float> ms;
+        for (int r = 0; r <= reps; ++r) {                  // run 0 warms up
+            am_status s = am_reset(ctx);
+            if (s == AM_OK) s = am_seed(ctx, net_id, h_origins, h_dirs, n_rays, R, nullptr);
+            if (s == AM_OK) s = am_march(ctx, &op);
+            if (s != AM_OK && s != AM_INCOMPLETE) return s;
+            if (r > 0) ms.push_back((float)ctx->stats.ms_march);
+        }
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[ms.size() / 2];
+        if ((int)c < max_points) h_points[c] = am_march_point{cands[c].p, cands[c].s, med};
+        if (bi < 0 || med < bms) { bi = (int)c; bms = med; }
+    }
+    am_status s = am_reset(ctx);
+    if (s != AM_OK) return s;
+    best->precision = cands[bi].p;
+    best->schedule = cands[bi].s;
+    if (n_points) *n_points = (int)cands.size();
+    return AM_OK;
+}
+
 am_status am_proposal_samples(am_ctx *ctx, int net_id, float *d_X, float *d_Y, int64_t max_samples,
                               int64_t *n_samples)
 {

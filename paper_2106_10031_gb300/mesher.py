@@ -197,6 +197,25 @@ class Mesher:
                 json.dump(table, f, indent=1, sort_keys=True)
         return dict(res, cached=False)
 
+    def autotune_march(self, net_id: int, origins, dirs, R: float = 2.0, max_cells: int = 0, reps: int = 2,
+                       box: float = 1.5, delta: float = 1e-10, candidates: str = "nearest") -> dict:
+        """Time every precision x schedule of the march on net_id from the given rays
+        (am_autotune_march) and return the fastest ({'precision', 'schedule'} as names, and every
+        candidate's median ms).  The context holds no cells afterwards."""
+        o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        cand = {"nearest": nt.AM_CAND_NEAREST, "learned": nt.AM_CAND_LEARNED, "none": nt.AM_CAND_NONE}[candidates]
+        best = nt.am_march_opts(box=box, delta=delta, candidates=cand)
+        pts = (nt.am_march_point * 8)()
+        cnt = C.c_int(0)
+        self._check(self.lib.am_autotune_march(self.ctx, net_id, _dp(o), _dp(d), int(o.shape[0]), float(R),
+                                               int(max_cells), int(reps), C.byref(best), pts, 8, C.byref(cnt)))
+        pname = {v: k for k, v in PRECISIONS.items()}
+        sname = {nt.AM_SCHED_PERSISTENT: "persistent", nt.AM_SCHED_LEVELS: "levels"}
+        return {"precision": pname[best.precision], "schedule": sname[best.schedule],
+                "candidates": [{"precision": pname[pts[i].precision], "schedule": sname[pts[i].schedule],
+                                "ms": pts[i].ms} for i in range(cnt.value)]}
+
     # ---- compose only
     def compose(self, net_id: int, keys, precision="fp64"):
         """Rows of the cells with activation patterns `keys` ((n, ceil(N/64)) uint64): returns

@@ -64,6 +64,10 @@ class am_tune_point(C.Structure):
     _fields_ = [("compose_tile_cells", C.c_int), ("ms", C.c_float)]
 
 
+class am_march_point(C.Structure):
+    _fields_ = [("precision", C.c_int), ("schedule", C.c_int), ("ms", C.c_float)]
+
+
 class am_stats_t(C.Structure):
     _fields_ = [("cells", C.c_int64), ("faces", C.c_int64), ("empty_faces", C.c_int64),
                 ("vertices", C.c_int64), ("corners", C.c_int64), ("degenerate", C.c_int64),
@@ -100,6 +104,8 @@ ENTRY_POINTS = [
     ("am_autotune_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_int, C.c_void_p]),
     ("am_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("am_autotune_march", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int64,
+                                    C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     ("am_proposal_samples", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("am_proposal_init", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64]),
     ("am_proposal_get_params", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) <= exported
 
 
-STRUCTS = ["am_ctx_opts", "am_mlp_desc", "am_march_opts", "am_stats_t", "am_mesh", "am_tuning", "am_tune_point"]
+STRUCTS = ["am_ctx_opts", "am_mlp_desc", "am_march_opts", "am_stats_t", "am_mesh", "am_tuning", "am_tune_point", "am_march_point"]
 
 
 def test_struct_layout_matches_header(tmp_path):

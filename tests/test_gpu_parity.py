@@ -160,3 +160,21 @@ def test_sliced_march_needs_one_net(am):
         with pytest.raises(am.AMError) as e:
             m.march(precision="sliced")
         assert e.value.status == 1           # AM_ERR_INVALID_ARG
+
+
+def test_march_autotuner_times_every_path(am):
+    # every precision x schedule gives the oracle's mesh, so the fastest one is a free choice
+    mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
+    with am.Mesher(max_cells=1 << 17, max_neurons=128, max_width=32) as m:
+        nid = m.load_mlp(mlp)
+        res = m.autotune_march(nid, np.zeros((1, 3)), RAY, max_cells=5000, reps=1)
+        tried = {(c["precision"], c["schedule"]) for c in res["candidates"]}
+        assert tried == {("fp64", "persistent"), ("mixed", "persistent"), ("fp64", "levels"), ("mixed", "levels"),
+                         ("sliced", "levels")}
+        assert all(c["ms"] > 0 for c in res["candidates"])
+        assert (res["precision"], res["schedule"]) in tried
+        assert m.stats()["cells"] == 0                   # the tuner leaves no cells behind
+        m.seed(nid, np.zeros((1, 3)), RAY)
+        m.march(precision=res["precision"], schedule=res["schedule"])
+        assert m.get_mesh(nid).n_faces > 10000
+        print(f"\nmarch autotuner: {res}")
