@@ -389,8 +389,10 @@ def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates=
 def compose_leg(dev, n_cells=4000, reps=5):
     """The compose step alone (am_compose) on the decoder-shaped net, (3 + 256) -> [512] x 8 -> 1
     with skip-concat at layer 4, for the patterns of the first n_cells cells of its march, in the
-    three precisions.  Dense work per cell per §8: 8 n_l n_{l-1} flops over the hidden layers;
-    the tensor path issues 4 m16n8k16 MMAs per 16 x 16 weight tile."""
+    four precisions.  Dense work per cell: 8 n_l n_{l-1} flops over the hidden layers (4 columns
+    of the cell's affine maps, Cor. 1); the split-BF16 path issues 4 m16n8k16 MMAs per 16 x 16
+    weight tile, the sliced path 36 digit-plane products per layer (the tile shape picked by the
+    autotuner on these patterns)."""
     import ctypes as C
 
     import torch
