@@ -431,13 +431,11 @@ def compose_leg(dev, n_cells=4000, reps=5):
                          "unit": "TFLOP/s", "frac": t["issued_tflops"] / BF16_PEAK_TFLOPS,
                          "peak_source": "measured cuBLAS bf16 burst"}
         out["tensor_speedup_vs_fp64"] = out["fp64"]["ms"] / t["ms"]
-        # sliced: 36 digit-plane products per 128-row tile of W_l (rows and K padded to 128 / 64),
-        # N = 4 x (cells per tile) columns
         sl = out["sliced"]
-        tc = out["autotune"]["compose_tile_cells"]
-        cols = -(-n // tc) * 4 * tc
-        sl["issued_tflops"] = 36 * 2 * cols * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
-                                                  for l in range(1, mlp.L)) / (sl["ms"] / 1e3) / 1e12
+        # 36 plane products per layer for each real cell's 4 columns (rows padded to the 128-row
+        # tile and K to 64; the tile's padding columns are not counted)
+        sl["issued_tflops"] = 36 * 2 * 4 * n * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
+                                                   for l in range(1, mlp.L)) / (sl["ms"] / 1e3) / 1e12
         sl["roofline"] = {"bound": "tensor", "achieved": sl["issued_tflops"], "peak": BF16_PEAK_TFLOPS,
                           "unit": "TFLOP/s", "frac": sl["issued_tflops"] / BF16_PEAK_TFLOPS,
                           "peak_source": "measured cuBLAS bf16 burst", "scope": "whole am_compose call"}
@@ -473,10 +471,9 @@ def decoder_leg(dev, n_cells=60000, reps=2):
             out[prec] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
                          "levels": st["levels"], "launches": st["kernel_launches"], "degenerate": st["degenerate"]}
             if prec == "sliced":
-                w, tc = mlp.widths, out["autotune"]["compose_tile_cells"]
-                cells = st["cells"]
-                issued = 36 * 2 * 4 * tc * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
-                                               for l in range(1, mlp.L)) * (cells / tc)
+                w, cells = mlp.widths, st["cells"]
+                issued = 36 * 2 * 4 * cells * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
+                                                  for l in range(1, mlp.L))
                 ach = issued / (st["ms_compose"] / 1e3) / 1e12
                 out[prec]["ms_compose"], out[prec]["ms_clip"] = st["ms_compose"], st["ms_clip"]
                 out[prec]["compose_roofline"] = {"kernel": "oz_gemm_kernel + oz_prep_kernel", "bound": "tensor",

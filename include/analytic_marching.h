@@ -244,7 +244,8 @@ typedef struct {
     int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 32 (UMMA N = 128,
                                  the 8 diagonals in two passes of 4), 16 (N = 64, all 8 diagonals
                                  at once, one tile per SM) or 8 (N = 32, two tiles per SM);
-                                 0 = default 16 */
+                                 0 (default) = automatic per batch and layer: the 32-cell tile
+                                 when its tiles fill every SM, else the 16-cell tile */
 } am_tuning;
 
 /* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */
@@ -260,10 +261,11 @@ typedef struct {
 } am_tune_point;
 
 /* Autotuner of the sliced tensor-core compose (K-stacking tile shape).  For every supported
- * compose_tile_cells it runs am_compose(AM_PREC_SLICED) of the n patterns d_keys (device,
+ * compose_tile_cells (the automatic choice 0 included) it runs am_compose(AM_PREC_SLICED) of the n patterns d_keys (device,
  * n x ceil(N/64) words) of net_id into d_rows (device, n x (N + 1) x 4 doubles) once untimed,
  * then `reps` times between CUDA events on the context's stream; it keeps the candidate with
- * the smallest median in the context (as am_set_tuning would) and writes every candidate, in
+ * the smallest median in the context (as am_set_tuning would; a later candidate must be more
+ * than 1 % faster than an earlier one, and the automatic choice is tried first) and writes every candidate, in
  * the order tried, to h_points (host, at most max_points entries; *n_points receives how many
  * were tried).  Every candidate computes the same rows bit for bit; only the time differs.
  * The best shape depends on the batch size: tune on batches of the size that will be composed

@@ -215,7 +215,7 @@ am_status sliced_compose_async(am_ctx *ctx, int net_id, const unsigned long long
         return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED needs every hidden fan-in <= %d", kOzMaxFanIn);
     am_status s = ensure_oz_scratch(ctx);
     if (s != AM_OK) return s;
-    const int tile = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
+    const int tile = ctx->oz_tile_cells;                   // 0: automatic per batch
     CU(oz_compose(oz_view(nh), d_keys, key_stride, n, d_rows, df, ctx->oz, tile, ctx->sm_count, ctx->stream));
     const int64_t batches = (n + ctx->oz.batch_cells - 1) / ctx->oz.batch_cells;
     ctx->stats.kernel_launches += (2 * (int64_t)nh.dev.L - 1) * batches;
@@ -985,7 +985,7 @@ am_status am_set_tuning(am_ctx *ctx, const am_tuning *t)
 am_status am_get_tuning(const am_ctx *ctx, am_tuning *t)
 {
     if (!ctx || !t) return AM_ERR_INVALID_ARG;
-    t->compose_tile_cells = ctx->oz_tile_cells > 0 ? ctx->oz_tile_cells : 16;
+    t->compose_tile_cells = ctx->oz_tile_cells;
     return AM_OK;
 }
 
@@ -1023,7 +1023,9 @@ am_status am_autotune_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, i
             h_points[i].compose_tile_cells = tiles[i];
             h_points[i].ms = med;
         }
-        if (best < 0 || med < best_ms) { best = tiles[i]; best_ms = med; }
+        // a later candidate must win by more than 1 % (timing noise): ties keep the earlier one,
+        // and the automatic choice, which adapts to every batch size, comes first
+        if (best < 0 || med < best_ms * 0.99f) { best = tiles[i]; best_ms = med; }
     }
     ctx->oz_tile_cells = best;
     if (n_points) *n_points = nt;

@@ -155,13 +155,13 @@ struct OzScratch {
 };
 int oz_kp(int width);             // K padded to the 64-element staging chunk
 int oz_mp(int width);             // rows padded to the 128-row tile
-const int *oz_tile_cells(int *n); // the supported cells per CTA (UMMA N = 4 x cells)
+const int *oz_tile_cells(int *n); // the supported cells per CTA (UMMA N = 4 x cells); 0 = automatic per batch
 void oz_slice_weights(const double *W, int n, int np, int fan, std::vector<uint16_t> &planes, std::vector<int> &eA);
 cudaError_t oz_encode_weights(void *map, const void *planes, int n, int np);
 int64_t oz_scratch_elems(int64_t batch_cells, int max_kp);
 // rows of the cells with keys (n x kw words): n x (N + 1) rows of 32 bytes, a_F last, each row
 // FP64 [a | a0] or, with df, FP32 pairs [hi x 4 | lo x 4]; batches smaller than sms x the tiles
-// resident per SM split the product's K over several CTAs
+// resident per SM split the product's K over several CTAs; tile_cells 0 picks the tile per batch
 cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, void *rows, bool df,
                        const OzScratch &scr, int tile_cells, int sms, cudaStream_t st);
 

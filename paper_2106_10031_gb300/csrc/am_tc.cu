@@ -1040,8 +1040,8 @@ int oz_mp(int width) { return (width + kOzM - 1) / kOzM * kOzM; }
 
 const int *oz_tile_cells(int *n)
 {
-    static const int cells[] = {32, 16, 8};
-    *n = 3;
+    static const int cells[] = {0, 32, 16, 8};     // 0: automatic per batch
+    *n = 4;
     return cells;
 }
 
@@ -1092,8 +1092,7 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
 {
     const int64_t rstride = 4 * (int64_t)(net.N + 1);
     const int64_t ncols = 4 * scr.batch_cells;
-    const int per_sm = tile_cells == 8 ? 2 : 1;        // resident tiles per SM (shared memory)
-    // the wide tile splits K at most over the 8 chunks of each of its 3 sweeps
+
     for (int64_t b0 = 0; b0 < n; b0 += scr.batch_cells) {
         const int64_t nb = std::min<int64_t>(scr.batch_cells, n - b0);
         OzPrep p{};
@@ -1115,20 +1114,26 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
             p.eBin = scr.eB[l & 1];                    // written by the prep of layer l - 1
             p.eBout = scr.eB[(l + 1) & 1];
             if (l >= 2) {
+                const int Mp = oz_mp(net.width[l]);
+                // automatic shape (tile_cells 0): the 32-cell tile when its tiles fill every SM,
+                // else the 16-cell tile, which makes twice as many
+                const int tc = tile_cells ? tile_cells
+                                          : ((int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) >= sms ? 32 : 16);
+                const int per_sm = tc == 8 ? 2 : 1;          // resident tiles per SM (shared memory)
                 CUtensorMap tmB;
                 const int Kp = oz_kp(net.width[l - 1]);
-                cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tile_cells);
+                cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tc);
                 if (e != cudaSuccess) return e;
                 OzGemm g{};
                 g.P = scr.P;
                 g.Q = scr.Q;
-                g.Mp = oz_mp(net.width[l]);
+                g.Mp = Mp;
                 g.n = nb;
                 g.KC = Kp / kOzBK;
                 g.ncols = ncols;
                 g.err = scr.err;
                 // a batch too small to fill the SMs splits K over more CTAs (exact integer sums)
-                const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tile_cells - 1) / (4 * tile_cells));
+                const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tc - 1) / (4 * tc));
                 int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
                 g.split = split > 1 ? 1 : 0;
                 if (g.split) {
@@ -1137,9 +1142,9 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
                     if (e != cudaSuccess) return e;
                 }
                 const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
-                e = tile_cells == 8    ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
-                    : tile_cells == 32 ? launch_gemm_wide<6>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
-                                       : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
+                e = tc == 8    ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                    : tc == 32 ? launch_gemm_wide<6>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                               : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
                 if (e != cudaSuccess) return e;
                 p.Mp = g.Mp;
                 p.eA = net.eA[l];
