@@ -1115,13 +1115,14 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
             p.eBout = scr.eB[(l + 1) & 1];
             if (l >= 2) {
                 const int Mp = oz_mp(net.width[l]);
-                // automatic shape (tile_cells 0): the 32-cell tile when its tiles fill every SM,
-                // else the 16-cell tile, which makes twice as many
+                const int Kp = oz_kp(net.width[l - 1]);
+                // automatic shape (tile_cells 0): the 32-cell tile when its tiles, split over up
+                // to 4 K ranges, fill every SM, else the 16-cell tile, which makes twice as many
                 const int tc = tile_cells ? tile_cells
-                                          : ((int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) >= sms ? 32 : 16);
+                                          : ((int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) * std::min(4, Kp / kOzBK) >= sms
+                                                 ? 32 : 16);
                 const int per_sm = tc == 8 ? 2 : 1;          // resident tiles per SM (shared memory)
                 CUtensorMap tmB;
-                const int Kp = oz_kp(net.width[l - 1]);
                 cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tc);
                 if (e != cudaSuccess) return e;
                 OzGemm g{};
