@@ -178,3 +178,15 @@ def test_march_autotuner_times_every_path(am):
         m.march(precision=res["precision"], schedule=res["schedule"])
         assert m.get_mesh(nid).n_faces > 10000
         print(f"\nmarch autotuner: {res}")
+
+
+@pytest.mark.parametrize("make,dirs", [
+    (lambda: tiny_net((6, 5, 4), 12), RAY),
+    (lambda: decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05), X_RAY),
+])
+def test_sliced_rows_with_the_plain_clip(oracle_mod, am, make, dirs):
+    # tensor-core rows clipped by every cutting row (no candidates): the plain method's path
+    mlp = make()
+    net, ref, mesh, st = _both(oracle_mod, am, mlp, dirs, precision="sliced", candidates="none")
+    parity.compare(ref, mesh, mlp.N, rtol=1e-9)
+    assert st["degenerate"] == 0 and st["fixups"] == st["cells"]       # every face found by the check
