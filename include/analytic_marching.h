@@ -245,8 +245,8 @@ typedef struct {
                                  the 8 diagonals in two passes of 4), 16 (N = 64, all 8 diagonals
                                  at once, one tile per SM) or 8 (N = 32, two tiles per SM);
                                  0 (default) = automatic per batch and layer: the 32-cell tile
-                                 when its tiles, split over up to 4 K ranges, fill every SM,
-                                 else the 16-cell tile */
+                                 when n_{l-1} > 448 (8 K chunks) and its tiles, split over up to
+                                 4 K ranges, fill every SM, else the 16-cell tile */
 } am_tuning;
 
 /* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */

@@ -1116,10 +1116,12 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
             if (l >= 2) {
                 const int Mp = oz_mp(net.width[l]);
                 const int Kp = oz_kp(net.width[l - 1]);
-                // automatic shape (tile_cells 0): the 32-cell tile when its tiles, split over up
-                // to 4 K ranges, fill every SM, else the 16-cell tile, which makes twice as many
+                // automatic shape (tile_cells 0): the 32-cell tile when K has at least 8 chunks
+                // (its two passes' fixed costs amortise) and its tiles, split over up to 4 K
+                // ranges, fill every SM; else the 16-cell tile, which makes twice as many
                 const int tc = tile_cells ? tile_cells
-                                          : ((int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) * std::min(4, Kp / kOzBK) >= sms
+                                          : (Kp / kOzBK >= 8 &&
+                                                     (int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) * 4 >= sms
                                                  ? 32 : 16);
                 const int per_sm = tc == 8 ? 2 : 1;          // resident tiles per SM (shared memory)
                 CUtensorMap tmB;
