@@ -254,7 +254,29 @@ def cpu_baseline(mlp, o, d, budget_s=12.0):
     faces = len(mesh.faces)
     return {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} cells of the breadth-first march ({faces} faces) in {dt:.1f} s, "
-                      f"single thread (plain C per cell + Python loop)"}
+                      f"single thread (plain C per cell + Python loop)"}, mesh
+
+
+def oracle_agreement(ref, mesh):
+    """The headline mesh against the oracle's mesh of the CPU-baseline run: every oracle face
+    must be a GPU face with the same edge cycle; vertex error relative to max(1, |v|)."""
+    from tests import parity
+    got = parity.gpu_faces(mesh)
+    errs, cycles, missing = [], 0, 0
+    for f in ref.faces:
+        g = got.get(f.key)
+        if g is None:
+            missing += 1
+            continue
+        if f.edges != g[0]:
+            cycles += 1
+            continue
+        errs.append(np.linalg.norm(f.verts - g[1], axis=1) / np.maximum(1.0, np.linalg.norm(f.verts, axis=1)))
+    e = np.concatenate(errs) if errs else np.zeros(1)
+    return {"oracle_faces": len(ref.faces), "gpu_faces": len(got), "missing_in_gpu": missing,
+            "edge_cycles_differing": cycles, "max_rel_vertex_err": float(e.max()),
+            "p99_rel_vertex_err": float(np.quantile(e, 0.99)),
+            "whole_mesh_identical": missing == 0 and cycles == 0 and len(ref.faces) == len(got)}
 
 
 def run_reference(args, dist):
@@ -579,9 +601,9 @@ def run_ours(args, dist):
     import paper_2106_10031_gb300 as am
     from paper_2106_10031_gb300 import native as nt
     mlp, o, d = workload()
-    base = None
+    base, ref_mesh = None, None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(mlp, o, d)          # before any GPU work
+        base, ref_mesh = cpu_baseline(mlp, o, d)          # before any GPU work
     dev = dist.local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
@@ -605,6 +627,7 @@ def run_ours(args, dist):
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     dist.barrier()
+    agreement = oracle_agreement(ref_mesh, m.get_mesh(nid)) if ref_mesh is not None else None
     max_ms = dist.allreduce(r["total_ms"], "max")
     all_faces = dist.allreduce(float(faces_per_step * args.steps), "sum")
     value = all_faces / (max_ms / 1e3)
@@ -669,7 +692,7 @@ def run_ours(args, dist):
         "legs": legs,
         "exactness": {"refined_cells": st["refined_cells"], "close_calls": st["close_calls"],
                       "fixups": st["fixups"], "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
-                      "degenerate": st["degenerate"]},
+                      "degenerate": st["degenerate"], "vs_oracle": agreement},
         "cpu_baseline": base,
         "e2e": e2e,
         "clocks": clk.summary(),
