@@ -151,3 +151,37 @@ def test_autotune_compose_and_tile_shapes_agree_bitwise(oracle_mod, tmp_path):
         with pytest.raises(am.AMError):
             m.set_tuning(compose_tile_cells=12)
         print(f"\nautotune: {res}")
+
+
+def test_sliced_compose_edge_cases(oracle_mod):
+    # one pattern; no pattern; a fan-in beyond the exact-accumulation limit (1638) is refused,
+    # by am_compose and by the march, instead of being computed inexactly
+    import paper_2106_10031_gb300 as am
+    from synth.nets import MLP
+    mlp = tiny_net((8, 8), 11)
+    net = oracle_mod.OracleNet(mlp)
+    s = np.random.default_rng(2).integers(0, 2, (1, mlp.N)).astype(np.uint8)
+    with am.Mesher(max_cells=1 << 10, max_neurons=64, max_width=32) as m:
+        nid = m.load_mlp(mlp)
+        rows, _ = m.compose(nid, _keys_from_states(s, mlp.N), "sliced")
+        A, aF = net.compose(s[0])
+        ref = np.vstack([(1.0 - 2.0 * s[0])[:, None] * A, aF[None, :]])
+        assert np.abs(rows[0] - ref).max() / (1.0 + np.abs(ref).max()) < 1e-11
+        empty, _ = m.compose(nid, np.zeros((0, 1), dtype=np.uint64), "sliced")
+        assert empty.shape[0] == 0
+    rng = np.random.default_rng(3)
+    wide = MLP(weights=[rng.normal(0, 0.5, (1700, 3)), rng.normal(0, 0.03, (8, 1700))],
+               biases=[np.zeros(1700), np.zeros(8)], w_out=np.ones(8), b_out=-0.5, name="fanin1700")
+    with am.Mesher(max_cells=1 << 10, max_neurons=2048, max_width=1700) as m:
+        nid = m.load_mlp(wide)
+        keys = _keys_from_states(rng.integers(0, 2, (2, wide.N)).astype(np.uint8), wide.N)
+        with pytest.raises(am.AMError) as e:
+            m.compose(nid, keys, "sliced")
+        assert e.value.status == 1                          # AM_ERR_INVALID_ARG
+        r64, _ = m.compose(nid, keys, "fp64")               # the other precisions still work
+        assert np.isfinite(r64).all()
+        with pytest.raises(am.AMError) as e:                 # refused before any work
+            m.march(precision="sliced")
+        assert e.value.status == 1
+        with pytest.raises(am.AMError):
+            m.set_tuning(compose_tile_cells=24)
