@@ -237,9 +237,12 @@ am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
 am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, am_precision precision,
                      double *d_rows, float *d_err);
 
-/* ---- launch shapes ---------------------------------------------------------------------
- * Kernels with more than one valid launch shape read it from the context.  am_set_tuning sets
- * it by hand; am_autotune_compose times every candidate and keeps the fastest. */
+/* ---- launch shapes and autotuning --------------------------------------------------------
+ * No counterpart in the paper: these calls change how fast a result is computed, never the
+ * result.  Kernels with more than one valid launch shape read it from the context;
+ * am_set_tuning sets it by hand, am_autotune_compose times every candidate and keeps the
+ * fastest.  am_autotune_march picks the march's precision and schedule, all of which give the
+ * same exact mesh (Alg. 1's output does not depend on the arithmetic path). */
 typedef struct {
     int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 32 (UMMA N = 128,
                                  the 8 diagonals in two passes of 4), 16 (N = 64, all 8 diagonals
