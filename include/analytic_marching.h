@@ -242,7 +242,7 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
  * result.  Kernels with more than one valid launch shape read it from the context;
  * am_set_tuning sets it by hand, am_autotune_compose times every candidate and keeps the
  * fastest.  am_autotune_march picks the march's precision and schedule, all of which give the
- * same exact mesh (Alg. 1's output does not depend on the arithmetic path). */
+ * same faces, edge cycles and vertex identities (vertex coordinates agree to rounding). */
 typedef struct {
     int compose_tile_cells;   /* AM_PREC_SLICED: cells stacked per tensor-core tile: 32 (UMMA N = 128,
                                  the 8 diagonals in two passes of 4), 16 (N = 64, all 8 diagonals
