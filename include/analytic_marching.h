@@ -284,8 +284,8 @@ typedef struct {
     float ms;                 /* median device time of am_march over the repetitions */
 } am_march_point;
 
-/* Autotuner of the march's execution path.  Every precision and schedule gives the same exact
- * mesh, so the choice is a matter of time.  For each candidate (FP64 and mixed precision, each
+/* Autotuner of the march's execution path.  Every precision and schedule gives the same faces
+ * and connectivity (coordinates agree to rounding), so the choice is a matter of time.  For each candidate (FP64 and mixed precision, each
  * with the persistent and the level schedule, and AM_PREC_SLICED when the context holds this
  * one net and its fan-ins allow it), it marches net_id from the given rays (as am_seed; host
  * arrays, n_rays x 3) up to max_cells cells (0 = the whole mesh), `reps` times after one untimed
