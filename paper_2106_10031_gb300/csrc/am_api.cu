@@ -72,7 +72,8 @@ struct am_ctx {
     am_stats_t stats{};
     std::string err;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
-    cudaEvent_t evc0 = nullptr, evc1 = nullptr, evc2 = nullptr;   // sliced march: compose / clip split
+    std::vector<cudaEvent_t> oz_ev;    // sliced march: 3 events per batch of a level, read after the level
+    int oz_err_host = 0;               // sliced march: the pipeline time-out flag, copied with the counters
     // seeding scratch (grown on demand)
     double *d_rays = nullptr;
     unsigned long long *d_seed_keys = nullptr;
@@ -281,9 +282,6 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaEventCreate(&ctx->ev2));
     CU(cudaEventCreate(&ctx->evk0));
     CU(cudaEventCreate(&ctx->evk1));
-    CU(cudaEventCreate(&ctx->evc0));
-    CU(cudaEventCreate(&ctx->evc1));
-    CU(cudaEventCreate(&ctx->evc2));
     Arena &ar = ctx->ar;
     ar.kw = (d.max_neurons + 63) / 64;
     ar.maxv = d.max_face_verts;
@@ -360,7 +358,7 @@ void am_destroy(am_ctx *ctx)
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
     if (ctx->evk0) cudaEventDestroy(ctx->evk0);
     if (ctx->evk1) cudaEventDestroy(ctx->evk1);
-    for (cudaEvent_t e : {ctx->evc0, ctx->evc1, ctx->evc2})
+    for (cudaEvent_t e : ctx->oz_ev)
         if (e) cudaEventDestroy(e);
     proposal_free(ctx->prop);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -859,30 +857,33 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             if (f0 >= limit) { incomplete = true; break; }
             f1 = std::min<int64_t>(f1, limit);
             CU(cudaEventRecord(ctx->evk0, ctx->stream));
+            int nbatch = 0;
             if (sliced) {
-                // per batch of the level: the rows on the tensor cores, then the FP64 clip and march
-                for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells) {
+                // per batch of the level: the rows on the tensor cores, then the clip and march;
+                // the batches' events are read after the level's one synchronisation
+                for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells, ++nbatch) {
                     const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
-                    CU(cudaEventRecord(ctx->evc0, ctx->stream));
+                    while ((int)ctx->oz_ev.size() < 3 * (nbatch + 1)) {
+                        cudaEvent_t e = nullptr;
+                        CU(cudaEventCreate(&e));
+                        ctx->oz_ev.push_back(e);
+                    }
+                    cudaEvent_t *ev = ctx->oz_ev.data() + 3 * nbatch;
+                    CU(cudaEventRecord(ev[0], ctx->stream));
                     s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, ctx->ar.kw, c1 - c0, ctx->oz_rows,
                                              true);
                     if (s != AM_OK) return s;
-                    CU(cudaEventRecord(ctx->evc1, ctx->stream));
+                    CU(cudaEventRecord(ev[1], ctx->stream));
                     ma.begin = c0;
                     ma.end = c1;
                     ma.rows_in = ctx->oz_rows;
                     launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
                     CU(cudaGetLastError());
-                    CU(cudaEventRecord(ctx->evc2, ctx->stream));
+                    CU(cudaEventRecord(ev[2], ctx->stream));
                     ctx->stats.cell_launches += 1;
                     ctx->stats.kernel_launches += 1;
-                    CU(cudaEventSynchronize(ctx->evc2));
-                    float a = 0.f, b = 0.f;
-                    CU(cudaEventElapsedTime(&a, ctx->evc0, ctx->evc1));
-                    CU(cudaEventElapsedTime(&b, ctx->evc1, ctx->evc2));
-                    ctx->stats.ms_compose += a;
-                    ctx->stats.ms_clip += b;
                 }
+                CU(cudaMemcpyAsync(&ctx->oz_err_host, ctx->oz.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
             } else {
                 ma.begin = f0;
                 ma.end = f1;
@@ -895,7 +896,20 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             ctx->stats.levels += 1;
             s = sync_status(ctx, hc);
             if (s != AM_OK) return s;
-            if (sliced && (s = sliced_check(ctx)) != AM_OK) return s;
+            if (sliced) {
+                for (int b = 0; b < nbatch; ++b) {
+                    float ta = 0.f, tb = 0.f;
+                    CU(cudaEventElapsedTime(&ta, ctx->oz_ev[3 * b], ctx->oz_ev[3 * b + 1]));
+                    CU(cudaEventElapsedTime(&tb, ctx->oz_ev[3 * b + 1], ctx->oz_ev[3 * b + 2]));
+                    ctx->stats.ms_compose += ta;
+                    ctx->stats.ms_clip += tb;
+                }
+                if (ctx->oz_err_host) {
+                    CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
+                    CU(cudaStreamSynchronize(ctx->stream));
+                    return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
+                }
+            }
             float kms = 0.f;
             CU(cudaEventElapsedTime(&kms, ctx->evk0, ctx->evk1));
             ctx->stats.ms_cell_kernels += kms;
