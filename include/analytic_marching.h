@@ -223,6 +223,15 @@ am_status am_march(am_ctx *ctx, const am_march_opts *opts);
 /* Copy out the assembled mesh of one net (two-call protocol, see am_mesh). */
 am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
 
+/* Device view of the assembled mesh of one net, without a copy (Alg. 1 output).  The array
+ * pointers of *mesh receive DEVICE addresses inside the context's own assembly buffers, in the
+ * layout am_get_mesh copies out (face_offsets start at 0 for this net; corner vertex indices
+ * refer to this net's xyz).  The arrays stay owned by the context and valid until the next
+ * am_march, am_reset, am_release_nets or am_destroy; the caller must not write or free them.
+ * The call synchronises the context's stream before it returns.  n_open_faces is set to -1
+ * (not computed here; am_get_mesh computes it). */
+am_status am_get_mesh_device(am_ctx *ctx, int net_id, am_mesh *mesh);
+
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
 

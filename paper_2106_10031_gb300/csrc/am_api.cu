@@ -85,6 +85,8 @@ struct am_ctx {
     int32_t *d_perm = nullptr;
     int64_t *d_coff = nullptr;
     int64_t coff_cap = 0;
+    int64_t *d_coff_net = nullptr;     // am_get_mesh_device: each net's face offsets rebased to 0
+    int64_t coff_net_cap = 0;
     int64_t *d_scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     int64_t faces_cap = 0;
@@ -338,7 +340,8 @@ void am_destroy(am_ctx *ctx)
     void *bufs[] = {ar.keys, ar.net, ar.hash, ar.nverts, ar.edges, ar.verts, ar.slots, ar.counters,
                     ar.ready, ar.entry_plane, ar.entry_pt,
                     (void *)ar.zob, ctx->d_nets, ctx->d_netcnt, ctx->d_rays, ctx->d_seed_keys, ctx->d_seed_x,
-                    ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv, ctx->d_fe,
+                    ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_coff_net, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv,
+                    ctx->d_fe,
                     ctx->d_xyz, ctx->d_fkeys, ctx->d_vslots};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -1242,6 +1245,34 @@ am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *m)
             if (m->edge_planes[c] >= N) { ++open; break; }
     }
     m->n_open_faces = open;
+    return AM_OK;
+}
+
+am_status am_get_mesh_device(am_ctx *ctx, int net_id, am_mesh *m)
+{
+    if (!ctx || !m) return fail(ctx, AM_ERR_INVALID_ARG, "null argument");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!ctx->mesh_valid || net_id >= (int)ctx->mesh.size()) return fail(ctx, AM_ERR_STATE, "no mesh: call am_march");
+    const MeshInfo &mi = ctx->mesh[net_id];
+    // every net's rebased offsets get their own region: face_base + net_id, faces + 1 long
+    int64_t total = 0;
+    for (const MeshInfo &x : ctx->mesh) total += x.faces + 1;
+    CU(grow(&ctx->d_coff_net, &ctx->coff_net_cap, total));
+    int64_t *off = ctx->d_coff_net + mi.face_base + net_id;
+    launch_rebase_offsets(ctx->d_coff + mi.face_base, mi.corner_base, off, mi.faces + 1, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    m->n_vertices = mi.verts;
+    m->n_faces = mi.faces;
+    m->n_corners = mi.corners;
+    m->key_words = ctx->ar.kw;
+    m->n_open_faces = -1;
+    m->xyz = ctx->d_xyz + 3 * mi.vert_base;
+    m->face_offsets = off;
+    m->face_vertices = ctx->d_fv + mi.corner_base;
+    m->edge_planes = ctx->d_fe + mi.corner_base;
+    m->face_keys = reinterpret_cast<uint64_t *>(ctx->d_fkeys + mi.face_base * ctx->ar.kw);
     return AM_OK;
 }
 

@@ -238,4 +238,16 @@ void launch_asm_vertices(const AsmArgs &a, cudaStream_t st) { asm_vertices_kerne
 void launch_asm_lookup(const AsmArgs &a, cudaStream_t st) { asm_lookup_kernel<<<grid_for(a.n_faces), kAsmThreads, 0, st>>>(a); }
 void launch_asm_write(const AsmArgs &a, cudaStream_t st) { asm_write_kernel<<<grid_for(a.n_faces), kAsmThreads, 0, st>>>(a); }
 
+// out[i] = in[i] - base for i < n: one net's face offsets relative to its first corner
+__global__ void rebase_offsets_kernel(const int64_t *in, int64_t base, int64_t *out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] - base;
+}
+
+void launch_rebase_offsets(const int64_t *in, int64_t base, int64_t *out, int64_t n, cudaStream_t st)
+{
+    if (n > 0) rebase_offsets_kernel<<<grid_for(n), kAsmThreads, 0, st>>>(in, base, out, n);
+}
+
 }  // namespace am

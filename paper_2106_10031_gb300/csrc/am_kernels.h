@@ -129,6 +129,8 @@ cudaError_t launch_asm_offsets(const AsmArgs &a, int64_t *scan_tmp, int64_t scan
 void launch_asm_vertices(const AsmArgs &a, cudaStream_t st);
 void launch_asm_lookup(const AsmArgs &a, cudaStream_t st);
 void launch_asm_write(const AsmArgs &a, cudaStream_t st);
+// out[i] = in[i] - base, i < n (one net's face offsets from the context's global corner offsets)
+void launch_rebase_offsets(const int64_t *in, int64_t base, int64_t *out, int64_t n, cudaStream_t st);
 
 // ---- compose on the tcgen05 tensor cores with error-free BF16 digit planes (am_tc.cu)
 constexpr int kOzDigits = 8;          // digit planes per operand (and accumulator diagonals)

@@ -306,6 +306,42 @@ class Mesher:
         self._check(self.lib.am_get_mesh(self.ctx, int(net_id), C.byref(m)))
         return Mesh(xyz, off, fv, fe, keys, int(m.n_open_faces))
 
+    def get_mesh_device(self, net_id: int) -> dict:
+        """Zero-copy device view of one net's mesh (am_get_mesh_device): a dict of CUDA torch
+        tensors aliasing the context's own assembly buffers -- xyz (V, 3) float64, face_offsets
+        (F + 1,) int64 starting at 0, face_vertices and edge_planes (corners,) int32, face_keys
+        (F, key_words) int64 holding the uint64 key bits.  Valid until the next march, reset,
+        release of the nets or close; each tensor keeps this Mesher object alive.  The tensors
+        are not marked read-only (torch has no such flag) but must not be written."""
+        import torch
+        m = nt.am_mesh()
+        self._check(self.lib.am_get_mesh_device(self.ctx, int(net_id), C.byref(m)))
+        dev = torch.device("cuda", self.device)
+
+        def view(ptr, shape, typestr):
+            n = int(np.prod(shape))
+            if n == 0:
+                return torch.empty(shape, dtype={"<f8": torch.float64, "<i8": torch.int64,
+                                                 "<i4": torch.int32}[typestr], device=dev)
+            holder = _DeviceArray(C.cast(ptr, C.c_void_p).value, shape, typestr, self)
+            return torch.as_tensor(holder, device=dev)
+
+        V, F, K, kw = int(m.n_vertices), int(m.n_faces), int(m.n_corners), int(m.key_words)
+        return {"xyz": view(m.xyz, (V, 3), "<f8"),
+                "face_offsets": view(m.face_offsets, (F + 1,), "<i8"),
+                "face_vertices": view(m.face_vertices, (K,), "<i4"),
+                "edge_planes": view(m.edge_planes, (K,), "<i4"),
+                "face_keys": view(m.face_keys, (F, kw), "<i8")}
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ holder for a context-owned device array."""
+
+    def __init__(self, ptr: int, shape, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
 
 def mesh_net(mlp, origins, dirs, R=2.0, box=1.5, delta=1e-10, **ctx_kw):
     """Convenience: one net, one march; returns (Mesh, stats)."""

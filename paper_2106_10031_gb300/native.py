@@ -99,6 +99,7 @@ ENTRY_POINTS = [
     ("am_march", C.c_int, [C.c_void_p, C.POINTER(am_march_opts)]),
     ("am_get_mesh", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_get_stats", C.c_int, [C.c_void_p, C.POINTER(am_stats_t)]),
+    ("am_get_mesh_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     ("am_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("am_autotune_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,

@@ -87,6 +87,31 @@ def test_parity_two_nets_one_march(oracle_mod, am):
             parity.compare(r, m.get_mesh(i), n.N, rtol=1e-9)
 
 
+def test_device_mesh_view_matches_the_copy(am):
+    """am_get_mesh_device hands out views of the context's buffers: for every net of a
+    two-net march they equal what am_get_mesh copies out, bit for bit, and a second net's
+    view leaves the first one's intact."""
+    import torch
+    nets = [sphere_net(seed=21, width=32, depth=4, sigma=0.05), tiny_net((8, 8), 11)]
+    with am.Mesher(max_cells=1 << 18, max_neurons=256, max_width=64) as m:
+        with pytest.raises(am.AMError):
+            m.get_mesh_device(0)
+        ids = [m.load_mlp(n) for n in nets]
+        for i in ids:
+            m.seed(i, np.zeros((1, 3)), RAY)
+        m.march()
+        views = [m.get_mesh_device(i) for i in ids]
+        for i, v in zip(ids, views):
+            host = m.get_mesh(i)
+            assert v["xyz"].is_cuda and v["xyz"].dtype == torch.float64
+            np.testing.assert_array_equal(v["xyz"].cpu().numpy(), host.xyz)
+            np.testing.assert_array_equal(v["face_offsets"].cpu().numpy(), host.face_offsets)
+            np.testing.assert_array_equal(v["face_vertices"].cpu().numpy(), host.face_vertices)
+            np.testing.assert_array_equal(v["edge_planes"].cpu().numpy(), host.edge_planes)
+            np.testing.assert_array_equal(v["face_keys"].cpu().numpy().view(np.uint64), host.face_keys)
+            assert host.n_faces > 0 and int(v["face_offsets"][0]) == 0
+
+
 @pytest.mark.parametrize("schedule", ["persistent", "levels"])
 def test_resume_after_max_cells(oracle_mod, am, schedule):
     mlp = sphere_net(seed=21, width=32, depth=4, sigma=0.05)
