@@ -408,3 +408,36 @@ out:
     free(slo); free(shi);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Trigger by sphere tracing for an SDF (Sec. 4.3.1): from x_0, step
+ *     x_{t+1} = x_t - eta F(x_t) grad F(x_t)
+ * where grad F(x_t) is the gradient of the affine piece of the cell x_t lies in, i.e. the
+ * first three entries of a_F composed (Cor. 1) for the state of x_t (a tie gives state 0).
+ * The walk stops after max_steps steps, or earlier once |F(x_t)| <= eps.  Outputs the last
+ * point, F there and the gradient of its cell, and the number of steps taken.  Returns 0,
+ * -1 (bad input) or -6 (a cell with a zero gradient: the walk cannot move).
+ */
+int orc_sphere_trace(const int *desc, const double *prm, const double *x0, double eta, int max_steps,
+                     double eps, double *x_out, double *F_out, double *g_out, int *steps)
+{
+    int N = orc_num_neurons(desc), t = 0, i, rc = 0;
+    unsigned char *s = (unsigned char *)malloc(N);
+    double *A = (double *)malloc(sizeof(double) * 4 * N);
+    double x[3], F = 0.0, aF[4];
+    if (!s || !A || max_steps < 0) { rc = -1; goto out; }
+    for (i = 0; i < 3; ++i) x[i] = x0[i];
+    for (;;) {
+        if (orc_state(desc, prm, x, s, &F) || orc_compose(desc, prm, s, A, aF)) { rc = -1; goto out; }
+        if (fabs(F) <= eps || t >= max_steps) break;
+        if (aF[0] == 0.0 && aF[1] == 0.0 && aF[2] == 0.0) { rc = -6; break; }
+        for (i = 0; i < 3; ++i) x[i] = x[i] - eta * F * aF[i];
+        ++t;
+    }
+    for (i = 0; i < 3; ++i) { x_out[i] = x[i]; g_out[i] = aF[i]; }
+    *F_out = F;
+out:
+    if (steps) *steps = t;
+    free(s); free(A);
+    return rc;
+}

@@ -28,7 +28,11 @@ Readings of the paper taken here (the CUDA path takes the same ones):
     and the midpoint of the switching edge (Sec. 4.2.1);
   * faces of area <= 1e-24 B^2 are dropped and counted (Sec. 3.1 "intersection");
   * seeds come from bisection along a ray (Sec. 4.3.2), stopped when both
-    bracket ends share one cell, then the exact affine root in that cell.
+    bracket ends share one cell, then the exact affine root in that cell;
+  * the sphere-tracing trigger (Sec. 4.3.1) stops after a step budget or once
+    |F| <= eps, then bisects a short segment along the gradient through its last
+    point (trace_bracket); the random-pair trigger (Sec. 4.3.2) pairs the r-th
+    positive sample with the r-th negative one (sign_pairs).
 """
 from __future__ import annotations
 
@@ -78,8 +82,9 @@ def load_library(path: str | None = None):
     lib.orc_pivot.argtypes = [I, P, P, I, P, D, I, P, P, P, P]
     lib.orc_nearest_line.argtypes = [I, P, P, P]
     lib.orc_seed_ray.argtypes = [P, P, P, P, D, I, P, P, P]
+    lib.orc_sphere_trace.argtypes = [P, P, P, D, I, D, P, P, P, P]
     for f in ("orc_forward", "orc_state", "orc_compose", "orc_cell_rows", "orc_pivot",
-              "orc_nearest_line", "orc_seed_ray"):
+              "orc_nearest_line", "orc_seed_ray", "orc_sphere_trace"):
         getattr(lib, f).restype = I
     if path is None:
         _lib = lib
@@ -182,6 +187,16 @@ class OracleNet:
         rc = self.lib.orc_seed_ray(_p(self.desc), _p(self.prm), _p(o), _p(d), float(R), int(max_halvings),
                                    _p(x), _p(s), _p(it))
         return rc, x, s, int(it[0])
+
+    # Sec. 4.3.1
+    def sphere_trace(self, x0, eta=1.0, max_steps=64, eps=1e-12):
+        """Sphere-tracing walk from x0: (rc, last point, F there, gradient of its cell, steps)."""
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        x, g, F = np.zeros(3), np.zeros(3), np.zeros(1)
+        t = np.zeros(1, dtype=np.int32)
+        rc = self.lib.orc_sphere_trace(_p(self.desc), _p(self.prm), _p(x0), float(eta), int(max_steps), float(eps),
+                                       _p(x), _p(F), _p(g), _p(t))
+        return rc, x, float(F[0]), g, int(t[0])
 
 
 def face_pivot(C, aF, start, x, delta=DEFAULT_DELTA, max_v=256, lib=None):
@@ -359,6 +374,58 @@ def seed_cells(net: OracleNet, origins, dirs, R=2.0):
         if rc == 0:
             seeds.append((state_to_key(s), x))
     return seeds
+
+
+# Reading of Sec. 4.3.1 (the paper stops at a point near the surface and says nothing about
+# how its cell is then taken): the walk's last point x_T lies at distance about |F|/|g| from
+# the zero crossing of its cell's affine piece along the unit gradient n = g/|g|.  The segment
+# from x_T - h n to x_T + h n with h = 2|F|/|g| + TRACE_PAD therefore has F of opposite signs
+# at its ends while it stays inside one cell, and the dichotomy of Sec. 4.3.2 along it (o =
+# x_T - h n, d = 2h n, t in [0, 1]) yields the seed cell and its exact root.
+TRACE_PAD = 1e-9
+
+
+def trace_bracket(x, F, g):
+    """The segment (o, d) with t in [0, 1] that brackets the zero crossing near x."""
+    gn = float(np.sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]))
+    n = np.asarray(g, dtype=np.float64) / gn
+    h = 2.0 * abs(F) / gn + TRACE_PAD
+    return x - h * n, (2.0 * h) * n
+
+
+def seed_sphere_trace(net: OracleNet, starts, eta=1.0, max_steps=64, eps=1e-12):
+    """Sec. 4.3.1 trigger for every start point: [(key, seed point) or None] in start order."""
+    out = []
+    for x0 in np.atleast_2d(starts):
+        rc, x, F, g, _ = net.sphere_trace(x0, eta, max_steps, eps)
+        if rc != 0:
+            out.append(None)
+            continue
+        o, d = trace_bracket(x, F, g)
+        rc, xs, s, _ = net.seed_ray(o, d, 1.0)
+        out.append((state_to_key(s), xs) if rc == 0 else None)
+    return out
+
+
+def sign_pairs(Fvals, max_pairs):
+    """Reading of Sec. 4.3.2's random sampling: the r-th sample with F > 0 is paired with the
+    r-th sample with F < 0, in sample order (samples with F == 0 are not used), for r below
+    min(#positive, #negative, max_pairs).  Returns [(index of x-, index of x+)]."""
+    pos = [i for i, f in enumerate(Fvals) if f > 0.0]
+    neg = [i for i, f in enumerate(Fvals) if f < 0.0]
+    return list(zip(neg, pos))[:max_pairs]
+
+
+def seed_pairs(net: OracleNet, points, max_pairs):
+    """Sec. 4.3.2 trigger from sampled points: pair samples of opposite sign (sign_pairs) and
+    bisect each segment from x- to x+.  [(key, seed point) or None] in pair order."""
+    P = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    Fvals = [net.F(p) for p in P]
+    out = []
+    for i, j in sign_pairs(Fvals, max_pairs):
+        rc, xs, s, _ = net.seed_ray(P[i], P[j] - P[i], 1.0)
+        out.append((state_to_key(s), xs) if rc == 0 else None)
+    return out
 
 
 def march(net: OracleNet, seeds, box=DEFAULT_BOX, delta=DEFAULT_DELTA, max_cells=None) -> Mesh:

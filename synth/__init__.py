@@ -17,4 +17,5 @@ from .nets import (  # noqa: F401
     proposal_target_net,
     tiny_net,
     seed_rays,
+    trigger_points,
 )

@@ -261,3 +261,10 @@ def seed_rays(n: int = 1, seed: int = 0, length: float = 2.0, direction=None):
         d /= np.linalg.norm(d, axis=1, keepdims=True)
     o = np.zeros((n, 3))
     return o, d, float(length)
+
+
+def trigger_points(n: int, seed: int = 0, box: float = 1.5) -> np.ndarray:
+    """n points drawn uniformly from the cube [-box, box]^3: start points for the
+    sphere-tracing trigger and samples for the random-pair trigger."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-box, box, size=(n, 3))

@@ -25,6 +25,8 @@ MUTANTS = {
     "box_rows_wrong_sign": ("r[3] = -B;", "r[3] = B;"),
     "validity_skips_last_row": ("for (k = 0; k < M; ++k) {\n        const double *r = C + (size_t)k * 4;\n        double d;",
                                 "for (k = 0; k < M - 7; ++k) {\n        const double *r = C + (size_t)k * 4;\n        double d;"),
+    "trace_steps_uphill": ("x[i] = x[i] - eta * F * aF[i];", "x[i] = x[i] + eta * F * aF[i];"),
+    "trace_drops_F": ("x[i] = x[i] - eta * F * aF[i];", "x[i] = x[i] - eta * aF[i];"),
 }
 
 
@@ -57,6 +59,12 @@ def _pins_pass(O, lib):
         ray = np.array([[1.0, 0.37, 0.21]]) / np.linalg.norm([1.0, 0.37, 0.21])
         mlp = polytope_max_of_planes()
         area_ref, vol_ref, _ = pins.polytope_facets(mlp.meta["normals"], mlp.meta["offset"])
+        net = O.OracleNet(mlp, lib=lib)
+        for n in mlp.meta["normals"][:3]:
+            # one sphere-tracing step, eta = 1/2, from 2 n_i where F = 3/2 and grad F = n_i
+            rc, x, F, g, t = net.sphere_trace(2.0 * n, 0.5, 1, 0.0)
+            if rc != 0 or np.abs(x - 1.25 * n).max() > 1e-12:
+                return False
         net, mesh = O.mesh_from_rays(mlp, np.zeros((1, 3)), ray, lib=lib)
         if mesh.failed or not mesh.faces:
             return False
