@@ -215,6 +215,31 @@ am_status am_release_nets(am_ctx *ctx);
 am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs,
                   int n_rays, double R, int *n_seeded);
 
+/* Trigger by sphere tracing for an SDF (Sec. 4.3.1): from each start point x_0 (h_starts:
+ * host, n_starts x 3 FP64) the device walks x <- x - eta F(x) grad F(x), grad F being the
+ * gradient of the affine piece of the cell x lies in (a tie gives state 0), until
+ * |F(x)| <= eps or max_steps steps.  Through the last point x_T it then bisects (as am_seed)
+ * the segment x_T + s n, |s| <= h, n = grad F / |grad F|, h = 2|F(x_T)|/|grad F| + 1e-9,
+ * which brackets the zero crossing of x_T's cell, and pushes the cell found.  Start points
+ * whose walk meets a cell with grad F = 0, or whose segment has no sign change, produce no
+ * seed.  0 < eta <= 1; 0 <= max_steps <= 65536; eps >= 0; 1 <= n_starts <= 2^24.
+ * *n_seeded (may be NULL): new seed cells.  h_seed_points (host, n_starts x 3, may be NULL):
+ * each start's seed point, NaN where it produced none.  AM_ERR_NO_SEED_CELL when no start
+ * produced a new cell. */
+am_status am_seed_sphere_trace(am_ctx *ctx, int net_id, const double *h_starts, int n_starts, double eta,
+                               int max_steps, double eps, int *n_seeded, double *h_seed_points);
+
+/* Trigger by random-pair dichotomy (Sec. 4.3.2): F is evaluated on the device at every sample
+ * (h_points: host, n_points x 3 FP64, drawn by the caller); the r-th sample with F < 0 is
+ * paired with the r-th sample with F > 0, in sample order, for r < min(#negative, #positive,
+ * max_pairs) (samples with F == 0 are not used); each pair's segment from x- to x+ is bisected
+ * as in am_seed and its cell pushed.  1 <= n_points, max_pairs <= 2^24.  *n_pairs and
+ * *n_seeded (may be NULL): pairs formed and new seed cells.  h_seed_points (host, max_pairs x 3,
+ * may be NULL): the seed point of pair r in row r, NaN where it produced none and in the rows
+ * past the last pair.  AM_ERR_NO_SEED_CELL when no pair formed or none produced a new cell. */
+am_status am_seed_pairs(am_ctx *ctx, int net_id, const double *h_points, int n_points, int max_pairs,
+                        int *n_pairs, int *n_seeded, double *h_seed_points);
+
 /* March (Alg. 1): solve every active cell (compose its affine maps, clip its face, push its
  * unseen neighbours), breadth first over all nets at once, then assemble the meshes.
  * opts may be NULL for defaults.  AM_INCOMPLETE when opts->max_cells stopped it early. */

@@ -20,6 +20,9 @@ using namespace am;
 namespace {
 
 constexpr int kMaxNets = 1024;
+constexpr int kMaxTriggerPoints = 1 << 24;   // start points / samples per trigger call
+constexpr int kMaxTraceSteps = 1 << 16;      // sphere-tracing step budget
+constexpr double kTracePad = 1e-9;           // half-length pad of the bracket after tracing
 constexpr unsigned long long kZobristSeed = 0x2106100310031ull;
 
 struct NetHost {
@@ -87,6 +90,8 @@ struct am_ctx {
     int64_t coff_cap = 0;
     int64_t *d_coff_net = nullptr;     // am_get_mesh_device: each net's face offsets rebased to 0
     int64_t coff_net_cap = 0;
+    double *d_trig = nullptr;          // trigger samples / start points and their scratch
+    int64_t trig_cap = 0;
     int64_t *d_scan_tmp = nullptr;
     int64_t scan_tmp_len = 0;
     int64_t faces_cap = 0;
@@ -340,7 +345,7 @@ void am_destroy(am_ctx *ctx)
     void *bufs[] = {ar.keys, ar.net, ar.hash, ar.nverts, ar.edges, ar.verts, ar.slots, ar.counters,
                     ar.ready, ar.entry_plane, ar.entry_pt,
                     (void *)ar.zob, ctx->d_nets, ctx->d_netcnt, ctx->d_rays, ctx->d_seed_keys, ctx->d_seed_x,
-                    ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_coff_net, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv,
+                    ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_coff_net, ctx->d_trig, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv,
                     ctx->d_fe,
                     ctx->d_xyz, ctx->d_fkeys, ctx->d_vslots};
     for (void *b : bufs)
@@ -608,28 +613,30 @@ am_status am_release_nets(am_ctx *ctx)
     return AM_OK;
 }
 
-am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays, double R,
-                  int *n_seeded)
+// Capacity of the seed buffers for n rays (rays: origins then dirs, n x 3 each at a stride of
+// seed_cap rows).
+static am_status ensure_seed_cap(am_ctx *ctx, int n)
 {
-    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
-    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
-    if (!h_origins || !h_dirs || n_rays < 1 || !(R > 0.0)) return fail(ctx, AM_ERR_INVALID_ARG, "bad rays");
-    if (n_rays > ctx->seed_cap) {
-        if (ctx->d_rays) cudaFree(ctx->d_rays);
-        if (ctx->d_seed_keys) cudaFree(ctx->d_seed_keys);
-        if (ctx->d_seed_x) cudaFree(ctx->d_seed_x);
-        if (ctx->d_seed_ok) cudaFree(ctx->d_seed_ok);
-        ctx->d_rays = nullptr; ctx->d_seed_keys = nullptr; ctx->d_seed_x = nullptr; ctx->d_seed_ok = nullptr;
-        ctx->seed_cap = 0;
-        CU(cudaMalloc(&ctx->d_rays, sizeof(double) * 6 * n_rays));
-        CU(cudaMalloc(&ctx->d_seed_keys, sizeof(unsigned long long) * ctx->ar.kw * n_rays));
-        CU(cudaMalloc(&ctx->d_seed_x, sizeof(double) * 3 * n_rays));
-        CU(cudaMalloc(&ctx->d_seed_ok, sizeof(int) * (n_rays + 2)));
-        ctx->seed_cap = n_rays;
-    }
-    CU(cudaMemcpyAsync(ctx->d_rays, h_origins, sizeof(double) * 3 * n_rays, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(ctx->d_rays + 3 * n_rays, h_dirs, sizeof(double) * 3 * n_rays, cudaMemcpyHostToDevice,
-                       ctx->stream));
+    if (n <= ctx->seed_cap) return AM_OK;
+    if (ctx->d_rays) cudaFree(ctx->d_rays);
+    if (ctx->d_seed_keys) cudaFree(ctx->d_seed_keys);
+    if (ctx->d_seed_x) cudaFree(ctx->d_seed_x);
+    if (ctx->d_seed_ok) cudaFree(ctx->d_seed_ok);
+    ctx->d_rays = nullptr; ctx->d_seed_keys = nullptr; ctx->d_seed_x = nullptr; ctx->d_seed_ok = nullptr;
+    ctx->seed_cap = 0;
+    CU(cudaMalloc(&ctx->d_rays, sizeof(double) * 6 * n));
+    CU(cudaMalloc(&ctx->d_seed_keys, sizeof(unsigned long long) * ctx->ar.kw * n));
+    CU(cudaMalloc(&ctx->d_seed_x, sizeof(double) * 3 * n));
+    CU(cudaMalloc(&ctx->d_seed_ok, sizeof(int) * (n + 2)));
+    ctx->seed_cap = n;
+    return AM_OK;
+}
+
+// Dichotomy on n_rays device segments o + t d, t in [0, R] (origins at d_rays, dirs at
+// d_rays + 3 seed_cap), then the push of the new seed cells.  h_points (may be NULL): the
+// seed point of every segment, NaN where it produced none.
+static am_status run_seed(am_ctx *ctx, int net_id, int n_rays, double R, int *n_seeded, double *h_points)
+{
     unsigned long long *d_new = ctx->d_netcnt + 5 * kMaxNets;
     CU(cudaMemsetAsync(d_new, 0, sizeof(unsigned long long), ctx->stream));
     SeedArgs a{};
@@ -638,7 +645,7 @@ am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double
     a.net = net_id;
     a.n_rays = n_rays;
     a.origins = ctx->d_rays;
-    a.dirs = ctx->d_rays + 3 * n_rays;
+    a.dirs = ctx->d_rays + 3 * (size_t)ctx->seed_cap;
     a.R = R;
     a.max_halvings = 200;
     a.max_n = ctx->opts.max_neurons;
@@ -652,17 +659,114 @@ am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double
     ctx->stats.kernel_launches += 2;
     unsigned long long hn = 0;
     CU(cudaMemcpyAsync(&hn, d_new, sizeof hn, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<int> ok(n_rays);
+    CU(cudaMemcpyAsync(ok.data(), ctx->d_seed_ok, sizeof(int) * n_rays, cudaMemcpyDeviceToHost, ctx->stream));
+    if (h_points)
+        CU(cudaMemcpyAsync(h_points, ctx->d_seed_x, sizeof(double) * 3 * n_rays, cudaMemcpyDeviceToHost,
+                           ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    if (h_points)
+        for (int r = 0; r < n_rays; ++r)
+            if (ok[r] != 1) h_points[3 * r] = h_points[3 * r + 1] = h_points[3 * r + 2] = std::nan("");
     if (n_seeded) *n_seeded = (int)hn;
     ctx->mesh_valid = false;
     if (hn == 0) {
-        std::vector<int> ok(n_rays);
-        CU(cudaMemcpy(ok.data(), ctx->d_seed_ok, sizeof(int) * n_rays, cudaMemcpyDeviceToHost));
         int nosign = 0;
         for (int v : ok) nosign += v == -4;
-        return fail(ctx, AM_ERR_NO_SEED_CELL, "no new seed cell (%d of %d rays without a sign change)", nosign, n_rays);
+        return fail(ctx, AM_ERR_NO_SEED_CELL, "no new seed cell (%d of %d segments without a sign change)", nosign,
+                    n_rays);
     }
     return AM_OK;
+}
+
+am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs, int n_rays, double R,
+                  int *n_seeded)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!h_origins || !h_dirs || n_rays < 1 || !(R > 0.0)) return fail(ctx, AM_ERR_INVALID_ARG, "bad rays");
+    am_status s = ensure_seed_cap(ctx, n_rays);
+    if (s != AM_OK) return s;
+    CU(cudaMemcpyAsync(ctx->d_rays, h_origins, sizeof(double) * 3 * n_rays, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_rays + 3 * (size_t)ctx->seed_cap, h_dirs, sizeof(double) * 3 * n_rays,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    return run_seed(ctx, net_id, n_rays, R, n_seeded, nullptr);
+}
+
+am_status am_seed_sphere_trace(am_ctx *ctx, int net_id, const double *h_starts, int n_starts, double eta,
+                               int max_steps, double eps, int *n_seeded, double *h_seed_points)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!h_starts || n_starts < 1 || n_starts > kMaxTriggerPoints) return fail(ctx, AM_ERR_INVALID_ARG, "bad starts");
+    if (!(eta > 0.0 && eta <= 1.0) || max_steps < 0 || max_steps > kMaxTraceSteps || !(eps >= 0.0) ||
+        !std::isfinite(eps))
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad tracing parameters (0 < eta <= 1, 0 <= max_steps <= %d, eps >= 0)",
+                    kMaxTraceSteps);
+    am_status s = ensure_seed_cap(ctx, n_starts);
+    if (s != AM_OK) return s;
+    CU(grow(&ctx->d_trig, &ctx->trig_cap, 3 * (int64_t)n_starts));
+    CU(cudaMemcpyAsync(ctx->d_trig, h_starts, sizeof(double) * 3 * n_starts, cudaMemcpyHostToDevice, ctx->stream));
+    TraceArgs t{};
+    t.nets = ctx->d_nets;
+    t.net = net_id;
+    t.n = n_starts;
+    t.starts = ctx->d_trig;
+    t.eta = eta;
+    t.eps = eps;
+    t.pad = kTracePad;
+    t.max_steps = max_steps;
+    t.max_n = ctx->opts.max_neurons;
+    t.max_w = ctx->opts.max_width;
+    t.origins = ctx->d_rays;
+    t.dirs = ctx->d_rays + 3 * (size_t)ctx->seed_cap;
+    launch_trace(t, ctx->stream);
+    CU(cudaGetLastError());
+    ctx->stats.kernel_launches += 1;
+    return run_seed(ctx, net_id, n_starts, 1.0, n_seeded, h_seed_points);
+}
+
+am_status am_seed_pairs(am_ctx *ctx, int net_id, const double *h_points, int n_points, int max_pairs, int *n_pairs,
+                        int *n_seeded, double *h_seed_points)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (!h_points || n_points < 1 || n_points > kMaxTriggerPoints || max_pairs < 1 || max_pairs > kMaxTriggerPoints)
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad samples (1 <= n_points, max_pairs <= %d)", kMaxTriggerPoints);
+    am_status s = ensure_seed_cap(ctx, max_pairs);
+    if (s != AM_OK) return s;
+    // samples (3 n), F (n), then the two index lists (2 max_pairs ints in max_pairs doubles)
+    CU(grow(&ctx->d_trig, &ctx->trig_cap, 4 * (int64_t)n_points + max_pairs + 1));
+    CU(cudaMemcpyAsync(ctx->d_trig, h_points, sizeof(double) * 3 * n_points, cudaMemcpyHostToDevice, ctx->stream));
+    int *d_np = ctx->d_seed_ok + ctx->seed_cap;
+    PairArgs p{};
+    p.nets = ctx->d_nets;
+    p.net = net_id;
+    p.n_points = n_points;
+    p.max_pairs = max_pairs;
+    p.points = ctx->d_trig;
+    p.F = ctx->d_trig + 3 * (size_t)n_points;
+    p.neg_idx = (int *)(ctx->d_trig + 4 * (size_t)n_points);
+    p.pos_idx = p.neg_idx + max_pairs;
+    p.max_n = ctx->opts.max_neurons;
+    p.max_w = ctx->opts.max_width;
+    p.origins = ctx->d_rays;
+    p.dirs = ctx->d_rays + 3 * (size_t)ctx->seed_cap;
+    p.n_pairs = d_np;
+    launch_pairs(p, ctx->stream);
+    CU(cudaGetLastError());
+    ctx->stats.kernel_launches += 2;
+    int hp = 0;
+    CU(cudaMemcpyAsync(&hp, d_np, sizeof hp, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (n_pairs) *n_pairs = hp;
+    if (h_seed_points)
+        for (int i = 0; i < 3 * max_pairs; ++i) h_seed_points[i] = std::nan("");
+    if (hp == 0) {
+        if (n_seeded) *n_seeded = 0;
+        return fail(ctx, AM_ERR_NO_SEED_CELL, "no pair of samples with F of opposite signs");
+    }
+    return run_seed(ctx, net_id, hp, 1.0, n_seeded, h_seed_points);
 }
 
 static am_status assemble(am_ctx *ctx, int64_t n_cells)

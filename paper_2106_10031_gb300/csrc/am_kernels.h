@@ -66,6 +66,35 @@ struct SeedArgs {
 cudaError_t prepare_seed_kernels(int max_n, int max_w);
 void launch_seed(const SeedArgs &a, cudaStream_t st);
 
+// sphere tracing (Sec. 4.3.1): one block per start point; writes the bracket segment of each
+// start (origin, direction; t in [0, 1]) for launch_seed
+struct TraceArgs {
+    const NetDev *nets;
+    int net;
+    int n;                          // start points
+    const double *starts;           // device, n x 3
+    double eta, eps, pad;
+    int max_steps;
+    int max_n, max_w;
+    double *origins, *dirs;         // device, n x 3 each (outputs)
+};
+void launch_trace(const TraceArgs &a, cudaStream_t st);
+
+// random-pair sampling (Sec. 4.3.2): F at every sample, then segment r from the r-th negative
+// sample to the r-th positive one, r < min(#neg, #pos, max_pairs)
+struct PairArgs {
+    const NetDev *nets;
+    int net;
+    int n_points, max_pairs;
+    const double *points;           // device, n_points x 3
+    double *F;                      // device, n_points (scratch)
+    int *neg_idx, *pos_idx;         // device, max_pairs each (scratch)
+    int max_n, max_w;
+    double *origins, *dirs;         // device, max_pairs x 3 each (outputs)
+    int *n_pairs;                   // device, 1 (output)
+};
+void launch_pairs(const PairArgs &a, cudaStream_t st);
+
 // ---- learned proposal (training and batch inference)
 struct ProposalDev {
     int n_in = 0, hidden = 0, n_out = 0, max_batch = 0;

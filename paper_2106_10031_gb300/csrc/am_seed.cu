@@ -1,4 +1,5 @@
-// am_seed.cu -- trigger cells by dichotomy along rays (Alg. 1 step 2; Sec. 4.3.2).
+// am_seed.cu -- trigger cells by dichotomy along rays (Alg. 1 step 2; Sec. 4.3.2), with the
+// sphere-tracing walk (Sec. 4.3.1) and the random-pair sampling (Sec. 4.3.2) in front of it.
 //
 // One thread block per ray.  F and the state pattern (Def. 2) come from a block-parallel
 // FP64 forward pass (Eq. 1).  The bracket [t_lo, t_hi] keeps F of opposite signs at its
@@ -155,10 +156,169 @@ __global__ void seed_insert_kernel(SeedArgs a)
     atomicOr(ar.counters + kStatus, kStHashFull);
 }
 
+// ---- customised triggers (Sec. 4.3)
+
+// grad F at the point whose pattern the last seed_forward left in `bits`: backpropagation
+// through the active units, delta_l = dF/da_l = m_l (AT_{l+1} delta_{l+1}), delta_L = m_L w_out,
+// and grad F = sum_l Cl_l[:, 0:3]^T delta_l (only the layers fed by x have non-zero columns).
+// d0, d1: two max_w scratch rows; red: 64 doubles.  Every thread returns the same g.
+__device__ void seed_grad(const NetDev &net, const unsigned *bits, double *d0, double *d1, double *red, double g[3])
+{
+    const int tid = threadIdx.x, T = blockDim.x;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+    double *dc = d0, *dn = d1;
+    {
+        const int nL = net.width[net.L], r0 = net.row0[net.L];
+        for (int k = tid; k < nL; k += T)
+            dc[k] = (bits[(r0 + k) >> 5] >> ((r0 + k) & 31)) & 1u ? net.w_out[k] : 0.0;
+    }
+    __syncthreads();
+    for (int l = net.L; l >= 1; --l) {
+        const int nl = net.width[l];
+        const double *Cl = net.Cl[l];
+        for (int k = tid; k < nl; k += T) {
+            const double dk = dc[k];
+            gx += Cl[k * 4 + 0] * dk;
+            gy += Cl[k * 4 + 1] * dk;
+            gz += Cl[k * 4 + 2] * dk;
+        }
+        if (l > 1) {
+            const int np = net.width[l - 1], rp = net.row0[l - 1];
+            const double *AT = net.AT[l];
+            for (int j = tid; j < np; j += T) {
+                double acc = 0.0;
+                if ((bits[(rp + j) >> 5] >> ((rp + j) & 31)) & 1u)
+                    for (int k = 0; k < nl; ++k) acc += AT[(size_t)j * nl + k] * dc[k];
+                dn[j] = acc;
+            }
+            __syncthreads();
+            double *t = dc; dc = dn; dn = t;
+        }
+    }
+    gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
+    if ((tid & 31) == 0) { red[(tid >> 5) * 3 + 0] = gx; red[(tid >> 5) * 3 + 1] = gy; red[(tid >> 5) * 3 + 2] = gz; }
+    __syncthreads();
+    g[0] = g[1] = g[2] = 0.0;
+    for (int w = 0; w < T / 32; ++w) { g[0] += red[w * 3]; g[1] += red[w * 3 + 1]; g[2] += red[w * 3 + 2]; }
+    __syncthreads();
+}
+
+// Sphere tracing (Sec. 4.3.1), one block per start point: x <- x - eta F(x) grad F(x) until
+// |F| <= eps or max_steps steps, then the bracket along the unit gradient n through the last
+// point: o = x - h n, d = 2h n with h = 2|F|/|grad F| + pad, bisected over t in [0, 1] by
+// seed_kernel.  A cell with grad F = 0 leaves d = 0, which seed_kernel reports as a ray
+// without a sign change.
+__global__ void __launch_bounds__(kSeedThreads) trace_kernel(TraceArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const NetDev &net = a.nets[a.net];
+    double *h0 = (double *)smem, *h1 = h0 + a.max_w;
+    unsigned *bits = (unsigned *)(h1 + a.max_w);
+    double *red = (double *)(((uintptr_t)(bits + 3 * ((a.max_n + 31) / 32)) + 15) & ~(uintptr_t)15);
+    const int i = blockIdx.x, tid = threadIdx.x;
+    double x[3] = {a.starts[i * 3], a.starts[i * 3 + 1], a.starts[i * 3 + 2]};
+    double F = 0.0, g[3] = {0.0, 0.0, 0.0};
+    bool flat = false;
+    for (int t = 0;; ++t) {
+        F = seed_forward(net, x, h0, h1, bits, red);
+        seed_grad(net, bits, h0, h1, red, g);
+        if (fabs(F) <= a.eps || t >= a.max_steps) break;
+        if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) { flat = true; break; }
+        for (int c = 0; c < 3; ++c) x[c] = x[c] - a.eta * F * g[c];
+    }
+    if (tid == 0) {
+        if (flat) {
+            for (int c = 0; c < 3; ++c) { a.origins[i * 3 + c] = x[c]; a.dirs[i * 3 + c] = 0.0; }
+        } else {
+            const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            const double h = 2.0 * fabs(F) / gn + a.pad;
+            for (int c = 0; c < 3; ++c) {
+                const double n = g[c] / gn;
+                a.origins[i * 3 + c] = x[c] - h * n;
+                a.dirs[i * 3 + c] = (2.0 * h) * n;
+            }
+        }
+    }
+}
+
+// F at every sample point (random-pair trigger, Sec. 4.3.2), one block per point.
+__global__ void __launch_bounds__(kSeedThreads) sample_eval_kernel(PairArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const NetDev &net = a.nets[a.net];
+    double *h0 = (double *)smem, *h1 = h0 + a.max_w;
+    unsigned *bits = (unsigned *)(h1 + a.max_w);
+    double *red = (double *)(((uintptr_t)(bits + 3 * ((a.max_n + 31) / 32)) + 15) & ~(uintptr_t)15);
+    const int i = blockIdx.x;
+    const double x[3] = {a.points[i * 3], a.points[i * 3 + 1], a.points[i * 3 + 2]};
+    const double F = seed_forward(net, x, h0, h1, bits, red);
+    if (threadIdx.x == 0) a.F[i] = F;
+}
+
+// Pair the r-th sample with F < 0 and the r-th sample with F > 0 (sample order) for r below
+// min(#neg, #pos, max_pairs) and write segment r: origin x-, direction x+ - x- (t in [0, 1]).
+// One block of kPairThreads threads walks the samples in chunks; ranks come from a block
+// scan of ballot counts.
+constexpr int kPairThreads = 1024;
+__global__ void __launch_bounds__(kPairThreads) pair_build_kernel(PairArgs a)
+{
+    __shared__ int wneg[kPairThreads / 32], wpos[kPairThreads / 32];
+    __shared__ int base[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) base[0] = base[1] = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < a.n_points; c0 += kPairThreads) {
+        if (base[0] >= a.max_pairs && base[1] >= a.max_pairs) break;   // block-uniform
+        const int i = c0 + tid;
+        const double f = i < a.n_points ? a.F[i] : 0.0;
+        const bool neg = i < a.n_points && f < 0.0, pos = i < a.n_points && f > 0.0;
+        const unsigned bn = __ballot_sync(0xffffffffu, neg), bp = __ballot_sync(0xffffffffu, pos);
+        if (lane == 0) { wneg[warp] = __popc(bn); wpos[warp] = __popc(bp); }
+        __syncthreads();
+        int rn = base[0] + __popc(bn & ((1u << lane) - 1u)), rp = base[1] + __popc(bp & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) { rn += wneg[w]; rp += wpos[w]; }
+        if (neg && rn < a.max_pairs) a.neg_idx[rn] = i;
+        if (pos && rp < a.max_pairs) a.pos_idx[rp] = i;
+        __syncthreads();
+        if (tid == 0) {
+            int tn = 0, tp = 0;
+            for (int w = 0; w < kPairThreads / 32; ++w) { tn += wneg[w]; tp += wpos[w]; }
+            base[0] += tn; base[1] += tp;
+        }
+        __syncthreads();
+    }
+    const int n_pairs = min(min(base[0], base[1]), a.max_pairs);
+    __syncthreads();   // every neg_idx / pos_idx write of the loop is visible below
+    for (int r = tid; r < n_pairs; r += kPairThreads) {
+        const int in = a.neg_idx[r], ip = a.pos_idx[r];
+        for (int c = 0; c < 3; ++c) {
+            const double xm = a.points[in * 3 + c];
+            a.origins[r * 3 + c] = xm;
+            a.dirs[r * 3 + c] = a.points[ip * 3 + c] - xm;
+        }
+    }
+    if (tid == 0) *a.n_pairs = n_pairs;
+}
+
 cudaError_t prepare_seed_kernels(int max_n, int max_w)
 {
-    return cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                seed_smem_bytes(max_n, max_w));
+    const int bytes = seed_smem_bytes(max_n, max_w);
+    cudaError_t e = cudaFuncSetAttribute(seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sample_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+void launch_trace(const TraceArgs &a, cudaStream_t st)
+{
+    trace_kernel<<<a.n, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
+}
+
+void launch_pairs(const PairArgs &a, cudaStream_t st)
+{
+    sample_eval_kernel<<<a.n_points, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
+    pair_build_kernel<<<1, kPairThreads, 0, st>>>(a);
 }
 
 void launch_seed(const SeedArgs &a, cudaStream_t st)

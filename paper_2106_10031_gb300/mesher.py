@@ -122,6 +122,26 @@ class Mesher:
         self._check(self.lib.am_seed(self.ctx, int(net_id), _dp(o), _dp(d), int(o.shape[0]), float(R), C.byref(n)))
         return n.value
 
+    # ---- customised triggers (Sec. 4.3)
+    def seed_sphere_trace(self, net_id: int, starts, eta: float = 1.0, max_steps: int = 64,
+                          eps: float = 1e-12) -> tuple:
+        """am_seed_sphere_trace: (new seed cells, (n, 3) seed point per start, NaN where none)."""
+        x = np.ascontiguousarray(np.atleast_2d(starts), dtype=np.float64)
+        pts = np.zeros_like(x)
+        n = C.c_int(0)
+        self._check(self.lib.am_seed_sphere_trace(self.ctx, int(net_id), x.ctypes.data, int(x.shape[0]), float(eta),
+                                                  int(max_steps), float(eps), C.byref(n), pts.ctypes.data))
+        return n.value, pts
+
+    def seed_pairs(self, net_id: int, points, max_pairs: int) -> tuple:
+        """am_seed_pairs: (pairs formed, new seed cells, (n_pairs, 3) seed point per pair)."""
+        x = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+        pts = np.zeros((int(max_pairs), 3))
+        npair, n = C.c_int(0), C.c_int(0)
+        self._check(self.lib.am_seed_pairs(self.ctx, int(net_id), x.ctypes.data, int(x.shape[0]), int(max_pairs),
+                                           C.byref(npair), C.byref(n), pts.ctypes.data))
+        return npair.value, n.value, pts[:npair.value]
+
     # ---- am_march
     def march(self, box: float = 1.5, delta: float = 1e-10, precision: int = nt.AM_PREC_FP64,
               max_cells: int = 0, candidates: int = nt.AM_CAND_NEAREST, schedule: int = nt.AM_SCHED_PERSISTENT,

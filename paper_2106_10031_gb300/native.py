@@ -100,6 +100,10 @@ ENTRY_POINTS = [
     ("am_get_mesh", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_get_stats", C.c_int, [C.c_void_p, C.POINTER(am_stats_t)]),
     ("am_get_mesh_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
+    ("am_seed_sphere_trace", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
+                                        C.POINTER(C.c_int), C.c_void_p]),
+    ("am_seed_pairs", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int), C.c_void_p]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     ("am_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("am_autotune_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
