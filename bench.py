@@ -96,6 +96,8 @@ def parse():
                    help="run only the 3-[256]x8-1 learned-proposal leg and print its JSON")
     p.add_argument("--decoder-only", action="store_true",
                    help="run only the decoder march leg (FP64 vs sliced tensor-core compose) and print its JSON")
+    p.add_argument("--triggers-only", action="store_true",
+                   help="run only the customised-trigger leg (sphere tracing, random pairs) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
                    help="run only the compose benchmark (am_compose on the decoder) and print its JSON")
     return p.parse_args()
@@ -562,6 +564,52 @@ def learned_leg(dev, n_cells=60000, reps=2):
     return out
 
 
+def trigger_leg(dev, n_starts=1024, n_samples=4096, reps=5):
+    """The customised triggers (Sec. 4.3) on the headline 3-[64]x4-1 net, with the paper's
+    1024 initial points: sphere tracing from n_starts points uniform in [-1.4, 1.4]^3 (eta 1,
+    at most 64 steps, eps 1e-12) and the random-pair dichotomy on n_samples points uniform in
+    [-1.5, 1.5]^3 (up to 1024 pairs).  Each call is timed whole on the host clock (copy of the
+    points in, the trigger kernels, the dichotomy, the push of the seed cells, the copy of the
+    seed points out), best of `reps` after one warm-up; the oracle's time for the same call on
+    a 64-point sample is reported beside it.  Afterwards the march from all traced seeds."""
+    import paper_2106_10031_gb300 as am
+    from oracle import oracle as orc
+    from synth import trigger_points
+    mlp, _, _ = workload()
+    starts = trigger_points(n_starts, seed=4, box=1.4)
+    samples = trigger_points(n_samples, seed=7, box=1.5)
+    out = {"workload": f"{mlp.name}: {n_starts} sphere-tracing starts, {n_samples} samples for up to 1024 pairs"}
+    with am.Mesher(device=dev, max_cells=1 << 18, max_neurons=max(64, mlp.N), max_width=max(mlp.widths)) as m:
+        nid = m.load_mlp(mlp)
+        for name, call in (("sphere_trace", lambda: m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12)),
+                           ("pairs", lambda: m.seed_pairs(nid, samples, 1024))):
+            times, res = [], None
+            for _ in range(reps + 1):                   # the first call warms up
+                m.reset()
+                t0 = time.perf_counter()
+                res = call()
+                times.append(time.perf_counter() - t0)
+            best = min(times[1:])
+            pts = res[-1]
+            n_in = n_starts if name == "sphere_trace" else n_samples
+            out[name] = {"ms": best * 1e3, "points_per_s": n_in / best, "seeds": int(np.sum(~np.isnan(pts[:, 0]))),
+                         "new_cells": int(res[-2] if name == "pairs" else res[0])}
+        m.reset()
+        m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12)
+        m.march()
+        out["march_from_traced_seeds"] = {"faces": m.stats()["faces"]}
+    net = orc.OracleNet(mlp)
+    t0 = time.perf_counter()
+    orc.seed_sphere_trace(net, starts[:64], eta=1.0, max_steps=64, eps=1e-12)
+    t_tr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    orc.seed_pairs(net, samples[:256], 64)
+    t_pr = time.perf_counter() - t0
+    out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": "64 starts / 256 samples",
+                           "sphere_trace_points_per_s": 64 / t_tr, "pairs_points_per_s": 256 / t_pr}
+    return out
+
+
 def train_proposal(m, mlp, o, d):
     """The learned proposal for the workload: trained on the plain method's mesh (full clip,
     FP64) of a nearby checkpoint of the net (every weight moved by N(0, 0.005^2)), outside
@@ -715,6 +763,10 @@ def main():
         if args.decoder_only:
             if dist.rank == 0:
                 print(json.dumps({"leg": "decoder", **decoder_leg(dist.local)}))
+            return 0
+        if args.triggers_only:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "triggers", **trigger_leg(dist.local)}))
             return 0
         if args.learned_only:
             if dist.rank == 0:
