@@ -257,6 +257,27 @@ am_status am_get_mesh(am_ctx *ctx, int net_id, am_mesh *mesh);
  * (not computed here; am_get_mesh computes it). */
 am_status am_get_mesh_device(am_ctx *ctx, int net_id, am_mesh *mesh);
 
+/* Canonical order of a host mesh (as filled by am_get_mesh), in place; no context, no device.
+ * Alg. 1 leaves the order of the faces to the march, and the device's breadth-first discovery
+ * is not deterministic; this order is:
+ *   faces ascending by cell key read as an N-bit unsigned integer (face_keys word key_words-1
+ *     is the most significant);
+ *   each face's ring (face_vertices and edge_planes together, orientation kept) starts at the
+ *     corner whose sorted pair of plane ids (the edge into it, the edge out of it) is smallest;
+ *   vertices numbered by first appearance along that corner sequence (xyz permuted to match;
+ *     vertices no face uses, if any, follow in their old order).
+ * The same surface therefore gives the same arrays, whatever order the march found it in.
+ * AM_ERR_INVALID_ARG for inconsistent arrays (offsets not rising from 0 to n_corners, a face
+ * with fewer than 3 corners, a vertex index out of range). */
+am_status am_mesh_canonicalize(am_mesh *mesh);
+
+/* Fan triangulation of a host mesh (Sec. 4.4: each convex face splits along diagonals into
+ * V - 2 triangles): face (v_0 ... v_{V-1}) gives (v_0, v_j, v_{j+1}), j = 1 .. V-2, in face
+ * order, so the triangles keep the face's orientation.  Two-call protocol: with tri NULL,
+ * *n_tri receives the count (n_corners - 2 n_faces); otherwise tri (host, 3 x *n_tri int32) is
+ * filled and AM_ERR_CAPACITY is returned when *n_tri is smaller than the count. */
+am_status am_mesh_triangulate(const am_mesh *mesh, int32_t *tri, int64_t *n_tri);
+
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
 

@@ -3,4 +3,4 @@
 Importing this package loads nothing; ``Mesher`` loads the CUDA library on first use and
 fails loudly if it is missing.
 """
-from .mesher import AMError, Mesh, Mesher, mesh_net  # noqa: F401
+from .mesher import AMError, Mesh, Mesher, canonicalize, mesh_net, triangulate  # noqa: F401

@@ -50,6 +50,53 @@ class Mesh:
         return self.edge_planes[o[i]:o[i + 1]]
 
 
+def _host_view(mesh: Mesh) -> nt.am_mesh:
+    m = nt.am_mesh()
+    m.n_vertices, m.n_faces, m.n_corners = len(mesh.xyz), mesh.n_faces, len(mesh.face_vertices)
+    m.key_words = mesh.face_keys.shape[1] if mesh.face_keys.ndim == 2 and mesh.face_keys.shape[1] else 1
+    m.n_open_faces = mesh.n_open_faces
+    m.xyz = mesh.xyz.ctypes.data_as(C.POINTER(C.c_double))
+    m.face_offsets = mesh.face_offsets.ctypes.data_as(C.POINTER(C.c_int64))
+    m.face_vertices = mesh.face_vertices.ctypes.data_as(C.POINTER(C.c_int32))
+    m.edge_planes = mesh.edge_planes.ctypes.data_as(C.POINTER(C.c_int32))
+    m.face_keys = mesh.face_keys.ctypes.data_as(C.POINTER(C.c_uint64))
+    return m
+
+
+def _host_arrays(mesh: Mesh) -> Mesh:
+    return Mesh(np.ascontiguousarray(mesh.xyz, dtype=np.float64).copy(),
+                np.ascontiguousarray(mesh.face_offsets, dtype=np.int64).copy(),
+                np.ascontiguousarray(mesh.face_vertices, dtype=np.int32).copy(),
+                np.ascontiguousarray(mesh.edge_planes, dtype=np.int32).copy(),
+                np.ascontiguousarray(mesh.face_keys, dtype=np.uint64).copy(), int(mesh.n_open_faces))
+
+
+def canonicalize(mesh: Mesh, lib_path=None) -> Mesh:
+    """am_mesh_canonicalize on a copy: faces by key, rings from their canonical corner,
+    vertices by first appearance (host only; no GPU needed)."""
+    out = _host_arrays(mesh)
+    st = nt.load(lib_path).am_mesh_canonicalize(C.byref(_host_view(out)))
+    if st != nt.AM_OK:
+        raise AMError(st, "inconsistent mesh arrays")
+    return out
+
+
+def triangulate(mesh: Mesh, lib_path=None) -> np.ndarray:
+    """am_mesh_triangulate: (T, 3) int32 vertex indices, fans from each face's first corner."""
+    lib = nt.load(lib_path)
+    src = _host_arrays(mesh)
+    view = _host_view(src)
+    n = C.c_int64(0)
+    st = lib.am_mesh_triangulate(C.byref(view), None, C.byref(n))
+    if st != nt.AM_OK:
+        raise AMError(st, "inconsistent mesh arrays")
+    tri = np.zeros((n.value, 3), dtype=np.int32)
+    st = lib.am_mesh_triangulate(C.byref(view), tri.ctypes.data, C.byref(n))
+    if st != nt.AM_OK:
+        raise AMError(st, "triangulation failed")
+    return tri
+
+
 class Mesher:
     def __init__(self, device: int = 0, max_cells: int = 1 << 20, max_neurons: int = 4096, max_width: int = 512,
                  max_face_verts: int = 32, hash_slots: int = 0, stream: int | None = None, lib_path=None):

@@ -102,6 +102,8 @@ ENTRY_POINTS = [
     ("am_get_mesh_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(am_mesh)]),
     ("am_seed_sphere_trace", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double,
                                         C.POINTER(C.c_int), C.c_void_p]),
+    ("am_mesh_canonicalize", C.c_int, [C.POINTER(am_mesh)]),
+    ("am_mesh_triangulate", C.c_int, [C.POINTER(am_mesh), C.c_void_p, C.POINTER(C.c_int64)]),
     ("am_seed_pairs", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.c_void_p]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
