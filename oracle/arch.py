@@ -26,6 +26,11 @@ plane flips that unit; crossing the row of i moves the maximum to i.
 Plane ids: unit k -> k (0..N-1); the pooling row of sub-network i -> N + i; the box faces
 +x, -x, +y, -y, +z, -z -> N + M + 0..5.  Cell key: the unit pattern as an integer plus
 j << N.  A plain ResNet is a MaxPool of one sub-network (no pooling rows, j = 0).
+
+Leaky / parametric ReLU (the paper's closing remarks name them as the next activations): with
+g(a) = a for a > 0 and slope * a otherwise, the state functional and hence the cells are those
+of Def. 2 unchanged; inside a cell the inactive units pass slope * a instead of 0, so
+diag(s_l) above becomes diag(s_l + slope (1 - s_l)).
 """
 from __future__ import annotations
 
@@ -44,6 +49,7 @@ class ResNet:
     w_out: np.ndarray                # n_L
     b_out: float
     shortcuts: dict = field(default_factory=dict)   # q -> (src, S or None for the identity)
+    slope: float = 0.0               # leaky / parametric ReLU: g(a) = a (a > 0), slope * a (a <= 0)
 
     @property
     def widths(self):
@@ -64,7 +70,7 @@ def res_forward(net: ResNet, x):
             src, S = net.shortcuts[l]
             a = a + (hs[src] if S is None else S @ hs[src])
         pre.append(a)
-        hs.append(np.where(a > 0.0, a, 0.0))
+        hs.append(np.where(a > 0.0, a, net.slope * a))
     return np.concatenate(pre), float(net.w_out @ hs[-1] + net.b_out)
 
 
@@ -81,7 +87,8 @@ def res_compose(net: ResNet, s):
             src, S = net.shortcuts[l]
             Z = Z + (Hs[src] if S is None else S @ Hs[src])
         rows.append(Z)
-        Hs.append(Z * s[off:off + n, None])
+        g = np.where(s[off:off + n] > 0, 1.0, net.slope)          # diag of the cell's slopes
+        Hs.append(Z * g[:, None])
         off += n
     aF = net.w_out @ Hs[-1]
     aF[3] += net.b_out

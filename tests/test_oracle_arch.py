@@ -63,7 +63,7 @@ def _torch_F(net, X):
             src, S = net.shortcuts[l]
             a = a + (hs[src] if S is None else tf.linear(hs[src], torch.as_tensor(S)))
         pres.append(a)
-        hs.append(torch.relu(a))
+        hs.append(tf.leaky_relu(a, net.slope) if net.slope else torch.relu(a))
     return torch.cat(pres, 1), hs[-1] @ torch.as_tensor(net.w_out) + net.b_out
 
 
@@ -78,7 +78,8 @@ def _frozen_maps(net, s):
             a = a + (hs[src] if S is None else hs[src] @ S.T)
         pres.append(a)
         n = W.shape[0]
-        hs.append(a * np.asarray(s[off:off + n], dtype=np.float64)[None, :])
+        st = np.asarray(s[off:off + n], dtype=np.float64)
+        hs.append(a * (st + net.slope * (1.0 - st))[None, :])
         off += n
     pre = np.hstack(pres)
     F = hs[-1] @ net.w_out + net.b_out
@@ -263,3 +264,56 @@ def test_planted_mistakes_are_caught(arch, monkeypatch):
     seed = arch.seed_ray(pool, np.zeros(3), np.array([1.0, 0.37, 0.21]) / np.linalg.norm([1.0, 0.37, 0.21]))
     mesh = arch.march(pool, [seed])
     assert mesh.failed or abs(sum(f.area() for f in mesh.faces) - area.sum()) > 1e-6
+
+
+@pytest.mark.parametrize("slope", [0.1, 0.3])
+def test_leaky_relu(arch, slope):
+    # forward and gradient by torch's leaky_relu, cell maps by the frozen network, every face
+    # of a tiny net by LP, and a closed surface on a larger one
+    import torch
+    net = _resnet(arch, 31, first=3, mid=3)
+    net.slope = slope
+    net.b_out = 0.0
+    net.b_out = -0.5 - arch.res_forward(net, np.zeros(3))[1]
+    rng = np.random.default_rng(32)
+    for x in rng.uniform(-1.0, 1.0, size=(15, 3)):
+        pre, F = arch.res_forward(net, x)
+        p_t, F_t = _torch_F(net, x)
+        np.testing.assert_allclose(pre, p_t.detach().numpy()[0], atol=1e-13)
+        assert abs(F - float(F_t.detach()[0])) < 1e-13
+        s = (pre > 0).astype(np.uint8)
+        A, aF = arch.res_compose(net, s)
+        A2, aF2 = _frozen_maps(net, s)
+        np.testing.assert_allclose(A, A2, atol=1e-12)
+        np.testing.assert_allclose(aF, aF2, atol=1e-12)
+        assert abs(aF @ np.append(x, 1.0) - F) < 1e-12
+        X = torch.tensor(x[None, :], requires_grad=True)
+        _torch_F(net, X)[1].sum().backward()
+        np.testing.assert_allclose(aF[:3], X.grad[0].numpy(), atol=1e-12)
+    pool = arch.as_pool(net)
+    brute = _brute_faces(arch, pool, 1.5)
+    mesh = arch.march(pool, list(brute.items()))
+    assert brute and not mesh.failed and {f.key for f in mesh.faces} == set(brute)
+    _check_polygons(arch, pool, mesh, 1.5)
+    big = _resnet(arch, 21, first=6, mid=6)
+    big.slope = slope
+    big.b_out = 0.0
+    big.b_out = -0.5 - arch.res_forward(big, np.zeros(3))[1]
+    bp = arch.as_pool(big)
+    m = arch.march(bp, [arch.seed_ray(bp, np.zeros(3), np.array([1.0, 0.0, 0.0]))])
+    assert m.faces and not m.failed
+    if all(e < bp.N for f in m.faces for e in f.edges):
+        _check_reciprocal_edges(arch, bp, m)
+
+
+def test_leaky_slope_is_caught_when_dropped(arch, monkeypatch):
+    # a compose that ignores the slope (plain ReLU masks) fails the frozen-network pin
+    net = _resnet(arch, 33, first=3, mid=3)
+    net.slope = 0.2
+    s = np.random.default_rng(1).integers(0, 2, net.N).astype(np.uint8)
+    orig = arch.res_compose
+
+    def plain(n, st):
+        return orig(arch.ResNet(n.weights, n.biases, n.w_out, n.b_out, n.shortcuts, 0.0), st)
+    monkeypatch.setattr(arch, "res_compose", plain)
+    assert not np.allclose(arch.res_compose(net, s)[1], _frozen_maps(net, s)[1], atol=1e-12)
