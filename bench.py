@@ -613,7 +613,6 @@ def trigger_leg(dev, n_starts=1024, n_samples=4096, reps=5):
     seed points out), best of `reps` after one warm-up; the oracle's time for the same call on
     a 64-point sample is reported beside it.  Afterwards the march from all traced seeds."""
     import paper_2106_10031_gb300 as am
-    from oracle import oracle as orc
     from synth import trigger_points
     mlp, _, _ = workload()
     starts = trigger_points(n_starts, seed=4, box=1.4)
@@ -638,16 +637,23 @@ def trigger_leg(dev, n_starts=1024, n_samples=4096, reps=5):
         m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12)
         m.march()
         out["march_from_traced_seeds"] = {"faces": m.stats()["faces"]}
+    out["cpu_baseline"] = trigger_cpu_baseline(mlp, starts[:64], samples[:256])
+    return out
+
+
+def trigger_cpu_baseline(mlp, starts, samples):
+    """The oracle's triggers as they stand, single-threaded, on a sample of the trigger leg's
+    points: sphere tracing from `starts`, random pairs (up to 64) from `samples`."""
+    from oracle import oracle as orc
     net = orc.OracleNet(mlp)
     t0 = time.perf_counter()
-    orc.seed_sphere_trace(net, starts[:64], eta=1.0, max_steps=64, eps=1e-12)
+    orc.seed_sphere_trace(net, starts, eta=1.0, max_steps=64, eps=1e-12)
     t_tr = time.perf_counter() - t0
     t0 = time.perf_counter()
-    orc.seed_pairs(net, samples[:256], 64)
+    orc.seed_pairs(net, samples, 64)
     t_pr = time.perf_counter() - t0
-    out["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": "64 starts / 256 samples",
-                           "sphere_trace_points_per_s": 64 / t_tr, "pairs_points_per_s": 256 / t_pr}
-    return out
+    return {"kind": "oracle", "cores": 1, "sample": f"{len(starts)} starts / {len(samples)} samples",
+            "sphere_trace_points_per_s": len(starts) / t_tr, "pairs_points_per_s": len(samples) / t_pr}
 
 
 def train_proposal(m, mlp, o, d):
