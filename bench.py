@@ -96,6 +96,8 @@ def parse():
                    help="run only the 3-[256]x8-1 learned-proposal leg and print its JSON")
     p.add_argument("--decoder-only", action="store_true",
                    help="run only the decoder march leg (FP64 vs sliced tensor-core compose) and print its JSON")
+    p.add_argument("--batch-only", action="store_true",
+                   help="run only the 64-net batch leg (nets sharded over the ranks) and print its JSON")
     p.add_argument("--triggers-only", action="store_true",
                    help="run only the customised-trigger leg (sphere tracing, random pairs) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
@@ -641,6 +643,50 @@ def trigger_leg(dev, n_starts=1024, n_samples=4096, reps=5):
     return out
 
 
+def shard_nets(n_nets: int, rank: int, world: int) -> list:
+    """Indices of the nets a rank meshes: round robin over the net index.  The nets are
+    independent problems, so the ranks exchange nothing on the data path; the round robin
+    spreads the batch's mix of small and large nets."""
+    return list(range(rank, n_nets, world))
+
+
+def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1):
+    """The 64-net batch: batch_nets(master_seed=4) (widths 32-256, depths 4-8, sigma in
+    [0.02, 0.1]), one seed ray along +x per net, all of a rank's nets in one persistent
+    launch, the first max_cells cells of the job (split evenly over the ranks).  Sharded by
+    net (shard_nets); value = all ranks' faces / the slowest rank's march time, by am_march's
+    CUDA events; strong scaling (the total work is fixed)."""
+    import paper_2106_10031_gb300 as am
+    from synth import batch_nets
+    nets = batch_nets()
+    mine = [nets[i] for i in shard_nets(len(nets), dist.rank, dist.world)]
+    cells = max_cells // dist.world
+    o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
+    with am.Mesher(device=dist.local, max_cells=cells + 4096, max_neurons=max(n.N for n in mine),
+                   max_width=max(max(n.widths) for n in mine)) as m:
+        ids = [m.load_mlp(n) for n in mine]
+        runs, unseeded = [], 0
+        for _ in range(reps + 1):                   # the first run warms up
+            m.reset()
+            unseeded = 0
+            for i in ids:
+                try:
+                    m.seed(i, o, d)
+                except am.AMError:
+                    unseeded += 1
+            dist.barrier()
+            m.march(precision=precision, max_cells=cells)
+            runs.append(m.stats())
+        st = min(runs[1:], key=lambda x: x["ms_march"])
+    faces = dist.allreduce(float(st["faces"]), "sum")
+    ms = dist.allreduce(float(st["ms_march"]), "max")
+    return {"workload": f"64 nets of batch_nets(master_seed=4), first {max_cells} cells of the job, {precision}",
+            "n_gpus": dist.world, "scaling": "strong", "sharding": "nets round robin over the ranks, no exchange",
+            "faces": int(faces), "ms": ms, "faces_per_s": faces / (ms / 1e3),
+            "rank0": {"nets": len(mine), "unseeded_nets": unseeded, "cells": int(st["cells"]),
+                      "faces": int(st["faces"]), "ms": float(st["ms_march"])}}
+
+
 def trigger_cpu_baseline(mlp, starts, samples):
     """The oracle's triggers as they stand, single-threaded, on a sample of the trigger leg's
     points: sphere tracing from `starts`, random pairs (up to 64) from `samples`."""
@@ -809,6 +855,11 @@ def main():
         if args.decoder_only:
             if dist.rank == 0:
                 print(json.dumps({"leg": "decoder", **decoder_leg(dist.local)}))
+            return 0
+        if args.batch_only:
+            out = batch_leg(dist, precision=args.precision)
+            if dist.rank == 0:
+                print(json.dumps({"leg": "batch64", **out}))
             return 0
         if args.triggers_only:
             if dist.rank == 0:

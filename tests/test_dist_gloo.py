@@ -48,3 +48,13 @@ def test_single_rank_needs_no_process_group():
     assert d.world == 1 and d.pg is None
     assert d.allreduce(3.5, "max") == 3.5
     d.close()
+
+
+def test_batch_shards_cover_every_net_once():
+    # the 64-net batch split by net over 1..8 ranks: every net on exactly one rank, sizes even
+    import bench
+    for world in range(1, 9):
+        parts = [bench.shard_nets(64, r, world) for r in range(world)]
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(64))
+        assert max(map(len, parts)) - min(map(len, parts)) <= 1
