@@ -23,6 +23,15 @@ PRECISIONS = {"fp64": nt.AM_PREC_FP64, "mixed": nt.AM_PREC_MIXED, "tensor": nt.A
               "sliced": nt.AM_PREC_SLICED}
 
 
+def _points(a, what: str) -> np.ndarray:
+    """A C-contiguous (n, 3) FP64 copy of `a` (one point per row), n >= 1; ValueError otherwise,
+    before any array reaches the C side."""
+    x = np.ascontiguousarray(np.atleast_2d(np.asarray(a, dtype=np.float64)))
+    if x.ndim != 2 or x.shape[1] != 3 or x.shape[0] < 1:
+        raise ValueError(f"{what}: expected an (n, 3) array of points, got shape {np.shape(a)}")
+    return x
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -145,7 +154,19 @@ class Mesher:
         width = (C.c_int * L)(*[int(w.shape[0]) for w in Ws])
         Wp = (C.POINTER(C.c_double) * L)(*[_dp(w) for w in Ws])
         bp = (C.POINTER(C.c_double) * L)(*[_dp(b) for b in bs])
-        z = None if mlp.latent is None else np.ascontiguousarray(mlp.latent, dtype=np.float64)
+        z = None if mlp.latent is None else np.ascontiguousarray(mlp.latent, dtype=np.float64).ravel()
+        # the C side reads W_l as n_l x fan_l: every shape is checked here first
+        in_dim = 3 + (0 if z is None else len(z))
+        skip = int(mlp.skip_layer)
+        if L < 1 or len(bs) != L or not (skip == 0 or 2 <= skip <= L):
+            raise ValueError(f"{L} weight matrices, {len(bs)} bias vectors, skip layer {skip}")
+        for l, (w, b) in enumerate(zip(Ws, bs), start=1):
+            fan = in_dim if l == 1 else Ws[l - 2].shape[0] + (in_dim if l == skip else 0)
+            if w.ndim != 2 or w.shape[1] != fan or b.shape != (w.shape[0],):
+                raise ValueError(f"layer {l}: W {w.shape}, b {b.shape}; expected ({w.shape[0]}, {fan}) and "
+                                 f"({w.shape[0]},)")
+        if w_out.shape != (Ws[-1].shape[0],):
+            raise ValueError(f"w_out {w_out.shape}; expected ({Ws[-1].shape[0]},)")
         d = nt.am_mlp_desc(latent_dim=0 if z is None else len(z), latent=None if z is None else _dp(z),
                            n_hidden=L, width=width, W=Wp, b=bp, skip_layer=int(mlp.skip_layer),
                            w_out=_dp(w_out), b_out=float(mlp.b_out))
@@ -163,8 +184,9 @@ class Mesher:
 
     # ---- am_seed
     def seed(self, net_id: int, origins, dirs, R: float = 2.0) -> int:
-        o = np.ascontiguousarray(np.atleast_2d(origins), dtype=np.float64)
-        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        o, d = _points(origins, "origins"), _points(dirs, "dirs")
+        if o.shape != d.shape:
+            raise ValueError(f"origins {o.shape} and dirs {d.shape} differ in shape")
         n = C.c_int(0)
         self._check(self.lib.am_seed(self.ctx, int(net_id), _dp(o), _dp(d), int(o.shape[0]), float(R), C.byref(n)))
         return n.value
@@ -173,7 +195,7 @@ class Mesher:
     def seed_sphere_trace(self, net_id: int, starts, eta: float = 1.0, max_steps: int = 64,
                           eps: float = 1e-12) -> tuple:
         """am_seed_sphere_trace: (new seed cells, (n, 3) seed point per start, NaN where none)."""
-        x = np.ascontiguousarray(np.atleast_2d(starts), dtype=np.float64)
+        x = _points(starts, "starts")
         pts = np.zeros_like(x)
         n = C.c_int(0)
         self._check(self.lib.am_seed_sphere_trace(self.ctx, int(net_id), x.ctypes.data, int(x.shape[0]), float(eta),
@@ -182,7 +204,9 @@ class Mesher:
 
     def seed_pairs(self, net_id: int, points, max_pairs: int) -> tuple:
         """am_seed_pairs: (pairs formed, new seed cells, (n_pairs, 3) seed point per pair)."""
-        x = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+        x = _points(points, "points")
+        if int(max_pairs) < 1:
+            raise ValueError("max_pairs must be at least 1")
         pts = np.zeros((int(max_pairs), 3))
         npair, n = C.c_int(0), C.c_int(0)
         self._check(self.lib.am_seed_pairs(self.ctx, int(net_id), x.ctypes.data, int(x.shape[0]), int(max_pairs),
@@ -269,8 +293,9 @@ class Mesher:
         """Time every precision x schedule of the march on net_id from the given rays
         (am_autotune_march) and return the fastest ({'precision', 'schedule'} as names, and every
         candidate's median ms).  The context holds no cells afterwards."""
-        o = np.ascontiguousarray(origins, dtype=np.float64).reshape(-1, 3)
-        d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        o, d = _points(origins, "origins"), _points(dirs, "dirs")
+        if o.shape != d.shape:
+            raise ValueError(f"origins {o.shape} and dirs {d.shape} differ in shape")
         cand = {"nearest": nt.AM_CAND_NEAREST, "learned": nt.AM_CAND_LEARNED, "none": nt.AM_CAND_NONE}[candidates]
         best = nt.am_march_opts(box=box, delta=delta, candidates=cand)
         pts = (nt.am_march_point * 8)()
