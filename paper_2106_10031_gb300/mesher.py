@@ -32,6 +32,16 @@ def _points(a, what: str) -> np.ndarray:
     return x
 
 
+def _key_array(keys, N: int) -> np.ndarray:
+    """Activation patterns as a C-contiguous (n, ceil(N/64)) uint64 array (n >= 0): the device
+    reads exactly that many words per pattern, so any other width is refused here."""
+    kw = (int(N) + 63) // 64
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    if k.ndim != 2 or k.shape[1] != kw:
+        raise ValueError(f"keys: expected an (n, {kw}) uint64 array for a net of {N} units, got shape {k.shape}")
+    return k
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -272,7 +282,7 @@ class Mesher:
             g = torch.Generator(device="cpu").manual_seed(seed)
             k = torch.randint(-2**62, 2**62, (n, kw), generator=g, dtype=torch.int64).to(dev)
         else:
-            k = torch.as_tensor(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64), device=dev)
+            k = torch.as_tensor(_key_array(keys, net.N).view(np.int64), device=dev)
         n = k.shape[0]
         rows = torch.empty((n, net.N + 1, 4), dtype=torch.float64, device=dev)
         pts = (nt.am_tune_point * 8)()
@@ -317,7 +327,7 @@ class Mesher:
             precision = PRECISIONS[precision]
         N = self.nets[net_id].N
         dev = torch.device("cuda", self.device)
-        k = torch.as_tensor(np.ascontiguousarray(keys, dtype=np.uint64).view(np.int64), device=dev)
+        k = torch.as_tensor(_key_array(keys, N).view(np.int64), device=dev)
         n = k.shape[0]
         rows = torch.empty((n, N + 1, 4), dtype=torch.float64, device=dev)
         err = torch.empty((n, N + 1), dtype=torch.float32, device=dev)

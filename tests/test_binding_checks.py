@@ -72,3 +72,12 @@ def test_point_arrays_are_checked(mesher):
     mesher.seed_sphere_trace(0, [[0.1, 0.2, 0.3]])
     mesher.seed_pairs(0, np.zeros((5, 3)), 2)
     assert mesher.lib.calls == ["am_seed", "am_seed_sphere_trace", "am_seed_pairs"]
+
+
+def test_key_arrays_are_checked():
+    from paper_2106_10031_gb300 import mesher as M
+    assert M._key_array(np.zeros((5, 2), dtype=np.uint64), 128).shape == (5, 2)
+    assert M._key_array(np.zeros((0, 1), dtype=np.uint64), 16).shape == (0, 1)
+    for bad, N in ((np.zeros((5, 1)), 128), (np.zeros(5), 16), (np.zeros((5, 3)), 128)):
+        with pytest.raises(ValueError):
+            M._key_array(bad, N)
