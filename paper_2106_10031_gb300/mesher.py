@@ -367,14 +367,38 @@ class Mesher:
         p = np.ascontiguousarray(p, dtype=np.float32)
         self._check(self.lib.am_proposal_set_params(self.ctx, p.ctypes.data_as(C.c_void_p), len(p)))
 
+    def _prop_rows(self, T, cols: int, what: str):
+        """A float32 CUDA tensor on this context's device with `cols` columns, contiguous: the
+        kernels read rows x cols floats from its data pointer, so nothing else gets through."""
+        import torch
+        if not isinstance(T, torch.Tensor) or not T.is_cuda or T.device.index != self.device:
+            raise ValueError(f"{what}: expected a CUDA tensor on device {self.device}")
+        if T.dtype != torch.float32 or T.dim() != 2 or T.shape[1] != cols:
+            raise ValueError(f"{what}: expected (n, {cols}) float32, got {tuple(T.shape)} {T.dtype}")
+        return T.contiguous()
+
+    def _prop_xy(self, X, Y=None):
+        shape = getattr(self, "prop_shape", None)
+        if shape is None:
+            raise ValueError("no proposal: call proposal_init first")
+        X = self._prop_rows(X, shape[0], "X")
+        if Y is None:
+            return X, None
+        Y = self._prop_rows(Y, shape[2], "Y")
+        if Y.shape[0] != X.shape[0]:
+            raise ValueError(f"X has {X.shape[0]} rows, Y {Y.shape[0]}")
+        return X, Y
+
     def proposal_forward(self, X):
         import torch
+        X, _ = self._prop_xy(X)
         Z = torch.empty((X.shape[0], self.prop_shape[2]), dtype=torch.float32, device=X.device)
         self._check(self.lib.am_proposal_forward(self.ctx, C.c_void_p(X.data_ptr()), X.shape[0],
                                                  C.c_void_p(Z.data_ptr())))
         return Z
 
     def proposal_grad(self, X, Y):
+        X, Y = self._prop_xy(X, Y)
         n = self.proposal_n_params()
         g = np.zeros(n, dtype=np.float32)
         loss = C.c_float()
@@ -383,7 +407,8 @@ class Mesher:
         return float(loss.value), g
 
     def proposal_train(self, X, Y, batch: int, steps: int, lr: float) -> np.ndarray:
-        losses = np.zeros(steps, dtype=np.float32)
+        X, Y = self._prop_xy(X, Y)
+        losses = np.zeros(max(int(steps), 0), dtype=np.float32)
         self._check(self.lib.am_proposal_train(self.ctx, C.c_void_p(X.data_ptr()), C.c_void_p(Y.data_ptr()),
                                                X.shape[0], batch, steps, float(lr),
                                                losses.ctypes.data_as(C.c_void_p)))

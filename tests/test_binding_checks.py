@@ -81,3 +81,18 @@ def test_key_arrays_are_checked():
     for bad, N in ((np.zeros((5, 1)), 128), (np.zeros(5), 16), (np.zeros((5, 3)), 128)):
         with pytest.raises(ValueError):
             M._key_array(bad, N)
+
+
+def test_proposal_tensors_are_checked(mesher):
+    # no CUDA here: every host tensor must be refused before a pointer reaches the library
+    import torch
+    mesher.prop_shape = (15, 32, 64)
+    X, Y = torch.zeros((8, 15)), torch.zeros((8, 64))
+    for call in (lambda: mesher.proposal_forward(X), lambda: mesher.proposal_grad(X, Y),
+                 lambda: mesher.proposal_train(X, Y, 4, 2, 1e-3)):
+        with pytest.raises(ValueError):
+            call()
+    assert mesher.lib.calls == []
+    del mesher.prop_shape
+    with pytest.raises(ValueError):
+        mesher.proposal_forward(X)
