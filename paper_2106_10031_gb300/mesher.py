@@ -70,6 +70,12 @@ class Mesh:
 
 
 def _host_view(mesh: Mesh) -> nt.am_mesh:
+    """am_mesh over the arrays of `mesh` (already C-contiguous, of the binding's dtypes); the
+    C side checks offsets and indices, the array lengths are checked here."""
+    F, K = len(mesh.face_offsets) - 1, len(mesh.face_vertices)
+    if (F < 0 or mesh.xyz.ndim != 2 or mesh.xyz.shape[1] != 3 or mesh.edge_planes.shape != (K,)
+            or mesh.face_keys.ndim != 2 or mesh.face_keys.shape[0] != F):
+        raise ValueError("mesh arrays of inconsistent lengths")
     m = nt.am_mesh()
     m.n_vertices, m.n_faces, m.n_corners = len(mesh.xyz), mesh.n_faces, len(mesh.face_vertices)
     m.key_words = mesh.face_keys.shape[1] if mesh.face_keys.ndim == 2 and mesh.face_keys.shape[1] else 1

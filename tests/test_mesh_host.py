@@ -134,3 +134,7 @@ def test_inconsistent_arrays_are_refused(am, oracle_mod):
     bad.face_offsets[1] = bad.face_offsets[0] + 2            # a face with two corners
     with pytest.raises(am.AMError):
         am.triangulate(bad)
+    bad = _shuffled(am, mesh, 4)
+    bad.edge_planes = bad.edge_planes[:-1]                    # arrays of inconsistent lengths
+    with pytest.raises(ValueError):
+        am.canonicalize(bad)
