@@ -10,7 +10,7 @@
  * Everything here is deliberately literal and slow: loops, no BLAS, no
  * blocking, FP64 throughout.  Affine maps are carried in homogeneous form, a
  * row [a_x a_y a_z | a_0] acting on [x; 1]: this is how the biases, which the
- * paper omits "for notational simplicity" (Sec. 2.2), enter every formula.
+ * paper leaves out of its notation (Sec. 2.2), enter every formula.
  *
  * Network format (packed by oracle/oracle.py):
  *   desc  = [L, in_dim, skip_layer, n_1, ..., n_L]          (int32)

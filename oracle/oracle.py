@@ -19,14 +19,15 @@ What it computes (the definition the CUDA path must reproduce):
 Readings of the paper taken here (the CUDA path takes the same ones):
   * biases kept, affine rows [a | a_0] (Sec. 2.2 omits them for notation);
   * a tie a_lk = 0 gives state 0 (Eq. 2);
-  * unbounded cells/faces are clipped to the box [-B, B]^3 (Sec. 3.1 allows
-    faces "towards infinity");
+  * unbounded cells/faces are clipped to the box [-B, B]^3 (Sec. 3.1 lets
+    faces extend without bound);
   * vertex validity (Alg. 1 step 8) uses a distance tolerance delta; rows within
     delta of an accepted vertex are counted as degenerate events;
   * Alg. 2's starting boundary for a seed cell is the row whose in-plane line
     is nearest to the seed point; marched cells start from the switching plane
     and the midpoint of the switching edge (Sec. 4.2.1);
-  * faces of area <= 1e-24 B^2 are dropped and counted (Sec. 3.1 "intersection");
+  * faces of area <= 1e-24 B^2 are dropped and counted (Sec. 3.1: a face exists
+    when the plane meets the cell's interior);
   * seeds come from bisection along a ray (Sec. 4.3.2), stopped when both
     bracket ends share one cell, then the exact affine root in that cell;
   * the sphere-tracing trigger (Sec. 4.3.1) stops after a step budget or once
