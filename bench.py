@@ -650,10 +650,11 @@ def shard_nets(n_nets: int, rank: int, world: int) -> list:
     return list(range(rank, n_nets, world))
 
 
-def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1):
+def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1, box=2.0):
     """The 64-net batch: batch_nets(master_seed=4) (widths 32-256, depths 4-8, sigma in
-    [0.02, 0.1]), one seed ray along +x per net, all of a rank's nets in one persistent
-    launch, the first max_cells cells of the job (split evenly over the ranks).  Sharded by
+    [0.02, 0.1]), one seed ray along +x per net, box [-2, 2]^3 (some of the deeper nets reach
+    past 1.5), all of a rank's nets in one persistent launch, the first max_cells cells of the
+    job (split evenly over the ranks).  Sharded by
     net (shard_nets); value = all ranks' faces / the slowest rank's march time, by am_march's
     CUDA events; strong scaling (the total work is fixed)."""
     import paper_2106_10031_gb300 as am
@@ -675,12 +676,13 @@ def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1):
                 except am.AMError:
                     unseeded += 1
             dist.barrier()
-            m.march(precision=precision, max_cells=cells)
+            m.march(box=box, precision=precision, max_cells=cells)
             runs.append(m.stats())
         st = min(runs[1:], key=lambda x: x["ms_march"])
     faces = dist.allreduce(float(st["faces"]), "sum")
     ms = dist.allreduce(float(st["ms_march"]), "max")
-    return {"workload": f"64 nets of batch_nets(master_seed=4), first {max_cells} cells of the job, {precision}",
+    return {"workload": f"64 nets of batch_nets(master_seed=4), box {box}, first {max_cells} cells of the job, "
+                        f"{precision}",
             "n_gpus": dist.world, "scaling": "strong", "sharding": "nets round robin over the ranks, no exchange",
             "faces": int(faces), "ms": ms, "faces_per_s": faces / (ms / 1e3),
             "rank0": {"nets": len(mine), "unseeded_nets": unseeded, "cells": int(st["cells"]),
