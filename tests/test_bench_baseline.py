@@ -1,0 +1,27 @@
+"""bench.py's CPU baseline on a small budget: the all-core figure next to the single-thread one,
+and the single-thread figure alone when the process pool cannot run.  CPU only."""
+import numpy as np
+import pytest
+
+
+def test_all_cores_and_single_thread():
+    import bench
+    mlp, o, d = bench.workload()
+    base, mesh = bench.cpu_baseline(mlp, o, d, budget_s=0.3)
+    assert base["kind"] == "oracle" and base["unit"] == "faces/s" and base["value"] > 0
+    assert "single_thread" in base and base["single_thread"]["cores"] == 1
+    assert base["cores"] >= 1 and len(mesh.faces) > 0
+
+
+def test_pool_failure_keeps_the_single_thread_figure(monkeypatch):
+    import bench
+    from oracle import parallel
+
+    class Broken:
+        def __init__(self, *a, **k):
+            raise RuntimeError("no workers")
+    monkeypatch.setattr(parallel, "LevelMarcher", Broken)
+    mlp, o, d = bench.workload()
+    base, mesh = bench.cpu_baseline(mlp, o, d, budget_s=0.3)
+    assert base["cores"] == 1 and "all_cores_unavailable" in base and base["value"] > 0
+    assert len(mesh.faces) > 0
