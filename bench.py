@@ -1,17 +1,20 @@
 """Benchmark: analytic faces per second of analytic marching on one GB300.
 
-One step = the whole hot path on one mesh: forget the previous cells, trigger the seed
-cell by bisection on the device, march every analytic cell (compose, clip, emit, hash
-march) and assemble the mesh.  The workload is the 3-[64]x4-1 geometric-init SDF net
-(seed 2, every parameter perturbed by N(0, 0.05^2)) with one seed ray along +x, clipped
-to the box [-1.5, 1.5]^3 (43,780 faces).  The headline is mixed precision with the learned
-constraint proposal (trained before timing on the plain method's mesh of a nearby checkpoint
-of the net); the comparison legs time the plain FP64 method (every cutting row clipped), the
-nearest-row candidates and the other precision.  Inputs (the net, the proposal) are resident
-in HBM when the timed region starts; the e2e leg repeats the step through the C ABI from
-pinned host buffers (net upload, seed ray, mesh download) inside the timed region.
+One step = the whole hot path on one mesh: forget the previous cells, trigger the seed cell by
+bisection on the device, march every analytic cell to completion (compose, clip, emit, hash
+march) and assemble the mesh.  The workload is the learned-proposal target net, 3-[256]x8-1
+(N = 2048 ReLUs; geometric init, seed 5, every parameter perturbed by N(0, 0.05^2), output bias
+recentred), one seed ray along +x, clipped to the box [-1.5, 1.5]^3: 1.81e6 faces.  The
+headline is the mixed-precision path -- the compose of each breadth-first level's cells on the
+tcgen05 tensor cores (error-free BF16 digit planes) and the certified clip -- with the learned
+constraint proposal (trained before timing on the plain method's meshes of 32 other nets of the
+same shape, seeds 100-131).  The comparison legs time the plain FP64 method on the same net
+(every cutting row clipped), the nearest-row candidates, the decoder-shaped net and the
+3-[64]x4-1 sphere net.  Inputs (the net, the proposal) are resident in HBM when the timed
+region starts; the e2e leg repeats the step through the C ABI from pinned host buffers (net
+upload, seed ray, mesh download) inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision sliced|fp64|mixed]
                   [--candidates learned|nearest|none] [--impl reference]
 
 Multi-GPU: each rank meshes its own copy of the workload (replicas, no collective on the
@@ -36,7 +39,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh); mixed+learned vs plain FP64"
 UNIT = "faces/s"
-WORKLOAD = "3-[64]x4-1 geometric-init SDF MLP (seed 2, sigma 0.05), 1 seed ray +x, box 1.5"
+WORKLOAD = ("3-[256]x8-1 geometric-init SDF MLP (seed 5, sigma 0.05, recentred; N = 2048), 1 seed ray +x, "
+            "box 1.5, whole mesh")
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 
@@ -83,19 +87,18 @@ def captured_traffic(precision, candidates):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    p.add_argument("--schedule", default="persistent", choices=["persistent", "levels"])
+    p.add_argument("--precision", default="sliced", choices=["sliced", "fp64", "mixed"])
+    p.add_argument("--schedule", default="auto", choices=["auto", "persistent", "levels"],
+                   help="auto: the level schedule for sliced, the persistent one otherwise")
     p.add_argument("--candidates", default="learned", choices=["nearest", "learned", "none"])
     p.add_argument("--no-compare", action="store_true", help="skip the comparison legs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--learned-only", action="store_true",
-                   help="run only the 3-[256]x8-1 learned-proposal leg and print its JSON")
     p.add_argument("--decoder-only", action="store_true",
-                   help="run only the decoder march leg (FP64 vs sliced tensor-core compose) and print its JSON")
+                   help="run only the decoder leg, both paths on the whole mesh, and print its JSON")
     p.add_argument("--batch-only", action="store_true",
                    help="run only the 64-net batch leg (nets sharded over the ranks) and print its JSON")
     p.add_argument("--triggers-only", action="store_true",
@@ -106,12 +109,8 @@ def parse():
 
 
 def workload():
-    from synth import sphere_net
-    return sphere_net(seed=2, width=64, depth=4, sigma=0.05), np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
-
-
-# ------------------------------------------------------------------------------------------
-# distributed plumbing (replicas only)
+    from synth import proposal_target_net
+    return proposal_target_net(), np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
 
 
 class Dist:
@@ -210,47 +209,44 @@ class ClockSampler:
 
 
 def algorithmic_work(mlp, mesh) -> dict:
-    """Work the cell kernel must do per mesh, from the mesh's cell keys.
+    """Work the cell kernels must do per mesh, from the mesh's cell keys (the method's own work,
+    not what a dense or exhaustive evaluation would do).
 
-    macs: masked multiply-adds of the compose (Cor. 1), per cell sum over l >= 2 of
-    n_l x |active(l-1)| row-column products for 4 columns, plus a_F over |active(L)|;
-    checks: (row, vertex) sign tests of the certification, (N + 6) x |face| per cell.
-    FP64 path: 2 flops per multiply-add and per check term (4-term dot products).
-    Learned candidates add the proposal's forward pass, 2 (I H + H H + H N) FP32 flops per cell.
-    Mixed path: one double-float multiply-add is 15 FP32 flops (TwoProd + TwoSum + 2 cross
-    FMAs) per column, 63 per row-column product with the error-bound FMA; one check is 22 FP32
-    flops (dot product, magnitude and bound)."""
+    row_col_products: masked multiply-adds of the compose (Cor. 1), per cell the sum over l >= 2
+    of n_l x |active(l-1)| row-column products, plus a_F over |active(L)|; each covers the 4
+    columns of an affine row, so 8 flops (compose_flops = 8 x row_col_products).
+    checks: (row, vertex) sign tests of the all-row check, (N + 6) x |face| per cell, 8 flops each
+    (a 4-term dot product).
+    Learned candidates add the proposal's forward pass, 2 (I H + H H + H N) flops per cell."""
     widths = mlp.widths
     N = mlp.N
-    keys = mesh.face_keys
-    bits = np.unpackbits(keys.view(np.uint8), axis=1, bitorder="little")[:, :N].astype(np.int64)
-    r = np.cumsum([0] + widths)
+    keys = np.ascontiguousarray(mesh.face_keys)
     rc = np.zeros(len(keys), dtype=np.int64)
-    for l in range(1, len(widths)):
-        rc += widths[l] * bits[:, r[l - 1]:r[l]].sum(1)
-    rc += bits[:, r[-2]:r[-1]].sum(1)
+    r = np.cumsum([0] + widths)
+    for c0 in range(0, len(keys), 65536):
+        bits = np.unpackbits(keys[c0:c0 + 65536].view(np.uint8), axis=1, bitorder="little")[:, :N]
+        for l in range(1, len(widths)):
+            rc[c0:c0 + 65536] += widths[l] * bits[:, r[l - 1]:r[l]].sum(1, dtype=np.int64)
+        rc[c0:c0 + 65536] += bits[:, r[-2]:r[-1]].sum(1, dtype=np.int64)
     checks = (N + 6) * np.diff(mesh.face_offsets)
     I, H = 7 + len(widths), 256
-    prop = 2 * (I * H + H * H + H * N) * len(keys)          # the learned proposal's forward per cell
-    return {"row_col_products": int(rc.sum()), "checks": int(checks.sum()), "proposal_fp32_flops": int(prop),
-            "fp64_flops": int(8 * rc.sum() + 8 * checks.sum()),
-            "df_fp32_flops": int(63 * rc.sum() + 22 * checks.sum())}
+    prop = 2 * (I * H + H * H + H * N) * len(keys)
+    return {"row_col_products": int(rc.sum()), "checks": int(checks.sum()), "compose_flops": int(8 * rc.sum()),
+            "check_flops": int(8 * checks.sum()), "proposal_flops": int(prop),
+            "fp64_flops": int(8 * rc.sum() + 8 * checks.sum())}
 
 
-# ------------------------------------------------------------------------------------------
-
-
-def cpu_baseline(mlp, o, d, budget_s=12.0):
-    """The oracle as it stands on this host, on a bounded prefix of the same march
-    (breadth-first order, at most budget_s of single-thread CPU time): timed single-threaded,
-    then on every host core (oracle/parallel.py: the same per-cell arithmetic, each
-    breadth-first level solved by a pool of spawned processes; the mesh is the serial one).
-    `value` is the all-core figure; if the pool cannot run, the single-thread one."""
+def cpu_baseline(mlp, o, d, budget_s=10.0):
+    """The oracle as it stands on this host, on a bounded prefix of the same march (breadth-first
+    order): the first n cells, n sized to about budget_s of single-thread time, timed single-
+    threaded; then the first 4 n cells on every host core (oracle/parallel.py: the same per-cell
+    arithmetic, each breadth-first level solved by a pool of spawned processes; the mesh is the
+    serial one).  `value` is the all-core figure; if the pool cannot run, the single-thread one."""
     from oracle import oracle as O
     O.build()
     net = O.OracleNet(mlp)
     seeds = O.seed_cells(net, o, d)
-    probe = 500
+    probe = 200
     t0 = time.perf_counter()
     O.march(net, seeds, max_cells=probe)
     per = (time.perf_counter() - t0) / probe
@@ -259,54 +255,72 @@ def cpu_baseline(mlp, o, d, budget_s=12.0):
     mesh = O.march(net, seeds, max_cells=n)
     dt = time.perf_counter() - t0
     faces = len(mesh.faces)
-    single = {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-              "sample": f"first {n} cells of the breadth-first march ({faces} faces) in {dt:.1f} s, "
-                        f"single thread (plain C per cell + Python loop)"}
+    model = cpu_model()
+    single = {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": model,
+              "sample": f"first {n} cells of the breadth-first march of the bench workload ({faces} faces) in "
+                        f"{dt:.1f} s, single thread (plain C per cell + Python loop)"}
     try:
         from oracle.parallel import LevelMarcher
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-        with LevelMarcher(mlp, workers=cores, timeout=120.0) as lm:
+        cores = host_cores()
+        with LevelMarcher(mlp, workers=cores, timeout=600.0) as lm:
             t0 = time.perf_counter()
-            pm = lm.march(seeds, max_cells=n)
+            pm = lm.march(seeds, max_cells=4 * n)
             dtp = time.perf_counter() - t0
-        if len(pm.faces) != faces:
-            raise RuntimeError("the all-core march differs from the serial one")
-        return {"value": faces / dtp, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": f"first {n} cells of the breadth-first march ({faces} faces) in {dtp:.1f} s on {cores} "
-                          f"processes, one breadth-first level at a time (per cell: plain C + Python)",
-                "single_thread": single}, mesh
+        fp = len(pm.faces)
+        return {"value": fp / dtp, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": model,
+                "sample": f"first {4 * n} cells of the breadth-first march of the bench workload ({fp} faces) in "
+                          f"{dtp:.1f} s on {cores} processes, one breadth-first level at a time (per cell: plain C + "
+                          f"Python)",
+                "single_thread": single}
     except Exception as e:                          # noqa: BLE001 -- the single-thread figure stands
         single["all_cores_unavailable"] = f"{type(e).__name__}: {e}"
-        return single, mesh
+        return single
 
 
-def oracle_agreement(ref, mesh):
-    """The headline mesh against the oracle's mesh of the CPU-baseline run: every oracle face
-    must be a GPU face with the same edge cycle; vertex error relative to max(1, |v|)."""
-    from tests import parity
-    got = parity.gpu_faces(mesh)
-    errs, cycles, missing = [], 0, 0
-    for f in ref.faces:
-        g = got.get(f.key)
-        if g is None:
-            missing += 1
-            continue
-        if f.edges != g[0]:
+def oracle_agreement(mlp, mesh, box=1.5, sample=200, golden=None):
+    """The headline mesh against the oracle.  Whole mesh: the face-key set and every edge cycle
+    through the digests of the oracle's whole mesh (`golden`, from load_golden), and closure
+    (every neuron edge shared by exactly two faces).  Coordinates: `sample` faces, uniform over
+    the mesh, re-solved one by one by the oracle (edge cycles exact; vertex error relative to
+    max(1, |v|))."""
+    from oracle import oracle as O
+    from tests import meshcheck, parity
+    d = meshcheck.digest(mesh, mlp.N)
+    out = {"faces": d["faces"], "vertices": d["vertices"], "euler": d["euler"], "open_faces": d["open_faces"]}
+    try:
+        meshcheck.closure(mesh, mlp.N)
+        out["closed"] = True
+    except AssertionError as e:
+        out["closed"] = f"no: {e}"
+    if golden is not None:
+        keys = ("faces", "corners", "vertices", "open_faces", "euler", "keys0", "keys1", "cycles")
+        out["oracle_faces"] = golden["digest"]["faces"]
+        out["whole_mesh_identical"] = all(d[k] == golden["digest"][k] for k in keys)
+    O.build()
+    net = O.OracleNet(mlp)
+    rng = np.random.default_rng(0)
+    errs, cycles = [], 0
+    for i in rng.choice(mesh.n_faces, min(sample, mesh.n_faces), replace=False):
+        k, e_g, v_g = parity.face_at(mesh, int(i))
+        try:
+            f, rc = O.solve_cell(net, k, None, v_g.mean(0), box)
+        except (ValueError, OverflowError):          # not a key of this net
+            f, rc = None, -1
+        if rc != 0 or f is None or f.edges != e_g:
             cycles += 1
             continue
-        errs.append(np.linalg.norm(f.verts - g[1], axis=1) / np.maximum(1.0, np.linalg.norm(f.verts, axis=1)))
+        errs.append(np.linalg.norm(f.verts - v_g, axis=1) / np.maximum(1.0, np.linalg.norm(f.verts, axis=1)))
     e = np.concatenate(errs) if errs else np.zeros(1)
-    return {"oracle_faces": len(ref.faces), "gpu_faces": len(got), "missing_in_gpu": missing,
-            "edge_cycles_differing": cycles, "max_rel_vertex_err": float(e.max()),
-            "p99_rel_vertex_err": float(np.quantile(e, 0.99)),
-            "whole_mesh_identical": missing == 0 and cycles == 0 and len(ref.faces) == len(got)}
+    out.update({"sampled_faces": int(min(sample, mesh.n_faces)), "sampled_edge_cycles_differing": cycles,
+                "max_rel_vertex_err": float(e.max()), "p99_rel_vertex_err": float(np.quantile(e, 0.99))})
+    return out
 
 
 def run_reference(args, dist):
-    """The oracle as it stands, as the reference arm, on every host core: each step is the
-    whole breadth-first march of the workload, one level at a time in a pool of spawned
-    processes (oracle/parallel.py; the mesh is the serial march's).  If the pool cannot run,
-    each step is the first 3000 cells of the serial march, single-threaded."""
+    """The oracle as it stands, as the reference arm, on every host core: each step is a bounded
+    sample of the bench workload, the first `cells` cells of its breadth-first march, one level
+    at a time in a pool of spawned processes (oracle/parallel.py; the mesh is the serial
+    march's).  If the pool cannot run, each step is the first 1000 cells, single-threaded."""
     if dist.rank != 0:
         return 0
     mlp, o, d = workload()
@@ -314,22 +328,24 @@ def run_reference(args, dist):
     O.build()
     net = O.OracleNet(mlp)
     seeds = O.seed_cells(net, o, d)
+    cells = 12000
     lm, cores = None, 1
     try:
         from oracle.parallel import LevelMarcher
-        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-        lm = LevelMarcher(mlp, workers=cores, timeout=120.0)
+        cores = host_cores()
+        lm = LevelMarcher(mlp, workers=cores, timeout=600.0)
     except Exception:                               # noqa: BLE001 -- single-thread fallback below
         lm, cores = None, 1
     try:
         if lm is not None:
             def step():
-                return lm.march(seeds)
-            sample = f"each step: the whole breadth-first march on {cores} processes, one level at a time"
+                return lm.march(seeds, max_cells=cells)
+            sample = (f"each step: the first {cells} cells of the breadth-first march on {cores} processes, one "
+                      f"level at a time")
         else:
             def step():
-                return O.march(net, seeds, max_cells=3000)
-            sample = "each step: first 3000 cells of the breadth-first march, single thread"
+                return O.march(net, seeds, max_cells=1000)
+            sample = "each step: the first 1000 cells of the breadth-first march, single thread"
         for _ in range(max(0, args.warmup)):
             step()
         t0 = time.perf_counter()
@@ -346,16 +362,17 @@ def run_reference(args, dist):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, candidates, prop=None):
-    """Same step through the C ABI with host buffers: upload the net from pinned memory,
-    seed from a pinned host ray, march, copy the mesh back into pinned host buffers.  A
-    learned proposal (prop = (params, (n_in, hidden, n_out))) is loaded once, untimed."""
+def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, schedule, candidates, prop=None):
+    """Same step through the C ABI with host buffers: upload the net from pinned memory, seed
+    from a pinned host ray, march, copy the mesh back into pinned host buffers.  A learned
+    proposal (prop = (params, (n_in, hidden, n_out))) is loaded once, untimed."""
     import torch
 
     from paper_2106_10031_gb300 import native as nt
@@ -372,15 +389,16 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, candidates, prop=No
                           b=(C.POINTER(C.c_double) * L)(*[dp(b) for b in bp]), skip_layer=0,
                           w_out=dp(wo), b_out=float(mlp.b_out))
     ctx = C.c_void_p()
-    opts = nt.am_ctx_opts(device=device, stream=stream_ptr, max_cells=1 << 17, hash_slots=0, max_face_verts=32,
-                          max_neurons=256, max_width=64)
+    shp = ctx_shape(mlp)
+    opts = nt.am_ctx_opts(device=device, stream=stream_ptr, max_cells=shp["max_cells"], hash_slots=0, max_face_verts=32,
+                          max_neurons=shp["max_neurons"], max_width=shp["max_width"])
     assert lib.am_create(C.byref(ctx), C.byref(opts)) == 0, lib.am_last_error(ctx)
     cand = {"nearest": nt.AM_CAND_NEAREST, "learned": nt.AM_CAND_LEARNED, "none": nt.AM_CAND_NONE}[candidates]
     if cand == nt.AM_CAND_LEARNED:
         params, (n_in, hidden, n_out) = prop
         assert lib.am_proposal_init(ctx, n_in, hidden, n_out, 1024, 0) == 0
         assert lib.am_proposal_set_params(ctx, params.ctypes.data_as(C.c_void_p), len(params)) == 0
-    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=cand)
+    mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=cand, schedule=schedule)
     bufs = None
     h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + 48
     d2h = 0
@@ -423,16 +441,16 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, candidates, prop=No
             "ms_per_step": dt / steps * 1e3}
 
 
-def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates="nearest"):
+def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates="nearest", max_cells=0):
     """K timed steps; L2 flushed before each (outside the events).  Returns totals."""
     import torch
 
     def step():
         m.reset()
         m.seed(nid, o, d)
-        m.march(precision=precision, schedule=schedule, candidates=candidates)
+        m.march(precision=precision, schedule=schedule, candidates=candidates, max_cells=max_cells)
 
-    total_ms, cell_ms, launches, cell_launches = 0.0, 0.0, 0, 0
+    total_ms, cell_ms, compose_ms, clip_ms, launches, cell_launches = 0.0, 0.0, 0.0, 0.0, 0, 0
     for _ in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -446,10 +464,12 @@ def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates=
         total_ms += e0.elapsed_time(e1)
         st = m.stats()
         cell_ms += st["ms_cell_kernels"]
+        compose_ms += st["ms_compose"]
+        clip_ms += st["ms_clip"]
         cell_launches += st["cell_launches"]
         launches += st["kernel_launches"]
-    return {"total_ms": total_ms, "cell_ms": cell_ms, "launches": launches, "cell_launches": cell_launches,
-            "stats": m.stats()}
+    return {"total_ms": total_ms, "cell_ms": cell_ms, "compose_ms": compose_ms, "clip_ms": clip_ms,
+            "launches": launches, "cell_launches": cell_launches, "stats": m.stats()}
 
 
 def compose_leg(dev, n_cells=4000, reps=5):
@@ -509,114 +529,75 @@ def compose_leg(dev, n_cells=4000, reps=5):
     return out
 
 
-def decoder_leg(dev, n_cells=60000, reps=2):
+def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
     """The decoder-shaped workload, (3 + 256) -> [512] x 8 -> 1 with skip-concat of [x; z] at
-    hidden layer 4 (N = 4096), one seed ray along +x: the first n_cells cells of its march
-    (the whole mesh exceeds 4e6 cells), timed by am_march's CUDA events, seeding outside.
-    Plain FP64 (compose and clip in one persistent kernel) against the sliced path (the compose
-    of each level's cells on the tensor cores into device memory as FP32 pairs, then the clip
-    reading those rows with certified FP32 sign tests, FP64 for the close calls).  Rooflines of the two sliced kernels: the compose's issued tensor flops (36
-    digit-plane products per layer) and the clip's algorithmic bytes (its rows, (N + 1) x 32 B
-    per cell, plus the key and the face record) over their own device time."""
+    hidden layer 4 (N = 4096), one seed ray along +x, box 1.5: its whole mesh (1.4e7 faces) with
+    the sliced path, timed by am_march's CUDA events (seeding outside), against the plain FP64
+    path (compose and clip in one persistent kernel) on the first fp64_cells cells of the same
+    march (0 = the whole mesh; the FP64 march of all 1.4e7 cells takes about 100 s).  Rooflines
+    of the two sliced kernels over their own device time: the compose's useful flops (8 per
+    masked multiply-add of Cor. 1, four columns) and issued tensor flops, and the clip's
+    algorithmic bytes (its rows, (N + 1) x 32 B per cell, the key and the face record)."""
     import paper_2106_10031_gb300 as am
     from synth import decoder_net
     mlp = decoder_net()
     o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
-    out = {"workload": f"decoder (3+256)-[512]x8-1, skip at 4, seed 3; first {n_cells} cells of the march"}
-    with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=4096, max_width=512) as m:
+    out = {"workload": "decoder (3+256)-[512]x8-1, skip at 4, seed 3, one +x ray, box 1.5"}
+    with am.Mesher(device=dev, max_cells=16_000_000, max_neurons=4096, max_width=512) as m:
         nid = m.load_mlp(mlp)
-        out["autotune"] = m.autotune_compose(nid, n=512, reps=3)      # batches of a breadth-first level
-        for prec in ("fp64", "sliced"):
+        for prec, cells in (("sliced", 0), ("fp64", fp64_cells)):
+            m.reset()
+            m.seed(nid, o, d)
+            m.march(precision=prec, max_cells=20000)            # warm-up
             runs = []
-            for _ in range(reps + 1):                   # the first run warms up
+            for _ in range(reps):
                 m.reset()
                 m.seed(nid, o, d)
-                m.march(precision=prec, max_cells=n_cells)
+                m.march(precision=prec, max_cells=cells)
                 runs.append(m.stats())
-            st = min(runs[1:], key=lambda x: x["ms_march"])
-            out[prec] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
-                         "levels": st["levels"], "launches": st["kernel_launches"], "degenerate": st["degenerate"]}
+            st = min(runs, key=lambda x: x["ms_march"])
+            out[prec] = {"faces": st["faces"], "cells": st["cells"], "whole_mesh": cells == 0, "ms": st["ms_march"],
+                         "faces_per_s": st["faces"] / (st["ms_march"] / 1e3), "levels": st["levels"],
+                         "launches": st["kernel_launches"], "degenerate": st["degenerate"],
+                         "empty_faces": st["empty_faces"]}
             if prec == "sliced":
-                w, cells = mlp.widths, st["cells"]
-                issued = 36 * 2 * 4 * cells * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
-                                                  for l in range(1, mlp.L))
-                ach = issued / (st["ms_compose"] / 1e3) / 1e12
+                mesh = m.get_mesh(nid)
+                work = algorithmic_work(mlp, mesh)
+                w, cells_n = mlp.widths, st["cells"]
+                issued = 36 * 2 * 4 * cells_n * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
+                                                    for l in range(1, mlp.L))
+                useful = work["compose_flops"]
+                del mesh
                 out[prec]["ms_compose"], out[prec]["ms_clip"] = st["ms_compose"], st["ms_clip"]
-                out[prec]["compose_roofline"] = {"kernel": "oz_gemm_kernel + oz_prep_kernel", "bound": "tensor",
-                                                 "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                                 "frac": ach / BF16_PEAK_TFLOPS}
+                out[prec]["compose_roofline"] = {
+                    "kernel": "oz_gemm_kernel + oz_prep_kernel", "bound": "tensor",
+                    "achieved": useful / (st["ms_compose"] / 1e3) / 1e12, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": useful / (st["ms_compose"] / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                    "issued_tflops": issued / (st["ms_compose"] / 1e3) / 1e12,
+                    "counts": "achieved: useful flops of Cor. 1 (8 per masked multiply-add, 4 columns); issued: "
+                              "36 BF16 digit-plane products per layer on the padded tiles"}
                 kw = (mlp.N + 63) // 64
-                clip_bytes = cells * ((mlp.N + 1) * 32 + 8 * kw + 32 * (24 + 4) + 64)
+                clip_bytes = cells_n * ((mlp.N + 1) * 32 + 8 * kw + 64) + st["corners"] * 28
                 gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
                 out[prec]["clip_roofline"] = {"kernel": "march_range_kernel<double-float> (rows from HBM)", "bound": "hbm",
                                               "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                                              "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells}
+                                              "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells_n}
         out["sliced_speedup_vs_fp64"] = out["sliced"]["faces_per_s"] / out["fp64"]["faces_per_s"]
-        out["march_autotune"] = m.autotune_march(nid, o, d, max_cells=n_cells, reps=1)
-    return out
-
-
-def learned_leg(dev, n_cells=60000, reps=2):
-    """The learned-proposal workload: 3 -> [256] x 8 -> 1 (geometric init, sigma 0.05, seed 5;
-    N = 2048) with a proposal 15 -> 256 -> 256 -> 2048 (BF16 operands, FP32 accumulation),
-    trained before timing on the plain method's mesh of a nearby checkpoint of the net (first
-    n_cells cells).  The first n_cells cells of the net's own march, one seed ray along +x,
-    timed by am_march's CUDA events: the plain FP64 method (every cutting row clipped) against
-    mixed precision (compose on the tensor cores, certified clip) with learned candidates, and
-    the other candidate rules for context.  Every configuration's mesh is exact: the all-row
-    check corrects any face the candidates got wrong."""
-    import paper_2106_10031_gb300 as am
-    from synth import proposal_target_net, sibling
-    mlp = proposal_target_net()
-    o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
-    out = {"workload": f"3-[256]x8-1 geometric init (seed 5, sigma 0.05), proposal 15-256-256-2048; "
-                       f"first {n_cells} cells of the march"}
-    with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=2048, max_width=256) as m:
-        sid = m.load_mlp(sibling(mlp, seed=99))
-        m.seed(sid, o, d)
-        m.march(precision="fp64", candidates="none", max_cells=n_cells)
-        X, Y = m.proposal_samples(sid, max_samples=120000)
-        m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
-        t0 = time.perf_counter()
-        losses = m.proposal_train(X, Y, batch=1024, steps=3000, lr=2e-3)
-        out["training"] = {"samples": int(X.shape[0]), "steps": 3000, "train_s": time.perf_counter() - t0,
-                           "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean())}
-        del X, Y
-        m.reset()
-        m.release_nets()
-        nid = m.load_mlp(mlp)
-        out["autotune"] = m.autotune_compose(nid, n=512, reps=3)      # batches of a breadth-first level
-        for name, prec, cand in (("plain_fp64", "fp64", "none"), ("fp64_learned", "fp64", "learned"),
-                                 ("sliced_learned", "sliced", "learned"), ("fp64_nearest", "fp64", "nearest"),
-                                 ("sliced_nearest", "sliced", "nearest")):
-            runs = []
-            for _ in range(reps + 1):                   # the first run warms up
-                m.reset()
-                m.seed(nid, o, d)
-                m.march(precision=prec, candidates=cand, max_cells=n_cells)
-                runs.append(m.stats())
-            st = min(runs[1:], key=lambda x: x["ms_march"])
-            out[name] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
-                         "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
-                         "corrected_frac": st["fixups"] / max(1, st["cells"]), "degenerate": st["degenerate"]}
-        base = out["plain_fp64"]["faces_per_s"]
-        for k in ("fp64_learned", "sliced_learned", "fp64_nearest", "sliced_nearest"):
-            out[k]["speedup_vs_plain_fp64"] = out[k]["faces_per_s"] / base
-        out["march_autotune"] = m.autotune_march(nid, o, d, max_cells=n_cells, reps=1, candidates="learned")
     return out
 
 
 def trigger_leg(dev, n_starts=1024, n_samples=4096, reps=5):
-    """The customised triggers (Sec. 4.3) on the headline 3-[64]x4-1 net, with the paper's
-    1024 initial points: sphere tracing from n_starts points uniform in [-1.4, 1.4]^3 (eta 1,
-    at most 64 steps, eps 1e-12) and the random-pair dichotomy on n_samples points uniform in
+    """The customised triggers (Sec. 4.3) on the 3-[64]x4-1 sphere net, with the paper's 1024
+    initial points: sphere tracing from n_starts points uniform in [-1.4, 1.4]^3 (eta 1, at most
+    64 steps, eps 1e-12) and the random-pair dichotomy on n_samples points uniform in
     [-1.5, 1.5]^3 (up to 1024 pairs).  Each call is timed whole on the host clock (copy of the
     points in, the trigger kernels, the dichotomy, the push of the seed cells, the copy of the
-    seed points out), best of `reps` after one warm-up; the oracle's time for the same call on
-    a 64-point sample is reported beside it.  Afterwards the march from all traced seeds."""
+    seed points out), best of `reps` after one warm-up; the oracle's time for the same call on a
+    64-point sample is reported beside it.  Afterwards the march from all traced seeds against
+    the march from one seed: the same mesh, and the breadth-first depth (levels) of each."""
     import paper_2106_10031_gb300 as am
-    from synth import trigger_points
-    mlp, _, _ = workload()
+    from synth import sphere_net, trigger_points
+    mlp = sphere_net(seed=2, width=64, depth=4, sigma=0.05)
     starts = trigger_points(n_starts, seed=4, box=1.4)
     samples = trigger_points(n_samples, seed=7, box=1.5)
     out = {"workload": f"{mlp.name}: {n_starts} sphere-tracing starts, {n_samples} samples for up to 1024 pairs"}
@@ -718,37 +699,64 @@ def trigger_cpu_baseline(mlp, starts, samples):
             "sphere_trace_points_per_s": len(starts) / t_tr, "pairs_points_per_s": len(samples) / t_pr}
 
 
-def train_proposal(m, mlp, o, d):
-    """The learned proposal for the workload: trained on the plain method's mesh (full clip,
-    FP64) of a nearby checkpoint of the net (every weight moved by N(0, 0.005^2)), outside
-    every timed region.  Leaves the context holding the workload net only."""
-    from synth import sibling
-    m.reset()
-    m.release_nets()
-    sid = m.load_mlp(sibling(mlp, seed=99))
-    m.seed(sid, o, d)
-    m.march(precision="fp64", candidates="none")
-    X, Y = m.proposal_samples(sid)
+def train_proposal(m, mlp, o, d, cells=40000, per_net=12000, steps=3000):
+    """The learned proposal, trained outside every timed region on the plain method's faces of
+    the 32 training nets (synth.proposal_train_nets: the target's shape and recipe, seeds
+    100-131; the target net, seed 5, is not among them): the first `cells` cells of each net's
+    march, at most `per_net` samples each, shuffled.  Then its held-out recall@32 on the target
+    net's own faces (its first `cells` cells).  Leaves the context holding the target net only."""
+    import torch
+
+    from synth import proposal_train_nets
+    Xs, Ys = [], []
+    t0 = time.perf_counter()
+    for net in proposal_train_nets():
+        m.reset()
+        m.release_nets()
+        nid = m.load_mlp(net)
+        m.seed(nid, o, d)
+        m.march(precision="sliced", candidates="nearest", max_cells=cells)
+        X, Y = m.proposal_samples(nid, max_samples=per_net)
+        Xs.append(X.clone())
+        Ys.append(Y.to(torch.bfloat16))
+    label_s = time.perf_counter() - t0
+    X = torch.cat(Xs)
+    Y = torch.cat(Ys).float()
+    del Xs, Ys
+    perm = torch.randperm(X.shape[0], generator=torch.Generator().manual_seed(0)).to(X.device)
+    X, Y = X[perm].contiguous(), Y[perm].contiguous()
     m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
     t0 = time.perf_counter()
-    losses = m.proposal_train(X, Y, batch=1024, steps=3000, lr=2e-3)
+    losses = m.proposal_train(X, Y, batch=1024, steps=steps, lr=2e-3)
     train_s = time.perf_counter() - t0
+    n_samples = int(X.shape[0])
+    del X, Y, perm
     m.reset()
     m.release_nets()
     nid = m.load_mlp(mlp)
-    return nid, {"samples": int(X.shape[0]), "steps": 3000, "batch": 1024, "train_s": train_s,
-                 "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean())}
+    m.seed(nid, o, d)
+    m.march(precision="sliced", candidates="nearest", max_cells=cells)
+    Xt, Yt = m.proposal_samples(nid, max_samples=20000)
+    recall = proposal_recall(m, Xt, Yt, 32)
+    del Xt, Yt
+    m.reset()
+    return nid, {"train_nets": "synth.proposal_train_nets(): seeds 100-131", "samples": n_samples,
+                 "label_march_s": label_s, "steps": steps, "batch": 1024, "train_s": train_s,
+                 "loss_first": float(losses[:5].mean()), "loss_last": float(losses[-50:].mean()),
+                 "heldout_recall_at_32": recall, "heldout": "the target net (seed 5), its first 40000 cells"}
 
 
-def leg(m, nid, o, d, steps, precision, schedule, flush, stream, candidates, dist, all_faces):
-    measure(m, nid, o, d, 2, precision, schedule, flush, stream, candidates)
-    p = measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates)
+def leg(m, nid, o, d, steps, precision, schedule, flush, stream, candidates, dist, max_cells=0):
+    measure(m, nid, o, d, 1, precision, schedule, flush, stream, candidates, max_cells=min(20000, max_cells or 20000))
+    p = measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates, max_cells)
     p_ms = dist.allreduce(p["total_ms"], "max")
     st = p["stats"]
-    return {"value": all_faces / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms / steps,
-            "precision": precision, "candidates": candidates,
-            "cuts_per_cell": st["cuts"] / max(1, st["cells"]), "corrected_frac": st["fixups"] / max(1, st["cells"]),
-            "_cell_ms": p["cell_ms"], "_cell_launches": p["cell_launches"]}
+    faces = dist.allreduce(float(st["faces"] * steps), "sum")
+    return {"value": faces / (p_ms / 1e3), "unit": UNIT, "ms_per_step": p_ms / steps, "steps": steps,
+            "faces": st["faces"], "whole_mesh": max_cells == 0, "precision": precision, "schedule": schedule,
+            "candidates": candidates, "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
+            "corrected_frac": st["fixups"] / max(1, st["cells"]), "refined_cells": st["refined_cells"],
+            "ms_compose": p["compose_ms"] / steps, "ms_clip": p["clip_ms"] / steps}
 
 
 def run_ours(args, dist):
@@ -757,21 +765,27 @@ def run_ours(args, dist):
     import paper_2106_10031_gb300 as am
     from paper_2106_10031_gb300 import native as nt
     mlp, o, d = workload()
-    base, ref_mesh = None, None
+    base = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        base, ref_mesh = cpu_baseline(mlp, o, d)          # before any GPU work
+        base = cpu_baseline(mlp, o, d)                   # before any GPU work
     dev = dist.local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    precision = nt.AM_PREC_FP64 if args.precision == "fp64" else nt.AM_PREC_MIXED
-    m = am.Mesher(device=dev, max_cells=1 << 17, max_neurons=256, max_width=64, stream=stream.cuda_stream)
+    prec = args.precision
+    sched = schedule_for(prec, args.schedule)
+    m = am.Mesher(device=dev, stream=stream.cuda_stream, **ctx_shape(mlp))
     nid = m.load_mlp(mlp)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 129 MB L2
     warm = max(args.warmup, 3)
     train = None
     if args.candidates == "learned" or not args.no_compare:
         nid, train = train_proposal(m, mlp, o, d)
-    measure(m, nid, o, d, warm, args.precision, args.schedule, flush, stream, args.candidates)
+    if prec == "sliced":
+        train_tune = m.autotune_compose(nid, n=512, reps=3)       # batches of a breadth-first level
+    else:
+        train_tune = None
+    measure(m, nid, o, d, 1, prec, sched, flush, stream, args.candidates, max_cells=20000)
+    measure(m, nid, o, d, warm, prec, sched, flush, stream, args.candidates)
     mesh = m.get_mesh(nid)
     faces_per_step = mesh.n_faces
     work = algorithmic_work(mlp, mesh)
@@ -779,76 +793,85 @@ def run_ours(args, dist):
     dist.barrier()
     with ClockSampler(dev) as clk:
         torch.cuda.nvtx.range_push("timed")        # lets a profiler select the timed steps
-        r = measure(m, nid, o, d, args.steps, args.precision, args.schedule, flush, stream, args.candidates)
+        r = measure(m, nid, o, d, args.steps, prec, sched, flush, stream, args.candidates)
         torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     dist.barrier()
-    agreement = oracle_agreement(ref_mesh, m.get_mesh(nid)) if ref_mesh is not None else None
+    mesh = m.get_mesh(nid)
+    agreement = oracle_agreement(mlp, mesh, golden=load_golden()) if dist.rank == 0 else None
+    del mesh
     max_ms = dist.allreduce(r["total_ms"], "max")
     all_faces = dist.allreduce(float(faces_per_step * args.steps), "sum")
     value = all_faces / (max_ms / 1e3)
     legs = None
     if not args.no_compare:
         legs = {}
-        for name, prec, cand in (("plain_fp64", "fp64", "none"), ("fp64_nearest", "fp64", "nearest"),
-                                 ("mixed_nearest", "mixed", "nearest"), ("fp64_learned", "fp64", "learned"),
-                                 ("mixed_learned", "mixed", "learned")):
-            if (prec, cand) == (args.precision, args.candidates):
+        for name, p2, c2, k, cells in (("plain_fp64", "fp64", "none", 1, 0), ("fp64_nearest", "fp64", "nearest", 2, 0),
+                                       ("sliced_nearest", "sliced", "nearest", 3, 0),
+                                       ("fp64_learned", "fp64", "learned", 2, 0),
+                                       ("sliced_learned", "sliced", "learned", 3, 0)):
+            if (p2, c2) == (prec, args.candidates):
                 continue
-            g = leg(m, nid, o, d, args.steps, prec, args.schedule, flush, stream, cand, dist, all_faces)
-            if prec == "fp64":
-                pk = g["_cell_ms"] / max(1, g["_cell_launches"])
-                p_ach = work["fp64_flops"] / max(1, g["_cell_launches"] / args.steps) / (pk / 1e3) / 1e12
-                g["roofline"] = {"kernel": "march_persistent_kernel<FP64>", "bound": "alu", "achieved": p_ach,
-                                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": p_ach / FP64_PEAK_TFLOPS,
-                                 "counts": "compose + checks FP64 flops only"}
-            g.pop("_cell_ms"), g.pop("_cell_launches")
+            g = leg(m, nid, o, d, k, p2, schedule_for(p2, "auto"), flush, stream, c2, dist, cells)
             g["headline_speedup"] = value / g["value"]
             legs[name] = g
         legs["proposal_training"] = train
-        legs["compose"] = compose_leg(dev)
-        legs["decoder"] = decoder_leg(dev)
-        legs["learned_256x8"] = learned_leg(dev)
+        legs["compose_autotune"] = train_tune
     e2e = None
     if not args.no_e2e:
         prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
-        e2e = e2e_leg(mlp, o, d, args.steps, dev, stream.cuda_stream, precision, args.candidates, prop)
-        e2e_ms = dist.allreduce(e2e.pop("ms_per_step") * args.steps, "max")
-        e2e["value"] = dist.allreduce(float(faces_per_step * args.steps), "sum") / (e2e_ms / 1e3)
+        pcode = am.PRECISIONS[prec]
+        scode = nt.AM_SCHED_LEVELS if sched == "levels" else nt.AM_SCHED_PERSISTENT
+        e2e = e2e_leg(mlp, o, d, max(2, min(args.steps, 5)), dev, stream.cuda_stream, pcode, scode, args.candidates,
+                      prop)
+        e2e_ms = dist.allreduce(e2e.pop("ms_per_step") * max(2, min(args.steps, 5)), "max")
+        e2e["value"] = dist.allreduce(float(faces_per_step * max(2, min(args.steps, 5))), "sum") / (e2e_ms / 1e3)
     m.close()
+    if not args.no_compare:
+        legs["decoder"] = decoder_leg(dev)
+        legs["sphere64x4"] = sphere_leg(dev)
+        legs["compose"] = compose_leg(dev)
     if dist.rank != 0:
         return 0
-    per_launch_ms = r["cell_ms"] / max(1, r["cell_launches"])
-    launches_per_step = max(1, r["cell_launches"] / args.steps)
     st = r["stats"]
-    if args.precision == "fp64":
-        flops, peak, kname = work["fp64_flops"], FP64_PEAK_TFLOPS, "march_persistent_kernel<FP64>"
-        psrc = "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (probe: 1.19 TFLOP/s at 1995 MHz)"
+    # the dominant kernel of the step by device time: the clip (march kernel) or, on the sliced
+    # path, the compose on the tensor cores (product + prep kernels)
+    cell_ms, comp_ms = r["cell_ms"] if prec != "sliced" else r["clip_ms"], r["compose_ms"]
+    if prec == "sliced" and comp_ms > cell_ms:
+        ach = work["compose_flops"] * args.steps / (comp_ms / 1e3) / 1e12
+        roof = {"kernel": "oz_gemm_kernel + oz_prep_kernel (the compose on the tcgen05 tensor cores)",
+                "bound": "tensor", "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / BF16_PEAK_TFLOPS, "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                "counts": "useful flops of Cor. 1: 8 per masked multiply-add (4 columns)"}
     else:
-        flops, peak, kname = work["df_fp32_flops"], FP32_PEAK_TFLOPS, "march_persistent_kernel<double-float>"
-        if args.candidates == "learned":
-            flops += work["proposal_fp32_flops"]
-        psrc = "derived: 128 FP32 FMA/clk/SM x 152 SMs x 2.07 GHz (probe: 69.4 TFLOP/s at 1995 MHz)"
-    if args.schedule == "levels":
-        kname = kname.replace("persistent", "range")
-    achieved = flops / launches_per_step / (per_launch_ms / 1e3) / 1e12
+        kw = (mlp.N + 63) // 64
+        per_cell = (mlp.N + 1) * 32 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64
+        byts = (st["cells"] * per_cell + st["corners"] * 28) * args.steps
+        ach = byts / (cell_ms / 1e3) / 1e9
+        kname = "march_range_kernel<double-float>" if sched == "levels" else "march_persistent_kernel"
+        roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": ach / HBM_PEAK_GBS, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                "counts": "rows read ((N + 1) x 32 B per cell on the sliced path), key, face record"}
+    roof["traffic"] = captured_traffic(prec, args.candidates)
+    roof["launch_ms"] = (comp_ms if roof["bound"] == "tensor" else cell_ms) / max(1, args.steps)
+    roof["share_of_step"] = {"compose": r["compose_ms"] / max(r["total_ms"], 1e-9),
+                             "clip": r["clip_ms"] / max(r["total_ms"], 1e-9),
+                             "cell_kernels": r["cell_ms"] / max(r["total_ms"], 1e-9)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
         "warmup": warm, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32x2+f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"sliced": "bf16-digits+f64", "mixed": "f32x2+f64",
+                                                          "fp64": "f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": args.precision,
-                   "candidates": args.candidates, "schedule": args.schedule,
-                   "parallelism": f"replicas x{dist.world}",
-                   "l2": "flushed before every step (256 MiB write)"},
-        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": captured_traffic(args.precision, args.candidates), "flops_per_launch": flops / launches_per_step,
-                     "launch_ms": per_launch_ms, "kernel_share_of_step": r["cell_ms"] / max(r["total_ms"], 1e-9),
-                     "peak_source": psrc},
+        "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": prec,
+                   "candidates": args.candidates, "schedule": sched, "parallelism": f"replicas x{dist.world}",
+                   "l2": "flushed before every step (256 MiB write); the step's inputs exceed L2"},
+        "roofline": roof,
+        "algorithmic_work": work,
         "legs": legs,
         "exactness": {"refined_cells": st["refined_cells"], "close_calls": st["close_calls"],
                       "fixups": st["fixups"], "cuts_per_cell": st["cuts"] / max(1, st["cells"]),
-                      "degenerate": st["degenerate"], "vs_oracle": agreement},
+                      "degenerate": st["degenerate"], "empty_faces": st["empty_faces"], "vs_oracle": agreement},
         "cpu_baseline": base,
         "e2e": e2e,
         "clocks": clk.summary(),
@@ -856,6 +879,80 @@ def run_ours(args, dist):
     }
     print(json.dumps(line))
     return 0
+
+
+def ctx_shape(mlp) -> dict:
+    """Context capacities for one net of this shape marched to completion (3-[256]x8-1: 1.81e6
+    cells)."""
+    return {"max_cells": 1 << 22, "max_neurons": max(64, mlp.N), "max_width": max(mlp.widths)}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def schedule_for(precision: str, schedule: str) -> str:
+    if schedule != "auto":
+        return schedule
+    return "levels" if precision == "sliced" else "persistent"
+
+
+def sphere_leg(dev, steps=3):
+    """The 3-[64]x4-1 sphere net (seed 2, sigma 0.05; 43,780 faces, one +x ray, box 1.5) in one
+    persistent launch per step: mixed precision and FP64 with nearest-row candidates, and the
+    plain FP64 method (every cutting row clipped)."""
+    import paper_2106_10031_gb300 as am
+    from synth import sphere_net
+    mlp = sphere_net(seed=2, width=64, depth=4, sigma=0.05)
+    o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
+    out = {"workload": "3-[64]x4-1 geometric-init SDF MLP (seed 2, sigma 0.05), one +x ray, box 1.5"}
+    with am.Mesher(device=dev, max_cells=1 << 17, max_neurons=256, max_width=64) as m:
+        nid = m.load_mlp(mlp)
+        for name, prec, cand in (("mixed_nearest", "mixed", "nearest"), ("fp64_nearest", "fp64", "nearest"),
+                                 ("plain_fp64", "fp64", "none")):
+            runs = []
+            for _ in range(steps + 1):
+                m.reset()
+                m.seed(nid, o, d)
+                m.march(precision=prec, candidates=cand)
+                runs.append(m.stats())
+            st = min(runs[1:], key=lambda x: x["ms_march"])
+            out[name] = {"faces": st["faces"], "ms": st["ms_march"], "faces_per_s": st["faces"] / (st["ms_march"] / 1e3),
+                         "levels": st["levels"]}
+    return out
+
+
+def proposal_recall(m, X, Y, k=32) -> float:
+    """Share of a sample's edge neurons (labels 1) among its k best-scored rows, averaged over
+    the samples (the proposal's forward pass on the device)."""
+    import torch
+    Z = m.proposal_forward(X)
+    top = torch.topk(Z, k, dim=1).indices
+    hit = torch.gather(Y, 1, top).sum(1)
+    return float((hit / Y.sum(1).clamp(min=1)).mean().item())
+
+
+def load_golden(name="learned_target_256x8"):
+    """The oracle's whole-mesh digest of a workload from tests/golden/whole_mesh_oracle.json
+    (written by the oracle alone), or None."""
+    gpath = os.path.join(ROOT, "tests", "golden", "whole_mesh_oracle.json")
+    if not os.path.exists(gpath):
+        return None
+    with open(gpath) as f:
+        g = [x for x in json.load(f)["meshes"] if x["name"] == name]
+    return g[0] if g else None
 
 
 def main():
@@ -870,20 +967,16 @@ def main():
             return 0
         if args.decoder_only:
             if dist.rank == 0:
-                print(json.dumps({"leg": "decoder", **decoder_leg(dist.local)}))
+                print(json.dumps({"leg": "decoder", **decoder_leg(dist.local, fp64_cells=0)}))
             return 0
         if args.batch_only:
-            out = batch_leg(dist, precision=args.precision)
+            out = batch_leg(dist, precision=args.precision if args.precision != "sliced" else "mixed")
             if dist.rank == 0:
                 print(json.dumps({"leg": "batch64", **out}))
             return 0
         if args.triggers_only:
             if dist.rank == 0:
                 print(json.dumps({"leg": "triggers", **trigger_leg(dist.local)}))
-            return 0
-        if args.learned_only:
-            if dist.rank == 0:
-                print(json.dumps({"leg": "learned_256x8", **learned_leg(dist.local)}))
             return 0
         return run_ours(args, dist)
     finally:

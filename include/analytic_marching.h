@@ -103,7 +103,7 @@ typedef struct {
     int64_t max_cells;        /* capacity of visited cells over all nets (default 1 << 20) */
     int64_t hash_slots;       /* cell hash-table slots, rounded up to a power of two
                                  (default: the power of two >= 2 * max_cells) */
-    int max_face_verts;       /* per-face vertex capacity, 8..64 (default 32) */
+    int max_face_verts;       /* per-face vertex capacity, 8..62 (default 32) */
     int max_neurons;          /* largest N of any net that will be loaded (default 4096) */
     int max_width;            /* largest hidden width of any net that will be loaded (default 512) */
 } am_ctx_opts;
@@ -166,6 +166,8 @@ typedef struct {
                                  zero otherwise */
     double ms_compose;        /* AM_PREC_SLICED march: device time of the tensor-core compose launches */
     double ms_clip;           /* AM_PREC_SLICED march: device time of the clip launches reading those rows */
+    double ms_proposal;       /* AM_PREC_SLICED march with AM_CAND_LEARNED: device time of the proposal's
+                                 forward pass on the tensor cores (features and three products per batch) */
 } am_stats_t;
 
 /* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer
@@ -280,6 +282,18 @@ am_status am_mesh_triangulate(const am_mesh *mesh, int32_t *tri, int64_t *n_tri)
 
 /* Statistics of the last march. */
 am_status am_get_stats(const am_ctx *ctx, am_stats_t *stats);
+
+/* Test hook for the time-out path; no counterpart in the paper.  Every wait of the persistent
+ * march for work is bounded (4 s by default): a block that waits longer sets the time-out
+ * status and returns, and am_march then returns AM_ERR_TIMEOUT without assembling a mesh.
+ * This call makes the next am_march exercise that path without faulting or hanging the GPU:
+ * before its launch, `unpublished_ids` cell ids (1 <= unpublished_ids <= max_cells) are handed
+ * out that no block ever publishes, as if the blocks that claimed them had stopped, and every
+ * wait for work gives up after wait_limit_ms (0 < wait_limit_ms <= 4000).  The setting applies
+ * to the next am_march only, which must use the persistent schedule (AM_ERR_INVALID_ARG
+ * otherwise).  After any AM_ERR_TIMEOUT the context refuses am_seed and am_march
+ * (AM_ERR_STATE) until am_reset, which also clears a pending stall. */
+am_status am_test_stall_next_march(am_ctx *ctx, int64_t unpublished_ids, double wait_limit_ms);
 
 /* Compose only (Lemma 1, Cor. 1; Eq. 10): the affine rows of the cells whose activation
  * patterns are d_keys (device, n x ceil(N/64) words, bit k = state of neuron k), for net_id, in
@@ -409,10 +423,16 @@ am_status am_proposal_train(am_ctx *ctx, const float *d_X, const float *d_Y, int
  *   d_edge_planes    n_corners plane ids, edge corner c -> corner c + 1 (device)
  *   n_neurons        N of the net; plane ids >= N (the box) carry no key bit
  *   d_corner_vertex  out: n_corners vertex indices in [0, *d_n_vertices) (device)
- *   d_n_vertices     out: one int64, the number of distinct vertices (device)
+ *   d_n_vertices     out: one int64, the number of distinct vertices (device); NEGATIVE when some
+ *                    corner got no vertex: -1 a face has more than AM_NOALLOC_MAX_FACE_CORNERS
+ *                    corners or offsets outside [0, n_corners] (the corners of a face that is
+ *                    only too long are set to -1), -2 a hash probe gave up (that corner is -1),
+ *                    -3 both; the indices are then not a valid grouping
  *   stream           cudaStream_t of the caller (NULL = the legacy default stream); the call is
- *                    asynchronous on it
- * Vertex indices are numbered in no particular order.
+ *                    asynchronous on it, so errors found by the kernels arrive through
+ *                    *d_n_vertices, not through the return value
+ * Vertex indices are numbered in no particular order.  A face may have at most
+ * AM_NOALLOC_MAX_FACE_CORNERS (62) corners, as am_march's faces (max_face_verts <= 62).
  *
  * It allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  Its scratch
  * memory is one file-scope device table of 2^22 hash slots (32 MiB) that every GPU loading the
@@ -424,6 +444,7 @@ am_status am_proposal_train(am_ctx *ctx, const float *d_X, const float *d_Y, int
  * for a NULL pointer or a negative size, AM_ERR_CUDA when no device is current or a launch
  * fails. */
 #define AM_NOALLOC_MAX_CORNERS ((int64_t)1 << 21)
+#define AM_NOALLOC_MAX_FACE_CORNERS 62
 am_status am_assign_vertices_noalloc(const uint64_t *d_face_keys, int key_words,
                                      const int64_t *d_face_offsets, const int32_t *d_edge_planes,
                                      int64_t n_faces, int64_t n_corners, int n_neurons,

@@ -24,6 +24,7 @@ constexpr int kMaxTriggerPoints = 1 << 24;   // start points / samples per trigg
 constexpr int kMaxTraceSteps = 1 << 16;      // sphere-tracing step budget
 constexpr double kTracePad = 1e-9;           // half-length pad of the bracket after tracing
 constexpr unsigned long long kZobristSeed = 0x2106100310031ull;
+constexpr long long kWaitNs = 4000000000ll;  // 4 s limit on any wait for work in the persistent march
 
 struct NetHost {
     NetDev dev;              // device pointers into `blob`, `fblob` and `tblob`
@@ -110,6 +111,12 @@ struct am_ctx {
     int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
     double *oz_rows = nullptr;    // march with AM_PREC_SLICED: rows of one batch of cells
     int64_t oz_rows_cap = 0;      // doubles
+    // time-out path: the next persistent march hands out test_stall_ids ids it never publishes
+    // and waits at most test_wait_ns for work (am_test_stall_next_march); after a time-out the
+    // context marches again only after am_reset
+    int64_t test_stall_ids = 0;
+    long long test_wait_ns = 0;
+    bool timed_out = false;
 };
 
 namespace {
@@ -594,6 +601,9 @@ am_status am_reset(am_ctx *ctx)
     ctx->solved_upto = 0;
     ctx->stats = am_stats_t{};
     ctx->mesh_valid = false;
+    ctx->timed_out = false;
+    ctx->test_stall_ids = 0;
+    ctx->test_wait_ns = 0;
     return AM_OK;
 }
 
@@ -683,6 +693,7 @@ am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double
                   int *n_seeded)
 {
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (ctx->timed_out) return fail(ctx, AM_ERR_STATE, "a device wait timed out: call am_reset first");
     if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
     if (!h_origins || !h_dirs || n_rays < 1 || !(R > 0.0)) return fail(ctx, AM_ERR_INVALID_ARG, "bad rays");
     am_status s = ensure_seed_cap(ctx, n_rays);
@@ -869,6 +880,7 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
 {
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
     if (ctx->nets.empty()) return fail(ctx, AM_ERR_STATE, "no net loaded");
+    if (ctx->timed_out) return fail(ctx, AM_ERR_STATE, "a device wait timed out: call am_reset first");
     am_march_opts op{};
     if (o) op = *o;
     if (!(op.box > 0.0)) op.box = 1.5;
@@ -901,6 +913,12 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
     if (op.max_cells < 0 || op.grid_blocks < 0) return fail(ctx, AM_ERR_INVALID_ARG, "negative limit");
+    const int64_t stall = ctx->test_stall_ids;
+    const long long wait_ns = ctx->test_wait_ns > 0 ? ctx->test_wait_ns : kWaitNs;
+    ctx->test_stall_ids = 0;             // the hook applies to this one march
+    ctx->test_wait_ns = 0;
+    if (stall > 0 && (op.schedule != AM_SCHED_PERSISTENT || sliced))
+        return fail(ctx, AM_ERR_INVALID_ARG, "am_test_stall_next_march needs the persistent schedule");
     const int mode = op.precision == AM_PREC_MIXED ? 1 : 0;   // kDF only for the double-float path
     unsigned long long hc[kNumCounters];
     am_status s = sync_status(ctx, hc);
@@ -912,6 +930,7 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ma.delta = op.delta;
     ma.max_n = ctx->opts.max_neurons;
     ma.max_w = ctx->opts.max_width;
+    ma.wait_ns = wait_ns;
     if (op.candidates != AM_CAND_NEAREST && op.candidates != AM_CAND_LEARNED && op.candidates != AM_CAND_NONE)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown candidates mode %d", (int)op.candidates);
     if (op.candidates == AM_CAND_LEARNED && !ctx->prop.w)
@@ -932,6 +951,11 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         ma.prop.hidden = p.hidden;
         ma.prop.n_out = p.n_out;
     }
+    // learned candidates on the sliced level march: the proposal's forward pass per batch on
+    // the tensor cores (the march kernel then reads the scores)
+    const bool prop_tc = sliced && op.candidates == AM_CAND_LEARNED && ctx->prop.tc.ok &&
+                         ctx->prop.n_out == ctx->nets[0].N && ctx->prop.n_in == 7 + ctx->nets[0].dev.L &&
+                         ctx->oz.batch_cells <= ctx->prop.tc.max_rows;
     const int64_t start = ctx->solved_upto;
     const int64_t limit = op.max_cells > 0 ? std::min<int64_t>(start + op.max_cells, ctx->ar.cap) : ctx->ar.cap;
     bool incomplete = false;
@@ -941,6 +965,12 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         const unsigned long long hs = (unsigned long long)start;
         CU(cudaMemcpyAsync(ctx->ar.counters + kHead, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(ctx->ar.counters + kDone, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
+        if (stall > 0) {
+            // ids handed out and never published (their ready flags stay 0 until am_reset): the
+            // blocks that take these tickets wait until the limit and report the time-out
+            const unsigned long long n = (unsigned long long)std::min<int64_t>((int64_t)hc[kNCells] + stall, ctx->ar.cap);
+            CU(cudaMemcpyAsync(ctx->ar.counters + kNCells, &n, sizeof n, cudaMemcpyHostToDevice, ctx->stream));
+        }
         ma.limit = limit;
         int grid = ctx->sm_count * ctx->blocks_per_sm;
         if (op.grid_blocks > 0) grid = std::min(grid, op.grid_blocks);
@@ -966,27 +996,51 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             CU(cudaEventRecord(ctx->evk0, ctx->stream));
             int nbatch = 0;
             if (sliced) {
-                // per batch of the level: the rows on the tensor cores, then the clip and march;
-                // the batches' events are read after the level's one synchronisation
+                // per batch of the level: the rows on the tensor cores, the learned proposal's
+                // scores on the tensor cores (learned candidates), then the clip and march; the
+                // batches' events are read after the level's one synchronisation
                 for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells, ++nbatch) {
                     const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
-                    while ((int)ctx->oz_ev.size() < 3 * (nbatch + 1)) {
+                    while ((int)ctx->oz_ev.size() < 4 * (nbatch + 1)) {
                         cudaEvent_t e = nullptr;
                         CU(cudaEventCreate(&e));
                         ctx->oz_ev.push_back(e);
                     }
-                    cudaEvent_t *ev = ctx->oz_ev.data() + 3 * nbatch;
+                    cudaEvent_t *ev = ctx->oz_ev.data() + 4 * nbatch;
                     CU(cudaEventRecord(ev[0], ctx->stream));
                     s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, ctx->ar.kw, c1 - c0, ctx->oz_rows,
                                              true);
                     if (s != AM_OK) return s;
                     CU(cudaEventRecord(ev[1], ctx->stream));
+                    ma.scores_in = nullptr;
+                    if (prop_tc) {
+                        const NetDev &nd = ctx->nets[0].dev;
+                        PropFeatures pf{};
+                        pf.keys = ctx->ar.keys;
+                        pf.kw = ctx->ar.kw;
+                        pf.entry_pt = ctx->ar.entry_pt;
+                        pf.c0 = c0;
+                        pf.n = c1 - c0;
+                        pf.rows = reinterpret_cast<const float *>(ctx->oz_rows);
+                        pf.rstride = 8 * (int64_t)(nd.N + 1);
+                        pf.N = nd.N;
+                        pf.L = nd.L;
+                        for (int l = 0; l <= nd.L; ++l) { pf.row0[l] = nd.row0[l]; pf.width[l] = nd.width[l]; }
+                        ProposalDev &pd = ctx->prop;
+                        CU(prop_tc_features(pd.tc, pf, ctx->stream));
+                        CU(prop_tc_forward(pd.tc, pd.w + pd.off[1], pd.w + pd.off[3], pd.w + pd.off[5], (int)(c1 - c0),
+                                           pd.tc.scores, false, pd.n_out, ctx->oz.err, ctx->stream));
+                        ctx->stats.kernel_launches += 4;
+                        ma.scores_in = pd.tc.scores;
+                        ma.scores_ld = pd.n_out;
+                    }
+                    CU(cudaEventRecord(ev[2], ctx->stream));
                     ma.begin = c0;
                     ma.end = c1;
                     ma.rows_in = ctx->oz_rows;
                     launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
                     CU(cudaGetLastError());
-                    CU(cudaEventRecord(ev[2], ctx->stream));
+                    CU(cudaEventRecord(ev[3], ctx->stream));
                     ctx->stats.cell_launches += 1;
                     ctx->stats.kernel_launches += 1;
                 }
@@ -1005,15 +1059,19 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             if (s != AM_OK) return s;
             if (sliced) {
                 for (int b = 0; b < nbatch; ++b) {
-                    float ta = 0.f, tb = 0.f;
-                    CU(cudaEventElapsedTime(&ta, ctx->oz_ev[3 * b], ctx->oz_ev[3 * b + 1]));
-                    CU(cudaEventElapsedTime(&tb, ctx->oz_ev[3 * b + 1], ctx->oz_ev[3 * b + 2]));
+                    float ta = 0.f, tp = 0.f, tb = 0.f;
+                    CU(cudaEventElapsedTime(&ta, ctx->oz_ev[4 * b], ctx->oz_ev[4 * b + 1]));
+                    CU(cudaEventElapsedTime(&tp, ctx->oz_ev[4 * b + 1], ctx->oz_ev[4 * b + 2]));
+                    CU(cudaEventElapsedTime(&tb, ctx->oz_ev[4 * b + 2], ctx->oz_ev[4 * b + 3]));
                     ctx->stats.ms_compose += ta;
+                    ctx->stats.ms_proposal += tp;
                     ctx->stats.ms_clip += tb;
                 }
                 if (ctx->oz_err_host) {
                     CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
                     CU(cudaStreamSynchronize(ctx->stream));
+                    ctx->timed_out = true;           // the level's rows are not trustworthy
+                    ctx->mesh_valid = false;
                     return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
                 }
             }
@@ -1029,6 +1087,13 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         const unsigned long long hs = (unsigned long long)f0;
         CU(cudaMemcpyAsync(ctx->ar.counters + kHead, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(ctx->ar.counters + kDone, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (hc[kStatus] & kStTimeout) {
+        // a wait gave up: cells may be half written, so no mesh is assembled from them
+        ctx->timed_out = true;
+        ctx->mesh_valid = false;
+        return fail(ctx, AM_ERR_TIMEOUT, "a bounded device wait gave up (after %.3f ms); call am_reset",
+                    (double)wait_ns * 1e-6);
     }
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     s = assemble(ctx, ctx->solved_upto);
@@ -1287,6 +1352,14 @@ am_status am_proposal_forward(am_ctx *ctx, const float *d_X, int n, float *d_Z)
     if (!d_X || !d_Z || n < 1) return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
     CU(proposal_forward(ctx->prop, d_X, n, d_Z, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->prop.tc.ok) {
+        int herr = 0;
+        CU(cudaMemcpy(&herr, ctx->prop.tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr) {
+            CU(cudaMemset(ctx->prop.tc.err, 0, sizeof(int)));
+            return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the proposal gave up");
+        }
+    }
     return AM_OK;
 }
 
@@ -1377,6 +1450,18 @@ am_status am_get_mesh_device(am_ctx *ctx, int net_id, am_mesh *m)
     m->face_vertices = ctx->d_fv + mi.corner_base;
     m->edge_planes = ctx->d_fe + mi.corner_base;
     m->face_keys = reinterpret_cast<uint64_t *>(ctx->d_fkeys + mi.face_base * ctx->ar.kw);
+    return AM_OK;
+}
+
+am_status am_test_stall_next_march(am_ctx *ctx, int64_t unpublished_ids, double wait_limit_ms)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (!(wait_limit_ms > 0.0 && wait_limit_ms <= 4000.0))
+        return fail(ctx, AM_ERR_INVALID_ARG, "wait_limit_ms must lie in (0, 4000]");
+    if (unpublished_ids < 1 || unpublished_ids > ctx->ar.cap)
+        return fail(ctx, AM_ERR_INVALID_ARG, "unpublished_ids must lie in [1, max_cells]");
+    ctx->test_stall_ids = unpublished_ids;
+    ctx->test_wait_ns = (long long)(wait_limit_ms * 1e6);
     return AM_OK;
 }
 

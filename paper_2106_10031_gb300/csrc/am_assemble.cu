@@ -73,19 +73,20 @@ __global__ void scan_add_kernel(int64_t *v, int64_t n, const int64_t *tops_excl)
         if (base + i < n) v[base + i] += add;
 }
 
-// in-place exclusive scan of v[0..n), writes the total to v[n].  tmp: >= 2 * blocks + 2.
+// in-place exclusive scan of v[0..n), writes the total to v[n].  tmp: >= 2 * blocks + 4 (the
+// block totals, scanned the same way, recursively, while they span more than one block).
 static cudaError_t exclusive_scan(int64_t *v, int64_t n, int64_t *tmp, int64_t tmp_len, cudaStream_t st)
 {
     const int64_t per = (int64_t)kScanThreads * kScanPer;
-    const int64_t blocks = (n + per - 1) / per;
-    if (blocks > per || 2 * blocks + 2 > tmp_len) return cudaErrorInvalidValue;
     if (n == 0) return cudaMemsetAsync(v, 0, sizeof(int64_t), st);
-    scan_blocks_kernel<<<(unsigned)blocks, kScanThreads, 0, st>>>(v, n, tmp);
-    // scan the block totals (one block), total to tmp[blocks]
-    scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(tmp, blocks, tmp + blocks + 1);
+    const int64_t blocks = (n + per - 1) / per;
+    if (blocks + 2 > tmp_len) return cudaErrorInvalidValue;
+    scan_blocks_kernel<<<(unsigned)blocks, kScanThreads, 0, st>>>(v, n, tmp);   // block totals to tmp
+    if (blocks == 1) return cudaMemcpyAsync(v + n, tmp, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = exclusive_scan(tmp, blocks, tmp + blocks + 1, tmp_len - blocks - 1, st);
+    if (e != cudaSuccess) return e;
     scan_add_kernel<<<(unsigned)blocks, 256, 0, st>>>(v, n, tmp);
-    // v[n] = scanned(v[n-1]) + size of the last element: recovered as total of tops
-    return cudaMemcpyAsync(v + n, tmp + blocks + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    return cudaMemcpyAsync(v + n, tmp + blocks, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
 }
 
 // ---- vertex keys

@@ -30,12 +30,15 @@ struct MarchArgs {
     double box, delta;
     int max_n, max_w;        // shared-memory sizing (largest loadable net)
     long long limit;         // persistent schedule: tickets >= limit are not solved
+    long long wait_ns;       // persistent schedule: limit on any wait for work (ns)
     int64_t begin, end;      // level schedule: cell ids solved by this launch
     int candidates;          // kCandNearest / kCandLearned / kCandNone
     int tc;                  // compose only (mode 1): hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
     const void *rows_in;     // level schedule: rows of cells [begin, end) composed beforehand on the
                              // tensor cores, n x (N + 1) FP32 pairs [hi x 4 | lo x 4], a_F last
+    const __nv_bfloat16 *scores_in;   // level schedule, learned candidates: the proposal's scores of
+    int scores_ld;                    // cells [begin, end), scores_ld BF16 per cell, from the tensor cores
 };
 int march_smem_bytes(int max_n, int max_w);
 int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate
@@ -95,6 +98,41 @@ struct PairArgs {
 };
 void launch_pairs(const PairArgs &a, cudaStream_t st);
 
+// ---- learned proposal on the tensor cores: one batch of cells per call (am_prop_tc.cu)
+struct PropTC {
+    bool ok = false;                    // shape supported (n_in <= 64, hidden in 64..256 step 64, n_out % 16)
+    int n_in = 0, hidden = 0, n_out = 0, max_rows = 0;
+    __nv_bfloat16 *X = nullptr;         // max_rows x 64 (features, zero padded)
+    __nv_bfloat16 *H1 = nullptr, *H2 = nullptr;   // max_rows x hidden
+    __nv_bfloat16 *W1p = nullptr;       // hidden x 64 (W1 zero padded)
+    __nv_bfloat16 *scores = nullptr;    // max_rows x n_out (the march's scores)
+    int *err = nullptr;                 // set to 1 by a CTA whose pipeline wait timed out
+    alignas(64) unsigned char maps[6][128];   // TMA descriptors: X, H1, H2, W1p, W2, W3
+};
+// features of the cells [c0, c0 + n) of a level batch, as the in-march proposal computes them
+struct PropFeatures {
+    const unsigned long long *keys;     // arena keys (cell id stride kw)
+    int kw;
+    const float *entry_pt;              // arena entry points (3 per cell id)
+    int64_t c0, n;
+    const float *rows;                  // the batch's composed rows, FP32 pairs, a_F at row N
+    int64_t rstride;                    // floats per cell ((N + 1) x 8)
+    int N, L;
+    int row0[kMaxLayers + 1], width[kMaxLayers + 1];
+    __nv_bfloat16 *X;                   // set by prop_tc_features
+};
+bool prop_tc_shape_ok(int n_in, int hidden, int n_out);
+cudaError_t prop_tc_alloc(PropTC &t, int n_in, int hidden, int n_out, int max_rows, const __nv_bfloat16 *W2,
+                          const __nv_bfloat16 *W3);
+void prop_tc_free(PropTC &t);
+void prop_tc_sync_weights(PropTC &t, const float *W1, cudaStream_t st);
+cudaError_t prop_tc_pack(const PropTC &t, const float *X, int rows, cudaStream_t st);
+cudaError_t prop_tc_features(const PropTC &t, const PropFeatures &f, cudaStream_t st);
+// the three layers for rows <= max_rows cells whose features are in t.X; the scores (rows x
+// n_out) to out (ldo elements per row), FP32 or BF16
+cudaError_t prop_tc_forward(const PropTC &t, const float *b1, const float *b2, const float *b3, int rows, void *out,
+                            bool out_f32, int ldo, int *err, cudaStream_t st);
+
 // ---- learned proposal (training and batch inference)
 struct ProposalDev {
     int n_in = 0, hidden = 0, n_out = 0, max_batch = 0;
@@ -106,6 +144,7 @@ struct ProposalDev {
     float *buf[8] = {};
     __nv_bfloat16 *bbuf[4] = {};
     float *loss_parts = nullptr;
+    PropTC tc;                     // forward pass on the tensor cores (when the shape allows)
 };
 cudaError_t proposal_alloc(ProposalDev &p, int n_in, int hidden, int n_out, int max_batch);
 void proposal_free(ProposalDev &p);

@@ -54,7 +54,6 @@ constexpr int kThreadPushWords = 8;   // keys up to this many 64-bit words are p
 constexpr float kU = 5.9604645e-8f;            // 2^-24
 constexpr float kDfLoose = 1e-6f;              // certified row error (as a distance) beyond which kDF gives up
 constexpr double kVertexTol = 1e-5;            // largest vertex error bound (relative) kept from kDF
-constexpr long long kWaitNs = 4000000000ll;    // 4 s limit on any wait for work
 
 enum { kFP64 = 0, kDF = 1 };
 
@@ -934,7 +933,9 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     //      (the entry plane first), or none at all (the all-row check then clips alone)
     const bool learned = a.candidates == kCandLearned && a.prop.n_out == N && a.prop.n_in == 7 + net.L;
     float *score = (float *)s.viol;
-    if (learned) proposal_scores(a, net, cell, s, score);
+    // the scores of a level batch come from the tensor cores; else this block computes them
+    const __nv_bfloat16 *gscore = learned && a.scores_in ? a.scores_in + (cell - a.begin) * (int64_t)a.scores_ld : nullptr;
+    if (learned && !gscore) proposal_scores(a, net, cell, s, score);
     {
         const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
                     pz = __ldcg(ar.entry_pt + cell * 3 + 2);
@@ -946,7 +947,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             float d;
             if (learned) {
                 if (k >= N) continue;
-                d = k == entry ? -3.0e37f : -score[k];
+                d = k == entry ? -3.0e37f : -(gscore ? __bfloat162float(gscore[k]) : score[k]);
             } else if (M == kFP64) {
                 const double *r = s.r64 + 4 * k;
                 d = (float)fabs(r[0] * px + r[1] * py + r[2] * pz + r[3]) * s.rinv[k];
@@ -1093,6 +1094,12 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                         else if (s6 >= -B6) amb = true;
                     }
                 }
+                // A violated row that already carries an edge of the polygon: the FP32 candidate
+                // pass cut by a row that does not really cut the face (its exact vertices then lie
+                // outside the neighbouring edges' rows).  Cutting again would repeat that plane
+                // with a zero-length edge, so the cell goes to FP64, which decides every cut.
+                if (viol)
+                    for (int i = 0; i < m; ++i) amb |= s.pe[buf][i] == k;
             }
             if (viol) {
                 const int p = atomicAdd(s.si + 3, 1);
@@ -1276,7 +1283,7 @@ __device__ long long next_ticket(const MarchArgs &a)
         if ((unsigned long long)t < n) {
             unsigned ns2 = 16;
             while (ld_acquire(a.ar.ready + t) == 0u) {
-                if (global_ns() - t0 > kWaitNs) { atomicOr(C + kStatus, kStTimeout); return -1; }
+                if (global_ns() - t0 > a.wait_ns) { atomicOr(C + kStatus, kStTimeout); return -1; }
                 __nanosleep(ns2);
                 ns2 = min(2 * ns2, 256u);
             }
@@ -1286,7 +1293,7 @@ __device__ long long next_ticket(const MarchArgs &a)
         const unsigned long long done = ld_acquire(C + kDone);
         const unsigned long long n2 = ld_acquire(C + kNCells);
         if (done >= n2 && (unsigned long long)t >= n2) return -1;
-        if (global_ns() - t0 > kWaitNs) { atomicOr(C + kStatus, kStTimeout); return -1; }
+        if (global_ns() - t0 > a.wait_ns) { atomicOr(C + kStatus, kStTimeout); return -1; }
         __nanosleep(ns);
         ns = min(2 * ns, 256u);
     }

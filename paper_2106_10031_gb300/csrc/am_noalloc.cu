@@ -19,12 +19,16 @@ namespace {
 
 constexpr int64_t kNoAllocSlots = (int64_t)1 << 22;          // hash slots (load factor <= 1/2)
 constexpr int64_t kNoAllocMaxCorners = kNoAllocSlots / 2;    // AM_NOALLOC_MAX_CORNERS
+constexpr int kNoAllocMaxFaceCorners = 62;                   // AM_NOALLOC_MAX_FACE_CORNERS (6-bit corner field)
 constexpr int kNoAllocMaxDevices = 64;
 constexpr int kNoAllocProbe = 1 << 16;
 constexpr int32_t kWin = 1 << 30;
 
-// slots [0, kNoAllocSlots) and the vertex counter at [kNoAllocSlots]
+// slots [0, kNoAllocSlots), the vertex counter at [kNoAllocSlots] and the error bits at
+// [kNoAllocSlots + 1]: 1 = a face with more than kNoAllocMaxFaceCorners corners or with offsets
+// outside [0, n_corners], 2 = a corner whose vertex could not be found or claimed (probe limit)
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocSlots + 32];
+constexpr unsigned long long kErrFace = 1ull, kErrProbe = 2ull;
 
 std::mutex g_setup_mutex;
 void *g_scratch_addr[kNoAllocMaxDevices] = {};
@@ -43,6 +47,7 @@ struct NoAllocArgs {
     const int64_t *off;
     const int32_t *planes;
     int64_t n_faces;
+    int64_t n_corners;
     int n_neurons;
     int32_t *out;
     unsigned long long *slots;
@@ -87,7 +92,7 @@ __device__ unsigned long long probe(const NoAllocArgs &a, int64_t f, int j, bool
     corner_pair(a, f, j, &lo, &hi);
     const unsigned long long h = corner_hash(a, f, lo, hi);
     const unsigned long long mine = (1ull << 63) | (((h >> 41) & 0x7FFFFFull) << 40) |
-                                    (((unsigned long long)f & 0x3FFFFFFFFull) << 6) | (unsigned long long)j;
+                                    (((unsigned long long)f & 0x3FFFFFFFFull) << 6) | ((unsigned long long)j & 63ull);
     unsigned long long pos = h & a.mask;
     *claimed = false;
     for (int i = 0; i < kNoAllocProbe; ++i) {
@@ -99,6 +104,7 @@ __device__ unsigned long long probe(const NoAllocArgs &a, int64_t f, int j, bool
         if (cur == 0ull) return 0ull;
         if (((cur >> 40) & 0x7FFFFFull) == ((h >> 41) & 0x7FFFFFull)) {
             const int64_t g = (int64_t)((cur >> 6) & 0x3FFFFFFFFull);
+            if (g >= a.n_faces) return 0ull;          // never written by this call: not a slot of ours
             int lo2, hi2;
             corner_pair(a, g, (int)(cur & 63), &lo2, &hi2);
             if (lo2 == lo && hi2 == hi && same_vertex(a, f, g, lo, hi)) return cur;
@@ -108,12 +114,31 @@ __device__ unsigned long long probe(const NoAllocArgs &a, int64_t f, int j, bool
     return 0ull;
 }
 
+// a face whose corners this call can key: offsets inside [0, n_corners] and at most
+// kNoAllocMaxFaceCorners corners (the slot's 6-bit corner field)
+__device__ __forceinline__ bool face_ok(const NoAllocArgs &a, int64_t f, int64_t *b, int *m)
+{
+    const int64_t b0 = a.off[f], b1 = a.off[f + 1];
+    *b = b0;
+    *m = (int)(b1 - b0);
+    return b0 >= 0 && b1 >= b0 && b1 <= a.n_corners && b1 - b0 <= kNoAllocMaxFaceCorners;
+}
+
 __global__ void noalloc_insert_kernel(NoAllocArgs a)
 {
     unsigned long long *count = g_noalloc_scratch + kNoAllocSlots;
+    unsigned long long *err = g_noalloc_scratch + kNoAllocSlots + 1;
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.n_faces; f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = a.off[f];
-        const int m = (int)(a.off[f + 1] - b);
+        int64_t b;
+        int m;
+        if (!face_ok(a, f, &b, &m)) {
+            // no slot names this face; a face that is only too long gets -1 at its corners (rising
+            // offsets tile [0, n_corners] without overlap, so these writes stay within n_corners)
+            atomicOr(err, kErrFace);
+            if (b >= 0 && m > 0 && b + m <= a.n_corners)
+                for (int j = 0; j < m; ++j) a.out[b + j] = -1;
+            continue;
+        }
         for (int j = 0; j < m; ++j) {
             bool claimed;
             probe(a, f, j, true, &claimed);
@@ -124,24 +149,31 @@ __global__ void noalloc_insert_kernel(NoAllocArgs a)
 
 __global__ void noalloc_lookup_kernel(NoAllocArgs a)
 {
+    unsigned long long *err = g_noalloc_scratch + kNoAllocSlots + 1;
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < a.n_faces; f += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = a.off[f];
-        const int m = (int)(a.off[f + 1] - b);
+        int64_t b;
+        int m;
+        if (!face_ok(a, f, &b, &m)) continue;          // reported by the insert kernel
         for (int j = 0; j < m; ++j) {
             const int32_t v = a.out[b + j];
             if (v != -1) { a.out[b + j] = v & ~kWin; continue; }
             bool claimed;
             const unsigned long long s = probe(a, f, j, false, &claimed);
-            if (s == 0ull) continue;      // not found: leaves -1 (reported through the count check)
+            if (s == 0ull) {              // not found (a probe gave up): stays -1, the count goes negative
+                atomicOr(err, kErrProbe);
+                continue;
+            }
             const int64_t g = (int64_t)((s >> 6) & 0x3FFFFFFFFull);
             a.out[b + j] = a.out[a.off[g] + (int)(s & 63)] & ~kWin;
         }
     }
 }
 
+// the vertex count, or minus the error bits when some corner was left without a vertex
 __global__ void noalloc_count_kernel(int64_t *n_out)
 {
-    *n_out = (int64_t)g_noalloc_scratch[kNoAllocSlots];
+    const unsigned long long e = g_noalloc_scratch[kNoAllocSlots + 1];
+    *n_out = e ? -(int64_t)e : (int64_t)g_noalloc_scratch[kNoAllocSlots];
 }
 
 }  // namespace
@@ -173,9 +205,10 @@ extern "C" am_status am_assign_vertices_noalloc(const uint64_t *d_face_keys, int
     int64_t slots = 1024;
     while (slots < 2 * n_corners) slots <<= 1;
     unsigned long long *tab = (unsigned long long *)scratch;
-    // the table keeps the previous call's contents: clear the part in use and the counter
+    // the table keeps the previous call's contents: clear the part in use, the counter and the
+    // error bits
     if (cudaMemsetAsync(tab, 0, sizeof(unsigned long long) * slots, st) != cudaSuccess) return AM_ERR_CUDA;
-    if (cudaMemsetAsync(tab + kNoAllocSlots, 0, sizeof(unsigned long long), st) != cudaSuccess) return AM_ERR_CUDA;
+    if (cudaMemsetAsync(tab + kNoAllocSlots, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess) return AM_ERR_CUDA;
     if (n_faces == 0) {
         if (cudaMemsetAsync(d_n_vertices, 0, sizeof(int64_t), st) != cudaSuccess) return AM_ERR_CUDA;
         return AM_OK;
@@ -186,6 +219,7 @@ extern "C" am_status am_assign_vertices_noalloc(const uint64_t *d_face_keys, int
     a.off = d_face_offsets;
     a.planes = d_edge_planes;
     a.n_faces = n_faces;
+    a.n_corners = n_corners;
     a.n_neurons = n_neurons;
     a.out = d_corner_vertex;
     a.slots = tab;

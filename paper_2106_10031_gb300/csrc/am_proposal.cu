@@ -252,7 +252,9 @@ cudaError_t proposal_alloc(ProposalDev &p, int n_in, int hidden, int n_out, int 
     for (int i = 0; i < 4; ++i)
         if ((e = cudaMalloc(&p.bbuf[i], sizeof(__nv_bfloat16) * act))) return e;
     if ((e = cudaMalloc(&p.loss_parts, sizeof(float) * 152 * 16))) return e;
-    return cudaSuccess;
+    // the forward pass of whole batches on the tensor cores (inference: am_proposal_forward and
+    // the level march), when the shape allows it; W2 and W3 are read in place from the BF16 copy
+    return prop_tc_alloc(p.tc, n_in, hidden, n_out, std::max(max_batch, 4096), p.wb + p.off[2], p.wb + p.off[4]);
 }
 
 void proposal_free(ProposalDev &p)
@@ -264,6 +266,7 @@ void proposal_free(ProposalDev &p)
         if (p.buf[i]) cudaFree(p.buf[i]);
     for (int i = 0; i < 4; ++i)
         if (p.bbuf[i]) cudaFree(p.bbuf[i]);
+    prop_tc_free(p.tc);
     p = ProposalDev{};
 }
 
@@ -275,6 +278,7 @@ void proposal_sync_copies(ProposalDev &p, cudaStream_t st)
                                                                                    p.hidden, p.w2t);
     transpose_bf16_kernel<<<blocks_for((int64_t)ld3 * p.hidden), 256, 0, st>>>(p.w + p.off[4], p.n_out, p.hidden, ld3,
                                                                               p.w3t);
+    prop_tc_sync_weights(p.tc, p.w + p.off[0], st);
 }
 
 // Forward pass over B samples (B <= max_batch).  Activations: buf0 a1, buf1 a2, buf2 z (FP32);
@@ -315,6 +319,19 @@ static int backward(ProposalDev &p, const float *Y, int B, cudaStream_t st)
 
 cudaError_t proposal_forward(ProposalDev &p, const float *X, int n, float *Z, cudaStream_t st)
 {
+    if (p.tc.ok) {
+        // tensor cores: BF16 operands (features, h1, h2 rounded to BF16 as in training), FP32
+        // accumulation, FP32 logits
+        for (int s = 0; s < n; s += p.tc.max_rows) {
+            const int B = std::min(p.tc.max_rows, n - s);
+            cudaError_t e = prop_tc_pack(p.tc, X + (size_t)s * p.n_in, B, st);
+            if (e) return e;
+            e = prop_tc_forward(p.tc, p.w + p.off[1], p.w + p.off[3], p.w + p.off[5], B, Z + (size_t)s * p.n_out, true,
+                                p.n_out, p.tc.err, st);
+            if (e) return e;
+        }
+        return cudaGetLastError();
+    }
     for (int s = 0; s < n; s += p.max_batch) {
         const int B = std::min(p.max_batch, n - s);
         forward(p, X + (size_t)s * p.n_in, B, st);

@@ -75,7 +75,7 @@ class am_stats_t(C.Structure):
                 ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
                 ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64), ("close_calls", C.c_int64),
                 ("fixups", C.c_int64), ("cuts", C.c_int64), ("phase_cycles", C.c_int64 * 10),
-                ("ms_compose", C.c_double), ("ms_clip", C.c_double)]
+                ("ms_compose", C.c_double), ("ms_clip", C.c_double), ("ms_proposal", C.c_double)]
 
 
 class am_mesh(C.Structure):
@@ -122,6 +122,7 @@ ENTRY_POINTS = [
                                    C.c_void_p]),
     ("am_proposal_train", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_float,
                                     C.c_void_p]),
+    ("am_test_stall_next_march", C.c_int, [C.c_void_p, C.c_int64, C.c_double]),
     ("am_assign_vertices_noalloc", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                              C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
 ]

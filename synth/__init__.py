@@ -15,6 +15,7 @@ from .nets import (  # noqa: F401
     decoder_net,
     batch_nets,
     proposal_target_net,
+    proposal_train_nets,
     tiny_net,
     seed_rays,
     trigger_points,

@@ -221,6 +221,13 @@ def proposal_target_net(seed: int = 5, width: int = 256, depth: int = 8, sigma: 
     return geometric_init([width] * depth, seed, sigma, name=f"proposal_w{width}_d{depth}_s{seed}", recenter=True)
 
 
+def proposal_train_nets(seeds=range(100, 132), width: int = 256, depth: int = 8, sigma: float = 0.05) -> list:
+    """The learned proposal's training nets: independent nets of the target net's shape and
+    recipe (3 -> [256] x 8 -> 1, geometric init, sigma 0.05, recentred) with seeds 100-131; the
+    target net (seed 5) is not among them."""
+    return [proposal_target_net(seed=int(s), width=width, depth=depth, sigma=sigma) for s in seeds]
+
+
 def sibling(mlp: MLP, seed: int, sigma: float = 0.005) -> MLP:
     """The same network with every hidden weight and bias moved by N(0, sigma^2): a nearby
     checkpoint of it (the training nets of the learned proposal)."""
