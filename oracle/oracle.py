@@ -287,7 +287,11 @@ class Face:
 
 
 def newell(V: np.ndarray) -> np.ndarray:
-    return np.cross(V, np.roll(V, -1, axis=0)).sum(0)
+    """Twice the vector area of the closed polygon V: the sum of V_i x V_{i+1}, taken about the
+    first vertex (the sum is translation invariant), so that a face far smaller than its
+    distance from the origin keeps its area instead of cancelling to zero."""
+    D = V - V[0]
+    return np.cross(D, np.roll(D, -1, axis=0)).sum(0)
 
 
 def canonical_face(key: int, V: np.ndarray, edges: list, aF: np.ndarray, ndeg: int = 0) -> Face:
@@ -319,6 +323,7 @@ class Mesh:
     faces: list = field(default_factory=list)
     failed: list = field(default_factory=list)      # (key, rc)
     empty: int = 0
+    empty_cells: list = field(default_factory=list)  # (key, face) of the cells dropped as empty
     degenerate: int = 0
     seeds: list = field(default_factory=list)       # (key, point)
 
@@ -451,6 +456,7 @@ def march(net: OracleNet, seeds, box=DEFAULT_BOX, delta=DEFAULT_DELTA, max_cells
             continue
         if f.area() <= area_min:
             mesh.empty += 1
+            mesh.empty_cells.append((key, f))
             continue
         mesh.faces.append(f)
         mesh.degenerate += f.ndeg

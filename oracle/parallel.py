@@ -115,6 +115,7 @@ class LevelMarcher:
                     continue
                 if area <= area_min:
                     mesh.empty += 1
+                    mesh.empty_cells.append((key, f))
                     continue
                 mesh.faces.append(f)
                 mesh.degenerate += f.ndeg

@@ -53,9 +53,11 @@ def whole_mesh(name, gen, call, box, workers):
         mesh = lm.march(seeds)
     dt = time.perf_counter() - t0
     d = meshcheck.digest(meshcheck.ArrayMesh(mesh, mlp.N), mlp.N)
+    empty = [{"key": f"{k:x}", "edges": f.edges, "verts": f.verts.tolist(), "area": f.area()}
+             for k, f in mesh.empty_cells]
     return {"name": name, "net": call, "N": mlp.N, "box": box, "seed_ray": "origin, +x, R = 2",
             "oracle": {"empty": mesh.empty, "degenerate": mesh.degenerate, "failed": len(mesh.failed),
-                       "cells": len(mesh.faces) + mesh.empty + len(mesh.failed)},
+                       "cells": len(mesh.faces) + mesh.empty + len(mesh.failed), "empty_cells": empty},
             "digest": d, "oracle_seconds": round(dt, 1), "workers": workers}
 
 

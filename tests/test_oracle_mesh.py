@@ -145,3 +145,21 @@ def test_invariants_sphere_net(oracle_mod, sphere_mesh):
     net, mesh = sphere_mesh
     assert len(mesh.faces) > 10000 and not mesh.failed and mesh.degenerate == 0
     _check_invariants(net, mesh, closed=True, chi=2)
+
+
+def test_face_area_of_a_tiny_face_far_from_the_origin(oracle_mod):
+    # A face whose sides (3.4e-9) are long next to delta but tiny next to its distance from the
+    # origin: its area (closed form 1/2 |a x b|, here 5e-18) must survive, far above the 1e-24 B^2
+    # threshold below which a face is dropped as empty.  Summing V_i x V_{i+1} on the absolute
+    # coordinates cancels to 0 in FP64; about the first vertex it keeps the closed form.
+    p0 = np.array([0.7, -1.1, 0.9])
+    a = np.array([3.3e-9, 0.4e-9, -0.2e-9])
+    b = np.array([-0.6e-9, 3.1e-9, 1.1e-9])
+    V = np.stack([p0, p0 + a, p0 + b])
+    exact = 0.5 * np.linalg.norm(np.cross(a, b))
+    f = oracle_mod.Face(key=0, edges=[0, 1, 2], verts=V, aF=np.array([0.0, 0.0, 1.0, 0.0]))
+    assert abs(f.area() - exact) <= 1e-6 * exact, (f.area(), exact)
+    assert f.area() > 1e-24 * 1.5 ** 2
+    # and the orientation test sees the same normal as the closed form
+    nrm = oracle_mod.newell(V)
+    assert np.dot(nrm, np.cross(a, b)) > 0.0
