@@ -563,9 +563,8 @@ def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
             if prec == "sliced":
                 mesh = m.get_mesh(nid)
                 work = algorithmic_work(mlp, mesh)
-                w, cells_n = mlp.widths, st["cells"]
-                issued = 36 * 2 * 4 * cells_n * sum(-(-w[l] // 128) * 128 * (-(-w[l - 1] // 64) * 64)
-                                                    for l in range(1, mlp.L))
+                cells_n = st["cells"]
+                issued = 2 * st["tensor_macs"]                  # BF16 digit-plane products issued
                 useful = work["compose_flops"]
                 del mesh
                 out[prec]["ms_compose"], out[prec]["ms_clip"] = st["ms_compose"], st["ms_clip"]
@@ -575,7 +574,8 @@ def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
                     "frac": useful / (st["ms_compose"] / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
                     "issued_tflops": issued / (st["ms_compose"] / 1e3) / 1e12,
                     "counts": "achieved: useful flops of Cor. 1 (8 per masked multiply-add, 4 columns); issued: "
-                              "36 BF16 digit-plane products per layer on the padded tiles"}
+                              "the BF16 digit-plane products the compose launched (36 per layer on the padded "
+                              "tiles; one column per rank-1 cell, four per full compose)"}
                 kw = (mlp.N + 63) // 64
                 clip_bytes = cells_n * ((mlp.N + 1) * 32 + 8 * kw + 64) + st["corners"] * 28
                 gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
@@ -820,7 +820,8 @@ def run_ours(args, dist):
     e2e = None
     if not args.no_e2e:
         prop = (m.proposal_params(), m.prop_shape) if args.candidates == "learned" else None
-        pcode = am.PRECISIONS[prec]
+        from paper_2106_10031_gb300.mesher import PRECISIONS
+        pcode = PRECISIONS[prec]
         scode = nt.AM_SCHED_LEVELS if sched == "levels" else nt.AM_SCHED_PERSISTENT
         e2e = e2e_leg(mlp, o, d, max(2, min(args.steps, 5)), dev, stream.cuda_stream, pcode, scode, args.candidates,
                       prop)
@@ -839,10 +840,11 @@ def run_ours(args, dist):
     cell_ms, comp_ms = r["cell_ms"] if prec != "sliced" else r["clip_ms"], r["compose_ms"]
     if prec == "sliced" and comp_ms > cell_ms:
         ach = work["compose_flops"] * args.steps / (comp_ms / 1e3) / 1e12
-        roof = {"kernel": "oz_gemm_kernel + oz_prep_kernel (the compose on the tcgen05 tensor cores)",
+        roof = {"kernel": "oz_gemm_kernel + oz_prep_kernel + rank-1 kernels (the compose on the tcgen05 tensor cores)",
                 "bound": "tensor", "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / BF16_PEAK_TFLOPS, "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
-                "counts": "useful flops of Cor. 1: 8 per masked multiply-add (4 columns)"}
+                "counts": "useful flops of Cor. 1: 8 per masked multiply-add (4 columns)",
+                "issued_tflops": 2 * st["tensor_macs"] / (comp_ms / args.steps / 1e3) / 1e12}
     else:
         kw = (mlp.N + 63) // 64
         per_cell = (mlp.N + 1) * 32 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64

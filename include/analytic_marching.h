@@ -64,7 +64,9 @@ typedef enum {
                                  rigorous error bound per row; vertices solved in FP64; every
                                  sign test certified against the bounds (FP32, then FP64 for
                                  close calls); a cell with an undecidable test is redone in FP64 */
-    AM_PREC_TENSOR = 2,       /* am_compose only: the hidden layers on the tensor cores, W and Z
+    AM_PREC_TENSOR = 2,       /* am_compose only, kept as the measured baseline that AM_PREC_SLICED
+                                 replaces (legacy mma.sync, not tcgen05): the hidden layers on the
+                                 tensor cores, W and Z
                                  split into three BF16 parts, four mma.sync products per tile
                                  accumulated in FP32 (about 1e-6 relative); each row carries an
                                  error ESTIMATE (random-sign model of the accumulation with a
@@ -168,6 +170,10 @@ typedef struct {
     double ms_clip;           /* AM_PREC_SLICED march: device time of the clip launches reading those rows */
     double ms_proposal;       /* AM_PREC_SLICED march with AM_CAND_LEARNED: device time of the proposal's
                                  forward pass on the tensor cores (features and three products per batch) */
+    int64_t clip_fallbacks;   /* AM_PREC_SLICED march: cells the warp-per-cell clip handed to the block
+                                 kernel (a test it could not decide outright, a large polygon) */
+    int64_t tensor_macs;      /* AM_PREC_SLICED: BF16 multiply-adds the compose issued on the tensor cores
+                                 (36 digit-plane products per layer over the padded tiles) */
 } am_stats_t;
 
 /* Assembled mesh of one net.  Two-call protocol for am_get_mesh: with every array pointer
@@ -306,6 +312,25 @@ am_status am_test_stall_next_march(am_ctx *ctx, int64_t unpublished_ids, double 
 am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n, am_precision precision,
                      double *d_rows, float *d_err);
 
+/* Rank-1 neighbour compose (Cor. 1 across one flipped neuron; Alg. 1 step 10): the rows of the n
+ * cells key(parent i) XOR e_{flip[i]} from their parents' rows.  Crossing the plane of neuron k of
+ * layer l leaves Z_1..Z_l unchanged (the sign of row k flips with its state), and for j > l Z_j
+ * changes by the rank-1 term v_j a^T: a = the parent's signed row k, v_{l+1} = W_{l+1}[:, k],
+ * v_j = W_j diag(s_{j-1}) v_{j-1}; a_F by (w_out . diag(s_L) v_L) a (w_out[k] a when l = L).  The
+ * products run on the tcgen05 tensor cores as in AM_PREC_SLICED, with one operand column per
+ * cell instead of four.  This is the compose the AM_PREC_SLICED march uses for most cells (see
+ * am_tuning.rank1_period); this call exposes it on caller arrays:
+ *   d_parent_keys  n x ceil(N/64) words, the parents' activation patterns (device)
+ *   d_parent_rows  n x (N + 1) x 4 doubles, the parents' rows as am_compose writes them (device)
+ *   d_flip         n neuron ids in [0, N), the neuron each child flips (device)
+ *   d_rows         out: n x (N + 1) x 4 doubles, the children's rows in am_compose's layout (device)
+ * The parents' rows are taken to 48 bits (FP32 pairs, the march's representation) on input.
+ * Synchronous; allocates its scratch per call.  AM_ERR_INVALID_ARG for a flip outside [0, N) or a
+ * net whose fan-ins exceed the sliced path's limit; AM_ERR_TIMEOUT if a tensor-core pipeline wait
+ * gave up. */
+am_status am_compose_neighbors(am_ctx *ctx, int net_id, const uint64_t *d_parent_keys, const double *d_parent_rows,
+                               const int32_t *d_flip, int64_t n, double *d_rows);
+
 /* ---- launch shapes and autotuning --------------------------------------------------------
  * No counterpart in the paper: these calls change how fast a result is computed, never the
  * result.  Kernels with more than one valid launch shape read it from the context;
@@ -319,6 +344,15 @@ typedef struct {
                                  0 (default) = automatic per batch and layer: the 32-cell tile
                                  when n_{l-1} > 448 (8 K chunks) and its tiles, split over up to
                                  4 K ranges, fill every SM, else the 16-cell tile */
+    int rank1_period;         /* AM_PREC_SLICED march: a cell entered across neuron k of layer l keeps its
+                                 parent's rows Z_1..Z_l and gets Z_{l+1..L} and a_F by a rank-1 update
+                                 from the parent's rows (one operand column instead of four, Cor. 1);
+                                 every rank1_period-th generation of a chain is composed in full,
+                                 which bounds the rounding the updates accumulate.  1 = always in
+                                 full; 0 (default) = 8 */
+    int clip_kernel;          /* AM_PREC_SLICED march with candidates: 0 (default) = one warp per cell for
+                                 every cell whose tests it decides outright, the block kernel for the
+                                 rest; 1 = the block kernel (one block per cell) for every cell */
 } am_tuning;
 
 /* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */

@@ -109,8 +109,18 @@ struct am_ctx {
     ProposalDev prop;
     OzScratch oz;                 // sliced tensor-core compose (allocated on first use)
     int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
-    double *oz_rows = nullptr;    // march with AM_PREC_SLICED: rows of one batch of cells
-    int64_t oz_rows_cap = 0;      // doubles
+    int oz_rank1_period = 0;      // rank-1 compose: full compose every this many generations (0 = 8)
+    int clip_kernel = 0;          // sliced march: 0 warp-per-cell clip with block fallback, 1 block kernel
+    int32_t *fb_list = nullptr;   // the warp clip's fallback cells (one chunk of a level) and their count
+    unsigned long long *fb_count = nullptr;
+    // march with AM_PREC_SLICED: the rows of the level being solved and of the level before it
+    // (the parents of the next level's rank-1 composes), FP32 pairs, (N + 1) x 32 B per cell
+    double *lv_rows[2] = {nullptr, nullptr};
+    int64_t lv_cap[2] = {0, 0};   // cells
+    R1Scratch r1;
+    unsigned long long r1_hcounts[kMaxLayers + 1] = {};
+    bool r1_planned = false;      // the cells of the next level are classified (r1_hcounts valid)
+    int64_t r1_prev0 = 0;         // first cell of the level whose rows the other buffer holds
     // time-out path: the next persistent march hands out test_stall_ids ids it never publishes
     // and waits at most test_wait_ns for work (am_test_stall_next_march); after a time-out the
     // context marches again only after am_reset
@@ -187,6 +197,7 @@ am_status ensure_oz_scratch(am_ctx *ctx)
     if (ctx->oz.B) return AM_OK;
     OzScratch &z = ctx->oz;
     z.batch_cells = 4096;
+    z.issued = &ctx->stats.tensor_macs;
     CU(cudaMalloc(&z.B, sizeof(__nv_bfloat16) * oz_scratch_elems(z.batch_cells, oz_kp(ctx->opts.max_width))));
     CU(cudaMalloc(&z.eB[0], sizeof(int) * 4 * z.batch_cells));
     CU(cudaMalloc(&z.eB[1], sizeof(int) * 4 * z.batch_cells));
@@ -209,6 +220,7 @@ OzNet oz_view(const NetHost &nh)
         v.Cl[l] = d.Cl[l];
         v.Clhi[l] = d.Clhi[l];
         v.Cllo[l] = d.Cllo[l];
+        v.AT[l] = d.AT[l];
         if (l >= 2) {
             v.eA[l] = reinterpret_cast<const int *>(reinterpret_cast<const unsigned char *>(nh.ozblob) + nh.oz_off_eA[l]);
             v.mapA[l] = nh.ozmap[l].b;
@@ -310,6 +322,9 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(cudaMalloc(&ar.ready, sizeof(unsigned) * ar.cap));
     CU(cudaMalloc(&ar.entry_plane, sizeof(int32_t) * ar.cap));
     CU(cudaMalloc(&ar.entry_pt, sizeof(float) * 3 * ar.cap));
+    CU(cudaMalloc(&ar.parent, sizeof(int32_t) * ar.cap));
+    CU(cudaMalloc(&ar.chain, sizeof(int32_t) * ar.cap));
+    CU(cudaMalloc(&ar.cls, sizeof(int32_t) * ar.cap));
     CU(cudaMalloc(&ar.slots, sizeof(unsigned long long) * d.hash_slots));
     CU(cudaMalloc(&ar.counters, sizeof(unsigned long long) * kNumCounters));
     {
@@ -337,6 +352,7 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     CU(prepare_march_kernels(d.max_neurons, d.max_width, &ctx->blocks_per_sm));
     if (ctx->blocks_per_sm < 1) return fail(ctx, AM_ERR_CUDA, "the march kernel cannot be resident");
     CU(prepare_seed_kernels(d.max_neurons, d.max_width));
+    CU(prepare_clip_warp());
     CU(cudaStreamSynchronize(ctx->stream));
     return AM_OK;
 }
@@ -350,7 +366,7 @@ void am_destroy(am_ctx *ctx)
     }
     Arena &ar = ctx->ar;
     void *bufs[] = {ar.keys, ar.net, ar.hash, ar.nverts, ar.edges, ar.verts, ar.slots, ar.counters,
-                    ar.ready, ar.entry_plane, ar.entry_pt,
+                    ar.ready, ar.entry_plane, ar.entry_pt, ar.parent, ar.chain, ar.cls,
                     (void *)ar.zob, ctx->d_nets, ctx->d_netcnt, ctx->d_rays, ctx->d_seed_keys, ctx->d_seed_x,
                     ctx->d_seed_ok, ctx->d_perm, ctx->d_coff, ctx->d_coff_net, ctx->d_trig, ctx->d_scan_tmp, ctx->d_cvid, ctx->d_fv,
                     ctx->d_fe,
@@ -367,7 +383,13 @@ void am_destroy(am_ctx *ctx)
     for (void *b : {(void *)ctx->oz.eB[0], (void *)ctx->oz.eB[1], (void *)ctx->oz.P, (void *)ctx->oz.Q})
         if (b) cudaFree(b);
     if (ctx->oz.err) cudaFree(ctx->oz.err);
-    if (ctx->oz_rows) cudaFree(ctx->oz_rows);
+    for (int b = 0; b < 2; ++b)
+        if (ctx->lv_rows[b]) cudaFree(ctx->lv_rows[b]);
+    if (ctx->fb_list) cudaFree(ctx->fb_list);
+    if (ctx->fb_count) cudaFree(ctx->fb_count);
+    for (void *b : {(void *)ctx->r1.full_list, (void *)ctx->r1.r1_list, (void *)ctx->r1.it_l, (void *)ctx->r1.it_k,
+                    (void *)ctx->r1.it_a, (void *)ctx->r1.counts, (void *)ctx->r1.offs})
+        if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->ev2) cudaEventDestroy(ctx->ev2);
@@ -876,6 +898,176 @@ static am_status assemble(am_ctx *ctx, int64_t n_cells)
     return AM_OK;
 }
 
+// Per-item scratch of the rank-1 compose (a batch of up to 4 x batch_cells children) and the
+// classification counters.
+static am_status ensure_r1_scratch(am_ctx *ctx)
+{
+    R1Scratch &r = ctx->r1;
+    if (r.counts) return AM_OK;
+    const int64_t items = 4 * ctx->oz.batch_cells;
+    CU(cudaMalloc(&r.counts, sizeof(unsigned long long) * (kMaxLayers + 1)));
+    CU(cudaMalloc(&r.offs, sizeof(int) * 2 * (kMaxLayers + 1)));
+    CU(cudaMalloc(&r.it_l, sizeof(int) * items));
+    CU(cudaMalloc(&r.it_k, sizeof(int) * items));
+    CU(cudaMalloc(&r.it_a, sizeof(double) * 4 * items));
+    r.item_cap = items;
+    CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * ctx->oz.batch_cells));
+    CU(cudaMalloc(&ctx->fb_count, sizeof(unsigned long long)));
+    return AM_OK;
+}
+
+// Level rows (FP32 pairs) for at least n cells in buffer b, keeping the other buffer (the parents).
+static am_status ensure_level_rows(am_ctx *ctx, int b, int64_t n)
+{
+    if (ctx->lv_cap[b] >= n && ctx->lv_rows[b]) return AM_OK;
+    if (ctx->lv_rows[b]) CU(cudaFree(ctx->lv_rows[b]));
+    ctx->lv_rows[b] = nullptr;
+    ctx->lv_cap[b] = 0;
+    const int64_t cap = std::max<int64_t>(n + n / 4, 4096);
+    CU(cudaMalloc(&ctx->lv_rows[b], sizeof(double) * 4 * (int64_t)(ctx->nets[0].N + 1) * cap));
+    ctx->lv_cap[b] = cap;
+    return AM_OK;
+}
+
+// One breadth-first level [f0, f1) of the AM_PREC_SLICED march.  The level's rows are composed on
+// the tensor cores into the level buffer: in full for the cells classified so (and for every
+// cell of the first level of a call), by the rank-1 update from the previous level's rows for the
+// others.  Then per chunk of the level the learned proposal's scores (tensor cores) and the clip
+// (certified FP32 tests on the rows, FP64 where they do not decide), and finally the
+// classification of the cells this level pushed.  Events: oz_ev[0..1] the compose, then three
+// per chunk; *nchunks receives the chunk count.
+static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1, bool prop_tc, int *nchunks)
+{
+    const NetHost &nh = ctx->nets[0];
+    const OzNet view = oz_view(nh);
+    const int L = nh.dev.L, N = nh.dev.N;
+    const int64_t nl = f1 - f0;
+    const int64_t chunk = ctx->oz.batch_cells;
+    const int nchunk = (int)((nl + chunk - 1) / chunk);
+    while ((int)ctx->oz_ev.size() < 2 + 3 * nchunk) {
+        cudaEvent_t e = nullptr;
+        CU(cudaEventCreate(&e));
+        ctx->oz_ev.push_back(e);
+    }
+    const int cur = ctx->stats.levels & 1;              // this level's buffer; the other holds its parents
+    am_status s = ensure_level_rows(ctx, cur, nl);
+    if (s != AM_OK) return s;
+    R1Scratch &r = ctx->r1;
+    if (r.list_cap < nl) {
+        if (r.full_list) CU(cudaFree(r.full_list));
+        if (r.r1_list) CU(cudaFree(r.r1_list));
+        r.full_list = r.r1_list = nullptr;
+        r.list_cap = 0;
+        const int64_t cap = std::max<int64_t>(nl + nl / 4, 4096);
+        CU(cudaMalloc(&r.full_list, sizeof(int32_t) * cap));
+        CU(cudaMalloc(&r.r1_list, sizeof(int32_t) * cap));
+        r.list_cap = cap;
+    }
+    const int period = ctx->oz_rank1_period > 0 ? ctx->oz_rank1_period : 8;
+    int64_t launches = 0;
+    cudaEvent_t *ev = ctx->oz_ev.data();
+    CU(cudaEventRecord(ev[0], ctx->stream));
+    double *rows = ctx->lv_rows[cur];
+    const unsigned long long *c = ctx->r1_hcounts;
+    int h_offs[2 * (kMaxLayers + 1)] = {};
+    int64_t acc = 0, cnt_le[kMaxLayers + 1] = {};
+    for (int l = 1; l <= L; ++l) {
+        h_offs[l] = (int)acc;
+        acc += (int64_t)c[l];
+        cnt_le[l] = acc;
+    }
+    const int64_t n_full = (int64_t)c[0], n_r1 = acc;
+    // the plan covers the whole next level; a level cut short by max_cells is composed in full
+    if (ctx->r1_planned && n_full + n_r1 == nl) {
+        // the previous level classified these cells: full list and rank-1 list (by flip layer)
+        CU(oz_rank1_scatter(ctx->ar, f0, f1, h_offs, L, r, ctx->stream));
+        launches += 1;
+        if (n_full > 0) {
+            CU(oz_compose(view, ctx->ar.keys, ctx->ar.kw, n_full, rows, true, ctx->oz, ctx->oz_tile_cells,
+                          ctx->sm_count, ctx->stream, r.full_list, f0));
+            launches += (2 * (int64_t)L - 1) * ((n_full + chunk - 1) / chunk);
+        }
+        if (n_r1 > 0) {
+            const R1Cells cells{ctx->ar.keys, ctx->ar.kw, ctx->ar.parent, ctx->ar.entry_plane};
+            CU(oz_rank1(view, cells, r.r1_list, n_r1, cnt_le, ctx->lv_rows[cur ^ 1], ctx->r1_prev0, rows, f0, ctx->oz, r,
+                        ctx->oz_tile_cells, ctx->sm_count, ctx->stream));
+            launches += 2 * (int64_t)L * ((n_r1 + 4 * chunk - 1) / (4 * chunk));
+        }
+    } else {
+        // every cell in full; their chains of rank-1 composes start here
+        CU(cudaMemsetAsync(ctx->ar.chain + f0, 0, sizeof(int32_t) * nl, ctx->stream));
+        CU(oz_compose(view, ctx->ar.keys + f0 * ctx->ar.kw, ctx->ar.kw, nl, rows, true, ctx->oz, ctx->oz_tile_cells,
+                      ctx->sm_count, ctx->stream));
+        launches += (2 * (int64_t)L - 1) * ((nl + chunk - 1) / chunk);
+    }
+    CU(cudaEventRecord(ev[1], ctx->stream));
+    const int64_t rstride = 8 * (int64_t)(N + 1);         // floats per cell
+    for (int b = 0; b < nchunk; ++b) {
+        const int64_t c0 = f0 + b * chunk, c1 = std::min<int64_t>(f1, c0 + chunk);
+        CU(cudaEventRecord(ev[2 + 3 * b], ctx->stream));
+        ma.scores_in = nullptr;
+        if (prop_tc) {
+            const NetDev &nd = nh.dev;
+            PropFeatures pf{};
+            pf.keys = ctx->ar.keys;
+            pf.kw = ctx->ar.kw;
+            pf.entry_pt = ctx->ar.entry_pt;
+            pf.c0 = c0;
+            pf.n = c1 - c0;
+            pf.rows = reinterpret_cast<const float *>(rows) + (c0 - f0) * rstride;
+            pf.rstride = rstride;
+            pf.N = nd.N;
+            pf.L = nd.L;
+            for (int l = 0; l <= nd.L; ++l) { pf.row0[l] = nd.row0[l]; pf.width[l] = nd.width[l]; }
+            ProposalDev &pd = ctx->prop;
+            CU(prop_tc_features(pd.tc, pf, ctx->stream));
+            CU(prop_tc_forward(pd.tc, pd.w + pd.off[1], pd.w + pd.off[3], pd.w + pd.off[5], (int)(c1 - c0), pd.tc.scores,
+                               false, pd.n_out, ctx->oz.err, ctx->stream));
+            launches += 4;
+            ma.scores_in = pd.tc.scores;
+            ma.scores_ld = pd.n_out;
+        }
+        CU(cudaEventRecord(ev[3 + 3 * b], ctx->stream));
+        ma.begin = c0;
+        ma.end = c1;
+        ma.rows_in = reinterpret_cast<const float *>(rows) + (c0 - f0) * rstride;
+        if (ctx->clip_kernel == 0 && ma.candidates != kCandNone && N <= kMaxNeurons) {
+            // one warp per cell; the cells it cannot decide outright go to the block kernel
+            CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
+            ma.fb_list = ctx->fb_list;
+            ma.fb_count = ctx->fb_count;
+            launch_clip_warp(ma, ctx->stream);
+            CU(cudaGetLastError());
+            MarchArgs mb = ma;
+            mb.list = ctx->fb_list;
+            mb.list_count = ctx->fb_count;
+            launch_march(mb, 1, false, (int)std::min<int64_t>(c1 - c0, 2 * (int64_t)ctx->sm_count), ctx->stream);
+            CU(cudaGetLastError());
+            ctx->stats.cell_launches += 2;
+            launches += 2;
+        } else {
+            launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
+            CU(cudaGetLastError());
+            ctx->stats.cell_launches += 1;
+            launches += 1;
+        }
+        CU(cudaEventRecord(ev[4 + 3 * b], ctx->stream));
+    }
+    // classify the cells this level pushed (the next level) for the rank-1 compose
+    ctx->r1_planned = false;
+    if (period > 1) {
+        CU(oz_rank1_classify(view, ctx->ar, f0, f1, f1, period, r, ctx->stream));
+        CU(cudaMemcpyAsync(ctx->r1_hcounts, r.counts, sizeof(unsigned long long) * (kMaxLayers + 1),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        launches += 1;
+        ctx->r1_planned = true;
+        ctx->r1_prev0 = f0;
+    }
+    ctx->stats.kernel_launches += launches;
+    *nchunks = nchunk;
+    return AM_OK;
+}
+
 am_status am_march(am_ctx *ctx, const am_march_opts *o)
 {
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
@@ -901,14 +1093,9 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
         op.schedule = AM_SCHED_LEVELS;
         am_status se = ensure_oz_scratch(ctx);
         if (se != AM_OK) return se;
-        const int64_t need = ctx->oz.batch_cells * 4 * (int64_t)(ctx->nets[0].N + 1);
-        if (ctx->oz_rows_cap < need) {
-            if (ctx->oz_rows) CU(cudaFree(ctx->oz_rows));
-            ctx->oz_rows = nullptr;
-            ctx->oz_rows_cap = 0;
-            CU(cudaMalloc(&ctx->oz_rows, sizeof(double) * need));
-            ctx->oz_rows_cap = need;
-        }
+        se = ensure_r1_scratch(ctx);
+        if (se != AM_OK) return se;
+        ctx->r1_planned = false;     // the first level of a call is composed in full
     }
     if (op.schedule != AM_SCHED_PERSISTENT && op.schedule != AM_SCHED_LEVELS)
         return fail(ctx, AM_ERR_INVALID_ARG, "unknown schedule %d", (int)op.schedule);
@@ -996,55 +1183,8 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             CU(cudaEventRecord(ctx->evk0, ctx->stream));
             int nbatch = 0;
             if (sliced) {
-                // per batch of the level: the rows on the tensor cores, the learned proposal's
-                // scores on the tensor cores (learned candidates), then the clip and march; the
-                // batches' events are read after the level's one synchronisation
-                for (int64_t c0 = f0; c0 < f1; c0 += ctx->oz.batch_cells, ++nbatch) {
-                    const int64_t c1 = std::min<int64_t>(f1, c0 + ctx->oz.batch_cells);
-                    while ((int)ctx->oz_ev.size() < 4 * (nbatch + 1)) {
-                        cudaEvent_t e = nullptr;
-                        CU(cudaEventCreate(&e));
-                        ctx->oz_ev.push_back(e);
-                    }
-                    cudaEvent_t *ev = ctx->oz_ev.data() + 4 * nbatch;
-                    CU(cudaEventRecord(ev[0], ctx->stream));
-                    s = sliced_compose_async(ctx, 0, ctx->ar.keys + c0 * ctx->ar.kw, ctx->ar.kw, c1 - c0, ctx->oz_rows,
-                                             true);
-                    if (s != AM_OK) return s;
-                    CU(cudaEventRecord(ev[1], ctx->stream));
-                    ma.scores_in = nullptr;
-                    if (prop_tc) {
-                        const NetDev &nd = ctx->nets[0].dev;
-                        PropFeatures pf{};
-                        pf.keys = ctx->ar.keys;
-                        pf.kw = ctx->ar.kw;
-                        pf.entry_pt = ctx->ar.entry_pt;
-                        pf.c0 = c0;
-                        pf.n = c1 - c0;
-                        pf.rows = reinterpret_cast<const float *>(ctx->oz_rows);
-                        pf.rstride = 8 * (int64_t)(nd.N + 1);
-                        pf.N = nd.N;
-                        pf.L = nd.L;
-                        for (int l = 0; l <= nd.L; ++l) { pf.row0[l] = nd.row0[l]; pf.width[l] = nd.width[l]; }
-                        ProposalDev &pd = ctx->prop;
-                        CU(prop_tc_features(pd.tc, pf, ctx->stream));
-                        CU(prop_tc_forward(pd.tc, pd.w + pd.off[1], pd.w + pd.off[3], pd.w + pd.off[5], (int)(c1 - c0),
-                                           pd.tc.scores, false, pd.n_out, ctx->oz.err, ctx->stream));
-                        ctx->stats.kernel_launches += 4;
-                        ma.scores_in = pd.tc.scores;
-                        ma.scores_ld = pd.n_out;
-                    }
-                    CU(cudaEventRecord(ev[2], ctx->stream));
-                    ma.begin = c0;
-                    ma.end = c1;
-                    ma.rows_in = ctx->oz_rows;
-                    launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
-                    CU(cudaGetLastError());
-                    CU(cudaEventRecord(ev[3], ctx->stream));
-                    ctx->stats.cell_launches += 1;
-                    ctx->stats.kernel_launches += 1;
-                }
-                CU(cudaMemcpyAsync(&ctx->oz_err_host, ctx->oz.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+                s = sliced_level(ctx, ma, f0, f1, prop_tc, &nbatch);
+                if (s != AM_OK) return s;
             } else {
                 ma.begin = f0;
                 ma.end = f1;
@@ -1058,12 +1198,14 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             s = sync_status(ctx, hc);
             if (s != AM_OK) return s;
             if (sliced) {
+                // events: 0..1 the level's compose, then per chunk of the level: proposal, clip
+                float ta = 0.f;
+                CU(cudaEventElapsedTime(&ta, ctx->oz_ev[0], ctx->oz_ev[1]));
+                ctx->stats.ms_compose += ta;
                 for (int b = 0; b < nbatch; ++b) {
-                    float ta = 0.f, tp = 0.f, tb = 0.f;
-                    CU(cudaEventElapsedTime(&ta, ctx->oz_ev[4 * b], ctx->oz_ev[4 * b + 1]));
-                    CU(cudaEventElapsedTime(&tp, ctx->oz_ev[4 * b + 1], ctx->oz_ev[4 * b + 2]));
-                    CU(cudaEventElapsedTime(&tb, ctx->oz_ev[4 * b + 2], ctx->oz_ev[4 * b + 3]));
-                    ctx->stats.ms_compose += ta;
+                    float tp = 0.f, tb = 0.f;
+                    CU(cudaEventElapsedTime(&tp, ctx->oz_ev[2 + 3 * b], ctx->oz_ev[3 + 3 * b]));
+                    CU(cudaEventElapsedTime(&tb, ctx->oz_ev[3 + 3 * b], ctx->oz_ev[4 + 3 * b]));
                     ctx->stats.ms_proposal += tp;
                     ctx->stats.ms_clip += tb;
                 }
@@ -1113,6 +1255,7 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ctx->stats.close_calls = (int64_t)hc[kCloseCalls];
     ctx->stats.fixups = (int64_t)hc[kFixups];
     ctx->stats.cuts = (int64_t)hc[kCuts];
+    ctx->stats.clip_fallbacks = (int64_t)hc[kWarpFallback];
     for (int i = 0; i < 10; ++i) ctx->stats.phase_cycles[i] = (int64_t)hc[kPhase0 + i * kCtrStride];
     s = status_error(ctx, hc[kStatus]);
     if (s != AM_OK) return s;
@@ -1155,6 +1298,87 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
     return AM_OK;
 }
 
+am_status am_compose_neighbors(am_ctx *ctx, int net_id, const uint64_t *d_parent_keys, const double *d_parent_rows,
+                               const int32_t *d_flip, int64_t n, double *d_rows)
+{
+    if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
+    if (net_id < 0 || net_id >= (int)ctx->nets.size()) return fail(ctx, AM_ERR_INVALID_ARG, "unknown net %d", net_id);
+    if (n < 0 || (n > 0 && (!d_parent_keys || !d_parent_rows || !d_flip || !d_rows)))
+        return fail(ctx, AM_ERR_INVALID_ARG, "bad arguments");
+    const NetHost &nh = ctx->nets[net_id];
+    if (!nh.oz_ok) return fail(ctx, AM_ERR_INVALID_ARG, "the rank-1 compose needs every hidden fan-in <= %d", kOzMaxFanIn);
+    if (n == 0) return AM_OK;
+    if (n > (int64_t)1 << 26) return fail(ctx, AM_ERR_CAPACITY, "at most 2^26 neighbours per call");
+    am_status s = ensure_oz_scratch(ctx);
+    if (s == AM_OK) s = ensure_r1_scratch(ctx);
+    if (s != AM_OK) return s;
+    const int N = nh.dev.N, L = nh.dev.L, kw = nh.dev.kw;
+    // host: the flips (checked), each child's key, the order by flip layer
+    std::vector<int32_t> flip(n);
+    std::vector<unsigned long long> keys((size_t)n * kw);
+    CU(cudaMemcpy(flip.data(), d_flip, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(keys.data(), d_parent_keys, sizeof(unsigned long long) * n * kw, cudaMemcpyDeviceToHost));
+    std::vector<int> layer(n);
+    int64_t cnt[kMaxLayers + 2] = {};
+    for (int64_t i = 0; i < n; ++i) {
+        const int e = flip[i];
+        if (e < 0 || e >= N) return fail(ctx, AM_ERR_INVALID_ARG, "flip %d of item %lld is not a neuron", e, (long long)i);
+        int l = L;
+        for (int ll = 1; ll <= L; ++ll)
+            if (e < nh.dev.row0[ll] + nh.dev.width[ll]) { l = ll; break; }
+        layer[i] = l;
+        cnt[l] += 1;
+        keys[(size_t)i * kw + (e >> 6)] ^= 1ull << (e & 63);
+    }
+    std::vector<int32_t> order(n), ident(n);
+    for (int64_t i = 0; i < n; ++i) ident[i] = (int32_t)i;
+    int64_t cnt_le[kMaxLayers + 1] = {}, pos[kMaxLayers + 2] = {};
+    for (int l = 1; l <= L; ++l) {
+        cnt_le[l] = cnt_le[l - 1] + cnt[l];
+        pos[l] = cnt_le[l - 1];
+    }
+    for (int64_t i = 0; i < n; ++i) order[pos[layer[i]]++] = (int32_t)i;
+    // device: keys, identity parents, flips, the order, the rows as FP32 pairs (in and out)
+    const int64_t rstride = 8 * (int64_t)(N + 1);
+    unsigned long long *dk = nullptr;
+    int32_t *dpar = nullptr, *dflip = nullptr, *dord = nullptr;
+    float *pin = nullptr, *pout = nullptr;
+    am_status rc = AM_OK;
+    auto release = [&]() {
+        for (void *b : {(void *)dk, (void *)dpar, (void *)dflip, (void *)dord, (void *)pin, (void *)pout})
+            if (b) cudaFree(b);
+    };
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaMalloc(&dk, sizeof(unsigned long long) * n * kw);
+    if (!e) e = cudaMalloc(&dpar, sizeof(int32_t) * n);
+    if (!e) e = cudaMalloc(&dflip, sizeof(int32_t) * n);
+    if (!e) e = cudaMalloc(&dord, sizeof(int32_t) * n);
+    if (!e) e = cudaMalloc(&pin, sizeof(float) * rstride * n);
+    if (!e) e = cudaMalloc(&pout, sizeof(float) * rstride * n);
+    if (!e) e = cudaMemcpyAsync(dk, keys.data(), sizeof(unsigned long long) * n * kw, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(dpar, ident.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(dflip, flip.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) e = cudaMemcpyAsync(dord, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (!e) {
+        rows_to_pairs(d_parent_rows, pin, n * (N + 1), ctx->stream);
+        e = cudaGetLastError();
+    }
+    if (!e) {
+        const R1Cells cells{dk, kw, dpar, dflip};
+        e = oz_rank1(oz_view(nh), cells, dord, n, cnt_le, pin, 0, pout, 0, ctx->oz, ctx->r1, ctx->oz_tile_cells,
+                     ctx->sm_count, ctx->stream);
+    }
+    if (!e) {
+        pairs_to_rows(pout, d_rows, n * (N + 1), ctx->stream);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    release();
+    if (e) return fail(ctx, AM_ERR_CUDA, "am_compose_neighbors: %s", cudaGetErrorString(e));
+    rc = sliced_check(ctx);
+    return rc;
+}
+
 am_status am_set_tuning(am_ctx *ctx, const am_tuning *t)
 {
     if (!ctx || !ctx->ar.keys) return fail(ctx, AM_ERR_STATE, "no context");
@@ -1164,7 +1388,13 @@ am_status am_set_tuning(am_ctx *ctx, const am_tuning *t)
     bool ok = t->compose_tile_cells == 0;
     for (int i = 0; i < nt; ++i) ok = ok || t->compose_tile_cells == tc[i];
     if (!ok) return fail(ctx, AM_ERR_INVALID_ARG, "unsupported compose_tile_cells %d", t->compose_tile_cells);
+    if (t->rank1_period < 0 || t->rank1_period > 1 << 20)
+        return fail(ctx, AM_ERR_INVALID_ARG, "rank1_period %d out of range", t->rank1_period);
+    if (t->clip_kernel != 0 && t->clip_kernel != 1)
+        return fail(ctx, AM_ERR_INVALID_ARG, "clip_kernel %d: 0 or 1", t->clip_kernel);
     ctx->oz_tile_cells = t->compose_tile_cells;
+    ctx->oz_rank1_period = t->rank1_period;
+    ctx->clip_kernel = t->clip_kernel;
     return AM_OK;
 }
 
@@ -1172,6 +1402,8 @@ am_status am_get_tuning(const am_ctx *ctx, am_tuning *t)
 {
     if (!ctx || !t) return AM_ERR_INVALID_ARG;
     t->compose_tile_cells = ctx->oz_tile_cells;
+    t->rank1_period = ctx->oz_rank1_period;
+    t->clip_kernel = ctx->clip_kernel;
     return AM_OK;
 }
 

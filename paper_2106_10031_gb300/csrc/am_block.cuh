@@ -121,6 +121,7 @@ __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned 
             ar.hash[id] = h;
             ar.nverts[id] = -1;
             ar.entry_plane[id] = (int32_t)flip;
+            ar.parent[id] = (int32_t)parent;
             ar.entry_pt[id * 3 + 0] = px;
             ar.entry_pt[id * 3 + 1] = py;
             ar.entry_pt[id * 3 + 2] = pz;
@@ -171,6 +172,7 @@ __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsi
                 ar.hash[id] = h;
                 ar.nverts[id] = -1;
                 ar.entry_plane[id] = (int32_t)flip;
+                ar.parent[id] = (int32_t)parent;
                 ar.entry_pt[id * 3 + 0] = px;
                 ar.entry_pt[id * 3 + 1] = py;
                 ar.entry_pt[id * 3 + 2] = pz;
@@ -199,6 +201,28 @@ __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsi
         pos = (pos + 1) & ar.slot_mask;
     }
     if (lane == 0) atomicOr(ar.counters + kStatus, kStHashFull);
+}
+
+// Vertex of planes p, q and the face plane f (Eq. 11 with biases) by Cramer's rule with cross
+// products; optionally the infinity norm of the inverse system matrix.
+template <class R>
+__device__ __forceinline__ bool solve3(const R *p, const R *q, const R *f, R *v, R *inv_norm)
+{
+    const R c0x = q[1] * f[2] - q[2] * f[1], c0y = q[2] * f[0] - q[0] * f[2], c0z = q[0] * f[1] - q[1] * f[0];
+    const R c1x = f[1] * p[2] - f[2] * p[1], c1y = f[2] * p[0] - f[0] * p[2], c1z = f[0] * p[1] - f[1] * p[0];
+    const R c2x = p[1] * q[2] - p[2] * q[1], c2y = p[2] * q[0] - p[0] * q[2], c2z = p[0] * q[1] - p[1] * q[0];
+    const R det = p[0] * c0x + p[1] * c0y + p[2] * c0z;
+    if (det == R(0)) return false;
+    const R inv = R(-1) / det;
+    v[0] = (p[3] * c0x + q[3] * c1x + f[3] * c2x) * inv;
+    v[1] = (p[3] * c0y + q[3] * c1y + f[3] * c2y) * inv;
+    v[2] = (p[3] * c0z + q[3] * c1z + f[3] * c2z) * inv;
+    if (inv_norm) {
+        const R ax = fabs(c0x) + fabs(c1x) + fabs(c2x), ay = fabs(c0y) + fabs(c1y) + fabs(c2y),
+                az = fabs(c0z) + fabs(c1z) + fabs(c2z);
+        *inv_norm = fmax(ax, fmax(ay, az)) * fabs(inv);
+    }
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
 }
 
 }  // namespace am

@@ -1,0 +1,473 @@
+// am_clip_warp.cu -- the clip of the sliced level march with one warp per cell (Alg. 1 steps 6-11
+// on rows composed beforehand on the tensor cores).
+//
+// A block holds kWW warps and each warp solves its own cell start to finish, so the serial
+// parts of a cell (the cuts of its polygon) occupy one warp instead of idling a whole block,
+// and many cells are in flight per SM.  The rows are read from memory (FP32 pairs [hi x 4 |
+// lo x 4], a_F last) where the block version stages them in shared memory.  Per cell:
+//   candidates : each lane keeps the two rows nearest to the point the cell was entered through
+//                among the rows it scans, and with learned candidates also the row the proposal
+//                scores highest among them (the proposal extends the nearest set);
+//   clip       : the square about the box section is cut by those 64 (96) candidates, nearest cutting
+//                row first, in FP32 (Eq. 11 per new vertex), then every vertex is re-solved in
+//                FP64 from its two planes;
+//   check      : every row at every vertex with a certified FP32 bound; close calls in FP64;
+//                violated rows are cut in (FP64) and the check repeats;
+//   emit, push : the face record, then each neuron edge pushes its neighbour (Alg. 1 step 10).
+// A cell that needs more than this (a test the FP64 close call cannot decide, a row within the
+// tolerance band of a vertex, a polygon beyond the warp's capacity, too many violators) is
+// handed, untouched, to a list that the block kernel then solves with its FP64 fallback, so the
+// result is the block kernel's in every case.
+#include <algorithm>
+#include <cuda_bf16.h>
+
+#include "am_block.cuh"
+#include "am_kernels.h"
+
+namespace am {
+
+namespace {
+
+constexpr int kWW = 8;            // warps (cells) per block
+constexpr int kWPoly = 48;        // polygon vertices a warp holds
+constexpr int kWViol = 32;        // violated rows cut in per check round
+constexpr int kWMaxKw = 128;      // key words (N <= 8190)
+constexpr int kWMaxFix = 8;       // check / fix-up rounds
+constexpr float kWU = 5.9604645e-8f;   // 2^-24
+constexpr double kWVertexTol = 1e-5;   // largest vertex bound (relative) kept
+
+struct WarpSh {
+    double pv[2][kWPoly][3];      // FP64 polygon
+    float pf[2][kWPoly][3];       // FP32 polygon of the candidate pass
+    int pe[2][kWPoly];            // edge planes (edge i: vertex i -> i + 1)
+    float vf[kWPoly][4];          // FP32 vertices and max(1, |v|_inf)
+    float dvb[kWPoly];            // bound on each FP64 vertex's error
+    float sq[4][4];               // the initial square's rows (planes N + 6 .. N + 9)
+    int viol[kWViol];
+    double aF[4];
+    float aFhi[4];
+    int nviol, flag;
+    unsigned key[2 * kWMaxKw];    // the cell's key as 32-bit words (pushes copy it)
+};
+
+int warp_smem_bytes() { return kWW * (int)sizeof(WarpSh); }
+
+// the rows of one cell: N rows in memory, the 6 box rows and the 4 square rows analytic
+struct WRows {
+    const float4 *p;              // [hi, lo] per row
+    int N;
+    float box;
+    const WarpSh *S;
+    __device__ __forceinline__ float4 hi(int k) const
+    {
+        if (k < N) return p[2 * k];
+        if (k < N + kBoxPlanes) {
+            const int i = k - N;
+            const float sg = (i & 1) ? -1.0f : 1.0f;
+            return make_float4((i >> 1) == 0 ? sg : 0.0f, (i >> 1) == 1 ? sg : 0.0f, (i >> 1) == 2 ? sg : 0.0f, -box);
+        }
+        const float *q = S->sq[k - N - kBoxPlanes];
+        return make_float4(q[0], q[1], q[2], q[3]);
+    }
+    __device__ __forceinline__ void f64(int k, double *r) const
+    {
+        const float4 h = hi(k);
+        if (k < N) {
+            const float4 l = p[2 * k + 1];
+            r[0] = (double)h.x + (double)l.x; r[1] = (double)h.y + (double)l.y;
+            r[2] = (double)h.z + (double)l.z; r[3] = (double)h.w + (double)l.w;
+        } else {
+            r[0] = h.x; r[1] = h.y; r[2] = h.z; r[3] = h.w;
+        }
+    }
+    __device__ __forceinline__ void f32(int k, float *r) const
+    {
+        const float4 h = hi(k);
+        r[0] = h.x; r[1] = h.y; r[2] = h.z; r[3] = h.w;
+    }
+};
+
+template <class R>
+__device__ __forceinline__ R wpdist(const R *r, R ri, const R *v)
+{
+    return (r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3]) * ri;
+}
+
+template <class R>
+__device__ __forceinline__ void wrow(const WRows &rv, int k, R *r)
+{
+    if constexpr (sizeof(R) == 8) rv.f64(k, r);
+    else rv.f32(k, r);
+}
+
+// One cut of the polygon P[buf] (m vertices) by row k, the warp's lanes over the vertices: a
+// vertex is cut off when its distance from row k's plane exceeds tol; the two new vertices are
+// solved from their planes and the face plane aF.  Returns the new count (0 = empty, -1 =
+// inconsistent or beyond kWPoly); *swapped: the result went to buffer buf ^ 1.
+template <class R>
+__device__ int wcut(WarpSh &S, R (*P)[kWPoly][3], int m, int buf, int k, R tol, const R *aF, const WRows &rv,
+                    bool *swapped)
+{
+    const int lane = threadIdx.x & 31;
+    *swapped = false;
+    R rk[4];
+    wrow<R>(rv, k, rk);
+    const R rn = sqrt(rk[0] * rk[0] + rk[1] * rk[1] + rk[2] * rk[2]);
+    if (rn == R(0)) return m;
+    const R ri = R(1) / rn;
+    const bool o0 = lane < m && wpdist(rk, ri, P[buf][lane]) > tol;
+    const bool o1 = lane + 32 < m && wpdist(rk, ri, P[buf][lane + 32]) > tol;
+    const unsigned long long out = (unsigned long long)__ballot_sync(0xffffffffu, o0) |
+                                   ((unsigned long long)__ballot_sync(0xffffffffu, o1) << 32);
+    const int nout = __popcll(out);
+    if (nout == 0) return m;
+    if (nout == m) return 0;
+    int ia = -1, ib = -1;
+    for (int i = lane; i < m; i += 32) {
+        const bool oi = (out >> i) & 1ull;
+        const int ip = i == 0 ? m - 1 : i - 1, in = i + 1 == m ? 0 : i + 1;
+        if (oi && !((out >> ip) & 1ull)) ia = i;
+        if (oi && !((out >> in) & 1ull)) ib = i;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ia = max(ia, __shfl_xor_sync(0xffffffffu, ia, o));
+        ib = max(ib, __shfl_xor_sync(0xffffffffu, ib, o));
+    }
+    if (ia < 0 || ib < 0 || ((ib - ia + m) % m) + 1 != nout) return -1;
+    const int nin = m - nout;
+    if (nin + 2 > kWPoly) return -1;
+    const int nb = buf ^ 1;
+    const int ea = S.pe[buf][ia == 0 ? m - 1 : ia - 1], eb = S.pe[buf][ib];
+    for (int i = lane; i < m; i += 32) {                 // the kept run b+1 .. a-1, in order
+        if ((out >> i) & 1ull) continue;
+        int ni = i - (ib + 1);
+        if (ni < 0) ni += m;
+        P[nb][ni][0] = P[buf][i][0]; P[nb][ni][1] = P[buf][i][1]; P[nb][ni][2] = P[buf][i][2];
+        S.pe[nb][ni] = S.pe[buf][i];
+    }
+    bool ok = true;
+    if (lane < 2) {
+        R pa[4], pb[4], v[3];
+        wrow<R>(rv, lane == 0 ? ea : k, pa);
+        wrow<R>(rv, lane == 0 ? k : eb, pb);
+        ok = solve3<R>(pa, pb, aF, v, nullptr);
+        P[nb][nin + lane][0] = v[0]; P[nb][nin + lane][1] = v[1]; P[nb][nin + lane][2] = v[2];
+        S.pe[nb][nin + lane] = lane == 0 ? k : eb;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();
+    *swapped = true;
+    return ok ? nin + 2 : -1;
+}
+
+// the polygon's vertices in FP64 from its planes' rows (exact pairs: no row error term), with
+// the bound on their rounding; false when a vertex cannot be solved
+__device__ bool wfinal(WarpSh &S, int m, int buf, const WRows &rv)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int i = lane; i < m; i += 32) {
+        const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
+        double ra[4], rb[4], v[3];
+        rv.f64(ea, ra);
+        rv.f64(eb, rb);
+        const bool good = solve3<double>(ra, rb, S.aF, v, nullptr);
+        const double X = fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2]))));
+        S.pv[buf][i][0] = v[0]; S.pv[buf][i][1] = v[1]; S.pv[buf][i][2] = v[2];
+        S.dvb[i] = (float)(4e-16 * X) * 1.01f;
+        ok = ok && good;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();
+    return ok;
+}
+
+__device__ __forceinline__ unsigned order_key(float d)
+{
+    const unsigned du = __float_as_uint(d);
+    return (du & 0x80000000u) ? ~du : (du | 0x80000000u);
+}
+
+}  // namespace
+
+int clip_warp_smem_bytes() { return warp_smem_bytes(); }
+
+__global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char wsm[];
+    WarpSh &S = reinterpret_cast<WarpSh *>(wsm)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const Arena &ar = a.ar;
+    unsigned long long n_solved = 0, n_empty = 0, n_fix = 0, n_cuts = 0, n_close = 0, n_fb = 0;
+    const int64_t stride = (int64_t)gridDim.x * kWW;
+    for (int64_t cell = a.begin + (int64_t)blockIdx.x * kWW + (threadIdx.x >> 5); cell < a.end; cell += stride) {
+        if (__ldcg(ar.nverts + cell) == -2) continue;          // a duplicate seed id: never solved
+        const int net_id = __ldcg(ar.net + cell);
+        const NetDev &net = a.nets[net_id];
+        const int N = net.N, NC = N + kBoxPlanes;
+        WRows rv;
+        rv.p = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * 2 * (int64_t)(N + 1);
+        rv.N = N;
+        rv.box = (float)a.box;
+        rv.S = &S;
+        for (int w = lane; w < ar.kw; w += 32) {
+            const unsigned long long x = __ldcg(ar.keys + cell * ar.kw + w);
+            S.key[2 * w] = (unsigned)x;
+            S.key[2 * w + 1] = (unsigned)(x >> 32);
+        }
+        if (lane < 4) {
+            const float h = reinterpret_cast<const float *>(rv.p + 2 * N)[lane];
+            const float l = reinterpret_cast<const float *>(rv.p + 2 * N + 1)[lane];
+            S.aF[lane] = (double)h + (double)l;
+            S.aFhi[lane] = h;
+        }
+        __syncwarp();
+        // ---- the face plane's frame (FP32) and the square about the box section (lane 0)
+        int m = 0;
+        if (lane == 0) {
+            const float F[4] = {(float)S.aF[0], (float)S.aF[1], (float)S.aF[2], (float)S.aF[3]};
+            const float nn = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+            if (nn > 0.0f && isfinite(nn)) {
+                const float inn = 1.0f / nn;
+                const float p0[3] = {-F[3] * F[0] * inn, -F[3] * F[1] * inn, -F[3] * F[2] * inn};
+                const float inv = rsqrtf(nn);
+                const float n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
+                const float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
+                const int ei = (ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2);
+                const float e0 = ei == 0 ? 1.0f : 0.0f, e1 = ei == 1 ? 1.0f : 0.0f, e2 = ei == 2 ? 1.0f : 0.0f;
+                float u[3] = {n[1] * e2 - n[2] * e1, n[2] * e0 - n[0] * e2, n[0] * e1 - n[1] * e0};
+                const float un = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                u[0] *= un; u[1] *= un; u[2] *= un;
+                const float w[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+                const float sz = 1.05f * 1.7320508f * (float)a.box;
+                const float d[4][3] = {{-w[0], -w[1], -w[2]}, {u[0], u[1], u[2]}, {w[0], w[1], w[2]}, {-u[0], -u[1], -u[2]}};
+                const float cu[4] = {-1.0f, 1.0f, 1.0f, -1.0f}, cw[4] = {-1.0f, -1.0f, 1.0f, 1.0f};
+                for (int i = 0; i < 4; ++i) {
+                    S.sq[i][0] = d[i][0]; S.sq[i][1] = d[i][1]; S.sq[i][2] = d[i][2];
+                    S.sq[i][3] = -(d[i][0] * p0[0] + d[i][1] * p0[1] + d[i][2] * p0[2]) - sz;
+                    for (int c = 0; c < 3; ++c) {
+                        const float x = p0[c] + sz * (cu[i] * u[c] + cw[i] * w[c]);
+                        S.pv[0][i][c] = (double)x;
+                        S.pf[0][i][c] = x;
+                    }
+                    S.pe[0][i] = N + kBoxPlanes + i;
+                }
+                m = 4;
+            }
+        }
+        m = __shfl_sync(FULL, m, 0);
+        __syncwarp();
+        bool fallback = m == 0;
+        // ---- candidates: per lane the two best of the rows it scans
+        const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
+                    pz = __ldcg(ar.entry_pt + cell * 3 + 2);
+        const int entry = __ldcg(ar.entry_plane + cell);
+        const bool learned = a.candidates == kCandLearned && a.scores_in && a.prop.n_out == N;
+        const __nv_bfloat16 *sc = learned ? a.scores_in + (cell - a.begin) * (int64_t)a.scores_ld : nullptr;
+        float b1 = 3.0e38f, b2 = 3.0e38f, b3 = 3.0e38f, s3 = 3.0e38f;
+        int k1 = -1, k2 = -1, k3 = -1;
+        if (!fallback) {
+            for (int k = lane; k < NC; k += 32) {
+                const float4 r = rv.hi(k);
+                const float n2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                if (n2 == 0.0f) continue;
+                const float d = fabsf(r.x * px + r.y * py + r.z * pz + r.w) * rsqrtf(n2);
+                if (d < b1) { b2 = b1; k2 = k1; b1 = d; k1 = k; }
+                else if (d < b2) { b2 = d; k2 = k; }
+                if (learned && k < N) {
+                    // the learned proposal adds the row it scores highest among this lane's
+                    const float q = k == entry ? -3.0e37f : -__bfloat162float(sc[k]);
+                    if (q < s3) { s3 = q; k3 = k; b3 = d; }
+                }
+            }
+            if (k3 == k1 || k3 == k2) k3 = -1;            // already a candidate
+        }
+        // ---- the candidate clip (FP32): nearest cutting row first; a row that holds on the
+        //      polygon holds on every later (smaller) one and retires
+        int buf = 0, ncut = 0;
+        {
+            // up to three candidate slots per lane, cut nearest first (the learned slot too)
+            const int kk[3] = {k1, k2, k3};
+            const unsigned key[3] = {order_key(b1), order_key(b2), order_key(b3)};
+            bool live[3] = {k1 >= 0, k2 >= 0, k3 >= 0};
+            while (!fallback && m > 0) {
+                bool c[3] = {false, false, false};
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (!live[j]) continue;
+                    float r[4];
+                    rv.f32(kk[j], r);
+                    const float ri = rsqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                    for (int i = 0; i < m && !c[j]; ++i) c[j] = wpdist(r, ri, S.pf[buf][i]) > 1e-7f;
+                }
+#pragma unroll
+                for (int j = 0; j < 3; ++j) live[j] = c[j];
+                if (!__any_sync(FULL, c[0] || c[1] || c[2])) break;
+                unsigned mine = 0xffffffffu;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (c[j]) mine = min(mine, key[j]);
+                const unsigned kmin = __reduce_min_sync(FULL, mine);
+                unsigned cand = 0xffffffffu;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (c[j] && key[j] == kmin) cand = min(cand, (unsigned)kk[j]);
+                const int kc = (int)__reduce_min_sync(FULL, cand);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (kk[j] == kc) live[j] = false;
+                bool sw;
+                const int nm = wcut<float>(S, S.pf, m, buf, kc, 1e-7f, S.aFhi, rv, &sw);
+                if (nm < 0) { fallback = true; break; }
+                if (sw) buf ^= 1;
+                m = nm;
+                ++ncut;
+            }
+        }
+        // an FP32 pass that emptied the polygon proves nothing: the FP64 fallback decides
+        if (m == 0) fallback = true;
+        if (!fallback) fallback = !wfinal(S, m, buf, rv);
+        // ---- the all-row check, certified; violators are cut in (FP64) and the check repeats
+        int rounds = 0, cell_close = 0;
+        while (!fallback) {
+            for (int i = lane; i < m; i += 32) {
+                const double *v = S.pv[buf][i];
+                S.vf[i][0] = (float)v[0]; S.vf[i][1] = (float)v[1]; S.vf[i][2] = (float)v[2];
+                S.vf[i][3] = (float)fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])))) * 1.0001f;
+            }
+            if (lane == 0) S.nviol = 0;
+            __syncwarp();
+            bool amb = false;
+            int close = 0;
+            for (int k = lane; k < NC; k += 32) {
+                const float4 r4 = rv.hi(k);
+                const float r[4] = {r4.x, r4.y, r4.z, r4.w};
+                const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+                if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
+                const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
+                const float band = (float)a.delta * sqrtf(n2) * 1.01f;   // delta |r|: the oracle's tolerance band
+                bool viol = false;
+                for (int i = 0; i < m; ++i) {
+                    const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
+                    if (k == ea || k == eb) continue;
+                    const float *v = S.vf[i];
+                    const float sl = r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3];
+                    const float mag = fabsf(r[0] * v[0]) + fabsf(r[1] * v[1]) + fabsf(r[2] * v[2]) + fabsf(r[3]);
+                    const float B = __fmaf_ru(8.5f * kWU, mag, __fmaf_ru(rl1, S.dvb[i], band));
+                    if (sl > B) { viol = true; continue; }
+                    if (sl >= -B) {                        // close call: FP64 from the exact pair
+                        ++close;
+                        double r6[4];
+                        rv.f64(k, r6);
+                        const double *v6 = S.pv[buf][i];
+                        const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
+                        const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
+                        const double B6 = (double)rl1 * 1.0001 * (double)S.dvb[i] + (double)band + 1e-15 * m6;
+                        if (s6 > B6) viol = true;
+                        else if (s6 >= -B6) amb = true;    // within the band: the FP64 path counts it
+                    }
+                }
+                if (viol) {
+                    for (int i = 0; i < m; ++i) amb |= S.pe[buf][i] == k;   // a spurious FP32 cut
+                    const int p = atomicAdd(&S.nviol, 1);
+                    if (p < kWViol) S.viol[p] = k;
+                    else amb = true;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) close += __shfl_xor_sync(FULL, close, o);
+            cell_close += close;
+            if (__any_sync(FULL, amb)) { fallback = true; break; }
+            __syncwarp();
+            const int nviol = S.nviol;
+            if (nviol == 0) break;
+            if (rounds + 1 >= kWMaxFix) { fallback = true; break; }
+            for (int t = 0; t < nviol && m > 0; ++t) {
+                bool sw;
+                const int nm = wcut<double>(S, S.pv, m, buf, S.viol[t], 0.0, S.aF, rv, &sw);
+                if (nm < 0) { fallback = true; break; }
+                if (sw) buf ^= 1;
+                m = nm;
+            }
+            ncut += nviol;
+            if (fallback || m == 0) { fallback = true; break; }
+            if (!wfinal(S, m, buf, rv)) { fallback = true; break; }
+            ++rounds;
+        }
+        if (fallback) {
+            // the block kernel solves this cell (double-float, then FP64 where needed)
+            if (lane == 0) {
+                const unsigned long long p = atomicAdd(a.fb_count, 1ull);
+                a.fb_list[p] = (int32_t)cell;
+            }
+            n_fb += 1;
+            continue;
+        }
+        // ---- a6 emit, a7 march
+        int emit = m >= 3 ? m : 0;
+        for (int i = 0; i < m; ++i)
+            if (S.pe[buf][i] >= N + kBoxPlanes) emit = 0;     // a square edge: the plane misses the box
+        if (emit) {
+            const double *p0 = S.pv[buf][0];
+            double nx = 0.0, ny = 0.0, nz = 0.0;
+            for (int i = lane + 1; i < m - 1; i += 32) {
+                const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1];
+                const double ax = p[0] - p0[0], ay = p[1] - p0[1], az = p[2] - p0[2];
+                const double bx = q[0] - p0[0], by = q[1] - p0[1], bz = q[2] - p0[2];
+                nx += ay * bz - az * by; ny += az * bx - ax * bz; nz += ax * by - ay * bx;
+            }
+            nx = warp_sum(nx); ny = warp_sum(ny); nz = warp_sum(nz);
+            const double amin = 2e-24 * a.box * a.box;    // twice the smallest kept area
+            if (!(nx * nx + ny * ny + nz * nz > amin * amin)) emit = 0;
+        }
+        if (emit > ar.maxv) {
+            if (lane == 0) atomicOr(ar.counters + kStatus, kStFaceVerts);
+            emit = 0;
+        }
+        if (lane == 0) ar.nverts[cell] = emit;
+        n_solved += 1;
+        if (!emit) n_empty += 1;
+        if (rounds) n_fix += 1;
+        n_cuts += (unsigned long long)ncut;
+        n_close += (unsigned long long)cell_close;
+        if (emit) {
+            for (int i = lane; i < m; i += 32) {
+                ar.edges[cell * ar.maxv + i] = S.pe[buf][i];
+                double *v = ar.verts + (cell * ar.maxv + i) * 3;
+                v[0] = S.pv[buf][i][0]; v[1] = S.pv[buf][i][1]; v[2] = S.pv[buf][i][2];
+            }
+            const unsigned long long h = __ldcg(ar.hash + cell);
+            for (int i = 0; i < m; ++i) {
+                const int e = S.pe[buf][i];
+                if (e >= N) continue;
+                const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1 == m ? 0 : i + 1];
+                insert_neighbor_warp(ar, S.key, cell, net_id, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+                                     (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        unsigned long long *C = ar.counters;
+        if (n_solved) atomicAdd(C + kSolved, n_solved);
+        if (n_empty) atomicAdd(C + kEmpty, n_empty);
+        if (n_fix) atomicAdd(C + kFixups, n_fix);
+        if (n_cuts) atomicAdd(C + kCuts, n_cuts);
+        if (n_close) atomicAdd(C + kCloseCalls, n_close);
+        if (n_fb) atomicAdd(C + kWarpFallback, n_fb);
+    }
+}
+
+cudaError_t prepare_clip_warp()
+{
+    return cudaFuncSetAttribute(clip_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
+}
+
+void launch_clip_warp(const MarchArgs &a, cudaStream_t st)
+{
+    const int64_t n = a.end - a.begin;
+    const int grid = (int)std::min<int64_t>((n + kWW - 1) / kWW, 152 * 64);
+    clip_warp_kernel<<<grid, kWW * 32, warp_smem_bytes(), st>>>(a);
+}
+
+}  // namespace am

@@ -47,7 +47,8 @@ enum {
     kFixups = 9 * kCtrStride,       // faces whose candidate polygon the full check corrected
     kPhase0 = 10 * kCtrStride,      // 10 per-phase cycle counters (timing builds only)
     kCuts = 20 * kCtrStride,        // half-plane cuts applied to candidate polygons (clip work)
-    kNumCounters = 21 * kCtrStride
+    kWarpFallback = 21 * kCtrStride,  // cells the warp clip handed to the block kernel
+    kNumCounters = 22 * kCtrStride
 };
 
 // One loaded network, folded for the device (row-major):
@@ -87,6 +88,10 @@ struct Arena {
     unsigned *ready;             // cap: 1 once the cell's record is written (persistent schedule)
     int32_t *entry_plane;        // cap: plane crossed to reach the cell (-1 for a seed)
     float *entry_pt;             // cap x 3: a point of the face (edge midpoint or seed point)
+    int32_t *parent;             // cap: the cell whose push created this one (-1 for a seed)
+    int32_t *chain;              // cap: rank-1 composes since the last full compose (sliced level march)
+    int32_t *cls;                // cap: sliced level march, per cell of the next level: -1 full compose,
+                                 //      else the layer of the flipped neuron (rank-1 compose from the parent)
     unsigned long long *slots;   // cell hash table
     unsigned long long slot_mask;
     const unsigned long long *zob;   // Zobrist table, one 64-bit value per neuron id

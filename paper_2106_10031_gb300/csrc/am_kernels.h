@@ -39,7 +39,15 @@ struct MarchArgs {
                              // tensor cores, n x (N + 1) FP32 pairs [hi x 4 | lo x 4], a_F last
     const __nv_bfloat16 *scores_in;   // level schedule, learned candidates: the proposal's scores of
     int scores_ld;                    // cells [begin, end), scores_ld BF16 per cell, from the tensor cores
+    const int32_t *list;              // level schedule: solve the cells list[0 .. *list_count) (ids in
+    const unsigned long long *list_count;   // [begin, end)) instead of the whole range
+    int32_t *fb_list;                 // warp clip: cells it hands to the block kernel, and their count
+    unsigned long long *fb_count;
 };
+// the sliced level march's clip, one warp per cell (am_clip_warp.cu): cells [begin, end), rows in
+// rows_in; cells it cannot decide are appended to fb_list for march_range_kernel (list mode)
+cudaError_t prepare_clip_warp();
+void launch_clip_warp(const MarchArgs &a, cudaStream_t st);
 int march_smem_bytes(int max_n, int max_w);
 int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
@@ -212,6 +220,7 @@ struct OzNet {
     const float *Clhi[kMaxLayers + 1] = {}, *Cllo[kMaxLayers + 1] = {};   // C_l as double-float pairs
     const int *eA[kMaxLayers + 1] = {};       // row exponents of W_l (device)
     const void *mapA[kMaxLayers + 1] = {};    // host CUtensorMap over the digit planes of W_l
+    const double *AT[kMaxLayers + 1] = {};    // hidden part of W_l transposed (n_{l-1} x n_l), FP64
     const double *w_out = nullptr;
     double b_out = 0.0;
 };
@@ -222,6 +231,7 @@ struct OzScratch {
     long long *Q = nullptr;       // ... and the raw sums of its last diagonal, rounded once by the prep
     int *err = nullptr;           // set to 1 by a kernel whose pipeline wait timed out
     int64_t batch_cells = 0;      // multiple of 16
+    int64_t *issued = nullptr;    // host counter: BF16 multiply-adds issued on the tensor cores
 };
 int oz_kp(int width);             // K padded to the 64-element staging chunk
 int oz_mp(int width);             // rows padded to the 128-row tile
@@ -229,10 +239,55 @@ const int *oz_tile_cells(int *n); // the supported cells per CTA (UMMA N = 4 x c
 void oz_slice_weights(const double *W, int n, int np, int fan, std::vector<uint16_t> &planes, std::vector<int> &eA);
 cudaError_t oz_encode_weights(void *map, const void *planes, int n, int np);
 int64_t oz_scratch_elems(int64_t batch_cells, int max_kp);
+
+// ---- rank-1 neighbour compose (sliced level march).  A cell entered across neuron k of layer l
+// has its parent's rows with row k's sign flipped (Z_1..Z_l are unchanged, s_k flips), and for
+// j > l Z_j changes by the rank-1 term v_j a~^T: a~ = delta Z_l[k] (delta = +1 if k turns active,
+// -1 if it turns inactive), v_{l+1} = W_{l+1}[:, k], v_j = W_j diag(s_{j-1}) v_{j-1}; a_F by
+// (w_out . diag(s_L) v_L) a~ (w_out[k] a~ when l = L).  One operand column per cell.
+struct R1Rows {
+    int row0[kMaxLayers + 2];         // first neuron of each layer, row0[L + 1] = N
+};
+struct R1Scratch {
+    int32_t *full_list = nullptr;     // cells of the level composed in full
+    int32_t *r1_list = nullptr;       // cells composed by the rank-1 update, grouped by flip layer (ascending)
+    int64_t list_cap = 0;
+    int *it_l = nullptr;              // per item of a rank-1 batch: flip layer, flip index within it
+    int *it_k = nullptr;
+    double *it_a = nullptr;           // per item: a~ (4 doubles)
+    int64_t item_cap = 0;
+    unsigned long long *counts = nullptr;   // device: [0] full, [l] rank-1 with flip layer l
+    int *offs = nullptr;              // device: [l] first r1_list slot of flip layer l, [kMaxLayers + 1 + l] cursors
+};
+// classify the cells [c_begin, n) of the next level (n = the cell counter, read on the device):
+// rank-1 when the parent lies in [p0, p1) (the level just solved) and its chain is below max_chain
+cudaError_t oz_rank1_classify(const OzNet &net, const Arena &ar, int64_t p0, int64_t p1, int64_t c_begin,
+                              int max_chain, R1Scratch &r, cudaStream_t st);
+// scatter the cells [c0, c1) into r.full_list and r.r1_list (offsets of the flip layers given)
+cudaError_t oz_rank1_scatter(const Arena &ar, int64_t c0, int64_t c1, const int *h_offs, int L, R1Scratch &r,
+                             cudaStream_t st);
+// rows of the n cells r1_list[0..n) (sorted by flip layer; cnt_le[l] = how many have flip layer
+// <= l) from their parents' rows (prev_rows, cell c at (c - prev0) (N + 1) x 32 B) into rows
+// (cell c at (c - cell0) ...), FP32 pairs
+struct R1Cells {
+    const unsigned long long *keys;   // cell c's key at keys + c kw (the child's key)
+    int kw;
+    const int32_t *parent;            // cell c's parent: its rows at prev_rows + (parent[c] - prev0) ...
+    const int32_t *entry;             // the flipped neuron of cell c
+};
+cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list, int64_t n, const int64_t *cnt_le,
+                     const void *prev_rows, int64_t prev0, void *rows, int64_t cell0, const OzScratch &scr,
+                     R1Scratch &r, int tile_cells, int sms, cudaStream_t st);
+// FP64 rows (n x (N + 1) x 4 doubles) <-> FP32 pairs (n x (N + 1) x [hi x 4 | lo x 4])
+void rows_to_pairs(const double *rows, float *pairs, int64_t nrows, cudaStream_t st);
+void pairs_to_rows(const float *pairs, double *rows, int64_t nrows, cudaStream_t st);
 // rows of the cells with keys (n x kw words): n x (N + 1) rows of 32 bytes, a_F last, each row
 // FP64 [a | a0] or, with df, FP32 pairs [hi x 4 | lo x 4]; batches smaller than sms x the tiles
 // resident per SM split the product's K over several CTAs; tile_cells 0 picks the tile per batch
+// list (optional): the batch is the cells list[0..n) (keys at keys + list[i] kw, rows at rows +
+// (list[i] - cell0) x (N + 1) x 32 B)
 cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, void *rows, bool df,
-                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st);
+                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st, const int32_t *list = nullptr,
+                       int64_t cell0 = 0);
 
 }  // namespace am

@@ -221,28 +221,6 @@ __device__ __forceinline__ void df_norm(float &h, float &l)
 // gamma-style coefficient of the double-float dot product bound: 2 (m + 4)^2 u^2
 __device__ __forceinline__ float df_gamma(int m) { return 2.0f * (float)(m + 4) * (float)(m + 4) * kU * kU; }
 
-// Vertex of planes p, q and the face plane f (Eq. 11 with biases) by Cramer's rule with cross
-// products; optionally the infinity norm of the inverse system matrix.
-template <class R>
-__device__ __forceinline__ bool solve3(const R *p, const R *q, const R *f, R *v, R *inv_norm)
-{
-    const R c0x = q[1] * f[2] - q[2] * f[1], c0y = q[2] * f[0] - q[0] * f[2], c0z = q[0] * f[1] - q[1] * f[0];
-    const R c1x = f[1] * p[2] - f[2] * p[1], c1y = f[2] * p[0] - f[0] * p[2], c1z = f[0] * p[1] - f[1] * p[0];
-    const R c2x = p[1] * q[2] - p[2] * q[1], c2y = p[2] * q[0] - p[0] * q[2], c2z = p[0] * q[1] - p[1] * q[0];
-    const R det = p[0] * c0x + p[1] * c0y + p[2] * c0z;
-    if (det == R(0)) return false;
-    const R inv = R(-1) / det;
-    v[0] = (p[3] * c0x + q[3] * c1x + f[3] * c2x) * inv;
-    v[1] = (p[3] * c0y + q[3] * c1y + f[3] * c2y) * inv;
-    v[2] = (p[3] * c0z + q[3] * c1z + f[3] * c2z) * inv;
-    if (inv_norm) {
-        const R ax = fabs(c0x) + fabs(c1x) + fabs(c2x), ay = fabs(c0y) + fabs(c1y) + fabs(c2y),
-                az = fabs(c0z) + fabs(c1z) + fabs(c2z);
-        *inv_norm = fmax(ax, fmax(ay, az)) * fabs(inv);
-    }
-    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
-}
-
 // row k as FP64 (both modes; in kDF hi + lo is exact in FP64)
 template <int M>
 __device__ __forceinline__ void row64(const Sh &s, int k, double *r)
@@ -1353,9 +1331,17 @@ __global__ void __launch_bounds__(kT, AM_MIN_BLOCKS) march_range_kernel(MarchArg
     extern __shared__ __align__(16) unsigned char smem[];
     const Sh s = make_sh(smem, a.max_n, a.max_w);
     blk_init(s);
-    for (int64_t cell = a.begin + blockIdx.x; cell < a.end; cell += gridDim.x) {
-        process_cell<MODE>(a, cell, s);
-        __syncthreads();
+    if (a.list) {
+        const int64_t n = (int64_t)__ldcg(a.list_count);
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+            process_cell<MODE>(a, a.list[i], s);
+            __syncthreads();
+        }
+    } else {
+        for (int64_t cell = a.begin + blockIdx.x; cell < a.end; cell += gridDim.x) {
+            process_cell<MODE>(a, cell, s);
+            __syncthreads();
+        }
     }
     blk_flush(a, s);
 }

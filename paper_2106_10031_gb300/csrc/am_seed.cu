@@ -132,6 +132,7 @@ __global__ void seed_insert_kernel(SeedArgs a)
     ar.hash[id] = h;
     ar.nverts[id] = -1;
     ar.entry_plane[id] = -1;
+    ar.parent[id] = -1;
     for (int c = 0; c < 3; ++c) ar.entry_pt[id * 3 + c] = (float)a.seed_x[ray * 3 + c];
     __threadfence();
     const unsigned long long mine = slot_make(h, (unsigned long long)id, kNoFlip);

@@ -119,7 +119,9 @@ __device__ __forceinline__ unsigned bf16_of_int(int d) { return __float_as_uint(
 // digit planes of the stacked operand, layer-1 rows, a_F
 
 struct OzPrep {
-    const unsigned long long *keys;   // cell i's key at keys + i * kw
+    const unsigned long long *keys;   // cell i's key at keys + i * kw (list: at keys + list[i] * kw)
+    const int32_t *list;              // null, or the cell ids of the batch (rows at rows + (list[i] - cell0) rstride)
+    int64_t cell0;
     int kw;
     int64_t n;                        // cells in the batch
     void *rows;                       // cell i's rows at rows + i * rstride (N rows, then a_F), 32 B each:
@@ -224,8 +226,9 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
     __shared__ double fred[kW][4];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t i = blockIdx.x;
-    const unsigned long long *key = p.keys + i * p.kw;
-    double *out = reinterpret_cast<double *>(p.rows) + i * p.rstride;     // 4 doubles = 8 floats per row
+    const int64_t cell = p.list ? (int64_t)p.list[i] : i;
+    const unsigned long long *key = p.keys + cell * p.kw;
+    double *out = reinterpret_cast<double *>(p.rows) + (p.list ? cell - p.cell0 : i) * p.rstride;   // 4 doubles = 8 floats per row
     float *outf = reinterpret_cast<float *>(out);
     // ---- rows of layer l, signed (1 - 2 s_k) as in Eq. 10, and the column maxima of
     //      |diag(s_l) Z_l| (bit patterns of non-negative values order as integers)
@@ -365,6 +368,223 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                 const int64_t row = (int64_t)t * p.ncols + 4 * i + j;
                 *reinterpret_cast<unsigned *>(p.B + row * p.Kp + k0) = dig[j][t];
             }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// rank-1 neighbour compose (Cor. 1 across one flipped neuron, Alg. 1 step 10)
+
+struct R1Init {
+    const unsigned long long *keys;
+    int kw;
+    const int32_t *list;              // items -> cell ids
+    const int32_t *parent, *entry;
+    const float *prev_rows;           // the parents' level: cell c at (c - prev0) rstride
+    int64_t prev0;
+    float *rows;                      // this level: cell c at (c - cell0) rstride
+    int64_t cell0, rstride;           // floats per cell: 8 (N + 1)
+    int L, N;
+    int row0[kMaxLayers + 2];         // row0[L + 1] = N
+    const double *w_out;
+    int *it_l, *it_k;
+    double *it_a;
+};
+
+// (h, l) += d, re-split into an FP32 pair (the rows' 48-bit representation)
+__device__ __forceinline__ void pair_add(float &h, float &l, double d)
+{
+    const double t = (double)h + (double)l + d;
+    h = (float)t;
+    l = (float)(t - (double)h);
+}
+
+// One block per child: the parent's rows, row k's sign flipped (s_k flips, Z_k does not), and
+// a~ = delta Z_l[k] = the parent's signed row k (its sign (1 - 2 s_k) is delta); for a flip in
+// the last layer a_F += w_out[k] a~ and nothing else changes.
+__global__ void __launch_bounds__(128) oz_r1_init_kernel(R1Init a)
+{
+    const int64_t i = blockIdx.x;
+    const int64_t c = a.list[i];
+    const int64_t p = a.parent[c];
+    const int e = a.entry[c];
+    const float4 *src = reinterpret_cast<const float4 *>(a.prev_rows + (p - a.prev0) * a.rstride);
+    float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
+    for (int q = threadIdx.x; q < 2 * (a.N + 1); q += blockDim.x) dst[q] = src[q];
+    __syncthreads();                                 // row e and a_F are rewritten below
+    if (threadIdx.x != 0) return;
+    int l = a.L;
+    for (int ll = 1; ll <= a.L; ++ll)
+        if (e < a.row0[ll + 1]) { l = ll; break; }
+    const float4 h = src[2 * e], lo = src[2 * e + 1];
+    const double at[4] = {(double)h.x + (double)lo.x, (double)h.y + (double)lo.y, (double)h.z + (double)lo.z,
+                          (double)h.w + (double)lo.w};
+    dst[2 * e] = make_float4(-h.x, -h.y, -h.z, -h.w);
+    dst[2 * e + 1] = make_float4(-lo.x, -lo.y, -lo.z, -lo.w);
+    a.it_l[i] = l;
+    a.it_k[i] = e - a.row0[l];
+    for (int q = 0; q < 4; ++q) a.it_a[4 * i + q] = at[q];
+    if (l == a.L) {
+        const double w = a.w_out[e - a.row0[l]];
+        float4 fh = dst[2 * a.N], fl = dst[2 * a.N + 1];
+        pair_add(fh.x, fl.x, w * at[0]);
+        pair_add(fh.y, fl.y, w * at[1]);
+        pair_add(fh.z, fl.z, w * at[2]);
+        pair_add(fh.w, fl.w, w * at[3]);
+        dst[2 * a.N] = fh;
+        dst[2 * a.N + 1] = fl;
+    }
+}
+
+struct R1Prep {
+    const unsigned long long *keys;
+    int kw;
+    const int32_t *list;
+    float *rows;
+    int64_t cell0, rstride;
+    int j, L, N, nj, row0j;
+    const double *ATj;                // W_j transposed (n_{j-1} x n_j)
+    const int *eA;                    // row exponents of W_j
+    const long long *P, *Q;           // the products of layer j (items with flip layer <= j - 2)
+    int Mp;
+    const int *eBin;                  // column exponents of layer j's operand
+    int *eBout;                       // column exponents of layer j + 1's operand
+    __nv_bfloat16 *B;                 // digit planes of layer j + 1's operand, column = item
+    int64_t ncols;
+    int Kp;                           // round_up(n_j, 64)
+    const double *w_out;
+    const int *it_l, *it_k;
+    const double *it_a;
+};
+
+// One block per child whose rows of layer j change (flip layer l <= j - 1): v_j (W_j's column k
+// when l = j - 1, else the exact product of layer j), the rows c_j += (1 - 2 s_j) v_j a~, and the
+// next operand diag(s_j) v_j as 8 digit planes (or, at the last layer, a_F += (w_out . diag(s_L)
+// v_L) a~).
+__global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
+{
+    constexpr int kW = kOzPrepThreads / 32;
+    extern __shared__ double r1v[];                  // diag(s_j) v_j, n_j values
+    __shared__ unsigned long long red[kW];
+    __shared__ double fred[kW];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t i = blockIdx.x;
+    const int64_t c = a.list[i];
+    const unsigned long long *key = a.keys + c * a.kw;
+    float *row = a.rows + (c - a.cell0) * a.rstride;
+    const int l = a.it_l[i];
+    const double at0 = a.it_a[4 * i], at1 = a.it_a[4 * i + 1], at2 = a.it_a[4 * i + 2], at3 = a.it_a[4 * i + 3];
+    unsigned long long mx = 0ull;
+    double fs = 0.0;
+    for (int m = tid; m < a.nj; m += kOzPrepThreads) {
+        double x;
+        if (l == a.j - 1) {
+            x = a.ATj[(int64_t)a.it_k[i] * a.nj + m];
+        } else {
+            const int64_t o = i * a.Mp + m;
+            x = i64_ldexp(a.P[o] + ((a.Q[o] + 32) >> 6), a.eA[m] + a.eBin[i] - 48);
+        }
+        const int r = a.row0j + m;
+        const bool act = key_bit(key, r);
+        const double sg = act ? -x : x;              // (1 - 2 s) v
+        float4 *rp = reinterpret_cast<float4 *>(row + 8 * (int64_t)r);
+        float4 h = rp[0], lo = rp[1];
+        pair_add(h.x, lo.x, sg * at0);
+        pair_add(h.y, lo.y, sg * at1);
+        pair_add(h.z, lo.z, sg * at2);
+        pair_add(h.w, lo.w, sg * at3);
+        rp[0] = h;
+        rp[1] = lo;
+        r1v[m] = act ? x : 0.0;
+        if (act) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+            mx = b > mx ? b : mx;
+            if (a.j == a.L) fs = fma(a.w_out[m], x, fs);
+        }
+    }
+    if (a.j == a.L) {
+        for (int o = 16; o > 0; o >>= 1) fs += __shfl_xor_sync(0xffffffffu, fs, o);
+        if (lane == 0) fred[wid] = fs;
+        __syncthreads();
+        if (tid == 0) {
+            double f = 0.0;
+            for (int w = 0; w < kW; ++w) f += fred[w];
+            float4 *fp = reinterpret_cast<float4 *>(row + 8 * (int64_t)a.N);
+            float4 fh = fp[0], fl = fp[1];
+            pair_add(fh.x, fl.x, f * at0);
+            pair_add(fh.y, fl.y, f * at1);
+            pair_add(fh.z, fl.z, f * at2);
+            pair_add(fh.w, fl.w, f * at3);
+            fp[0] = fh;
+            fp[1] = fl;
+        }
+        return;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    if (lane == 0) red[wid] = mx;
+    __syncthreads();
+    unsigned long long m2 = 0ull;
+    for (int w = 0; w < kW; ++w) m2 = red[w] > m2 ? red[w] : m2;
+    const int e = col_exponent(m2);
+    if (tid == 0) a.eBout[i] = e;
+    for (int k0 = 2 * tid; k0 < a.Kp; k0 += 2 * kOzPrepThreads) {
+        unsigned dig[kOzPlanes];
+#pragma unroll
+        for (int t = 0; t < kOzPlanes; ++t) dig[t] = 0u;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int k = k0 + hh;
+            if (k >= a.nj) continue;
+            long long x = fixed62(r1v[k], e);
+#pragma unroll
+            for (int t = 0; t < kOzPlanes; ++t) {
+                const int sh = 56 - 6 * t;
+                const long long d = (x + (1ll << (sh - 1))) >> sh;   // nearest digit
+                x -= d << sh;
+                dig[t] |= bf16_of_int((int)d) << (16 * hh);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kOzPlanes; ++t)
+            *reinterpret_cast<unsigned *>(a.B + ((int64_t)t * a.ncols + i) * a.Kp + k0) = dig[t];
+    }
+}
+
+// the cells [c_begin, n) of the next level: rank-1 from the parent when it lies in [p0, p1)
+// and its chain of rank-1 composes is below max_chain - 1, else a full compose
+__global__ void oz_r1_classify_kernel(Arena ar, int64_t p0, int64_t p1, int64_t c_begin, int max_chain, int L,
+                                      R1Rows rr, unsigned long long *counts)
+{
+    const unsigned long long nc = __ldcg(ar.counters + kNCells);
+    const int64_t n = (int64_t)nc < ar.cap ? (int64_t)nc : ar.cap;
+    for (int64_t c = c_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = ar.parent[c];
+        const int e = ar.entry_plane[c];
+        int cls = -1;
+        if (p >= p0 && p < p1 && e >= 0) {
+            const int ch = ar.chain[p];
+            if (ch + 1 < max_chain) {
+                cls = L;
+                for (int ll = 1; ll <= L; ++ll)
+                    if (e < rr.row0[ll + 1]) { cls = ll; break; }
+                ar.chain[c] = ch + 1;
+            }
+        }
+        if (cls < 0) ar.chain[c] = 0;
+        ar.cls[c] = cls;
+        atomicAdd(counts + (cls < 0 ? 0 : cls), 1ull);
+    }
+}
+
+__global__ void oz_r1_scatter_kernel(Arena ar, int64_t c0, int64_t c1, int32_t *full, int32_t *r1, int *offs)
+{
+    for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1; c += (int64_t)gridDim.x * blockDim.x) {
+        const int cls = ar.cls[c];
+        if (cls < 0) full[atomicAdd(offs + kMaxLayers + 1, 1)] = (int32_t)c;
+        else r1[offs[cls] + atomicAdd(offs + kMaxLayers + 1 + cls, 1)] = (int32_t)c;
     }
 }
 
@@ -918,8 +1138,52 @@ int64_t oz_scratch_elems(int64_t batch_cells, int max_kp)
     return (int64_t)kOzPlanes * 4 * batch_cells * max_kp;
 }
 
+// One layer's product on the tensor cores: the digit planes of W_l (net.mapA[l]) times the
+// first ncols_used columns of the stacked operand (scr.B, written by the previous prep) into the
+// exact products P, Q.  The tile shape: tile_cells, or (0) the 32-cell tile when K has at least 8
+// chunks (its two passes' fixed costs amortise) and its tiles, split over up to 4 K ranges, fill
+// every SM, else the 16-cell tile, which makes twice as many.  A product too small to fill the
+// SMs splits K over more CTAs (exact integer sums).
+static cudaError_t oz_layer_product(const OzNet &net, int l, const OzScratch &scr, int64_t ncols_used, int tile_cells,
+                                    int sms, cudaStream_t st)
+{
+    const int64_t ncols = 4 * scr.batch_cells;
+    const int Mp = oz_mp(net.width[l]);
+    const int Kp = oz_kp(net.width[l - 1]);
+    const int64_t nb = (ncols_used + 3) / 4;                  // in units of 4 columns
+    const int tc = tile_cells ? tile_cells
+                              : (Kp / kOzBK >= 8 && (int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) * 4 >= sms ? 32 : 16);
+    const int per_sm = tc == 8 ? 2 : 1;                       // resident tiles per SM (shared memory)
+    CUtensorMap tmB;
+    cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tc);
+    if (e != cudaSuccess) return e;
+    OzGemm g{};
+    g.P = scr.P;
+    g.Q = scr.Q;
+    g.Mp = Mp;
+    g.n = nb;
+    g.KC = Kp / kOzBK;
+    g.ncols = ncols;
+    g.err = scr.err;
+    const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tc - 1) / (4 * tc));
+    int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
+    g.split = split > 1 ? 1 : 0;
+    if (g.split) {
+        e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * 4 * nb * g.Mp, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr.Q, 0, sizeof(long long) * 4 * nb * g.Mp, st);
+        if (e != cudaSuccess) return e;
+    }
+    const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
+    // 36 digit-plane products per layer over the padded tiles of the columns in use
+    if (scr.issued) *scr.issued += (int64_t)36 * (4 * nb) * Mp * Kp;
+    return tc == 8    ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+           : tc == 32 ? launch_gemm_wide<6>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
+                      : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
+}
+
 cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw, int64_t n, void *rows, bool df,
-                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st)
+                       const OzScratch &scr, int tile_cells, int sms, cudaStream_t st, const int32_t *list,
+                       int64_t cell0)
 {
     const int64_t rstride = 4 * (int64_t)(net.N + 1);
     const int64_t ncols = 4 * scr.batch_cells;
@@ -927,10 +1191,12 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
     for (int64_t b0 = 0; b0 < n; b0 += scr.batch_cells) {
         const int64_t nb = std::min<int64_t>(scr.batch_cells, n - b0);
         OzPrep p{};
-        p.keys = keys + b0 * kw;
+        p.keys = list ? keys : keys + b0 * kw;
+        p.list = list ? list + b0 : nullptr;
+        p.cell0 = cell0;
         p.kw = kw;
         p.n = nb;
-        p.rows = reinterpret_cast<double *>(rows) + b0 * rstride;
+        p.rows = list ? rows : reinterpret_cast<double *>(rows) + b0 * rstride;
         p.rstride = rstride;
         p.df = df ? 1 : 0;
         p.L = net.L;
@@ -945,42 +1211,9 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
             p.eBin = scr.eB[l & 1];                    // written by the prep of layer l - 1
             p.eBout = scr.eB[(l + 1) & 1];
             if (l >= 2) {
-                const int Mp = oz_mp(net.width[l]);
-                const int Kp = oz_kp(net.width[l - 1]);
-                // automatic shape (tile_cells 0): the 32-cell tile when K has at least 8 chunks
-                // (its two passes' fixed costs amortise) and its tiles, split over up to 4 K
-                // ranges, fill every SM; else the 16-cell tile, which makes twice as many
-                const int tc = tile_cells ? tile_cells
-                                          : (Kp / kOzBK >= 8 &&
-                                                     (int64_t)(Mp / kOzM) * ((4 * nb + 127) / 128) * 4 >= sms
-                                                 ? 32 : 16);
-                const int per_sm = tc == 8 ? 2 : 1;          // resident tiles per SM (shared memory)
-                CUtensorMap tmB;
-                cudaError_t e = encode_map(&tmB, scr.B, Kp, (int64_t)kOzPlanes * ncols, 4 * tc);
+                cudaError_t e = oz_layer_product(net, l, scr, 4 * nb, tile_cells, sms, st);
                 if (e != cudaSuccess) return e;
-                OzGemm g{};
-                g.P = scr.P;
-                g.Q = scr.Q;
-                g.Mp = Mp;
-                g.n = nb;
-                g.KC = Kp / kOzBK;
-                g.ncols = ncols;
-                g.err = scr.err;
-                // a batch too small to fill the SMs splits K over more CTAs (exact integer sums)
-                const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tc - 1) / (4 * tc));
-                int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
-                g.split = split > 1 ? 1 : 0;
-                if (g.split) {
-                    e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * 4 * nb * g.Mp, st);
-                    if (e == cudaSuccess) e = cudaMemsetAsync(scr.Q, 0, sizeof(long long) * 4 * nb * g.Mp, st);
-                    if (e != cudaSuccess) return e;
-                }
-                const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
-                e = tc == 8    ? launch_gemm<8, 2>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
-                    : tc == 32 ? launch_gemm_wide<6>(tmA, tmB, g, g.Mp, 4 * nb, split, st)
-                               : launch_gemm<16, 6>(tmA, tmB, g, g.Mp, 4 * nb, split, st);
-                if (e != cudaSuccess) return e;
-                p.Mp = g.Mp;
+                p.Mp = oz_mp(net.width[l]);
                 p.eA = net.eA[l];
             }
             p.l = l;
@@ -992,6 +1225,142 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
             p.Kp = oz_kp(net.width[l]);
             oz_prep_kernel<<<(unsigned)nb, kOzPrepThreads, 0, st>>>(p);
             cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+
+__global__ void rows_to_pairs_kernel(const double *rows, float *pairs, int64_t nrows)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+        float h[4], l[4];
+        for (int q = 0; q < 4; ++q) {
+            const double v = rows[4 * i + q];
+            h[q] = (float)v;
+            l[q] = (float)(v - (double)h[q]);
+        }
+        reinterpret_cast<float4 *>(pairs)[2 * i] = make_float4(h[0], h[1], h[2], h[3]);
+        reinterpret_cast<float4 *>(pairs)[2 * i + 1] = make_float4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+__global__ void pairs_to_rows_kernel(const float *pairs, double *rows, int64_t nrows)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 h = reinterpret_cast<const float4 *>(pairs)[2 * i], l = reinterpret_cast<const float4 *>(pairs)[2 * i + 1];
+        rows[4 * i] = (double)h.x + (double)l.x;
+        rows[4 * i + 1] = (double)h.y + (double)l.y;
+        rows[4 * i + 2] = (double)h.z + (double)l.z;
+        rows[4 * i + 3] = (double)h.w + (double)l.w;
+    }
+}
+
+void rows_to_pairs(const double *rows, float *pairs, int64_t nrows, cudaStream_t st)
+{
+    rows_to_pairs_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(rows, pairs, nrows);
+}
+
+void pairs_to_rows(const float *pairs, double *rows, int64_t nrows, cudaStream_t st)
+{
+    pairs_to_rows_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(pairs, rows, nrows);
+}
+
+cudaError_t oz_rank1_classify(const OzNet &net, const Arena &ar, int64_t p0, int64_t p1, int64_t c_begin,
+                              int max_chain, R1Scratch &r, cudaStream_t st)
+{
+    R1Rows rr{};
+    for (int l = 1; l <= net.L; ++l) rr.row0[l] = net.row0[l];
+    rr.row0[net.L + 1] = net.N;
+    cudaError_t e = cudaMemsetAsync(r.counts, 0, sizeof(unsigned long long) * (kMaxLayers + 1), st);
+    if (e != cudaSuccess) return e;
+    oz_r1_classify_kernel<<<152 * 4, 256, 0, st>>>(ar, p0, p1, c_begin, max_chain, net.L, rr, r.counts);
+    return cudaGetLastError();
+}
+
+cudaError_t oz_rank1_scatter(const Arena &ar, int64_t c0, int64_t c1, const int *h_offs, int L, R1Scratch &r,
+                             cudaStream_t st)
+{
+    (void)L;
+    cudaError_t e = cudaMemcpyAsync(r.offs, h_offs, sizeof(int) * 2 * (kMaxLayers + 1), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int64_t n = c1 - c0;
+    if (n <= 0) return cudaSuccess;
+    oz_r1_scatter_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(ar, c0, c1, r.full_list,
+                                                                                                  r.r1_list, r.offs);
+    return cudaGetLastError();
+}
+
+cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list, int64_t n, const int64_t *cnt_le,
+                     const void *prev_rows, int64_t prev0, void *rows, int64_t cell0, const OzScratch &scr,
+                     R1Scratch &r, int tile_cells, int sms, cudaStream_t st)
+{
+    const int64_t cap = 4 * scr.batch_cells;              // one operand column per child
+    const int64_t rstride = 8 * (int64_t)(net.N + 1);
+    for (int64_t b0 = 0; b0 < n; b0 += cap) {
+        const int64_t nb = std::min<int64_t>(cap, n - b0);
+        auto le = [&](int x) {                            // children of this batch with flip layer <= x
+            const int64_t v = x < 1 ? 0 : cnt_le[x] - b0;
+            return std::max<int64_t>(0, std::min<int64_t>(nb, v));
+        };
+        R1Init in{};
+        in.keys = cells.keys;
+        in.kw = cells.kw;
+        in.list = list + b0;
+        in.parent = cells.parent;
+        in.entry = cells.entry;
+        in.prev_rows = reinterpret_cast<const float *>(prev_rows);
+        in.prev0 = prev0;
+        in.rows = reinterpret_cast<float *>(rows);
+        in.cell0 = cell0;
+        in.rstride = rstride;
+        in.L = net.L;
+        in.N = net.N;
+        for (int l = 1; l <= net.L; ++l) in.row0[l] = net.row0[l];
+        in.row0[net.L + 1] = net.N;
+        in.w_out = net.w_out;
+        in.it_l = r.it_l;
+        in.it_k = r.it_k;
+        in.it_a = r.it_a;
+        oz_r1_init_kernel<<<(unsigned)nb, 128, 0, st>>>(in);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        for (int j = 2; j <= net.L; ++j) {
+            const int64_t g = le(j - 2), pc = le(j - 1);
+            if (g > 0) {
+                e = oz_layer_product(net, j, scr, g, tile_cells, sms, st);
+                if (e != cudaSuccess) return e;
+            }
+            if (pc == 0) continue;
+            R1Prep pp{};
+            pp.keys = cells.keys;
+            pp.kw = cells.kw;
+            pp.list = list + b0;
+            pp.rows = reinterpret_cast<float *>(rows);
+            pp.cell0 = cell0;
+            pp.rstride = rstride;
+            pp.j = j;
+            pp.L = net.L;
+            pp.N = net.N;
+            pp.nj = net.width[j];
+            pp.row0j = net.row0[j];
+            pp.ATj = net.AT[j];
+            pp.eA = net.eA[j];
+            pp.P = scr.P;
+            pp.Q = scr.Q;
+            pp.Mp = oz_mp(net.width[j]);
+            pp.eBin = scr.eB[j & 1];
+            pp.eBout = scr.eB[(j + 1) & 1];
+            pp.B = scr.B;
+            pp.ncols = 4 * scr.batch_cells;
+            pp.Kp = oz_kp(net.width[j]);
+            pp.w_out = net.w_out;
+            pp.it_l = r.it_l;
+            pp.it_k = r.it_k;
+            pp.it_a = r.it_a;
+            oz_r1_prep_kernel<<<(unsigned)pc, kOzPrepThreads, sizeof(double) * net.width[j], st>>>(pp);
+            e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
     }

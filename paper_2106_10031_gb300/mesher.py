@@ -252,8 +252,13 @@ class Mesher:
         return out
 
     # ---- launch shapes
-    def set_tuning(self, compose_tile_cells: int = 0):
-        t = nt.am_tuning(compose_tile_cells=compose_tile_cells)
+    def set_tuning(self, compose_tile_cells: int | None = None, rank1_period: int | None = None,
+                   clip_kernel: int | None = None):
+        """Launch shapes of the sliced path; None keeps the current value."""
+        cur = self.get_tuning()
+        pick = lambda v, k: cur[k] if v is None else v  # noqa: E731
+        t = nt.am_tuning(compose_tile_cells=pick(compose_tile_cells, "compose_tile_cells"),
+                         rank1_period=pick(rank1_period, "rank1_period"), clip_kernel=pick(clip_kernel, "clip_kernel"))
         self._check(self.lib.am_set_tuning(self.ctx, C.byref(t)))
 
     def get_tuning(self) -> dict:
@@ -340,6 +345,27 @@ class Mesher:
         self._check(self.lib.am_compose(self.ctx, net_id, C.c_void_p(k.data_ptr()), n, precision,
                                         C.c_void_p(rows.data_ptr()), C.c_void_p(err.data_ptr())))
         return rows.cpu().numpy(), err.cpu().numpy()
+
+    def compose_neighbors(self, net_id: int, parent_keys, parent_rows, flips):
+        """am_compose_neighbors: rows (n, N + 1, 4) float64 of the cells parent_keys[i] ^ e_flips[i]
+        from the parents' rows ((n, N + 1, 4) float64, as compose() returns them) by the rank-1
+        update on the tensor cores."""
+        import torch
+        N = self.nets[net_id].N
+        dev = torch.device("cuda", self.device)
+        k = torch.as_tensor(_key_array(parent_keys, N).view(np.int64), device=dev)
+        n = k.shape[0]
+        pr = np.ascontiguousarray(parent_rows, dtype=np.float64)
+        fl = np.ascontiguousarray(flips, dtype=np.int32)
+        if pr.shape != (n, N + 1, 4) or fl.shape != (n,):
+            raise ValueError(f"parent_rows {pr.shape}, flips {fl.shape}; expected ({n}, {N + 1}, 4) and ({n},)")
+        rows_in = torch.as_tensor(pr, device=dev)
+        f = torch.as_tensor(fl, device=dev)
+        out = torch.empty((n, N + 1, 4), dtype=torch.float64, device=dev)
+        self._check(self.lib.am_compose_neighbors(self.ctx, net_id, C.c_void_p(k.data_ptr()),
+                                                  C.c_void_p(rows_in.data_ptr()), C.c_void_p(f.data_ptr()), n,
+                                                  C.c_void_p(out.data_ptr())))
+        return out.cpu().numpy()
 
     # ---- learned proposal (device arrays are torch CUDA tensors)
     def proposal_init(self, n_in: int, hidden: int, n_out: int, max_batch: int = 4096, seed: int = 0):

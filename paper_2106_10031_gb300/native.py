@@ -57,7 +57,7 @@ class am_march_opts(C.Structure):
 
 
 class am_tuning(C.Structure):
-    _fields_ = [("compose_tile_cells", C.c_int)]
+    _fields_ = [("compose_tile_cells", C.c_int), ("rank1_period", C.c_int), ("clip_kernel", C.c_int)]
 
 
 class am_tune_point(C.Structure):
@@ -75,7 +75,8 @@ class am_stats_t(C.Structure):
                 ("ms_march", C.c_double), ("ms_assemble", C.c_double), ("ms_cell_kernels", C.c_double),
                 ("cell_launches", C.c_int64), ("kernel_launches", C.c_int64), ("close_calls", C.c_int64),
                 ("fixups", C.c_int64), ("cuts", C.c_int64), ("phase_cycles", C.c_int64 * 10),
-                ("ms_compose", C.c_double), ("ms_clip", C.c_double), ("ms_proposal", C.c_double)]
+                ("ms_compose", C.c_double), ("ms_clip", C.c_double), ("ms_proposal", C.c_double),
+                ("clip_fallbacks", C.c_int64), ("tensor_macs", C.c_int64)]
 
 
 class am_mesh(C.Structure):
@@ -107,6 +108,8 @@ ENTRY_POINTS = [
     ("am_seed_pairs", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int),
                                  C.POINTER(C.c_int), C.c_void_p]),
     ("am_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    ("am_compose_neighbors", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                       C.c_void_p]),
     ("am_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("am_autotune_compose", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_int, C.c_void_p]),
