@@ -645,21 +645,21 @@ def shard_nets(n_nets: int, rank: int, world: int) -> list:
     return list(range(rank, n_nets, world))
 
 
-def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1, box=2.0):
+def batch_leg(dist, max_cells=0, precision="mixed", reps=1, box=2.0, capacity=60_000_000):
     """The 64-net batch: batch_nets(master_seed=4) (widths 32-256, depths 4-8, sigma in
     [0.02, 0.1]), one seed ray along +x per net, box [-2, 2]^3 (some of the deeper nets reach
-    past 1.5), all of a rank's nets in one persistent launch, the first max_cells cells of the
-    job (split evenly over the ranks).  Sharded by
-    net (shard_nets); value = all ranks' faces / the slowest rank's march time, by am_march's
-    CUDA events; strong scaling (the total work is fixed)."""
+    past 1.5), all of a rank's nets in one persistent launch, marched to completion (3.05e7
+    faces in all), or the first max_cells cells of the job (split evenly over the ranks).
+    Sharded by net (shard_nets); value = all ranks' faces / the slowest rank's march time, by
+    am_march's CUDA events; strong scaling (the total work is fixed)."""
     import paper_2106_10031_gb300 as am
     from synth import batch_nets
     nets = batch_nets()
     mine = [nets[i] for i in shard_nets(len(nets), dist.rank, dist.world)]
     cells = max_cells // dist.world
     o, d = np.zeros((1, 3)), np.array([[1.0, 0.0, 0.0]])
-    with am.Mesher(device=dist.local, max_cells=cells + 4096, max_neurons=max(n.N for n in mine),
-                   max_width=max(max(n.widths) for n in mine)) as m:
+    with am.Mesher(device=dist.local, max_cells=(cells + 4096) if cells else capacity // dist.world,
+                   max_neurons=max(n.N for n in mine), max_width=max(max(n.widths) for n in mine)) as m:
         ids = [m.load_mlp(n) for n in mine]
         runs, unseeded = [], 0
         for _ in range(reps + 1):                   # the first run warms up
@@ -676,8 +676,8 @@ def batch_leg(dist, max_cells=2_000_000, precision="mixed", reps=1, box=2.0):
         st = min(runs[1:], key=lambda x: x["ms_march"])
     faces = dist.allreduce(float(st["faces"]), "sum")
     ms = dist.allreduce(float(st["ms_march"]), "max")
-    return {"workload": f"64 nets of batch_nets(master_seed=4), box {box}, first {max_cells} cells of the job, "
-                        f"{precision}",
+    return {"workload": f"64 nets of batch_nets(master_seed=4), box {box}, "
+                        f"{'the whole batch' if not max_cells else f'first {max_cells} cells of the job'}, {precision}",
             "n_gpus": dist.world, "scaling": "strong", "sharding": "nets round robin over the ranks, no exchange",
             "faces": int(faces), "ms": ms, "faces_per_s": faces / (ms / 1e3),
             "rank0": {"nets": len(mine), "unseeded_nets": unseeded, "cells": int(st["cells"]),

@@ -125,6 +125,12 @@ typedef struct {
     int skip_layer;           /* 0 = none, else the 1-based hidden layer taking the concat */
     const double *w_out;      /* width[L] */
     double b_out;
+    double slope;             /* the hidden activation g(a) = a for a > 0, slope * a otherwise: 0 = ReLU,
+                                 else a leaky / parametric ReLU (the paper's closing remarks).  The
+                                 cells are Def. 2's either way; inside a cell the masks diag(s_l) of
+                                 Cor. 1 become diag(s_l + slope (1 - s_l)).  |slope| < 1; such nets
+                                 march in FP64 (AM_PREC_MIXED falls back to it; AM_PREC_SLICED and
+                                 am_compose other than FP64 refuse them) */
 } am_mlp_desc;
 
 /* Options of one march. */

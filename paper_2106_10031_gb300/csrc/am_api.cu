@@ -414,6 +414,8 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         return fail(ctx, AM_ERR_INVALID_ARG, "bad net description (layers %d, latent %d)", L, zd);
     if (dsc->skip_layer != 0 && (dsc->skip_layer < 2 || dsc->skip_layer > L))
         return fail(ctx, AM_ERR_INVALID_ARG, "skip_layer %d out of range", dsc->skip_layer);
+    if (!(std::fabs(dsc->slope) < 1.0))
+        return fail(ctx, AM_ERR_INVALID_ARG, "activation slope %g: |slope| < 1", dsc->slope);
     if ((int)ctx->nets.size() >= kMaxNets) return fail(ctx, AM_ERR_CAPACITY, "too many nets");
     int N = 0, mw = 0;
     for (int l = 0; l < L; ++l) {
@@ -569,12 +571,13 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
             }
             rel += 2.0 * (np + 8.0) * (np + 8.0) * u * u * growth;
         }
-        nd.df_ok = rel < 1e-7 ? 1 : 0;
+        nd.df_ok = rel < 1e-7 && dsc->slope == 0.0 ? 1 : 0;
     }
+    nd.slope = dsc->slope;
     {
         // sliced tensor-core compose: 8 BF16 digit planes of each hidden W_l, row exponents, and
         // a TMA descriptor per layer; only when every fan-in keeps the accumulation exact
-        nh.oz_ok = true;
+        nh.oz_ok = dsc->slope == 0.0;           // the sliced operands mask with s_l alone
         for (int l = 2; l <= L; ++l) nh.oz_ok = nh.oz_ok && dsc->width[l - 2] <= kOzMaxFanIn;
         if (nh.oz_ok && L >= 2) {
             std::vector<std::vector<uint16_t>> planes(L + 1);
@@ -1089,7 +1092,8 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
             return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED marches one net (context holds %d)",
                         (int)ctx->nets.size());
         if (!ctx->nets[0].oz_ok)
-            return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED needs every hidden fan-in <= %d", kOzMaxFanIn);
+            return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_SLICED needs a ReLU net with every hidden fan-in <= %d",
+                        kOzMaxFanIn);
         op.schedule = AM_SCHED_LEVELS;
         am_status se = ensure_oz_scratch(ctx);
         if (se != AM_OK) return se;
@@ -1281,6 +1285,8 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
         CU(cudaStreamSynchronize(ctx->stream));
         return AM_OK;
     }
+    if (precision != AM_PREC_FP64 && nh.dev.slope != 0.0)
+        return fail(ctx, AM_ERR_INVALID_ARG, "a leaky / parametric ReLU net composes in AM_PREC_FP64 only");
     if (precision == AM_PREC_TENSOR && !tc_fits(nh.dev.width, nh.dev.L, ctx->opts.max_neurons))
         return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= max_neurons + 10");
     if (n == 0) return AM_OK;

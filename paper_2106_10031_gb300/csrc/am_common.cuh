@@ -75,6 +75,7 @@ struct NetDev {
     const float *wn[kMaxLayers + 1];
     unsigned long long salt;     // per-net hash salt
     int df_ok;                   // 1: the double-float bound stays useful through this net's depth
+    double slope;                // hidden activation a (a > 0), slope a (a <= 0); 0 = ReLU
 };
 
 // Device arenas (all sized at context creation).

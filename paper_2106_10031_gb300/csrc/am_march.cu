@@ -404,11 +404,13 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
     for (int l = (M == kDF && tc) ? net.L + 1 : 2; l <= net.L; ++l) {
         const int np = net.width[l - 1], nl = net.width[l], rp = net.row0[l - 1], rl = net.row0[l];
         const int S = nl >= kT ? 1 : kT / nl;
-        // active list of layer l-1 (diag(s_{l-1}) selects these rows)
+        // active list of layer l-1 (diag(s_{l-1}) selects these rows); with a leaky ReLU every
+        // row takes part, the inactive ones scaled by the slope (diag(s + slope (1 - s)))
+        const bool leaky = M == kFP64 && net.slope != 0.0;
         int nact = 0;
         for (int base = 0; base < np; base += kT) {
             const int j = base + tid;
-            const int f = (j < np) ? (int)bit_of(s.mask, rp + j) : 0;
+            const int f = (j < np) ? (leaky ? 1 : (int)bit_of(s.mask, rp + j)) : 0;
             int tot;
             const int pos = block_scan_excl(f, s.wsum, &tot);
             if (f) s.act[nact + pos] = j;
@@ -432,12 +434,24 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
             if (M == kFP64) {
                 const double *AT = net.AT[l];
                 double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                if (leaky) {
+                    // active: z = -row (weight 1); inactive: z = +row, weight slope
+                    const double sl = net.slope;
+                    for (int t = sp; t < nact; t += S) {
+                        const int j = s.act[t];
+                        double w = __ldg(AT + (size_t)j * nl + k);
+                        if (!bit_of(s.mask, rp + j)) w *= -sl;
+                        const double *z = s.r64 + 4 * (rp + j);
+                        a0 -= w * z[0]; a1 -= w * z[1]; a2 -= w * z[2]; a3 -= w * z[3];
+                    }
+                } else {
 #pragma unroll 4
-                for (int t = sp; t < nact; t += S) {
-                    const int j = s.act[t];
-                    const double w = __ldg(AT + (size_t)j * nl + k);
-                    const double *z = s.r64 + 4 * (rp + j);          // active: z = -row
-                    a0 -= w * z[0]; a1 -= w * z[1]; a2 -= w * z[2]; a3 -= w * z[3];
+                    for (int t = sp; t < nact; t += S) {
+                        const int j = s.act[t];
+                        const double w = __ldg(AT + (size_t)j * nl + k);
+                        const double *z = s.r64 + 4 * (rp + j);          // active: z = -row
+                        a0 -= w * z[0]; a1 -= w * z[1]; a2 -= w * z[2]; a3 -= w * z[3];
+                    }
                 }
                 if (S == 1) {
                     const double sg = bit_of(s.mask, rl + k) ? -1.0 : 1.0;
@@ -519,11 +533,12 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
         const int nL = net.width[net.L], rL = net.row0[net.L];
         if (M == kFP64) {
             double f[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int k = tid; k < nL; k += kT)
-                if (bit_of(s.mask, rL + k)) {
-                    const double w = net.w_out[k];
+            for (int k = tid; k < nL; k += kT) {
+                // active: row = -Z (weight 1); inactive: row = +Z, weight slope (0 for a ReLU)
+                const double w = bit_of(s.mask, rL + k) ? net.w_out[k] : -net.slope * net.w_out[k];
+                if (w != 0.0)
                     for (int c = 0; c < 4; ++c) f[c] -= w * s.r64[4 * (rL + k) + c];
-                }
+            }
             for (int c = 0; c < 4; ++c) f[c] = warp_sum(f[c]);
             if ((tid & 31) == 0)
                 for (int c = 0; c < 4; ++c) s.partd[4 * (tid >> 5) + c] = f[c];

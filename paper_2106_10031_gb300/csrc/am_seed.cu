@@ -36,7 +36,7 @@ __device__ double seed_forward(const NetDev &net, const double *x, double *h0, d
                 const double hj = hp[j];
                 if (hj != 0.0) a += AT[(size_t)j * nl + k] * hj;
             }
-            hn[k] = a > 0.0 ? a : 0.0;
+            hn[k] = a > 0.0 ? a : net.slope * a;             // ReLU, or leaky with slope != 0
             if (a > 0.0) atomicOr(bits + ((rl + k) >> 5), 1u << ((rl + k) & 31));
         }
         __syncthreads();
@@ -160,7 +160,8 @@ __global__ void seed_insert_kernel(SeedArgs a)
 // ---- customised triggers (Sec. 4.3)
 
 // grad F at the point whose pattern the last seed_forward left in `bits`: backpropagation
-// through the active units, delta_l = dF/da_l = m_l (AT_{l+1} delta_{l+1}), delta_L = m_L w_out,
+// through the units, delta_l = dF/da_l = g'_l (AT_{l+1} delta_{l+1}), delta_L = g'_L w_out with
+// g' = 1 on active units and the slope (0 for a ReLU) on the others,
 // and grad F = sum_l Cl_l[:, 0:3]^T delta_l (only the layers fed by x have non-zero columns).
 // d0, d1: two max_w scratch rows; red: 64 doubles.  Every thread returns the same g.
 __device__ void seed_grad(const NetDev &net, const unsigned *bits, double *d0, double *d1, double *red, double g[3])
@@ -171,7 +172,7 @@ __device__ void seed_grad(const NetDev &net, const unsigned *bits, double *d0, d
     {
         const int nL = net.width[net.L], r0 = net.row0[net.L];
         for (int k = tid; k < nL; k += T)
-            dc[k] = (bits[(r0 + k) >> 5] >> ((r0 + k) & 31)) & 1u ? net.w_out[k] : 0.0;
+            dc[k] = (bits[(r0 + k) >> 5] >> ((r0 + k) & 31)) & 1u ? net.w_out[k] : net.slope * net.w_out[k];
     }
     __syncthreads();
     for (int l = net.L; l >= 1; --l) {
@@ -187,10 +188,12 @@ __device__ void seed_grad(const NetDev &net, const unsigned *bits, double *d0, d
             const int np = net.width[l - 1], rp = net.row0[l - 1];
             const double *AT = net.AT[l];
             for (int j = tid; j < np; j += T) {
+                // dF/da_j = g'(a_j) sum_k W_kj dF/da_k with g' = 1 (active) or the slope
+                const double gp = (bits[(rp + j) >> 5] >> ((rp + j) & 31)) & 1u ? 1.0 : net.slope;
                 double acc = 0.0;
-                if ((bits[(rp + j) >> 5] >> ((rp + j) & 31)) & 1u)
+                if (gp != 0.0)
                     for (int k = 0; k < nl; ++k) acc += AT[(size_t)j * nl + k] * dc[k];
-                dn[j] = acc;
+                dn[j] = gp * acc;
             }
             __syncthreads();
             double *t = dc; dc = dn; dn = t;

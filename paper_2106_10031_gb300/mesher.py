@@ -185,7 +185,7 @@ class Mesher:
             raise ValueError(f"w_out {w_out.shape}; expected ({Ws[-1].shape[0]},)")
         d = nt.am_mlp_desc(latent_dim=0 if z is None else len(z), latent=None if z is None else _dp(z),
                            n_hidden=L, width=width, W=Wp, b=bp, skip_layer=int(mlp.skip_layer),
-                           w_out=_dp(w_out), b_out=float(mlp.b_out))
+                           w_out=_dp(w_out), b_out=float(mlp.b_out), slope=float(getattr(mlp, "slope", 0.0)))
         nid = C.c_int(-1)
         self._check(self.lib.am_load_mlp(self.ctx, C.byref(d), C.byref(nid)))
         self.nets.append(mlp)

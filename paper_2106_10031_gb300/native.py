@@ -47,7 +47,7 @@ class am_mlp_desc(C.Structure):
     _fields_ = [("latent_dim", C.c_int), ("latent", C.POINTER(C.c_double)), ("n_hidden", C.c_int),
                 ("width", C.POINTER(C.c_int)), ("W", C.POINTER(C.POINTER(C.c_double))),
                 ("b", C.POINTER(C.POINTER(C.c_double))), ("skip_layer", C.c_int),
-                ("w_out", C.POINTER(C.c_double)), ("b_out", C.c_double)]
+                ("w_out", C.POINTER(C.c_double)), ("b_out", C.c_double), ("slope", C.c_double)]
 
 
 class am_march_opts(C.Structure):

@@ -17,6 +17,7 @@ from .nets import (  # noqa: F401
     proposal_target_net,
     proposal_train_nets,
     tiny_net,
+    leaky,
     seed_rays,
     trigger_points,
 )

@@ -26,6 +26,7 @@ class MLP:
     latent: np.ndarray | None = None   # z (latent_dim,), fixed per network
     skip_layer: int = 0      # 0 = none, else 1-based hidden layer taking concat(h_{l-1}, [x; z])
     name: str = ""
+    slope: float = 0.0       # hidden activation a (a > 0), slope * a otherwise: 0 = ReLU, else leaky
     meta: dict = field(default_factory=dict)
 
     @property
@@ -237,6 +238,15 @@ def sibling(mlp: MLP, seed: int, sigma: float = 0.005) -> MLP:
             mlp.w_out.copy(), float(mlp.b_out), None if mlp.latent is None else mlp.latent.copy(),
             mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta))
     m.validate()
+    return m
+
+
+def leaky(mlp: MLP, slope: float) -> MLP:
+    """The same network with the leaky / parametric ReLU g(a) = a (a > 0), slope * a (a <= 0)."""
+    import copy
+    m = copy.deepcopy(mlp)
+    m.slope = float(slope)
+    m.name = f"{mlp.name}_leaky{slope:g}"
     return m
 
 
