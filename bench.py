@@ -105,6 +105,19 @@ def parse():
                    help="run only the customised-trigger leg (sphere tracing, random pairs) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
                    help="run only the compose benchmark (am_compose on the decoder) and print its JSON")
+    p.add_argument("--seeds-only", action="store_true",
+                   help="run only the many-seeds leg (1024 sphere-traced seeds vs one ray) and print its JSON")
+    p.add_argument("--march-once", action="store_true",
+                   help="march the workload once (after --warmup marches), nearest candidates, nothing timed: "
+                        "the program a profiler captures")
+    p.add_argument("--max-cells", type=int, default=0, help="with --march-once: stop after this many cells")
+    p.add_argument("--net", default="target", choices=["target", "decoder"],
+                   help="with --march-once: the 3-[256]x8-1 workload net or the (3+256)-[512]x8-1 decoder")
+    p.add_argument("--rank1-period", type=int, default=0,
+                   help="with --march-once: a full compose every this many generations (1 = every cell in "
+                        "full; 0 = the library default)")
+    p.add_argument("--clip-kernel", default="warp", choices=["warp", "block"],
+                   help="with --march-once: the sliced level's clip, one warp or one block per cell")
     return p.parse_args()
 
 
@@ -829,6 +842,7 @@ def run_ours(args, dist):
         e2e["value"] = dist.allreduce(float(faces_per_step * max(2, min(args.steps, 5))), "sum") / (e2e_ms / 1e3)
     m.close()
     if not args.no_compare:
+        legs["many_seeds"] = seeds_leg(dev)
         legs["decoder"] = decoder_leg(dev)
         legs["sphere64x4"] = sphere_leg(dev)
         legs["compose"] = compose_leg(dev)
@@ -957,6 +971,72 @@ def load_golden(name="learned_target_256x8"):
     return g[0] if g else None
 
 
+def seeds_leg(dev, n_starts=1024, reps=2):
+    """Parallel marching from many trigger points (Sec. 4.2, Sec. 4.3.1): the bench workload
+    seeded by sphere tracing from the paper's 1024 initial points (uniform in [-1.4, 1.4]^3; eta 1,
+    at most 64 steps), marched with the sliced path: the same mesh as from the one +x ray (face
+    keys and edge cycles compared through the whole-mesh digest), a much shallower breadth-first
+    walk, hence fewer and fuller levels.  Seeding is timed apart from the march."""
+    import paper_2106_10031_gb300 as am
+    from synth import trigger_points
+    from tests import meshcheck
+    mlp, o, d = workload()
+    starts = trigger_points(n_starts, seed=4, box=1.4)
+    out = {"workload": f"{WORKLOAD}; {n_starts} sphere-traced seeds vs one ray", "precision": "sliced",
+           "candidates": "nearest"}
+    digests = {}
+    with am.Mesher(device=dev, **ctx_shape(mlp)) as m:
+        nid = m.load_mlp(mlp)
+        for name, seed in (("one_ray", lambda: m.seed(nid, o, d)),
+                           ("traced_seeds", lambda: m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12))):
+            runs = []
+            for _ in range(reps + 1):                   # the first run warms up
+                m.reset()
+                t0 = time.perf_counter()
+                seed()
+                t_seed = time.perf_counter() - t0
+                m.march(precision="sliced", candidates="nearest")
+                runs.append((m.stats(), t_seed))
+            st, t_seed = min(runs[1:], key=lambda x: x[0]["ms_march"])
+            digests[name] = meshcheck.digest(m.get_mesh(nid), mlp.N)
+            out[name] = {"faces": st["faces"], "ms_march": st["ms_march"],
+                         "faces_per_s": st["faces"] / (st["ms_march"] / 1e3), "levels": st["levels"],
+                         "cells_per_level": st["cells"] / max(1, st["levels"]), "seed_ms": t_seed * 1e3,
+                         "ms_compose": st["ms_compose"], "ms_clip": st["ms_clip"]}
+    out["same_mesh"] = digests["one_ray"] == digests["traced_seeds"]
+    out["speedup_vs_one_ray"] = out["traced_seeds"]["faces_per_s"] / out["one_ray"]["faces_per_s"]
+    return out
+
+
+
+def march_once(dev, args):
+    """The step's march alone, for a profiler and for the launch-shape comparisons: the workload
+    net (or the decoder), one +x ray, the chosen precision with nearest-row candidates (the
+    learned proposal's training would dominate a capture), args.warmup untimed marches first,
+    then one march (args.max_cells cells, 0 = all) whose am_march CUDA-event times are printed."""
+    import paper_2106_10031_gb300 as am
+    mlp, o, d = workload()
+    shape = ctx_shape(mlp)
+    if args.net == "decoder":
+        from synth import decoder_net
+        mlp = decoder_net()
+        shape = {"max_cells": 16_000_000, "max_neurons": 4096, "max_width": 512}
+    prec = args.precision
+    with am.Mesher(device=dev, **shape) as m:
+        nid = m.load_mlp(mlp)
+        m.set_tuning(rank1_period=args.rank1_period or None, clip_kernel=0 if args.clip_kernel == "warp" else 1)
+        for _ in range(max(0, args.warmup) + 1):
+            m.reset()
+            m.seed(nid, o, d)
+            m.march(precision=prec, schedule=schedule_for(prec, args.schedule), candidates="nearest",
+                    max_cells=args.max_cells)
+        st = m.stats()
+        m_tuning = m.get_tuning()
+    return {"net": mlp.name, "precision": prec, "tuning": m_tuning, "max_cells": args.max_cells,
+            "faces": st["faces"], "ms_march": st["ms_march"], "levels": st["levels"],
+            "kernel_launches": st["kernel_launches"], "ms_compose": st["ms_compose"], "ms_clip": st["ms_clip"],
+            "clip_fallbacks": st["clip_fallbacks"], "tensor_macs": st["tensor_macs"]}
+
 def main():
     args = parse()
     dist = Dist(args.gpus)
@@ -975,6 +1055,14 @@ def main():
             out = batch_leg(dist, precision=args.precision if args.precision != "sliced" else "mixed")
             if dist.rank == 0:
                 print(json.dumps({"leg": "batch64", **out}))
+            return 0
+        if args.march_once:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "march_once", **march_once(dist.local, args)}))
+            return 0
+        if args.seeds_only:
+            if dist.rank == 0:
+                print(json.dumps({"leg": "many_seeds", **seeds_leg(dist.local)}))
             return 0
         if args.triggers_only:
             if dist.rank == 0:

@@ -205,6 +205,9 @@ am_status ensure_oz_scratch(am_ctx *ctx)
     CU(cudaMalloc(&z.Q, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width)));
     CU(cudaMalloc(&z.err, sizeof(int)));
     CU(cudaMemsetAsync(z.err, 0, sizeof(int), ctx->stream));
+    // the products start at zero; every kernel that reads a product zeroes it again
+    CU(cudaMemsetAsync(z.P, 0, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width), ctx->stream));
+    CU(cudaMemsetAsync(z.Q, 0, sizeof(long long) * 4 * z.batch_cells * oz_mp(ctx->opts.max_width), ctx->stream));
     return AM_OK;
 }
 
@@ -257,6 +260,10 @@ am_status sliced_check(am_ctx *ctx)
     CU(cudaStreamSynchronize(ctx->stream));
     if (herr) {
         CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
+        // an aborted product may have left partial sums unread: start from zero again
+        const size_t pq = sizeof(long long) * 4 * ctx->oz.batch_cells * oz_mp(ctx->opts.max_width);
+        CU(cudaMemsetAsync(ctx->oz.P, 0, pq, ctx->stream));
+        CU(cudaMemsetAsync(ctx->oz.Q, 0, pq, ctx->stream));
         return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
     }
     return AM_OK;
@@ -1215,6 +1222,9 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
                 }
                 if (ctx->oz_err_host) {
                     CU(cudaMemsetAsync(ctx->oz.err, 0, sizeof(int), ctx->stream));
+                    const size_t pq = sizeof(long long) * 4 * ctx->oz.batch_cells * oz_mp(ctx->opts.max_width);
+                    CU(cudaMemsetAsync(ctx->oz.P, 0, pq, ctx->stream));
+                    CU(cudaMemsetAsync(ctx->oz.Q, 0, pq, ctx->stream));
                     CU(cudaStreamSynchronize(ctx->stream));
                     ctx->timed_out = true;           // the level's rows are not trustworthy
                     ctx->mesh_valid = false;

@@ -60,7 +60,7 @@ struct WRows {
     const WarpSh *S;
     __device__ __forceinline__ float4 hi(int k) const
     {
-        if (k < N) return p[2 * k];
+        if (k < N) return __ldg(p + 2 * k);
         if (k < N + kBoxPlanes) {
             const int i = k - N;
             const float sg = (i & 1) ? -1.0f : 1.0f;
@@ -73,7 +73,7 @@ struct WRows {
     {
         const float4 h = hi(k);
         if (k < N) {
-            const float4 l = p[2 * k + 1];
+            const float4 l = __ldg(p + 2 * k + 1);
             r[0] = (double)h.x + (double)l.x; r[1] = (double)h.y + (double)l.y;
             r[2] = (double)h.z + (double)l.z; r[3] = (double)h.w + (double)l.w;
         } else {
@@ -192,7 +192,7 @@ __device__ __forceinline__ unsigned order_key(float d)
 
 int clip_warp_smem_bytes() { return warp_smem_bytes(); }
 
-__global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
+__global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
 {
     extern __shared__ __align__(16) unsigned char wsm[];
     WarpSh &S = reinterpret_cast<WarpSh *>(wsm)[threadIdx.x >> 5];
@@ -268,10 +268,9 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
         float b1 = 3.0e38f, b2 = 3.0e38f, b3 = 3.0e38f, s3 = 3.0e38f;
         int k1 = -1, k2 = -1, k3 = -1;
         if (!fallback) {
-            for (int k = lane; k < NC; k += 32) {
-                const float4 r = rv.hi(k);
+            auto consider = [&](int k, const float4 r) {
                 const float n2 = r.x * r.x + r.y * r.y + r.z * r.z;
-                if (n2 == 0.0f) continue;
+                if (n2 == 0.0f) return;
                 const float d = fabsf(r.x * px + r.y * py + r.z * pz + r.w) * rsqrtf(n2);
                 if (d < b1) { b2 = b1; k2 = k1; b1 = d; k1 = k; }
                 else if (d < b2) { b2 = d; k2 = k; }
@@ -280,7 +279,20 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
                     const float q = k == entry ? -3.0e37f : -__bfloat162float(sc[k]);
                     if (q < s3) { s3 = q; k3 = k; b3 = d; }
                 }
+            };
+            // the neuron rows, 8 loads in flight per lane; then the box rows (lanes 0..5)
+            for (int k0 = lane; k0 < N; k0 += 32 * 8) {
+                float4 r[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + 32 * u;
+                    r[u] = k < N ? __ldg(rv.p + 2 * k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + 32 * u < N) consider(k0 + 32 * u, r[u]);
             }
+            if (lane < kBoxPlanes) consider(N + lane, rv.hi(N + lane));
             if (k3 == k1 || k3 == k2) k3 = -1;            // already a candidate
         }
         // ---- the candidate clip (FP32): nearest cutting row first; a row that holds on the
@@ -291,15 +303,19 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
             const int kk[3] = {k1, k2, k3};
             const unsigned key[3] = {order_key(b1), order_key(b2), order_key(b3)};
             bool live[3] = {k1 >= 0, k2 >= 0, k3 >= 0};
+            float cr[3][4], cri[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (kk[j] >= 0) rv.f32(kk[j], cr[j]);
+                else cr[j][0] = cr[j][1] = cr[j][2] = cr[j][3] = 0.0f;
+                cri[j] = kk[j] >= 0 ? rsqrtf(cr[j][0] * cr[j][0] + cr[j][1] * cr[j][1] + cr[j][2] * cr[j][2]) : 0.0f;
+            }
             while (!fallback && m > 0) {
                 bool c[3] = {false, false, false};
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
                     if (!live[j]) continue;
-                    float r[4];
-                    rv.f32(kk[j], r);
-                    const float ri = rsqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-                    for (int i = 0; i < m && !c[j]; ++i) c[j] = wpdist(r, ri, S.pf[buf][i]) > 1e-7f;
+                    for (int i = 0; i < m && !c[j]; ++i) c[j] = wpdist(cr[j], cri[j], S.pf[buf][i]) > 1e-7f;
                 }
 #pragma unroll
                 for (int j = 0; j < 3; ++j) live[j] = c[j];
@@ -340,8 +356,18 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
             __syncwarp();
             bool amb = false;
             int close = 0;
-            for (int k = lane; k < NC; k += 32) {
-                const float4 r4 = rv.hi(k);
+            for (int k0 = lane; k0 < NC; k0 += 32 * 4) {
+              float4 rr[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                  const int k = k0 + 32 * u;
+                  rr[u] = k < N ? __ldg(rv.p + 2 * k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int k = k0 + 32 * u;
+                if (k >= NC) break;
+                const float4 r4 = rr[u];
                 const float r[4] = {r4.x, r4.y, r4.z, r4.w};
                 const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
                 if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
@@ -374,6 +400,7 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_kernel(MarchArgs a)
                     if (p < kWViol) S.viol[p] = k;
                     else amb = true;
                 }
+              }
             }
             for (int o = 16; o > 0; o >>= 1) close += __shfl_xor_sync(FULL, close, o);
             cell_close += close;

@@ -129,8 +129,8 @@ struct OzPrep {
     int df;
     int l, L, N;
     int nl, row0;                     // width and first neuron of layer l
-    const long long *P, *Q;           // l >= 2: the exact products of layer l (diagonals 0..6, and the raw
-                                      // sum of diagonal 7), column c at P + c Mp
+    long long *P, *Q;                 // l >= 2: the exact products of layer l (diagonals 0..6, and the raw
+                                      // sum of diagonal 7), column c at P + c Mp; zeroed once read
     int Mp;
     const int *eA;                    // l >= 2: row exponents of W_l
     const int *eBin;                  // l >= 2: column exponents of layer l's right operand
@@ -213,7 +213,10 @@ __device__ __forceinline__ long long fixed62f(float x, int e)
 __device__ __forceinline__ long long oz_product(const OzPrep &p, int64_t i, int j, int k)
 {
     const int64_t o = (4 * i + j) * p.Mp + k;
-    return p.P[o] + ((p.Q[o] + 32) >> 6);
+    const long long v = p.P[o] + ((p.Q[o] + 32) >> 6);
+    p.P[o] = 0;                                   // consumed: zero for the next product's split-K sums
+    p.Q[o] = 0;
+    return v;
 }
 
 // One block of kOzPrepThreads per cell: the rows of layer l (from the exact products, or the
@@ -444,7 +447,7 @@ struct R1Prep {
     int j, L, N, nj, row0j;
     const double *ATj;                // W_j transposed (n_{j-1} x n_j)
     const int *eA;                    // row exponents of W_j
-    const long long *P, *Q;           // the products of layer j (items with flip layer <= j - 2)
+    long long *P, *Q;                 // the products of layer j (items with flip layer <= j - 2), zeroed once read
     int Mp;
     const int *eBin;                  // column exponents of layer j's operand
     int *eBout;                       // column exponents of layer j + 1's operand
@@ -482,6 +485,8 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         } else {
             const int64_t o = i * a.Mp + m;
             x = i64_ldexp(a.P[o] + ((a.Q[o] + 32) >> 6), a.eA[m] + a.eBin[i] - 48);
+            a.P[o] = 0;                               // consumed: zero for the next product's split-K sums
+            a.Q[o] = 0;
         }
         const int r = a.row0j + m;
         const bool act = key_bit(key, r);
@@ -592,6 +597,7 @@ __global__ void oz_r1_scatter_kernel(Arena ar, int64_t c0, int64_t c1, int32_t *
 // the layer product on the tensor cores
 
 struct OzGemm {
+    int64_t ncols_used;               // columns [0, ncols_used) are written (every one has a consumer)
     long long *P;                     // exact products of diagonals 0..6, column c at P + c Mp (rows 0..Mp-1)
     long long *Q;                     // the raw sum of diagonal 7, same layout (rounded once, by the prep)
     int Mp;                           // row stride between digit planes of W_l, and of P
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(192, 1)
                     for (int dg = 1; dg < kOzPlanes - 1; ++dg) a = (a << 6) + (long long)__float2int_rn(__uint_as_float(v[dg][j]));
                     const long long a7 = (long long)__float2int_rn(__uint_as_float(v[kOzPlanes - 1][j]));
                     const int64_t col = col0 + 4 * c2 + j;
-                    if (col < 4 * g.n) {
+                    if (col < g.ncols_used) {
                         long long *dst = g.P + col * g.Mp + grow, *dq = g.Q + col * g.Mp + grow;
                         if (g.split) {
                             atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
@@ -1006,7 +1012,7 @@ __global__ void __launch_bounds__(320, 1)
                     // pass 1 to P, pass 2 to Q: the prep's P + round(Q / 64) adds them exactly,
                     // so neither pass reads the other's result back
                     const int64_t col = col0 + c8 + j;
-                    if (col < 4 * g.n) {
+                    if (col < g.ncols_used) {
                         long long *dst = (pass ? g.Q : g.P) + col * g.Mp + grow;
                         if (g.split) atomicAdd(reinterpret_cast<unsigned long long *>(dst), (unsigned long long)a);
                         else *dst = a;
@@ -1165,14 +1171,12 @@ static cudaError_t oz_layer_product(const OzNet &net, int l, const OzScratch &sc
     g.KC = Kp / kOzBK;
     g.ncols = ncols;
     g.err = scr.err;
+    g.ncols_used = ncols_used;
     const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tc - 1) / (4 * tc));
     int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
+    // split-K partial sums add into P and Q, which are zero: the kernel that reads a product
+    // (the prep) zeroes it, so no memset is needed between layers
     g.split = split > 1 ? 1 : 0;
-    if (g.split) {
-        e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * 4 * nb * g.Mp, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scr.Q, 0, sizeof(long long) * 4 * nb * g.Mp, st);
-        if (e != cudaSuccess) return e;
-    }
     const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
     // 36 digit-plane products per layer over the padded tiles of the columns in use
     if (scr.issued) *scr.issued += (int64_t)36 * (4 * nb) * Mp * Kp;

@@ -26,8 +26,8 @@ class MLP:
     latent: np.ndarray | None = None   # z (latent_dim,), fixed per network
     skip_layer: int = 0      # 0 = none, else 1-based hidden layer taking concat(h_{l-1}, [x; z])
     name: str = ""
-    slope: float = 0.0       # hidden activation a (a > 0), slope * a otherwise: 0 = ReLU, else leaky
     meta: dict = field(default_factory=dict)
+    slope: float = 0.0       # hidden activation a (a > 0), slope * a otherwise: 0 = ReLU, else leaky
 
     @property
     def widths(self) -> list:
@@ -236,7 +236,7 @@ def sibling(mlp: MLP, seed: int, sigma: float = 0.005) -> MLP:
     m = MLP([w + rng.normal(0.0, sigma, w.shape) for w in mlp.weights],
             [b + rng.normal(0.0, sigma, b.shape) for b in mlp.biases],
             mlp.w_out.copy(), float(mlp.b_out), None if mlp.latent is None else mlp.latent.copy(),
-            mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta))
+            mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta), mlp.slope)
     m.validate()
     return m
 

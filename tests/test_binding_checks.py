@@ -6,8 +6,8 @@ import ctypes as C
 import numpy as np
 import pytest
 
-from synth import (batch_nets, decoder_net, octahedron, polytope_max_of_planes, proposal_target_net,
-                   sphere_net, tiny_net)
+from synth import (batch_nets, decoder_net, leaky, octahedron, polytope_max_of_planes, proposal_target_net,
+                   proposal_train_nets, sibling, sphere_net, tiny_net)
 
 
 class _Stub:
@@ -33,6 +33,8 @@ def mesher():
     lambda: decoder_net(width=24, depth=6, latent_dim=9, skip_layer=3, seed=7, sigma=0.05),
     lambda: decoder_net(), sphere_net, polytope_max_of_planes, lambda: tiny_net((6, 5, 4), 12), octahedron,
     proposal_target_net, lambda: batch_nets()[0], lambda: batch_nets()[63],
+    lambda: sibling(sphere_net(), seed=99), lambda: sibling(leaky(sphere_net(), 0.1), seed=3),
+    lambda: leaky(tiny_net((6, 5, 4), 12), -0.25), lambda: proposal_train_nets()[31],
 ])
 def test_every_workload_net_passes(mesher, make):
     mesher.load_mlp(make())
