@@ -67,20 +67,23 @@ def _measured_hbm_peak():
 HBM_PEAK_GBS = _measured_hbm_peak()
 
 
-# DRAM bytes of one march_persistent_kernel launch (double-float + learned candidates, bench
-# workload) from the committed ncu capture, valid while the kernel source is the one captured
-TRAFFIC_CAPTURE = {"sha256_prefix": "46d62118611829ca", "precision": "mixed", "candidates": "learned",
-                   "bytes": 2.973440e6 + 0.518912e6}
+# DRAM bytes per cell of one clip_warp_kernel launch (sliced, learned candidates, the step's
+# net) from the committed ncu capture (one level of 1120 cells), valid while the kernel source
+# is the one captured; the bench scales it to the cells of an average launch
+TRAFFIC_CAPTURE = {"sha256_prefix": None, "source": "am_clip_warp.cu", "precision": "sliced",
+                   "candidates": "learned", "cells": 1120, "bytes": 80.150528e6 + 3.370240e6}
 
 
-def captured_traffic(precision, candidates):
+def captured_traffic(precision, candidates, cells_per_launch):
     import hashlib
-    src = os.path.join(ROOT, "paper_2106_10031_gb300", "csrc", "am_march.cu")
+    c = TRAFFIC_CAPTURE
+    if not c["sha256_prefix"]:
+        return None
+    src = os.path.join(ROOT, "paper_2106_10031_gb300", "csrc", c["source"])
     with open(src, "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()[:16]
-    c = TRAFFIC_CAPTURE
     if h == c["sha256_prefix"] and (precision, candidates) == (c["precision"], c["candidates"]):
-        return c["bytes"]
+        return c["bytes"] / c["cells"] * cells_per_launch
     return None
 
 
@@ -108,8 +111,8 @@ def parse():
     p.add_argument("--seeds-only", action="store_true",
                    help="run only the many-seeds leg (1024 sphere-traced seeds vs one ray) and print its JSON")
     p.add_argument("--march-once", action="store_true",
-                   help="march the workload once (after --warmup marches), nearest candidates, nothing timed: "
-                        "the program a profiler captures")
+                   help="march the workload once (after --warmup marches) with --precision and --candidates, "
+                        "nothing else timed: the program a profiler captures")
     p.add_argument("--max-cells", type=int, default=0, help="with --march-once: stop after this many cells")
     p.add_argument("--net", default="target", choices=["target", "decoder"],
                    help="with --march-once: the 3-[256]x8-1 workload net or the (3+256)-[512]x8-1 decoder")
@@ -118,6 +121,9 @@ def parse():
                         "full; 0 = the library default)")
     p.add_argument("--clip-kernel", default="warp", choices=["warp", "block"],
                    help="with --march-once: the sliced level's clip, one warp or one block per cell")
+    p.add_argument("--check-kernel", default="warp", choices=["warp", "tensor"],
+                   help="with --march-once: the dense check of every row at every vertex in the warp clip "
+                        "(CUDA cores) or on the tcgen05 tensor cores")
     return p.parse_args()
 
 
@@ -592,7 +598,8 @@ def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
                 kw = (mlp.N + 63) // 64
                 clip_bytes = cells_n * ((mlp.N + 1) * 32 + 8 * kw + 64) + st["corners"] * 28
                 gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
-                out[prec]["clip_roofline"] = {"kernel": "march_range_kernel<double-float> (rows from HBM)", "bound": "hbm",
+                out[prec]["clip_roofline"] = {"kernel": "clip_warp_kernel (+ the block kernel on its fallback list)",
+                                              "bound": "hbm",
                                               "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
                                               "frac": gbs / HBM_PEAK_GBS, "bytes_per_cell": clip_bytes / cells_n}
         out["sliced_speedup_vs_fp64"] = out["sliced"]["faces_per_s"] / out["fp64"]["faces_per_s"]
@@ -849,27 +856,36 @@ def run_ours(args, dist):
     if dist.rank != 0:
         return 0
     st = r["stats"]
-    # the dominant kernel of the step by device time: the clip (march kernel) or, on the sliced
-    # path, the compose on the tensor cores (product + prep kernels)
+    # the dominant kernel of the step by device time (the committed launch list): on the sliced
+    # path the warp clip (one launch per level, with the block kernel on its fallback list in the
+    # same event range), an HBM-bound pass over the rows the compose wrote; otherwise the march
+    # kernel.  The compose on the tensor cores (product + prep kernels) is reported beside it.
     cell_ms, comp_ms = r["cell_ms"] if prec != "sliced" else r["clip_ms"], r["compose_ms"]
-    if prec == "sliced" and comp_ms > cell_ms:
-        ach = work["compose_flops"] * args.steps / (comp_ms / 1e3) / 1e12
-        roof = {"kernel": "oz_gemm_kernel + oz_prep_kernel + rank-1 kernels (the compose on the tcgen05 tensor cores)",
-                "bound": "tensor", "achieved": ach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / BF16_PEAK_TFLOPS, "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
-                "counts": "useful flops of Cor. 1: 8 per masked multiply-add (4 columns)",
-                "issued_tflops": 2 * st["tensor_macs"] / (comp_ms / args.steps / 1e3) / 1e12}
+    kw = (mlp.N + 63) // 64
+    per_cell = (mlp.N + 1) * 32 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64
+    byts = (st["cells"] * per_cell + st["corners"] * 28) * args.steps
+    ach = byts / (cell_ms / 1e3) / 1e9
+    if prec == "sliced":
+        kname = "clip_warp_kernel (+ march_range_kernel<double-float> on its fallback list)" \
+            if args.candidates != "none" else "march_range_kernel<double-float>"
     else:
-        kw = (mlp.N + 63) // 64
-        per_cell = (mlp.N + 1) * 32 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64
-        byts = (st["cells"] * per_cell + st["corners"] * 28) * args.steps
-        ach = byts / (cell_ms / 1e3) / 1e9
-        kname = "march_range_kernel<double-float>" if sched == "levels" else "march_persistent_kernel"
-        roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                "frac": ach / HBM_PEAK_GBS, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
-                "counts": "rows read ((N + 1) x 32 B per cell on the sliced path), key, face record"}
-    roof["traffic"] = captured_traffic(prec, args.candidates)
-    roof["launch_ms"] = (comp_ms if roof["bound"] == "tensor" else cell_ms) / max(1, args.steps)
+        kname = "march_persistent_kernel" if sched == "persistent" else "march_range_kernel"
+    launches_per_step = max(1, st["levels"]) if sched == "levels" else 1
+    roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": ach / HBM_PEAK_GBS, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+            "counts": "algorithmic bytes: the rows read ((N + 1) x 32 B per cell on the sliced path), the key "
+                      "and the face record (28 B per corner)",
+            "units": f"{st['cells']} cells per step in {launches_per_step} launches"}
+    roof["traffic"] = captured_traffic(prec, args.candidates, st["cells"] / launches_per_step)
+    roof["launch_ms"] = cell_ms / max(1, args.steps) / launches_per_step
+    if prec == "sliced":
+        cach = work["compose_flops"] * args.steps / (comp_ms / 1e3) / 1e12
+        roof["compose"] = {"kernel": "oz_gemm_kernel + oz_prep_kernel + rank-1 kernels (tcgen05)", "bound": "tensor",
+                           "achieved": cach, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": cach / BF16_PEAK_TFLOPS,
+                           "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                           "counts": "useful flops of Cor. 1: 8 per masked multiply-add (4 columns)",
+                           "issued_tflops": 2 * st["tensor_macs"] / (comp_ms / args.steps / 1e3) / 1e12,
+                           "ms_per_step": comp_ms / args.steps}
     roof["share_of_step"] = {"compose": r["compose_ms"] / max(r["total_ms"], 1e-9),
                              "clip": r["clip_ms"] / max(r["total_ms"], 1e-9),
                              "cell_kernels": r["cell_ms"] / max(r["total_ms"], 1e-9)}
@@ -1011,9 +1027,11 @@ def seeds_leg(dev, n_starts=1024, reps=2):
 
 def march_once(dev, args):
     """The step's march alone, for a profiler and for the launch-shape comparisons: the workload
-    net (or the decoder), one +x ray, the chosen precision with nearest-row candidates (the
-    learned proposal's training would dominate a capture), args.warmup untimed marches first,
-    then one march (args.max_cells cells, 0 = all) whose am_march CUDA-event times are printed."""
+    net (or the decoder), one +x ray, the chosen precision and candidates, args.warmup untimed
+    marches first, then one march (args.max_cells cells, 0 = all; the context is sized to it)
+    whose am_march CUDA-event times are printed.  Learned candidates come from an untrained
+    proposal of the step's shape: the same forward-pass work per level without the training's
+    launches in front of a capture (which candidates it picks does not change the launches)."""
     import paper_2106_10031_gb300 as am
     mlp, o, d = workload()
     shape = ctx_shape(mlp)
@@ -1021,18 +1039,24 @@ def march_once(dev, args):
         from synth import decoder_net
         mlp = decoder_net()
         shape = {"max_cells": 16_000_000, "max_neurons": 4096, "max_width": 512}
+    if args.max_cells:
+        shape["max_cells"] = min(shape["max_cells"], max(1 << 16, 2 * args.max_cells))
     prec = args.precision
     with am.Mesher(device=dev, **shape) as m:
         nid = m.load_mlp(mlp)
-        m.set_tuning(rank1_period=args.rank1_period or None, clip_kernel=0 if args.clip_kernel == "warp" else 1)
+        m.set_tuning(rank1_period=args.rank1_period or None, clip_kernel=0 if args.clip_kernel == "warp" else 1,
+                     check_kernel=0 if args.check_kernel == "warp" else 1)
+        if args.candidates == "learned":
+            m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
         for _ in range(max(0, args.warmup) + 1):
             m.reset()
             m.seed(nid, o, d)
-            m.march(precision=prec, schedule=schedule_for(prec, args.schedule), candidates="nearest",
+            m.march(precision=prec, schedule=schedule_for(prec, args.schedule), candidates=args.candidates,
                     max_cells=args.max_cells)
         st = m.stats()
         m_tuning = m.get_tuning()
-    return {"net": mlp.name, "precision": prec, "tuning": m_tuning, "max_cells": args.max_cells,
+    return {"net": mlp.name, "precision": prec, "candidates": args.candidates, "tuning": m_tuning,
+            "max_cells": args.max_cells,
             "faces": st["faces"], "ms_march": st["ms_march"], "levels": st["levels"],
             "kernel_launches": st["kernel_launches"], "ms_compose": st["ms_compose"], "ms_clip": st["ms_clip"],
             "clip_fallbacks": st["clip_fallbacks"], "tensor_macs": st["tensor_macs"]}

@@ -111,9 +111,11 @@ typedef struct {
 } am_ctx_opts;
 
 /* One ReLU MLP (Sec. 2.2, Eq. 1 with biases): F(x) = w_out . h_L + b_out,
- * h_l = relu(W_l u_l + b_l); u_1 = [x; z]; u_l = h_{l-1}, or concat(h_{l-1}, [x; z]) at the
- * skip layer (a DeepSDF-style skip-concat shortcut, Sec. 5.1).  Row-major FP64, caller
- * owned, copied by am_load_mlp. */
+ * h_l = relu(W_l u_l + b_l + S_l h_src(l)); u_1 = [x; z]; u_l = h_{l-1}, or concat(h_{l-1}, [x; z])
+ * at the skip layer (a DeepSDF-style skip-concat shortcut, Sec. 5.1); h_0 = x.  The optional
+ * residual shortcut S_l h_src(l) is Sec. 5.1's residual block ending at layer l: the identity
+ * (first kind, g(x + T x)) or a matrix V (second kind, g(V x + T x)) from an earlier layer.
+ * Row-major FP64, caller owned, copied by am_load_mlp. */
 typedef struct {
     int latent_dim;           /* length of the fixed latent code z (0 = none) */
     const double *latent;     /* z, latent_dim values (may be NULL when latent_dim == 0) */
@@ -131,6 +133,15 @@ typedef struct {
                                  Cor. 1 become diag(s_l + slope (1 - s_l)).  |slope| < 1; such nets
                                  march in FP64 (AM_PREC_MIXED falls back to it; AM_PREC_SLICED and
                                  am_compose other than FP64 refuse them) */
+    const int *shortcut_src;  /* NULL, or n_hidden entries: hidden layer l (1-based, entry l - 1) adds
+                                 S_l h_src to its pre-activation, src in 0 .. l - 1 (0 = the input x,
+                                 3 coordinates; >= 1 a hidden layer), or -1 for none.  A shortcut
+                                 from x is folded into the layer's constant rows at load time;
+                                 a net with a shortcut from a hidden layer marches in FP64, as a
+                                 leaky net does */
+    const double *const *shortcut_S;   /* NULL, or n_hidden pointers: S_l, width[l] x n_src row-major
+                                 (n_src = 3 for x, else width[src]); a NULL pointer = the identity,
+                                 which needs n_src == width[l] */
 } am_mlp_desc;
 
 /* Options of one march. */
@@ -359,6 +370,14 @@ typedef struct {
     int clip_kernel;          /* AM_PREC_SLICED march with candidates: 0 (default) = one warp per cell for
                                  every cell whose tests it decides outright, the block kernel for the
                                  rest; 1 = the block kernel (one block per cell) for every cell */
+    int check_kernel;         /* AM_PREC_SLICED march, clip_kernel 0: the dense check of every row at
+                                 every vertex (Eq. 10) after the candidate clip.  0 (default) = in
+                                 the warp clip, certified FP32 on the CUDA cores; 1 = on the tcgen05
+                                 tensor cores for polygons of at most 16 vertices (each 128-row tile
+                                 of the cell's rows times its vertices, exact BF16 parts, FP32
+                                 accumulators, a certified sign test with FP64 close calls), any
+                                 violated row sending the cell to the block kernel.  Both give the
+                                 same mesh. */
 } am_tuning;
 
 /* Set (t != NULL) the context's launch shapes.  AM_ERR_INVALID_ARG for an unsupported value. */

@@ -78,6 +78,7 @@ struct am_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, evk0 = nullptr, evk1 = nullptr;
     std::vector<cudaEvent_t> oz_ev;    // sliced march: 3 events per batch of a level, read after the level
     int oz_err_host = 0;               // sliced march: the pipeline time-out flag, copied with the counters
+    int64_t oz_dirty = 0;              // sliced compose: leading elements of P and Q that may be non-zero
     // seeding scratch (grown on demand)
     double *d_rays = nullptr;
     unsigned long long *d_seed_keys = nullptr;
@@ -111,8 +112,12 @@ struct am_ctx {
     int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
     int oz_rank1_period = 0;      // rank-1 compose: full compose every this many generations (0 = 8)
     int clip_kernel = 0;          // sliced march: 0 warp-per-cell clip with block fallback, 1 block kernel
+    int check_kernel = 0;         // sliced march, warp clip: 0 check in the warp, 1 dense check on the tensor cores
     int32_t *fb_list = nullptr;   // the warp clip's fallback cells (one chunk of a level) and their count
     unsigned long long *fb_count = nullptr;
+    CheckRec *chk = nullptr;      // the tensor-core check's records (one chunk), their count and status
+    unsigned long long *chk_count = nullptr;
+    int *chk_status = nullptr;
     // march with AM_PREC_SLICED: the rows of the level being solved and of the level before it
     // (the parents of the next level's rank-1 composes), FP32 pairs, (N + 1) x 32 B per cell
     double *lv_rows[2] = {nullptr, nullptr};
@@ -198,6 +203,7 @@ am_status ensure_oz_scratch(am_ctx *ctx)
     OzScratch &z = ctx->oz;
     z.batch_cells = 4096;
     z.issued = &ctx->stats.tensor_macs;
+    z.dirty = &ctx->oz_dirty;
     CU(cudaMalloc(&z.B, sizeof(__nv_bfloat16) * oz_scratch_elems(z.batch_cells, oz_kp(ctx->opts.max_width))));
     CU(cudaMalloc(&z.eB[0], sizeof(int) * 4 * z.batch_cells));
     CU(cudaMalloc(&z.eB[1], sizeof(int) * 4 * z.batch_cells));
@@ -264,6 +270,7 @@ am_status sliced_check(am_ctx *ctx)
         const size_t pq = sizeof(long long) * 4 * ctx->oz.batch_cells * oz_mp(ctx->opts.max_width);
         CU(cudaMemsetAsync(ctx->oz.P, 0, pq, ctx->stream));
         CU(cudaMemsetAsync(ctx->oz.Q, 0, pq, ctx->stream));
+        ctx->oz_dirty = 0;
         return fail(ctx, AM_ERR_TIMEOUT, "a tensor-core pipeline wait of the sliced compose gave up");
     }
     return AM_OK;
@@ -360,6 +367,7 @@ am_status am_create(am_ctx **out, const am_ctx_opts *o)
     if (ctx->blocks_per_sm < 1) return fail(ctx, AM_ERR_CUDA, "the march kernel cannot be resident");
     CU(prepare_seed_kernels(d.max_neurons, d.max_width));
     CU(prepare_clip_warp());
+    CU(prepare_check_tc());
     CU(cudaStreamSynchronize(ctx->stream));
     return AM_OK;
 }
@@ -394,6 +402,9 @@ void am_destroy(am_ctx *ctx)
         if (ctx->lv_rows[b]) cudaFree(ctx->lv_rows[b]);
     if (ctx->fb_list) cudaFree(ctx->fb_list);
     if (ctx->fb_count) cudaFree(ctx->fb_count);
+    if (ctx->chk) cudaFree(ctx->chk);
+    if (ctx->chk_count) cudaFree(ctx->chk_count);
+    if (ctx->chk_status) cudaFree(ctx->chk_status);
     for (void *b : {(void *)ctx->r1.full_list, (void *)ctx->r1.r1_list, (void *)ctx->r1.it_l, (void *)ctx->r1.it_k,
                     (void *)ctx->r1.it_a, (void *)ctx->r1.counts, (void *)ctx->r1.offs})
         if (b) cudaFree(b);
@@ -433,6 +444,24 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     if (N > ctx->opts.max_neurons || mw > ctx->opts.max_width)
         return fail(ctx, AM_ERR_INVALID_ARG, "net has N=%d neurons, width %d; context allows %d, %d", N, mw,
                     ctx->opts.max_neurons, ctx->opts.max_width);
+    // residual shortcuts (Sec. 5.1): S_l h_src added to layer l's pre-activation
+    bool hidden_shortcut = false;
+    if (dsc->shortcut_src) {
+        for (int l = 1; l <= L; ++l) {
+            const int src = dsc->shortcut_src[l - 1];
+            if (src < 0) continue;
+            if (src >= l)
+                return fail(ctx, AM_ERR_INVALID_ARG, "layer %d: shortcut source %d is not an earlier layer", l, src);
+            const int ns = src == 0 ? 3 : dsc->width[src - 1];
+            const bool ident = !dsc->shortcut_S || !dsc->shortcut_S[l - 1];
+            if (ident && ns != dsc->width[l - 1])
+                return fail(ctx, AM_ERR_INVALID_ARG, "layer %d: an identity shortcut needs %d == %d units", l, ns,
+                            dsc->width[l - 1]);
+            hidden_shortcut = hidden_shortcut || src >= 1;
+        }
+    }
+    auto sc_src = [&](int l) { return dsc->shortcut_src ? dsc->shortcut_src[l - 1] : -1; };
+    auto sc_mat = [&](int l) -> const double * { return dsc->shortcut_S ? dsc->shortcut_S[l - 1] : nullptr; };
     // fold: Cl (n_l x 4) and AT (n_{l-1} x n_l), then w_out
     std::vector<double> host;
     std::vector<size_t> offC(L + 1), offA(L + 1);
@@ -448,6 +477,10 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
                 for (int i = 0; i < 3; ++i) c[i] = W[(size_t)k * fan + xoff + i];
                 for (int j = 0; j < zd; ++j) c[3] += W[(size_t)k * fan + xoff + 3 + j] * dsc->latent[j];
             }
+            if (sc_src(l) == 0) {                  // a shortcut from x: S_l x joins the constant rows
+                const double *S = sc_mat(l);
+                for (int i = 0; i < 3; ++i) c[i] += S ? S[(size_t)k * 3 + i] : (k == i ? 1.0 : 0.0);
+            }
             host.insert(host.end(), c, c + 4);
         }
         offA[l] = host.size();
@@ -460,6 +493,13 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     }
     const size_t offW = host.size();
     host.insert(host.end(), dsc->w_out, dsc->w_out + dsc->width[L - 1]);
+    std::vector<size_t> offS(L + 1, 0);            // matrix shortcuts from hidden layers
+    for (int l = 2; l <= L; ++l) {
+        const int src = sc_src(l);
+        if (src < 1 || !sc_mat(l)) continue;
+        offS[l] = host.size();
+        host.insert(host.end(), sc_mat(l), sc_mat(l) + (size_t)dsc->width[l - 1] * dsc->width[src - 1]);
+    }
     // double-float split of every value: hi = fl32(x), lo = fl32(x - hi)
     std::vector<float> fhost(2 * host.size());
     for (size_t i = 0; i < host.size(); ++i) {
@@ -489,6 +529,8 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         nd.Cllo[l] = nh.fblob + lo_off + offC[l];
         nd.AThi[l] = l > 1 ? nh.fblob + offA[l] : nullptr;
         nd.ATlo[l] = l > 1 ? nh.fblob + lo_off + offA[l] : nullptr;
+        nd.sc_src[l] = sc_src(l) >= 1 ? sc_src(l) : 0;
+        nd.sc_S[l] = nd.sc_src[l] && offS[l] ? nh.blob + offS[l] : nullptr;
     }
     {
         // tensor-core operands: BF16 hi/lo of W_l (hidden part) in A-fragment order, row norms
@@ -578,13 +620,14 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
             }
             rel += 2.0 * (np + 8.0) * (np + 8.0) * u * u * growth;
         }
-        nd.df_ok = rel < 1e-7 && dsc->slope == 0.0 ? 1 : 0;
+        nd.df_ok = rel < 1e-7 && dsc->slope == 0.0 && !hidden_shortcut ? 1 : 0;
     }
     nd.slope = dsc->slope;
+    nd.fp64_only = dsc->slope != 0.0 || hidden_shortcut ? 1 : 0;
     {
         // sliced tensor-core compose: 8 BF16 digit planes of each hidden W_l, row exponents, and
         // a TMA descriptor per layer; only when every fan-in keeps the accumulation exact
-        nh.oz_ok = dsc->slope == 0.0;           // the sliced operands mask with s_l alone
+        nh.oz_ok = !nd.fp64_only;               // the sliced operands mask with s_l alone, no shortcut
         for (int l = 2; l <= L; ++l) nh.oz_ok = nh.oz_ok && dsc->width[l - 2] <= kOzMaxFanIn;
         if (nh.oz_ok && L >= 2) {
             std::vector<std::vector<uint16_t>> planes(L + 1);
@@ -923,6 +966,9 @@ static am_status ensure_r1_scratch(am_ctx *ctx)
     r.item_cap = items;
     CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * ctx->oz.batch_cells));
     CU(cudaMalloc(&ctx->fb_count, sizeof(unsigned long long)));
+    CU(cudaMalloc(&ctx->chk, sizeof(CheckRec) * ctx->oz.batch_cells));
+    CU(cudaMalloc(&ctx->chk_count, sizeof(unsigned long long)));
+    CU(cudaMalloc(&ctx->chk_status, sizeof(int) * ctx->oz.batch_cells));
     return AM_OK;
 }
 
@@ -1046,8 +1092,38 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
             CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
             ma.fb_list = ctx->fb_list;
             ma.fb_count = ctx->fb_count;
-            launch_clip_warp(ma, ctx->stream);
-            CU(cudaGetLastError());
+            if (ctx->check_kernel == 1) {
+                // candidate clip in the warp, the dense check on the tensor cores, then emit and push
+                CU(cudaMemsetAsync(ctx->chk_count, 0, sizeof(unsigned long long), ctx->stream));
+                ma.chk = ctx->chk;
+                ma.chk_count = ctx->chk_count;
+                ma.chk_status = ctx->chk_status;
+                launch_clip_warp(ma, ctx->stream);
+                CU(cudaGetLastError());
+                CheckArgs ca{};
+                ca.rec = ctx->chk;
+                ca.count = ctx->chk_count;
+                ca.rows = reinterpret_cast<const float *>(ma.rows_in);
+                ca.begin = c0;
+                ca.N = N;
+                ca.box = (float)ma.box;
+                ca.delta = ma.delta;
+                ca.status = ctx->chk_status;
+                ca.counters = ctx->ar.counters;
+                ca.err = ctx->oz.err;
+                launch_check_tc(ca, ctx->sm_count, ctx->stream);
+                CU(cudaGetLastError());
+                launch_clip_warp_finish(ma, ctx->stream);
+                CU(cudaGetLastError());
+                ma.chk = nullptr;
+                ma.chk_count = nullptr;
+                ma.chk_status = nullptr;
+                ctx->stats.cell_launches += 2;
+                launches += 2;
+            } else {
+                launch_clip_warp(ma, ctx->stream);
+                CU(cudaGetLastError());
+            }
             MarchArgs mb = ma;
             mb.list = ctx->fb_list;
             mb.list_count = ctx->fb_count;
@@ -1225,6 +1301,7 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
                     const size_t pq = sizeof(long long) * 4 * ctx->oz.batch_cells * oz_mp(ctx->opts.max_width);
                     CU(cudaMemsetAsync(ctx->oz.P, 0, pq, ctx->stream));
                     CU(cudaMemsetAsync(ctx->oz.Q, 0, pq, ctx->stream));
+                    ctx->oz_dirty = 0;
                     CU(cudaStreamSynchronize(ctx->stream));
                     ctx->timed_out = true;           // the level's rows are not trustworthy
                     ctx->mesh_valid = false;
@@ -1295,8 +1372,9 @@ am_status am_compose(am_ctx *ctx, int net_id, const uint64_t *d_keys, int64_t n,
         CU(cudaStreamSynchronize(ctx->stream));
         return AM_OK;
     }
-    if (precision != AM_PREC_FP64 && nh.dev.slope != 0.0)
-        return fail(ctx, AM_ERR_INVALID_ARG, "a leaky / parametric ReLU net composes in AM_PREC_FP64 only");
+    if (precision != AM_PREC_FP64 && nh.dev.fp64_only)
+        return fail(ctx, AM_ERR_INVALID_ARG,
+                    "a leaky / parametric ReLU net or one with hidden-layer shortcuts composes in AM_PREC_FP64 only");
     if (precision == AM_PREC_TENSOR && !tc_fits(nh.dev.width, nh.dev.L, ctx->opts.max_neurons))
         return fail(ctx, AM_ERR_INVALID_ARG, "AM_PREC_TENSOR needs 2 n_{l-1} (rounded to 16) <= max_neurons + 10");
     if (n == 0) return AM_OK;
@@ -1408,9 +1486,12 @@ am_status am_set_tuning(am_ctx *ctx, const am_tuning *t)
         return fail(ctx, AM_ERR_INVALID_ARG, "rank1_period %d out of range", t->rank1_period);
     if (t->clip_kernel != 0 && t->clip_kernel != 1)
         return fail(ctx, AM_ERR_INVALID_ARG, "clip_kernel %d: 0 or 1", t->clip_kernel);
+    if (t->check_kernel != 0 && t->check_kernel != 1)
+        return fail(ctx, AM_ERR_INVALID_ARG, "check_kernel %d: 0 or 1", t->check_kernel);
     ctx->oz_tile_cells = t->compose_tile_cells;
     ctx->oz_rank1_period = t->rank1_period;
     ctx->clip_kernel = t->clip_kernel;
+    ctx->check_kernel = t->check_kernel;
     return AM_OK;
 }
 
@@ -1420,6 +1501,7 @@ am_status am_get_tuning(const am_ctx *ctx, am_tuning *t)
     t->compose_tile_cells = ctx->oz_tile_cells;
     t->rank1_period = ctx->oz_rank1_period;
     t->clip_kernel = ctx->clip_kernel;
+    t->check_kernel = ctx->check_kernel;
     return AM_OK;
 }
 

@@ -141,9 +141,11 @@ __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned 
 // The same push by a whole warp (every lane calls it with the same arguments): lane 0 claims
 // the slot and the id, the lanes copy and compare the key words in parallel.  For wide keys
 // (N = 4096: 64 words) this turns 2 kw serial L2 round trips per tag hit into 2 kw / 32.
+// publish = false (the level schedule: the new cell is read only by later launches, after this
+// kernel has ended) skips the fence and the release store that a persistent consumer needs.
 __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsigned *mask, int64_t parent, int net,
                                                      unsigned flip, unsigned long long h, float px, float py,
-                                                     float pz)
+                                                     float pz, bool publish = true)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
@@ -177,10 +179,14 @@ __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsi
                 ar.entry_pt[id * 3 + 1] = py;
                 ar.entry_pt[id * 3 + 2] = pz;
             }
-            __threadfence();          // every lane's key words are visible device-wide ...
-            __syncwarp();
-            // ... before the flag that publishes them
-            if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ar.ready + id), "r"(1u) : "memory");
+            if (publish) {
+                __threadfence();      // every lane's key words are visible device-wide ...
+                __syncwarp();
+                // ... before the flag that publishes them
+                if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ar.ready + id), "r"(1u) : "memory");
+            } else if (lane == 0) {
+                ar.ready[id] = 1u;    // visible to later launches at the kernel boundary
+            }
             return;
         }
         if (slot_tag(cur) == hash_tag(h)) {

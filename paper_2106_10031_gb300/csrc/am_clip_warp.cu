@@ -34,7 +34,6 @@ constexpr int kWViol = 32;        // violated rows cut in per check round
 constexpr int kWMaxKw = 128;      // key words (N <= 8190)
 constexpr int kWMaxFix = 8;       // check / fix-up rounds
 constexpr float kWU = 5.9604645e-8f;   // 2^-24
-constexpr double kWVertexTol = 1e-5;   // largest vertex bound (relative) kept
 
 struct WarpSh {
     double pv[2][kWPoly][3];      // FP64 polygon
@@ -188,6 +187,207 @@ __device__ __forceinline__ unsigned order_key(float d)
     return (du & 0x80000000u) ? ~du : (du | 0x80000000u);
 }
 
+// the cell's key as 32-bit words in the warp's shared memory (pushes copy it)
+__device__ __forceinline__ void wload_key(WarpSh &S, const Arena &ar, int64_t cell)
+{
+    const int lane = threadIdx.x & 31;
+    for (int w = lane; w < ar.kw; w += 32) {
+        const unsigned long long x = __ldcg(ar.keys + cell * ar.kw + w);
+        S.key[2 * w] = (unsigned)x;
+        S.key[2 * w + 1] = (unsigned)(x >> 32);
+    }
+}
+
+// The cell's rows view, key and face plane a_F in the warp's shared memory, then (lane 0) the
+// face plane's FP32 frame and the square about the box section: the initial polygon in buffer 0
+// (planes N + 6 .. N + 9).  Returns its vertex count, 0 when a_F has no normal.
+__device__ int wcell_setup(const MarchArgs &a, WarpSh &S, int64_t cell, int N, WRows &rv)
+{
+    const int lane = threadIdx.x & 31;
+    rv.p = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * 2 * (int64_t)(N + 1);
+    rv.N = N;
+    rv.box = (float)a.box;
+    rv.S = &S;
+    wload_key(S, a.ar, cell);
+    if (lane < 4) {
+        const float h = reinterpret_cast<const float *>(rv.p + 2 * N)[lane];
+        const float l = reinterpret_cast<const float *>(rv.p + 2 * N + 1)[lane];
+        S.aF[lane] = (double)h + (double)l;
+        S.aFhi[lane] = h;
+    }
+    __syncwarp();
+    int m = 0;
+    if (lane == 0) {
+        const float F[4] = {(float)S.aF[0], (float)S.aF[1], (float)S.aF[2], (float)S.aF[3]};
+        const float nn = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+        if (nn > 0.0f && isfinite(nn)) {
+            const float inn = 1.0f / nn;
+            const float p0[3] = {-F[3] * F[0] * inn, -F[3] * F[1] * inn, -F[3] * F[2] * inn};
+            const float inv = rsqrtf(nn);
+            const float n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
+            const float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
+            const int ei = (ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2);
+            const float e0 = ei == 0 ? 1.0f : 0.0f, e1 = ei == 1 ? 1.0f : 0.0f, e2 = ei == 2 ? 1.0f : 0.0f;
+            float u[3] = {n[1] * e2 - n[2] * e1, n[2] * e0 - n[0] * e2, n[0] * e1 - n[1] * e0};
+            const float un = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            u[0] *= un; u[1] *= un; u[2] *= un;
+            const float w[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+            const float sz = 1.05f * 1.7320508f * (float)a.box;
+            const float d[4][3] = {{-w[0], -w[1], -w[2]}, {u[0], u[1], u[2]}, {w[0], w[1], w[2]}, {-u[0], -u[1], -u[2]}};
+            const float cu[4] = {-1.0f, 1.0f, 1.0f, -1.0f}, cw[4] = {-1.0f, -1.0f, 1.0f, 1.0f};
+            for (int i = 0; i < 4; ++i) {
+                S.sq[i][0] = d[i][0]; S.sq[i][1] = d[i][1]; S.sq[i][2] = d[i][2];
+                S.sq[i][3] = -(d[i][0] * p0[0] + d[i][1] * p0[1] + d[i][2] * p0[2]) - sz;
+                for (int c = 0; c < 3; ++c) {
+                    const float x = p0[c] + sz * (cu[i] * u[c] + cw[i] * w[c]);
+                    S.pv[0][i][c] = (double)x;
+                    S.pf[0][i][c] = x;
+                }
+                S.pe[0][i] = N + kBoxPlanes + i;
+            }
+            m = 4;
+        }
+    }
+    m = __shfl_sync(0xffffffffu, m, 0);
+    __syncwarp();
+    return m;
+}
+
+// The certified all-row check of the polygon in buffer buf (FP64 vertices): every row at every
+// vertex in FP32 with a bound, close calls in FP64 from the exact pair; violated rows are cut in
+// (FP64) and the check repeats, at most kWMaxFix rounds.  Returns true when the cell must go to
+// the block kernel (a row within the band, a violated row that is already an edge, too many
+// violators or rounds, a cut that fails).
+__device__ bool wcheck(const MarchArgs &a, WarpSh &S, const WRows &rv, int N, int &m, int &buf, int &rounds,
+                       int &ncut, int &cell_close)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const int NC = N + kBoxPlanes;
+    bool fallback = false;
+    while (true) {
+        for (int i = lane; i < m; i += 32) {
+            const double *v = S.pv[buf][i];
+            S.vf[i][0] = (float)v[0]; S.vf[i][1] = (float)v[1]; S.vf[i][2] = (float)v[2];
+            S.vf[i][3] = (float)fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])))) * 1.0001f;
+        }
+        if (lane == 0) S.nviol = 0;
+        __syncwarp();
+        bool amb = false;
+        int close = 0;
+        for (int k0 = lane; k0 < NC; k0 += 32 * 4) {
+          float4 rr[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+              const int k = k0 + 32 * u;
+              rr[u] = k < N ? __ldg(rv.p + 2 * k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int k = k0 + 32 * u;
+            if (k >= NC) break;
+            const float4 r4 = rr[u];
+            const float r[4] = {r4.x, r4.y, r4.z, r4.w};
+            const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
+            const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
+            const float band = (float)a.delta * sqrtf(n2) * 1.01f;   // delta |r|: the oracle's tolerance band
+            bool viol = false;
+            for (int i = 0; i < m; ++i) {
+                const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
+                if (k == ea || k == eb) continue;
+                const float *v = S.vf[i];
+                const float sl = r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3];
+                const float mag = fabsf(r[0] * v[0]) + fabsf(r[1] * v[1]) + fabsf(r[2] * v[2]) + fabsf(r[3]);
+                const float B = __fmaf_ru(8.5f * kWU, mag, __fmaf_ru(rl1, S.dvb[i], band));
+                if (sl > B) { viol = true; continue; }
+                if (sl >= -B) {                        // close call: FP64 from the exact pair
+                    ++close;
+                    double r6[4];
+                    rv.f64(k, r6);
+                    const double *v6 = S.pv[buf][i];
+                    const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
+                    const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
+                    const double B6 = (double)rl1 * 1.0001 * (double)S.dvb[i] + (double)band + 1e-15 * m6;
+                    if (s6 > B6) viol = true;
+                    else if (s6 >= -B6) amb = true;    // within the band: the FP64 path counts it
+                }
+            }
+            if (viol) {
+                for (int i = 0; i < m; ++i) amb |= S.pe[buf][i] == k;   // a spurious FP32 cut
+                const int p = atomicAdd(&S.nviol, 1);
+                if (p < kWViol) S.viol[p] = k;
+                else amb = true;
+            }
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) close += __shfl_xor_sync(FULL, close, o);
+        cell_close += close;
+        if (__any_sync(FULL, amb)) { fallback = true; break; }
+        __syncwarp();
+        const int nviol = S.nviol;
+        if (nviol == 0) break;
+        if (rounds + 1 >= kWMaxFix) { fallback = true; break; }
+        for (int t = 0; t < nviol && m > 0; ++t) {
+            bool sw;
+            const int nm = wcut<double>(S, S.pv, m, buf, S.viol[t], 0.0, S.aF, rv, &sw);
+            if (nm < 0) { fallback = true; break; }
+            if (sw) buf ^= 1;
+            m = nm;
+        }
+        ncut += nviol;
+        if (fallback || m == 0) { fallback = true; break; }
+        if (!wfinal(S, m, buf, rv)) { fallback = true; break; }
+        ++rounds;
+    }
+    return fallback;
+}
+
+// a6 emit, a7 march for a solved cell: the face record (empty when it has fewer than 3 vertices,
+// a square edge, or no area), then one push per neuron edge; returns whether a face was written
+__device__ bool wemit(const MarchArgs &a, WarpSh &S, int64_t cell, int net_id, int N, int m, int buf)
+{
+    const int lane = threadIdx.x & 31;
+    const Arena &ar = a.ar;
+    int emit = m >= 3 ? m : 0;
+    for (int i = 0; i < m; ++i)
+        if (S.pe[buf][i] >= N + kBoxPlanes) emit = 0;     // a square edge: the plane misses the box
+    if (emit) {
+        const double *p0 = S.pv[buf][0];
+        double nx = 0.0, ny = 0.0, nz = 0.0;
+        for (int i = lane + 1; i < m - 1; i += 32) {
+            const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1];
+            const double ax = p[0] - p0[0], ay = p[1] - p0[1], az = p[2] - p0[2];
+            const double bx = q[0] - p0[0], by = q[1] - p0[1], bz = q[2] - p0[2];
+            nx += ay * bz - az * by; ny += az * bx - ax * bz; nz += ax * by - ay * bx;
+        }
+        nx = warp_sum(nx); ny = warp_sum(ny); nz = warp_sum(nz);
+        const double amin = 2e-24 * a.box * a.box;    // twice the smallest kept area
+        if (!(nx * nx + ny * ny + nz * nz > amin * amin)) emit = 0;
+    }
+    if (emit > ar.maxv) {
+        if (lane == 0) atomicOr(ar.counters + kStatus, kStFaceVerts);
+        emit = 0;
+    }
+    if (lane == 0) ar.nverts[cell] = emit;
+    if (emit) {
+        for (int i = lane; i < m; i += 32) {
+            ar.edges[cell * ar.maxv + i] = S.pe[buf][i];
+            double *v = ar.verts + (cell * ar.maxv + i) * 3;
+            v[0] = S.pv[buf][i][0]; v[1] = S.pv[buf][i][1]; v[2] = S.pv[buf][i][2];
+        }
+        const unsigned long long h = __ldcg(ar.hash + cell);
+        for (int i = 0; i < m; ++i) {
+            const int e = S.pe[buf][i];
+            if (e >= N) continue;
+            const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1 == m ? 0 : i + 1];
+            insert_neighbor_warp(ar, S.key, cell, net_id, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
+                                 (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])), false);
+        }
+    }
+    return emit != 0;
+}
+
 }  // namespace
 
 int clip_warp_smem_bytes() { return warp_smem_bytes(); }
@@ -204,60 +404,9 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
     for (int64_t cell = a.begin + (int64_t)blockIdx.x * kWW + (threadIdx.x >> 5); cell < a.end; cell += stride) {
         if (__ldcg(ar.nverts + cell) == -2) continue;          // a duplicate seed id: never solved
         const int net_id = __ldcg(ar.net + cell);
-        const NetDev &net = a.nets[net_id];
-        const int N = net.N, NC = N + kBoxPlanes;
+        const int N = a.nets[net_id].N;
         WRows rv;
-        rv.p = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * 2 * (int64_t)(N + 1);
-        rv.N = N;
-        rv.box = (float)a.box;
-        rv.S = &S;
-        for (int w = lane; w < ar.kw; w += 32) {
-            const unsigned long long x = __ldcg(ar.keys + cell * ar.kw + w);
-            S.key[2 * w] = (unsigned)x;
-            S.key[2 * w + 1] = (unsigned)(x >> 32);
-        }
-        if (lane < 4) {
-            const float h = reinterpret_cast<const float *>(rv.p + 2 * N)[lane];
-            const float l = reinterpret_cast<const float *>(rv.p + 2 * N + 1)[lane];
-            S.aF[lane] = (double)h + (double)l;
-            S.aFhi[lane] = h;
-        }
-        __syncwarp();
-        // ---- the face plane's frame (FP32) and the square about the box section (lane 0)
-        int m = 0;
-        if (lane == 0) {
-            const float F[4] = {(float)S.aF[0], (float)S.aF[1], (float)S.aF[2], (float)S.aF[3]};
-            const float nn = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
-            if (nn > 0.0f && isfinite(nn)) {
-                const float inn = 1.0f / nn;
-                const float p0[3] = {-F[3] * F[0] * inn, -F[3] * F[1] * inn, -F[3] * F[2] * inn};
-                const float inv = rsqrtf(nn);
-                const float n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
-                const float ax = fabsf(n[0]), ay = fabsf(n[1]), az = fabsf(n[2]);
-                const int ei = (ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2);
-                const float e0 = ei == 0 ? 1.0f : 0.0f, e1 = ei == 1 ? 1.0f : 0.0f, e2 = ei == 2 ? 1.0f : 0.0f;
-                float u[3] = {n[1] * e2 - n[2] * e1, n[2] * e0 - n[0] * e2, n[0] * e1 - n[1] * e0};
-                const float un = rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-                u[0] *= un; u[1] *= un; u[2] *= un;
-                const float w[3] = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
-                const float sz = 1.05f * 1.7320508f * (float)a.box;
-                const float d[4][3] = {{-w[0], -w[1], -w[2]}, {u[0], u[1], u[2]}, {w[0], w[1], w[2]}, {-u[0], -u[1], -u[2]}};
-                const float cu[4] = {-1.0f, 1.0f, 1.0f, -1.0f}, cw[4] = {-1.0f, -1.0f, 1.0f, 1.0f};
-                for (int i = 0; i < 4; ++i) {
-                    S.sq[i][0] = d[i][0]; S.sq[i][1] = d[i][1]; S.sq[i][2] = d[i][2];
-                    S.sq[i][3] = -(d[i][0] * p0[0] + d[i][1] * p0[1] + d[i][2] * p0[2]) - sz;
-                    for (int c = 0; c < 3; ++c) {
-                        const float x = p0[c] + sz * (cu[i] * u[c] + cw[i] * w[c]);
-                        S.pv[0][i][c] = (double)x;
-                        S.pf[0][i][c] = x;
-                    }
-                    S.pe[0][i] = N + kBoxPlanes + i;
-                }
-                m = 4;
-            }
-        }
-        m = __shfl_sync(FULL, m, 0);
-        __syncwarp();
+        int m = wcell_setup(a, S, cell, N, rv);
         bool fallback = m == 0;
         // ---- candidates: per lane the two best of the rows it scans
         const float px = __ldcg(ar.entry_pt + cell * 3), py = __ldcg(ar.entry_pt + cell * 3 + 1),
@@ -344,83 +493,24 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
         // an FP32 pass that emptied the polygon proves nothing: the FP64 fallback decides
         if (m == 0) fallback = true;
         if (!fallback) fallback = !wfinal(S, m, buf, rv);
+        if (!fallback && a.chk && m <= kChkMaxV) {
+            // the dense check runs on the tensor cores (check_tc); the finish pass emits the cell
+            unsigned long long p = 0;
+            if (lane == 0) p = atomicAdd(a.chk_count, 1ull);
+            p = __shfl_sync(FULL, p, 0);
+            CheckRec &R = a.chk[p];
+            if (lane == 0) { R.cell = (int32_t)cell; R.m = m; }
+            for (int i = lane; i < m; i += 32) {
+                R.pe[i] = S.pe[buf][i];
+                R.v[i][0] = S.pv[buf][i][0]; R.v[i][1] = S.pv[buf][i][1]; R.v[i][2] = S.pv[buf][i][2];
+            }
+            n_cuts += (unsigned long long)ncut;
+            __syncwarp();
+            continue;
+        }
         // ---- the all-row check, certified; violators are cut in (FP64) and the check repeats
         int rounds = 0, cell_close = 0;
-        while (!fallback) {
-            for (int i = lane; i < m; i += 32) {
-                const double *v = S.pv[buf][i];
-                S.vf[i][0] = (float)v[0]; S.vf[i][1] = (float)v[1]; S.vf[i][2] = (float)v[2];
-                S.vf[i][3] = (float)fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])))) * 1.0001f;
-            }
-            if (lane == 0) S.nviol = 0;
-            __syncwarp();
-            bool amb = false;
-            int close = 0;
-            for (int k0 = lane; k0 < NC; k0 += 32 * 4) {
-              float4 rr[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                  const int k = k0 + 32 * u;
-                  rr[u] = k < N ? __ldg(rv.p + 2 * k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-              }
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int k = k0 + 32 * u;
-                if (k >= NC) break;
-                const float4 r4 = rr[u];
-                const float r[4] = {r4.x, r4.y, r4.z, r4.w};
-                const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-                if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
-                const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
-                const float band = (float)a.delta * sqrtf(n2) * 1.01f;   // delta |r|: the oracle's tolerance band
-                bool viol = false;
-                for (int i = 0; i < m; ++i) {
-                    const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
-                    if (k == ea || k == eb) continue;
-                    const float *v = S.vf[i];
-                    const float sl = r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3];
-                    const float mag = fabsf(r[0] * v[0]) + fabsf(r[1] * v[1]) + fabsf(r[2] * v[2]) + fabsf(r[3]);
-                    const float B = __fmaf_ru(8.5f * kWU, mag, __fmaf_ru(rl1, S.dvb[i], band));
-                    if (sl > B) { viol = true; continue; }
-                    if (sl >= -B) {                        // close call: FP64 from the exact pair
-                        ++close;
-                        double r6[4];
-                        rv.f64(k, r6);
-                        const double *v6 = S.pv[buf][i];
-                        const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
-                        const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
-                        const double B6 = (double)rl1 * 1.0001 * (double)S.dvb[i] + (double)band + 1e-15 * m6;
-                        if (s6 > B6) viol = true;
-                        else if (s6 >= -B6) amb = true;    // within the band: the FP64 path counts it
-                    }
-                }
-                if (viol) {
-                    for (int i = 0; i < m; ++i) amb |= S.pe[buf][i] == k;   // a spurious FP32 cut
-                    const int p = atomicAdd(&S.nviol, 1);
-                    if (p < kWViol) S.viol[p] = k;
-                    else amb = true;
-                }
-              }
-            }
-            for (int o = 16; o > 0; o >>= 1) close += __shfl_xor_sync(FULL, close, o);
-            cell_close += close;
-            if (__any_sync(FULL, amb)) { fallback = true; break; }
-            __syncwarp();
-            const int nviol = S.nviol;
-            if (nviol == 0) break;
-            if (rounds + 1 >= kWMaxFix) { fallback = true; break; }
-            for (int t = 0; t < nviol && m > 0; ++t) {
-                bool sw;
-                const int nm = wcut<double>(S, S.pv, m, buf, S.viol[t], 0.0, S.aF, rv, &sw);
-                if (nm < 0) { fallback = true; break; }
-                if (sw) buf ^= 1;
-                m = nm;
-            }
-            ncut += nviol;
-            if (fallback || m == 0) { fallback = true; break; }
-            if (!wfinal(S, m, buf, rv)) { fallback = true; break; }
-            ++rounds;
-        }
+        if (!fallback) fallback = wcheck(a, S, rv, N, m, buf, rounds, ncut, cell_close);
         if (fallback) {
             // the block kernel solves this cell (double-float, then FP64 where needed)
             if (lane == 0) {
@@ -431,47 +521,77 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
             continue;
         }
         // ---- a6 emit, a7 march
-        int emit = m >= 3 ? m : 0;
-        for (int i = 0; i < m; ++i)
-            if (S.pe[buf][i] >= N + kBoxPlanes) emit = 0;     // a square edge: the plane misses the box
-        if (emit) {
-            const double *p0 = S.pv[buf][0];
-            double nx = 0.0, ny = 0.0, nz = 0.0;
-            for (int i = lane + 1; i < m - 1; i += 32) {
-                const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1];
-                const double ax = p[0] - p0[0], ay = p[1] - p0[1], az = p[2] - p0[2];
-                const double bx = q[0] - p0[0], by = q[1] - p0[1], bz = q[2] - p0[2];
-                nx += ay * bz - az * by; ny += az * bx - ax * bz; nz += ax * by - ay * bx;
-            }
-            nx = warp_sum(nx); ny = warp_sum(ny); nz = warp_sum(nz);
-            const double amin = 2e-24 * a.box * a.box;    // twice the smallest kept area
-            if (!(nx * nx + ny * ny + nz * nz > amin * amin)) emit = 0;
-        }
-        if (emit > ar.maxv) {
-            if (lane == 0) atomicOr(ar.counters + kStatus, kStFaceVerts);
-            emit = 0;
-        }
-        if (lane == 0) ar.nverts[cell] = emit;
+        const bool emitted = wemit(a, S, cell, net_id, N, m, buf);
         n_solved += 1;
-        if (!emit) n_empty += 1;
+        if (!emitted) n_empty += 1;
         if (rounds) n_fix += 1;
         n_cuts += (unsigned long long)ncut;
         n_close += (unsigned long long)cell_close;
-        if (emit) {
+        __syncwarp();
+    }
+    if (lane == 0) {
+        unsigned long long *C = ar.counters;
+        if (n_solved) atomicAdd(C + kSolved, n_solved);
+        if (n_empty) atomicAdd(C + kEmpty, n_empty);
+        if (n_fix) atomicAdd(C + kFixups, n_fix);
+        if (n_cuts) atomicAdd(C + kCuts, n_cuts);
+        if (n_close) atomicAdd(C + kCloseCalls, n_close);
+        if (n_fb) atomicAdd(C + kWarpFallback, n_fb);
+    }
+}
+
+// After check_tc: one warp per record.  A cell whose rows all hold is emitted and pushes its
+// neighbours; a cell with a violated or undecided row gets the warp's own check (violators cut in,
+// FP64 close calls), and what that cannot decide goes to the block kernel's list.
+__global__ void __launch_bounds__(kWW * 32) clip_warp_finish_kernel(MarchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char wsm[];
+    WarpSh &S = reinterpret_cast<WarpSh *>(wsm)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const Arena &ar = a.ar;
+    unsigned long long n_solved = 0, n_empty = 0, n_fix = 0, n_cuts = 0, n_close = 0, n_fb = 0;
+    const int64_t n = (int64_t)__ldcg(a.chk_count);
+    const int64_t stride = (int64_t)gridDim.x * kWW;
+    for (int64_t idx = (int64_t)blockIdx.x * kWW + (threadIdx.x >> 5); idx < n; idx += stride) {
+        const CheckRec &R = a.chk[idx];
+        const int64_t cell = R.cell;
+        int m = R.m, buf = 0, rounds = 0, ncut = 0, cell_close = 0;
+        const int net_id = __ldcg(ar.net + cell);
+        const int N = a.nets[net_id].N;
+        bool fallback = false;
+        if (a.chk_status[idx] == 0) {
+            wload_key(S, ar, cell);
+        } else {
+            WRows rv;
+            fallback = wcell_setup(a, S, cell, N, rv) == 0;   // key, a_F and the square's rows
             for (int i = lane; i < m; i += 32) {
-                ar.edges[cell * ar.maxv + i] = S.pe[buf][i];
-                double *v = ar.verts + (cell * ar.maxv + i) * 3;
-                v[0] = S.pv[buf][i][0]; v[1] = S.pv[buf][i][1]; v[2] = S.pv[buf][i][2];
+                S.pe[0][i] = R.pe[i];
             }
-            const unsigned long long h = __ldcg(ar.hash + cell);
-            for (int i = 0; i < m; ++i) {
-                const int e = S.pe[buf][i];
-                if (e >= N) continue;
-                const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1 == m ? 0 : i + 1];
-                insert_neighbor_warp(ar, S.key, cell, net_id, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
-                                     (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+            __syncwarp();
+            if (!fallback) fallback = !wfinal(S, m, 0, rv);     // the same FP64 vertices and their bounds
+            if (!fallback) fallback = wcheck(a, S, rv, N, m, buf, rounds, ncut, cell_close);
+        }
+        if (fallback) {
+            if (lane == 0) {
+                const unsigned long long p = atomicAdd(a.fb_count, 1ull);
+                a.fb_list[p] = (int32_t)cell;
+            }
+            n_fb += 1;
+            continue;
+        }
+        if (a.chk_status[idx] == 0) {
+            for (int i = lane; i < m; i += 32) {
+                S.pe[0][i] = R.pe[i];
+                S.pv[0][i][0] = R.v[i][0]; S.pv[0][i][1] = R.v[i][1]; S.pv[0][i][2] = R.v[i][2];
             }
         }
+        __syncwarp();
+        const bool emitted = wemit(a, S, cell, net_id, N, m, buf);
+        n_solved += 1;
+        if (!emitted) n_empty += 1;
+        if (rounds) n_fix += 1;
+        n_cuts += (unsigned long long)ncut;
+        n_close += (unsigned long long)cell_close;
         __syncwarp();
     }
     if (lane == 0) {
@@ -487,7 +607,9 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
 
 cudaError_t prepare_clip_warp()
 {
-    return cudaFuncSetAttribute(clip_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(clip_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(clip_warp_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
 }
 
 void launch_clip_warp(const MarchArgs &a, cudaStream_t st)
@@ -495,6 +617,13 @@ void launch_clip_warp(const MarchArgs &a, cudaStream_t st)
     const int64_t n = a.end - a.begin;
     const int grid = (int)std::min<int64_t>((n + kWW - 1) / kWW, 152 * 64);
     clip_warp_kernel<<<grid, kWW * 32, warp_smem_bytes(), st>>>(a);
+}
+
+void launch_clip_warp_finish(const MarchArgs &a, cudaStream_t st)
+{
+    const int64_t n = a.end - a.begin;                 // the records are at most the cells
+    const int grid = (int)std::min<int64_t>((n + kWW - 1) / kWW, 152 * 16);
+    clip_warp_finish_kernel<<<grid, kWW * 32, warp_smem_bytes(), st>>>(a);
 }
 
 }  // namespace am

@@ -76,6 +76,11 @@ struct NetDev {
     unsigned long long salt;     // per-net hash salt
     int df_ok;                   // 1: the double-float bound stays useful through this net's depth
     double slope;                // hidden activation a (a > 0), slope a (a <= 0); 0 = ReLU
+    // residual shortcuts from hidden layers (Sec. 5.1): layer l adds S_l h_{sc_src[l]} (sc_src 0 =
+    // none; a shortcut from x is folded into Cl); sc_S[l] = S_l (n_l x n_src) or null = identity
+    int sc_src[kMaxLayers + 1];
+    const double *sc_S[kMaxLayers + 1];
+    int fp64_only;               // 1: composes in FP64 only (leaky activation or a hidden shortcut)
 };
 
 // Device arenas (all sized at context creation).

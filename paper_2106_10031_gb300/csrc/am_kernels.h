@@ -24,6 +24,7 @@ struct ProposalView {
     int n_in, hidden, n_out;
 };
 
+struct CheckRec;
 struct MarchArgs {
     const NetDev *nets;
     Arena ar;
@@ -43,11 +44,47 @@ struct MarchArgs {
     const unsigned long long *list_count;   // [begin, end)) instead of the whole range
     int32_t *fb_list;                 // warp clip: cells it hands to the block kernel, and their count
     unsigned long long *fb_count;
+    CheckRec *chk;                    // warp clip with the dense check on the tensor cores: the clipped
+    unsigned long long *chk_count;    // polygons it hands to check_tc (null: the warp checks them itself)
+    const int *chk_status;            // finish pass: per record 0 = every row holds, else the block kernel
+};
+// A polygon the warp clip hands to the dense check (am_check_tc.cu): the cell, its m <= kChkMaxV
+// vertices (FP64) and the plane of each edge (edge i: vertex i -> i + 1).
+constexpr int kChkMaxV = 16;
+struct CheckRec {
+    int32_t cell, m;
+    int32_t pe[kChkMaxV];
+    double v[kChkMaxV][3];
 };
 // the sliced level march's clip, one warp per cell (am_clip_warp.cu): cells [begin, end), rows in
-// rows_in; cells it cannot decide are appended to fb_list for march_range_kernel (list mode)
+// rows_in; cells it cannot decide are appended to fb_list for march_range_kernel (list mode).
+// With a.chk set, polygons of at most kChkMaxV vertices are not checked here but appended to
+// a.chk; after check_tc, launch_clip_warp_finish emits and pushes the records whose status is 0
+// and hands the others to fb_list.
 cudaError_t prepare_clip_warp();
 void launch_clip_warp(const MarchArgs &a, cudaStream_t st);
+void launch_clip_warp_finish(const MarchArgs &a, cudaStream_t st);
+// The dense all-constraint check on the tcgen05 tensor cores: for every record, every neuron row
+// of its cell (FP32 pairs in rows, cell c at rows + (c - begin) 8 (N + 1) floats) at every vertex,
+// as the products [rows x K] . [K x 3 m] of BF16 parts (K: the row's hi word split into three
+// BF16 parts per coordinate; columns: the vertex's FP32 coordinates split likewise), FP32
+// accumulators in TMEM, then a certified sign test per (row, vertex) with FP64 close calls on
+// the exact pair; the 6 box rows on the ALU.  status[i] = 0 when every row holds at every vertex,
+// 1 when a row is violated or within the tolerance band (the block kernel then solves the cell).
+struct CheckArgs {
+    const CheckRec *rec;
+    const unsigned long long *count;  // records (read on the device)
+    const float *rows;
+    int64_t begin;
+    int N;
+    float box;
+    double delta;
+    int *status;
+    unsigned long long *counters;     // close calls are added to counters[kCloseCalls]
+    int *err;                         // set to 1 when a pipeline wait timed out
+};
+cudaError_t prepare_check_tc();
+void launch_check_tc(const CheckArgs &a, int sms, cudaStream_t st);
 int march_smem_bytes(int max_n, int max_w);
 int proposal_max_hidden();      // widest proposal hidden layer the march can evaluate
 cudaError_t prepare_march_kernels(int max_n, int max_w, int *blocks_per_sm);
@@ -232,6 +269,8 @@ struct OzScratch {
     int *err = nullptr;           // set to 1 by a kernel whose pipeline wait timed out
     int64_t batch_cells = 0;      // multiple of 16
     int64_t *issued = nullptr;    // host counter: BF16 multiply-adds issued on the tensor cores
+    int64_t *dirty = nullptr;     // host: P and Q may be non-zero in their first *dirty elements (a split-K
+                                  // product needs zeros; the prep of a split product zeroes what it reads)
 };
 int oz_kp(int width);             // K padded to the 64-element staging chunk
 int oz_mp(int width);             // rows padded to the 128-row tile

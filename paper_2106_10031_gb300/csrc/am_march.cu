@@ -373,6 +373,28 @@ __device__ __noinline__ void compose_tc_layers(const NetDev &net, const Sh &s, i
 // ------------------------------------------------------------------------------------------
 // a2/a3: compose the rows of every neuron of the cell, and a_F
 
+// The residual shortcut of layer l (Sec. 5.1) for its row k, FP64: a += sum_j S_kj H_src[j] with
+// H_src = diag(g) Z_src (g = 1 on active units, the slope on the others) and the stored row
+// (1 - 2 s) Z, so H_src[j] = -row_j when unit j is active and slope * row_j otherwise; S = null
+// is the identity (H_src[k]).
+__device__ __forceinline__ void add_shortcut(const NetDev &net, const Sh &s, int l, int k, double &a0, double &a1,
+                                             double &a2, double &a3)
+{
+    const int src = net.sc_src[l];
+    if (src <= 0) return;
+    const int rs = net.row0[src], ns = net.width[src];
+    const double *S = net.sc_S[l];
+    const int j0 = S ? 0 : k, j1 = S ? ns : k + 1;
+    for (int j = j0; j < j1; ++j) {
+        const double w = S ? __ldg(S + (size_t)k * ns + j) : 1.0;
+        const int r = rs + j;
+        const double f = w * (bit_of(s.mask, r) ? -1.0 : net.slope);
+        if (f == 0.0) continue;
+        const double *z = s.r64 + 4 * r;
+        a0 += f * z[0]; a1 += f * z[1]; a2 += f * z[2]; a3 += f * z[3];
+    }
+}
+
 template <int M>
 __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc, int nrows)
 {
@@ -454,6 +476,7 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
                     }
                 }
                 if (S == 1) {
+                    add_shortcut(net, s, l, k, a0, a1, a2, a3);
                     const double sg = bit_of(s.mask, rl + k) ? -1.0 : 1.0;
                     const double *C = net.Cl[l] + 4 * k;
                     double *r = s.r64 + 4 * (rl + k);
@@ -503,6 +526,7 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
                         const double *p = s.partd + 4 * (sp * nl + k);
                         a0 += p[0]; a1 += p[1]; a2 += p[2]; a3 += p[3];
                     }
+                    add_shortcut(net, s, l, k, a0, a1, a2, a3);
                     const double sg = bit_of(s.mask, rl + k) ? -1.0 : 1.0;
                     double *r = s.r64 + 4 * (rl + k);
                     r[0] = sg * a0; r[1] = sg * a1; r[2] = sg * a2; r[3] = sg * a3;

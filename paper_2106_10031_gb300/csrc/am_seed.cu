@@ -15,35 +15,43 @@ constexpr int kSeedThreads = 256;
 
 __host__ __device__ inline int seed_smem_bytes(int max_n, int max_w)
 {
+    (void)max_w;
     const int words = (max_n + 31) / 32;
-    return 2 * max_w * (int)sizeof(double) + 3 * words * (int)sizeof(unsigned) + 16 + 64 * (int)sizeof(double);
+    return max_n * (int)sizeof(double) + 3 * words * (int)sizeof(unsigned) + 16 + 64 * (int)sizeof(double);
 }
 
-// Forward pass at x: F (returned to every thread) and the pattern bits in `bits`.
-__device__ double seed_forward(const NetDev &net, const double *x, double *h0, double *h1, unsigned *bits,
-                               double *red)
+// Forward pass at x: F (returned to every thread) and the pattern bits in `bits`.  H holds every
+// hidden layer's output (N values, layer l at row0[l]), which the residual shortcuts read.
+__device__ double seed_forward(const NetDev &net, const double *x, double *H, unsigned *bits, double *red)
 {
     const int tid = threadIdx.x, T = blockDim.x;
     for (int w = tid; w < (net.N + 31) / 32; w += T) bits[w] = 0u;
     __syncthreads();
-    double *hp = h0, *hn = h1;
     for (int l = 1; l <= net.L; ++l) {
         const int nl = net.width[l], np = l > 1 ? net.width[l - 1] : 0, rl = net.row0[l];
         const double *Cl = net.Cl[l], *AT = net.AT[l];
+        const double *hp = l > 1 ? H + net.row0[l - 1] : nullptr;
+        const int src = net.sc_src[l];
+        const double *hs = src > 0 ? H + net.row0[src] : nullptr, *S = net.sc_S[l];
+        const int ns = src > 0 ? net.width[src] : 0;
         for (int k = tid; k < nl; k += T) {
             double a = Cl[k * 4 + 0] * x[0] + Cl[k * 4 + 1] * x[1] + Cl[k * 4 + 2] * x[2] + Cl[k * 4 + 3];
             for (int j = 0; j < np; ++j) {
                 const double hj = hp[j];
                 if (hj != 0.0) a += AT[(size_t)j * nl + k] * hj;
             }
-            hn[k] = a > 0.0 ? a : net.slope * a;             // ReLU, or leaky with slope != 0
+            if (hs) {                                          // the residual shortcut S_l h_src
+                if (S) for (int j = 0; j < ns; ++j) a += S[(size_t)k * ns + j] * hs[j];
+                else a += hs[k];
+            }
+            H[rl + k] = a > 0.0 ? a : net.slope * a;         // ReLU, or leaky with slope != 0
             if (a > 0.0) atomicOr(bits + ((rl + k) >> 5), 1u << ((rl + k) & 31));
         }
         __syncthreads();
-        double *t = hp; hp = hn; hn = t;
     }
     double f = 0.0;
-    for (int k = tid; k < net.width[net.L]; k += T) f += net.w_out[k] * hp[k];
+    const double *hL = H + net.row0[net.L];
+    for (int k = tid; k < net.width[net.L]; k += T) f += net.w_out[k] * hL[k];
     f = warp_sum(f);
     if ((tid & 31) == 0) red[tid >> 5] = f;
     __syncthreads();
@@ -58,8 +66,8 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(SeedArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const NetDev &net = a.nets[a.net];
     const int words = (net.N + 31) / 32;
-    double *h0 = (double *)smem, *h1 = h0 + a.max_w;
-    unsigned *blo = (unsigned *)(h1 + a.max_w), *bhi = blo + (a.max_n + 31) / 32, *bm = bhi + (a.max_n + 31) / 32;
+    double *H = (double *)smem;
+    unsigned *blo = (unsigned *)(H + a.max_n), *bhi = blo + (a.max_n + 31) / 32, *bm = bhi + (a.max_n + 31) / 32;
     double *red = (double *)(((uintptr_t)(bm + (a.max_n + 31) / 32) + 15) & ~(uintptr_t)15);
     const int ray = blockIdx.x, tid = threadIdx.x;
     const double o[3] = {a.origins[ray * 3], a.origins[ray * 3 + 1], a.origins[ray * 3 + 2]};
@@ -68,9 +76,9 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(SeedArgs a)
 
     double tlo = 0.0, thi = a.R;
     for (int c = 0; c < 3; ++c) x[c] = o[c];
-    double flo = seed_forward(net, x, h0, h1, blo, red);
+    double flo = seed_forward(net, x, H, blo, red);
     for (int c = 0; c < 3; ++c) x[c] = o[c] + a.R * d[c];
-    double fhi = seed_forward(net, x, h0, h1, bhi, red);
+    double fhi = seed_forward(net, x, H, bhi, red);
     int rc = 1;
     if (!((flo < 0.0 && fhi > 0.0) || (flo > 0.0 && fhi < 0.0))) rc = -4;
     int it = 0;
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(kSeedThreads) seed_kernel(SeedArgs a)
         if (it >= a.max_halvings) { rc = -5; break; }
         const double tm = 0.5 * (tlo + thi);
         for (int c = 0; c < 3; ++c) x[c] = o[c] + tm * d[c];
-        const double fm = seed_forward(net, x, h0, h1, bm, red);
+        const double fm = seed_forward(net, x, H, bm, red);
         if ((fm < 0.0) == (flo < 0.0) && fm != 0.0) {
             tlo = tm; flo = fm;
             for (int w = tid; w < words; w += blockDim.x) blo[w] = bm[w];
@@ -159,44 +167,52 @@ __global__ void seed_insert_kernel(SeedArgs a)
 
 // ---- customised triggers (Sec. 4.3)
 
-// grad F at the point whose pattern the last seed_forward left in `bits`: backpropagation
-// through the units, delta_l = dF/da_l = g'_l (AT_{l+1} delta_{l+1}), delta_L = g'_L w_out with
-// g' = 1 on active units and the slope (0 for a ReLU) on the others,
-// and grad F = sum_l Cl_l[:, 0:3]^T delta_l (only the layers fed by x have non-zero columns).
-// d0, d1: two max_w scratch rows; red: 64 doubles.  Every thread returns the same g.
-__device__ void seed_grad(const NetDev &net, const unsigned *bits, double *d0, double *d1, double *red, double g[3])
+// grad F at the point whose pattern the last seed_forward left in `bits`, by backpropagation
+// through the units: E[r] = dF/dh_r accumulates from every layer that reads unit r (the next
+// layer through W_{l+1}^T, and a residual shortcut through S_q^T), then D_r = g'(a_r) E[r] = dF/da_r
+// with g' = 1 on active units and the slope (0 for a ReLU) on the others, and
+// grad F = sum_l Cl_l[:, 0:3]^T D_l (the layers fed by x, shortcuts from x included).
+// E: N doubles (overwrites the forward pass's H); red: 64 doubles.  Every thread returns g.
+__device__ void seed_grad(const NetDev &net, const unsigned *bits, double *E, double *red, double g[3])
 {
     const int tid = threadIdx.x, T = blockDim.x;
     double gx = 0.0, gy = 0.0, gz = 0.0;
-    double *dc = d0, *dn = d1;
-    {
-        const int nL = net.width[net.L], r0 = net.row0[net.L];
-        for (int k = tid; k < nL; k += T)
-            dc[k] = (bits[(r0 + k) >> 5] >> ((r0 + k) & 31)) & 1u ? net.w_out[k] : net.slope * net.w_out[k];
-    }
+    const int rL = net.row0[net.L];
+    for (int r = tid; r < net.N; r += T) E[r] = r >= rL ? net.w_out[r - rL] : 0.0;
     __syncthreads();
     for (int l = net.L; l >= 1; --l) {
-        const int nl = net.width[l];
+        const int nl = net.width[l], rl = net.row0[l];
         const double *Cl = net.Cl[l];
         for (int k = tid; k < nl; k += T) {
-            const double dk = dc[k];
+            const double gp = (bits[(rl + k) >> 5] >> ((rl + k) & 31)) & 1u ? 1.0 : net.slope;
+            const double dk = gp * E[rl + k];
+            E[rl + k] = dk;
             gx += Cl[k * 4 + 0] * dk;
             gy += Cl[k * 4 + 1] * dk;
             gz += Cl[k * 4 + 2] * dk;
         }
+        __syncthreads();
         if (l > 1) {
             const int np = net.width[l - 1], rp = net.row0[l - 1];
             const double *AT = net.AT[l];
             for (int j = tid; j < np; j += T) {
-                // dF/da_j = g'(a_j) sum_k W_kj dF/da_k with g' = 1 (active) or the slope
-                const double gp = (bits[(rp + j) >> 5] >> ((rp + j) & 31)) & 1u ? 1.0 : net.slope;
                 double acc = 0.0;
-                if (gp != 0.0)
-                    for (int k = 0; k < nl; ++k) acc += AT[(size_t)j * nl + k] * dc[k];
-                dn[j] = gp * acc;
+                for (int k = 0; k < nl; ++k) acc += AT[(size_t)j * nl + k] * E[rl + k];
+                E[rp + j] += acc;
             }
             __syncthreads();
-            double *t = dc; dc = dn; dn = t;
+        }
+        const int src = net.sc_src[l];
+        if (src > 0) {
+            const int ns = net.width[src], rs = net.row0[src];
+            const double *S = net.sc_S[l];
+            for (int j = tid; j < ns; j += T) {
+                double acc = 0.0;
+                if (S) for (int k = 0; k < nl; ++k) acc += S[(size_t)k * ns + j] * E[rl + k];
+                else acc = E[rl + j];
+                E[rs + j] += acc;
+            }
+            __syncthreads();
         }
     }
     gx = warp_sum(gx); gy = warp_sum(gy); gz = warp_sum(gz);
@@ -216,16 +232,16 @@ __global__ void __launch_bounds__(kSeedThreads) trace_kernel(TraceArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const NetDev &net = a.nets[a.net];
-    double *h0 = (double *)smem, *h1 = h0 + a.max_w;
-    unsigned *bits = (unsigned *)(h1 + a.max_w);
+    double *H = (double *)smem;
+    unsigned *bits = (unsigned *)(H + a.max_n);
     double *red = (double *)(((uintptr_t)(bits + 3 * ((a.max_n + 31) / 32)) + 15) & ~(uintptr_t)15);
     const int i = blockIdx.x, tid = threadIdx.x;
     double x[3] = {a.starts[i * 3], a.starts[i * 3 + 1], a.starts[i * 3 + 2]};
     double F = 0.0, g[3] = {0.0, 0.0, 0.0};
     bool flat = false;
     for (int t = 0;; ++t) {
-        F = seed_forward(net, x, h0, h1, bits, red);
-        seed_grad(net, bits, h0, h1, red, g);
+        F = seed_forward(net, x, H, bits, red);
+        seed_grad(net, bits, H, red, g);
         if (fabs(F) <= a.eps || t >= a.max_steps) break;
         if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) { flat = true; break; }
         for (int c = 0; c < 3; ++c) x[c] = x[c] - a.eta * F * g[c];
@@ -250,12 +266,12 @@ __global__ void __launch_bounds__(kSeedThreads) sample_eval_kernel(PairArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const NetDev &net = a.nets[a.net];
-    double *h0 = (double *)smem, *h1 = h0 + a.max_w;
-    unsigned *bits = (unsigned *)(h1 + a.max_w);
+    double *H = (double *)smem;
+    unsigned *bits = (unsigned *)(H + a.max_n);
     double *red = (double *)(((uintptr_t)(bits + 3 * ((a.max_n + 31) / 32)) + 15) & ~(uintptr_t)15);
     const int i = blockIdx.x;
     const double x[3] = {a.points[i * 3], a.points[i * 3 + 1], a.points[i * 3 + 2]};
-    const double F = seed_forward(net, x, h0, h1, bits, red);
+    const double F = seed_forward(net, x, H, bits, red);
     if (threadIdx.x == 0) a.F[i] = F;
 }
 

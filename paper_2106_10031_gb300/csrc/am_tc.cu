@@ -130,7 +130,8 @@ struct OzPrep {
     int l, L, N;
     int nl, row0;                     // width and first neuron of layer l
     long long *P, *Q;                 // l >= 2: the exact products of layer l (diagonals 0..6, and the raw
-                                      // sum of diagonal 7), column c at P + c Mp; zeroed once read
+                                      // sum of diagonal 7), column c at P + c Mp; zeroed once read when
+    int zero;                         // zero is set (the product added split-K partial sums into them)
     int Mp;
     const int *eA;                    // l >= 2: row exponents of W_l
     const int *eBin;                  // l >= 2: column exponents of layer l's right operand
@@ -214,8 +215,10 @@ __device__ __forceinline__ long long oz_product(const OzPrep &p, int64_t i, int 
 {
     const int64_t o = (4 * i + j) * p.Mp + k;
     const long long v = p.P[o] + ((p.Q[o] + 32) >> 6);
-    p.P[o] = 0;                                   // consumed: zero for the next product's split-K sums
-    p.Q[o] = 0;
+    if (p.zero) {                                 // consumed: zero for the next product's split-K sums
+        p.P[o] = 0;
+        p.Q[o] = 0;
+    }
     return v;
 }
 
@@ -447,7 +450,8 @@ struct R1Prep {
     int j, L, N, nj, row0j;
     const double *ATj;                // W_j transposed (n_{j-1} x n_j)
     const int *eA;                    // row exponents of W_j
-    long long *P, *Q;                 // the products of layer j (items with flip layer <= j - 2), zeroed once read
+    long long *P, *Q;                 // the products of layer j (items with flip layer <= j - 2), zeroed
+    int zero;                         // once read when zero is set (a split-K product)
     int Mp;
     const int *eBin;                  // column exponents of layer j's operand
     int *eBout;                       // column exponents of layer j + 1's operand
@@ -485,8 +489,10 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         } else {
             const int64_t o = i * a.Mp + m;
             x = i64_ldexp(a.P[o] + ((a.Q[o] + 32) >> 6), a.eA[m] + a.eBin[i] - 48);
-            a.P[o] = 0;                               // consumed: zero for the next product's split-K sums
-            a.Q[o] = 0;
+            if (a.zero) {                             // consumed: zero for the next product's split-K sums
+                a.P[o] = 0;
+                a.Q[o] = 0;
+            }
         }
         const int r = a.row0j + m;
         const bool act = key_bit(key, r);
@@ -1149,9 +1155,11 @@ int64_t oz_scratch_elems(int64_t batch_cells, int max_kp)
 // exact products P, Q.  The tile shape: tile_cells, or (0) the 32-cell tile when K has at least 8
 // chunks (its two passes' fixed costs amortise) and its tiles, split over up to 4 K ranges, fill
 // every SM, else the 16-cell tile, which makes twice as many.  A product too small to fill the
-// SMs splits K over more CTAs (exact integer sums).
+// SMs splits K over more CTAs (exact integer sums) that add into P and Q, which must then be zero:
+// *split_out tells the caller's prep to zero what it reads, and a product that writes without
+// splitting leaves P and Q dirty (a memset then precedes the next split product).
 static cudaError_t oz_layer_product(const OzNet &net, int l, const OzScratch &scr, int64_t ncols_used, int tile_cells,
-                                    int sms, cudaStream_t st)
+                                    int sms, cudaStream_t st, int *split_out)
 {
     const int64_t ncols = 4 * scr.batch_cells;
     const int Mp = oz_mp(net.width[l]);
@@ -1174,9 +1182,18 @@ static cudaError_t oz_layer_product(const OzNet &net, int l, const OzScratch &sc
     g.ncols_used = ncols_used;
     const int64_t tiles = (int64_t)(g.Mp / kOzM) * ((4 * nb + 4 * tc - 1) / (4 * tc));
     int split = (int)std::min<int64_t>(std::min<int64_t>(g.KC, 4), std::max<int64_t>(1, (int64_t)sms * per_sm / tiles));
-    // split-K partial sums add into P and Q, which are zero: the kernel that reads a product
-    // (the prep) zeroes it, so no memset is needed between layers
     g.split = split > 1 ? 1 : 0;
+    *split_out = g.split;
+    if (g.split) {
+        if (scr.dirty && *scr.dirty > 0) {
+            e = cudaMemsetAsync(scr.P, 0, sizeof(long long) * *scr.dirty, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(scr.Q, 0, sizeof(long long) * *scr.dirty, st);
+            if (e != cudaSuccess) return e;
+            *scr.dirty = 0;
+        }
+    } else if (scr.dirty) {
+        *scr.dirty = std::max<int64_t>(*scr.dirty, ncols_used * (int64_t)g.Mp);
+    }
     const CUtensorMap &tmA = *reinterpret_cast<const CUtensorMap *>(net.mapA[l]);
     // 36 digit-plane products per layer over the padded tiles of the columns in use
     if (scr.issued) *scr.issued += (int64_t)36 * (4 * nb) * Mp * Kp;
@@ -1214,8 +1231,9 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
         for (int l = 1; l <= net.L; ++l) {
             p.eBin = scr.eB[l & 1];                    // written by the prep of layer l - 1
             p.eBout = scr.eB[(l + 1) & 1];
+            p.zero = 0;
             if (l >= 2) {
-                cudaError_t e = oz_layer_product(net, l, scr, 4 * nb, tile_cells, sms, st);
+                cudaError_t e = oz_layer_product(net, l, scr, 4 * nb, tile_cells, sms, st, &p.zero);
                 if (e != cudaSuccess) return e;
                 p.Mp = oz_mp(net.width[l]);
                 p.eA = net.eA[l];
@@ -1332,8 +1350,9 @@ cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list
         if (e != cudaSuccess) return e;
         for (int j = 2; j <= net.L; ++j) {
             const int64_t g = le(j - 2), pc = le(j - 1);
+            int zero = 0;
             if (g > 0) {
-                e = oz_layer_product(net, j, scr, g, tile_cells, sms, st);
+                e = oz_layer_product(net, j, scr, g, tile_cells, sms, st, &zero);
                 if (e != cudaSuccess) return e;
             }
             if (pc == 0) continue;
@@ -1353,6 +1372,7 @@ cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list
             pp.eA = net.eA[j];
             pp.P = scr.P;
             pp.Q = scr.Q;
+            pp.zero = zero;
             pp.Mp = oz_mp(net.width[j]);
             pp.eBin = scr.eB[j & 1];
             pp.eBout = scr.eB[(j + 1) & 1];

@@ -183,9 +183,32 @@ class Mesher:
                                  f"({w.shape[0]},)")
         if w_out.shape != (Ws[-1].shape[0],):
             raise ValueError(f"w_out {w_out.shape}; expected ({Ws[-1].shape[0]},)")
+        # residual shortcuts {l: (src, S or None)}: S is n_l x n_src (n_src = 3 for x)
+        sc = dict(getattr(mlp, "shortcuts", None) or {})
+        src_arr, S_ptrs, S_keep = None, None, []
+        if sc:
+            src = [-1] * L
+            S_ptrs = (C.POINTER(C.c_double) * L)()
+            for l, (s0, S) in sc.items():
+                l, s0 = int(l), int(s0)
+                if not (1 <= l <= L and 0 <= s0 < l):
+                    raise ValueError(f"shortcut into layer {l} from {s0}: the source must be an earlier layer")
+                n_l, n_s = Ws[l - 1].shape[0], 3 if s0 == 0 else Ws[s0 - 1].shape[0]
+                src[l - 1] = s0
+                if S is None:
+                    if n_s != n_l:
+                        raise ValueError(f"identity shortcut into layer {l}: {n_s} source units, {n_l} units")
+                else:
+                    S = np.ascontiguousarray(S, dtype=np.float64)
+                    if S.shape != (n_l, n_s):
+                        raise ValueError(f"shortcut into layer {l}: S {S.shape}; expected ({n_l}, {n_s})")
+                    S_keep.append(S)
+                    S_ptrs[l - 1] = _dp(S)
+            src_arr = (C.c_int * L)(*src)
         d = nt.am_mlp_desc(latent_dim=0 if z is None else len(z), latent=None if z is None else _dp(z),
                            n_hidden=L, width=width, W=Wp, b=bp, skip_layer=int(mlp.skip_layer),
-                           w_out=_dp(w_out), b_out=float(mlp.b_out), slope=float(getattr(mlp, "slope", 0.0)))
+                           w_out=_dp(w_out), b_out=float(mlp.b_out), slope=float(getattr(mlp, "slope", 0.0)),
+                           shortcut_src=src_arr, shortcut_S=S_ptrs)
         nid = C.c_int(-1)
         self._check(self.lib.am_load_mlp(self.ctx, C.byref(d), C.byref(nid)))
         self.nets.append(mlp)
@@ -253,12 +276,13 @@ class Mesher:
 
     # ---- launch shapes
     def set_tuning(self, compose_tile_cells: int | None = None, rank1_period: int | None = None,
-                   clip_kernel: int | None = None):
+                   clip_kernel: int | None = None, check_kernel: int | None = None):
         """Launch shapes of the sliced path; None keeps the current value."""
         cur = self.get_tuning()
         pick = lambda v, k: cur[k] if v is None else v  # noqa: E731
         t = nt.am_tuning(compose_tile_cells=pick(compose_tile_cells, "compose_tile_cells"),
-                         rank1_period=pick(rank1_period, "rank1_period"), clip_kernel=pick(clip_kernel, "clip_kernel"))
+                         rank1_period=pick(rank1_period, "rank1_period"), clip_kernel=pick(clip_kernel, "clip_kernel"),
+                         check_kernel=pick(check_kernel, "check_kernel"))
         self._check(self.lib.am_set_tuning(self.ctx, C.byref(t)))
 
     def get_tuning(self) -> dict:

@@ -47,7 +47,8 @@ class am_mlp_desc(C.Structure):
     _fields_ = [("latent_dim", C.c_int), ("latent", C.POINTER(C.c_double)), ("n_hidden", C.c_int),
                 ("width", C.POINTER(C.c_int)), ("W", C.POINTER(C.POINTER(C.c_double))),
                 ("b", C.POINTER(C.POINTER(C.c_double))), ("skip_layer", C.c_int),
-                ("w_out", C.POINTER(C.c_double)), ("b_out", C.c_double), ("slope", C.c_double)]
+                ("w_out", C.POINTER(C.c_double)), ("b_out", C.c_double), ("slope", C.c_double),
+                ("shortcut_src", C.POINTER(C.c_int)), ("shortcut_S", C.POINTER(C.POINTER(C.c_double)))]
 
 
 class am_march_opts(C.Structure):
@@ -57,7 +58,8 @@ class am_march_opts(C.Structure):
 
 
 class am_tuning(C.Structure):
-    _fields_ = [("compose_tile_cells", C.c_int), ("rank1_period", C.c_int), ("clip_kernel", C.c_int)]
+    _fields_ = [("compose_tile_cells", C.c_int), ("rank1_period", C.c_int), ("clip_kernel", C.c_int),
+                ("check_kernel", C.c_int)]
 
 
 class am_tune_point(C.Structure):

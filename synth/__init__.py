@@ -18,6 +18,8 @@ from .nets import (  # noqa: F401
     proposal_train_nets,
     tiny_net,
     leaky,
+    residual_net,
+    pooled_net,
     seed_rays,
     trigger_points,
 )

@@ -28,6 +28,8 @@ class MLP:
     name: str = ""
     meta: dict = field(default_factory=dict)
     slope: float = 0.0       # hidden activation a (a > 0), slope * a otherwise: 0 = ReLU, else leaky
+    shortcuts: dict = field(default_factory=dict)   # residual blocks {l: (src, S or None = identity)}
+    heads: list = field(default_factory=list)        # max pooling: [(w_i, b_i)], F = max_i w_i . h_L + b_i
 
     @property
     def widths(self) -> list:
@@ -64,6 +66,16 @@ class MLP:
             assert W.shape == (self.widths[l - 1], self.fan_in(l)), (l, W.shape)
             assert b.shape == (self.widths[l - 1],)
         assert self.w_out.shape == (self.widths[-1],)
+        for w, b in self.heads:
+            assert w.shape == (self.widths[-1],) and np.isscalar(b)
+        assert len(self.heads) != 1
+        for l, (src, S) in self.shortcuts.items():
+            assert 1 <= l <= self.L and 0 <= src < l, (l, src)
+            n_s = 3 if src == 0 else self.widths[src - 1]
+            if S is None:
+                assert n_s == self.widths[l - 1], (l, src)
+            else:
+                assert S.shape == (self.widths[l - 1], n_s), (l, S.shape)
 
 
 # --------------------------------------------------------------------------------------------
@@ -140,13 +152,17 @@ def polytope_max_of_planes(seed: int = 1, offset: float = 0.5, C: float = 10.0) 
 
 
 def _value_at_origin(m: MLP) -> float:
-    """F(0) of the network (plain numpy evaluation of Eq. 1)."""
+    """F(0) of the network (plain numpy evaluation of Eq. 1, with its shortcuts and slope)."""
     u0 = np.zeros(3) if m.latent is None else np.concatenate([np.zeros(3), m.latent])
-    h = None
+    hs = [np.zeros(3)]
     for l, (W, b) in enumerate(zip(m.weights, m.biases), start=1):
-        inp = u0 if l == 1 else (np.concatenate([h, u0]) if l == m.skip_layer else h)
-        h = np.maximum(W @ inp + b, 0.0)
-    return float(m.w_out @ h + m.b_out)
+        inp = u0 if l == 1 else (np.concatenate([hs[-1], u0]) if l == m.skip_layer else hs[-1])
+        a = W @ inp + b
+        if l in m.shortcuts:
+            src, S = m.shortcuts[l]
+            a = a + (hs[src] if S is None else S @ hs[src])
+        hs.append(np.where(a > 0.0, a, m.slope * a))
+    return float(m.w_out @ hs[-1] + m.b_out)
 
 
 def geometric_init(widths, seed: int, sigma: float, radius: float = 0.6,
@@ -189,6 +205,66 @@ def geometric_init(widths, seed: int, sigma: float, radius: float = 0.6,
             meta={"seed": seed, "sigma": sigma, "radius": radius, "recentered": recenter})
     if recenter:
         m.b_out = float(m.b_out - (_value_at_origin(m) + radius))
+    m.validate()
+    return m
+
+
+def residual_net(seed: int = 31, width: int = 24, depth: int = 5, sigma: float = 0.05, radius: float = 0.6,
+                 v_scale: float = 0.1, t_scale: float = 0.25) -> MLP:
+    """3 -> [width] x depth -> 1 with the residual blocks of Sec. 5.1: a block of the second kind
+    (g(V x + T x), V ~ v_scale N(0, 1), width x 3) ending at layer 2, and blocks of the first kind
+    (g(h + T h), the identity from the layer before the block) over layers 3-4, 5-6, ...  The
+    branch T of a first-kind block is a geometric-init layer pair scaled by t_scale, so each
+    block stays close to the identity and the net close to a sphere's distance function; F(0)
+    is recentred to -radius."""
+    m = geometric_init([width] * depth, seed, sigma, radius=radius, name=f"residual_w{width}_d{depth}_s{seed}")
+    rng = np.random.default_rng(seed + 1000)
+    sc = {2: (0, v_scale * rng.normal(size=(width, 3)))}
+    for q in range(4, depth + 1, 2):
+        sc[q] = (q - 2, None)
+        m.weights[q - 2] = t_scale * m.weights[q - 2]
+        m.weights[q - 1] = t_scale * m.weights[q - 1]
+    m.shortcuts = sc
+    m.b_out = float(m.b_out - (_value_at_origin(m) + radius))
+    m.meta["shortcuts"] = {int(k): int(v[0]) for k, v in sc.items()}
+    m.validate()
+    return m
+
+
+def pooled_net(seed: int = 61, count: int = 4, width: int = 32, depth: int = 4, sigma: float = 0.05,
+               radius: float = 0.6, offset: float = 0.2) -> MLP:
+    """Sec. 5.2's final max pooling over `count` sub-networks 3 -> [width] x depth -> 1 (the shape
+    of the paper's local decoder, 4 x D4-W32): sub-network i is a geometric-init sphere net
+    (seed + i, recentred) moved to the centre c_i = offset e_i (e_i = +x, -x, +y, -y, +z, -z, ...),
+    and F = max_i F_i, whose negative side is the intersection of theirs.  Returned as one MLP
+    whose hidden layers hold the sub-networks side by side (block-diagonal weights, the units of
+    sub-network i at i * width of every layer) and whose `heads` are [(w_i, b_i)], head i reading
+    sub-network i's last-layer units only.  meta["subnet_width"] = width."""
+    dirs = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+    subs = []
+    for i in range(count):
+        g = geometric_init([width] * depth, seed + i, sigma, radius=radius, recenter=True)
+        c = offset * dirs[i % 6] * (1 + i // 6)
+        g.biases[0] = g.biases[0] - g.weights[0] @ c          # F_i(x) = G_i(x - c_i)
+        subs.append(g)
+    n = count * width
+    Ws, bs = [], []
+    for l in range(depth):
+        if l == 0:
+            W = np.vstack([g.weights[0] for g in subs])
+        else:
+            W = np.zeros((n, n))
+            for i, g in enumerate(subs):
+                W[i * width:(i + 1) * width, i * width:(i + 1) * width] = g.weights[l]
+        Ws.append(W)
+        bs.append(np.concatenate([g.biases[l] for g in subs]))
+    heads = []
+    for i, g in enumerate(subs):
+        w = np.zeros(n)
+        w[i * width:(i + 1) * width] = g.w_out
+        heads.append((w, float(g.b_out)))
+    m = MLP(Ws, bs, heads[0][0].copy(), heads[0][1], name=f"pooled{count}_w{width}_d{depth}_s{seed}",
+            meta={"seed": seed, "sigma": sigma, "subnet_width": width, "count": count}, heads=heads)
     m.validate()
     return m
 
@@ -236,7 +312,7 @@ def sibling(mlp: MLP, seed: int, sigma: float = 0.005) -> MLP:
     m = MLP([w + rng.normal(0.0, sigma, w.shape) for w in mlp.weights],
             [b + rng.normal(0.0, sigma, b.shape) for b in mlp.biases],
             mlp.w_out.copy(), float(mlp.b_out), None if mlp.latent is None else mlp.latent.copy(),
-            mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta), mlp.slope)
+            mlp.skip_layer, f"{mlp.name}_sib{seed}", dict(mlp.meta), mlp.slope, dict(mlp.shortcuts))
     m.validate()
     return m
 

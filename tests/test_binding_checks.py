@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from synth import (batch_nets, decoder_net, leaky, octahedron, polytope_max_of_planes, proposal_target_net,
-                   proposal_train_nets, sibling, sphere_net, tiny_net)
+                   proposal_train_nets, residual_net, sibling, sphere_net, tiny_net)
 
 
 class _Stub:
@@ -35,6 +35,7 @@ def mesher():
     proposal_target_net, lambda: batch_nets()[0], lambda: batch_nets()[63],
     lambda: sibling(sphere_net(), seed=99), lambda: sibling(leaky(sphere_net(), 0.1), seed=3),
     lambda: leaky(tiny_net((6, 5, 4), 12), -0.25), lambda: proposal_train_nets()[31],
+    lambda: residual_net(seed=40, width=12, depth=6), lambda: leaky(residual_net(seed=32, width=24, depth=6), 0.1),
 ])
 def test_every_workload_net_passes(mesher, make):
     mesher.load_mlp(make())
@@ -52,7 +53,13 @@ def test_malformed_nets_never_reach_the_library(mesher):
     bad_out.w_out = np.zeros(5)
     bad_skip = copy.deepcopy(base)
     bad_skip.skip_layer = 9
-    for mlp in (bad_fan, bad_bias, bad_out, bad_skip):
+    bad_sc_src = copy.deepcopy(base)
+    bad_sc_src.shortcuts = {2: (2, None)}                  # not an earlier layer
+    bad_sc_id = copy.deepcopy(base)
+    bad_sc_id.shortcuts = {3: (1, None)}                   # identity from 6 units into 4
+    bad_sc_S = copy.deepcopy(base)
+    bad_sc_S.shortcuts = {3: (1, np.zeros((4, 5)))}        # S must be 4 x 6
+    for mlp in (bad_fan, bad_bias, bad_out, bad_skip, bad_sc_src, bad_sc_id, bad_sc_S):
         with pytest.raises(ValueError):
             mesher.load_mlp(mlp)
     assert mesher.lib.calls == []
