@@ -142,7 +142,21 @@ typedef struct {
     const double *const *shortcut_S;   /* NULL, or n_hidden pointers: S_l, width[l] x n_src row-major
                                  (n_src = 3 for x, else width[src]); a NULL pointer = the identity,
                                  which needs n_src == width[l] */
+    int n_heads;              /* 0 or 1: one output (w_out, b_out).  M = n_heads in 2..AM_MAX_HEADS: a
+                                 final max pooling (Sec. 5.2), F = max_i (w_heads[i] . h_L + b_heads[i]),
+                                 w_out and b_out unused.  M sub-networks sit side by side in the hidden
+                                 layers (block-diagonal W_l, the caller's layout) and head i reads its
+                                 sub-network's last layer.  A cell is a unit pattern together with the
+                                 index j of the pooled maximum (the first on a tie); its face lies on
+                                 head j's plane a_F(j) and its system gains the pooling rows
+                                 a_F(i) - a_F(j) (i != j) as planes N_units + i, so the net has
+                                 N = N_units + M plane ids and key bits (j one-hot in the last M),
+                                 and the box planes are N + 0..5.  Crossing pooling plane N_units + i
+                                 moves the maximum to i.  Pooled nets march in FP64 */
+    const double *w_heads;    /* n_heads x width[L] (n_heads >= 2) */
+    const double *b_heads;    /* n_heads */
 } am_mlp_desc;
+#define AM_MAX_HEADS 64
 
 /* Options of one march. */
 typedef struct {
@@ -480,7 +494,9 @@ am_status am_proposal_train(am_ctx *ctx, const float *d_X, const float *d_Y, int
  *   d_face_keys      n_faces x key_words cell keys (device)
  *   d_face_offsets   n_faces + 1 corner offsets, d_face_offsets[0] == 0 (device)
  *   d_edge_planes    n_corners plane ids, edge corner c -> corner c + 1 (device)
- *   n_neurons        N of the net; plane ids >= N (the box) carry no key bit
+ *   n_neurons        N of the net; plane ids >= N (the box) carry no key bit.  A max-pooled net's
+ *                    pooling planes are not named by their pair of heads here (am_get_mesh's
+ *                    assembly does that): pass its faces to am_get_mesh instead
  *   d_corner_vertex  out: n_corners vertex indices in [0, *d_n_vertices) (device)
  *   d_n_vertices     out: one int64, the number of distinct vertices (device); NEGATIVE when some
  *                    corner got no vertex: -1 a face has more than AM_NOALLOC_MAX_FACE_CORNERS

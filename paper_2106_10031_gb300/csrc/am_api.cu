@@ -441,6 +441,13 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
         N += dsc->width[l];
         mw = std::max(mw, dsc->width[l]);
     }
+    // final max pooling over M heads (Sec. 5.2): M pooling rows and key bits after the units
+    const int M = dsc->n_heads >= 2 ? dsc->n_heads : 0;
+    if (dsc->n_heads < 0 || dsc->n_heads > AM_MAX_HEADS || (M && (!dsc->w_heads || !dsc->b_heads)))
+        return fail(ctx, AM_ERR_INVALID_ARG, "n_heads %d: 0, 1 or 2..%d with w_heads and b_heads", dsc->n_heads,
+                    AM_MAX_HEADS);
+    const int n_units = N;
+    N += M;
     if (N > ctx->opts.max_neurons || mw > ctx->opts.max_width)
         return fail(ctx, AM_ERR_INVALID_ARG, "net has N=%d neurons, width %d; context allows %d, %d", N, mw,
                     ctx->opts.max_neurons, ctx->opts.max_width);
@@ -493,6 +500,11 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     }
     const size_t offW = host.size();
     host.insert(host.end(), dsc->w_out, dsc->w_out + dsc->width[L - 1]);
+    const size_t offH = host.size();               // pooling heads: M x n_L weights, then M offsets
+    if (M) {
+        host.insert(host.end(), dsc->w_heads, dsc->w_heads + (size_t)M * dsc->width[L - 1]);
+        host.insert(host.end(), dsc->b_heads, dsc->b_heads + M);
+    }
     std::vector<size_t> offS(L + 1, 0);            // matrix shortcuts from hidden layers
     for (int l = 2; l <= L; ++l) {
         const int src = sc_src(l);
@@ -597,6 +609,10 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
     nd.w_out_hi = nh.fblob + offW;
     nd.w_out_lo = nh.fblob + lo_off + offW;
     nd.b_out = dsc->b_out;
+    nd.M = M;
+    nd.n_units = n_units;
+    nd.w_heads = M ? nh.blob + offH : nullptr;
+    nd.b_heads = M ? nh.blob + offH + (size_t)M * dsc->width[L - 1] : nullptr;
     const int id = (int)ctx->nets.size();
     nd.salt = splitmix64(0xA11CE5EEDull + (unsigned long long)id * 0x9E3779B97F4A7C15ull);
     {
@@ -620,10 +636,10 @@ am_status am_load_mlp(am_ctx *ctx, const am_mlp_desc *dsc, int *net_id)
             }
             rel += 2.0 * (np + 8.0) * (np + 8.0) * u * u * growth;
         }
-        nd.df_ok = rel < 1e-7 && dsc->slope == 0.0 && !hidden_shortcut ? 1 : 0;
+        nd.df_ok = rel < 1e-7 && dsc->slope == 0.0 && !hidden_shortcut && !M ? 1 : 0;
     }
     nd.slope = dsc->slope;
-    nd.fp64_only = dsc->slope != 0.0 || hidden_shortcut ? 1 : 0;
+    nd.fp64_only = dsc->slope != 0.0 || hidden_shortcut || M ? 1 : 0;
     {
         // sliced tensor-core compose: 8 BF16 digit planes of each hidden W_l, row exponents, and
         // a TMA descriptor per layer; only when every fan-in keeps the accumulation exact

@@ -90,31 +90,72 @@ static cudaError_t exclusive_scan(int64_t *v, int64_t n, int64_t *tmp, int64_t t
 }
 
 // ---- vertex keys
-__device__ __forceinline__ void corner_planes(const Arena &ar, int32_t cell, int nv, int j, int *lo, int *hi)
+constexpr int kPairCode = 1 << 20;      // codes of pooling planes and of their triple points
+constexpr int kTripleCode = 1 << 24;
+
+// The two planes meeting at corner j of a cell's face (edges j - 1 and j), as codes that every
+// face sharing the vertex gives it alike, lo <= hi.  Unit and box planes are their ids.  On a
+// max-pooled net (Sec. 5.2) the pooling plane between heads i and j, which the cell of pooled
+// index j names N_units + i and the cell of index i names N_units + j, is the pair {i, j}; a
+// vertex on two pooling planes is the triple of their heads.  *pool: the vertex lies on a
+// pooling plane, so its key leaves out the pooled index.
+__device__ __forceinline__ void corner_planes(const Arena &ar, const NetDev &net, int32_t cell, int nv, int j, int *lo,
+                                              int *hi, bool *pool)
 {
-    const int a = ar.edges[(int64_t)cell * ar.maxv + (j + nv - 1) % nv];
-    const int b = ar.edges[(int64_t)cell * ar.maxv + j];
+    int a = ar.edges[(int64_t)cell * ar.maxv + (j + nv - 1) % nv];
+    int b = ar.edges[(int64_t)cell * ar.maxv + j];
+    *pool = false;
+    if (net.M >= 2) {
+        const bool pa = a >= net.n_units && a < net.N, pb = b >= net.n_units && b < net.N;
+        if (pa || pb) {
+            *pool = true;
+            const int own = pooled_index(net, ar.keys + (int64_t)cell * ar.kw);
+            if (pa && pb) {
+                int t0 = a - net.n_units, t1 = b - net.n_units, t2 = own, t;
+                if (t0 > t1) { t = t0; t0 = t1; t1 = t; }
+                if (t1 > t2) { t = t1; t1 = t2; t2 = t; }
+                if (t0 > t1) { t = t0; t0 = t1; t1 = t; }
+                a = b = kTripleCode + ((t0 << 12) | (t1 << 6) | t2);
+            } else {
+                const int i = (pa ? a : b) - net.n_units;
+                const int code = kPairCode + ((min(i, own) << 6) | max(i, own));
+                if (pa) a = code;
+                else b = code;
+            }
+        }
+    }
     *lo = a < b ? a : b;
     *hi = a < b ? b : a;
 }
 
+// the first plane id that is not a unit (a pooled net's pooling planes carry the one-hot index)
+__device__ __forceinline__ int unit_planes(const NetDev &net) { return net.M >= 2 ? net.n_units : net.N; }
+
 __device__ __forceinline__ unsigned long long vertex_hash(const Arena &ar, const NetDev &net, int32_t cell, int lo,
-                                                          int hi)
+                                                          int hi, bool pool)
 {
     unsigned long long h = ar.hash[cell];
     const unsigned long long *k = ar.keys + (int64_t)cell * ar.kw;
-    if (lo < net.N && ((k[lo >> 6] >> (lo & 63)) & 1ull)) h ^= ar.zob[lo];
-    if (hi < net.N && ((k[hi >> 6] >> (hi & 63)) & 1ull)) h ^= ar.zob[hi];
+    const int nU = unit_planes(net);
+    if (lo < nU && ((k[lo >> 6] >> (lo & 63)) & 1ull)) h ^= ar.zob[lo];
+    if (hi < nU && ((k[hi >> 6] >> (hi & 63)) & 1ull)) h ^= ar.zob[hi];
+    if (pool) h ^= ar.zob[net.n_units + pooled_index(net, k)];
     return h ^ splitmix64(((unsigned long long)lo << 20) ^ (unsigned long long)hi ^ 0x5bd1e995ull);
 }
 
-__device__ __forceinline__ bool vertex_keys_equal(const Arena &ar, int32_t c1, int32_t c2, int lo, int hi)
+__device__ __forceinline__ bool vertex_keys_equal(const Arena &ar, const NetDev &net, int32_t c1, int32_t c2, int lo,
+                                                  int hi, bool pool)
 {
     const unsigned long long *k1 = ar.keys + (int64_t)c1 * ar.kw, *k2 = ar.keys + (int64_t)c2 * ar.kw;
+    const int nU = unit_planes(net);
     for (int w = 0; w < ar.kw; ++w) {
         unsigned long long x = k1[w] ^ k2[w];
-        if ((lo >> 6) == w) x &= ~(1ull << (lo & 63));
-        if ((hi >> 6) == w) x &= ~(1ull << (hi & 63));
+        if (lo < nU && (lo >> 6) == w) x &= ~(1ull << (lo & 63));
+        if (hi < nU && (hi >> 6) == w) x &= ~(1ull << (hi & 63));
+        if (pool) {
+            const int a = max(net.n_units - 64 * w, 0), b = min(net.N - 64 * w, 64);
+            if (a < b) x &= ~((b >= 64 ? ~0ull : ((1ull << b) - 1ull)) & ~((1ull << a) - 1ull));
+        }
         if (x) return false;
     }
     return true;
@@ -126,11 +167,12 @@ __device__ __forceinline__ unsigned long long vslot_make(unsigned long long h, i
            (unsigned long long)(corner & 63);
 }
 
-// find (or claim) the slot of vertex (lo, hi, key of cell) ; returns the slot value
+// find (or claim) the slot of vertex (lo, hi, key of cell) (corner j of face `face`, codes of
+// corner_planes); returns the slot value
 __device__ unsigned long long vertex_probe(const AsmArgs &a, const NetDev &net, int64_t face, int j, int32_t cell,
-                                           int net_id, int lo, int hi, bool claim, bool *claimed)
+                                           int net_id, int lo, int hi, bool pool, bool claim, bool *claimed)
 {
-    const unsigned long long h = vertex_hash(a.ar, net, cell, lo, hi);
+    const unsigned long long h = vertex_hash(a.ar, net, cell, lo, hi, pool);
     const unsigned long long mine = vslot_make(h, face, j);
     unsigned long long pos = h & a.vslot_mask;
     *claimed = false;
@@ -147,8 +189,9 @@ __device__ unsigned long long vertex_probe(const AsmArgs &a, const NetDev &net, 
             const int32_t c2 = a.perm[f2];
             if (a.ar.net[c2] == net_id) {
                 int lo2, hi2;
-                corner_planes(a.ar, c2, a.ar.nverts[c2], j2, &lo2, &hi2);
-                if (lo2 == lo && hi2 == hi && vertex_keys_equal(a.ar, cell, c2, lo, hi)) return cur;
+                bool pool2;
+                corner_planes(a.ar, net, c2, a.ar.nverts[c2], j2, &lo2, &hi2, &pool2);
+                if (lo2 == lo && hi2 == hi && vertex_keys_equal(a.ar, net, cell, c2, lo, hi, pool)) return cur;
             }
         }
         pos = (pos + 1) & a.vslot_mask;
@@ -166,9 +209,10 @@ __global__ void asm_vertices_kernel(AsmArgs a)
         const int64_t off = a.corner_off[f];
         for (int j = 0; j < nv; ++j) {
             int lo, hi;
-            corner_planes(a.ar, c, nv, j, &lo, &hi);
+            bool pool;
+            corner_planes(a.ar, net, c, nv, j, &lo, &hi, &pool);
             bool claimed;
-            vertex_probe(a, net, f, j, c, net_id, lo, hi, true, &claimed);
+            vertex_probe(a, net, f, j, c, net_id, lo, hi, pool, true, &claimed);
             if (claimed) {
                 const int32_t vid = (int32_t)atomicAdd(a.vert_count + net_id, 1ull);
                 a.corner_vid[off + j] = vid | kWinBit;
@@ -189,9 +233,10 @@ __global__ void asm_lookup_kernel(AsmArgs a)
         for (int j = 0; j < nv; ++j) {
             if (a.corner_vid[off + j] != kUnset) continue;
             int lo, hi;
-            corner_planes(a.ar, c, nv, j, &lo, &hi);
+            bool pool;
+            corner_planes(a.ar, net, c, nv, j, &lo, &hi, &pool);
             bool claimed;
-            const unsigned long long s = vertex_probe(a, net, f, j, c, net_id, lo, hi, false, &claimed);
+            const unsigned long long s = vertex_probe(a, net, f, j, c, net_id, lo, hi, pool, false, &claimed);
             if (s == 0ull) continue;
             const int64_t f2 = (int64_t)((s >> 6) & 0x3FFFFFFFFull);
             const int j2 = (int)(s & 63);

@@ -77,28 +77,49 @@ __device__ __forceinline__ void block_argmax(double v, int idx, double *red_v, i
     __syncthreads();
 }
 
-// key(pa) ^ e_fa == key(pb) ^ e_fb ?  (kNoFlip = no bit flipped)
+constexpr int kNoPool = 1 << 30;       // pooling bit range of a net without pooling
+
+// Word w of the key reached from key word x by crossing plane `flip` (kNoFlip: none).  A unit's
+// plane flips its bit (Alg. 1 step 10); a pooling plane of a max-pooled net (pool0 <= flip < pool1,
+// Sec. 5.2) moves the one-hot pooled index, bits pool0 .. pool1 - 1, to flip.
+__device__ __forceinline__ unsigned long long child_word(unsigned long long x, int w, unsigned flip, int pool0,
+                                                         int pool1)
+{
+    if (flip == kNoFlip) return x;
+    if ((int)flip >= pool0 && (int)flip < pool1) {
+        const int lo = max(pool0 - 64 * w, 0), hi = min(pool1 - 64 * w, 64);
+        if (lo < hi) x &= ~((hi >= 64 ? ~0ull : ((1ull << hi) - 1ull)) & ~((1ull << lo) - 1ull));
+        if ((int)(flip >> 6) == w) x |= 1ull << (flip & 63);
+        return x;
+    }
+    if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
+    return x;
+}
+
+// key(pa) crossed at fa == key(pb) crossed at fb ?  (kNoFlip = nothing crossed)
 // Keys written by other blocks of a running kernel are read through L2 (ld.global.cg): the
 // SM's L1 is not coherent with other SMs' writes and may hold a stale copy of the line.
-__device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsigned fa, int64_t pb, unsigned fb)
+__device__ __forceinline__ bool ref_keys_equal(const Arena &ar, int64_t pa, unsigned fa, int64_t pb, unsigned fb,
+                                               int pool0 = kNoPool, int pool1 = kNoPool)
 {
     const unsigned long long *ka = ar.keys + pa * ar.kw, *kb = ar.keys + pb * ar.kw;
     for (int w = 0; w < ar.kw; ++w) {
-        unsigned long long x = __ldcg(ka + w) ^ __ldcg(kb + w);
-        if (fa != kNoFlip && (int)(fa >> 6) == w) x ^= 1ull << (fa & 63);
-        if (fb != kNoFlip && (int)(fb >> 6) == w) x ^= 1ull << (fb & 63);
+        const unsigned long long x = child_word(__ldcg(ka + w), w, fa, pool0, pool1) ^
+                                     child_word(__ldcg(kb + w), w, fb, pool0, pool1);
         if (x) return false;
     }
     return true;
 }
 
-// Alg. 1 steps 10-11: the neighbour key(parent) ^ e_flip (hash h) is pushed unless it was
-// seen before.  The slot records (parent, flip), from which any later probe rebuilds the
-// key, so a claim never waits for a key to be written.  A claim hands out the next cell id,
-// writes the new cell's record there (key, net, hash, the crossed plane and a point of the
-// shared edge), then publishes it through ready[id].
+// Alg. 1 steps 10-11: the neighbour across plane `flip` (hash h) is pushed unless it was seen
+// before.  The slot records (parent, flip), from which any later probe rebuilds the key, so a
+// claim never waits for a key to be written.  A claim hands out the next cell id, writes the
+// new cell's record there (key, net, hash, the crossed plane as the new cell names it, entry,
+// or flip when entry < 0, and a point of the shared edge), then publishes it through ready[id].
+// pool0, pool1: the pooling bits of a max-pooled net (child_word).
 __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned *mask, int64_t parent, int net,
-                                                unsigned flip, unsigned long long h, float px, float py, float pz)
+                                                unsigned flip, unsigned long long h, float px, float py, float pz,
+                                                int pool0 = kNoPool, int pool1 = kNoPool, int entry = -1)
 {
     const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
     unsigned long long pos = h & ar.slot_mask;
@@ -113,14 +134,13 @@ __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned 
             // the parent's key is its state, held by the block in shared memory
             unsigned long long *kn = ar.keys + id * ar.kw;
             for (int w = 0; w < ar.kw; ++w) {
-                unsigned long long x = (unsigned long long)mask[2 * w] | ((unsigned long long)mask[2 * w + 1] << 32);
-                if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
-                kn[w] = x;
+                const unsigned long long x = (unsigned long long)mask[2 * w] | ((unsigned long long)mask[2 * w + 1] << 32);
+                kn[w] = child_word(x, w, flip, pool0, pool1);
             }
             ar.net[id] = net;
             ar.hash[id] = h;
             ar.nverts[id] = -1;
-            ar.entry_plane[id] = (int32_t)flip;
+            ar.entry_plane[id] = entry >= 0 ? entry : (int32_t)flip;
             ar.parent[id] = (int32_t)parent;
             ar.entry_pt[id * 3 + 0] = px;
             ar.entry_pt[id * 3 + 1] = py;
@@ -131,7 +151,8 @@ __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned 
         }
         if (slot_tag(cur) == hash_tag(h)) {
             const int64_t pb = slot_parent(cur);
-            if (__ldcg(ar.net + pb) == net && ref_keys_equal(ar, parent, flip, pb, slot_flip(cur))) return;
+            if (__ldcg(ar.net + pb) == net && ref_keys_equal(ar, parent, flip, pb, slot_flip(cur), pool0, pool1))
+                return;
         }
         pos = (pos + 1) & ar.slot_mask;
     }
@@ -145,7 +166,8 @@ __device__ __forceinline__ void insert_neighbor(const Arena &ar, const unsigned 
 // kernel has ended) skips the fence and the release store that a persistent consumer needs.
 __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsigned *mask, int64_t parent, int net,
                                                      unsigned flip, unsigned long long h, float px, float py,
-                                                     float pz, bool publish = true)
+                                                     float pz, bool publish = true, int pool0 = kNoPool,
+                                                     int pool1 = kNoPool, int entry = -1)
 {
     const int lane = threadIdx.x & 31;
     const unsigned long long mine = slot_make(h, (unsigned long long)parent, flip);
@@ -165,15 +187,14 @@ __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsi
             // the parent's key is its state, held by the block in shared memory
             unsigned long long *kn = ar.keys + id * ar.kw;
             for (int w = lane; w < ar.kw; w += 32) {
-                unsigned long long x = (unsigned long long)mask[2 * w] | ((unsigned long long)mask[2 * w + 1] << 32);
-                if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
-                kn[w] = x;
+                const unsigned long long x = (unsigned long long)mask[2 * w] | ((unsigned long long)mask[2 * w + 1] << 32);
+                kn[w] = child_word(x, w, flip, pool0, pool1);
             }
             if (lane == 0) {
                 ar.net[id] = net;
                 ar.hash[id] = h;
                 ar.nverts[id] = -1;
-                ar.entry_plane[id] = (int32_t)flip;
+                ar.entry_plane[id] = entry >= 0 ? entry : (int32_t)flip;
                 ar.parent[id] = (int32_t)parent;
                 ar.entry_pt[id * 3 + 0] = px;
                 ar.entry_pt[id * 3 + 1] = py;
@@ -196,9 +217,8 @@ __device__ __forceinline__ void insert_neighbor_warp(const Arena &ar, const unsi
                 const unsigned long long *ka = ar.keys + parent * ar.kw, *kb = ar.keys + pb * ar.kw;
                 bool diff = false;
                 for (int w = lane; w < ar.kw; w += 32) {
-                    unsigned long long x = __ldcg(ka + w) ^ __ldcg(kb + w);
-                    if ((int)(flip >> 6) == w) x ^= 1ull << (flip & 63);
-                    if (fb != kNoFlip && (int)(fb >> 6) == w) x ^= 1ull << (fb & 63);
+                    const unsigned long long x = child_word(__ldcg(ka + w), w, flip, pool0, pool1) ^
+                                                 child_word(__ldcg(kb + w), w, fb, pool0, pool1);
                     diff |= x != 0ull;
                 }
                 if (!__any_sync(0xffffffffu, diff)) return;

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
         float b1 = 3.0e38f, b2 = 3.0e38f, b3 = 3.0e38f, s3 = 3.0e38f;
         int k1 = -1, k2 = -1, k3 = -1;
         if (!fallback) {
-            auto consider = [&](int k, const float4 r) {
+            auto consider = [&](int k, const float4 r, float score) {
                 const float n2 = r.x * r.x + r.y * r.y + r.z * r.z;
                 if (n2 == 0.0f) return;
                 const float d = fabsf(r.x * px + r.y * py + r.z * pz + r.w) * rsqrtf(n2);
@@ -425,23 +425,26 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
                 else if (d < b2) { b2 = d; k2 = k; }
                 if (learned && k < N) {
                     // the learned proposal adds the row it scores highest among this lane's
-                    const float q = k == entry ? -3.0e37f : -__bfloat162float(sc[k]);
+                    const float q = k == entry ? -3.0e37f : -score;
                     if (q < s3) { s3 = q; k3 = k; b3 = d; }
                 }
             };
-            // the neuron rows, 8 loads in flight per lane; then the box rows (lanes 0..5)
+            // the neuron rows and their scores, 8 of each in flight per lane; then the box rows
+            // (lanes 0..5)
             for (int k0 = lane; k0 < N; k0 += 32 * 8) {
                 float4 r[8];
+                float q[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int k = k0 + 32 * u;
                     r[u] = k < N ? __ldg(rv.p + 2 * k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    q[u] = learned && k < N ? __bfloat162float(sc[k]) : 0.0f;
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    if (k0 + 32 * u < N) consider(k0 + 32 * u, r[u]);
+                    if (k0 + 32 * u < N) consider(k0 + 32 * u, r[u], q[u]);
             }
-            if (lane < kBoxPlanes) consider(N + lane, rv.hi(N + lane));
+            if (lane < kBoxPlanes) consider(N + lane, rv.hi(N + lane), 0.0f);
             if (k3 == k1 || k3 == k2) k3 = -1;            // already a candidate
         }
         // ---- the candidate clip (FP32): nearest cutting row first; a row that holds on the

@@ -80,8 +80,23 @@ struct NetDev {
     // none; a shortcut from x is folded into Cl); sc_S[l] = S_l (n_l x n_src) or null = identity
     int sc_src[kMaxLayers + 1];
     const double *sc_S[kMaxLayers + 1];
-    int fp64_only;               // 1: composes in FP64 only (leaky activation or a hidden shortcut)
+    int fp64_only;               // 1: composes in FP64 only (leaky activation, a hidden shortcut, pooling)
+    // final max pooling over M heads (Sec. 5.2); M = 0 for a single output.  The units are rows
+    // 0 .. n_units - 1, the pooling rows (and one-hot key bits of the pooled index) n_units .. N - 1
+    int M, n_units;
+    const double *w_heads;       // M x n_L
+    const double *b_heads;       // M
 };
+
+// The pooled index j of a cell of a pooled net: the one-hot key bit among n_units .. N - 1
+__device__ __forceinline__ int pooled_index(const NetDev &net, const unsigned long long *key)
+{
+    for (int i = 0; i < net.M; ++i) {
+        const int b = net.n_units + i;
+        if ((key[b >> 6] >> (b & 63)) & 1ull) return i;
+    }
+    return 0;
+}
 
 // Device arenas (all sized at context creation).
 struct Arena {

@@ -553,6 +553,43 @@ __device__ __forceinline__ void compose(const NetDev &net, const Sh &s, bool tc,
         }
     }
     // a_F = w_out^T diag(s_L) Z_L + [0 | b_out]  (Cor. 1, Eq. 8)
+    if (M == kFP64 && net.M >= 2) {
+        // final max pooling (Sec. 5.2): a_F(i) of every head into row n_units + i, then the face
+        // plane a_F(j) of the cell's pooled index j and the pooling rows a_F(i) - a_F(j)
+        const int nL = net.width[net.L], rL = net.row0[net.L];
+        for (int i = 0; i < net.M; ++i) {
+            const double *wh = net.w_heads + (size_t)i * nL;
+            double f[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int k = tid; k < nL; k += kT) {
+                const double w = bit_of(s.mask, rL + k) ? wh[k] : -net.slope * wh[k];
+                if (w != 0.0)
+                    for (int c = 0; c < 4; ++c) f[c] -= w * s.r64[4 * (rL + k) + c];
+            }
+            for (int c = 0; c < 4; ++c) f[c] = warp_sum(f[c]);
+            if ((tid & 31) == 0)
+                for (int c = 0; c < 4; ++c) s.partd[4 * (tid >> 5) + c] = f[c];
+            __syncthreads();
+            if (tid == 0) {
+                double F[4] = {0.0, 0.0, 0.0, net.b_heads[i]};
+                for (int w = 0; w < kNW; ++w)
+                    for (int c = 0; c < 4; ++c) F[c] += s.partd[4 * w + c];
+                for (int c = 0; c < 4; ++c) s.r64[4 * (net.n_units + i) + c] = F[c];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int j = 0;
+            for (int i = 0; i < net.M; ++i)
+                if (bit_of(s.mask, net.n_units + i)) { j = i; break; }
+            for (int c = 0; c < 4; ++c) s.aF[c] = s.r64[4 * (net.n_units + j) + c];
+            s.eF[0] = 0.0f;
+        }
+        __syncthreads();
+        if (tid < net.M)
+            for (int c = 0; c < 4; ++c) s.r64[4 * (net.n_units + tid) + c] -= s.aF[c];
+        __syncthreads();
+        return;
+    }
     {
         const int nL = net.width[net.L], rL = net.row0[net.L];
         if (M == kFP64) {
@@ -1201,14 +1238,33 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         }
         const unsigned long long h = __ldcg(ar.hash + cell);
         const int nid = __ldcg(ar.net + cell);
+        // a max-pooled net (Sec. 5.2): crossing pooling plane n_units + i moves the pooled index j
+        // to i (two key bits change), and the new cell enters through its pooling row of j
+        int pj = 0;
+        if (net.M >= 2)
+            for (int i = 0; i < net.M; ++i)
+                if (bit_of(s.mask, net.n_units + i)) { pj = i; break; }
+        const int pool0 = net.M >= 2 ? net.n_units : kNoPool, pool1 = net.M >= 2 ? N : kNoPool;
+        auto child = [&](int e, unsigned long long *hc, int *entry) {
+            if (e >= pool0 && e < pool1) {
+                *hc = h ^ ar.zob[e] ^ ar.zob[pool0 + pj];
+                *entry = pool0 + pj;
+            } else {
+                *hc = h ^ ar.zob[e];
+                *entry = -1;
+            }
+        };
         if (ar.kw <= kThreadPushWords) {
             // narrow keys: one thread per edge
             for (int i = tid; i < m; i += kT) {
                 const int e = s.pe[buf][i];
                 if (e >= N) continue;
                 const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
-                insert_neighbor(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
-                                (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+                unsigned long long hc;
+                int entry;
+                child(e, &hc, &entry);
+                insert_neighbor(ar, s.mask, cell, nid, (unsigned)e, hc, (float)(0.5 * (p[0] + q[0])),
+                                (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])), pool0, pool1, entry);
             }
         } else {
             // wide keys: one warp per edge, the key words split over the lanes
@@ -1216,8 +1272,12 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
                 const int e = s.pe[buf][i];
                 if (e >= N) continue;
                 const double *p = s.pv[buf][i], *q = s.pv[buf][(i + 1) % m];
-                insert_neighbor_warp(ar, s.mask, cell, nid, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
-                                     (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])));
+                unsigned long long hc;
+                int entry;
+                child(e, &hc, &entry);
+                insert_neighbor_warp(ar, s.mask, cell, nid, (unsigned)e, hc, (float)(0.5 * (p[0] + q[0])),
+                                     (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])), true, pool0,
+                                     pool1, entry);
             }
         }
     }

@@ -49,9 +49,31 @@ __device__ double seed_forward(const NetDev &net, const double *x, double *H, un
         }
         __syncthreads();
     }
-    double f = 0.0;
     const double *hL = H + net.row0[net.L];
-    for (int k = tid; k < net.width[net.L]; k += T) f += net.w_out[k] * hL[k];
+    const int nL = net.width[net.L];
+    if (net.M >= 2) {
+        // final max pooling (Sec. 5.2): F = max_i F_i, the pooled index j = the first maximum,
+        // as its one-hot key bit n_units + j
+        double F = 0.0;
+        int j = 0;
+        for (int i = 0; i < net.M; ++i) {
+            const double *wh = net.w_heads + (size_t)i * nL;
+            double f = 0.0;
+            for (int k = tid; k < nL; k += T) f += wh[k] * hL[k];
+            f = warp_sum(f);
+            if ((tid & 31) == 0) red[tid >> 5] = f;
+            __syncthreads();
+            double Fi = net.b_heads[i];
+            for (int w = 0; w < T / 32; ++w) Fi += red[w];
+            __syncthreads();
+            if (i == 0 || Fi > F) { F = Fi; j = i; }
+        }
+        if (tid == 0) atomicOr(bits + ((net.n_units + j) >> 5), 1u << ((net.n_units + j) & 31));
+        __syncthreads();
+        return F;
+    }
+    double f = 0.0;
+    for (int k = tid; k < nL; k += T) f += net.w_out[k] * hL[k];
     f = warp_sum(f);
     if ((tid & 31) == 0) red[tid >> 5] = f;
     __syncthreads();
@@ -177,8 +199,12 @@ __device__ void seed_grad(const NetDev &net, const unsigned *bits, double *E, do
 {
     const int tid = threadIdx.x, T = blockDim.x;
     double gx = 0.0, gy = 0.0, gz = 0.0;
-    const int rL = net.row0[net.L];
-    for (int r = tid; r < net.N; r += T) E[r] = r >= rL ? net.w_out[r - rL] : 0.0;
+    const int rL = net.row0[net.L], nU = net.M >= 2 ? net.n_units : net.N;
+    const double *wo = net.w_out;                   // a pooled net: the head of the pooled index
+    if (net.M >= 2)
+        for (int i = 0; i < net.M; ++i)
+            if ((bits[(nU + i) >> 5] >> ((nU + i) & 31)) & 1u) { wo = net.w_heads + (size_t)i * net.width[net.L]; break; }
+    for (int r = tid; r < nU; r += T) E[r] = r >= rL ? wo[r - rL] : 0.0;
     __syncthreads();
     for (int l = net.L; l >= 1; --l) {
         const int nl = net.width[l], rl = net.row0[l];

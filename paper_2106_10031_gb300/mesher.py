@@ -46,6 +46,13 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def device_N(mlp) -> int:
+    """Plane ids (and key bits) of a net on the device: its units, plus one pooling row per head
+    of a max-pooled net (Sec. 5.2)."""
+    heads = getattr(mlp, "heads", None) or []
+    return int(mlp.N) + (len(heads) if len(heads) >= 2 else 0)
+
+
 @dataclass
 class Mesh:
     """Assembled mesh of one net (all arrays host numpy)."""
@@ -205,10 +212,21 @@ class Mesher:
                     S_keep.append(S)
                     S_ptrs[l - 1] = _dp(S)
             src_arr = (C.c_int * L)(*src)
+        # final max pooling over heads [(w_i, b_i)] (Sec. 5.2)
+        heads = list(getattr(mlp, "heads", None) or [])
+        wh = bh = None
+        if len(heads) == 1 or len(heads) > 64:
+            raise ValueError(f"{len(heads)} pooling heads: none, or 2..64")
+        if heads:
+            wh = np.ascontiguousarray(np.stack([np.asarray(w, dtype=np.float64) for w, _ in heads]))
+            bh = np.ascontiguousarray([float(b) for _, b in heads], dtype=np.float64)
+            if wh.shape != (len(heads), Ws[-1].shape[0]):
+                raise ValueError(f"pooling heads {wh.shape}; expected ({len(heads)}, {Ws[-1].shape[0]})")
         d = nt.am_mlp_desc(latent_dim=0 if z is None else len(z), latent=None if z is None else _dp(z),
                            n_hidden=L, width=width, W=Wp, b=bp, skip_layer=int(mlp.skip_layer),
                            w_out=_dp(w_out), b_out=float(mlp.b_out), slope=float(getattr(mlp, "slope", 0.0)),
-                           shortcut_src=src_arr, shortcut_S=S_ptrs)
+                           shortcut_src=src_arr, shortcut_S=S_ptrs, n_heads=len(heads),
+                           w_heads=None if wh is None else _dp(wh), b_heads=None if bh is None else _dp(bh))
         nid = C.c_int(-1)
         self._check(self.lib.am_load_mlp(self.ctx, C.byref(d), C.byref(nid)))
         self.nets.append(mlp)
@@ -312,14 +330,14 @@ class Mesher:
             if cache_key in table:
                 self.set_tuning(compose_tile_cells=int(table[cache_key]["compose_tile_cells"]))
                 return dict(table[cache_key], cached=True)
-        kw = (net.N + 63) // 64
+        kw = (device_N(net) + 63) // 64
         if keys is None:
             g = torch.Generator(device="cpu").manual_seed(seed)
             k = torch.randint(-2**62, 2**62, (n, kw), generator=g, dtype=torch.int64).to(dev)
         else:
-            k = torch.as_tensor(_key_array(keys, net.N).view(np.int64), device=dev)
+            k = torch.as_tensor(_key_array(keys, device_N(net)).view(np.int64), device=dev)
         n = k.shape[0]
-        rows = torch.empty((n, net.N + 1, 4), dtype=torch.float64, device=dev)
+        rows = torch.empty((n, device_N(net) + 1, 4), dtype=torch.float64, device=dev)
         pts = (nt.am_tune_point * 8)()
         cnt = C.c_int(0)
         self._check(self.lib.am_autotune_compose(self.ctx, net_id, C.c_void_p(k.data_ptr()), n,
@@ -360,7 +378,7 @@ class Mesher:
         import torch
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        N = self.nets[net_id].N
+        N = device_N(self.nets[net_id])
         dev = torch.device("cuda", self.device)
         k = torch.as_tensor(_key_array(keys, N).view(np.int64), device=dev)
         n = k.shape[0]
@@ -375,7 +393,7 @@ class Mesher:
         from the parents' rows ((n, N + 1, 4) float64, as compose() returns them) by the rank-1
         update on the tensor cores."""
         import torch
-        N = self.nets[net_id].N
+        N = device_N(self.nets[net_id])
         dev = torch.device("cuda", self.device)
         k = torch.as_tensor(_key_array(parent_keys, N).view(np.int64), device=dev)
         n = k.shape[0]

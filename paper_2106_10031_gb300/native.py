@@ -48,7 +48,8 @@ class am_mlp_desc(C.Structure):
                 ("width", C.POINTER(C.c_int)), ("W", C.POINTER(C.POINTER(C.c_double))),
                 ("b", C.POINTER(C.POINTER(C.c_double))), ("skip_layer", C.c_int),
                 ("w_out", C.POINTER(C.c_double)), ("b_out", C.c_double), ("slope", C.c_double),
-                ("shortcut_src", C.POINTER(C.c_int)), ("shortcut_S", C.POINTER(C.POINTER(C.c_double)))]
+                ("shortcut_src", C.POINTER(C.c_int)), ("shortcut_S", C.POINTER(C.POINTER(C.c_double))),
+                ("n_heads", C.c_int), ("w_heads", C.POINTER(C.c_double)), ("b_heads", C.POINTER(C.c_double))]
 
 
 class am_march_opts(C.Structure):

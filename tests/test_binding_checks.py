@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from synth import (batch_nets, decoder_net, leaky, octahedron, polytope_max_of_planes, proposal_target_net,
-                   proposal_train_nets, residual_net, sibling, sphere_net, tiny_net)
+                   pooled_net, proposal_train_nets, residual_net, sibling, sphere_net, tiny_net)
 
 
 class _Stub:
@@ -36,6 +36,7 @@ def mesher():
     lambda: sibling(sphere_net(), seed=99), lambda: sibling(leaky(sphere_net(), 0.1), seed=3),
     lambda: leaky(tiny_net((6, 5, 4), 12), -0.25), lambda: proposal_train_nets()[31],
     lambda: residual_net(seed=40, width=12, depth=6), lambda: leaky(residual_net(seed=32, width=24, depth=6), 0.1),
+    lambda: pooled_net(seed=62, count=4, width=8, depth=3), lambda: pooled_net(),
 ])
 def test_every_workload_net_passes(mesher, make):
     mesher.load_mlp(make())
@@ -59,7 +60,11 @@ def test_malformed_nets_never_reach_the_library(mesher):
     bad_sc_id.shortcuts = {3: (1, None)}                   # identity from 6 units into 4
     bad_sc_S = copy.deepcopy(base)
     bad_sc_S.shortcuts = {3: (1, np.zeros((4, 5)))}        # S must be 4 x 6
-    for mlp in (bad_fan, bad_bias, bad_out, bad_skip, bad_sc_src, bad_sc_id, bad_sc_S):
+    bad_heads = copy.deepcopy(base)
+    bad_heads.heads = [(np.zeros(4), 0.0), (np.zeros(5), 0.0)]   # a head must read the 4 last units
+    one_head = copy.deepcopy(base)
+    one_head.heads = [(np.zeros(4), 0.0)]                   # pooling needs two heads or more
+    for mlp in (bad_fan, bad_bias, bad_out, bad_skip, bad_sc_src, bad_sc_id, bad_sc_S, bad_heads, one_head):
         with pytest.raises(ValueError):
             mesher.load_mlp(mlp)
     assert mesher.lib.calls == []
