@@ -1,10 +1,12 @@
 """Benchmark: analytic faces per second of analytic marching on one GB300.
 
-One step = the whole hot path on one mesh: forget the previous cells, trigger the seed cell by
-bisection on the device, march every analytic cell to completion (compose, clip, emit, hash
+One step = the whole hot path on one mesh: forget the previous cells, trigger the seed cells
+on the device (the random-pair trigger of Sec. 4.3.2: F at 16384 fixed uniform samples of
+[-1.4, 1.4]^3, up to 1024 pairs of opposite sign, each bisected to its cell; --seeding ray: one
+ray along +x instead), march every analytic cell to completion (compose, clip, emit, hash
 march) and assemble the mesh.  The workload is the learned-proposal target net, 3-[256]x8-1
 (N = 2048 ReLUs; geometric init, seed 5, every parameter perturbed by N(0, 0.05^2), output bias
-recentred), one seed ray along +x, clipped to the box [-1.5, 1.5]^3: 1.81e6 faces.  The
+recentred), clipped to the box [-1.5, 1.5]^3: 1.81e6 faces, the same mesh from either seeding.  The
 headline is the mixed-precision path -- the compose of each breadth-first level's cells on the
 tcgen05 tensor cores (error-free BF16 digit planes) and the certified clip -- with the learned
 constraint proposal (trained before timing on the plain method's meshes of 32 other nets of the
@@ -12,10 +14,10 @@ same shape, seeds 100-131).  The comparison legs time the plain FP64 method on t
 (every cutting row clipped), the nearest-row candidates, the decoder-shaped net and the
 3-[64]x4-1 sphere net.  Inputs (the net, the proposal) are resident in HBM when the timed
 region starts; the e2e leg repeats the step through the C ABI from pinned host buffers (net
-upload, seed ray, mesh download) inside the timed region.
+upload, seed samples, mesh download) inside the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision sliced|fp64|mixed]
-                  [--candidates learned|nearest|none] [--impl reference]
+                  [--candidates learned|nearest|none] [--seeding pairs|ray] [--impl reference]
 
 Multi-GPU: each rank meshes its own copy of the workload (replicas, no collective on the
 data path); the job's value is the faces of all ranks over the slowest rank's time.
@@ -39,8 +41,38 @@ import numpy as np  # noqa: E402
 
 METRIC = "analytic faces/sec on 1 GB300 (oracle-exact mesh); mixed+learned vs plain FP64"
 UNIT = "faces/s"
-WORKLOAD = ("3-[256]x8-1 geometric-init SDF MLP (seed 5, sigma 0.05, recentred; N = 2048), 1 seed ray +x, "
-            "box 1.5, whole mesh")
+WORKLOAD_NET = "3-[256]x8-1 geometric-init SDF MLP (seed 5, sigma 0.05, recentred; N = 2048)"
+SEEDINGS = {
+    "pairs": "seeded by the random-pair trigger (Sec. 4.3.2: 16384 uniform samples in [-1.4, 1.4]^3, up to 1024 "
+             "sign-change pairs bisected to their cells)",
+    "ray": "1 seed ray +x",
+}
+PAIR_SAMPLES, PAIR_MAX = 16384, 1024
+SEEDING = "pairs"                                  # the step's seeding; --seeding sets it
+
+
+def workload_name(seeding=None) -> str:
+    return f"{WORKLOAD_NET}, {SEEDINGS[seeding or SEEDING]}, box 1.5, whole mesh"
+
+
+def pair_samples():
+    from synth import trigger_points
+    return trigger_points(PAIR_SAMPLES, seed=5, box=1.4)
+
+
+def oracle_seeds(O, net, o, d):
+    """The oracle's seed cells for the step's seeding (the same samples or ray as the GPU's)."""
+    if SEEDING == "pairs":
+        return [x for x in O.seed_pairs(net, pair_samples(), PAIR_MAX) if x is not None]
+    return O.seed_cells(net, o, d)
+
+
+def seed_step(m, nid, o, d, seeding=None):
+    """The step's seed cells: the random-pair trigger on the fixed samples, or the one ray."""
+    if (seeding or SEEDING) == "pairs":
+        m.seed_pairs(nid, pair_samples(), PAIR_MAX)
+    else:
+        m.seed(nid, o, d)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12     # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12   # 128 FFMA/clk/SM x 152 SMs x 2.07 GHz (derived)
 
@@ -108,6 +140,9 @@ def parse():
                    help="run only the customised-trigger leg (sphere tracing, random pairs) and print its JSON")
     p.add_argument("--compose-only", action="store_true",
                    help="run only the compose benchmark (am_compose on the decoder) and print its JSON")
+    p.add_argument("--seeding", default="pairs", choices=["pairs", "ray"],
+                   help="the step's seed cells: the random-pair trigger (Sec. 4.3.2) on 16384 fixed samples, or one "
+                        "ray along +x")
     p.add_argument("--seeds-only", action="store_true",
                    help="run only the many-seeds leg (1024 sphere-traced seeds vs one ray) and print its JSON")
     p.add_argument("--march-once", action="store_true",
@@ -264,7 +299,7 @@ def cpu_baseline(mlp, o, d, budget_s=10.0):
     from oracle import oracle as O
     O.build()
     net = O.OracleNet(mlp)
-    seeds = O.seed_cells(net, o, d)
+    seeds = oracle_seeds(O, net, o, d)
     probe = 200
     t0 = time.perf_counter()
     O.march(net, seeds, max_cells=probe)
@@ -346,7 +381,7 @@ def run_reference(args, dist):
     from oracle import oracle as O
     O.build()
     net = O.OracleNet(mlp)
-    seeds = O.seed_cells(net, o, d)
+    seeds = oracle_seeds(O, net, o, d)
     cells = 12000
     lm, cores = None, 1
     try:
@@ -380,7 +415,7 @@ def run_reference(args, dist):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": workload_name(), "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -390,7 +425,8 @@ def run_reference(args, dist):
 
 def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, schedule, candidates, prop=None):
     """Same step through the C ABI with host buffers: upload the net from pinned memory, seed
-    from a pinned host ray, march, copy the mesh back into pinned host buffers.  A learned
+    from pinned host sample points (or a pinned host ray), march, copy the mesh back into pinned
+    host buffers.  A learned
     proposal (prop = (params, (n_in, hidden, n_out))) is loaded once, untimed."""
     import torch
 
@@ -401,6 +437,7 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, schedule, candidate
     bp = [pin(b) for b in mlp.biases]
     wo = pin(mlp.w_out)
     ray_o, ray_d = pin(o), pin(d)
+    pts = pin(pair_samples()) if SEEDING == "pairs" else None
     L = mlp.L
     dp = lambda t: C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_double))  # noqa: E731
     desc = nt.am_mlp_desc(latent_dim=0, latent=None, n_hidden=L, width=(C.c_int * L)(*mlp.widths),
@@ -419,7 +456,7 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, schedule, candidate
         assert lib.am_proposal_set_params(ctx, params.ctypes.data_as(C.c_void_p), len(params)) == 0
     mo = nt.am_march_opts(box=1.5, delta=1e-10, precision=precision, max_cells=0, candidates=cand, schedule=schedule)
     bufs = None
-    h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + 48
+    h2d = sum(w.numel() * 8 for w in Wp + bp) + wo.numel() * 8 + (pts.numel() * 8 if pts is not None else 48)
     d2h = 0
 
     def step():
@@ -428,7 +465,12 @@ def e2e_leg(mlp, o, d, steps, device, stream_ptr, precision, schedule, candidate
         nid = C.c_int()
         assert lib.am_load_mlp(ctx, C.byref(desc), C.byref(nid)) == 0
         ns = C.c_int()
-        assert lib.am_seed(ctx, nid, dp(ray_o), dp(ray_d), 1, 2.0, C.byref(ns)) == 0
+        if pts is not None:
+            npair = C.c_int()
+            assert lib.am_seed_pairs(ctx, nid, dp(pts), int(pts.shape[0]), PAIR_MAX, C.byref(npair), C.byref(ns),
+                                     None) == 0, lib.am_last_error(ctx)
+        else:
+            assert lib.am_seed(ctx, nid, dp(ray_o), dp(ray_d), 1, 2.0, C.byref(ns)) == 0
         assert lib.am_march(ctx, C.byref(mo)) == 0, lib.am_last_error(ctx)
         m = nt.am_mesh()
         assert lib.am_get_mesh(ctx, nid, C.byref(m)) == 0
@@ -464,9 +506,14 @@ def measure(m, nid, o, d, steps, precision, schedule, flush, stream, candidates=
     """K timed steps; L2 flushed before each (outside the events).  Returns totals."""
     import torch
 
+    samples = pair_samples() if SEEDING == "pairs" else None
+
     def step():
         m.reset()
-        m.seed(nid, o, d)
+        if samples is not None:
+            m.seed_pairs(nid, samples, PAIR_MAX)
+        else:
+            m.seed(nid, o, d)
         m.march(precision=precision, schedule=schedule, candidates=candidates, max_cells=max_cells)
 
     total_ms, cell_ms, compose_ms, clip_ms, launches, cell_launches = 0.0, 0.0, 0.0, 0.0, 0, 0
@@ -895,7 +942,7 @@ def run_ours(args, dist):
         "scaling": "weak", "vs_baseline": None, "dtype": {"sliced": "bf16-digits+f64", "mixed": "f32x2+f64",
                                                           "fp64": "f64"}[prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "faces_per_step": faces_per_step, "precision": prec,
+        "config": {"workload": workload_name(), "faces_per_step": faces_per_step, "precision": prec,
                    "candidates": args.candidates, "schedule": sched, "parallelism": f"replicas x{dist.world}",
                    "l2": "flushed before every step (256 MiB write); the step's inputs exceed L2"},
         "roofline": roof,
@@ -998,13 +1045,18 @@ def seeds_leg(dev, n_starts=1024, reps=2):
     from tests import meshcheck
     mlp, o, d = workload()
     starts = trigger_points(n_starts, seed=4, box=1.4)
-    out = {"workload": f"{WORKLOAD}; {n_starts} sphere-traced seeds vs one ray", "precision": "sliced",
+    out = {"workload": f"{workload_name('ray')}; seedings compared: one ray, {n_starts} sphere-traced starts, "
+                       f"random pairs", "precision": "sliced",
            "candidates": "nearest"}
     digests = {}
     with am.Mesher(device=dev, **ctx_shape(mlp)) as m:
         nid = m.load_mlp(mlp)
+        samples = trigger_points(16 * n_starts, seed=5, box=1.4)
         for name, seed in (("one_ray", lambda: m.seed(nid, o, d)),
-                           ("traced_seeds", lambda: m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12))):
+                           ("traced_seeds", lambda: m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=64, eps=1e-12)),
+                           ("traced_seeds_8_steps", lambda: m.seed_sphere_trace(nid, starts, eta=1.0, max_steps=8,
+                                                                                 eps=1e-12)),
+                           ("pair_seeds", lambda: m.seed_pairs(nid, samples, n_starts))):
             runs = []
             for _ in range(reps + 1):                   # the first run warms up
                 m.reset()
@@ -1019,15 +1071,19 @@ def seeds_leg(dev, n_starts=1024, reps=2):
                          "faces_per_s": st["faces"] / (st["ms_march"] / 1e3), "levels": st["levels"],
                          "cells_per_level": st["cells"] / max(1, st["levels"]), "seed_ms": t_seed * 1e3,
                          "ms_compose": st["ms_compose"], "ms_clip": st["ms_clip"]}
-    out["same_mesh"] = digests["one_ray"] == digests["traced_seeds"]
+    out["same_mesh"] = all(digests[k] == digests["one_ray"] for k in digests)
     out["speedup_vs_one_ray"] = out["traced_seeds"]["faces_per_s"] / out["one_ray"]["faces_per_s"]
+    for k in ("traced_seeds", "traced_seeds_8_steps", "pair_seeds"):
+        out[k]["same_mesh"] = digests[k] == digests["one_ray"]
+        out[k]["seeded_march_ms"] = out[k]["ms_march"] + out[k]["seed_ms"]
     return out
 
 
 
 def march_once(dev, args):
     """The step's march alone, for a profiler and for the launch-shape comparisons: the workload
-    net (or the decoder), one +x ray, the chosen precision and candidates, args.warmup untimed
+    net seeded as the step is (--seeding; the decoder from one +x ray), the chosen precision and
+    candidates, args.warmup untimed
     marches first, then one march (args.max_cells cells, 0 = all; the context is sized to it)
     whose am_march CUDA-event times are printed.  Learned candidates come from an untrained
     proposal of the step's shape: the same forward-pass work per level without the training's
@@ -1050,7 +1106,10 @@ def march_once(dev, args):
             m.proposal_init(7 + mlp.L, 256, mlp.N, max_batch=1024, seed=0)
         for _ in range(max(0, args.warmup) + 1):
             m.reset()
-            m.seed(nid, o, d)
+            if args.net == "decoder":
+                m.seed(nid, o, d)
+            else:
+                seed_step(m, nid, o, d)
             m.march(precision=prec, schedule=schedule_for(prec, args.schedule), candidates=args.candidates,
                     max_cells=args.max_cells)
         st = m.stats()
@@ -1062,7 +1121,9 @@ def march_once(dev, args):
             "clip_fallbacks": st["clip_fallbacks"], "tensor_macs": st["tensor_macs"]}
 
 def main():
+    global SEEDING
     args = parse()
+    SEEDING = args.seeding
     dist = Dist(args.gpus)
     try:
         if args.impl == "reference":

@@ -1033,8 +1033,14 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
         const int64_t cap = std::max<int64_t>(nl + nl / 4, 4096);
         CU(cudaMalloc(&r.full_list, sizeof(int32_t) * cap));
         CU(cudaMalloc(&r.r1_list, sizeof(int32_t) * cap));
+        // the warp clip's fallback cells of the whole level
+        if (ctx->fb_list) CU(cudaFree(ctx->fb_list));
+        ctx->fb_list = nullptr;
+        CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * cap));
         r.list_cap = cap;
     }
+    const bool warp_clip = ctx->clip_kernel == 0 && ma.candidates != kCandNone && N <= kMaxNeurons;
+    if (warp_clip) CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
     const int period = ctx->oz_rank1_period > 0 ? ctx->oz_rank1_period : 8;
     int64_t launches = 0;
     cudaEvent_t *ev = ctx->oz_ev.data();
@@ -1103,9 +1109,9 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
         ma.begin = c0;
         ma.end = c1;
         ma.rows_in = reinterpret_cast<const float *>(rows) + (c0 - f0) * rstride;
-        if (ctx->clip_kernel == 0 && ma.candidates != kCandNone && N <= kMaxNeurons) {
-            // one warp per cell; the cells it cannot decide outright go to the block kernel
-            CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
+        if (warp_clip) {
+            // one warp per cell; the cells it cannot decide outright go to the block kernel, once
+            // for the whole level after its last chunk
             ma.fb_list = ctx->fb_list;
             ma.fb_count = ctx->fb_count;
             if (ctx->check_kernel == 1) {
@@ -1122,7 +1128,8 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
                 ca.rows = reinterpret_cast<const float *>(ma.rows_in);
                 ca.begin = c0;
                 ca.N = N;
-                ca.box = (float)ma.box;
+                ca.box = ma.box_hi;
+                ca.box_lo = ma.box_lo;
                 ca.delta = ma.delta;
                 ca.status = ctx->chk_status;
                 ca.counters = ctx->ar.counters;
@@ -1140,13 +1147,24 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
                 launch_clip_warp(ma, ctx->stream);
                 CU(cudaGetLastError());
             }
-            MarchArgs mb = ma;
-            mb.list = ctx->fb_list;
-            mb.list_count = ctx->fb_count;
-            launch_march(mb, 1, false, (int)std::min<int64_t>(c1 - c0, 2 * (int64_t)ctx->sm_count), ctx->stream);
-            CU(cudaGetLastError());
-            ctx->stats.cell_launches += 2;
-            launches += 2;
+            ctx->stats.cell_launches += 1;
+            launches += 1;
+            if (b == nchunk - 1) {
+                // the level's fallback cells: rows from the level's buffer, nearest candidates (the
+                // proposal's scores cover the last chunk only; the candidates never change the face)
+                MarchArgs mb = ma;
+                mb.begin = f0;
+                mb.end = f1;
+                mb.rows_in = rows;
+                mb.scores_in = nullptr;
+                if (mb.candidates == kCandLearned) mb.candidates = kCandNearest;
+                mb.list = ctx->fb_list;
+                mb.list_count = ctx->fb_count;
+                launch_march(mb, 1, false, (int)std::min<int64_t>(nl, 2 * (int64_t)ctx->sm_count), ctx->stream);
+                CU(cudaGetLastError());
+                ctx->stats.cell_launches += 1;
+                launches += 1;
+            }
         } else {
             launch_march(ma, 1, false, (int)(c1 - c0), ctx->stream);   // certified FP32 tests on the pairs
             CU(cudaGetLastError());
@@ -1217,6 +1235,8 @@ am_status am_march(am_ctx *ctx, const am_march_opts *o)
     ma.nets = ctx->d_nets;
     ma.ar = ctx->ar;
     ma.box = op.box;
+    ma.box_hi = (float)op.box;
+    ma.box_lo = (float)(op.box - (double)ma.box_hi);
     ma.delta = op.delta;
     ma.max_n = ctx->opts.max_neurons;
     ma.max_w = ctx->opts.max_width;
@@ -1470,7 +1490,7 @@ am_status am_compose_neighbors(am_ctx *ctx, int net_id, const uint64_t *d_parent
     if (!e) e = cudaMemcpyAsync(dflip, flip.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (!e) e = cudaMemcpyAsync(dord, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (!e) {
-        rows_to_pairs(d_parent_rows, pin, n * (N + 1), ctx->stream);
+        rows_to_pairs(d_parent_rows, pin, n, N + 1, ctx->stream);
         e = cudaGetLastError();
     }
     if (!e) {
@@ -1479,7 +1499,7 @@ am_status am_compose_neighbors(am_ctx *ctx, int net_id, const uint64_t *d_parent
                      ctx->sm_count, ctx->stream);
     }
     if (!e) {
-        pairs_to_rows(pout, d_rows, n * (N + 1), ctx->stream);
+        pairs_to_rows(pout, d_rows, n, N + 1, ctx->stream);
         e = cudaGetLastError();
     }
     if (!e) e = cudaStreamSynchronize(ctx->stream);

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kCT, 4) check_tc_kernel(CheckArgs a)
         for (int t = 0; t < ntiles && !dead; ++t) {
             // ---- stage row t kCT + tid: [r1 | r2] in chunk 0, [r3 | 0] in chunk 1
             const int r = t * kCT + tid;
-            const float4 h = r < N ? __ldg(rp + 2 * r) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const float4 h = r < N ? __ldg(rp + r) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             {
                 unsigned a0[4], a1[4], a2[4];
                 split3(h.x, a0[0], a1[0], a2[0]);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kCT, 4) check_tc_kernel(CheckArgs a)
                     if (sl > B) { bad = true; continue; }
                     if (sl >= -B) {                     // close call: FP64 from the exact pair
                         ++n_close;
-                        const float4 lo = __ldg(rp + 2 * r + 1);
+                        const float4 lo = __ldg(rp + (N + 1) + r);
                         const double r6[4] = {(double)h.x + (double)lo.x, (double)h.y + (double)lo.y,
                                               (double)h.z + (double)lo.z, (double)h.w + (double)lo.w};
                         const double *v6 = S.v[i];
@@ -247,7 +247,8 @@ __global__ void __launch_bounds__(kCT, 4) check_tc_kernel(CheckArgs a)
                 if (sl >= -B) {
                     ++n_close;
                     const double *v6 = S.v[j];
-                    const double s6 = (double)rr[0] * v6[0] + (double)rr[1] * v6[1] + (double)rr[2] * v6[2] + (double)rr[3];
+                    const double s6 = (double)rr[0] * v6[0] + (double)rr[1] * v6[1] + (double)rr[2] * v6[2] + (double)rr[3] -
+                                      (double)a.box_lo;
                     const double B6 = 1.0001 * (double)S.dvb[j] + (double)band + 1e-15 * (fabs(v6[ax]) + (double)a.box);
                     if (s6 >= -B6) { bad = true; break; }
                 }

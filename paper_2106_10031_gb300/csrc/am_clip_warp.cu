@@ -3,7 +3,8 @@
 //
 // A block holds kWW warps and each warp solves its own cell start to finish, so the serial
 // parts of a cell (the cuts of its polygon) occupy one warp instead of idling a whole block,
-// and many cells are in flight per SM.  The rows are read from memory (FP32 pairs [hi x 4 |
+// and many cells are in flight per SM.  The rows are read from memory (FP32 pairs: the cell's hi
+// words [hi x 4], then its lo words [lo x 4], so a pass that reads only hi words reads half the bytes |
 // lo x 4], a_F last) where the block version stages them in shared memory.  Per cell:
 //   candidates : each lane keeps the two rows nearest to the point the cell was entered through
 //                among the rows it scans, and with learned candidates also the row the proposal
@@ -55,11 +56,11 @@ int warp_smem_bytes() { return kWW * (int)sizeof(WarpSh); }
 struct WRows {
     const float4 *p;              // [hi, lo] per row
     int N;
-    float box;
+    float box, box_lo;            // the box as an FP32 pair: box rows' offsets -box (hi), -box_lo (lo)
     const WarpSh *S;
     __device__ __forceinline__ float4 hi(int k) const
     {
-        if (k < N) return __ldg(p + 2 * k);
+        if (k < N) return __ldg(p + k);
         if (k < N + kBoxPlanes) {
             const int i = k - N;
             const float sg = (i & 1) ? -1.0f : 1.0f;
@@ -72,11 +73,12 @@ struct WRows {
     {
         const float4 h = hi(k);
         if (k < N) {
-            const float4 l = __ldg(p + 2 * k + 1);
+            const float4 l = __ldg(p + (N + 1) + k);
             r[0] = (double)h.x + (double)l.x; r[1] = (double)h.y + (double)l.y;
             r[2] = (double)h.z + (double)l.z; r[3] = (double)h.w + (double)l.w;
         } else {
-            r[0] = h.x; r[1] = h.y; r[2] = h.z; r[3] = h.w;
+            r[0] = h.x; r[1] = h.y; r[2] = h.z;
+            r[3] = k < N + kBoxPlanes ? (double)h.w - (double)box_lo : (double)h.w;
         }
     }
     __device__ __forceinline__ void f32(int k, float *r) const
@@ -206,12 +208,13 @@ __device__ int wcell_setup(const MarchArgs &a, WarpSh &S, int64_t cell, int N, W
     const int lane = threadIdx.x & 31;
     rv.p = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * 2 * (int64_t)(N + 1);
     rv.N = N;
-    rv.box = (float)a.box;
+    rv.box = a.box_hi;
+    rv.box_lo = a.box_lo;
     rv.S = &S;
     wload_key(S, a.ar, cell);
     if (lane < 4) {
-        const float h = reinterpret_cast<const float *>(rv.p + 2 * N)[lane];
-        const float l = reinterpret_cast<const float *>(rv.p + 2 * N + 1)[lane];
+        const float h = reinterpret_cast<const float *>(rv.p + N)[lane];
+        const float l = reinterpret_cast<const float *>(rv.p + 2 * N + 1)[lane];   // lo block: N + 1 + N
         S.aF[lane] = (double)h + (double)l;
         S.aFhi[lane] = h;
     }
@@ -280,7 +283,7 @@ __device__ bool wcheck(const MarchArgs &a, WarpSh &S, const WRows &rv, int N, in
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
               const int k = k0 + 32 * u;
-              rr[u] = k < N ? __ldg(rv.p + 2 * k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+              rr[u] = k < N ? __ldg(rv.p + k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int k = k0 + 32 * u;
-                    r[u] = k < N ? __ldg(rv.p + 2 * k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    r[u] = k < N ? __ldg(rv.p + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     q[u] = learned && k < N ? __bfloat162float(sc[k]) : 0.0f;
                 }
 #pragma unroll

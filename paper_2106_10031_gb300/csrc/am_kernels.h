@@ -29,6 +29,7 @@ struct MarchArgs {
     const NetDev *nets;
     Arena ar;
     double box, delta;
+    float box_hi, box_lo;    // box as an FP32 pair (box_hi + box_lo == box), set on the host with box
     int max_n, max_w;        // shared-memory sizing (largest loadable net)
     long long limit;         // persistent schedule: tickets >= limit are not solved
     long long wait_ns;       // persistent schedule: limit on any wait for work (ns)
@@ -37,7 +38,8 @@ struct MarchArgs {
     int tc;                  // compose only (mode 1): hidden layers composed on the tensor cores
     ProposalView prop;       // used with kCandLearned for nets with N == prop.n_out
     const void *rows_in;     // level schedule: rows of cells [begin, end) composed beforehand on the
-                             // tensor cores, n x (N + 1) FP32 pairs [hi x 4 | lo x 4], a_F last
+                             // tensor cores, n x (N + 1) FP32 pairs, a_F last: per cell the N + 1 hi
+                             // words [hi x 4], then the N + 1 lo words [lo x 4]
     const __nv_bfloat16 *scores_in;   // level schedule, learned candidates: the proposal's scores of
     int scores_ld;                    // cells [begin, end), scores_ld BF16 per cell, from the tensor cores
     const int32_t *list;              // level schedule: solve the cells list[0 .. *list_count) (ids in
@@ -77,7 +79,7 @@ struct CheckArgs {
     const float *rows;
     int64_t begin;
     int N;
-    float box;
+    float box, box_lo;
     double delta;
     int *status;
     unsigned long long *counters;     // close calls are added to counters[kCloseCalls]
@@ -317,11 +319,13 @@ struct R1Cells {
 cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list, int64_t n, const int64_t *cnt_le,
                      const void *prev_rows, int64_t prev0, void *rows, int64_t cell0, const OzScratch &scr,
                      R1Scratch &r, int tile_cells, int sms, cudaStream_t st);
-// FP64 rows (n x (N + 1) x 4 doubles) <-> FP32 pairs (n x (N + 1) x [hi x 4 | lo x 4])
-void rows_to_pairs(const double *rows, float *pairs, int64_t nrows, cudaStream_t st);
-void pairs_to_rows(const float *pairs, double *rows, int64_t nrows, cudaStream_t st);
+// FP64 rows (n cells x (N + 1) rows x 4 doubles) <-> FP32 pairs (per cell: the N + 1 hi words
+// [hi x 4], then the N + 1 lo words [lo x 4]); rows_per_cell = N + 1
+void rows_to_pairs(const double *rows, float *pairs, int64_t n_cells, int rows_per_cell, cudaStream_t st);
+void pairs_to_rows(const float *pairs, double *rows, int64_t n_cells, int rows_per_cell, cudaStream_t st);
 // rows of the cells with keys (n x kw words): n x (N + 1) rows of 32 bytes, a_F last, each row
-// FP64 [a | a0] or, with df, FP32 pairs [hi x 4 | lo x 4]; batches smaller than sms x the tiles
+// FP64 [a | a0] or, with df, FP32 pairs (the N + 1 hi words [hi x 4], then the N + 1 lo words
+// [lo x 4]); batches smaller than sms x the tiles
 // resident per SM split the product's K over several CTAs; tile_cells 0 picks the tile per batch
 // list (optional): the batch is the cells list[0..n) (keys at keys + list[i] kw, rows at rows +
 // (list[i] - cell0) x (N + 1) x 32 B)

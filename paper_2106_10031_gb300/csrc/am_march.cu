@@ -869,12 +869,13 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     long long tp0 = 0, tp1 = 0, tp2 = 0, tp2a = 0, tp3a = 0, tp3 = 0, tp4 = 0, tp4a = 0, tp5 = 0;
     AM_TICK(tp0);
     if (a.rows_in) {
-        // rows composed beforehand on the tensor cores, as FP32 pairs [hi x 4 | lo x 4] per row
+        // rows composed beforehand on the tensor cores, as FP32 pairs (the hi words [hi x 4] of
+        // rows 0..N, then their lo words [lo x 4])
         // (signs as compose<M>, a_F last).  The pairs are the rows: the double-float tests are
         // certified against them with no further row error, as FP64 tests take FP64 rows.
         const float4 *src = reinterpret_cast<const float4 *>(a.rows_in) + (cell - a.begin) * (int64_t)(N + 1) * 2;
         for (int k = tid; k < N; k += kT) {
-            const float4 h = __ldcs(src + 2 * k), l = __ldcs(src + 2 * k + 1);
+            const float4 h = __ldcs(src + k), l = __ldcs(src + (N + 1) + k);
             if (M == kFP64) {
                 double *r = s.r64 + 4 * k;
                 r[0] = (double)h.x + (double)l.x; r[1] = (double)h.y + (double)l.y;
@@ -886,7 +887,7 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
             }
         }
         if (tid < 4) {
-            const float h = reinterpret_cast<const float *>(src + 2 * N)[tid];
+            const float h = reinterpret_cast<const float *>(src + N)[tid];
             const float l = reinterpret_cast<const float *>(src + 2 * N + 1)[tid];
             s.aF[tid] = (double)h + (double)l;
             if (M == kDF) { s.aFhi[tid] = h; s.aFlo[tid] = l; }
@@ -899,18 +900,18 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
     AM_TICK(tp1);
 
     // box rows (exact), frame and the initial square (thread 0)
+    // (kDF: the pairs are stored as they are, exact FP32 words: the normal's components are
+    // 0 and +-1 and the offset is the host's split of the box, so no conversion runs here)
     for (int i = tid; i < kBoxPlanes; i += kT) {
-        const double sgn = (i & 1) ? -1.0 : 1.0;
-        const double r[4] = {(i >> 1) == 0 ? sgn : 0.0, (i >> 1) == 1 ? sgn : 0.0, (i >> 1) == 2 ? sgn : 0.0, -a.box};
-        const int k = N + i;
+        const int ax = i >> 1, k = N + i;
+        const float sg = (i & 1) ? -1.0f : 1.0f;
+        const float n0 = ax == 0 ? sg : 0.0f, n1 = ax == 1 ? sg : 0.0f, n2 = ax == 2 ? sg : 0.0f;
         if (M == kFP64) {
-            for (int c = 0; c < 4; ++c) s.r64[4 * k + c] = r[c];
+            double *r = s.r64 + 4 * k;
+            r[0] = n0; r[1] = n1; r[2] = n2; r[3] = -a.box;
         } else {
-            for (int c = 0; c < 4; ++c) {
-                const float h = (float)r[c];
-                s.rhi[4 * k + c] = h;
-                s.rlo[4 * k + c] = (float)(r[c] - (double)h);
-            }
+            *reinterpret_cast<float4 *>(s.rhi + 4 * k) = make_float4(n0, n1, n2, -a.box_hi);
+            *reinterpret_cast<float4 *>(s.rlo + 4 * k) = make_float4(0.0f, 0.0f, 0.0f, -a.box_lo);
             s.err[k] = 0.0f;
         }
     }
@@ -1181,15 +1182,22 @@ __device__ __noinline__ CellOut solve_cell(const MarchArgs &a, const NetDev &net
         if (wid == 0) {
             int mm = m, bb = buf, status = 0, t = 0;
             const double tol = M == kFP64 ? a.delta : 0.0;
+            bool changed = false;
             for (; t < nviol && mm > 0; ++t) {
                 bool sw;
                 const int nm = warp_cut<double, M>(s, s.pv, mm, bb, s.viol[t], tol, s.aF, &sw);
                 if (nm < 0) { status = 1; mm = 0; break; }
                 if (sw) bb ^= 1;
+                changed |= sw || nm != mm;
                 mm = nm;
             }
             if (M == kDF && mm > 0) df_final_vertices(s, mm, bb, kVertexTol);
-            if (lane == 0) { s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; s.blk[6] += (unsigned long long)t; }
+            if (lane == 0) {
+                s.si[0] = mm; s.si[1] = bb; s.si[2] = status; s.si[9] += 1; s.blk[6] += (unsigned long long)t;
+                // kDF: rows the certified FP32 test calls violated that the cut on the pairs in FP64
+                // does not move: the two views of the rows disagree, so FP64 decides the cell
+                if (M == kDF && !changed && status == 0) s.si[10] = 1;
+            }
         }
         __syncthreads();
     }

@@ -236,16 +236,17 @@ __global__ void prop_pad_w1_kernel(const float *W1, int hidden, int n_in, __nv_b
 // Features of the cells [c0, c0 + n) of the level march, one warp per cell, in the layout the
 // in-march proposal uses: entry point (3), unit normal of a_F (3), a_F offset / |normal| (1),
 // active fraction of each hidden layer (L), zero padded to kPBK BF16 values.  a_F is row N of
-// the cell's composed rows (FP32 pairs [hi x 4 | lo x 4]).
+// the cell's composed rows (FP32 pairs: the hi words [hi x 4] of rows 0..N, then their lo words).
 __global__ void prop_features_kernel(PropFeatures f)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= f.n) return;
     const int64_t cell = f.c0 + i;
-    const float *aF = f.rows + i * f.rstride + 8 * (int64_t)f.N;
-    const double F0 = (double)aF[0] + (double)aF[4], F1 = (double)aF[1] + (double)aF[5],
-                 F2 = (double)aF[2] + (double)aF[6], F3 = (double)aF[3] + (double)aF[7];
+    const float *aF = f.rows + i * f.rstride + 4 * (int64_t)f.N;             // hi words of a_F
+    const float *aL = f.rows + i * f.rstride + 4 * (int64_t)(2 * f.N + 1);   // its lo words
+    const double F0 = (double)aF[0] + (double)aL[0], F1 = (double)aF[1] + (double)aL[1],
+                 F2 = (double)aF[2] + (double)aL[2], F3 = (double)aF[3] + (double)aL[3];
     const double inv = 1.0 / sqrt(F0 * F0 + F1 * F1 + F2 * F2);
     __nv_bfloat16 *o = f.X + i * kPBK;
     for (int j = lane; j < kPBK; j += 32) {

@@ -125,7 +125,8 @@ struct OzPrep {
     int kw;
     int64_t n;                        // cells in the batch
     void *rows;                       // cell i's rows at rows + i * rstride (N rows, then a_F), 32 B each:
-    int64_t rstride;                  //   FP64 [a | a0], or FP32 pairs [hi x4 | lo x4] when df
+    int64_t rstride;                  //   FP64 [a | a0], or, when df, FP32 pairs as two blocks: the N + 1
+                                      //   hi words [hi x4] first, then the N + 1 lo words [lo x4]
     int df;
     int l, L, N;
     int nl, row0;                     // width and first neuron of layer l
@@ -280,14 +281,14 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                     mx[j] = a > mx[j] ? a : mx[j];
                 }
             }
-            float4 *o = reinterpret_cast<float4 *>(outf + 8 * (int64_t)r);
-            o[0] = make_float4(h[0], h[1], h[2], h[3]);
-            o[1] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            float4 *o = reinterpret_cast<float4 *>(outf);
+            o[r] = make_float4(h[0], h[1], h[2], h[3]);
+            o[p.N + 1 + r] = make_float4(lo[0], lo[1], lo[2], lo[3]);
         }
     }
     __syncthreads();                               // the block reads back the rows it wrote
     const double *Z = out + 4 * (int64_t)p.row0;
-    const float *Zf = outf + 8 * (int64_t)p.row0;
+    const float *Zh = outf + 4 * (int64_t)p.row0, *Zl = outf + 4 * (int64_t)(p.N + 1 + p.row0);   // df: the pairs
     if (p.l == p.L) {
         // a_F = w_out^T diag(s_L) Z_L + [0 | b_out] (Cor. 1, Eq. 8); an active row is -Z_k
         double f[4] = {0.0, 0.0, 0.0, 0.0};
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                 const double w = p.w_out[k];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const double r = p.df ? (double)Zf[8 * k + j] + (double)Zf[8 * k + 4 + j] : Z[4 * k + j];
+                    const double r = p.df ? (double)Zh[4 * k + j] + (double)Zl[4 * k + j] : Z[4 * k + j];
                     f[j] = fma(-w, r, f[j]);
                 }
             }
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
                 out[4 * (int64_t)p.N + tid] = F;
             } else {
                 const float h = (float)F;
-                outf[8 * (int64_t)p.N + tid] = h;
-                outf[8 * (int64_t)p.N + 4 + tid] = (float)(F - (double)h);
+                outf[4 * (int64_t)p.N + tid] = h;
+                outf[4 * (int64_t)(2 * p.N + 1) + tid] = (float)(F - (double)h);
             }
         }
         return;
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_prep_kernel(OzPrep p)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 // active: z = -row
-                long long x = p.df ? -(fixed62f(Zf[8 * k + j], e[j]) + fixed62f(Zf[8 * k + 4 + j], e[j]))
+                long long x = p.df ? -(fixed62f(Zh[4 * k + j], e[j]) + fixed62f(Zl[4 * k + j], e[j]))
                                    : fixed62(-Z[4 * k + j], e[j]);
 #pragma unroll
                 for (int t = 0; t < kOzPlanes; ++t) {
@@ -415,29 +416,30 @@ __global__ void __launch_bounds__(128) oz_r1_init_kernel(R1Init a)
     const int e = a.entry[c];
     const float4 *src = reinterpret_cast<const float4 *>(a.prev_rows + (p - a.prev0) * a.rstride);
     float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
+    const int lo0 = a.N + 1;                         // the lo block follows the N + 1 hi words
     for (int q = threadIdx.x; q < 2 * (a.N + 1); q += blockDim.x) dst[q] = src[q];
     __syncthreads();                                 // row e and a_F are rewritten below
     if (threadIdx.x != 0) return;
     int l = a.L;
     for (int ll = 1; ll <= a.L; ++ll)
         if (e < a.row0[ll + 1]) { l = ll; break; }
-    const float4 h = src[2 * e], lo = src[2 * e + 1];
+    const float4 h = src[e], lo = src[lo0 + e];
     const double at[4] = {(double)h.x + (double)lo.x, (double)h.y + (double)lo.y, (double)h.z + (double)lo.z,
                           (double)h.w + (double)lo.w};
-    dst[2 * e] = make_float4(-h.x, -h.y, -h.z, -h.w);
-    dst[2 * e + 1] = make_float4(-lo.x, -lo.y, -lo.z, -lo.w);
+    dst[e] = make_float4(-h.x, -h.y, -h.z, -h.w);
+    dst[lo0 + e] = make_float4(-lo.x, -lo.y, -lo.z, -lo.w);
     a.it_l[i] = l;
     a.it_k[i] = e - a.row0[l];
     for (int q = 0; q < 4; ++q) a.it_a[4 * i + q] = at[q];
     if (l == a.L) {
         const double w = a.w_out[e - a.row0[l]];
-        float4 fh = dst[2 * a.N], fl = dst[2 * a.N + 1];
+        float4 fh = dst[a.N], fl = dst[lo0 + a.N];
         pair_add(fh.x, fl.x, w * at[0]);
         pair_add(fh.y, fl.y, w * at[1]);
         pair_add(fh.z, fl.z, w * at[2]);
         pair_add(fh.w, fl.w, w * at[3]);
-        dst[2 * a.N] = fh;
-        dst[2 * a.N + 1] = fl;
+        dst[a.N] = fh;
+        dst[lo0 + a.N] = fl;
     }
 }
 
@@ -497,14 +499,14 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         const int r = a.row0j + m;
         const bool act = key_bit(key, r);
         const double sg = act ? -x : x;              // (1 - 2 s) v
-        float4 *rp = reinterpret_cast<float4 *>(row + 8 * (int64_t)r);
-        float4 h = rp[0], lo = rp[1];
+        float4 *rh = reinterpret_cast<float4 *>(row) + r, *rl = rh + (a.N + 1);
+        float4 h = *rh, lo = *rl;
         pair_add(h.x, lo.x, sg * at0);
         pair_add(h.y, lo.y, sg * at1);
         pair_add(h.z, lo.z, sg * at2);
         pair_add(h.w, lo.w, sg * at3);
-        rp[0] = h;
-        rp[1] = lo;
+        *rh = h;
+        *rl = lo;
         r1v[m] = act ? x : 0.0;
         if (act) {
             const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
@@ -519,14 +521,14 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         if (tid == 0) {
             double f = 0.0;
             for (int w = 0; w < kW; ++w) f += fred[w];
-            float4 *fp = reinterpret_cast<float4 *>(row + 8 * (int64_t)a.N);
-            float4 fh = fp[0], fl = fp[1];
+            float4 *fp = reinterpret_cast<float4 *>(row) + a.N, *fq = fp + (a.N + 1);
+            float4 fh = *fp, fl = *fq;
             pair_add(fh.x, fl.x, f * at0);
             pair_add(fh.y, fl.y, f * at1);
             pair_add(fh.z, fl.z, f * at2);
             pair_add(fh.w, fl.w, f * at3);
-            fp[0] = fh;
-            fp[1] = fl;
+            *fp = fh;
+            *fq = fl;
         }
         return;
     }
@@ -1254,7 +1256,11 @@ cudaError_t oz_compose(const OzNet &net, const unsigned long long *keys, int kw,
 }
 
 
-__global__ void rows_to_pairs_kernel(const double *rows, float *pairs, int64_t nrows)
+// row i = cell c = i / per, row k = i % per: the cell's pairs hold its `per` hi words, then its
+// `per` lo words
+__device__ __forceinline__ int64_t pair_hi(int64_t i, int per) { return (i / per) * 2 * per + i % per; }
+
+__global__ void rows_to_pairs_kernel(const double *rows, float *pairs, int64_t nrows, int per)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
         float h[4], l[4];
@@ -1263,15 +1269,17 @@ __global__ void rows_to_pairs_kernel(const double *rows, float *pairs, int64_t n
             h[q] = (float)v;
             l[q] = (float)(v - (double)h[q]);
         }
-        reinterpret_cast<float4 *>(pairs)[2 * i] = make_float4(h[0], h[1], h[2], h[3]);
-        reinterpret_cast<float4 *>(pairs)[2 * i + 1] = make_float4(l[0], l[1], l[2], l[3]);
+        const int64_t o = pair_hi(i, per);
+        reinterpret_cast<float4 *>(pairs)[o] = make_float4(h[0], h[1], h[2], h[3]);
+        reinterpret_cast<float4 *>(pairs)[o + per] = make_float4(l[0], l[1], l[2], l[3]);
     }
 }
 
-__global__ void pairs_to_rows_kernel(const float *pairs, double *rows, int64_t nrows)
+__global__ void pairs_to_rows_kernel(const float *pairs, double *rows, int64_t nrows, int per)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 h = reinterpret_cast<const float4 *>(pairs)[2 * i], l = reinterpret_cast<const float4 *>(pairs)[2 * i + 1];
+        const int64_t o = pair_hi(i, per);
+        const float4 h = reinterpret_cast<const float4 *>(pairs)[o], l = reinterpret_cast<const float4 *>(pairs)[o + per];
         rows[4 * i] = (double)h.x + (double)l.x;
         rows[4 * i + 1] = (double)h.y + (double)l.y;
         rows[4 * i + 2] = (double)h.z + (double)l.z;
@@ -1279,14 +1287,18 @@ __global__ void pairs_to_rows_kernel(const float *pairs, double *rows, int64_t n
     }
 }
 
-void rows_to_pairs(const double *rows, float *pairs, int64_t nrows, cudaStream_t st)
+void rows_to_pairs(const double *rows, float *pairs, int64_t n_cells, int rows_per_cell, cudaStream_t st)
 {
-    rows_to_pairs_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(rows, pairs, nrows);
+    const int64_t nrows = n_cells * rows_per_cell;
+    rows_to_pairs_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(rows, pairs, nrows,
+                                                                                                    rows_per_cell);
 }
 
-void pairs_to_rows(const float *pairs, double *rows, int64_t nrows, cudaStream_t st)
+void pairs_to_rows(const float *pairs, double *rows, int64_t n_cells, int rows_per_cell, cudaStream_t st)
 {
-    pairs_to_rows_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(pairs, rows, nrows);
+    const int64_t nrows = n_cells * rows_per_cell;
+    pairs_to_rows_kernel<<<(unsigned)std::min<int64_t>((nrows + 255) / 256, 152 * 16), 256, 0, st>>>(pairs, rows, nrows,
+                                                                                                    rows_per_cell);
 }
 
 cudaError_t oz_rank1_classify(const OzNet &net, const Arena &ar, int64_t p0, int64_t p1, int64_t c_begin,
