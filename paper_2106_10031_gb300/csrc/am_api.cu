@@ -978,7 +978,7 @@ static am_status ensure_r1_scratch(am_ctx *ctx)
     CU(cudaMalloc(&r.offs, sizeof(int) * 2 * (kMaxLayers + 1)));
     CU(cudaMalloc(&r.it_l, sizeof(int) * items));
     CU(cudaMalloc(&r.it_k, sizeof(int) * items));
-    CU(cudaMalloc(&r.it_a, sizeof(double) * 4 * items));
+    CU(cudaMalloc(&r.it_a, sizeof(float) * 8 * items));
     r.item_cap = items;
     CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * ctx->oz.batch_cells));
     CU(cudaMalloc(&ctx->fb_count, sizeof(unsigned long long)));

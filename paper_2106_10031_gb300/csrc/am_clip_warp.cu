@@ -3,9 +3,9 @@
 //
 // A block holds kWW warps and each warp solves its own cell start to finish, so the serial
 // parts of a cell (the cuts of its polygon) occupy one warp instead of idling a whole block,
-// and many cells are in flight per SM.  The rows are read from memory (FP32 pairs: the cell's hi
-// words [hi x 4], then its lo words [lo x 4], so a pass that reads only hi words reads half the bytes |
-// lo x 4], a_F last) where the block version stages them in shared memory.  Per cell:
+// and many cells are in flight per SM.  The rows are read from memory where the block version
+// stages them in shared memory: FP32 pairs, a_F last, the cell's N + 1 hi words [hi x 4] and then
+// its N + 1 lo words [lo x 4], so a pass that reads only hi words reads half the bytes.  Per cell:
 //   candidates : each lane keeps the two rows nearest to the point the cell was entered through
 //                among the rows it scans, and with learned candidates also the row the proposal
 //                scores highest among them (the proposal extends the nearest set);

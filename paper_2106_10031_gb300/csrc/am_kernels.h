@@ -295,7 +295,7 @@ struct R1Scratch {
     int64_t list_cap = 0;
     int *it_l = nullptr;              // per item of a rank-1 batch: flip layer, flip index within it
     int *it_k = nullptr;
-    double *it_a = nullptr;           // per item: a~ (4 doubles)
+    float *it_a = nullptr;            // per item: a~ as FP32 pairs, [hi x 4 | lo x 4]
     int64_t item_cap = 0;
     unsigned long long *counts = nullptr;   // device: [0] full, [l] rank-1 with flip layer l
     int *offs = nullptr;              // device: [l] first r1_list slot of flip layer l, [kMaxLayers + 1 + l] cursors

@@ -394,7 +394,7 @@ struct R1Init {
     int row0[kMaxLayers + 2];         // row0[L + 1] = N
     const double *w_out;
     int *it_l, *it_k;
-    double *it_a;
+    float *it_a;                      // per item: a~ as FP32 pairs, [hi x 4 | lo x 4]
 };
 
 // (h, l) += d, re-split into an FP32 pair (the rows' 48-bit representation)
@@ -405,48 +405,56 @@ __device__ __forceinline__ void pair_add(float &h, float &l, double d)
     l = (float)(t - (double)h);
 }
 
-// One block per child: the parent's rows, row k's sign flipped (s_k flips, Z_k does not), and
-// a~ = delta Z_l[k] = the parent's signed row k (its sign (1 - 2 s_k) is delta); for a flip in
-// the last layer a_F += w_out[k] a~ and nothing else changes.
+// One block per child: the parent's rows of layers 1..l and a_F (the rows of the later layers
+// are written by the prep of each layer, from the parent's), row k's sign flipped (s_k flips,
+// Z_k does not), and a~ = delta Z_l[k] = the parent's signed row k (its sign (1 - 2 s_k) is
+// delta); for a flip in the last layer a_F += w_out[k] a~ and nothing else changes.
 __global__ void __launch_bounds__(128) oz_r1_init_kernel(R1Init a)
 {
     const int64_t i = blockIdx.x;
     const int64_t c = a.list[i];
     const int64_t p = a.parent[c];
     const int e = a.entry[c];
-    const float4 *src = reinterpret_cast<const float4 *>(a.prev_rows + (p - a.prev0) * a.rstride);
-    float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
-    const int lo0 = a.N + 1;                         // the lo block follows the N + 1 hi words
-    for (int q = threadIdx.x; q < 2 * (a.N + 1); q += blockDim.x) dst[q] = src[q];
-    __syncthreads();                                 // row e and a_F are rewritten below
-    if (threadIdx.x != 0) return;
     int l = a.L;
     for (int ll = 1; ll <= a.L; ++ll)
         if (e < a.row0[ll + 1]) { l = ll; break; }
+    const float4 *src = reinterpret_cast<const float4 *>(a.prev_rows + (p - a.prev0) * a.rstride);
+    float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
+    const int lo0 = a.N + 1;                         // the lo block follows the N + 1 hi words
+    const int nc = a.row0[l + 1];                    // rows of layers 1..l
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+        dst[q] = src[q];
+        dst[lo0 + q] = src[lo0 + q];
+    }
+    __syncthreads();                                 // row e is rewritten below
+    if (threadIdx.x != 0) return;
     const float4 h = src[e], lo = src[lo0 + e];
-    const double at[4] = {(double)h.x + (double)lo.x, (double)h.y + (double)lo.y, (double)h.z + (double)lo.z,
-                          (double)h.w + (double)lo.w};
     dst[e] = make_float4(-h.x, -h.y, -h.z, -h.w);
     dst[lo0 + e] = make_float4(-lo.x, -lo.y, -lo.z, -lo.w);
     a.it_l[i] = l;
     a.it_k[i] = e - a.row0[l];
-    for (int q = 0; q < 4; ++q) a.it_a[4 * i + q] = at[q];
+    float *at = a.it_a + 8 * i;
+    at[0] = h.x; at[1] = h.y; at[2] = h.z; at[3] = h.w;
+    at[4] = lo.x; at[5] = lo.y; at[6] = lo.z; at[7] = lo.w;
+    float4 fh = src[a.N], fl = src[lo0 + a.N];
     if (l == a.L) {
         const double w = a.w_out[e - a.row0[l]];
-        float4 fh = dst[a.N], fl = dst[lo0 + a.N];
-        pair_add(fh.x, fl.x, w * at[0]);
-        pair_add(fh.y, fl.y, w * at[1]);
-        pair_add(fh.z, fl.z, w * at[2]);
-        pair_add(fh.w, fl.w, w * at[3]);
-        dst[a.N] = fh;
-        dst[lo0 + a.N] = fl;
+        pair_add(fh.x, fl.x, w * ((double)h.x + (double)lo.x));
+        pair_add(fh.y, fl.y, w * ((double)h.y + (double)lo.y));
+        pair_add(fh.z, fl.z, w * ((double)h.z + (double)lo.z));
+        pair_add(fh.w, fl.w, w * ((double)h.w + (double)lo.w));
     }
+    dst[a.N] = fh;
+    dst[lo0 + a.N] = fl;
 }
 
 struct R1Prep {
     const unsigned long long *keys;
     int kw;
     const int32_t *list;
+    const int32_t *parent;
+    const float *prev_rows;           // the parents' level: cell c at (c - prev0) rstride
+    int64_t prev0;
     float *rows;
     int64_t cell0, rstride;
     int j, L, N, nj, row0j;
@@ -462,56 +470,78 @@ struct R1Prep {
     int Kp;                           // round_up(n_j, 64)
     const double *w_out;
     const int *it_l, *it_k;
-    const double *it_a;
+    const float *it_a;                // per item: a~ as FP32 pairs, [hi x 4 | lo x 4]
 };
 
 // One block per child whose rows of layer j change (flip layer l <= j - 1): v_j (W_j's column k
-// when l = j - 1, else the exact product of layer j), the rows c_j += (1 - 2 s_j) v_j a~, and the
-// next operand diag(s_j) v_j as 8 digit planes (or, at the last layer, a_F += (w_out . diag(s_L)
-// v_L) a~).
+// when l = j - 1, else the exact product of layer j) as an FP32 pair, the child's rows
+// c_j = the parent's + (1 - 2 s_j) v_j a~ in double-float arithmetic (the FP32 pipes: the
+// product of the pairs by FMA, TwoSum into the row), and the next operand diag(s_j) v_j as 8
+// digit planes (or, at the last layer, a_F += (w_out . diag(s_L) v_L) a~).
 __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
 {
     constexpr int kW = kOzPrepThreads / 32;
-    extern __shared__ double r1v[];                  // diag(s_j) v_j, n_j values
-    __shared__ unsigned long long red[kW];
+    extern __shared__ float r1v[];                   // diag(s_j) v_j: hi words [0, n_j), lo words [n_j, 2 n_j)
+    __shared__ unsigned red[kW];
     __shared__ double fred[kW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t i = blockIdx.x;
     const int64_t c = a.list[i];
     const unsigned long long *key = a.keys + c * a.kw;
-    float *row = a.rows + (c - a.cell0) * a.rstride;
+    const float4 *src = reinterpret_cast<const float4 *>(a.prev_rows + (a.parent[c] - a.prev0) * a.rstride);
+    float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
+    const int lo0 = a.N + 1;
     const int l = a.it_l[i];
-    const double at0 = a.it_a[4 * i], at1 = a.it_a[4 * i + 1], at2 = a.it_a[4 * i + 2], at3 = a.it_a[4 * i + 3];
-    unsigned long long mx = 0ull;
+    float ah[4], al[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ah[q] = a.it_a[8 * i + q];
+        al[q] = a.it_a[8 * i + 4 + q];
+    }
+    unsigned mx = 0u;
     double fs = 0.0;
     for (int m = tid; m < a.nj; m += kOzPrepThreads) {
-        double x;
+        float xh, xl;
         if (l == a.j - 1) {
-            x = a.ATj[(int64_t)a.it_k[i] * a.nj + m];
+            const double w = a.ATj[(int64_t)a.it_k[i] * a.nj + m];
+            xh = (float)w;
+            xl = (float)(w - (double)xh);
         } else {
             const int64_t o = i * a.Mp + m;
-            x = i64_ldexp(a.P[o] + ((a.Q[o] + 32) >> 6), a.eA[m] + a.eBin[i] - 48);
+            const long long acc = a.P[o] + ((a.Q[o] + 32) >> 6);
             if (a.zero) {                             // consumed: zero for the next product's split-K sums
                 a.P[o] = 0;
                 a.Q[o] = 0;
             }
+            const int e = a.eA[m] + a.eBin[i] - 48;
+            long long hi_int, lo_int;
+            xh = i64_to_f32(acc, e, &hi_int);
+            xl = i64_to_f32(acc - hi_int, e, &lo_int);
         }
         const int r = a.row0j + m;
         const bool act = key_bit(key, r);
-        const double sg = act ? -x : x;              // (1 - 2 s) v
-        float4 *rh = reinterpret_cast<float4 *>(row) + r, *rl = rh + (a.N + 1);
-        float4 h = *rh, lo = *rl;
-        pair_add(h.x, lo.x, sg * at0);
-        pair_add(h.y, lo.y, sg * at1);
-        pair_add(h.z, lo.z, sg * at2);
-        pair_add(h.w, lo.w, sg * at3);
-        *rh = h;
-        *rl = lo;
-        r1v[m] = act ? x : 0.0;
+        const float sg = act ? -1.0f : 1.0f;         // (1 - 2 s) v
+        const float4 h4 = src[r], l4 = src[lo0 + r];
+        float h[4] = {h4.x, h4.y, h4.z, h4.w}, lo[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // (xh + xl)(ah + al) as pp + pe: the exact product of the hi words by FMA, the two
+            // cross terms into its error (xl al, below 2^-48 of the product, is dropped)
+            const float pp = xh * ah[q];
+            float pe = fmaf(xh, ah[q], -pp);
+            pe = fmaf(xh, al[q], pe);
+            pe = fmaf(xl, ah[q], pe);
+            df_add(h[q], lo[q], sg * pp, sg * pe);
+            df_norm(h[q], lo[q]);
+        }
+        dst[r] = make_float4(h[0], h[1], h[2], h[3]);
+        dst[lo0 + r] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+        r1v[m] = act ? xh : 0.0f;
+        r1v[a.nj + m] = act ? xl : 0.0f;
         if (act) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned b = __float_as_uint(xh) & 0x7FFFFFFFu;
             mx = b > mx ? b : mx;
-            if (a.j == a.L) fs = fma(a.w_out[m], x, fs);
+            if (a.j == a.L) fs = fma(a.w_out[m], (double)xh + (double)xl, fs);
         }
     }
     if (a.j == a.L) {
@@ -521,26 +551,27 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         if (tid == 0) {
             double f = 0.0;
             for (int w = 0; w < kW; ++w) f += fred[w];
-            float4 *fp = reinterpret_cast<float4 *>(row) + a.N, *fq = fp + (a.N + 1);
-            float4 fh = *fp, fl = *fq;
-            pair_add(fh.x, fl.x, f * at0);
-            pair_add(fh.y, fl.y, f * at1);
-            pair_add(fh.z, fl.z, f * at2);
-            pair_add(fh.w, fl.w, f * at3);
-            *fp = fh;
-            *fq = fl;
+            float4 fh = dst[a.N], fl = dst[lo0 + a.N];
+            pair_add(fh.x, fl.x, f * ((double)ah[0] + (double)al[0]));
+            pair_add(fh.y, fl.y, f * ((double)ah[1] + (double)al[1]));
+            pair_add(fh.z, fl.z, f * ((double)ah[2] + (double)al[2]));
+            pair_add(fh.w, fl.w, f * ((double)ah[3] + (double)al[3]));
+            dst[a.N] = fh;
+            dst[lo0 + a.N] = fl;
         }
         return;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        const unsigned v = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = v > mx ? v : mx;
     }
     if (lane == 0) red[wid] = mx;
     __syncthreads();
-    unsigned long long m2 = 0ull;
+    unsigned m2 = 0u;
     for (int w = 0; w < kW; ++w) m2 = red[w] > m2 ? red[w] : m2;
-    const int e = col_exponent(m2);
+    // |hi + lo| <= |hi| (1 + 2^-24): one binade of headroom above the largest |hi|
+    const int be = (int)(m2 >> 23);
+    const int e = m2 == 0u ? 0 : (be == 0 ? -126 : be - 127 + 1);
     if (tid == 0) a.eBout[i] = e;
     for (int k0 = 2 * tid; k0 < a.Kp; k0 += 2 * kOzPrepThreads) {
         unsigned dig[kOzPlanes];
@@ -550,7 +581,7 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
         for (int hh = 0; hh < 2; ++hh) {
             const int k = k0 + hh;
             if (k >= a.nj) continue;
-            long long x = fixed62(r1v[k], e);
+            long long x = fixed62f(r1v[k], e) + fixed62f(r1v[a.nj + k], e);
 #pragma unroll
             for (int t = 0; t < kOzPlanes; ++t) {
                 const int sh = 56 - 6 * t;
@@ -1372,6 +1403,9 @@ cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list
             pp.keys = cells.keys;
             pp.kw = cells.kw;
             pp.list = list + b0;
+            pp.parent = cells.parent;
+            pp.prev_rows = reinterpret_cast<const float *>(prev_rows);
+            pp.prev0 = prev0;
             pp.rows = reinterpret_cast<float *>(rows);
             pp.cell0 = cell0;
             pp.rstride = rstride;
@@ -1395,7 +1429,7 @@ cudaError_t oz_rank1(const OzNet &net, const R1Cells &cells, const int32_t *list
             pp.it_l = r.it_l;
             pp.it_k = r.it_k;
             pp.it_a = r.it_a;
-            oz_r1_prep_kernel<<<(unsigned)pc, kOzPrepThreads, sizeof(double) * net.width[j], st>>>(pp);
+            oz_r1_prep_kernel<<<(unsigned)pc, kOzPrepThreads, 2 * sizeof(float) * net.width[j], st>>>(pp);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
