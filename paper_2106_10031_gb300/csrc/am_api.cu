@@ -113,8 +113,9 @@ struct am_ctx {
     int oz_rank1_period = 0;      // rank-1 compose: full compose every this many generations (0 = 8)
     int clip_kernel = 0;          // sliced march: 0 warp-per-cell clip with block fallback, 1 block kernel
     int check_kernel = 0;         // sliced march, warp clip: 0 check in the warp, 1 dense check on the tensor cores
-    int32_t *fb_list = nullptr;   // the warp clip's fallback cells (one chunk of a level) and their count
+    int32_t *fb_list = nullptr;   // the warp clip's fallback cells (one level) and their count
     unsigned long long *fb_count = nullptr;
+    unsigned long long *clip_work = nullptr;   // the warp clip's cell counter (zeroed before each launch)
     CheckRec *chk = nullptr;      // the tensor-core check's records (one chunk), their count and status
     unsigned long long *chk_count = nullptr;
     int *chk_status = nullptr;
@@ -402,6 +403,7 @@ void am_destroy(am_ctx *ctx)
         if (ctx->lv_rows[b]) cudaFree(ctx->lv_rows[b]);
     if (ctx->fb_list) cudaFree(ctx->fb_list);
     if (ctx->fb_count) cudaFree(ctx->fb_count);
+    if (ctx->clip_work) cudaFree(ctx->clip_work);
     if (ctx->chk) cudaFree(ctx->chk);
     if (ctx->chk_count) cudaFree(ctx->chk_count);
     if (ctx->chk_status) cudaFree(ctx->chk_status);
@@ -982,6 +984,7 @@ static am_status ensure_r1_scratch(am_ctx *ctx)
     r.item_cap = items;
     CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * ctx->oz.batch_cells));
     CU(cudaMalloc(&ctx->fb_count, sizeof(unsigned long long)));
+    CU(cudaMalloc(&ctx->clip_work, sizeof(unsigned long long)));
     CU(cudaMalloc(&ctx->chk, sizeof(CheckRec) * ctx->oz.batch_cells));
     CU(cudaMalloc(&ctx->chk_count, sizeof(unsigned long long)));
     CU(cudaMalloc(&ctx->chk_status, sizeof(int) * ctx->oz.batch_cells));
@@ -1014,8 +1017,12 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
     const OzNet view = oz_view(nh);
     const int L = nh.dev.L, N = nh.dev.N;
     const int64_t nl = f1 - f0;
-    const int64_t chunk = ctx->oz.batch_cells;
-    const int nchunk = (int)((nl + chunk - 1) / chunk);
+    const int64_t chunk = ctx->oz.batch_cells;           // the compose's batch
+    const bool warp_clip = ctx->clip_kernel == 0 && ma.candidates != kCandNone && N <= kMaxNeurons;
+    // the proposal and the clip take the whole level in one launch each (the warp clip draws its
+    // cells from a counter), except with the tensor-core check, whose records hold one batch
+    const int64_t cchunk = warp_clip && ctx->check_kernel != 1 ? std::max<int64_t>(nl, 1) : chunk;
+    const int nchunk = (int)((nl + cchunk - 1) / cchunk);
     while ((int)ctx->oz_ev.size() < 2 + 3 * nchunk) {
         cudaEvent_t e = nullptr;
         CU(cudaEventCreate(&e));
@@ -1039,8 +1046,8 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
         CU(cudaMalloc(&ctx->fb_list, sizeof(int32_t) * cap));
         r.list_cap = cap;
     }
-    const bool warp_clip = ctx->clip_kernel == 0 && ma.candidates != kCandNone && N <= kMaxNeurons;
     if (warp_clip) CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
+    if (prop_tc) CU(prop_tc_grow(ctx->prop.tc, (int)cchunk));
     const int period = ctx->oz_rank1_period > 0 ? ctx->oz_rank1_period : 8;
     int64_t launches = 0;
     cudaEvent_t *ev = ctx->oz_ev.data();
@@ -1081,7 +1088,7 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
     CU(cudaEventRecord(ev[1], ctx->stream));
     const int64_t rstride = 8 * (int64_t)(N + 1);         // floats per cell
     for (int b = 0; b < nchunk; ++b) {
-        const int64_t c0 = f0 + b * chunk, c1 = std::min<int64_t>(f1, c0 + chunk);
+        const int64_t c0 = f0 + b * cchunk, c1 = std::min<int64_t>(f1, c0 + cchunk);
         CU(cudaEventRecord(ev[2 + 3 * b], ctx->stream));
         ma.scores_in = nullptr;
         if (prop_tc) {
@@ -1144,8 +1151,11 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
                 ctx->stats.cell_launches += 2;
                 launches += 2;
             } else {
+                CU(cudaMemsetAsync(ctx->clip_work, 0, sizeof(unsigned long long), ctx->stream));
+                ma.work = ctx->clip_work;
                 launch_clip_warp(ma, ctx->stream);
                 CU(cudaGetLastError());
+                ma.work = nullptr;
             }
             ctx->stats.cell_launches += 1;
             launches += 1;

@@ -267,12 +267,15 @@ __device__ bool wcheck(const MarchArgs &a, WarpSh &S, const WRows &rv, int N, in
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     const int NC = N + kBoxPlanes;
+    const float delta = (float)a.delta * 1.01f;
     bool fallback = false;
     while (true) {
         for (int i = lane; i < m; i += 32) {
             const double *v = S.pv[buf][i];
-            S.vf[i][0] = (float)v[0]; S.vf[i][1] = (float)v[1]; S.vf[i][2] = (float)v[2];
-            S.vf[i][3] = (float)fmax(1.0, fmax(fabs(v[0]), fmax(fabs(v[1]), fabs(v[2])))) * 1.0001f;
+            const float x = (float)v[0], y = (float)v[1], z = (float)v[2];
+            S.vf[i][0] = x; S.vf[i][1] = y; S.vf[i][2] = z;
+            // max(1, |v|_inf) from the rounded coordinates (each within half an ulp of |v|'s)
+            S.vf[i][3] = fmaxf(1.0f, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)))) * 1.0001f;
         }
         if (lane == 0) S.nviol = 0;
         __syncwarp();
@@ -294,7 +297,7 @@ __device__ bool wcheck(const MarchArgs &a, WarpSh &S, const WRows &rv, int N, in
             const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
             if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
             const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
-            const float band = (float)a.delta * sqrtf(n2) * 1.01f;   // delta |r|: the oracle's tolerance band
+            const float band = delta * sqrtf(n2);       // delta |r|: the oracle's tolerance band
             bool viol = false;
             for (int i = 0; i < m; ++i) {
                 const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
@@ -380,12 +383,21 @@ __device__ bool wemit(const MarchArgs &a, WarpSh &S, int64_t cell, int net_id, i
             v[0] = S.pv[buf][i][0]; v[1] = S.pv[buf][i][1]; v[2] = S.pv[buf][i][2];
         }
         const unsigned long long h = __ldcg(ar.hash + cell);
+        // the entry point of each neighbour (the midpoint of the shared edge), one edge per lane,
+        // kept in the FP32 polygon's buffer (buf ^ 1 is free: the face is in buf)
+        float (*mid)[3] = S.pf[buf ^ 1];
+        for (int i = lane; i < m; i += 32) {
+            const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1 == m ? 0 : i + 1];
+            mid[i][0] = (float)(0.5 * (p[0] + q[0]));
+            mid[i][1] = (float)(0.5 * (p[1] + q[1]));
+            mid[i][2] = (float)(0.5 * (p[2] + q[2]));
+        }
+        __syncwarp();
         for (int i = 0; i < m; ++i) {
             const int e = S.pe[buf][i];
             if (e >= N) continue;
-            const double *p = S.pv[buf][i], *q = S.pv[buf][i + 1 == m ? 0 : i + 1];
-            insert_neighbor_warp(ar, S.key, cell, net_id, (unsigned)e, h ^ ar.zob[e], (float)(0.5 * (p[0] + q[0])),
-                                 (float)(0.5 * (p[1] + q[1])), (float)(0.5 * (p[2] + q[2])), false);
+            insert_neighbor_warp(ar, S.key, cell, net_id, (unsigned)e, h ^ ar.zob[e], mid[i][0], mid[i][1], mid[i][2],
+                                 false);
         }
     }
     return emit != 0;
@@ -404,7 +416,16 @@ __global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
     const Arena &ar = a.ar;
     unsigned long long n_solved = 0, n_empty = 0, n_fix = 0, n_cuts = 0, n_close = 0, n_fb = 0;
     const int64_t stride = (int64_t)gridDim.x * kWW;
-    for (int64_t cell = a.begin + (int64_t)blockIdx.x * kWW + (threadIdx.x >> 5); cell < a.end; cell += stride) {
+    // with a.work the warps take cells one at a time from a shared counter (cells differ in
+    // their cost: the cuts, the fix-up rounds), else in a fixed stride
+    auto next = [&](int64_t cur) -> int64_t {
+        if (!a.work) return cur + stride;
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.work, 1ull);
+        return a.begin + (int64_t)__shfl_sync(FULL, t, 0);
+    };
+    for (int64_t cell = a.work ? next(0) : a.begin + (int64_t)blockIdx.x * kWW + (threadIdx.x >> 5); cell < a.end;
+         cell = next(cell)) {
         if (__ldcg(ar.nverts + cell) == -2) continue;          // a duplicate seed id: never solved
         const int net_id = __ldcg(ar.net + cell);
         const int N = a.nets[net_id].N;
@@ -611,17 +632,29 @@ __global__ void __launch_bounds__(kWW * 32) clip_warp_finish_kernel(MarchArgs a)
     }
 }
 
+static int g_clip_resident = 0;       // clip_warp_kernel blocks resident on the whole GPU at once
+
 cudaError_t prepare_clip_warp()
 {
     cudaError_t e = cudaFuncSetAttribute(clip_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(clip_warp_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
+    e = cudaFuncSetAttribute(clip_warp_finish_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem_bytes());
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clip_warp_kernel, kWW * 32, warp_smem_bytes());
+    if (e != cudaSuccess) return e;
+    g_clip_resident = std::max(1, sms * per_sm);
+    return cudaSuccess;
 }
 
 void launch_clip_warp(const MarchArgs &a, cudaStream_t st)
 {
     const int64_t n = a.end - a.begin;
-    const int grid = (int)std::min<int64_t>((n + kWW - 1) / kWW, 152 * 64);
+    // with a work counter: one resident wave that drains the cells; else one warp per cell
+    const int64_t cap = a.work && g_clip_resident > 0 ? g_clip_resident : 152 * 64;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + kWW - 1) / kWW, cap));
     clip_warp_kernel<<<grid, kWW * 32, warp_smem_bytes(), st>>>(a);
 }
 

@@ -46,6 +46,8 @@ struct MarchArgs {
     const unsigned long long *list_count;   // [begin, end)) instead of the whole range
     int32_t *fb_list;                 // warp clip: cells it hands to the block kernel, and their count
     unsigned long long *fb_count;
+    unsigned long long *work;         // warp clip: zero before the launch; the warps take cells begin + the
+                                      // counter's next value (null: a fixed stride over a one-warp-per-cell grid)
     CheckRec *chk;                    // warp clip with the dense check on the tensor cores: the clipped
     unsigned long long *chk_count;    // polygons it hands to check_tc (null: the warp checks them itself)
     const int *chk_status;            // finish pass: per record 0 = every row holds, else the block kernel
@@ -172,6 +174,9 @@ bool prop_tc_shape_ok(int n_in, int hidden, int n_out);
 cudaError_t prop_tc_alloc(PropTC &t, int n_in, int hidden, int n_out, int max_rows, const __nv_bfloat16 *W2,
                           const __nv_bfloat16 *W3);
 void prop_tc_free(PropTC &t);
+// room for at least rows cells in the activation and score buffers (the tensor maps over them are
+// encoded again; the weights and their maps are kept)
+cudaError_t prop_tc_grow(PropTC &t, int rows);
 void prop_tc_sync_weights(PropTC &t, const float *W1, cudaStream_t st);
 cudaError_t prop_tc_pack(const PropTC &t, const float *X, int rows, cudaStream_t st);
 cudaError_t prop_tc_features(const PropTC &t, const PropFeatures &f, cudaStream_t st);

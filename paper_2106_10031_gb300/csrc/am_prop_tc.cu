@@ -318,6 +318,28 @@ void prop_tc_free(PropTC &t)
     t = PropTC{};
 }
 
+cudaError_t prop_tc_grow(PropTC &t, int rows)
+{
+    if (!t.ok || rows <= t.max_rows) return cudaSuccess;
+    const int cap = ((rows + rows / 4 + kPM - 1) / kPM) * kPM;
+    for (void *p : {(void *)t.X, (void *)t.H1, (void *)t.H2, (void *)t.scores})
+        if (p) cudaFree(p);
+    t.X = t.H1 = t.H2 = t.scores = nullptr;
+    t.ok = false;
+    cudaError_t e;
+    if ((e = cudaMalloc(&t.X, sizeof(__nv_bfloat16) * (size_t)cap * kPBK))) return e;
+    if ((e = cudaMalloc(&t.H1, sizeof(__nv_bfloat16) * (size_t)cap * t.hidden))) return e;
+    if ((e = cudaMalloc(&t.H2, sizeof(__nv_bfloat16) * (size_t)cap * t.hidden))) return e;
+    if ((e = cudaMalloc(&t.scores, sizeof(__nv_bfloat16) * (size_t)cap * t.n_out))) return e;
+    auto *m = reinterpret_cast<CUtensorMap *>(t.maps);
+    if ((e = encode(&m[0], t.X, kPBK, cap, kPM))) return e;
+    if ((e = encode(&m[1], t.H1, t.hidden, cap, kPM))) return e;
+    if ((e = encode(&m[2], t.H2, t.hidden, cap, kPM))) return e;
+    t.max_rows = cap;
+    t.ok = true;
+    return cudaSuccess;
+}
+
 void prop_tc_sync_weights(PropTC &t, const float *W1, cudaStream_t st)
 {
     if (!t.ok) return;
