@@ -757,6 +757,7 @@ static am_status run_seed(am_ctx *ctx, int net_id, int n_rays, double R, int *n_
     a.seed_x = ctx->d_seed_x;
     a.seed_ok = ctx->d_seed_ok;
     a.n_new = d_new;
+    a.df = ctx->nets[net_id].dev.fp64_only ? 0 : 1;
     launch_seed(a, ctx->stream);
     CU(cudaGetLastError());
     ctx->stats.kernel_launches += 2;
@@ -857,6 +858,7 @@ am_status am_seed_pairs(am_ctx *ctx, int net_id, const double *h_points, int n_p
     p.origins = ctx->d_rays;
     p.dirs = ctx->d_rays + 3 * (size_t)ctx->seed_cap;
     p.n_pairs = d_np;
+    p.df = ctx->nets[net_id].dev.fp64_only ? 0 : 1;
     launch_pairs(p, ctx->stream);
     CU(cudaGetLastError());
     ctx->stats.kernel_launches += 2;

@@ -114,6 +114,8 @@ struct SeedArgs {
     double *seed_x;                 // device, n_rays x 3
     int *seed_ok;                   // device, n_rays: 1 ok, -4 no sign change, -5 no common cell
     unsigned long long *n_new;      // device counter of new live seed cells
+    int df;                         // 1: the double-float dichotomy (nets without hidden shortcuts,
+                                    // pooling or leaky units), 0: FP64
 };
 cudaError_t prepare_seed_kernels(int max_n, int max_w);
 void launch_seed(const SeedArgs &a, cudaStream_t st);
@@ -144,6 +146,7 @@ struct PairArgs {
     int max_n, max_w;
     double *origins, *dirs;         // device, max_pairs x 3 each (outputs)
     int *n_pairs;                   // device, 1 (output)
+    int df;                         // 1: F in double-float (as SeedArgs.df), 0: FP64
 };
 void launch_pairs(const PairArgs &a, cudaStream_t st);
 

@@ -287,6 +287,259 @@ __global__ void __launch_bounds__(kSeedThreads) trace_kernel(TraceArgs a)
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// The same forward pass in double-float arithmetic, kDfPts points per block, for nets without
+// hidden shortcuts, pooling or leaky units: the pairs (hi, lo) of FP32 words carry about 44 bits
+// (the product of two pairs split exactly by an FMA, sums by TwoSum), so F and the pattern bits
+// agree with an FP64 evaluation wherever they are not within ~1e-12 of zero.  Each weight pair
+// is read once per block for all its points, and the arithmetic runs on the FP32 pipes (this
+// part's FP64 pipe is 1/64 of them).
+
+constexpr int kDfPts = 8;                  // points per block
+constexpr int kDfW = kSeedThreads / 32;
+
+__host__ __device__ inline int df_seed_smem_bytes(int max_n, int max_w)
+{
+    const int words = (max_n + 31) / 32;
+    return 2 * max_w * 2 * kDfPts * (int)sizeof(float)           // two layers' outputs: [j][hi x 8 | lo x 8]
+           + 3 * kDfPts * words * (int)sizeof(unsigned)          // patterns: the bracket's ends, the midpoint
+           + kDfPts * 8 * (int)sizeof(float)                     // the points as pairs
+           + kDfPts * kDfW * 2 * (int)sizeof(float)              // partial sums of F
+           + kDfPts * (int)sizeof(double) + 64;
+}
+
+struct DfSm {
+    float *h[2];                // layer outputs, element (j, p): hi at [16 j + p], lo at [16 j + 8 + p]
+    unsigned *blo, *bhi, *bm;   // patterns, point p at [p words]
+    float *xp;                  // point p: [xh, yh, zh, xl, yl, zl] at [8 p]
+    float *red;
+    double *F;
+};
+
+__device__ inline DfSm df_carve(unsigned char *base, int max_n, int max_w)
+{
+    const int words = (max_n + 31) / 32;
+    DfSm s;
+    float *f = reinterpret_cast<float *>(base);
+    s.h[0] = f;
+    s.h[1] = f + 16 * max_w;
+    unsigned *u = reinterpret_cast<unsigned *>(f + 32 * max_w);
+    s.blo = u;
+    s.bhi = u + kDfPts * words;
+    s.bm = u + 2 * kDfPts * words;
+    s.xp = reinterpret_cast<float *>(u + 3 * kDfPts * words);
+    s.red = s.xp + 8 * kDfPts;
+    s.F = reinterpret_cast<double *>(((uintptr_t)(s.red + 2 * kDfW * kDfPts) + 15) & ~(uintptr_t)15);
+    return s;
+}
+
+// (sh, sl) += (ah + al)(zh + zl): TwoProd of the hi words by FMA, the cross terms into the
+// error, TwoSum into the sum
+__device__ __forceinline__ void dfs_fma(float &sh, float &sl, float ah, float al, float zh, float zl)
+{
+    const float p = __fmul_rn(ah, zh);
+    float pe = __fmaf_rn(ah, zh, -p);
+    pe = __fmaf_rn(ah, zl, pe);
+    pe = __fmaf_rn(al, zh, pe);
+    const float t = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, pe));
+}
+
+__device__ __forceinline__ void dfs_add(float &sh, float &sl, float bh, float bl)
+{
+    const float t = __fadd_rn(sh, bh);
+    const float bp = __fsub_rn(t, sh);
+    const float te = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(bh, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(te, bl));
+}
+
+// point p of the block at x (thread p): its coordinates as pairs
+__device__ __forceinline__ void df_set_point(const DfSm &s, int p, const double *x)
+{
+    for (int c = 0; c < 3; ++c) {
+        const float h = (float)x[c];
+        s.xp[8 * p + c] = h;
+        s.xp[8 * p + 3 + c] = (float)(x[c] - (double)h);
+    }
+}
+
+// F at the block's kDfPts points (s.xp; the caller sets every point, unused ones anywhere
+// finite) into s.F, and their patterns (Def. 2) into bits[p words].  Every thread calls it.
+__device__ void df_forward_batch(const NetDev &net, const DfSm &s, unsigned *bits)
+{
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int words = (net.N + 31) / 32;
+    for (int w = tid; w < kDfPts * words; w += T) bits[w] = 0u;
+    __syncthreads();
+    for (int l = 1; l <= net.L; ++l) {
+        const int nl = net.width[l], np = l > 1 ? net.width[l - 1] : 0, rl = net.row0[l];
+        const float *Ch = net.Clhi[l], *Cc = net.Cllo[l];
+        const float *Ah = net.AThi[l], *Al = net.ATlo[l];
+        const float *ph = s.h[(l - 1) & 1];
+        float *out = s.h[l & 1];
+        for (int k = tid; k < nl; k += T) {
+            float sh[kDfPts], sl[kDfPts];
+            const float bh = Ch[4 * k + 3], bl = Cc[4 * k + 3];
+#pragma unroll
+            for (int p = 0; p < kDfPts; ++p) { sh[p] = bh; sl[p] = bl; }
+            for (int c = 0; c < 3; ++c) {                // the input columns (layer 1, and skip layers)
+                const float wh = Ch[4 * k + c], wl = Cc[4 * k + c];
+                if (wh == 0.0f && wl == 0.0f) continue;
+#pragma unroll
+                for (int p = 0; p < kDfPts; ++p) dfs_fma(sh[p], sl[p], wh, wl, s.xp[8 * p + c], s.xp[8 * p + 3 + c]);
+            }
+            for (int j = 0; j < np; ++j) {
+                const float ah = __ldg(Ah + (size_t)j * nl + k), al = __ldg(Al + (size_t)j * nl + k);
+                const float4 *hj = reinterpret_cast<const float4 *>(ph + 16 * j);
+                const float4 h0 = hj[0], h1 = hj[1], l0 = hj[2], l1 = hj[3];
+                const float zh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                const float zl[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+                for (int p = 0; p < kDfPts; ++p) dfs_fma(sh[p], sl[p], ah, al, zh[p], zl[p]);
+            }
+#pragma unroll
+            for (int p = 0; p < kDfPts; ++p) {
+                const float t = __fadd_rn(sh[p], sl[p]);       // renormalise: sign(pair) = sign(hi)
+                const float lo = __fsub_rn(sl[p], __fsub_rn(t, sh[p]));
+                const bool act = t > 0.0f;
+                out[16 * k + p] = act ? t : 0.0f;
+                out[16 * k + 8 + p] = act ? lo : 0.0f;
+                if (act) atomicOr(bits + p * words + ((rl + k) >> 5), 1u << ((rl + k) & 31));
+            }
+        }
+        __syncthreads();
+    }
+    const int nL = net.width[net.L];
+    const float *hL = s.h[net.L & 1];
+    float fh[kDfPts], fl[kDfPts];
+#pragma unroll
+    for (int p = 0; p < kDfPts; ++p) { fh[p] = 0.0f; fl[p] = 0.0f; }
+    for (int k = tid; k < nL; k += T) {
+        const float wh = net.w_out_hi[k], wl = net.w_out_lo[k];
+#pragma unroll
+        for (int p = 0; p < kDfPts; ++p) dfs_fma(fh[p], fl[p], wh, wl, hL[16 * k + p], hL[16 * k + 8 + p]);
+    }
+#pragma unroll
+    for (int p = 0; p < kDfPts; ++p) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, fh[p], o), ol = __shfl_xor_sync(0xffffffffu, fl[p], o);
+            dfs_add(fh[p], fl[p], oh, ol);
+        }
+        if (lane == 0) { s.red[2 * (p * kDfW + wid)] = fh[p]; s.red[2 * (p * kDfW + wid) + 1] = fl[p]; }
+    }
+    __syncthreads();
+    if (tid < kDfPts) {
+        double F = net.b_out;
+        for (int w = 0; w < T / 32; ++w) F += (double)s.red[2 * (tid * kDfW + w)] + (double)s.red[2 * (tid * kDfW + w) + 1];
+        s.F[tid] = F;
+    }
+    __syncthreads();
+}
+
+// F at every sample point (random-pair trigger, Sec. 4.3.2), kDfPts points per block
+__global__ void __launch_bounds__(kSeedThreads) sample_eval_df_kernel(PairArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const NetDev &net = a.nets[a.net];
+    const DfSm s = df_carve(smem, a.max_n, a.max_w);
+    const int i0 = blockIdx.x * kDfPts, P = min(kDfPts, a.n_points - i0);
+    if (threadIdx.x < kDfPts) {
+        const int i = i0 + (threadIdx.x < P ? threadIdx.x : 0);
+        const double x[3] = {a.points[3 * i], a.points[3 * i + 1], a.points[3 * i + 2]};
+        df_set_point(s, threadIdx.x, x);
+    }
+    __syncthreads();
+    df_forward_batch(net, s, s.bm);
+    if (threadIdx.x < P) a.F[i0 + threadIdx.x] = s.F[threadIdx.x];
+}
+
+// The dichotomy of seed_kernel for kDfPts rays per block, in double-float (one batched forward
+// pass per halving step for every ray of the block still bracketing more than one cell).
+__global__ void __launch_bounds__(kSeedThreads) seed_df_kernel(SeedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double tlo[kDfPts], thi[kDfPts], flo[kDfPts], fhi[kDfPts], tm[kDfPts];
+    __shared__ int rc[kDfPts], act[kDfPts], side[kDfPts];
+    const NetDev &net = a.nets[a.net];
+    const DfSm s = df_carve(smem, a.max_n, a.max_w);
+    const int tid = threadIdx.x, words = (net.N + 31) / 32;
+    const int r0 = blockIdx.x * kDfPts, P = min(kDfPts, a.n_rays - r0);
+    auto point = [&](int p, double t) {                 // thread p: ray p's point at t (or ray 0's)
+        const int r = r0 + (p < P ? p : 0);
+        const double x[3] = {a.origins[3 * r] + t * a.dirs[3 * r], a.origins[3 * r + 1] + t * a.dirs[3 * r + 1],
+                             a.origins[3 * r + 2] + t * a.dirs[3 * r + 2]};
+        df_set_point(s, p, x);
+    };
+    if (tid < kDfPts) { tlo[tid] = 0.0; thi[tid] = a.R; point(tid, 0.0); }
+    __syncthreads();
+    df_forward_batch(net, s, s.blo);
+    if (tid < kDfPts) { flo[tid] = s.F[tid]; point(tid, a.R); }
+    __syncthreads();
+    df_forward_batch(net, s, s.bhi);
+    if (tid < kDfPts) {
+        fhi[tid] = s.F[tid];
+        const double f0 = flo[tid], f1 = fhi[tid];
+        rc[tid] = tid >= P ? 0 : ((f0 < 0.0 && f1 > 0.0) || (f0 > 0.0 && f1 < 0.0)) ? 1 : -4;
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        if (tid < kDfPts) {
+            int diff = 0;
+            if (rc[tid] == 1)
+                for (int w = 0; w < words; ++w) diff |= s.blo[tid * words + w] != s.bhi[tid * words + w];
+            act[tid] = diff;
+        }
+        __syncthreads();
+        const int any = tid < kDfPts ? act[tid] : 0;
+        if (!__syncthreads_or(any)) break;
+        if (it >= a.max_halvings) {
+            if (tid < kDfPts && act[tid]) rc[tid] = -5;
+            break;
+        }
+        if (tid < kDfPts) {
+            tm[tid] = act[tid] ? 0.5 * (tlo[tid] + thi[tid]) : tlo[tid];
+            point(tid, tm[tid]);
+        }
+        __syncthreads();
+        df_forward_batch(net, s, s.bm);
+        if (tid < kDfPts) {
+            const double fm = s.F[tid];
+            side[tid] = 0;
+            if (act[tid]) {
+                if ((fm < 0.0) == (flo[tid] < 0.0) && fm != 0.0) { tlo[tid] = tm[tid]; flo[tid] = fm; side[tid] = 1; }
+                else { thi[tid] = tm[tid]; fhi[tid] = fm; side[tid] = 2; }
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < kDfPts * words; q += blockDim.x) {
+            const int sd = side[q / words];
+            if (sd == 1) s.blo[q] = s.bm[q];
+            else if (sd == 2) s.bhi[q] = s.bm[q];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int p = 0; p < P; ++p) {
+        const int ray = r0 + p;
+        if (rc[p] == 1) {
+            const double ts = tlo[p] + flo[p] / (flo[p] - fhi[p]) * (thi[p] - tlo[p]);
+            if (tid < 3) a.seed_x[ray * 3 + tid] = a.origins[ray * 3 + tid] + ts * a.dirs[ray * 3 + tid];
+            for (int w = tid; w < a.ar.kw; w += blockDim.x) {
+                const unsigned lo = 2 * w < words ? s.blo[p * words + 2 * w] : 0u;
+                const unsigned hi = 2 * w + 1 < words ? s.blo[p * words + 2 * w + 1] : 0u;
+                a.seed_keys[(size_t)ray * a.ar.kw + w] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+            }
+        } else if (tid == 0) {
+            atomicOr(a.ar.counters + kStatus, rc[p] == -4 ? kStSeedNoSign : kStSeedNoCell);
+        }
+        if (tid == 0) a.seed_ok[ray] = rc[p];
+    }
+}
+
 // F at every sample point (random-pair trigger, Sec. 4.3.2), one block per point.
 __global__ void __launch_bounds__(kSeedThreads) sample_eval_kernel(PairArgs a)
 {
@@ -353,6 +606,10 @@ cudaError_t prepare_seed_kernels(int max_n, int max_w)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(trace_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sample_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int dbytes = df_seed_smem_bytes(max_n, max_w);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sample_eval_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dbytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(seed_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dbytes);
     return e;
 }
 
@@ -363,13 +620,20 @@ void launch_trace(const TraceArgs &a, cudaStream_t st)
 
 void launch_pairs(const PairArgs &a, cudaStream_t st)
 {
-    sample_eval_kernel<<<a.n_points, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
+    if (a.df)
+        sample_eval_df_kernel<<<(a.n_points + kDfPts - 1) / kDfPts, kSeedThreads, df_seed_smem_bytes(a.max_n, a.max_w),
+                                st>>>(a);
+    else
+        sample_eval_kernel<<<a.n_points, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
     pair_build_kernel<<<1, kPairThreads, 0, st>>>(a);
 }
 
 void launch_seed(const SeedArgs &a, cudaStream_t st)
 {
-    seed_kernel<<<a.n_rays, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
+    if (a.df)
+        seed_df_kernel<<<(a.n_rays + kDfPts - 1) / kDfPts, kSeedThreads, df_seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
+    else
+        seed_kernel<<<a.n_rays, kSeedThreads, seed_smem_bytes(a.max_n, a.max_w), st>>>(a);
     seed_insert_kernel<<<(a.n_rays + 127) / 128, 128, 0, st>>>(a);
 }
 
