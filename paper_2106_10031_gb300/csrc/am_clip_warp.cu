@@ -40,7 +40,8 @@ struct WarpSh {
     double pv[2][kWPoly][3];      // FP64 polygon
     float pf[2][kWPoly][3];       // FP32 polygon of the candidate pass
     int pe[2][kWPoly];            // edge planes (edge i: vertex i -> i + 1)
-    float vf[kWPoly][4];          // FP32 vertices and max(1, |v|_inf)
+    float4 vf[kWPoly];            // FP32 vertices (x, y, z) and the vertex term of the check's bound (w)
+    int2 ve[kWPoly];              // the planes of the two edges at each vertex
     float dvb[kWPoly];            // bound on each FP64 vertex's error
     float sq[4][4];               // the initial square's rows (planes N + 6 .. N + 9)
     int viol[kWViol];
@@ -256,6 +257,23 @@ __device__ int wcell_setup(const MarchArgs &a, WarpSh &S, int64_t cell, int N, W
     return m;
 }
 
+// A close call of the FP32 test: row k at the FP64 vertex v6 from the exact pair, against the
+// vertex's own error (|r|_1 dvb), the tolerance band and the FP64 evaluation's rounding.
+// Returns 1 when the row is violated, 2 when the vertex is within the band (the FP64 path
+// decides), 0 when it holds.  Out of line: the FP32 test decides nearly every pair.
+__device__ __noinline__ int wclose(const WRows &rv, int k, const double *v6, float rl1, float dvb, float delta)
+{
+    double r6[4];
+    rv.f64(k, r6);
+    const float4 h = rv.hi(k);
+    const float band = delta * sqrtf(h.x * h.x + h.y * h.y + h.z * h.z);   // delta |r|: the tolerance band
+    const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
+    const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
+    const double B6 = (double)rl1 * 1.0001 * (double)dvb + (double)band + 1e-15 * m6;
+    if (s6 > B6) return 1;
+    return s6 >= -B6 ? 2 : 0;
+}
+
 // The certified all-row check of the polygon in buffer buf (FP64 vertices): every row at every
 // vertex in FP32 with a bound, close calls in FP64 from the exact pair; violated rows are cut in
 // (FP64) and the check repeats, at most kWMaxFix rounds.  Returns true when the cell must go to
@@ -273,59 +291,64 @@ __device__ bool wcheck(const MarchArgs &a, WarpSh &S, const WRows &rv, int N, in
         for (int i = lane; i < m; i += 32) {
             const double *v = S.pv[buf][i];
             const float x = (float)v[0], y = (float)v[1], z = (float)v[2];
-            S.vf[i][0] = x; S.vf[i][1] = y; S.vf[i][2] = z;
-            // max(1, |v|_inf) from the rounded coordinates (each within half an ulp of |v|'s)
-            S.vf[i][3] = fmaxf(1.0f, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)))) * 1.0001f;
+            // the bound on the FP32 test of row r at this vertex (evaluation, the dropped lo words,
+            // the vertex rounded to FP32: 8.5 u (|r|_1 |v|_inf + |r_3|); the FP64 vertex's own error:
+            // |r|_1 dvb) is |r|_1 w + c_r with w = 8.5 u max(1, |v|_inf) + dvb and c_r = 8.5 u |r_3|
+            // + delta |r| (|r . v| <= |r|_1 |v|_inf; each coordinate within half an ulp of v's)
+            const float X = fmaxf(1.0f, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z)))) * 1.0001f;
+            S.vf[i] = make_float4(x, y, z, __fmaf_ru(8.5f * kWU, X, S.dvb[i]));
+            S.ve[i] = make_int2(S.pe[buf][i == 0 ? m - 1 : i - 1], S.pe[buf][i]);
         }
         if (lane == 0) S.nviol = 0;
         __syncwarp();
         bool amb = false;
         int close = 0;
         for (int k0 = lane; k0 < NC; k0 += 32 * 4) {
-          float4 rr[4];
+            float4 rr[4];
+            float rl1[4], cr[4];
+            bool viol[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-              const int k = k0 + 32 * u;
-              rr[u] = k < N ? __ldg(rv.p + k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
-          }
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + 32 * u;
+                rr[u] = k < N ? __ldg(rv.p + k) : (k < NC ? rv.hi(k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+            }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int k = k0 + 32 * u;
-            if (k >= NC) break;
-            const float4 r4 = rr[u];
-            const float r[4] = {r4.x, r4.y, r4.z, r4.w};
-            const float n2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-            if (n2 == 0.0f) continue;                  // zero normal: constant row, holds in its own cell
-            const float rl1 = fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]);
-            const float band = delta * sqrtf(n2);       // delta |r|: the oracle's tolerance band
-            bool viol = false;
+            for (int u = 0; u < 4; ++u) {
+                const float4 r = rr[u];
+                const float n2 = r.x * r.x + r.y * r.y + r.z * r.z;
+                // a zero normal (a constant row, which holds in its own cell) or no row: skipped
+                rl1[u] = n2 == 0.0f ? -1.0f : fabsf(r.x) + fabsf(r.y) + fabsf(r.z);
+                cr[u] = __fmaf_ru(8.5f * kWU, fabsf(r.w), delta * sqrtf(n2));   // + delta |r|: the tolerance band
+                viol[u] = false;
+            }
             for (int i = 0; i < m; ++i) {
-                const int ea = S.pe[buf][i == 0 ? m - 1 : i - 1], eb = S.pe[buf][i];
-                if (k == ea || k == eb) continue;
-                const float *v = S.vf[i];
-                const float sl = r[0] * v[0] + r[1] * v[1] + r[2] * v[2] + r[3];
-                const float mag = fabsf(r[0] * v[0]) + fabsf(r[1] * v[1]) + fabsf(r[2] * v[2]) + fabsf(r[3]);
-                const float B = __fmaf_ru(8.5f * kWU, mag, __fmaf_ru(rl1, S.dvb[i], band));
-                if (sl > B) { viol = true; continue; }
-                if (sl >= -B) {                        // close call: FP64 from the exact pair
-                    ++close;
-                    double r6[4];
-                    rv.f64(k, r6);
-                    const double *v6 = S.pv[buf][i];
-                    const double s6 = r6[0] * v6[0] + r6[1] * v6[1] + r6[2] * v6[2] + r6[3];
-                    const double m6 = fabs(r6[0] * v6[0]) + fabs(r6[1] * v6[1]) + fabs(r6[2] * v6[2]) + fabs(r6[3]);
-                    const double B6 = (double)rl1 * 1.0001 * (double)S.dvb[i] + (double)band + 1e-15 * m6;
-                    if (s6 > B6) viol = true;
-                    else if (s6 >= -B6) amb = true;    // within the band: the FP64 path counts it
+                const float4 V = S.vf[i];
+                const int2 E = S.ve[i];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (rl1[u] < 0.0f || k == E.x || k == E.y) continue;
+                    const float4 r = rr[u];
+                    const float sl = fmaf(r.x, V.x, fmaf(r.y, V.y, fmaf(r.z, V.z, r.w)));
+                    const float B = __fmaf_ru(rl1[u], V.w, cr[u]);
+                    if (sl > B) { viol[u] = true; continue; }
+                    if (sl >= -B) {                        // close call: FP64 from the exact pair
+                        ++close;
+                        const int c = wclose(rv, k, S.pv[buf][i], rl1[u], S.dvb[i], delta);
+                        viol[u] |= c == 1;
+                        amb |= c == 2;
+                    }
                 }
             }
-            if (viol) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!viol[u]) continue;
+                const int k = k0 + 32 * u;
                 for (int i = 0; i < m; ++i) amb |= S.pe[buf][i] == k;   // a spurious FP32 cut
                 const int p = atomicAdd(&S.nviol, 1);
                 if (p < kWViol) S.viol[p] = k;
                 else amb = true;
             }
-          }
         }
         for (int o = 16; o > 0; o >>= 1) close += __shfl_xor_sync(FULL, close, o);
         cell_close += close;
@@ -407,7 +430,10 @@ __device__ bool wemit(const MarchArgs &a, WarpSh &S, int64_t cell, int net_id, i
 
 int clip_warp_smem_bytes() { return warp_smem_bytes(); }
 
-__global__ void __launch_bounds__(kWW * 32, 3) clip_warp_kernel(MarchArgs a)
+#ifndef AM_CLIP_MIN_BLOCKS
+#define AM_CLIP_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(kWW * 32, AM_CLIP_MIN_BLOCKS) clip_warp_kernel(MarchArgs a)
 {
     extern __shared__ __align__(16) unsigned char wsm[];
     WarpSh &S = reinterpret_cast<WarpSh *>(wsm)[threadIdx.x >> 5];
