@@ -380,7 +380,7 @@ typedef struct {
                                  from the parent's rows (one operand column instead of four, Cor. 1);
                                  every rank1_period-th generation of a chain is composed in full,
                                  which bounds the rounding the updates accumulate.  1 = always in
-                                 full; 0 (default) = 8 */
+                                 full; 0 (default) = 32 */
     int clip_kernel;          /* AM_PREC_SLICED march with candidates: 0 (default) = one warp per cell for
                                  every cell whose tests it decides outright, the block kernel for the
                                  rest; 1 = the block kernel (one block per cell) for every cell */

@@ -110,7 +110,7 @@ struct am_ctx {
     ProposalDev prop;
     OzScratch oz;                 // sliced tensor-core compose (allocated on first use)
     int oz_tile_cells = 0;        // cells per tensor-core tile (0 = default 16)
-    int oz_rank1_period = 0;      // rank-1 compose: full compose every this many generations (0 = 8)
+    int oz_rank1_period = 0;      // rank-1 compose: full compose every this many generations (0 = 32)
     int clip_kernel = 0;          // sliced march: 0 warp-per-cell clip with block fallback, 1 block kernel
     int check_kernel = 0;         // sliced march, warp clip: 0 check in the warp, 1 dense check on the tensor cores
     int32_t *fb_list = nullptr;   // the warp clip's fallback cells (one level) and their count
@@ -1050,7 +1050,7 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
     }
     if (warp_clip) CU(cudaMemsetAsync(ctx->fb_count, 0, sizeof(unsigned long long), ctx->stream));
     if (prop_tc) CU(prop_tc_grow(ctx->prop.tc, (int)cchunk));
-    const int period = ctx->oz_rank1_period > 0 ? ctx->oz_rank1_period : 8;
+    const int period = ctx->oz_rank1_period > 0 ? ctx->oz_rank1_period : 32;
     int64_t launches = 0;
     cudaEvent_t *ev = ctx->oz_ev.data();
     CU(cudaEventRecord(ev[0], ctx->stream));
