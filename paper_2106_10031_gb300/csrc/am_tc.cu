@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(128) oz_r1_init_kernel(R1Init a)
     float4 *dst = reinterpret_cast<float4 *>(a.rows + (c - a.cell0) * a.rstride);
     const int lo0 = a.N + 1;                         // the lo block follows the N + 1 hi words
     const int nc = a.row0[l + 1];                    // rows of layers 1..l
+#pragma unroll 4
     for (int q = threadIdx.x; q < nc; q += blockDim.x) {
         dst[q] = src[q];
         dst[lo0 + q] = src[lo0 + q];
@@ -500,48 +501,73 @@ __global__ void __launch_bounds__(kOzPrepThreads) oz_r1_prep_kernel(R1Prep a)
     }
     unsigned mx = 0u;
     double fs = 0.0;
-    for (int m = tid; m < a.nj; m += kOzPrepThreads) {
-        float xh, xl;
-        if (l == a.j - 1) {
-            const double w = a.ATj[(int64_t)a.it_k[i] * a.nj + m];
-            xh = (float)w;
-            xl = (float)(w - (double)xh);
-        } else {
-            const int64_t o = i * a.Mp + m;
-            const long long acc = a.P[o] + ((a.Q[o] + 32) >> 6);
-            if (a.zero) {                             // consumed: zero for the next product's split-K sums
-                a.P[o] = 0;
-                a.Q[o] = 0;
-            }
-            const int e = a.eA[m] + a.eBin[i] - 48;
-            long long hi_int, lo_int;
-            xh = i64_to_f32(acc, e, &hi_int);
-            xl = i64_to_f32(acc - hi_int, e, &lo_int);
-        }
-        const int r = a.row0j + m;
-        const bool act = key_bit(key, r);
-        const float sg = act ? -1.0f : 1.0f;         // (1 - 2 s) v
-        const float4 h4 = src[r], l4 = src[lo0 + r];
-        float h[4] = {h4.x, h4.y, h4.z, h4.w}, lo[4] = {l4.x, l4.y, l4.z, l4.w};
+    // two rows per thread and pass (n_j = 256 is one pass of 128 threads), every load of both
+    // issued before any arithmetic: the kernel is bound by memory latency
+    for (int m0 = tid; m0 < a.nj; m0 += 2 * kOzPrepThreads) {
+        float4 h4[2], l4[2];
+        long long acc[2] = {0, 0};
+        double w[2] = {0.0, 0.0};
+        int ex[2] = {0, 0};
+        bool ok[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            // (xh + xl)(ah + al) as pp + pe: the exact product of the hi words by FMA, the two
-            // cross terms into its error (xl al, below 2^-48 of the product, is dropped)
-            const float pp = xh * ah[q];
-            float pe = fmaf(xh, ah[q], -pp);
-            pe = fmaf(xh, al[q], pe);
-            pe = fmaf(xl, ah[q], pe);
-            df_add(h[q], lo[q], sg * pp, sg * pe);
-            df_norm(h[q], lo[q]);
+        for (int u = 0; u < 2; ++u) {
+            const int m = m0 + u * kOzPrepThreads;
+            ok[u] = m < a.nj;
+            if (!ok[u]) continue;
+            const int r = a.row0j + m;
+            h4[u] = src[r];
+            l4[u] = src[lo0 + r];
+            if (l == a.j - 1) {
+                w[u] = a.ATj[(int64_t)a.it_k[i] * a.nj + m];
+            } else {
+                const int64_t o = i * a.Mp + m;
+                acc[u] = a.P[o] + ((a.Q[o] + 32) >> 6);
+                ex[u] = a.eA[m];
+            }
         }
-        dst[r] = make_float4(h[0], h[1], h[2], h[3]);
-        dst[lo0 + r] = make_float4(lo[0], lo[1], lo[2], lo[3]);
-        r1v[m] = act ? xh : 0.0f;
-        r1v[a.nj + m] = act ? xl : 0.0f;
-        if (act) {
-            const unsigned b = __float_as_uint(xh) & 0x7FFFFFFFu;
-            mx = b > mx ? b : mx;
-            if (a.j == a.L) fs = fma(a.w_out[m], (double)xh + (double)xl, fs);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            const int m = m0 + u * kOzPrepThreads;
+            float xh, xl;
+            if (l == a.j - 1) {
+                xh = (float)w[u];
+                xl = (float)(w[u] - (double)xh);
+            } else {
+                if (a.zero) {                         // consumed: zero for the next product's split-K sums
+                    const int64_t o = i * a.Mp + m;
+                    a.P[o] = 0;
+                    a.Q[o] = 0;
+                }
+                const int e = ex[u] + a.eBin[i] - 48;
+                long long hi_int, lo_int;
+                xh = i64_to_f32(acc[u], e, &hi_int);
+                xl = i64_to_f32(acc[u] - hi_int, e, &lo_int);
+            }
+            const int r = a.row0j + m;
+            const bool act = key_bit(key, r);
+            const float sg = act ? -1.0f : 1.0f;     // (1 - 2 s) v
+            float h[4] = {h4[u].x, h4[u].y, h4[u].z, h4[u].w}, lo[4] = {l4[u].x, l4[u].y, l4[u].z, l4[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // (xh + xl)(ah + al) as pp + pe: the exact product of the hi words by FMA, the two
+                // cross terms into its error (xl al, below 2^-48 of the product, is dropped)
+                const float pp = xh * ah[q];
+                float pe = fmaf(xh, ah[q], -pp);
+                pe = fmaf(xh, al[q], pe);
+                pe = fmaf(xl, ah[q], pe);
+                df_add(h[q], lo[q], sg * pp, sg * pe);
+                df_norm(h[q], lo[q]);
+            }
+            dst[r] = make_float4(h[0], h[1], h[2], h[3]);
+            dst[lo0 + r] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            r1v[m] = act ? xh : 0.0f;
+            r1v[a.nj + m] = act ? xl : 0.0f;
+            if (act) {
+                const unsigned b = __float_as_uint(xh) & 0x7FFFFFFFu;
+                mx = b > mx ? b : mx;
+                if (a.j == a.L) fs = fma(a.w_out[m], (double)xh + (double)xl, fs);
+            }
         }
     }
     if (a.j == a.L) {
