@@ -99,11 +99,12 @@ def _measured_hbm_peak():
 HBM_PEAK_GBS = _measured_hbm_peak()
 
 
-# DRAM bytes per cell of one clip_warp_kernel launch (sliced, learned candidates, the step's
-# net) from the committed ncu capture (one level of 1120 cells), valid while the kernel source
-# is the one captured; the bench scales it to the cells of an average launch
-TRAFFIC_CAPTURE = {"sha256_prefix": None, "source": "am_clip_warp.cu", "precision": "sliced",
-                   "candidates": "learned", "cells": 1120, "bytes": 80.150528e6 + 3.370240e6}
+# DRAM bytes per cell of clip_warp_kernel (sliced, learned candidates, the step's net) from the
+# committed ncu capture (every clip launch of the first 399,997 cells of the step's march: 15
+# levels), valid while the kernel source is the one captured; the bench scales it to the cells
+# of an average launch
+TRAFFIC_CAPTURE = {"sha256_prefix": "e0e3939a8554252b", "source": "am_clip_warp.cu", "precision": "sliced",
+                   "candidates": "learned", "cells": 399997, "bytes": 27015762432 + 1479644928}
 
 
 def captured_traffic(precision, candidates, cells_per_launch):
@@ -603,7 +604,7 @@ def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
     march (0 = the whole mesh; the FP64 march of all 1.4e7 cells takes about 100 s).  Rooflines
     of the two sliced kernels over their own device time: the compose's useful flops (8 per
     masked multiply-add of Cor. 1, four columns) and issued tensor flops, and the clip's
-    algorithmic bytes (its rows, (N + 1) x 32 B per cell, the key and the face record)."""
+    algorithmic bytes (the FP32 rows its check reads, (N + 1) x 16 B per cell, the key and the face record)."""
     import paper_2106_10031_gb300 as am
     from synth import decoder_net
     mlp = decoder_net()
@@ -643,7 +644,7 @@ def decoder_leg(dev, fp64_cells=2_000_000, reps=1):
                               "the BF16 digit-plane products the compose launched (36 per layer on the padded "
                               "tiles; one column per rank-1 cell, four per full compose)"}
                 kw = (mlp.N + 63) // 64
-                clip_bytes = cells_n * ((mlp.N + 1) * 32 + 8 * kw + 64) + st["corners"] * 28
+                clip_bytes = cells_n * ((mlp.N + 1) * 16 + 8 * kw + 64) + st["corners"] * 28
                 gbs = clip_bytes / (st["ms_clip"] / 1e3) / 1e9
                 out[prec]["clip_roofline"] = {"kernel": "clip_warp_kernel (+ the block kernel on its fallback list)",
                                               "bound": "hbm",
@@ -909,7 +910,7 @@ def run_ours(args, dist):
     # kernel.  The compose on the tensor cores (product + prep kernels) is reported beside it.
     cell_ms, comp_ms = r["cell_ms"] if prec != "sliced" else r["clip_ms"], r["compose_ms"]
     kw = (mlp.N + 63) // 64
-    per_cell = (mlp.N + 1) * 32 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64
+    per_cell = (mlp.N + 1) * 16 + 8 * kw + 64 if prec == "sliced" else 8 * kw + 64
     byts = (st["cells"] * per_cell + st["corners"] * 28) * args.steps
     ach = byts / (cell_ms / 1e3) / 1e9
     if prec == "sliced":
@@ -920,8 +921,8 @@ def run_ours(args, dist):
     launches_per_step = max(1, st["levels"]) if sched == "levels" else 1
     roof = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": HBM_PEAK_GBS, "unit": "GB/s",
             "frac": ach / HBM_PEAK_GBS, "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
-            "counts": "algorithmic bytes: the rows read ((N + 1) x 32 B per cell on the sliced path), the key "
-                      "and the face record (28 B per corner)",
+            "counts": "algorithmic bytes: the FP32 rows the all-row check reads ((N + 1) x 16 B per cell on the "
+                      "sliced path: the hi words of the pairs), the key and the face record (28 B per corner)",
             "units": f"{st['cells']} cells per step in {launches_per_step} launches"}
     roof["traffic"] = captured_traffic(prec, args.candidates, st["cells"] / launches_per_step)
     roof["launch_ms"] = cell_ms / max(1, args.steps) / launches_per_step
