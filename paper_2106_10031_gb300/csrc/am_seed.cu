@@ -367,13 +367,16 @@ __device__ __forceinline__ void df_set_point(const DfSm &s, int p, const double 
     }
 }
 
-// F at the block's kDfPts points (s.xp; the caller sets every point, unused ones anywhere
+// F at the block's first NP points (s.xp; the caller sets each of them, unused ones anywhere
 // finite) into s.F, and their patterns (Def. 2) into bits[p words].  Every thread calls it.
+// NP is 8, 4, 2 or 1: a dichotomy whose other rays are done evaluates only what is left.
+template <int NP>
 __device__ void df_forward_batch(const NetDev &net, const DfSm &s, unsigned *bits)
 {
+    static_assert(NP == 1 || NP == 2 || NP == 4 || NP == 8, "points per pass");
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int words = (net.N + 31) / 32;
-    for (int w = tid; w < kDfPts * words; w += T) bits[w] = 0u;
+    for (int w = tid; w < NP * words; w += T) bits[w] = 0u;
     __syncthreads();
     for (int l = 1; l <= net.L; ++l) {
         const int nl = net.width[l], np = l > 1 ? net.width[l - 1] : 0, rl = net.row0[l];
@@ -382,27 +385,36 @@ __device__ void df_forward_batch(const NetDev &net, const DfSm &s, unsigned *bit
         const float *ph = s.h[(l - 1) & 1];
         float *out = s.h[l & 1];
         for (int k = tid; k < nl; k += T) {
-            float sh[kDfPts], sl[kDfPts];
+            float sh[NP], sl[NP];
             const float bh = Ch[4 * k + 3], bl = Cc[4 * k + 3];
 #pragma unroll
-            for (int p = 0; p < kDfPts; ++p) { sh[p] = bh; sl[p] = bl; }
+            for (int p = 0; p < NP; ++p) { sh[p] = bh; sl[p] = bl; }
             for (int c = 0; c < 3; ++c) {                // the input columns (layer 1, and skip layers)
                 const float wh = Ch[4 * k + c], wl = Cc[4 * k + c];
                 if (wh == 0.0f && wl == 0.0f) continue;
 #pragma unroll
-                for (int p = 0; p < kDfPts; ++p) dfs_fma(sh[p], sl[p], wh, wl, s.xp[8 * p + c], s.xp[8 * p + 3 + c]);
+                for (int p = 0; p < NP; ++p) dfs_fma(sh[p], sl[p], wh, wl, s.xp[8 * p + c], s.xp[8 * p + 3 + c]);
             }
             for (int j = 0; j < np; ++j) {
                 const float ah = __ldg(Ah + (size_t)j * nl + k), al = __ldg(Al + (size_t)j * nl + k);
-                const float4 *hj = reinterpret_cast<const float4 *>(ph + 16 * j);
-                const float4 h0 = hj[0], h1 = hj[1], l0 = hj[2], l1 = hj[3];
-                const float zh[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                const float zl[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                float zh[NP], zl[NP];
+                if constexpr (NP >= 4) {
+                    const float4 *hj = reinterpret_cast<const float4 *>(ph + 16 * j);
 #pragma unroll
-                for (int p = 0; p < kDfPts; ++p) dfs_fma(sh[p], sl[p], ah, al, zh[p], zl[p]);
+                    for (int g = 0; g < NP / 4; ++g) {
+                        const float4 h4 = hj[g], l4 = hj[2 + g];
+                        zh[4 * g] = h4.x; zh[4 * g + 1] = h4.y; zh[4 * g + 2] = h4.z; zh[4 * g + 3] = h4.w;
+                        zl[4 * g] = l4.x; zl[4 * g + 1] = l4.y; zl[4 * g + 2] = l4.z; zl[4 * g + 3] = l4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) { zh[p] = ph[16 * j + p]; zl[p] = ph[16 * j + 8 + p]; }
+                }
+#pragma unroll
+                for (int p = 0; p < NP; ++p) dfs_fma(sh[p], sl[p], ah, al, zh[p], zl[p]);
             }
 #pragma unroll
-            for (int p = 0; p < kDfPts; ++p) {
+            for (int p = 0; p < NP; ++p) {
                 const float t = __fadd_rn(sh[p], sl[p]);       // renormalise: sign(pair) = sign(hi)
                 const float lo = __fsub_rn(sl[p], __fsub_rn(t, sh[p]));
                 const bool act = t > 0.0f;
@@ -415,16 +427,16 @@ __device__ void df_forward_batch(const NetDev &net, const DfSm &s, unsigned *bit
     }
     const int nL = net.width[net.L];
     const float *hL = s.h[net.L & 1];
-    float fh[kDfPts], fl[kDfPts];
+    float fh[NP], fl[NP];
 #pragma unroll
-    for (int p = 0; p < kDfPts; ++p) { fh[p] = 0.0f; fl[p] = 0.0f; }
+    for (int p = 0; p < NP; ++p) { fh[p] = 0.0f; fl[p] = 0.0f; }
     for (int k = tid; k < nL; k += T) {
         const float wh = net.w_out_hi[k], wl = net.w_out_lo[k];
 #pragma unroll
-        for (int p = 0; p < kDfPts; ++p) dfs_fma(fh[p], fl[p], wh, wl, hL[16 * k + p], hL[16 * k + 8 + p]);
+        for (int p = 0; p < NP; ++p) dfs_fma(fh[p], fl[p], wh, wl, hL[16 * k + p], hL[16 * k + 8 + p]);
     }
 #pragma unroll
-    for (int p = 0; p < kDfPts; ++p) {
+    for (int p = 0; p < NP; ++p) {
         for (int o = 16; o > 0; o >>= 1) {
             const float oh = __shfl_xor_sync(0xffffffffu, fh[p], o), ol = __shfl_xor_sync(0xffffffffu, fl[p], o);
             dfs_add(fh[p], fl[p], oh, ol);
@@ -432,12 +444,21 @@ __device__ void df_forward_batch(const NetDev &net, const DfSm &s, unsigned *bit
         if (lane == 0) { s.red[2 * (p * kDfW + wid)] = fh[p]; s.red[2 * (p * kDfW + wid) + 1] = fl[p]; }
     }
     __syncthreads();
-    if (tid < kDfPts) {
+    if (tid < NP) {
         double F = net.b_out;
         for (int w = 0; w < T / 32; ++w) F += (double)s.red[2 * (tid * kDfW + w)] + (double)s.red[2 * (tid * kDfW + w) + 1];
         s.F[tid] = F;
     }
     __syncthreads();
+}
+
+// the forward pass of the first n (1..8) points, in the smallest batch that holds them
+__device__ void df_forward_n(const NetDev &net, const DfSm &s, unsigned *bits, int n)
+{
+    if (n > 4) df_forward_batch<8>(net, s, bits);
+    else if (n > 2) df_forward_batch<4>(net, s, bits);
+    else if (n > 1) df_forward_batch<2>(net, s, bits);
+    else df_forward_batch<1>(net, s, bits);
 }
 
 // F at every sample point (random-pair trigger, Sec. 4.3.2), kDfPts points per block
@@ -453,33 +474,34 @@ __global__ void __launch_bounds__(kSeedThreads) sample_eval_df_kernel(PairArgs a
         df_set_point(s, threadIdx.x, x);
     }
     __syncthreads();
-    df_forward_batch(net, s, s.bm);
+    df_forward_n(net, s, s.bm, P);
     if (threadIdx.x < P) a.F[i0 + threadIdx.x] = s.F[threadIdx.x];
 }
 
-// The dichotomy of seed_kernel for kDfPts rays per block, in double-float (one batched forward
-// pass per halving step for every ray of the block still bracketing more than one cell).
+// The dichotomy of seed_kernel for kDfPts rays per block, in double-float: one batched forward
+// pass per halving step of the block's rays that still bracket more than one cell, packed into
+// the first slots so that a step with fewer rays left evaluates fewer points.
 __global__ void __launch_bounds__(kSeedThreads) seed_df_kernel(SeedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double tlo[kDfPts], thi[kDfPts], flo[kDfPts], fhi[kDfPts], tm[kDfPts];
-    __shared__ int rc[kDfPts], act[kDfPts], side[kDfPts];
+    __shared__ int rc[kDfPts], act[kDfPts], side[kDfPts], slot_ray[kDfPts], n_act;
     const NetDev &net = a.nets[a.net];
     const DfSm s = df_carve(smem, a.max_n, a.max_w);
     const int tid = threadIdx.x, words = (net.N + 31) / 32;
     const int r0 = blockIdx.x * kDfPts, P = min(kDfPts, a.n_rays - r0);
-    auto point = [&](int p, double t) {                 // thread p: ray p's point at t (or ray 0's)
+    auto point = [&](int q, int p, double t) {          // slot q: ray p's point at t (rays past P: ray 0)
         const int r = r0 + (p < P ? p : 0);
         const double x[3] = {a.origins[3 * r] + t * a.dirs[3 * r], a.origins[3 * r + 1] + t * a.dirs[3 * r + 1],
                              a.origins[3 * r + 2] + t * a.dirs[3 * r + 2]};
-        df_set_point(s, p, x);
+        df_set_point(s, q, x);
     };
-    if (tid < kDfPts) { tlo[tid] = 0.0; thi[tid] = a.R; point(tid, 0.0); }
+    if (tid < kDfPts) { tlo[tid] = 0.0; thi[tid] = a.R; point(tid, tid, 0.0); }
     __syncthreads();
-    df_forward_batch(net, s, s.blo);
-    if (tid < kDfPts) { flo[tid] = s.F[tid]; point(tid, a.R); }
+    df_forward_n(net, s, s.blo, P);
+    if (tid < kDfPts) { flo[tid] = s.F[tid]; point(tid, tid, a.R); }
     __syncthreads();
-    df_forward_batch(net, s, s.bhi);
+    df_forward_n(net, s, s.bhi, P);
     if (tid < kDfPts) {
         fhi[tid] = s.F[tid];
         const double f0 = flo[tid], f1 = fhi[tid];
@@ -492,33 +514,40 @@ __global__ void __launch_bounds__(kSeedThreads) seed_df_kernel(SeedArgs a)
             if (rc[tid] == 1)
                 for (int w = 0; w < words; ++w) diff |= s.blo[tid * words + w] != s.bhi[tid * words + w];
             act[tid] = diff;
+            side[tid] = 0;
         }
         __syncthreads();
-        const int any = tid < kDfPts ? act[tid] : 0;
-        if (!__syncthreads_or(any)) break;
+        if (tid == 0) {
+            int q = 0;
+            for (int p = 0; p < kDfPts; ++p)
+                if (act[p]) slot_ray[q++] = p;
+            n_act = q;
+        }
+        __syncthreads();
+        const int nact = n_act;
+        if (nact == 0) break;
         if (it >= a.max_halvings) {
             if (tid < kDfPts && act[tid]) rc[tid] = -5;
             break;
         }
-        if (tid < kDfPts) {
-            tm[tid] = act[tid] ? 0.5 * (tlo[tid] + thi[tid]) : tlo[tid];
-            point(tid, tm[tid]);
+        if (tid < nact) {
+            const int p = slot_ray[tid];
+            tm[p] = 0.5 * (tlo[p] + thi[p]);
+            point(tid, p, tm[p]);
         }
         __syncthreads();
-        df_forward_batch(net, s, s.bm);
-        if (tid < kDfPts) {
+        df_forward_n(net, s, s.bm, nact);
+        if (tid < nact) {
+            const int p = slot_ray[tid];
             const double fm = s.F[tid];
-            side[tid] = 0;
-            if (act[tid]) {
-                if ((fm < 0.0) == (flo[tid] < 0.0) && fm != 0.0) { tlo[tid] = tm[tid]; flo[tid] = fm; side[tid] = 1; }
-                else { thi[tid] = tm[tid]; fhi[tid] = fm; side[tid] = 2; }
-            }
+            if ((fm < 0.0) == (flo[p] < 0.0) && fm != 0.0) { tlo[p] = tm[p]; flo[p] = fm; side[p] = 1; }
+            else { thi[p] = tm[p]; fhi[p] = fm; side[p] = 2; }
         }
         __syncthreads();
-        for (int q = tid; q < kDfPts * words; q += blockDim.x) {
-            const int sd = side[q / words];
-            if (sd == 1) s.blo[q] = s.bm[q];
-            else if (sd == 2) s.bhi[q] = s.bm[q];
+        for (int q = tid; q < nact * words; q += blockDim.x) {
+            const int slot = q / words, w = q - slot * words, p = slot_ray[slot];
+            if (side[p] == 1) s.blo[p * words + w] = s.bm[q];
+            else if (side[p] == 2) s.bhi[p * words + w] = s.bm[q];
         }
         __syncthreads();
     }
