@@ -250,7 +250,9 @@ am_status am_release_nets(am_ctx *ctx);
  * affine root in that cell and push its cell into the active set.  h_origins, h_dirs: host,
  * n_rays x 3 FP64.  *n_seeded (may be NULL) receives the number of new seed cells (rays
  * landing in an already seeded cell count once).  AM_ERR_NO_SEED_CELL when no ray
- * produced one. */
+ * produced one.  F and the patterns are evaluated in double-float arithmetic (FP32 pairs,
+ * about 44 bits) for nets without hidden shortcuts, pooling or leaky units, else in FP64: a
+ * sign or a pattern bit can differ from an FP64 evaluation only within about 1e-12 of zero. */
 am_status am_seed(am_ctx *ctx, int net_id, const double *h_origins, const double *h_dirs,
                   int n_rays, double R, int *n_seeded);
 
@@ -269,7 +271,7 @@ am_status am_seed_sphere_trace(am_ctx *ctx, int net_id, const double *h_starts, 
                                int max_steps, double eps, int *n_seeded, double *h_seed_points);
 
 /* Trigger by random-pair dichotomy (Sec. 4.3.2): F is evaluated on the device at every sample
- * (h_points: host, n_points x 3 FP64, drawn by the caller); the r-th sample with F < 0 is
+ * (h_points: host, n_points x 3 FP64, drawn by the caller; in the precision am_seed states); the r-th sample with F < 0 is
  * paired with the r-th sample with F > 0, in sample order, for r < min(#negative, #positive,
  * max_pairs) (samples with F == 0 are not used); each pair's segment from x- to x+ is bisected
  * as in am_seed and its cell pushed.  1 <= n_points, max_pairs <= 2^24.  *n_pairs and
