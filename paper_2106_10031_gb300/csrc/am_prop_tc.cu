@@ -243,11 +243,12 @@ __global__ void prop_features_kernel(PropFeatures f)
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= f.n) return;
     const int64_t cell = f.c0 + i;
+    // the unit face plane in FP32 from the hi and lo words of a_F: the features are BF16 (8
+    // bits), so FP32 carries them with room to spare, and this part's FP64 pipe is narrow
     const float *aF = f.rows + i * f.rstride + 4 * (int64_t)f.N;             // hi words of a_F
     const float *aL = f.rows + i * f.rstride + 4 * (int64_t)(2 * f.N + 1);   // its lo words
-    const double F0 = (double)aF[0] + (double)aL[0], F1 = (double)aF[1] + (double)aL[1],
-                 F2 = (double)aF[2] + (double)aL[2], F3 = (double)aF[3] + (double)aL[3];
-    const double inv = 1.0 / sqrt(F0 * F0 + F1 * F1 + F2 * F2);
+    const float F0 = aF[0] + aL[0], F1 = aF[1] + aL[1], F2 = aF[2] + aL[2], F3 = aF[3] + aL[3];
+    const float inv = rsqrtf(F0 * F0 + F1 * F1 + F2 * F2);
     __nv_bfloat16 *o = f.X + i * kPBK;
     for (int j = lane; j < kPBK; j += 32) {
         float x = 0.0f;
