@@ -1009,10 +1009,11 @@ static am_status ensure_level_rows(am_ctx *ctx, int b, int64_t n)
 // One breadth-first level [f0, f1) of the AM_PREC_SLICED march.  The level's rows are composed on
 // the tensor cores into the level buffer: in full for the cells classified so (and for every
 // cell of the first level of a call), by the rank-1 update from the previous level's rows for the
-// others.  Then per chunk of the level the learned proposal's scores (tensor cores) and the clip
-// (certified FP32 tests on the rows, FP64 where they do not decide), and finally the
-// classification of the cells this level pushed.  Events: oz_ev[0..1] the compose, then three
-// per chunk; *nchunks receives the chunk count.
+// others.  Then the learned proposal's scores (tensor cores) and the clip (certified FP32 tests on
+// the rows, FP64 where they do not decide), per chunk of the level: the whole level in one chunk
+// with the warp clip, batches of oz.batch_cells with the tensor-core check or the block clip; and
+// finally the classification of the cells this level pushed.  Events: oz_ev[0..1] the compose,
+// then three per chunk; *nchunks receives the chunk count.
 static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1, bool prop_tc, int *nchunks)
 {
     const NetHost &nh = ctx->nets[0];
@@ -1162,8 +1163,9 @@ static am_status sliced_level(am_ctx *ctx, MarchArgs &ma, int64_t f0, int64_t f1
             ctx->stats.cell_launches += 1;
             launches += 1;
             if (b == nchunk - 1) {
-                // the level's fallback cells: rows from the level's buffer, nearest candidates (the
-                // proposal's scores cover the last chunk only; the candidates never change the face)
+                // the level's fallback cells: rows from the level's buffer, nearest candidates (with
+                // several chunks the proposal's scores cover the last one only; the candidates never
+                // change the face)
                 MarchArgs mb = ma;
                 mb.begin = f0;
                 mb.end = f1;
